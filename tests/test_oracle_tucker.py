@@ -1,0 +1,246 @@
+"""Pins for the oracle's Tucker algorithms (oracle.tucker) -- CPU only.
+
+Each check is fixed by the paper or by the mathematics, not by the oracle itself:
+* exact recovery of tensors with exact multilinear rank (Alg. 1-3);
+* R-STHOSVD with a full-width sketch equals STHOSVD (the range finder then spans
+  the whole column space);
+* HOSVD factors are the leading eigenvectors of X_(j) X_(j)^T (eigh, a different
+  library route) and obey Thm. lem:mode_err;
+* the STHOSVD equality of Thm. lem:st_mode_err and ||X||^2 - ||G||^2;
+* seed-averaged expectation bounds (Thm. randsvd_err, rhosvd_err, rst_err, pass_error);
+* Table 4 of the paper for the adaptive R-STHOSVD (golden file);
+* SP-STHOSVD invariants of Thm. pass_error: identity submatrix, |A_ij| <= 2,
+  ||A_j||_2 <= g(I_j, l_j), core entries taken from X, COO == dense.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tucker
+from oracle.tensor import frob, multi_ttm, rel_error, ttm, unfold
+from workloads import hilbert, lowrank_plus_noise_np
+
+
+def _proj(A):
+    Q, _ = np.linalg.qr(A)
+    return Q @ Q.T
+
+
+def test_default_order_is_decreasing_size():
+    assert tucker.default_order([10, 30, 20, 30]) == [1, 3, 2, 0]
+
+
+@pytest.mark.parametrize("alg", ["rhosvd", "rsthosvd"])
+def test_exact_multilinear_rank_is_recovered(alg):
+    X = lowrank_plus_noise_np([20, 18, 16], [4, 5, 3], 0.8, 0.0, seed=1)
+    f = getattr(tucker, alg)
+    out = f(X, [4, 5, 3], 3, seed=11)
+    assert rel_error(X, out["core"], out["factors"]) < 1e-13
+    for A in out["factors"]:
+        assert np.abs(A.T @ A - np.eye(A.shape[1])).max() < 1e-14 * 10 * A.shape[1]
+
+
+def test_exact_rank_4way():
+    X = lowrank_plus_noise_np([9, 8, 7, 6], [2, 3, 2, 3], 0.9, 0.0, seed=2)
+    out = tucker.rsthosvd(X, [2, 3, 2, 3], 2, seed=3)
+    assert rel_error(X, out["core"], out["factors"]) < 1e-13
+
+
+def test_full_width_sketch_equals_sthosvd():
+    X = lowrank_plus_noise_np([8, 7, 6], [3, 3, 3], 0.7, 1e-2, seed=4)
+    ranks = [3, 3, 3]
+    Gd, Ad = tucker.sthosvd(X, ranks, rho=[0, 1, 2])
+    # p = I_n - r_n on every mode: ell = I_n for this cubic-ish shape in order 0,1,2
+    out = tucker.rsthosvd(X, ranks, 5, seed=9, rho=[0, 1, 2], clamp=True)
+    for n in range(3):
+        assert np.abs(_proj(out["factors"][n]) - _proj(Ad[n])).max() < 1e-12
+    assert abs(rel_error(X, out["core"], out["factors"]) - rel_error(X, Gd, Ad)) < 1e-13
+
+
+def test_hosvd_factors_are_gram_eigenvectors_and_obey_bound():
+    X = lowrank_plus_noise_np([7, 6, 5], [3, 3, 3], 0.6, 5e-2, seed=5)
+    ranks = [2, 3, 2]
+    G, A = tucker.hosvd(X, ranks)
+    for n in range(3):
+        w, V = np.linalg.eigh(unfold(X, n) @ unfold(X, n).T)
+        V = V[:, np.argsort(w)[::-1][: ranks[n]]]
+        assert np.abs(_proj(A[n]) - V @ V.T).max() < 1e-10
+    err2 = frob(X - multi_ttm(G, A)) ** 2
+    assert err2 <= sum(tucker.delta2(X, ranks)) * (1 + 1e-12)
+
+
+def test_sthosvd_error_equalities():
+    X = lowrank_plus_noise_np([8, 7, 6], [3, 3, 3], 0.6, 5e-2, seed=6)
+    ranks = [2, 2, 3]
+    G, A = tucker.sthosvd(X, ranks, rho=[0, 1, 2])
+    err2 = frob(X - multi_ttm(G, A)) ** 2
+    # sum of successive-iterate differences (Thm. lem:st_mode_err, first equality)
+    Xh_prev, s = X, 0.0
+    for j in range(3):
+        Gj = X
+        for i in range(j + 1):
+            Gj = ttm(Gj, A[i].T, i)
+        Xh = Gj
+        for i in range(j + 1):
+            Xh = ttm(Xh, A[i], i)
+        s += frob(Xh_prev - Xh) ** 2
+        Xh_prev = Xh
+    assert abs(err2 - s) < 1e-12 * frob(X) ** 2
+    assert abs(err2 - (frob(X) ** 2 - frob(G) ** 2)) < 1e-12 * frob(X) ** 2
+    assert err2 <= sum(tucker.delta2(X, ranks)) * (1 + 1e-12)
+
+
+def test_randsvd_expectation_bound():
+    rs = np.random.default_rng(8)
+    m, n, r, p = 40, 60, 5, 4
+    U, _ = np.linalg.qr(rs.standard_normal((m, m)))
+    V, _ = np.linalg.qr(rs.standard_normal((n, m)))
+    s = 0.7 ** np.arange(m)
+    Xm = (U * s) @ V.T
+    bound = (1 + r / (p - 1)) * np.sum(s[r:] ** 2)
+    errs = []
+    from oracle.rng import omega
+    for seed in range(60):
+        Om = omega(seed, 0, 0, np.arange(n), r + p).astype(np.float64)
+        Uh, _, _, info = tucker.randsvd(Xm, r, Om)
+        Q = info["Q"]
+        errs.append(frob(Xm - Q @ (Q.T @ Xm)) ** 2)
+    assert np.mean(errs) <= bound
+    assert min(errs) >= np.sum(s[r + p:] ** 2) * (1 - 1e-9)   # cannot beat rank r+p optimum
+
+
+@pytest.mark.parametrize("alg", ["rhosvd", "rsthosvd"])
+def test_seed_averaged_tensor_bound(alg):
+    X = lowrank_plus_noise_np([12, 11, 10], [6, 6, 6], 0.6, 1e-2, seed=9)
+    ranks, p = [3, 3, 3], 3
+    bound = tucker.randomized_bound(X, ranks, p)
+    f = getattr(tucker, alg)
+    errs = [frob(X - multi_ttm(o["core"], o["factors"]))
+            for o in (f(X, ranks, p, seed=s) for s in range(30))]
+    assert np.mean(errs) <= bound
+    assert np.mean(errs) >= math.sqrt(max(tucker.delta2(X, ranks))) * (1 - 1e-9)
+
+
+def test_rsthosvd_norm_identity_and_projector_lemma():
+    X = lowrank_plus_noise_np([14, 12, 10], [4, 4, 4], 0.7, 1e-2, seed=10)
+    out = tucker.rsthosvd(X, [4, 4, 4], 4, seed=1)
+    G, A = out["core"], out["factors"]
+    err2 = frob(X - multi_ttm(G, A)) ** 2
+    assert err2 / frob(X) ** 2 > 1e-6
+    assert abs(err2 - (frob(X) ** 2 - frob(G) ** 2)) < 1e-11 * frob(X) ** 2
+
+
+def test_hilbert_200_rsthosvd_near_deterministic():
+    X = hilbert([200, 200, 200], offset=1)
+    Gd, Ad = tucker.sthosvd(X, [20, 20, 20], rho=[0, 1, 2])
+    e_det = rel_error(X, Gd, Ad)
+    out = tucker.rsthosvd(X, [20, 20, 20], 5, seed=0, rho=[0, 1, 2])
+    e_r = rel_error(X, out["core"], out["factors"])
+    assert e_det < 1e-12 and e_r < 1e-12
+    assert e_r < 10 * e_det
+
+
+def _table4(golden_dir):
+    rows = []
+    with open(os.path.join(golden_dir, "table4_adaptive_ranks.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            rows.append((int(t[0]), float(t[1]), tuple(int(x) for x in t[2:5])))
+    return rows
+
+
+@pytest.mark.parametrize("b", [1, 8])
+def test_table4_adaptive_ranks(golden_dir, b):
+    rows = _table4(golden_dir)
+    assert len(rows) == 15
+    cache = {}
+    for I, eps, ranks in rows:
+        X = cache.setdefault(I, hilbert([I, I, I], offset=3))
+        out = tucker.adaptive_rsthosvd(X, eps, b, 5, seed=0, rho=[0, 1, 2])
+        got = tuple(A.shape[1] for A in out["factors"])
+        assert got == ranks, (I, eps, got, ranks)
+        assert rel_error(X, out["core"], out["factors"]) <= eps
+
+
+def test_adaptive_rhosvd_meets_tolerance():
+    X = lowrank_plus_noise_np([16, 15, 14], [5, 5, 5], 0.5, 1e-3, seed=12)
+    for eps in (1e-1, 1e-2):
+        out = tucker.adaptive_rhosvd(X, eps, 2, 3, seed=4)
+        assert rel_error(X, out["core"], out["factors"]) <= eps
+
+
+def _sparse_tensor(seed, dims=(30, 28, 26), density=0.08):
+    rs = np.random.default_rng(seed)
+    X = np.zeros(dims)
+    for i in range(1, 9):
+        vecs = [np.where(rs.random(n) < 0.3, rs.random(n), 0.0) for n in dims]
+        X += (4.0 / i ** 2) * np.einsum("i,j,k->ijk", *vecs)
+    X += np.where(rs.random(dims) < density, rs.random(dims), 0.0) * 1e-2
+    return X
+
+
+def test_sp_sthosvd_invariants():
+    X = _sparse_tensor(0)
+    ranks, p = [4, 4, 4], 3
+    out = tucker.sp_sthosvd(X, ranks, p, seed=5)
+    for n, (A, P) in enumerate(zip(out["factors"], out["selected"])):
+        ell = ranks[n] + p
+        assert A.shape == (X.shape[n], ell) and P.size == ell
+        assert np.abs(A[P, :] - np.eye(ell)).max() < 1e-12
+        assert np.abs(A).max() <= 2.0 + 1e-9
+        assert np.linalg.norm(A, 2) <= math.sqrt(1 + 4 * ell * (X.shape[n] - ell))
+    core = X[np.ix_(*out["selected"])]
+    assert np.array_equal(out["core"], core)
+
+
+def test_sp_sthosvd_exact_recovery():
+    rs = np.random.default_rng(3)
+    dims = (24, 22, 20)
+    X = np.zeros(dims)
+    for _ in range(3):
+        X += np.einsum("i,j,k->ijk", *[np.where(rs.random(n) < 0.5, rs.random(n), 0.0) for n in dims])
+    out = tucker.sp_sthosvd(X, [2, 2, 2], 2, seed=1)
+    assert rel_error(X, out["core"], out["factors"]) < 1e-12
+
+
+def test_sp_sthosvd_coo_equals_dense():
+    X = _sparse_tensor(4)
+    idx = np.argwhere(X != 0)
+    vals = X[X != 0]
+    out = tucker.sp_sthosvd(X, [3, 3, 3], 3, seed=2)
+    oc = tucker.sp_sthosvd_coo(idx, vals, X.shape, [3, 3, 3], 3, seed=2)
+    for n in range(3):
+        assert np.array_equal(oc["selected"][n], out["selected"][n])
+        assert np.allclose(oc["factors"][n], out["factors"][n], atol=1e-10)
+    assert np.array_equal(oc["core"], out["core"])
+
+
+def test_sp_sthosvd_seed_averaged_bound():
+    X = _sparse_tensor(1)
+    ranks, p = [3, 3, 3], 3
+    bound = tucker.sp_bound(X, ranks, p, rho=tucker.default_order(X.shape))
+    errs = [frob(X - multi_ttm(o["core"], o["factors"]))
+            for o in (tucker.sp_sthosvd(X, ranks, p, seed=s) for s in range(10))]
+    assert np.mean(errs) <= bound
+
+
+def test_srrqr_condition_and_determinant_growth():
+    rs = np.random.default_rng(2)
+    Q, _ = np.linalg.qr(rs.standard_normal((60, 6)) * np.array([1, 1, 1, 1e-2, 1e-3, 1e-4]))
+    P = tucker.srrqr_select(Q, 2.0)
+    A = Q @ np.linalg.inv(Q[P])
+    mask = np.ones(60, dtype=bool)
+    mask[P] = False
+    assert np.abs(A[mask]).max() <= 2.0 + 1e-12
+    # no single swap can raise |det(P^T Q)| by more than a factor 2
+    d0 = abs(np.linalg.det(Q[P]))
+    for i in np.nonzero(mask)[0][:20]:
+        for j in range(6):
+            S = P.copy()
+            S[j] = i
+            assert abs(np.linalg.det(Q[S])) <= 2.0 * d0 * (1 + 1e-9)

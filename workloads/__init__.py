@@ -1,0 +1,137 @@
+"""Seeded synthetic input tensors shared by the tests, the bench and the oracle runs.
+
+This module holds no step of the compression method: it only builds input
+tensors (and their documented shapes).  Both the CUDA path and the oracle consume
+the bytes it produces, so the two sides always see identical inputs.
+
+Workloads (sizes follow the paper's experiments and the library's benchmark set):
+
+* ``hilbert(dims, offset)``: X(i_1..i_d) = 1 / (i_1 + ... + i_d + offset) with
+  0-based indices.  offset = d gives the paper's 1-based Hilbert tensor (Sec. 6.1,
+  Eq. hilbert); offset = 1 gives the 200^3 tensor 1/(i+j+k+1).
+* ``lowrank_plus_noise``: core of N(0,1) entries scaled by decay^(i_1+...+i_d)
+  (0-based), factors U_n = orthonormal Q of an N(0,1) I_n x r_n matrix, plus
+  N(0,1) noise rescaled to ``noise_rel`` times the Frobenius norm of the signal.
+* ``zipf_coo``: sparse count tensor with per-mode Zipf(s) coordinates,
+  deduplicated, values log(1 + Poisson(lam) + 1).
+
+Tensors are returned column-major (index 1 fastest) as numpy arrays of shape
+(I_1, ..., I_d) with Fortran order, or as torch tensors holding that flat buffer.
+"""
+
+import numpy as np
+
+
+def hilbert(dims, offset, dtype=np.float64):
+    """Hilbert-type tensor 1/(sum of 0-based indices + offset), Fortran order."""
+    dims = [int(x) for x in dims]
+    s = np.zeros(dims, dtype=np.float64, order="F")
+    for n, I in enumerate(dims):
+        shape = [1] * len(dims)
+        shape[n] = I
+        s = s + np.arange(I, dtype=np.float64).reshape(shape)
+    return np.asfortranarray((1.0 / (s + float(offset))).astype(dtype))
+
+
+def lowrank_plus_noise_np(dims, core_dims, decay, noise_rel, seed, dtype=np.float64):
+    """Small-size numpy version of the low-rank + noise workload (CPU tests)."""
+    rs = np.random.default_rng(seed)
+    d = len(dims)
+    core = rs.standard_normal(core_dims)
+    for n, r in enumerate(core_dims):
+        shape = [1] * d
+        shape[n] = r
+        core = core * (float(decay) ** np.arange(r, dtype=np.float64)).reshape(shape)
+    U = [np.linalg.qr(rs.standard_normal((int(dims[n]), int(core_dims[n]))))[0] for n in range(d)]
+    X = core
+    for n in range(d):
+        X = np.moveaxis(np.tensordot(U[n], X, axes=([1], [n])), 0, n)
+    if noise_rel > 0:
+        E = rs.standard_normal(dims)
+        E *= noise_rel * np.linalg.norm(X) / np.linalg.norm(E)
+        X = X + E
+    return np.asfortranarray(X.astype(dtype))
+
+
+def lowrank_plus_noise_torch(dims, core_dims, decay, noise_rel, seed, dtype, device):
+    """Large-size version built with torch on ``device``; returns a flat column-major tensor.
+
+    Steps: factors and core from a CPU generator seeded with ``seed``; the signal
+    G x_1 U_1 ... x_d U_d by successive mode products in float64 on the device
+    (float32 when the tensor exceeds 2^28 elements); noise from a generator on
+    ``device`` seeded with ``seed + 1``.  The flat buffer is X(i_1, ..., i_d) at
+    i_1 + I_1 (i_2 + I_2 (...)).
+    """
+    import torch
+
+    g = torch.Generator(device="cpu").manual_seed(int(seed))
+    d = len(dims)
+    core = torch.randn(*core_dims, generator=g, dtype=torch.float64)
+    for n, r in enumerate(core_dims):
+        shape = [1] * d
+        shape[n] = r
+        core = core * (float(decay) ** torch.arange(r, dtype=torch.float64)).reshape(shape)
+    U = [torch.linalg.qr(torch.randn(int(dims[n]), int(core_dims[n]), generator=g, dtype=torch.float64))[0]
+         for n in range(d)]
+    N = int(np.prod(dims))
+    wdt = torch.float64 if N <= (1 << 28) else torch.float32
+    # torch tensors here use C order with reversed axes: T[i_d, ..., i_1] so that the
+    # flat buffer is column-major in (i_1..i_d).
+    T = core.permute(*reversed(range(d))).contiguous().to(device=device, dtype=wdt)
+    for n in range(d):
+        ax = d - 1 - n
+        Un = U[n].to(device=device, dtype=wdt)
+        T = torch.movedim(torch.tensordot(Un, T, dims=([1], [ax])), 0, ax).contiguous()
+    X = T.reshape(-1).to(dtype)
+    del T
+    if noise_rel > 0:
+        gd = torch.Generator(device=device).manual_seed(int(seed) + 1)
+        E = torch.randn(N, generator=gd, device=device, dtype=torch.float32)
+        sig = torch.linalg.vector_norm(X.to(torch.float64))
+        en = torch.linalg.vector_norm(E.to(torch.float64))
+        X = (X.to(torch.float64 if dtype == torch.float64 else torch.float32)
+             + (E * float(noise_rel * sig / en)).to(X.dtype)).to(dtype)
+        del E
+    return X
+
+
+def zipf_coo(dims, nnz, s, lam, seed, batch=None):
+    """Sparse count tensor: coordinates Zipf(s) per mode (rank k -> index k-1), deduplicated.
+
+    Draws batches of coordinate tuples until ``nnz`` distinct ones exist, keeps
+    the first ``nnz`` distinct in draw order, sorts them lexicographically (mode 1
+    slowest), values log(1 + Poisson(lam) + 1) in float64 stored as float32.
+    Returns (idx int32 array nnz x d, vals float32 array).
+    """
+    rs = np.random.default_rng(seed)
+    dims = [int(x) for x in dims]
+    d = len(dims)
+    cdfs = []
+    for I in dims:
+        w = np.arange(1, I + 1, dtype=np.float64) ** (-float(s))
+        c = np.cumsum(w)
+        cdfs.append(c / c[-1])
+    batch = batch or max(1024, nnz // 2)
+    keys = np.zeros(0, dtype=np.int64)
+    mult = [1] * d
+    for n in range(d - 2, -1, -1):
+        mult[n] = mult[n + 1] * dims[n + 1]
+    while True:
+        cols = [np.minimum(np.searchsorted(cdfs[n], rs.random(batch)), dims[n] - 1).astype(np.int64)
+                for n in range(d)]
+        k = np.zeros(batch, dtype=np.int64)
+        for n in range(d):
+            k += cols[n] * mult[n]
+        keys = np.concatenate([keys, k])
+        _, first = np.unique(keys, return_index=True)
+        if first.size >= nnz:
+            keep = np.sort(first)[:nnz]
+            keys = np.sort(keys[keep])
+            break
+    idx = np.zeros((nnz, d), dtype=np.int32)
+    rem = keys.copy()
+    for n in range(d):
+        idx[:, n] = (rem // mult[n]).astype(np.int32)
+        rem = rem % mult[n]
+    vals = np.log(1.0 + rs.poisson(lam, nnz).astype(np.float64) + 1.0).astype(np.float32)
+    return idx, vals
