@@ -1,0 +1,436 @@
+"""Benchmark: R-STHOSVD time-to-Tucker and TFLOP/s on the dense 1024^3 FP32 workload.
+
+Workload (one step = one full R-STHOSVD, Alg. 3 with RandSVD on every mode):
+  X = G x_1 U_1 x_2 U_2 x_3 U_3 + E, 1024 x 1024 x 1024 FP32, core 50^3 of N(0,1) entries
+  scaled by 0.9^(i+j+k), U_n orthonormal (QR of N(0,1) 1024 x 50), E Gaussian with
+  ||E||_F = 1e-3 ||signal||_F; ranks (50, 50, 50), p = 10, Omega seed 0, order 1 -> 2 -> 3.
+  X (4.3 GB) is far larger than L2, so no flush is needed between steps.
+
+``value`` is algorithmic TFLOP/s summed over ranks (each rank decomposes its own tensor,
+weak scaling, no data-path collective).  Algorithmic flops per mode with current core
+size N_c, M = N_c / I_n and ell = r + p: sketch 2 N_c ell + mode product 2 N_c ell +
+tall-skinny QR of B^T 4 M ell^2 + truncated-core product 2 M ell r.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "R-STHOSVD time-to-Tucker & TFLOP/s at equal rel. error vs plain FP64 GPU"
+DIMS = [1024, 1024, 1024]
+RANKS = [50, 50, 50]
+P = 10
+SEED = 0
+RHO = [0, 1, 2]
+WORKLOAD = "dense 3-way FP32 1024x1024x1024, low-rank 50^3 (decay 0.9) + 1e-3 noise; R-STHOSVD rank (50,50,50), p=10"
+
+
+def algorithmic_flops(dims, ranks, p, rho):
+    cur = list(dims)
+    total = 0.0
+    for n in rho:
+        Nc = float(np.prod(cur))
+        I = cur[n]
+        M = Nc / I
+        ell = min(ranks[n] + p, I, int(M))
+        r = min(ranks[n], ell)
+        total += 4.0 * Nc * ell + 4.0 * M * ell * ell + 2.0 * M * ell * r
+        cur[n] = r
+    return total
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rh_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) < 9:
+                    continue
+                try:
+                    sm.append(float(t[1]))
+                    smax.append(float(t[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, t[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_input(torch, device, seed_offset=0):
+    from workloads import lowrank_plus_noise_torch
+
+    return lowrank_plus_noise_torch(DIMS, [50, 50, 50], 0.9, 1e-3, 2 + seed_offset, torch.float32, device)
+
+
+# ---------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample of the workload
+# ---------------------------------------------------------------------------------
+def cpu_baseline(X_gpu, slab=96, repeats=1):
+    """Oracle R-STHOSVD on the slab X[:, :, :slab] (same generator, same ranks and p)."""
+    from oracle import tucker
+
+    n0, n1 = DIMS[0], DIMS[1]
+    sub = X_gpu[: n0 * n1 * slab].double().cpu().numpy()
+    Xs = np.reshape(sub, (n0, n1, slab), order="F")
+    ranks = [RANKS[0], RANKS[1], min(RANKS[2], slab - P)]
+    rho = RHO
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        tucker.rsthosvd(Xs, ranks, P, SEED, rho=rho)
+    dt = (time.perf_counter() - t0) / repeats
+    fl = algorithmic_flops([n0, n1, slab], ranks, P, rho)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle R-STHOSVD (numpy FP64, BLAS on all host cores) on the {n0}x{n1}x{slab} slab "
+                      f"X[:, :, :{slab}] of the same tensor, ranks {ranks}, p={P}; {dt:.2f} s per run"}, dt
+
+
+# ---------------------------------------------------------------------------------
+# plain FP64 GPU comparator (PyTorch FP64 matmul / QR / SVD on the device)
+# ---------------------------------------------------------------------------------
+def _unfold_rev(torch, T, n):
+    """Kolda mode-n unfolding of a tensor stored with reversed axes (axis d-1-k holds mode k)."""
+    d = T.dim()
+    a = d - 1 - n
+    perm = [a] + [x for x in range(d) if x != a]      # remaining modes from the highest down
+    return T.permute(perm).reshape(T.shape[a], -1), perm
+
+
+def _fold_rev(torch, Mt, perm, shape_rev):
+    tmp = Mt.reshape([shape_rev[perm[0]]] + [shape_rev[x] for x in perm[1:]])
+    inv = [0] * len(perm)
+    for i, q in enumerate(perm):
+        inv[q] = i
+    return tmp.permute(inv).contiguous()
+
+
+def fp64_gpu_rsthosvd(torch, rh, X64, dims, ranks, p, seed, rho):
+    """Alg. 3 in plain PyTorch FP64 on the device (matmul, linalg.qr, linalg.svd);
+    Omega columns from the library's stream, so both runs use the same test matrices."""
+    d = len(dims)
+    G = X64.reshape(list(reversed(dims)))
+    factors = [None] * d
+    for n in rho:
+        Gm, perm = _unfold_rev(torch, G, n)
+        I, M = Gm.shape
+        ell = ranks[n] + p
+        Om = rh.omega(seed, 0, n, 0, M, ell).double().T      # M x ell
+        Q, _ = torch.linalg.qr(Gm @ Om)
+        B = Q.T @ Gm
+        Ub, s, Vt = torch.linalg.svd(B, full_matrices=False)
+        r = ranks[n]
+        factors[n] = Q @ Ub[:, :r]
+        shape_rev = list(G.shape)
+        shape_rev[d - 1 - n] = r
+        G = _fold_rev(torch, s[:r, None] * Vt[:r], perm, shape_rev)
+    return factors, G
+
+
+# ---------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1905_07311_gb300 import build
+
+    if rank == 0 or not build.up_to_date():
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1905_07311_gb300 as rh
+    from paper_1905_07311_gb300 import _lib
+
+    L = _lib.lib()
+    X = make_input(torch, device, seed_offset=rank)
+    call = rh.RsthosvdCall(DIMS, torch.float32, RANKS, p=P, seed=SEED, rho=RHO, device=device)
+    for _ in range(args.warmup):
+        call.run(X)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device events on the launching stream) ----
+    clocks = Clocks(local)
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    L.rh_profile_enable(1)
+    launches0 = L.rh_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        T = call.run(X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = L.rh_kernel_launches() - launches0
+    L.rh_profile_enable(0)
+    cap = 100000
+    kinds = (ctypes.c_int32 * cap)()
+    tags = (ctypes.c_int32 * cap)()
+    ms = (ctypes.c_float * cap)()
+    nrec = min(L.rh_profile_collect(kinds, tags, ms, cap), cap)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item())
+
+    flops = algorithmic_flops(DIMS, RANKS, P, RHO)
+    value = world * flops / (ms_step * 1e-3) / 1e12
+
+    # ---- dominant kernel and its roofline ----
+    per = {}
+    for i in range(nrec):
+        per.setdefault((kinds[i], tags[i]), []).append(ms[i])
+    names = {0: "sketch", 1: "mode_product", 2: "qr", 3: "trunc_svd", 4: "core_product", 5: "jacobi"}
+    breakdown = {f"{names[k]}[{t_}]": round(sum(v) / len(v), 4) for (k, t_), v in sorted(per.items())}
+    dom = max([(0, 0), (1, 0)], key=lambda key: sum(per.get(key, [0.0])))
+    dom_ms = sum(per[dom]) / len(per[dom])
+    N = float(np.prod(DIMS))
+    ell = RANKS[0] + P
+    dom_bytes = N * 4 + (N / DIMS[0]) * ell * 4 * (dom[0] == 1)
+    dom_flops = 2.0 * N * ell
+    peaks, src = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # FFMA lanes x 2 flops x clock
+    hbm_frac = dom_bytes / (dom_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    roofline = {"kernel": "sketch_kernel<float>" if dom[0] == 0 else "ttm_kernel<float>", "bound": "alu",
+                "achieved": round(dom_flops / (dom_ms * 1e-3) / 1e12, 3),
+                "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(dom_flops / (dom_ms * 1e-3) / 1e12 / fp32_peak, 4),
+                "traffic": traffic_for(dom[0]),
+                "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled SM clock)",
+                "hbm_frac_of_" + src: round(hbm_frac, 4), "avg_launch_ms": round(dom_ms, 4)}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hc = rh.RsthosvdHostCall(DIMS, torch.float32, RANKS, p=P, seed=SEED, rho=RHO, device=device)
+        Xh = X.cpu().pin_memory()
+        hc.run(Xh)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ke = max(1, min(args.steps, 3))
+        f0.record(stream)
+        for _ in range(ke):
+            hc.run(Xh)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = f0.elapsed_time(f1) / ke
+        te = torch.tensor([ms_e2e], dtype=torch.float64, device=device)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        ms_e2e = float(te.item())
+        e2e = {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+               "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": hc.h2d_bytes,
+               "d2h_bytes_per_step": hc.d2h_bytes}
+        del Xh, hc
+
+    # ---- accuracy of this run and the plain FP64 GPU comparator (rank 0, untimed for value) ----
+    extra = {}
+    if rank == 0 and not args.no_fp64:
+        extra = fp64_comparison(torch, rh, X, T, device)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, _ = cpu_baseline(X, slab=args.cpu_slab)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "time_to_tucker_ms": round(ms_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded generator, inputs resident in HBM before timing)",
+                "config": {"workload": WORKLOAD, "dims": DIMS, "ranks": RANKS, "p": P, "seed": SEED,
+                           "order": [n + 1 for n in RHO], "parallelism": f"independent tensor per GPU x{world}",
+                           "l2": "input (4.3 GB) larger than L2; no flush"},
+                "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+                "cpu_baseline": cpu, "breakdown_ms": breakdown}
+        line.update(extra)
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def traffic_for(kind):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+
+    want = {0: "sketch", 1: "ttm"}[kind]
+    src = os.path.join(ROOT, "paper_1905_07311_gb300", "csrc", f"{want}.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if len(t) >= 3 and t[0] == want and t[1] == h:
+                return float(t[2])
+    return None
+
+
+def fp64_comparison(torch, rh, X, T, device):
+    """Relative errors of this run and of a plain PyTorch FP64 R-STHOSVD, plus its time."""
+    try:
+        X64 = X.double()
+        A = [f.T.contiguous() for f in T.factors]   # I_n x r_n
+        core = T.core.reshape(list(reversed(T.core_dims)))
+        nx = torch.linalg.vector_norm(X64)
+        e_ours = float(torch.linalg.vector_norm(X64 - _reconstruct(torch, core, A)) / nx)
+        for _ in range(1):
+            fp64_gpu_rsthosvd(torch, rh, X64, DIMS, RANKS, P, SEED, RHO)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fac, G = fp64_gpu_rsthosvd(torch, rh, X64, DIMS, RANKS, P, SEED, RHO)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        e_ref = float(torch.linalg.vector_norm(X64 - _reconstruct(torch, G, fac)) / nx)
+        del X64
+        return {"rel_error": e_ours, "fp64_gpu": {"ms_per_step": round(ms, 3), "rel_error": e_ref,
+                                                  "what": "plain PyTorch FP64 (matmul, linalg.qr, linalg.svd) Alg. 3 "
+                                                          "on the same device and Omega stream",
+                                                  "speedup_of_ours": None}}
+    except Exception as exc:  # comparator is informational
+        return {"fp64_gpu": {"error": repr(exc)}}
+
+
+def _reconstruct(torch, core_rev, factors):
+    """X_hat = G x_1 A_1 ... x_d A_d for tensors stored with reversed axes (C order)."""
+    T = core_rev
+    d = len(factors)
+    for n in range(d):
+        ax = d - 1 - n
+        T = torch.movedim(torch.tensordot(factors[n], T, dims=([1], [ax])), 0, ax)
+    return T.reshape(-1)
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import torch
+
+    device = "cuda" if torch.cuda.is_available() else "cpu"
+    X = make_input(torch, device)
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        cpu, dt = cpu_baseline(X, slab=args.cpu_slab)
+        if i >= args.warmup:
+            times.append(dt)
+            info = cpu
+    dt = sum(times) / len(times)
+    n0, n1 = DIMS[0], DIMS[1]
+    fl = algorithmic_flops([n0, n1, args.cpu_slab], [RANKS[0], RANKS[1], min(RANKS[2], args.cpu_slab - P)], P, RHO)
+    value = fl / dt / 1e12
+    info["value"] = round(value, 6)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "dims": DIMS, "ranks": RANKS, "p": P,
+                                            "sample": f"slab {n0}x{n1}x{args.cpu_slab}"},
+            "cpu_baseline": info,
+            "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-slab", type=int, default=None,
+                    help="mode-3 extent of the CPU sample (default 384 for the baseline, 128 per reference step)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.cpu_slab = args.cpu_slab or 128
+        run_reference(args)
+    else:
+        args.cpu_slab = args.cpu_slab or 384
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * rhosvd.h -- C ABI of the GB300 (sm_103a) randomized Tucker compression library.
+ *
+ * Method: Minster, Saibaba, Kilmer, "Randomized algorithms for low-rank tensor
+ * decompositions in the Tucker format".  The library computes, on one GPU:
+ *   - the randomized range finder on a mode-n unfolding, Y_n = X_(n) Omega_n with a
+ *     Gaussian Omega_n of ell = r_n + p columns generated on the fly (Alg. 1 step 1,
+ *     Sec. 3.1), followed by a thin QR (Alg. 1 step 2);
+ *   - the mode-n products that form the core (Alg. 1 step 3, Alg. 2 step 6,
+ *     Alg. 3 step 6) and the truncation of Alg. 1 steps 4-6.
+ *
+ * Conventions shared by every entry point
+ *   Layout     Dense tensors are column-major: X(i_1,...,i_d) lives at
+ *              i_1 + I_1 (i_2 + I_2 (i_3 + ...)), 0-based.  The mode-n unfolding
+ *              X_(n) (Sec. 2.1) has columns indexed by the remaining indices with the
+ *              earliest mode fastest (the order of Eq. kron).  Matrices are
+ *              column-major with leading dimension equal to their row count.
+ *   Memory     Every data pointer is a DEVICE pointer on the current CUDA device,
+ *              owned by the caller.  Inputs are read only.  The library allocates no
+ *              device memory: scratch space is the caller's ``workspace`` buffer of
+ *              ``workspace_bytes`` bytes (256-byte aligned), sized by the matching
+ *              ``*_workspace_size`` query.  Host arrays (dims, ranks, rho, the
+ *              arrays of factor pointers) are read during the call only.
+ *   Streams    ``stream`` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *              enqueue kernels and return without synchronising; results are ready
+ *              when the stream reaches that point.  A call never waits on the device.
+ *   Omega      Omega_n(row, col) ~ N(0,1) from Philox4x32-10 (key = seed,
+ *              counter = (col/4, row lo, row hi, (tensor_id << 4) | mode)) and a
+ *              Box-Muller transform in FP32 with the library's own log / sin / cos.
+ *              ``row`` is the Kolda column index of the unfolding being sketched.
+ *              The FP64 paths use these FP32 normals promoted exactly.
+ *   Errors     Every call returns an rh_status.  Argument errors return RH_EINVAL
+ *              before anything is enqueued; a failed launch returns RH_ECUDA.  The
+ *              message of the last failure on the calling thread is rh_last_error().
+ *              No C++ exception crosses this boundary.
+ *   Dtypes     RH_F64: FP64 storage, FP64 arithmetic.  RH_F32: FP32 storage, FP32
+ *              products with FP32 accumulation inside a tile and FP64 accumulation
+ *              across tiles; the small dense factorizations run in FP64 (QR) or in
+ *              the storage precision (truncation SVD).
+ */
+#ifndef RHOSVD_H
+#define RHOSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RH_MAX_ORDER 8
+#define RH_MAX_ELL 64
+
+typedef int32_t rh_status;
+enum {
+  RH_OK = 0,
+  RH_EINVAL = 1,        /* bad argument (size rule, null pointer, unsupported combination) */
+  RH_ENOMEM = 2,        /* workspace_bytes smaller than the *_workspace_size query        */
+  RH_ECUDA = 3,         /* a CUDA launch or runtime call failed                           */
+  RH_ENUMERIC = 4,      /* numerical failure detected on the host side                    */
+  RH_ETIMEOUT = 5,      /* a bounded device wait gave up                                  */
+  RH_EUNSUPPORTED = 6   /* valid request that this build does not implement               */
+};
+
+enum { RH_F64 = 0, RH_F32 = 1 };
+
+/* Options of the fixed-rank algorithms (Alg. 2, Alg. 3). */
+typedef struct rh_options {
+  uint64_t seed;                 /* Philox key of every Omega_n                                   */
+  int32_t tensor_id;             /* Philox stream word (0 .. 2^28-1); distinguishes tensors      */
+  int32_t p;                     /* oversampling, ell_n = r_n + p (Alg. 1 REQUIRE)                */
+  int32_t rho[RH_MAX_ORDER];     /* processing order, 0-based; rho[0] < 0: decreasing I_n,       */
+                                 /* ties to the lower mode (Sec. 3.3, "Processing order")        */
+  int32_t clamp;                 /* 0: RH_EINVAL when r_n + p > min(I_n, prod_{k!=n} I_k)        */
+                                 /*    (Alg. 2/3 REQUIRE, checked on the current core);          */
+                                 /* 1: ell_n = min(r_n + p, I_n, prod_{k!=n} I_k)                */
+  int32_t truncate;              /* 1: rank r_n via the SVD of B (Alg. 1 steps 4-6, default)     */
+                                 /* 0: keep all ell_n columns, A_n = Q_n, G <- Q_n^T G           */
+} rh_options;
+
+/* Fill ``opts`` with defaults: seed 0, tensor_id 0, p 5, rho decreasing, clamp 0, truncate 1. */
+void rh_options_default(rh_options* opts);
+
+/* Version string and the message of the last failure on this thread ("" after success). */
+const char* rh_version(void);
+const char* rh_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all threads). */
+uint64_t rh_kernel_launches(void);
+
+/*
+ * Per-launch timing of the main kernels (measurement support, off by default).
+ *   rh_profile_enable(1) makes later calls bracket these launches with CUDA events on the
+ *   caller's stream: kind 0 the sketch kernel, 1 the mode product B = Q^T G_(n),
+ *   2 the QR of the sketch, 3 the truncation SVD, 4 the truncated-core mode product,
+ *   5 the Jacobi SVD inside the truncation (tag 0);
+ *   tag = step of the algorithm (0 = first processed mode).
+ *   rh_profile_collect waits for the recorded events, writes up to ``cap`` records
+ *   (kind, tag, milliseconds; any pointer may be NULL), clears the list and returns the
+ *   number of records that were pending.
+ */
+void rh_profile_enable(int32_t on);
+int32_t rh_profile_collect(int32_t* kinds, int32_t* tags, float* ms, int32_t cap);
+
+/*
+ * rh_omega -- materialise a block of Omega_mode (test and inspection use).
+ *   Writes out[i + nrows * c] = Omega_mode(row0 + i, c) for 0 <= i < nrows, 0 <= c < ell,
+ *   FP32.  Entries are bit-identical to the ones the sketch kernels generate.
+ *   Defines the Gaussian test matrix of Alg. 1 (REQUIRE) / Alg. 2 step 2 / Alg. 3 step 3.
+ *   RH_EINVAL: nrows < 0, ell < 1, mode not in [0,16), tensor_id not in [0, 2^28), out NULL.
+ */
+rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0, int64_t nrows,
+                   int32_t ell, float* out, void* stream);
+
+/*
+ * rhosvd_sketch -- range-finder sketch Y = X_(mode) Omega_mode (Alg. 1 step 1 applied to an
+ * unfolding, as in Alg. 2 step 3 and Alg. 3 step 4).
+ *   X       order-``order`` tensor with sizes dims[0..order-1], column-major, dtype RH_F64/RH_F32.
+ *   mode    0-based mode n;  ell  number of columns, 1 <= ell <= RH_MAX_ELL.
+ *   Y       output, I_n x ell FP64, column-major (ld = I_n).
+ *   norm2   optional (may be NULL): receives ||X||_F^2 (one FP64 value), accumulated
+ *           in FP64 from the same pass over X.
+ *   Omega is generated from (seed, tensor_id, mode); rows are Kolda column indices of X_(n).
+ *   RH_EINVAL: order not in [1, RH_MAX_ORDER], a dim < 1, mode out of range, ell out of
+ *   range, NULL X / Y.  RH_ENOMEM: workspace too small.
+ */
+size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode,
+                                    int32_t ell);
+rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
+                        int32_t ell, uint64_t seed, int32_t tensor_id, double* Y, double* norm2,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rh_orthonormalize -- thin QR of a tall matrix, Y = Q R, returning Q (Alg. 1 step 2).
+ *   Y  m x n FP64 column-major (read only), 1 <= n <= RH_MAX_ELL, n <= m.
+ *   Q  m x n FP64 column-major output with orthonormal columns spanning range(Y).
+ *   Method: CholeskyQR2 in FP64; if a Cholesky pivot falls below 1e-14 of its diagonal
+ *   (kappa(Y) beyond ~1e7) the result comes from a Householder QR instead.  The switch
+ *   happens on the device (no host synchronisation).  ``info`` (optional device int32)
+ *   receives 1 when the Householder branch produced Q, else 0.
+ */
+size_t rh_orthonormalize_workspace_size(int64_t m, int32_t n);
+rh_status rh_orthonormalize(int64_t m, int32_t n, const double* Y, double* Q, int32_t* info,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rsthosvd -- R-STHOSVD (Alg. 3) with RandSVD (Alg. 1) on each current core unfolding.
+ *   X        input tensor (order, dims, dtype), column-major device buffer.
+ *   ranks    target ranks r_n (host array of ``order`` values, 1 <= r_n).
+ *   opts     options (NULL = rh_options_default).
+ *   factors  host array of ``order`` device pointers; factors[n] receives A_n, I_n x k_n FP64
+ *            column-major with orthonormal columns, where k_n = r_n (truncate = 1) or
+ *            ell_n (truncate = 0).
+ *   core     device buffer receiving G, k_1 x ... x k_d FP64 column-major.
+ *   norms    optional device buffer of 2 FP64 values: ||X||_F^2 and ||G||_F^2.  For the
+ *            orthonormal factors of Alg. 3, ||X - X_hat||^2 = ||X||^2 - ||G||^2 exactly
+ *            (Thm. lem:st_mode_err); the difference is meaningful only above ~1e-6 relative.
+ *   info     optional device int32 array of ``order`` values: 1 where mode n's QR took the
+ *            Householder branch.
+ *   Size rule: ell_n <= min(I_n, prod of the other current sizes), else RH_EINVAL (or
+ *   clamped, opts->clamp).  Steps per mode n (in order rho):
+ *     sketch Y = G_(n) Omega_n; Q = orth(Y); B = Q^T G_(n) (mode-n product);
+ *     B^T = Q_B R (tall-skinny Householder QR); one-sided Jacobi SVD of R gives U_B;
+ *     A_n = Q U_B(:, 1:r_n); G <- U_B(:, 1:r_n)^T B.
+ */
+size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                               const rh_options* opts);
+rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
+                   const rh_options* opts, double* const* factors, double* core, double* norms,
+                   int32_t* info, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rsthosvd_host -- the same R-STHOSVD with HOST buffers: enqueues the copy of X to the
+ * device, the decomposition and the copies of the factors, the core and the norms back
+ * to the host, all on ``stream``; the results are valid once the stream is synchronised.
+ *   X_host       host tensor (pinned memory gives asynchronous copies), column-major.
+ *   factors_host host array of ``order`` host pointers, I_n x k_n FP64 each.
+ *   core_host    host buffer, k_1 x ... x k_d FP64;  norms_host optional, 2 FP64.
+ *   workspace    DEVICE buffer of rsthosvd_host_workspace_size bytes; it holds the device
+ *                copy of X, the device outputs and the rsthosvd workspace.
+ */
+size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                                    const rh_options* opts);
+rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const void* X_host,
+                        const int32_t* ranks, const rh_options* opts, double* const* factors_host,
+                        double* core_host, double* norms_host, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHOSVD_H */

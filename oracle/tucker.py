@@ -60,16 +60,47 @@ def _ell(r, p, I, M, clamp, strict=False):
     return ell
 
 
+def canon_signs(U):
+    """Column signs making the largest-magnitude entry of each column positive (first index on ties).
+
+    The thin QR and the SVD of Alg. 1 fix their columns only up to sign.  In the
+    sequential algorithms the sign of A_j changes the next core and hence the next
+    sketch, so the library fixes this convention on both sides.
+    """
+    U = np.asarray(U)
+    if U.shape[0] == 0:
+        return np.ones(U.shape[1])
+    idx = np.argmax(np.abs(U), axis=0)
+    v = U[idx, np.arange(U.shape[1])]
+    return np.where(v < 0, -1.0, 1.0)
+
+
+def canon_qr(Y):
+    """Thin Householder QR of Y with the column-sign convention of ``canon_signs`` applied to Q."""
+    Q, _ = np.linalg.qr(Y)
+    return Q * canon_signs(Q)
+
+
 # ---------------------------------------------------------------------------------
 # Alg. 1 -- RandSVD
 # ---------------------------------------------------------------------------------
 def randsvd(Xm, r, Omega):
-    """Alg. 1: Y = X Omega; Y = QR; B = Q^T X; B = U_B S V^T; U = Q U_B(:, 1:r)."""
+    """Alg. 1: Y = X Omega; Y = QR; B = Q^T X; B = U_B S V^T; U = Q U_B(:, 1:r).
+
+    Column signs of Q and of U follow ``canon_signs``; the flip of U's column k is
+    applied to U_B(:, k) and V(:, k) as well, so U S V^T is unchanged.
+    """
     Y = Xm @ Omega                                  # step 1
-    Q, _ = np.linalg.qr(Y)                          # step 2 (thin, Householder)
+    Q = canon_qr(Y)                                 # step 2 (thin, Householder)
     B = Q.T @ Xm                                    # step 3
     Ub, s, Vt = np.linalg.svd(B, full_matrices=False)   # step 4
     U = Q @ Ub[:, :r]                               # step 5
+    sg = canon_signs(U)
+    U = U * sg
+    Ub = Ub.copy()
+    Ub[:, :r] *= sg
+    Vt = Vt.copy()
+    Vt[:r] *= sg[:, None]
     return U, s[:r], Vt[:r].T, {"Y": Y, "Q": Q, "sv_B": s, "Ub": Ub}   # step 6
 
 
@@ -125,11 +156,14 @@ def rhosvd(X, ranks, p, seed, tensor_id=0, omega_round=None, clamp=False, record
     return out
 
 
-def rsthosvd(X, ranks, p, seed, rho=None, tensor_id=0, omega_round=None, clamp=False, record=False):
+def rsthosvd(X, ranks, p, seed, rho=None, tensor_id=0, omega_round=None, clamp=False, record=False,
+             truncate=True):
     """Alg. 3 (R-STHOSVD).
 
     G = X; for j = 1..d: Omega_{rho_j} over the current other-mode extent;
     [U, S, V] = RandSVD(G_(rho_j), r, p, Omega); A_{rho_j} = U; G_(rho_j) <- S V^T.
+    ``truncate=False`` stops RandSVD after step 3: A_{rho_j} = Q, G_(rho_j) <- Q^T G_(rho_j)
+    (the untruncated core G = X x_1 Q_1^T ... of the range finder).
     """
     X = np.asarray(X, dtype=np.float64)
     d = X.ndim
@@ -146,6 +180,15 @@ def rsthosvd(X, ranks, p, seed, rho=None, tensor_id=0, omega_round=None, clamp=F
         ell = _ell(ranks[n], p, I, M, clamp)
         r = min(int(ranks[n]), ell)
         Om = omega_matrix(seed, tensor_id, n, M, ell, omega_round)       # step 3
+        if not truncate:
+            Gm = unfold(G, n)
+            Y = Gm @ Om
+            Q = canon_qr(Y)
+            A[n] = Q
+            shape[n] = ell
+            G = fold(Q.T @ Gm, n, shape)
+            recs.append(dict(mode=n, ell=ell, Y=Y, Q=Q, sv_B=np.linalg.svd(Q.T @ Gm, compute_uv=False)))
+            continue
         U, s, V, info = randsvd(unfold(G, n), r, Om)                     # step 4
         A[n] = U                                                         # step 5
         shape[n] = r
@@ -186,7 +229,7 @@ def adapt_range_finder(Gm, tol, b, p, omega_cols, cap=None):
         Y = Y - Q @ (Q.T @ Y)
         Qi, _ = np.linalg.qr(Y)
         Qi = Qi - Q @ (Q.T @ Qi)
-        Qi, _ = np.linalg.qr(Qi)
+        Qi = canon_qr(Qi)
         Bi = Qi.T @ Gm
         return np.hstack([Q, Qi]), np.vstack([B, Bi])
 
@@ -206,6 +249,7 @@ def adapt_range_finder(Gm, tol, b, p, omega_cols, cap=None):
     ok = np.nonzero(tails <= tol2)[0]
     r = int(ok[0]) + 1 if ok.size else int(s.size)
     A = Q @ Ub[:, :r]
+    A = A * canon_signs(A)
     return A, {"k": k_found, "ell": Q.shape[1], "rank": r, "sv_B": s, "res2": res2}
 
 

@@ -1,0 +1,222 @@
+"""Randomized Tucker compression on GB300 (sm_103a).
+
+Python names mirror the C ABI of include/rhosvd.h: ``omega``, ``rhosvd_sketch``,
+``orthonormalize``, ``rsthosvd``.  Tensors are torch CUDA tensors holding the flat
+column-major buffer of the tensor (index 1 fastest) together with its ``dims``.
+Outputs and the workspace are allocated with torch on the tensor's device; every
+call runs on the current torch CUDA stream.
+"""
+
+import ctypes
+
+from . import _lib
+from ._lib import RH_F32, RH_F64, RhError, check, i32_array, i64_array, lib, make_options
+
+__all__ = ["omega", "rhosvd_sketch", "orthonormalize", "rsthosvd", "RhError", "version"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return RH_F64
+    if t.dtype == torch.float32:
+        return RH_F32
+    raise TypeError(f"unsupported dtype {t.dtype}: use float64 or float32")
+
+
+def _stream(device):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_input(X, dims):
+    torch = _torch()
+    if not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor")
+    if not X.is_contiguous():
+        raise ValueError("X must be contiguous (flat column-major buffer)")
+    n = 1
+    for v in dims:
+        n *= int(v)
+    if X.numel() != n:
+        raise ValueError(f"X has {X.numel()} elements but dims multiply to {n}")
+    return torch
+
+
+def version():
+    return lib().rh_version().decode()
+
+
+def omega(seed, tensor_id, mode, row0, nrows, ell, device="cuda"):
+    """Omega_mode(row0 + i, c) for i < nrows, c < ell as an (ell, nrows) FP32 tensor (column c = row c)."""
+    torch = _torch()
+    out = torch.empty((ell, nrows), dtype=torch.float32, device=device)
+    check(lib().rh_omega(int(seed) & 0xFFFFFFFFFFFFFFFF, int(tensor_id), int(mode), int(row0), int(nrows), int(ell),
+                         _ptr(out), _stream(out.device)))
+    return out
+
+
+def rhosvd_sketch(X, dims, mode, ell, seed=0, tensor_id=0, with_norm=False):
+    """Y = X_(mode) Omega_mode as an (ell, I_mode) FP64 tensor holding the column-major I x ell matrix."""
+    torch = _check_input(X, dims)
+    d = len(dims)
+    dt = _dtype_code(X)
+    da = i64_array(dims)
+    ws_bytes = lib().rhosvd_sketch_workspace_size(d, da, dt, int(mode), int(ell))
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=X.device)
+    Y = torch.empty((ell, int(dims[mode])), dtype=torch.float64, device=X.device)
+    nrm = torch.empty(1, dtype=torch.float64, device=X.device) if with_norm else None
+    check(lib().rhosvd_sketch(d, da, dt, _ptr(X), int(mode), int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                              int(tensor_id), _ptr(Y), _ptr(nrm), _ptr(ws), ws_bytes, _stream(X.device)))
+    return (Y, nrm) if with_norm else Y
+
+
+def orthonormalize(Y):
+    """Thin QR of the column-major m x n matrix held in the (n, m) FP64 tensor Y; returns (Q, info)."""
+    torch = _torch()
+    n, m = Y.shape
+    ws_bytes = lib().rh_orthonormalize_workspace_size(m, n)
+    if ws_bytes == 0:
+        raise ValueError("need 1 <= n <= min(m, 64)")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=Y.device)
+    Q = torch.empty_like(Y)
+    info = torch.zeros(1, dtype=torch.int32, device=Y.device)
+    check(lib().rh_orthonormalize(m, n, _ptr(Y.contiguous()), _ptr(Q), _ptr(info), _ptr(ws), ws_bytes,
+                                  _stream(Y.device)))
+    return Q, info
+
+
+class Tucker:
+    """Tucker factors (list of (k_n, I_n) FP64 tensors holding column-major I_n x k_n matrices),
+    the FP64 core (flat, column-major, sizes ``core_dims``), the norms ||X||^2, ||G||^2 and the
+    per-mode flag of the Householder QR branch."""
+
+    def __init__(self, factors, core, core_dims, norms, info):
+        self.factors = factors
+        self.core = core
+        self.core_dims = core_dims
+        self.norms = norms
+        self.info = info
+
+
+class RsthosvdCall:
+    """A prepared R-STHOSVD call: outputs and workspace allocated once, ``run()`` enqueues it.
+
+    Reusing the prepared buffers keeps allocation out of repeated calls (benchmarks).
+    """
+
+    def __init__(self, dims, dtype, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True,
+                 device="cuda"):
+        torch = _torch()
+        self.dims = [int(x) for x in dims]
+        d = len(self.dims)
+        self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
+        self.da = i64_array(self.dims)
+        self.ra = i32_array(ranks)
+        self.ws_bytes = lib().rsthosvd_workspace_size(d, self.da, self.dt, self.ra, ctypes.byref(self.opts))
+        if self.ws_bytes == 0:
+            # re-run the validation through the call itself to get the message
+            check(lib().rsthosvd(d, self.da, self.dt, None, self.ra, ctypes.byref(self.opts), None, None, None,
+                                 None, None, 0, None))
+            raise ValueError("invalid R-STHOSVD request")
+        ko = self._out_ranks(ranks, p, clamp, truncate, rho)
+        self.core_dims = ko
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.factors = [torch.empty((ko[n], self.dims[n]), dtype=torch.float64, device=device) for n in range(d)]
+        ncore = 1
+        for k in ko:
+            ncore *= k
+        self.core = torch.empty(ncore, dtype=torch.float64, device=device)
+        self.norms = torch.empty(2, dtype=torch.float64, device=device)
+        self.info = torch.zeros(d, dtype=torch.int32, device=device)
+        self.fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in self.factors])
+
+    def _out_ranks(self, ranks, p, clamp, truncate, rho):
+        d = len(self.dims)
+        cur = list(self.dims)
+        order = list(rho) if rho is not None else sorted(range(d), key=lambda n: (-cur[n], n))
+        out = [0] * d
+        for n in order:
+            M = 1
+            for k in range(d):
+                if k != n:
+                    M *= cur[k]
+            ell = int(ranks[n]) + int(p)
+            if clamp:
+                ell = min(ell, cur[n], M)
+            k = min(int(ranks[n]), ell) if truncate else ell
+            out[n] = k
+            cur[n] = k
+        return out
+
+    def run(self, X):
+        _check_input(X, self.dims)
+        check(lib().rsthosvd(len(self.dims), self.da, self.dt, _ptr(X), self.ra, ctypes.byref(self.opts), self.fptrs,
+                             _ptr(self.core), _ptr(self.norms), _ptr(self.info), _ptr(self.ws), self.ws_bytes,
+                             _stream(X.device)))
+        return Tucker(self.factors, self.core, self.core_dims, self.norms, self.info)
+
+
+def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True):
+    """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``."""
+    call = RsthosvdCall(dims, X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
+                        truncate=truncate, device=X.device)
+    return call.run(X)
+
+
+class RsthosvdHostCall:
+    """R-STHOSVD through ``rsthosvd_host``: X and the outputs live in (pinned) host memory.
+
+    ``run(X_host)`` enqueues H2D copy, decomposition and D2H copies on the current stream;
+    after the stream is synchronised the numpy views ``factors`` / ``core`` / ``norms``
+    hold the result.  ``h2d_bytes`` / ``d2h_bytes`` are the bytes copied per call.
+    """
+
+    def __init__(self, dims, dtype, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True,
+                 device="cuda"):
+        torch = _torch()
+        dev_call = RsthosvdCall.__new__(RsthosvdCall)
+        dev_call.dims = [int(x) for x in dims]
+        ko = RsthosvdCall._out_ranks(dev_call, ranks, p, clamp, truncate, rho)
+        self.dims = dev_call.dims
+        d = len(self.dims)
+        self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
+        self.da = i64_array(self.dims)
+        self.ra = i32_array(ranks)
+        self.ws_bytes = lib().rsthosvd_host_workspace_size(d, self.da, self.dt, self.ra, ctypes.byref(self.opts))
+        if self.ws_bytes == 0:
+            raise ValueError("invalid R-STHOSVD request")
+        self.core_dims = ko
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.factors = [torch.empty((ko[n], self.dims[n]), dtype=torch.float64).pin_memory() for n in range(d)]
+        ncore = 1
+        for k in ko:
+            ncore *= k
+        self.core = torch.empty(ncore, dtype=torch.float64).pin_memory()
+        self.norms = torch.empty(2, dtype=torch.float64).pin_memory()
+        self.fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in self.factors])
+        n = 1
+        for v in self.dims:
+            n *= v
+        self.h2d_bytes = n * (8 if self.dt == RH_F64 else 4)
+        self.d2h_bytes = 8 * (sum(self.dims[k] * ko[k] for k in range(d)) + ncore + 2)
+        self.device = torch.device(device)
+
+    def run(self, X_host):
+        if X_host.is_cuda:
+            raise ValueError("X_host must be a host tensor")
+        check(lib().rsthosvd_host(len(self.dims), self.da, self.dt, _ptr(X_host), self.ra, ctypes.byref(self.opts),
+                                  self.fptrs, _ptr(self.core), _ptr(self.norms), _ptr(self.ws), self.ws_bytes,
+                                  _stream(self.device)))

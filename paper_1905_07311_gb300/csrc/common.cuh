@@ -1,0 +1,110 @@
+// Shared host/device helpers of the library: status plumbing, workspace carving,
+// launch checks.  No arithmetic of the method lives here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/rhosvd.h"
+
+namespace rh {
+
+// Thread-local message of the last failure (rh_last_error).
+void set_error(const std::string& msg);
+void clear_error();
+
+struct Status {
+  rh_status code = RH_OK;
+  bool ok() const { return code == RH_OK; }
+};
+
+#define RH_CHECK_ARG(cond, msg)                      \
+  do {                                               \
+    if (!(cond)) {                                   \
+      ::rh::set_error(std::string("invalid argument: ") + (msg)); \
+      return RH_EINVAL;                              \
+    }                                                \
+  } while (0)
+
+#define RH_CUDA_TRY(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      ::rh::set_error(std::string("CUDA error ") + cudaGetErrorString(_e) + " at " +  \
+                      __FILE__ + ":" + std::to_string(__LINE__));                      \
+      return RH_ECUDA;                                                                 \
+    }                                                                                  \
+  } while (0)
+
+// Every kernel launch of the library goes through RH_LAUNCH_CHECK, which also counts it
+// (rh_kernel_launches() in the C ABI).
+void count_launch();
+#define RH_LAUNCH_CHECK()   \
+  do {                      \
+    ::rh::count_launch();   \
+    RH_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+// Bump allocator over the caller's workspace.  With base == nullptr it only
+// measures, so the *_workspace_size queries run the same carving code as the calls.
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0;
+  explicit Arena(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + ((count * sizeof(T) + 255) & ~size_t(255));
+    return base ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+};
+
+// Per-launch timing (profile.cu): a scope records an event before and after the kernels
+// it encloses when profiling is on.  kind: 0 sketch, 1 mode product, 2 QR of the sketch,
+// 3 truncation SVD; tag: the step of the algorithm (0 = first processed mode).
+enum { PROF_SKETCH = 0, PROF_TTM = 1, PROF_ORTH = 2, PROF_TRUNC = 3, PROF_TTM_CORE = 4, PROF_JACOBI = 5 };
+class ProfileScope {
+ public:
+  ProfileScope(int kind, int tag, cudaStream_t st);
+  ~ProfileScope();
+  ProfileScope(const ProfileScope&) = delete;
+  ProfileScope& operator=(const ProfileScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int idx_ = -1;
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int num_sms() {
+  static int n = -1;
+  if (n < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 148;
+  }
+  return n;
+}
+
+// 3-D view (L, I, R) of mode n of a column-major tensor: L = prod_{k<n} dims,
+// I = dims[n], R = prod_{k>n} dims.  Element (l, i, r) sits at l + L*(i + I*r); the
+// Kolda column index of X_(n) for (l, r) is p = l + L*r.
+struct ModeView {
+  int64_t L, I, R;
+  int64_t M() const { return L * R; }
+};
+
+inline ModeView mode_view(int order, const int64_t* dims, int n) {
+  ModeView v{1, dims[n], 1};
+  for (int k = 0; k < n; ++k) v.L *= dims[k];
+  for (int k = n + 1; k < order; ++k) v.R *= dims[k];
+  return v;
+}
+
+inline int ell_pad_of(int ell) { return ell <= 32 ? 32 : 64; }
+
+}  // namespace rh

@@ -1,0 +1,60 @@
+// Launchers shared between the translation units of the library (host side).
+#pragma once
+
+#include "common.cuh"
+
+namespace rh {
+
+// ---- sketch Y = G_(n) Omega_n  (sketch.cu) -----------------------------------------
+struct SketchPlan {
+  ModeView v;
+  int ell, ellp;
+  int gx, S;
+  int64_t chunk;
+  size_t part_elems() const { return (size_t)S * ell * v.I; }
+  size_t norm_elems() const { return (size_t)S * gx; }
+};
+SketchPlan plan_sketch(const ModeView& v, int ell);
+
+template <typename T>
+rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_t sid, T* part, double* part_norm,
+                        cudaStream_t st);
+template <typename T>
+rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y,
+                               double* norm2, cudaStream_t st);
+
+// ---- mode-n product B = G x_n Q^T  (ttm.cu) ------------------------------------------
+// B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.
+template <typename T, typename TO>
+rh_status launch_ttm(const ModeView& v, const T* G, const T* Q, int ko, TO* B, cudaStream_t st);
+
+// ---- small dense linear algebra (smallla.cu) --------------------------------------------
+size_t orth_workspace_elems(int64_t m, int n);   // doubles
+rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
+                                cudaStream_t st);
+
+// Truncation of B (mode-n unfolding of a L x ell x R tensor, entries of type T):
+// TSQR of B_(n)^T, one-sided Jacobi SVD of the ell x ell triangle -> U_B (ell x ell, FP64,
+// columns sorted by decreasing singular value) and the singular values.
+struct TruncPlan {
+  ModeView v;         // view of B: (L, ell, R)
+  int ell;
+  int rows0;          // rows per first-level block
+  int fan;            // blocks merged per higher level
+  int64_t nblk0;      // first-level blocks
+};
+TruncPlan plan_trunc(const ModeView& vb, int ell);
+template <typename T>
+size_t trunc_workspace_elems(const TruncPlan& pl);   // elements of T
+template <typename T>
+rh_status launch_trunc_svd(const TruncPlan& pl, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st);
+
+// A = Q * Ub(:, 0:r)  (I x r, FP64);  Uc = (T) Ub(:, 0:r) (ell x r)
+template <typename T>
+rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, const double* Ub, double* A, T* Uc,
+                                 cudaStream_t st);
+template <typename T>
+rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st);
+rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st);
+
+}  // namespace rh

@@ -1,0 +1,403 @@
+// Host drivers of the C ABI: rhosvd_sketch, rh_orthonormalize and rsthosvd (Alg. 3 with
+// RandSVD, Alg. 1, on each current core unfolding).  Host code only sequences kernels
+// on the caller's stream; every arithmetic step runs on the device.
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rh {
+namespace {
+
+bool dtype_ok(int32_t dtype) { return dtype == RH_F64 || dtype == RH_F32; }
+
+rh_status check_tensor(int32_t order, const int64_t* dims, int32_t dtype) {
+  RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER, "order must be in [1, 8]");
+  RH_CHECK_ARG(dims != nullptr, "dims is NULL");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(dims[k] >= 1, "every dimension must be >= 1");
+  RH_CHECK_ARG(dtype_ok(dtype), "dtype must be RH_F64 or RH_F32");
+  return RH_OK;
+}
+
+// ---- sketch -----------------------------------------------------------------------
+struct SketchBufs {
+  void* part;
+  double* part_norm;
+};
+
+SketchBufs carve_sketch(Arena& ar, const SketchPlan& pl, int32_t dtype) {
+  SketchBufs b;
+  b.part = (dtype == RH_F64) ? (void*)ar.take<double>(pl.part_elems()) : (void*)ar.take<float>(pl.part_elems());
+  b.part_norm = ar.take<double>(pl.norm_elems());
+  return b;
+}
+
+template <typename T>
+rh_status run_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_t sid, const SketchBufs& b, double* Y,
+                     double* norm2, cudaStream_t st) {
+  rh_status s = launch_sketch<T>(pl, G, seed, sid, static_cast<T*>(b.part), b.part_norm, st);
+  if (s != RH_OK) return s;
+  return launch_sketch_reduce<T>(pl, static_cast<const T*>(b.part), b.part_norm, Y, norm2, st);
+}
+
+// ---- R-STHOSVD plan ------------------------------------------------------------------
+struct Step {
+  int mode;
+  ModeView v;   // view of the current core for this mode
+  int ell;      // sketch width r + p (possibly clamped)
+  int ko;       // output width of the mode: r (truncate) or ell
+  SketchPlan sk;
+  TruncPlan tr;
+};
+
+struct Plan {
+  int d;
+  int32_t dtype;
+  std::vector<Step> steps;
+  size_t max_I_ell = 0, max_tensor = 0, max_orth = 0, max_trunc = 0, max_part = 0, max_pnorm = 0;
+};
+
+rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks, const rh_options& o,
+                    Plan& pl) {
+  rh_status s = check_tensor(order, dims, dtype);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
+  RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
+  RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");
+  std::vector<int> rho(order);
+  if (o.rho[0] < 0) {
+    std::iota(rho.begin(), rho.end(), 0);
+    std::stable_sort(rho.begin(), rho.end(), [&](int a, int b) { return dims[a] > dims[b]; });
+  } else {
+    std::vector<int> seen(order, 0);
+    for (int k = 0; k < order; ++k) {
+      RH_CHECK_ARG(o.rho[k] >= 0 && o.rho[k] < order && !seen[o.rho[k]], "rho must be a permutation of 0..order-1");
+      seen[o.rho[k]] = 1;
+      rho[k] = o.rho[k];
+    }
+  }
+  pl.d = order;
+  pl.dtype = dtype;
+  std::vector<int64_t> cur(dims, dims + order);
+  const size_t tsz = (dtype == RH_F64) ? sizeof(double) : sizeof(float);
+  for (int j = 0; j < order; ++j) {
+    Step st;
+    st.mode = rho[j];
+    st.v = mode_view(order, cur.data(), st.mode);
+    const int64_t lim = std::min<int64_t>(st.v.I, st.v.M());
+    int64_t ell = (int64_t)ranks[st.mode] + o.p;
+    if (ell > lim) {
+      if (!o.clamp) {
+        set_error("invalid argument: r_n + p = " + std::to_string(ell) + " exceeds min(I_n, prod of the other sizes) = " +
+                  std::to_string(lim) + " for mode " + std::to_string(st.mode));
+        return RH_EINVAL;
+      }
+      ell = lim;
+    }
+    if (ell > RH_MAX_ELL) {
+      set_error("unsupported: r_n + p = " + std::to_string(ell) + " exceeds RH_MAX_ELL (64)");
+      return RH_EUNSUPPORTED;
+    }
+    st.ell = (int)ell;
+    st.ko = o.truncate ? std::min<int>(ranks[st.mode], st.ell) : st.ell;
+    st.sk = plan_sketch(st.v, st.ell);
+    st.tr = plan_trunc(ModeView{st.v.L, st.ell, st.v.R}, st.ell);
+    pl.max_I_ell = std::max(pl.max_I_ell, (size_t)(st.v.I * st.ell));
+    pl.max_tensor = std::max(pl.max_tensor, (size_t)(st.v.M() * st.ell));   // B
+    pl.max_part = std::max(pl.max_part, st.sk.part_elems());
+    pl.max_pnorm = std::max(pl.max_pnorm, st.sk.norm_elems());
+    pl.max_orth = std::max(pl.max_orth, orth_workspace_elems(st.v.I, st.ell));
+    pl.max_trunc = std::max(pl.max_trunc, dtype == RH_F64 ? trunc_workspace_elems<double>(st.tr)
+                                                           : trunc_workspace_elems<float>(st.tr));
+    cur[st.mode] = st.ko;
+    pl.steps.push_back(st);
+  }
+  (void)tsz;
+  return RH_OK;
+}
+
+struct Bufs {
+  void* part;
+  double* part_norm;
+  double* normx;
+  double* Y;
+  double* orth;
+  double* Q;
+  void* Qc;
+  void* W[2];
+  void* trunc;
+  double* Ub;
+  double* sv;
+  void* Uc;
+};
+
+Bufs carve(Arena& ar, const Plan& pl) {
+  Bufs b;
+  const bool f64 = pl.dtype == RH_F64;
+  auto takeT = [&](size_t n) -> void* { return f64 ? (void*)ar.take<double>(n) : (void*)ar.take<float>(n); };
+  b.part = takeT(pl.max_part);
+  b.part_norm = ar.take<double>(pl.max_pnorm);
+  b.normx = ar.take<double>(1);
+  b.Y = ar.take<double>(pl.max_I_ell);
+  b.orth = ar.take<double>(pl.max_orth);
+  b.Q = ar.take<double>(pl.max_I_ell);
+  b.Qc = takeT(pl.max_I_ell);
+  b.W[0] = takeT(pl.max_tensor);
+  b.W[1] = takeT(pl.max_tensor);
+  b.trunc = takeT(pl.max_trunc);
+  b.Ub = ar.take<double>(RH_MAX_ELL * RH_MAX_ELL);
+  b.sv = ar.take<double>(RH_MAX_ELL);
+  b.Uc = takeT(RH_MAX_ELL * RH_MAX_ELL);
+  return b;
+}
+
+template <typename T>
+rh_status run_rsthosvd(const Plan& pl, const T* X, const rh_options& o, double* const* factors, double* core,
+                       double* norms, int32_t* info, const Bufs& b, cudaStream_t st) {
+  const T* cur = X;
+  int cur_buf = -1;  // -1: the input tensor
+  rh_status s;
+  const int nsteps = (int)pl.steps.size();
+  for (int j = 0; j < nsteps; ++j) {
+    const Step& sp = pl.steps[j];
+    const bool last = (j == nsteps - 1);
+    const uint32_t sid = ((uint32_t)o.tensor_id << 4) | (uint32_t)sp.mode;
+    // Alg. 1 step 1: Y = G_(n) Omega_n   (+ ||X||^2 on the first pass)
+    SketchBufs sb{b.part, b.part_norm};
+    double* n2 = (j == 0) ? (norms ? norms : b.normx) : nullptr;
+    {
+      ProfileScope ps(PROF_SKETCH, j, st);
+      if ((s = launch_sketch<T>(sp.sk, cur, o.seed, sid, static_cast<T*>(sb.part), sb.part_norm, st)) != RH_OK)
+        return s;
+    }
+    if ((s = launch_sketch_reduce<T>(sp.sk, static_cast<const T*>(sb.part), sb.part_norm, b.Y, n2, st)) != RH_OK)
+      return s;
+    // Alg. 1 step 2: Q = orth(Y)
+    {
+      ProfileScope ps(PROF_ORTH, j, st);
+      if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st)) !=
+          RH_OK)
+        return s;
+    }
+    if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
+    // Alg. 1 step 3: B = Q^T G_(n)   (the mode-n product G x_n Q^T)
+    const int wb = (cur_buf == 0) ? 1 : 0;
+    T* B = static_cast<T*>(b.W[wb]);
+    const bool direct_core = last && !o.truncate;
+    {
+      ProfileScope ps(PROF_TTM, j, st);
+      if (direct_core) {
+        if ((s = launch_ttm<T, double>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, core, st)) != RH_OK) return s;
+      } else {
+        if ((s = launch_ttm<T, T>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) return s;
+      }
+    }
+    if (o.truncate) {
+      // Alg. 1 steps 4-6: SVD of B, A_n = Q U_B(:, 1:r), G_(n) <- S V^T = U_B(:, 1:r)^T B
+      {
+        ProfileScope ps(PROF_TRUNC, j, st);
+        if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st)) != RH_OK) return s;
+      }
+      if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
+                                         st)) != RH_OK)
+        return s;
+      const ModeView vb{sp.v.L, sp.ell, sp.v.R};
+      ProfileScope ps(PROF_TTM_CORE, j, st);
+      if (last) {
+        if ((s = launch_ttm<T, double>(vb, B, static_cast<const T*>(b.Uc), sp.ko, core, st)) != RH_OK) return s;
+      } else {
+        const int wg = 1 - wb;
+        if ((s = launch_ttm<T, T>(vb, B, static_cast<const T*>(b.Uc), sp.ko, static_cast<T*>(b.W[wg]), st)) != RH_OK)
+          return s;
+        cur = static_cast<const T*>(b.W[wg]);
+        cur_buf = wg;
+      }
+    } else {
+      RH_CUDA_TRY(cudaMemcpyAsync(factors[sp.mode], b.Q, sizeof(double) * sp.v.I * sp.ell, cudaMemcpyDeviceToDevice, st));
+      if (!last) {
+        cur = B;
+        cur_buf = wb;
+      }
+    }
+  }
+  if (norms) {
+    int64_t ncore = 1;
+    // final core sizes
+    std::vector<int64_t> dims_out(pl.d, 0);
+    for (const Step& sp : pl.steps) dims_out[sp.mode] = sp.ko;
+    for (int k = 0; k < pl.d; ++k) ncore *= dims_out[k];
+    if ((s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
+  }
+  return RH_OK;
+}
+
+rh_options opts_or_default(const rh_options* o) {
+  rh_options d;
+  rh_options_default(&d);
+  return o ? *o : d;
+}
+
+}  // namespace
+}  // namespace rh
+
+using namespace rh;
+
+extern "C" {
+
+size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t ell) {
+  if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || ell < 1 || ell > RH_MAX_ELL) return 0;
+  const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
+  Arena ar(nullptr);
+  carve_sketch(ar, pl, dtype);
+  return ar.used;
+}
+
+rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode, int32_t ell,
+                        uint64_t seed, int32_t tensor_id, double* Y, double* norm2, void* workspace,
+                        size_t workspace_bytes, void* stream) {
+  clear_error();
+  rh_status s = check_tensor(order, dims, dtype);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(mode >= 0 && mode < order && mode < 16, "mode out of range");
+  RH_CHECK_ARG(ell >= 1 && ell <= RH_MAX_ELL, "ell must be in [1, 64]");
+  RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
+  const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
+  Arena ar(workspace);
+  Arena meas(nullptr);
+  carve_sketch(meas, pl, dtype);
+  if (workspace == nullptr || workspace_bytes < meas.used) {
+    set_error("workspace too small: need " + std::to_string(meas.used) + " bytes");
+    return RH_ENOMEM;
+  }
+  const SketchBufs b = carve_sketch(ar, pl, dtype);
+  const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)mode;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == RH_F64) return run_sketch<double>(pl, static_cast<const double*>(X), seed, sid, b, Y, norm2, st);
+  return run_sketch<float>(pl, static_cast<const float*>(X), seed, sid, b, Y, norm2, st);
+}
+
+size_t rh_orthonormalize_workspace_size(int64_t m, int32_t n) {
+  if (m < 1 || n < 1 || n > RH_MAX_ELL || n > m) return 0;
+  return sizeof(double) * orth_workspace_elems(m, n) + 256;
+}
+
+rh_status rh_orthonormalize(int64_t m, int32_t n, const double* Y, double* Q, int32_t* info, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  clear_error();
+  RH_CHECK_ARG(m >= 1 && n >= 1 && n <= RH_MAX_ELL && n <= m, "need 1 <= n <= min(m, 64)");
+  RH_CHECK_ARG(Y != nullptr && Q != nullptr, "Y and Q must be non-NULL");
+  if (workspace == nullptr || workspace_bytes < rh_orthonormalize_workspace_size(m, n)) {
+    set_error("workspace too small");
+    return RH_ENOMEM;
+  }
+  return launch_orthonormalize(m, n, Y, Q, info, static_cast<double*>(workspace), (cudaStream_t)stream);
+}
+
+size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                               const rh_options* opts) {
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  if (make_plan(order, dims, dtype, ranks, o, pl) != RH_OK) return 0;
+  Arena ar(nullptr);
+  carve(ar, pl);
+  return ar.used;
+}
+
+rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
+                   const rh_options* opts, double* const* factors, double* core, double* norms, int32_t* info,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  rh_status s = make_plan(order, dims, dtype, ranks, o, pl);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(X != nullptr && factors != nullptr && core != nullptr, "X, factors and core must be non-NULL");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(factors[k] != nullptr, "every factors[n] must be non-NULL");
+  Arena meas(nullptr);
+  carve(meas, pl);
+  if (workspace == nullptr || workspace_bytes < meas.used) {
+    set_error("workspace too small: need " + std::to_string(meas.used) + " bytes");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  const Bufs b = carve(ar, pl);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (info) RH_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * order, st));
+  if (dtype == RH_F64)
+    return run_rsthosvd<double>(pl, static_cast<const double*>(X), o, factors, core, norms, info, b, st);
+  return run_rsthosvd<float>(pl, static_cast<const float*>(X), o, factors, core, norms, info, b, st);
+}
+
+size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                                    const rh_options* opts) {
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  if (make_plan(order, dims, dtype, ranks, o, pl) != RH_OK) return 0;
+  Arena ar(nullptr);
+  int64_t n = 1, ncore = 1;
+  for (int k = 0; k < order; ++k) n *= dims[k];
+  const size_t esz = dtype == RH_F64 ? sizeof(double) : sizeof(float);
+  ar.take<char>((size_t)n * esz);
+  std::vector<int64_t> kout(order, 0);
+  for (const Step& sp : pl.steps) kout[sp.mode] = sp.ko;
+  for (int k = 0; k < order; ++k) {
+    ar.take<double>((size_t)dims[k] * kout[k]);
+    ncore *= kout[k];
+  }
+  ar.take<double>((size_t)ncore);
+  ar.take<double>(2);
+  carve(ar, pl);
+  return ar.used;
+}
+
+rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const void* X_host, const int32_t* ranks,
+                        const rh_options* opts, double* const* factors_host, double* core_host, double* norms_host,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  rh_status s = make_plan(order, dims, dtype, ranks, o, pl);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(X_host != nullptr && factors_host != nullptr && core_host != nullptr,
+               "X_host, factors_host and core_host must be non-NULL");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(factors_host[k] != nullptr, "every factors_host[n] must be non-NULL");
+  const size_t need = rsthosvd_host_workspace_size(order, dims, dtype, ranks, opts);
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  int64_t n = 1, ncore = 1;
+  for (int k = 0; k < order; ++k) n *= dims[k];
+  const size_t esz = dtype == RH_F64 ? sizeof(double) : sizeof(float);
+  void* Xd = ar.take<char>((size_t)n * esz);
+  std::vector<int64_t> kout(order, 0);
+  for (const Step& sp : pl.steps) kout[sp.mode] = sp.ko;
+  std::vector<double*> fd(order);
+  for (int k = 0; k < order; ++k) {
+    fd[k] = ar.take<double>((size_t)dims[k] * kout[k]);
+    ncore *= kout[k];
+  }
+  double* cored = ar.take<double>((size_t)ncore);
+  double* normsd = ar.take<double>(2);
+  const Bufs b = carve(ar, pl);
+  cudaStream_t st = (cudaStream_t)stream;
+  RH_CUDA_TRY(cudaMemcpyAsync(Xd, X_host, (size_t)n * esz, cudaMemcpyHostToDevice, st));
+  if (dtype == RH_F64)
+    s = run_rsthosvd<double>(pl, static_cast<const double*>(Xd), o, fd.data(), cored, normsd, nullptr, b, st);
+  else
+    s = run_rsthosvd<float>(pl, static_cast<const float*>(Xd), o, fd.data(), cored, normsd, nullptr, b, st);
+  if (s != RH_OK) return s;
+  for (int k = 0; k < order; ++k)
+    RH_CUDA_TRY(cudaMemcpyAsync(factors_host[k], fd[k], sizeof(double) * dims[k] * kout[k], cudaMemcpyDeviceToHost, st));
+  RH_CUDA_TRY(cudaMemcpyAsync(core_host, cored, sizeof(double) * ncore, cudaMemcpyDeviceToHost, st));
+  if (norms_host) RH_CUDA_TRY(cudaMemcpyAsync(norms_host, normsd, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  return RH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// Range-finder sketch Y_n = G_(n) Omega_n with Omega generated on the fly
+// (Alg. 1 step 1; Sec. 3.1: Omega need not be stored).
+//
+// G is read through its 3-D mode view (L, I, R): element (i, p) of the unfolding,
+// p = l + L r its Kolda column index, sits at (p % L) + L I (p / L) + L i.  Nothing is
+// materialised: the unfolding is an index map.
+//
+// Parallelisation: CTA (bx, s) owns rows i in [128 bx, 128 bx + 128) and the column
+// range p in [s chunk, (s+1) chunk) of X_(n) (split-K over the long dimension).  Per
+// k-step of 32 columns it generates the 32 x ellp Omega tile into shared memory,
+// stages the 32 x 128 tile of G, and accumulates a 128 x ellp register tile.  Each
+// element of G is read exactly once over the whole grid, so the same pass also
+// accumulates ||G||_F^2.  Partial sketches land in a workspace and are summed in FP64
+// in a fixed order (deterministic).
+#include "common.cuh"
+#include "kernels.cuh"
+#include "philox.cuh"
+
+namespace rh {
+
+namespace {
+
+constexpr int kTI = 128;   // rows of Y per CTA
+constexpr int kKP = 32;    // columns of X_(n) per k-step
+constexpr int kNT = 256;   // threads per CTA
+constexpr int kFlush = 16; // FP32: k-steps per inner accumulator before folding into the outer one
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+// Swizzled column of the (k, col) element of a [32][128] staging tile: groups of one
+// 16-byte vector are XOR-permuted by the row so that both the column-wise stores and
+// the row-wise vector loads are free of bank conflicts.
+template <typename T>
+__device__ __forceinline__ int swz(int k, int col) {
+  return col ^ ((k & 7) * Vec<T>::n);
+}
+
+template <typename T, int ELLP, bool KCONTIG>
+__global__ void __launch_bounds__(kNT, 2)
+    sketch_kernel(const T* __restrict__ G, int64_t L, int64_t I, int64_t R, int ell, int64_t chunk, uint32_t k0,
+                  uint32_t k1, uint32_t sid, T* __restrict__ part, double* __restrict__ part_norm) {
+  constexpr int CG = ELLP / 4;      // groups of 4 Omega columns
+  constexpr int IG = kNT / CG;      // groups of rows
+  constexpr int TM = kTI / IG;      // rows per thread
+  constexpr int VN = Vec<T>::n;
+  using V = typename Vec<T>::type;
+  static_assert(TM % VN == 0, "row group must be a whole number of vectors");
+
+  __shared__ __align__(16) T Xs[kKP][kTI];
+  __shared__ __align__(16) float Os[kKP][ELLP];
+  __shared__ int64_t base_s[kKP];
+  __shared__ double red[kNT / 32];
+
+  const int tid = threadIdx.x;
+  const int tc = tid % CG;
+  const int ti = tid / CG;
+  const int64_t i0 = (int64_t)blockIdx.x * kTI;
+  const int64_t M = L * R;
+  const int64_t pb = (int64_t)blockIdx.y * chunk;
+  const int64_t pe = min(M, pb + chunk);
+
+  T acc[TM][4];
+  T acc2[TM][4];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = acc2[a][b] = T(0);
+  double nrm = 0.0;
+
+  int step = 0;
+  for (int64_t p0 = pb; p0 < pe; p0 += kKP, ++step) {
+    // -- column offsets of this k-step (non-contiguous view only)
+    if (!KCONTIG) {
+      if (tid < kKP) {
+        const int64_t p = p0 + tid;
+        base_s[tid] = (p < pe) ? (p % L) + L * I * (p / L) : int64_t(-1);
+      }
+      __syncthreads();
+    }
+    // -- Omega tile
+    for (int t = tid; t < kKP * CG; t += kNT) {
+      const int kp = t / CG, q = t % CG;
+      const int64_t p = p0 + kp;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < pe) v = rng::omega4(k0, k1, sid, p, (uint32_t)q);
+      *reinterpret_cast<float4*>(&Os[kp][4 * q]) = v;
+    }
+    // -- G tile, Xs[kp][ii] = G(i0 + ii, p0 + kp)
+    T ss = T(0);
+    if (KCONTIG) {
+      // L == 1: element at I p + i, rows contiguous.
+#pragma unroll 4
+      for (int j = 0; j < (kKP * kTI) / kNT; ++j) {
+        const int t = tid + j * kNT;
+        const int ii = t % kTI, kp = t / kTI;
+        const int64_t p = p0 + kp, i = i0 + ii;
+        T x = T(0);
+        if (p < pe && i < I) x = __ldg(G + I * p + i);
+        ss += x * x;
+        Xs[kp][swz<T>(kp, ii)] = x;
+      }
+    } else {
+      const int lane = tid & 31, w = tid >> 5;
+#pragma unroll 4
+      for (int j = 0; j < (kKP * kTI) / kNT; ++j) {
+        const int kp = (lane & 7) + 8 * (j & 3);
+        const int ii = (lane >> 3) + 4 * w + 32 * (j >> 2);
+        const int64_t b = base_s[kp];
+        const int64_t i = i0 + ii;
+        T x = T(0);
+        if (b >= 0 && i < I) x = __ldg(G + b + L * i);
+        ss += x * x;
+        Xs[kp][swz<T>(kp, ii)] = x;
+      }
+    }
+    nrm += (double)ss;
+    __syncthreads();
+    // -- accumulate the 128 x ELLP register tile
+#pragma unroll 8
+    for (int kp = 0; kp < kKP; ++kp) {
+      T xv[TM];
+#pragma unroll
+      for (int a = 0; a < TM; a += VN) {
+        const V v = *reinterpret_cast<const V*>(&Xs[kp][swz<T>(kp, ti * TM + a)]);
+        if constexpr (VN == 4) {
+          xv[a] = v.x; xv[a + 1] = v.y; xv[a + 2] = v.z; xv[a + 3] = v.w;
+        } else {
+          xv[a] = v.x; xv[a + 1] = v.y;
+        }
+      }
+      const float4 o = *reinterpret_cast<const float4*>(&Os[kp][4 * tc]);
+      const T ov[4] = {T(o.x), T(o.y), T(o.z), T(o.w)};
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xv[a], ov[b], acc[a][b]);
+    }
+    if (sizeof(T) == 4 && (step % kFlush) == kFlush - 1) {
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc2[a][b] += acc[a][b];
+          acc[a][b] = T(0);
+        }
+    }
+    __syncthreads();
+  }
+  // -- write the partial sketch part[s][c][i]
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int64_t i = i0 + ti * TM + a;
+    if (i >= I) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = 4 * tc + b;
+      if (c < ell) part[((int64_t)blockIdx.y * ell + c) * I + i] = acc2[a][b] + acc[a][b];
+    }
+  }
+  // -- partial ||G||^2 of the elements this CTA loaded
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((tid & 31) == 0) red[tid >> 5] = nrm;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kNT / 32; ++k) s += red[k];
+    part_norm[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void sketch_reduce_kernel(const T* __restrict__ part, int S, int64_t I, int ell, double* __restrict__ Y,
+                                     const double* __restrict__ part_norm, int nnorm, double* __restrict__ norm2) {
+  const int64_t total = I * ell;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % I;
+    const int64_t c = t / I;
+    double s = 0.0;
+    for (int k = 0; k < S; ++k) s += (double)part[((int64_t)k * ell + c) * I + i];
+    Y[i + I * c] = s;
+  }
+  if (norm2 != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nnorm; ++k) s += part_norm[k];
+    *norm2 = s;
+  }
+}
+
+}  // namespace
+
+SketchPlan plan_sketch(const ModeView& v, int ell) {
+  SketchPlan pl;
+  pl.v = v;
+  pl.ell = ell;
+  pl.ellp = ell_pad_of(ell);
+  pl.gx = (int)ceil_div(v.I, kTI);
+  const int64_t M = v.M();
+  const int64_t ksteps = ceil_div(M, kKP);
+  const int64_t target = 4LL * num_sms();
+  int64_t S = std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, pl.gx), ksteps));
+  pl.chunk = ceil_div(ceil_div(M, S), kKP) * kKP;
+  pl.S = (int)ceil_div(M, pl.chunk);
+  return pl;
+}
+
+template <typename T>
+rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_t sid, T* part, double* part_norm,
+                        cudaStream_t st) {
+  const dim3 grid(pl.gx, pl.S);
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  const bool kc = (pl.v.L == 1);
+#define RH_SK(E, KC)                                                                                     \
+  sketch_kernel<T, E, KC><<<grid, kNT, 0, st>>>(G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, \
+                                                part_norm)
+  if (pl.ellp == 32) {
+    if (kc) RH_SK(32, true); else RH_SK(32, false);
+  } else {
+    if (kc) RH_SK(64, true); else RH_SK(64, false);
+  }
+#undef RH_SK
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+template <typename T>
+rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y, double* norm2,
+                               cudaStream_t st) {
+  const int64_t total = pl.v.I * pl.ell;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>(ceil_div(total, threads), 4096);
+  sketch_reduce_kernel<T><<<blocks, threads, 0, st>>>(part, pl.S, pl.v.I, pl.ell, Y, part_norm,
+                                                      (int)pl.norm_elems(), norm2);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+template rh_status launch_sketch<float>(const SketchPlan&, const float*, uint64_t, uint32_t, float*, double*,
+                                        cudaStream_t);
+template rh_status launch_sketch<double>(const SketchPlan&, const double*, uint64_t, uint32_t, double*, double*,
+                                         cudaStream_t);
+template rh_status launch_sketch_reduce<float>(const SketchPlan&, const float*, const double*, double*, double*,
+                                               cudaStream_t);
+template rh_status launch_sketch_reduce<double>(const SketchPlan&, const double*, const double*, double*, double*,
+                                                cudaStream_t);
+
+}  // namespace rh

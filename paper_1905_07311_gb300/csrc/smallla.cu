@@ -1,0 +1,690 @@
+// Small dense linear algebra of RandSVD (Alg. 1 steps 2 and 4-5), all on the device:
+//
+//   orthonormalize  thin QR of the sketch Y (I x ell): CholeskyQR2 in FP64; a Cholesky
+//                   pivot below 1e-14 of its diagonal (kappa(Y) beyond ~1e7) raises a
+//                   device flag and a single-CTA Householder QR then produces Q.  The
+//                   branch is taken on the device, with no host synchronisation.
+//   trunc_svd       SVD of B = Q^T G_(n) (ell x M): tall-skinny Householder QR of B^T
+//                   (a tree of per-CTA QRs, never the Gram matrix B B^T, so the small
+//                   singular values survive), then a one-sided Jacobi SVD of the final
+//                   ell x ell triangle R.  B = R^T Q_B^T, so the left singular vectors of
+//                   B are the right singular vectors of R, i.e. the accumulated rotations.
+//   factor          A_n = Q U_B(:, 1:r) (Alg. 1 step 5).
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rh {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum for blockDim.x a multiple of 32 (<= 1024); every thread gets the result.
+template <typename T>
+__device__ T block_sum(T v, T* scratch /* >= 33 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T s = lane < nw ? scratch[lane] : T(0);
+    s = warp_sum(s);
+    if (lane == 0) scratch[32] = s;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+// ---------------------------------------------------------------------------------
+// CholeskyQR2
+// ---------------------------------------------------------------------------------
+// Gpart[b] = A_b^T A_b over row block b (rows [b rb, b rb + rb)), upper triangle j <= k.
+__global__ void gram_partial_kernel(const double* __restrict__ A, int64_t m, int n, int rb,
+                                    double* __restrict__ Gpart, const int32_t* __restrict__ flag) {
+  if (flag != nullptr && *flag) return;
+  extern __shared__ double As[];  // rb x n, row-major
+  const int64_t r0 = (int64_t)blockIdx.x * rb;
+  const int rows = (int)(m - r0 < rb ? m - r0 : rb);
+  for (int t = threadIdx.x; t < rb * n; t += blockDim.x) {
+    const int r = t % rb, c = t / rb;
+    As[r * n + c] = (r < rows) ? A[r0 + r + m * (int64_t)c] : 0.0;
+  }
+  __syncthreads();
+  const int npair = n * (n + 1) / 2;
+  for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+    // e -> (j, k), j <= k, column-major upper triangle
+    int k = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while ((k + 1) * (k + 2) / 2 <= e) ++k;
+    while (k * (k + 1) / 2 > e) --k;
+    const int j = e - k * (k + 1) / 2;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s = fma(As[r * n + j], As[r * n + k], s);
+    Gpart[(int64_t)blockIdx.x * n * n + j + n * k] = s;
+  }
+}
+
+// C = sum_b Gpart[b] (fixed order), upper triangle; one thread per entry.
+__global__ void gram_reduce_kernel(const double* __restrict__ Gpart, int nb, int n, double* __restrict__ C,
+                                   const int32_t* __restrict__ flag) {
+  if (flag != nullptr && *flag) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int j = e % n, k = e / n;
+  if (j > k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += Gpart[(int64_t)b * n * n + e];
+  C[e] = s;
+}
+
+// Cholesky C = R^T R (R upper) in one CTA; flag <- 1 on a pivot <= 1e-14 C_kk (or not finite).
+__global__ void cholesky_kernel(const double* __restrict__ C, int n, double* __restrict__ R,
+                                int32_t* __restrict__ flag) {
+  if (*flag) return;
+  extern __shared__ double S[];  // n x n column-major working copy (upper part used)
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e % n, k = e / n;
+    S[e] = (j <= k) ? C[e] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const double d = S[k + n * k];
+    const double diag0 = C[k + n * k];
+    if (!(d > 1e-14 * diag0) || !isfinite(d)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;  // uniform across the block (all threads read the same d)
+    }
+    const double rkk = sqrt(d);
+    __syncthreads();
+    // row k of R: R[k, j] = S[k, j] / rkk, j > k
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) S[k + n * j] /= rkk;
+    __syncthreads();
+    if (threadIdx.x == 0) S[k + n * k] = rkk;
+    // trailing update S[i, j] -= R[k, i] R[k, j], k < i <= j
+    const int m2 = n - k - 1;
+    for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) {
+      const int i = k + 1 + e % m2, j = k + 1 + e / m2;
+      if (i <= j) S[i + n * j] -= S[k + n * i] * S[k + n * j];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) *flag = 1;
+    return;
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e % n, k = e / n;
+    R[e] = (j <= k) ? S[e] : 0.0;
+  }
+}
+
+// Out = A R^{-1} row by row (forward substitution on x^T R = a^T); one warp per row.
+__global__ void trsm_rows_kernel(const double* __restrict__ A, int64_t m, int n, const double* __restrict__ R,
+                                 double* __restrict__ Out, const int32_t* __restrict__ flag) {
+  if (*flag) return;
+  extern __shared__ double Rs[];  // n x n column-major
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[e] = R[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
+    // lane holds columns lane and lane + 32
+    double y0 = lane < n ? A[row + m * lane] : 0.0;
+    double y1 = lane + 32 < n ? A[row + m * (lane + 32)] : 0.0;
+    for (int c = 0; c < n; ++c) {
+      const double yc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31);
+      const double xc = yc / Rs[c + n * c];
+      if (lane == (c & 31)) {
+        if (c < 32) y0 = xc; else y1 = xc;
+      }
+      // subtract xc R[c, j] from the not yet solved columns j > c
+      if (lane > c && lane < n) y0 -= xc * Rs[c + n * lane];
+      if (lane + 32 > c && lane + 32 < n) y1 -= xc * Rs[c + n * (lane + 32)];
+    }
+    if (lane < n) Out[row + m * lane] = y0;
+    if (lane + 32 < n) Out[row + m * (lane + 32)] = y1;
+  }
+}
+
+// Householder QR of Y (m x n) with explicit thin Q, one CTA; runs only when *flag is set
+// (or always when flag == nullptr).  W is an m x n FP64 scratch copy; beta has n slots.
+__global__ void householder_q_kernel(const double* __restrict__ Y, int64_t m, int n, double* __restrict__ W,
+                                     double* __restrict__ beta, double* __restrict__ Q,
+                                     const int32_t* __restrict__ flag, int32_t* __restrict__ info) {
+  const bool run = (flag == nullptr) || (*flag != 0);
+  if (info != nullptr && threadIdx.x == 0) *info = run ? 1 : 0;
+  if (!run) return;
+  __shared__ double scratch[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) W[e] = Y[e];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double* x = W + m * (int64_t)k;
+    double s = 0.0;
+    for (int64_t i = k + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
+    s = block_sum(s, scratch);
+    const double alpha = x[k];
+    const double nrm = sqrt(s);
+    double b = 0.0;
+    if (nrm > 0.0) {
+      const double sg = alpha >= 0.0 ? 1.0 : -1.0;
+      b = 1.0 / (nrm * (nrm + fabs(alpha)));
+      __syncthreads();
+      if (threadIdx.x == 0) x[k] = alpha + sg * nrm;  // v = x + sign(alpha) ||x|| e_1
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) beta[k] = b;
+    // apply H = I - b v v^T to columns j > k
+    for (int j = k + 1 + w; j < n; j += nw) {
+      double* y = W + m * (int64_t)j;
+      double d = 0.0;
+      for (int64_t i = k + lane; i < m; i += 32) d += x[i] * y[i];
+      d = warp_sum(d) * b;
+      for (int64_t i = k + lane; i < m; i += 32) y[i] -= d * x[i];
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{n-1} [I_n; 0], accumulated backwards
+  for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
+    const int64_t i = e % m, j = e / m;
+    Q[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = n - 1; k >= 0; --k) {
+    const double* v = W + m * (int64_t)k;
+    const double b = beta[k];
+    if (b != 0.0) {
+      for (int j = k + w; j < n; j += nw) {
+        double* q = Q + m * (int64_t)j;
+        double d = 0.0;
+        for (int64_t i = k + lane; i < m; i += 32) d += v[i] * q[i];
+        d = warp_sum(d) * b;
+        for (int64_t i = k + lane; i < m; i += 32) q[i] -= d * v[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Tall-skinny QR (R only) of B^T and the one-sided Jacobi SVD
+// ---------------------------------------------------------------------------------
+// In-shared-memory Householder triangularisation of a rows x n block (column-major,
+// leading dimension ld, which the callers keep odd so that a warp reading one row of 32
+// consecutive columns hits 32 different banks), leaving R in the upper triangle.
+// Per column k: the norm of the trailing part of column k (block reduction); then
+// w_j = v^T A(k:, j) for all j > k with the columns spread over the lanes and the rows
+// over CW-wide thread groups (partials reduced through shared memory); then the rank-1
+// update A(k:, j) -= beta w_j v with the same thread layout.  ``red`` holds >= nt + 64
+// elements of T.
+template <typename T>
+__device__ void smem_householder_r(T* A, int rows, int n, int ld, T* scratch, T* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int CW = (n <= 32) ? 32 : 64;        // column slots
+  const int NCH = nt / CW;                    // row groups
+  const int jj = tid % CW, ch = tid / CW;
+  const int kmax = min(rows, n);
+  T* wv = red + nt;                            // CW scaled dot products
+  for (int k = 0; k < kmax; ++k) {
+    T* x = A + (int64_t)ld * k;
+    T s = T(0);
+    for (int i = k + tid; i < rows; i += nt) s += x[i] * x[i];
+    s = block_sum(s, scratch);
+    const T alpha = x[k];
+    const T nrm = sqrt(s);
+    if (nrm == T(0)) continue;  // uniform
+    const T sg = alpha >= T(0) ? T(1) : T(-1);
+    const T b = T(1) / (nrm * (nrm + fabs(alpha)));
+    __syncthreads();
+    if (tid == 0) x[k] = alpha + sg * nrm;     // v = x + sign(alpha) ||x|| e_1
+    __syncthreads();
+    const int j = k + 1 + jj;
+    const bool active = j < n;
+    const T* y = A + (int64_t)ld * (active ? j : k);
+    T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+    int i = k + ch;
+    if (active) {
+      for (; i + 3 * NCH < rows; i += 4 * NCH) {
+        d0 += x[i] * y[i];
+        d1 += x[i + NCH] * y[i + NCH];
+        d2 += x[i + 2 * NCH] * y[i + 2 * NCH];
+        d3 += x[i + 3 * NCH] * y[i + 3 * NCH];
+      }
+      for (; i < rows; i += NCH) d0 += x[i] * y[i];
+    }
+    red[ch * CW + jj] = (d0 + d1) + (d2 + d3);
+    __syncthreads();
+    if (tid < CW) {
+      T w = T(0);
+      for (int c = 0; c < NCH; ++c) w += red[c * CW + tid];
+      wv[tid] = w * b;
+    }
+    __syncthreads();
+    if (active) {
+      const T w = wv[jj];
+      T* yy = A + (int64_t)ld * j;
+      for (int r = k + ch; r < rows; r += NCH) yy[r] -= w * x[r];
+    }
+    __syncthreads();
+    if (tid == 0) x[k] = -sg * nrm;            // R_kk
+    __syncthreads();
+  }
+}
+
+// Level 0: block b holds rows [b rows0, ...) of B^T, with B^T[p, c] = B[(p % L) + L n (p / L) + L c].
+template <typename T>
+__global__ void __launch_bounds__(1024) tsqr_leaf_kernel(const T* __restrict__ B, int64_t L, int64_t R, int n,
+                                                         int rows0, int ld, T* __restrict__ Rout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* red = A + (int64_t)ld * n;
+  __shared__ T scratch[33];
+  const int64_t M = L * R;
+  const int64_t p0 = (int64_t)blockIdx.x * rows0;
+  const int rows = (int)(M - p0 < rows0 ? M - p0 : rows0);
+  if (L == 1) {
+    // B^T rows are contiguous: element (r, c) at n (p0 + r) + c; read the block linearly
+    const T* src = B + n * p0;
+    for (int e = threadIdx.x; e < rows0 * n; e += blockDim.x) {
+      const int r = e / n, c = e % n;
+      A[r + (int64_t)ld * c] = (r < rows) ? src[e] : T(0);
+    }
+  } else {
+    for (int r = threadIdx.x; r < rows0; r += blockDim.x) {
+      const int64_t p = p0 + r;
+      if (r < rows) {
+        const int64_t base = (p % L) + L * (int64_t)n * (p / L);
+        for (int c = 0; c < n; ++c) A[r + (int64_t)ld * c] = B[base + L * c];
+      } else {
+        for (int c = 0; c < n; ++c) A[r + (int64_t)ld * c] = T(0);
+      }
+    }
+  }
+  __syncthreads();
+  smem_householder_r(A, max(rows, n), n, ld, scratch, red);
+  T* o = Rout + (int64_t)blockIdx.x * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e % n, k = e / n;
+    o[e] = (j <= k && j < rows) ? A[j + (int64_t)ld * k] : T(0);
+  }
+}
+
+// Higher level: block b stacks R's [b fan, b fan + fan) (each n x n) and re-triangularises.
+template <typename T>
+__global__ void __launch_bounds__(1024) tsqr_merge_kernel(const T* __restrict__ Rin, int64_t nin, int n, int fan,
+                                                          int ld, T* __restrict__ Rout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* red = A + (int64_t)ld * n;
+  __shared__ T scratch[33];
+  const int64_t b0 = (int64_t)blockIdx.x * fan;
+  const int cnt = (int)(nin - b0 < fan ? nin - b0 : fan);
+  const int rows = cnt * n;
+  for (int e = threadIdx.x; e < ld * n; e += blockDim.x) {
+    const int r = e % ld, c = e / ld;
+    const int q = r / n, j = r % n;
+    A[r + (int64_t)ld * c] = (q < cnt && r < fan * n) ? Rin[(b0 + q) * n * n + j + n * c] : T(0);
+  }
+  __syncthreads();
+  smem_householder_r(A, rows, n, ld, scratch, red);
+  T* o = Rout + (int64_t)blockIdx.x * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e % n, k = e / n;
+    o[e] = (j <= k) ? A[j + (int64_t)ld * k] : T(0);
+  }
+}
+
+// One-sided Jacobi on the columns of R (n x n): R V = U S.  Writes Ub = V with columns
+// sorted by decreasing singular value and sv (both FP64).  One warp per column pair,
+// round-robin ordering; at most 60 sweeps.
+template <typename T>
+__global__ void jacobi_svd_kernel(const T* __restrict__ Rin, int n, double* __restrict__ Ub, double* __restrict__ sv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int np = (n + 1) & ~1;  // even number of players, last one a dummy if n is odd
+  T* Mt = reinterpret_cast<T*>(smem_raw);   // np columns of length n
+  T* V = Mt + (int64_t)np * n;              // np columns of length n
+  __shared__ int rotated;
+  __shared__ T sig[RH_MAX_ELL + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    Mt[e] = (j < n) ? Rin[i + n * j] : T(0);
+    V[e] = (j < n && i == j) ? T(1) : T(0);
+  }
+  // rotation threshold max(n, 8) * eps: below the rounding level of the inner products
+  // the test could never be met and the sweeps would run to the cap
+  const T tol = T(max(n, 8)) * ((sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16));
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int pr = w; pr < np / 2; pr += nw) {
+        int a, b;
+        if (pr == 0) {
+          a = np - 1;
+          b = rnd;
+        } else {
+          a = (rnd + pr) % (np - 1);
+          b = (rnd - pr + (np - 1)) % (np - 1);
+        }
+        if (a >= n || b >= n) continue;
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        T* xa = Mt + (int64_t)n * a;
+        T* xb = Mt + (int64_t)n * b;
+        T al = T(0), be = T(0), ga = T(0);
+        for (int i = lane; i < n; i += 32) {
+          al += xa[i] * xa[i];
+          be += xb[i] * xb[i];
+          ga += xa[i] * xb[i];
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const T zeta = (be - al) / (T(2) * ga);
+          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + t * t);
+          const T s = c * t;
+          T* va = V + (int64_t)n * a;
+          T* vb = V + (int64_t)n * b;
+          for (int i = lane; i < n; i += 32) {
+            const T xai = xa[i], xbi = xb[i];
+            xa[i] = c * xai - s * xbi;
+            xb[i] = s * xai + c * xbi;
+            const T vai = va[i], vbi = vb[i];
+            va[i] = c * vai - s * vbi;
+            vb[i] = s * vai + c * vbi;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;  // uniform: read after the barrier that ends the last round
+    __syncthreads();
+  }
+  // singular values and the sort
+  for (int j = w; j < n; j += nw) {
+    const T* x = Mt + (int64_t)n * j;
+    T s = T(0);
+    for (int i = lane; i < n; i += 32) s += x[i] * x[i];
+    s = warp_sum(s);
+    if (lane == 0) sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int rank = 0;
+    for (int k = 0; k < n; ++k) rank += (sig[k] > sig[j]) || (sig[k] == sig[j] && k < j);
+    sv[rank] = (double)sig[j];
+    for (int i = 0; i < n; ++i) Ub[i + n * rank] = (double)V[i + n * j];
+  }
+}
+
+template <typename T>
+__global__ void factor_cast_kernel(int64_t I, int ell, int r, const double* __restrict__ Q,
+                                   const double* __restrict__ Ub, double* __restrict__ A, T* __restrict__ Uc) {
+  const int64_t total = I * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % I;
+    const int k = (int)(e / I);
+    double s = 0.0;
+    for (int c = 0; c < ell; ++c) s = fma(Q[i + I * c], Ub[c + (int64_t)ell * k], s);
+    A[e] = s;
+  }
+  if (Uc != nullptr) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)ell * r;
+         e += (int64_t)gridDim.x * blockDim.x)
+      Uc[e] = (T)Ub[e];
+  }
+}
+
+// Column-sign convention shared with the oracle: flip column k of A (m x n) so that its
+// largest-magnitude entry (first index on ties) is positive; apply the same flip to
+// column k of ``other`` (rows_o x n, leading dimension rows_o) when given.  One CTA per column.
+template <typename T>
+__global__ void colsign_kernel(double* __restrict__ A, int64_t m, int n, T* __restrict__ other, int rows_o) {
+  __shared__ double sv[32];
+  __shared__ int64_t si[32];
+  __shared__ double sgn;
+  const int k = blockIdx.x;
+  double* a = A + m * (int64_t)k;
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const double v = fabs(a[i]);
+    if (v > best) {  // strictly greater keeps the first index within a thread
+      best = v;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    sv[w] = best;
+    si[w] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sv[0];
+    int64_t ii = si[0];
+    for (int q = 1; q < nw; ++q)
+      if (sv[q] > b || (sv[q] == b && si[q] < ii)) {
+        b = sv[q];
+        ii = si[q];
+      }
+    sgn = (a[ii] < 0.0) ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  if (sgn < 0.0) {
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) a[i] = -a[i];
+    if (other != nullptr)
+      for (int i = threadIdx.x; i < rows_o; i += blockDim.x) other[i + (int64_t)rows_o * k] = -other[i + (int64_t)rows_o * k];
+  }
+}
+
+template <typename T>
+__global__ void cast_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+
+__global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+  __shared__ double scratch[33];
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s = fma(x[e], x[e], s);
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) *out = s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------
+static int gram_rows(int64_t m) {
+  const int64_t target = std::max<int64_t>(1, num_sms());
+  return (int)std::max<int64_t>(8, std::min<int64_t>(96, ceil_div(m, target)));
+}
+
+size_t orth_workspace_elems(int64_t m, int n) {
+  const int rb = gram_rows(m);
+  const int64_t nb = ceil_div(m, rb);
+  // Gpart | C | R | Q1 | W (Householder copy) | beta | flag (as one double)
+  return (size_t)(nb * n * n + n * n + n * n + m * n + m * n + n + 2) + 64;
+}
+
+rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
+                                cudaStream_t st) {
+  const int rb = gram_rows(m);
+  const int nb = (int)ceil_div(m, rb);
+  double* Gpart = ws;
+  double* C = Gpart + (size_t)nb * n * n;
+  double* R = C + n * n;
+  double* Q1 = R + n * n;
+  double* W = Q1 + m * n;
+  double* beta = W + m * n;
+  int32_t* flag = reinterpret_cast<int32_t*>(beta + n);
+  RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+  RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
+  const size_t gsm = sizeof(double) * rb * n;
+  const size_t nsm = sizeof(double) * n * n;
+  const int rblocks = (int)ceil_div((int64_t)n * n, 256);
+  const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
+  const double* src = Y;
+  double* dst = Q1;
+  for (int pass = 0; pass < 2; ++pass) {
+    gram_partial_kernel<<<nb, 256, gsm, st>>>(src, m, n, rb, Gpart, flag);
+    RH_LAUNCH_CHECK();
+    gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
+    RH_LAUNCH_CHECK();
+    cholesky_kernel<<<1, 256, nsm, st>>>(C, n, R, flag);
+    RH_LAUNCH_CHECK();
+    trsm_rows_kernel<<<tblocks, 256, nsm, st>>>(src, m, n, R, dst, flag);
+    RH_LAUNCH_CHECK();
+    src = Q1;
+    dst = Q;
+  }
+  householder_q_kernel<<<1, 1024, 0, st>>>(Y, m, n, W, beta, Q, flag, info);
+  RH_LAUNCH_CHECK();
+  colsign_kernel<double><<<n, 256, 0, st>>>(Q, m, n, nullptr, 0);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+static int smem_budget() { return 96 * 1024; }
+
+TruncPlan plan_trunc(const ModeView& vb, int ell) {
+  TruncPlan pl;
+  pl.v = vb;
+  pl.ell = ell;
+  return pl;
+}
+
+constexpr int kTsqrThreads = 1024;
+
+template <typename T>
+static void trunc_dims(TruncPlan& pl) {
+  const int n = pl.ell;
+  const int budget = smem_budget() - (int)sizeof(T) * (kTsqrThreads + 64);
+  int rows0 = budget / (int)(sizeof(T) * n) - 1;
+  rows0 = std::min(rows0, 512);
+  rows0 = std::max(rows0, 2 * n);
+  pl.rows0 = rows0;
+  pl.fan = std::max(2, rows0 / n);
+  pl.nblk0 = ceil_div(pl.v.M(), rows0);
+}
+
+static int odd_ld(int rows) { return rows | 1; }
+
+template <typename T>
+size_t trunc_workspace_elems(const TruncPlan& pl0) {
+  TruncPlan pl = pl0;
+  trunc_dims<T>(pl);
+  const int64_t nn = (int64_t)pl.ell * pl.ell;
+  // two ping-pong buffers of R's
+  return (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+}
+
+template <typename T>
+rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st) {
+  TruncPlan pl = pl0;
+  trunc_dims<T>(pl);
+  const int n = pl.ell;
+  const int64_t nn = (int64_t)n * n;
+  T* buf0 = ws;
+  T* buf1 = ws + pl.nblk0 * nn;
+  const int ld0 = odd_ld(pl.rows0);
+  const int ldm = odd_ld(pl.fan * n);
+  const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
+  const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
+  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+  tsqr_leaf_kernel<T><<<(unsigned)pl.nblk0, kTsqrThreads, sm0, st>>>(B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0);
+  RH_LAUNCH_CHECK();
+  int64_t cnt = pl.nblk0;
+  T* cur = buf0;
+  T* nxt = buf1;
+  while (cnt > 1) {
+    const int64_t nout = ceil_div(cnt, pl.fan);
+    tsqr_merge_kernel<T><<<(unsigned)nout, kTsqrThreads, smm, st>>>(cur, cnt, n, pl.fan, ldm, nxt);
+    RH_LAUNCH_CHECK();
+    cnt = nout;
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  const int np = (n + 1) & ~1;
+  const size_t smj = sizeof(T) * 2 * (size_t)np * n;
+  RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
+  {
+    ProfileScope ps(PROF_JACOBI, 0, st);
+    jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(cur, n, Ub, sv);
+    RH_LAUNCH_CHECK();
+  }
+  return RH_OK;
+}
+
+template <typename T>
+rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, const double* Ub, double* A, T* Uc,
+                                 cudaStream_t st) {
+  const int64_t total = std::max<int64_t>(I * r, (int64_t)ell * r);
+  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 8 * num_sms());
+  factor_cast_kernel<T><<<blocks, 256, 0, st>>>(I, ell, r, Q, Ub, A, Uc);
+  RH_LAUNCH_CHECK();
+  colsign_kernel<T><<<r, 256, 0, st>>>(A, I, r, Uc, ell);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+template <typename T>
+rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
+  cast_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>(src, dst, n);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st) {
+  sumsq_kernel<<<1, 1024, 0, st>>>(x, n, out);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+template size_t trunc_workspace_elems<float>(const TruncPlan&);
+template size_t trunc_workspace_elems<double>(const TruncPlan&);
+template rh_status launch_trunc_svd<float>(const TruncPlan&, const float*, float*, double*, double*, cudaStream_t);
+template rh_status launch_trunc_svd<double>(const TruncPlan&, const double*, double*, double*, double*, cudaStream_t);
+template rh_status launch_factor_and_cast<float>(int64_t, int, int, const double*, const double*, double*, float*,
+                                                 cudaStream_t);
+template rh_status launch_factor_and_cast<double>(int64_t, int, int, const double*, const double*, double*, double*,
+                                                  cudaStream_t);
+template rh_status launch_cast<float>(const double*, float*, int64_t, cudaStream_t);
+template rh_status launch_cast<double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace rh

@@ -1,0 +1,120 @@
+"""The C-ABI library on a machine without a GPU: it builds, loads, exports every symbol
+that include/rhosvd.h declares, and rejects invalid arguments before touching the device.
+No compute call is made here.
+"""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1905_07311_gb300 import build as b
+
+    b.build()
+    from paper_1905_07311_gb300 import _lib
+
+    return _lib.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "rhosvd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:rh_status|size_t|const char\*|void|uint64_t)\s+(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for n in ["rh_omega", "rhosvd_sketch", "rh_orthonormalize", "rsthosvd", "rh_last_error", "rh_version"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_1905_07311_gb300 import _lib
+
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s+(\w+)$", out, flags=re.M))
+    for n in _declared():
+        assert n in exported, n
+        assert hasattr(L, n)
+
+
+def test_version_and_defaults(L):
+    from paper_1905_07311_gb300 import _lib
+
+    assert b"sm_103a" in L.rh_version()
+    o = _lib.make_options()
+    assert o.p == 5 and o.rho[0] == -1 and o.truncate == 1 and o.clamp == 0
+
+
+def _ws(L, dims, ranks, dtype=0, **kw):
+    from paper_1905_07311_gb300 import _lib
+
+    o = _lib.make_options(**kw)
+    return L.rsthosvd_workspace_size(len(dims), _lib.i64_array(dims), dtype, _lib.i32_array(ranks), ctypes.byref(o))
+
+
+def _call_invalid(L, dims, ranks, dtype=0, **kw):
+    from paper_1905_07311_gb300 import _lib
+
+    o = _lib.make_options(**kw)
+    fp = (ctypes.c_void_p * len(dims))(*([1] * len(dims)))
+    code = L.rsthosvd(len(dims), _lib.i64_array(dims), dtype, ctypes.c_void_p(1), _lib.i32_array(ranks),
+                      ctypes.byref(o), fp, ctypes.c_void_p(1), None, None, None, 0, None)
+    return code, L.rh_last_error().decode()
+
+
+def test_size_rule_is_enforced_before_launch(L):
+    # r + p > I_n violates the REQUIRE line of Alg. 3
+    code, msg = _call_invalid(L, [10, 40, 40], [8, 4, 4], p=5)
+    assert code == 1 and "exceeds" in msg
+    assert _ws(L, [10, 40, 40], [8, 4, 4], p=5) == 0
+    # the same request is accepted with clamping
+    assert _ws(L, [10, 40, 40], [8, 4, 4], p=5, clamp=True) > 0
+    # the rule is checked on the current core: after mode 0 is truncated to 2, mode 1 sees M = 2 * 3
+    code, msg = _call_invalid(L, [50, 50, 3], [2, 5, 3], p=2, rho=[0, 1, 2])
+    assert code == 1
+
+
+@pytest.mark.parametrize("bad", [dict(dims=[0, 4]), dict(dims=[4] * 9), dict(ranks=[0, 2])])
+def test_invalid_shapes(L, bad):
+    dims = bad.get("dims", [8, 8])
+    ranks = bad.get("ranks", [2] * len(dims))
+    code, _ = _call_invalid(L, dims, ranks, p=1)
+    assert code == 1
+
+
+def test_bad_dtype_and_order(L):
+    code, msg = _call_invalid(L, [8, 8], [2, 2], dtype=7, p=1)
+    assert code == 1 and "dtype" in msg
+    code, msg = _call_invalid(L, [8, 8], [2, 2], p=1, rho=[0, 0])
+    assert code == 1 and "permutation" in msg
+
+
+def test_ell_beyond_64_is_unsupported(L):
+    code, msg = _call_invalid(L, [200, 200, 200], [60, 20, 20], p=10)
+    assert code == 6 and "64" in msg
+
+
+def test_workspace_query_is_positive_and_monotone(L):
+    a = _ws(L, [100, 100, 100], [10, 10, 10], p=5)
+    b = _ws(L, [200, 200, 200], [10, 10, 10], p=5)
+    assert 0 < a < b
+
+
+def test_omega_and_sketch_argument_checks(L):
+    assert L.rh_omega(0, 0, 16, 0, 4, 4, ctypes.c_void_p(1), None) == 1
+    assert L.rh_omega(0, -1, 0, 0, 4, 4, ctypes.c_void_p(1), None) == 1
+    from paper_1905_07311_gb300 import _lib
+
+    dims = _lib.i64_array([5, 6])
+    assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 2, 4, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 1
+    assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 0, 65, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 1
+    assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 0, 4, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 2
