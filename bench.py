@@ -124,7 +124,7 @@ def dist_setup():
 def make_input(torch, device, seed_offset=0):
     from workloads import lowrank_plus_noise_torch
 
-    return lowrank_plus_noise_torch(DIMS, [50, 50, 50], 0.9, 1e-3, 2 + seed_offset, torch.float32, device)
+    return lowrank_plus_noise_torch(DIMS, [50] * len(DIMS), 0.9, 1e-3, 2 + seed_offset, torch.float32, device)
 
 
 # ---------------------------------------------------------------------------------
@@ -317,7 +317,7 @@ def run_ours(args):
                 "data": "synthetic (seeded generator, inputs resident in HBM before timing)",
                 "config": {"workload": WORKLOAD, "dims": DIMS, "ranks": RANKS, "p": P, "seed": SEED,
                            "order": [n + 1 for n in RHO], "parallelism": f"independent tensor per GPU x{world}",
-                           "l2": "input (4.3 GB) larger than L2; no flush"},
+                           "l2": f"input ({np.prod(DIMS) * 4 / 1e9:.2f} GB) larger than L2 (129 MB); no flush"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "cpu_baseline": cpu, "breakdown_ms": breakdown}
         line.update(extra)
@@ -423,7 +423,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--dims", type=int, nargs=3, default=None,
+                    help="smaller cube for profiling captures (default 1024 1024 1024)")
     args = ap.parse_args()
+    if args.dims:
+        global DIMS, WORKLOAD
+        DIMS = list(args.dims)
+        WORKLOAD = WORKLOAD.replace("1024x1024x1024", "x".join(str(v) for v in DIMS))
     if args.impl == "reference":
         args.cpu_slab = args.cpu_slab or 128
         run_reference(args)
