@@ -131,6 +131,26 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * rhosvd_sketch_static -- rhosvd_sketch for callers that must not allocate device memory.
+ *   The paper has no counterpart: this is a deployment variant of the sketch above, with the
+ *   same arguments minus the workspace and the same output (up to the order of the FP32/FP64
+ *   partial sums).  Its scratch lives in a 16 MiB static device array inside the library that
+ *   every GPU loading the library keeps until the process exits; the caller allocates only
+ *   X, Y and norm2.  Intended for code that may not call cudaMalloc: plugins whose host
+ *   framework owns all device memory, loops that cannot take cudaMalloc's implicit device
+ *   synchronisation, processes whose device memory budget is fully reserved.
+ *   Limit: I_mode * ell * (4 or 8 bytes) plus a few KB of partial norms must fit in 16 MiB,
+ *   otherwise RH_EINVAL with a message (the number of split-K partials shrinks to fit).
+ *   The first call on a device looks up the array's address (cudaGetSymbolAddress) and must
+ *   precede any stream capture.  All calls share the array and leave their contents in it;
+ *   every element a call reads is written by that call first, but calls that overlap on the
+ *   GPU race.  No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+rh_status rhosvd_sketch_static(int32_t order, const int64_t* dims, int32_t dtype, const void* X,
+                               int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id, double* Y,
+                               double* norm2, void* stream);
+
+/*
  * rh_orthonormalize -- thin QR of a tall matrix, Y = Q R, returning Q (Alg. 1 step 2).
  *   Y  m x n FP64 column-major (read only), 1 <= n <= RH_MAX_ELL, n <= m.
  *   Q  m x n FP64 column-major output with orthonormal columns spanning range(Y).

@@ -47,6 +47,7 @@ SIGNATURES = {
     "rh_omega": (_I32, [_U64, _I32, _I32, _I64, _I64, _I32, _P, _P]),
     "rhosvd_sketch_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _I32]),
     "rhosvd_sketch": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P, _SZ, _P]),
+    "rhosvd_sketch_static": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P]),
     "rh_orthonormalize_workspace_size": (_SZ, [_I64, _I32]),
     "rh_orthonormalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _SZ, _P]),
     "rsthosvd_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
