@@ -164,6 +164,31 @@ rh_status rh_orthonormalize(int64_t m, int32_t n, const double* Y, double* Q, in
                             void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * rh_mode_product -- mode-n product (Sec. 2.1: Y = X x_n M means Y_(n) = M X_(n)), the step that
+ * forms B = Q^T X in Alg. 1 step 3, the core G = X x_1 A_1^T ... of Alg. 2 step 6 and the
+ * reconstruction G x_1 A_1 ... of a Tucker tensor.
+ *   X          tensor (order, dims, dtype), column-major.
+ *   transpose  1: A is I_mode x k (column-major), Y = X x_mode A^T;
+ *              0: A is k x I_mode (column-major), Y = X x_mode A.   A has X's dtype; k >= 1.
+ *   Y          output tensor with dims[mode] replaced by k, column-major, out_dtype = dtype or
+ *              RH_F64 (FP32 input with FP64 output).  The unfolding is never materialised.
+ */
+rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
+                          int32_t k, const void* A, int32_t transpose, int32_t out_dtype, void* Y, void* stream);
+
+/*
+ * rh_left_svd -- left singular vectors and singular values of the mode-n unfolding B_(n) of a tensor
+ * whose mode n is short (I_mode <= RH_MAX_ELL): the thin SVD of Alg. 1 step 4 applied to
+ * B = Q^T X.  B_(n)^T is triangularised by a tree of Householder QRs (no Gram matrix) and the
+ * I_mode x I_mode triangle is diagonalised by one-sided Jacobi, in B's precision.
+ *   U   I_mode x I_mode FP64, column-major, columns ordered by decreasing singular value
+ *       (column signs arbitrary);  sv  I_mode FP64 singular values, decreasing.
+ */
+size_t rh_left_svd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode);
+rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const void* B, int32_t mode,
+                      double* U, double* sv, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * rsthosvd -- R-STHOSVD (Alg. 3) with RandSVD (Alg. 1) on each current core unfolding.
  *   X        input tensor (order, dims, dtype), column-major device buffer.
  *   ranks    target ranks r_n (host array of ``order`` values, 1 <= r_n).
@@ -188,6 +213,43 @@ size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype
 rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
                    const rh_options* opts, double* const* factors, double* core, double* norms,
                    int32_t* info, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rhosvd -- R-HOSVD (Alg. 2): RandSVD (Alg. 1) of every unfolding X_(n) of the input with its own
+ * Omega_n, then the core G = X x_1 A_1^T ... x_d A_d^T (Alg. 2 step 6).  Arguments, outputs,
+ * options (rho is ignored: the modes are independent), size rule (on the input sizes, Alg. 2
+ * REQUIRE) and errors as rsthosvd; norms[1] = ||G||^2 (for R-HOSVD ||X - X_hat||^2 <= ||X||^2 -
+ * ||G||^2 only holds as an inequality; use rh_tucker_residual for the error).
+ */
+size_t rhosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                             const rh_options* opts);
+rh_status rhosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
+                 const rh_options* opts, double* const* factors, double* core, double* norms, int32_t* info,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * core_ttm -- G = X x_1 A_1^T x_2 A_2^T ... x_d A_d^T (Alg. 2 step 6; Sec. 2.2, HOSVD core).
+ *   factors  host array of ``order`` device pointers, A_n of size I_n x ks[n], FP64 column-major
+ *            (cast to X's precision for the products).
+ *   G        device output, ks[0] x ... x ks[order-1], FP64 column-major.
+ *   The modes are applied in the order that shrinks the intermediate tensor most first.
+ */
+size_t core_ttm_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ks);
+rh_status core_ttm(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const double* const* factors,
+                   const int32_t* ks, double* G, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rh_tucker_residual -- direct error of a Tucker approximation (validation of Thm. lem:st_mode_err
+ * and of the bounds of Sec. 3.2 without the cancellation of ||X||^2 - ||G||^2).
+ *   out[0] = ||X - G x_1 A_1 ... x_d A_d||_F^2,  out[1] = ||X||_F^2  (device, FP64).
+ *   factors: A_n, I_n x ks[n] FP64; core: ks[0] x ... FP64.  The reconstruction is computed in X's
+ *   precision, expanding all modes but one and fusing the last expansion with the comparison, so
+ *   X_hat is never stored; the squared differences are summed in FP64.
+ */
+size_t rh_tucker_residual_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ks);
+rh_status rh_tucker_residual(int32_t order, const int64_t* dims, int32_t dtype, const void* X,
+                             const double* const* factors, const int32_t* ks, const double* core, double* out,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * rsthosvd_host -- the same R-STHOSVD with HOST buffers: enqueues the copy of X to the

@@ -12,7 +12,8 @@ import ctypes
 from . import _lib
 from ._lib import RH_F32, RH_F64, RhError, check, i32_array, i64_array, lib, make_options
 
-__all__ = ["omega", "rhosvd_sketch", "orthonormalize", "rsthosvd", "RhError", "version"]
+__all__ = ["omega", "rhosvd_sketch", "orthonormalize", "mode_product", "left_svd", "core_ttm", "tucker_residual",
+           "rsthosvd", "rhosvd", "RhError", "version"]
 
 
 def _torch():
@@ -96,6 +97,79 @@ def orthonormalize(Y):
     return Q, info
 
 
+def mode_product(X, dims, mode, A, out_dtype=None, transpose=True):
+    """Y = X x_mode A^T (A: tensor (k, I_mode) holding the column-major I_mode x k matrix), or with
+    ``transpose=False`` Y = X x_mode A (A: tensor (I_mode, k) holding the column-major k x I_mode matrix)."""
+    torch = _check_input(X, dims)
+    k = int(A.shape[0]) if transpose else int(A.shape[1])
+    dt = _dtype_code(X)
+    odt = dt if out_dtype is None else (_lib.RH_F64 if out_dtype == torch.float64 else _lib.RH_F32)
+    out_dims = list(dims)
+    out_dims[mode] = k
+    n = 1
+    for v in out_dims:
+        n *= int(v)
+    Y = torch.empty(n, dtype=torch.float64 if odt == _lib.RH_F64 else torch.float32, device=X.device)
+    check(lib().rh_mode_product(len(dims), i64_array(dims), dt, _ptr(X), int(mode), k, _ptr(A.contiguous()),
+                                int(bool(transpose)), odt, _ptr(Y), _stream(X.device)))
+    return Y, out_dims
+
+
+def left_svd(B, dims, mode):
+    """(U, sv) of the mode-``mode`` unfolding of B (I_mode <= 64); U as (I, I) holding column-major U."""
+    torch = _check_input(B, dims)
+    dt = _dtype_code(B)
+    I = int(dims[mode])
+    da = i64_array(dims)
+    ws_bytes = lib().rh_left_svd_workspace_size(len(dims), da, dt, int(mode))
+    if ws_bytes == 0:
+        raise ValueError("left_svd needs I_mode <= 64")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=B.device)
+    U = torch.empty((I, I), dtype=torch.float64, device=B.device)
+    sv = torch.empty(I, dtype=torch.float64, device=B.device)
+    check(lib().rh_left_svd(len(dims), da, dt, _ptr(B), int(mode), _ptr(U), _ptr(sv), _ptr(ws), ws_bytes,
+                            _stream(B.device)))
+    return U, sv
+
+
+def _fptrs(factors):
+    return (ctypes.c_void_p * len(factors))(*[f.data_ptr() for f in factors])
+
+
+def core_ttm(X, dims, factors):
+    """G = X x_1 A_1^T ... with factors given as (k_n, I_n) FP64 tensors (column-major I_n x k_n)."""
+    torch = _check_input(X, dims)
+    d = len(dims)
+    dt = _dtype_code(X)
+    ks = [int(f.shape[0]) for f in factors]
+    da, ka = i64_array(dims), i32_array(ks)
+    ws_bytes = lib().core_ttm_workspace_size(d, da, dt, ka)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=X.device)
+    n = 1
+    for k in ks:
+        n *= k
+    G = torch.empty(n, dtype=torch.float64, device=X.device)
+    fs = [f.contiguous() for f in factors]
+    check(lib().core_ttm(d, da, dt, _ptr(X), _fptrs(fs), ka, _ptr(G), _ptr(ws), ws_bytes, _stream(X.device)))
+    return G, ks
+
+
+def tucker_residual(X, dims, factors, core):
+    """Device tensor [||X - X_hat||^2, ||X||^2] for a Tucker tensor (FP64 core and factors)."""
+    torch = _check_input(X, dims)
+    d = len(dims)
+    dt = _dtype_code(X)
+    ks = [int(f.shape[0]) for f in factors]
+    da, ka = i64_array(dims), i32_array(ks)
+    ws_bytes = lib().rh_tucker_residual_workspace_size(d, da, dt, ka)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=X.device)
+    out = torch.empty(2, dtype=torch.float64, device=X.device)
+    fs = [f.contiguous() for f in factors]
+    check(lib().rh_tucker_residual(d, da, dt, _ptr(X), _fptrs(fs), ka, _ptr(core.contiguous()), _ptr(out), _ptr(ws),
+                                   ws_bytes, _stream(X.device)))
+    return out
+
+
 class Tucker:
     """Tucker factors (list of (k_n, I_n) FP64 tensors holding column-major I_n x k_n matrices),
     the FP64 core (flat, column-major, sizes ``core_dims``), the norms ||X||^2, ||G||^2 and the
@@ -115,6 +189,8 @@ class RsthosvdCall:
     Reusing the prepared buffers keeps allocation out of repeated calls (benchmarks).
     """
 
+    ALG = "rsthosvd"
+
     def __init__(self, dims, dtype, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True,
                  device="cuda"):
         torch = _torch()
@@ -124,13 +200,15 @@ class RsthosvdCall:
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
         self.da = i64_array(self.dims)
         self.ra = i32_array(ranks)
-        self.ws_bytes = lib().rsthosvd_workspace_size(d, self.da, self.dt, self.ra, ctypes.byref(self.opts))
+        self._fn = getattr(lib(), self.ALG)
+        self.ws_bytes = getattr(lib(), self.ALG + "_workspace_size")(d, self.da, self.dt, self.ra,
+                                                                      ctypes.byref(self.opts))
         if self.ws_bytes == 0:
             # re-run the validation through the call itself to get the message
-            check(lib().rsthosvd(d, self.da, self.dt, None, self.ra, ctypes.byref(self.opts), None, None, None,
-                                 None, None, 0, None))
-            raise ValueError("invalid R-STHOSVD request")
-        ko = self._out_ranks(ranks, p, clamp, truncate, rho)
+            check(self._fn(d, self.da, self.dt, None, self.ra, ctypes.byref(self.opts), None, None, None,
+                           None, None, 0, None))
+            raise ValueError("invalid request")
+        ko = self._out_ranks(ranks, p, clamp, truncate, None if self.ALG == "rhosvd" else rho)
         self.core_dims = ko
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
         self.factors = [torch.empty((ko[n], self.dims[n]), dtype=torch.float64, device=device) for n in range(d)]
@@ -145,6 +223,7 @@ class RsthosvdCall:
     def _out_ranks(self, ranks, p, clamp, truncate, rho):
         d = len(self.dims)
         cur = list(self.dims)
+        independent = self.ALG == "rhosvd"
         order = list(rho) if rho is not None else sorted(range(d), key=lambda n: (-cur[n], n))
         out = [0] * d
         for n in order:
@@ -157,15 +236,29 @@ class RsthosvdCall:
                 ell = min(ell, cur[n], M)
             k = min(int(ranks[n]), ell) if truncate else ell
             out[n] = k
-            cur[n] = k
+            if not independent:
+                cur[n] = k
         return out
 
     def run(self, X):
         _check_input(X, self.dims)
-        check(lib().rsthosvd(len(self.dims), self.da, self.dt, _ptr(X), self.ra, ctypes.byref(self.opts), self.fptrs,
-                             _ptr(self.core), _ptr(self.norms), _ptr(self.info), _ptr(self.ws), self.ws_bytes,
-                             _stream(X.device)))
+        check(self._fn(len(self.dims), self.da, self.dt, _ptr(X), self.ra, ctypes.byref(self.opts), self.fptrs,
+                       _ptr(self.core), _ptr(self.norms), _ptr(self.info), _ptr(self.ws), self.ws_bytes,
+                       _stream(X.device)))
         return Tucker(self.factors, self.core, self.core_dims, self.norms, self.info)
+
+
+class RhosvdCall(RsthosvdCall):
+    """A prepared R-HOSVD (Alg. 2) call."""
+
+    ALG = "rhosvd"
+
+
+def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True):
+    """R-HOSVD (Alg. 2) of the flat column-major tensor X with sizes ``dims``."""
+    call = RhosvdCall(dims, X.dtype, ranks, p=p, seed=seed, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
+                      device=X.device)
+    return call.run(X)
 
 
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True):

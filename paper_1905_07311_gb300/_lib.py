@@ -48,10 +48,19 @@ SIGNATURES = {
     "rhosvd_sketch_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _I32]),
     "rhosvd_sketch": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P, _SZ, _P]),
     "rhosvd_sketch_static": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P]),
+    "rh_mode_product": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P]),
+    "rh_left_svd_workspace_size": (_SZ, [_I32, _P, _I32, _I32]),
+    "rh_left_svd": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
     "rh_orthonormalize_workspace_size": (_SZ, [_I64, _I32]),
     "rh_orthonormalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _SZ, _P]),
     "rsthosvd_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
     "rsthosvd": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
+    "rhosvd_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
+    "rhosvd": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
+    "core_ttm_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
+    "core_ttm": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    "rh_tucker_residual_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
+    "rh_tucker_residual": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
     "rsthosvd_host": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _SZ, _P]),
 }

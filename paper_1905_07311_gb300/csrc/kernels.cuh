@@ -27,6 +27,23 @@ rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double
 // B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.
 template <typename T, typename TO>
 rh_status launch_ttm(const ModeView& v, const T* G, const T* Q, int ko, TO* B, cudaStream_t st);
+// general factor layout: Q(i, c) = Q[i qsi + c qsc]; any ko >= 1
+template <typename T, typename TO>
+rh_status launch_ttm_strided(const ModeView& v, const T* G, const T* Q, int64_t qsi, int64_t qsc, int ko, TO* B,
+                             cudaStream_t st);
+// *out = sum (Xref - G x_n Q^T)^2 with Xref laid out like the product; part holds
+// ttm_resid_parts(v, ko) doubles
+int64_t ttm_resid_parts(const ModeView& v, int ko);
+template <typename T>
+rh_status launch_ttm_residual(const ModeView& v, const T* G, const T* Q, int64_t qsi, int64_t qsc, int ko,
+                              const T* Xref, double* part, double* out, cudaStream_t st);
+
+// ---- core G = X x_1 A_1^T ... x_d A_d^T (tucker.cu) ----------------------------------------
+// returns the elements of each of the two ping-pong buffers; *fac_elems = sum I_n k_n
+size_t core_chain_elems(int d, const int64_t* dims, const int32_t* ks, size_t* fac_elems);
+template <typename T>
+rh_status launch_core_ttm(int d, const int64_t* dims, const T* X, const double* const* factors, const int32_t* ks,
+                          double* G, T* fac, T* W0, T* W1, cudaStream_t st);
 
 // ---- small dense linear algebra (smallla.cu) --------------------------------------------
 size_t orth_workspace_elems(int64_t m, int n);   // doubles

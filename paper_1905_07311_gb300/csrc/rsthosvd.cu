@@ -58,6 +58,7 @@ struct Plan {
   int32_t dtype;
   std::vector<Step> steps;
   size_t max_I_ell = 0, max_tensor = 0, max_orth = 0, max_trunc = 0, max_part = 0, max_pnorm = 0;
+  size_t fac_elems = 0;   // R-HOSVD: factor copies in the tensor's precision for the core chain
 };
 
 rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks, const rh_options& o,
@@ -120,6 +121,56 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
   return RH_OK;
 }
 
+// Alg. 2: every mode is sketched on the input tensor itself (no current core).
+rh_status make_plan_hosvd(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                          const rh_options& o, Plan& pl) {
+  rh_status s = check_tensor(order, dims, dtype);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
+  RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
+  RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");
+  pl.d = order;
+  pl.dtype = dtype;
+  for (int n = 0; n < order; ++n) {
+    Step st;
+    st.mode = n;
+    st.v = mode_view(order, dims, n);
+    const int64_t lim = std::min<int64_t>(st.v.I, st.v.M());
+    int64_t ell = (int64_t)ranks[n] + o.p;
+    if (ell > lim) {
+      if (!o.clamp) {
+        set_error("invalid argument: r_n + p = " + std::to_string(ell) + " exceeds min(I_n, prod of the other sizes) = " +
+                  std::to_string(lim) + " for mode " + std::to_string(n));
+        return RH_EINVAL;
+      }
+      ell = lim;
+    }
+    if (ell > RH_MAX_ELL) {
+      set_error("unsupported: r_n + p = " + std::to_string(ell) + " exceeds RH_MAX_ELL (64)");
+      return RH_EUNSUPPORTED;
+    }
+    st.ell = (int)ell;
+    st.ko = o.truncate ? std::min<int>(ranks[n], st.ell) : st.ell;
+    st.sk = plan_sketch(st.v, st.ell);
+    st.tr = plan_trunc(ModeView{st.v.L, st.ell, st.v.R}, st.ell);
+    pl.max_I_ell = std::max(pl.max_I_ell, (size_t)(st.v.I * st.ell));
+    pl.max_tensor = std::max(pl.max_tensor, (size_t)(st.v.M() * st.ell));
+    pl.max_part = std::max(pl.max_part, st.sk.part_elems());
+    pl.max_pnorm = std::max(pl.max_pnorm, st.sk.norm_elems());
+    pl.max_orth = std::max(pl.max_orth, orth_workspace_elems(st.v.I, st.ell));
+    pl.max_trunc = std::max(pl.max_trunc, dtype == RH_F64 ? trunc_workspace_elems<double>(st.tr)
+                                                           : trunc_workspace_elems<float>(st.tr));
+    pl.steps.push_back(st);
+  }
+  std::vector<int32_t> ks(order);
+  for (const Step& st : pl.steps) ks[st.mode] = st.ko;
+  size_t fe = 0;
+  pl.max_tensor = std::max(pl.max_tensor, core_chain_elems(order, dims, ks.data(), &fe));
+  pl.fac_elems = fe;
+  return RH_OK;
+}
+
 struct Bufs {
   void* part;
   double* part_norm;
@@ -133,6 +184,7 @@ struct Bufs {
   double* Ub;
   double* sv;
   void* Uc;
+  void* fac;
 };
 
 Bufs carve(Arena& ar, const Plan& pl) {
@@ -152,6 +204,7 @@ Bufs carve(Arena& ar, const Plan& pl) {
   b.Ub = ar.take<double>(RH_MAX_ELL * RH_MAX_ELL);
   b.sv = ar.take<double>(RH_MAX_ELL);
   b.Uc = takeT(RH_MAX_ELL * RH_MAX_ELL);
+  b.fac = pl.fac_elems ? takeT(pl.fac_elems) : nullptr;
   return b;
 }
 
@@ -235,6 +288,60 @@ rh_status run_rsthosvd(const Plan& pl, const T* X, const rh_options& o, double* 
   return RH_OK;
 }
 
+template <typename T>
+rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_options& o, double* const* factors,
+                     double* core, double* norms, int32_t* info, const Bufs& b, cudaStream_t st) {
+  rh_status s;
+  std::vector<int32_t> ks(pl.d);
+  for (size_t j = 0; j < pl.steps.size(); ++j) {
+    const Step& sp = pl.steps[j];
+    ks[sp.mode] = sp.ko;
+    const uint32_t sid = ((uint32_t)o.tensor_id << 4) | (uint32_t)sp.mode;
+    double* n2 = (j == 0) ? (norms ? norms : b.normx) : nullptr;
+    {
+      ProfileScope ps(PROF_SKETCH, (int)j, st);
+      if ((s = launch_sketch<T>(sp.sk, X, o.seed, sid, static_cast<T*>(b.part), b.part_norm, st)) != RH_OK) return s;
+    }
+    if ((s = launch_sketch_reduce<T>(sp.sk, static_cast<const T*>(b.part), b.part_norm, b.Y, n2, st)) != RH_OK)
+      return s;
+    {
+      ProfileScope ps(PROF_ORTH, (int)j, st);
+      if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st)) !=
+          RH_OK)
+        return s;
+    }
+    if (!o.truncate) {
+      RH_CUDA_TRY(cudaMemcpyAsync(factors[sp.mode], b.Q, sizeof(double) * sp.v.I * sp.ell, cudaMemcpyDeviceToDevice, st));
+      continue;
+    }
+    if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
+    T* B = static_cast<T*>(b.W[0]);
+    {
+      ProfileScope ps(PROF_TTM, (int)j, st);
+      if ((s = launch_ttm<T, T>(sp.v, X, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) return s;
+    }
+    {
+      ProfileScope ps(PROF_TRUNC, (int)j, st);
+      if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st)) != RH_OK) return s;
+    }
+    if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
+                                       st)) != RH_OK)
+      return s;
+  }
+  {
+    ProfileScope ps(PROF_TTM_CORE, 0, st);
+    if ((s = launch_core_ttm<T>(pl.d, dims, X, factors, ks.data(), core, static_cast<T*>(b.fac),
+                                static_cast<T*>(b.W[0]), static_cast<T*>(b.W[1]), st)) != RH_OK)
+      return s;
+  }
+  if (norms) {
+    int64_t ncore = 1;
+    for (int k = 0; k < pl.d; ++k) ncore *= ks[k];
+    if ((s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
+  }
+  return RH_OK;
+}
+
 rh_options opts_or_default(const rh_options* o) {
   rh_options d;
   rh_options_default(&d);
@@ -279,6 +386,60 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == RH_F64) return run_sketch<double>(pl, static_cast<const double*>(X), seed, sid, b, Y, norm2, st);
   return run_sketch<float>(pl, static_cast<const float*>(X), seed, sid, b, Y, norm2, st);
+}
+
+rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
+                          int32_t k, const void* A, int32_t transpose, int32_t out_dtype, void* Y, void* stream) {
+  clear_error();
+  rh_status s = check_tensor(order, dims, dtype);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(mode >= 0 && mode < order, "mode out of range");
+  RH_CHECK_ARG(k >= 1, "k must be >= 1");
+  RH_CHECK_ARG(transpose == 0 || transpose == 1, "transpose must be 0 or 1");
+  RH_CHECK_ARG(out_dtype == RH_F64 || out_dtype == dtype, "out_dtype must equal dtype or be RH_F64");
+  RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
+  const ModeView v = mode_view(order, dims, mode);
+  cudaStream_t st = (cudaStream_t)stream;
+  // transpose = 1: A is I_n x k, Y = X x_n A^T;  transpose = 0: A is k x I_n, Y = X x_n A
+  const int64_t qsi = transpose ? 1 : k, qsc = transpose ? v.I : 1;
+  if (dtype == RH_F64)
+    return launch_ttm_strided<double, double>(v, static_cast<const double*>(X), static_cast<const double*>(A), qsi, qsc,
+                                              k, static_cast<double*>(Y), st);
+  if (out_dtype == RH_F64)
+    return launch_ttm_strided<float, double>(v, static_cast<const float*>(X), static_cast<const float*>(A), qsi, qsc,
+                                             k, static_cast<double*>(Y), st);
+  return launch_ttm_strided<float, float>(v, static_cast<const float*>(X), static_cast<const float*>(A), qsi, qsc, k,
+                                          static_cast<float*>(Y), st);
+}
+
+size_t rh_left_svd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode) {
+  if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || dims[mode] > RH_MAX_ELL) return 0;
+  const ModeView v = mode_view(order, dims, mode);
+  const TruncPlan tp = plan_trunc(v, (int)v.I);
+  const size_t e = dtype == RH_F64 ? trunc_workspace_elems<double>(tp) * sizeof(double)
+                                   : trunc_workspace_elems<float>(tp) * sizeof(float);
+  return e + 256;
+}
+
+rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const void* B, int32_t mode, double* U,
+                      double* sv, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  rh_status s = check_tensor(order, dims, dtype);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(mode >= 0 && mode < order, "mode out of range");
+  RH_CHECK_ARG(dims[mode] <= RH_MAX_ELL, "I_mode must be <= 64");
+  RH_CHECK_ARG(B != nullptr && U != nullptr && sv != nullptr, "B, U and sv must be non-NULL");
+  const size_t need = rh_left_svd_workspace_size(order, dims, dtype, mode);
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    return RH_ENOMEM;
+  }
+  const ModeView v = mode_view(order, dims, mode);
+  const TruncPlan tp = plan_trunc(v, (int)v.I);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == RH_F64)
+    return launch_trunc_svd<double>(tp, static_cast<const double*>(B), static_cast<double*>(workspace), U, sv, st);
+  return launch_trunc_svd<float>(tp, static_cast<const float*>(B), static_cast<float*>(workspace), U, sv, st);
 }
 
 size_t rh_orthonormalize_workspace_size(int64_t m, int32_t n) {
@@ -331,6 +492,41 @@ rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void
   if (dtype == RH_F64)
     return run_rsthosvd<double>(pl, static_cast<const double*>(X), o, factors, core, norms, info, b, st);
   return run_rsthosvd<float>(pl, static_cast<const float*>(X), o, factors, core, norms, info, b, st);
+}
+
+size_t rhosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                             const rh_options* opts) {
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  if (make_plan_hosvd(order, dims, dtype, ranks, o, pl) != RH_OK) return 0;
+  Arena ar(nullptr);
+  carve(ar, pl);
+  return ar.used;
+}
+
+rh_status rhosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
+                 const rh_options* opts, double* const* factors, double* core, double* norms, int32_t* info,
+                 void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  rh_status s = make_plan_hosvd(order, dims, dtype, ranks, o, pl);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(X != nullptr && factors != nullptr && core != nullptr, "X, factors and core must be non-NULL");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(factors[k] != nullptr, "every factors[n] must be non-NULL");
+  Arena meas(nullptr);
+  carve(meas, pl);
+  if (workspace == nullptr || workspace_bytes < meas.used) {
+    set_error("workspace too small: need " + std::to_string(meas.used) + " bytes");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  const Bufs b = carve(ar, pl);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (info) RH_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * order, st));
+  if (dtype == RH_F64)
+    return run_rhosvd<double>(pl, dims, static_cast<const double*>(X), o, factors, core, norms, info, b, st);
+  return run_rhosvd<float>(pl, dims, static_cast<const float*>(X), o, factors, core, norms, info, b, st);
 }
 
 size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,

@@ -88,70 +88,79 @@ __global__ void gram_reduce_kernel(const double* __restrict__ Gpart, int nb, int
   C[e] = s;
 }
 
-// Cholesky C = R^T R (R upper) in one CTA; flag <- 1 on a pivot <= 1e-14 C_kk (or not finite).
-__global__ void cholesky_kernel(const double* __restrict__ C, int n, double* __restrict__ R,
-                                int32_t* __restrict__ flag) {
+// Cholesky C = R^T R (R upper) in one CTA of 256 threads; also writes rdiag = 1 / diag(R).
+// flag <- 1 on a pivot <= 1e-14 C_kk (or not finite): CholeskyQR2 is then not accurate enough
+// and the Householder branch takes over.  Trailing update: thread t owns column j = t % 64
+// and rows i = t / 64, t / 64 + 4, ... (no index division in the loop).
+__global__ void __launch_bounds__(256) cholesky_kernel(const double* __restrict__ C, int n, double* __restrict__ R,
+                                                       double* __restrict__ rdiag, int32_t* __restrict__ flag) {
   if (*flag) return;
   extern __shared__ double S[];  // n x n column-major working copy (upper part used)
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+  __shared__ double rk_inv;
+  const int t = threadIdx.x;
+  if (t == 0) bad = 0;
+  for (int e = t; e < n * n; e += blockDim.x) {
     const int j = e % n, k = e / n;
     S[e] = (j <= k) ? C[e] : 0.0;
   }
   __syncthreads();
+  const int jc = t & 63, i0 = t >> 6;
   for (int k = 0; k < n; ++k) {
-    const double d = S[k + n * k];
-    const double diag0 = C[k + n * k];
-    if (!(d > 1e-14 * diag0) || !isfinite(d)) {
-      if (threadIdx.x == 0) bad = 1;
-      break;  // uniform across the block (all threads read the same d)
+    if (t == 0) {
+      const double d = S[k + n * k];
+      if (!(d > 1e-14 * C[k + n * k]) || !isfinite(d)) {
+        bad = 1;
+      } else {
+        const double rkk = sqrt(d);
+        S[k + n * k] = rkk;
+        rk_inv = 1.0 / rkk;
+        rdiag[k] = rk_inv;
+      }
     }
-    const double rkk = sqrt(d);
     __syncthreads();
-    // row k of R: R[k, j] = S[k, j] / rkk, j > k
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) S[k + n * j] /= rkk;
+    if (bad) break;  // uniform: read after the barrier
+    // row k of R: R[k, j] = S[k, j] / R[k, k] for j > k
+    if (jc > k && jc < n && i0 == 0) S[k + n * jc] *= rk_inv;
     __syncthreads();
-    if (threadIdx.x == 0) S[k + n * k] = rkk;
-    // trailing update S[i, j] -= R[k, i] R[k, j], k < i <= j
-    const int m2 = n - k - 1;
-    for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) {
-      const int i = k + 1 + e % m2, j = k + 1 + e / m2;
-      if (i <= j) S[i + n * j] -= S[k + n * i] * S[k + n * j];
+    // trailing update S[i, j] -= R[k, i] R[k, j] for k < i <= j
+    if (jc > k && jc < n) {
+      const double rkj = S[k + n * jc];
+      for (int i = k + 1 + i0; i <= jc; i += 4) S[i + n * jc] -= S[k + n * i] * rkj;
     }
     __syncthreads();
   }
-  __syncthreads();
   if (bad) {
-    if (threadIdx.x == 0) *flag = 1;
+    if (t == 0) *flag = 1;
     return;
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+  for (int e = t; e < n * n; e += blockDim.x) {
     const int j = e % n, k = e / n;
     R[e] = (j <= k) ? S[e] : 0.0;
   }
 }
 
-// Out = A R^{-1} row by row (forward substitution on x^T R = a^T); one warp per row.
+// Out = A R^{-1} row by row (forward substitution on x^T R = a^T); one warp per row, the
+// diagonal applied through its precomputed reciprocals.
 __global__ void trsm_rows_kernel(const double* __restrict__ A, int64_t m, int n, const double* __restrict__ R,
-                                 double* __restrict__ Out, const int32_t* __restrict__ flag) {
+                                 const double* __restrict__ rdiag, double* __restrict__ Out,
+                                 const int32_t* __restrict__ flag) {
   if (*flag) return;
-  extern __shared__ double Rs[];  // n x n column-major
+  extern __shared__ double Rs[];  // n x n column-major, then n reciprocals
+  double* rd = Rs + n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[e] = R[e];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) rd[e] = rdiag[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
-    // lane holds columns lane and lane + 32
     double y0 = lane < n ? A[row + m * lane] : 0.0;
     double y1 = lane + 32 < n ? A[row + m * (lane + 32)] : 0.0;
     for (int c = 0; c < n; ++c) {
-      const double yc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31);
-      const double xc = yc / Rs[c + n * c];
+      const double xc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31) * rd[c];
       if (lane == (c & 31)) {
         if (c < 32) y0 = xc; else y1 = xc;
       }
-      // subtract xc R[c, j] from the not yet solved columns j > c
       if (lane > c && lane < n) y0 -= xc * Rs[c + n * lane];
       if (lane + 32 > c && lane + 32 < n) y1 -= xc * Rs[c + n * (lane + 32)];
     }
@@ -348,93 +357,120 @@ __global__ void __launch_bounds__(1024) tsqr_merge_kernel(const T* __restrict__ 
   }
 }
 
-// One-sided Jacobi on the columns of R (n x n): R V = U S.  Writes Ub = V with columns
-// sorted by decreasing singular value and sv (both FP64).  One warp per column pair,
-// round-robin ordering; at most 60 sweeps.
+// One-sided Jacobi on the columns of R (n x n, n <= 64): R V = U S.  Writes Ub = V with columns
+// sorted by decreasing singular value and sv (both FP64).
+// Schedule: np = n rounded up to even "players" (a zero dummy when n is odd); warp w owns the
+// players at circle positions w and np-1-w.  In every round each warp rotates its pair, then
+// the players at positions 1..np-1 move one place round the circle (position 0 stays), which
+// pairs every two players once per sweep of np-1 rounds.  Columns travel between warps through
+// two alternating shared-memory buffers, so a round needs a single barrier.
+// Each player carries its squared norm: a round computes only the inner product g = a^T b and
+// updates the norms of the rotated pair in closed form (a'^2 = a^2 - t g, b'^2 = b^2 + t g);
+// the norms are re-measured at the start of every sweep.  The rotation angle t is computed in
+// FP32 (c = 1/sqrt(1+t^2), s = c t are then formed in T, so c^2 + s^2 = 1 to T's rounding).  A
+// rotation is applied when |g| > tol |a| |b|, tol = 8 max(n, 8) eps: the computed inner product
+// carries a rounding error up to n eps |a| |b|, so a threshold at that level is never met.
 template <typename T>
-__global__ void jacobi_svd_kernel(const T* __restrict__ Rin, int n, double* __restrict__ Ub, double* __restrict__ sv) {
+__global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ Rin, int n, double* __restrict__ Ub,
+                                                          double* __restrict__ sv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int np = (n + 1) & ~1;  // even number of players, last one a dummy if n is odd
-  T* Mt = reinterpret_cast<T*>(smem_raw);   // np columns of length n
-  T* V = Mt + (int64_t)np * n;              // np columns of length n
-  __shared__ int rotated;
-  __shared__ T sig[RH_MAX_ELL + 1];
+  const int np = (n + 1) & ~1;
+  const int half = np / 2;
+  // buffer b (0/1): for each position q, the column (n values) and its V column (n values)
+  T* buf0 = reinterpret_cast<T*>(smem_raw);
+  T* buf1 = buf0 + (size_t)2 * np * n;
+  __shared__ T nrm2[2][RH_MAX_ELL];
+  __shared__ T sig[RH_MAX_ELL];
+  __shared__ int pid[2][RH_MAX_ELL];   // original column index held at each position
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    Mt[e] = (j < n) ? Rin[i + n * j] : T(0);
-    V[e] = (j < n && i == j) ? T(1) : T(0);
+    const int i = e % n, q = e / n;
+    buf0[(size_t)2 * n * q + i] = (q < n) ? Rin[i + n * q] : T(0);
+    buf0[(size_t)2 * n * q + n + i] = (q < n && i == q) ? T(1) : T(0);
   }
-  // rotation threshold max(n, 8) * eps: below the rounding level of the inner products
-  // the test could never be met and the sweeps would run to the cap
-  const T tol = T(max(n, 8)) * ((sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16));
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < np - 1; ++rnd) {
-      for (int pr = w; pr < np / 2; pr += nw) {
-        int a, b;
-        if (pr == 0) {
-          a = np - 1;
-          b = rnd;
-        } else {
-          a = (rnd + pr) % (np - 1);
-          b = (rnd - pr + (np - 1)) % (np - 1);
-        }
-        if (a >= n || b >= n) continue;
-        if (a > b) {
-          const int t = a;
-          a = b;
-          b = t;
-        }
-        T* xa = Mt + (int64_t)n * a;
-        T* xb = Mt + (int64_t)n * b;
-        T al = T(0), be = T(0), ga = T(0);
-        for (int i = lane; i < n; i += 32) {
-          al += xa[i] * xa[i];
-          be += xb[i] * xb[i];
-          ga += xa[i] * xb[i];
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const T zeta = (be - al) / (T(2) * ga);
-          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          const T c = T(1) / sqrt(T(1) + t * t);
-          const T s = c * t;
-          T* va = V + (int64_t)n * a;
-          T* vb = V + (int64_t)n * b;
-          for (int i = lane; i < n; i += 32) {
-            const T xai = xa[i], xbi = xb[i];
-            xa[i] = c * xai - s * xbi;
-            xb[i] = s * xai + c * xbi;
-            const T vai = va[i], vbi = vb[i];
-            va[i] = c * vai - s * vbi;
-            vb[i] = s * vai + c * vbi;
-          }
-          if (lane == 0) rotated = 1;
-        }
+  for (int q = threadIdx.x; q < np; q += blockDim.x) pid[0][q] = q;
+  __syncthreads();
+  const float tol = (float)(8 * (n > 8 ? n : 8)) * ((sizeof(T) == 4) ? 5.9604645e-8f : 1.1102230246e-16f);
+  int cur = 0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    // re-measure the squared norms of all players
+    {
+      const T* src = cur ? buf1 : buf0;
+      for (int q = w; q < np; q += nw) {
+        const T* x = src + (size_t)2 * n * q;
+        T a = T(0);
+        for (int i = lane; i < n; i += 32) a += x[i] * x[i];
+        a = warp_sum(a);
+        if (lane == 0) nrm2[cur][q] = a;
       }
       __syncthreads();
     }
-    if (!rotated) break;  // uniform: read after the barrier that ends the last round
-    __syncthreads();
+    int rotated = 0;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      T* src = cur ? buf1 : buf0;
+      T* dst = cur ? buf0 : buf1;
+      if (w < half) {
+        const int qa = w, qb = np - 1 - w;
+        const T* ca = src + (size_t)2 * n * qa;
+        const T* cb = src + (size_t)2 * n * qb;
+        T xa0 = lane < n ? ca[lane] : T(0), xa1 = lane + 32 < n ? ca[lane + 32] : T(0);
+        T xb0 = lane < n ? cb[lane] : T(0), xb1 = lane + 32 < n ? cb[lane + 32] : T(0);
+        T va0 = lane < n ? ca[n + lane] : T(0), va1 = lane + 32 < n ? ca[n + lane + 32] : T(0);
+        T vb0 = lane < n ? cb[n + lane] : T(0), vb1 = lane + 32 < n ? cb[n + lane + 32] : T(0);
+        T al = nrm2[cur][qa], be = nrm2[cur][qb];
+        T ga = warp_sum(xa0 * xb0 + xa1 * xb1);
+        const bool dummy = (pid[cur][qa] >= n) || (pid[cur][qb] >= n);
+        const float gf = (float)ga, af = (float)al, bf = (float)be;
+        if (!dummy && gf != 0.0f && fabsf(gf) > tol * sqrtf(af) * sqrtf(bf)) {
+          const float zeta = (bf - af) / (2.0f * gf);
+          const float tf = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+          const T t = (T)tf;
+          const T c = T(1) / sqrt(T(1) + t * t);
+          const T sn = c * t;
+          T u;
+          u = xa0; xa0 = c * u - sn * xb0; xb0 = sn * u + c * xb0;
+          u = xa1; xa1 = c * u - sn * xb1; xb1 = sn * u + c * xb1;
+          u = va0; va0 = c * u - sn * vb0; vb0 = sn * u + c * vb0;
+          u = va1; va1 = c * u - sn * vb1; vb1 = sn * u + c * vb1;
+          al = al - t * ga;
+          be = be + t * ga;
+          rotated = 1;
+        }
+        // positions after the move round the circle: 0 -> 0, np-1 -> 1, q -> q+1
+        const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
+        const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
+        T* da = dst + (size_t)2 * n * na;
+        T* db = dst + (size_t)2 * n * nb;
+        if (lane < n) { da[lane] = xa0; db[lane] = xb0; da[n + lane] = va0; db[n + lane] = vb0; }
+        if (lane + 32 < n) { da[lane + 32] = xa1; db[lane + 32] = xb1; da[n + lane + 32] = va1; db[n + lane + 32] = vb1; }
+        if (lane == 0) {
+          pid[cur ^ 1][na] = pid[cur][qa];
+          pid[cur ^ 1][nb] = pid[cur][qb];
+          nrm2[cur ^ 1][na] = al;
+          nrm2[cur ^ 1][nb] = be;
+        }
+      }
+      cur ^= 1;
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) break;
   }
-  // singular values and the sort
-  for (int j = w; j < n; j += nw) {
-    const T* x = Mt + (int64_t)n * j;
+  T* fin = cur ? buf1 : buf0;
+  for (int q = w; q < np; q += nw) {
+    const T* x = fin + (size_t)2 * n * q;
     T s = T(0);
     for (int i = lane; i < n; i += 32) s += x[i] * x[i];
     s = warp_sum(s);
-    if (lane == 0) sig[j] = sqrt(s);
+    if (lane == 0) sig[q] = (pid[cur][q] < n) ? sqrt(s) : T(-1);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    if (pid[cur][q] >= n) continue;
     int rank = 0;
-    for (int k = 0; k < n; ++k) rank += (sig[k] > sig[j]) || (sig[k] == sig[j] && k < j);
-    sv[rank] = (double)sig[j];
-    for (int i = 0; i < n; ++i) Ub[i + n * rank] = (double)V[i + n * j];
+    for (int k = 0; k < np; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && pid[cur][k] < pid[cur][q]);
+    sv[rank] = (double)sig[q];
+    const T* v = fin + (size_t)2 * n * q + n;
+    for (int i = 0; i < n; ++i) Ub[i + n * rank] = (double)v[i];
   }
 }
 
@@ -535,8 +571,8 @@ static int gram_rows(int64_t m) {
 size_t orth_workspace_elems(int64_t m, int n) {
   const int rb = gram_rows(m);
   const int64_t nb = ceil_div(m, rb);
-  // Gpart | C | R | Q1 | W (Householder copy) | beta | flag (as one double)
-  return (size_t)(nb * n * n + n * n + n * n + m * n + m * n + n + 2) + 64;
+  // Gpart | C | R | rdiag | Q1 | W (Householder copy) | beta | flag (as one double)
+  return (size_t)(nb * n * n + n * n + n * n + n + m * n + m * n + n + 2) + 64;
 }
 
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
@@ -546,7 +582,8 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
   double* Gpart = ws;
   double* C = Gpart + (size_t)nb * n * n;
   double* R = C + n * n;
-  double* Q1 = R + n * n;
+  double* rdiag = R + n * n;
+  double* Q1 = rdiag + n;
   double* W = Q1 + m * n;
   double* beta = W + m * n;
   int32_t* flag = reinterpret_cast<int32_t*>(beta + n);
@@ -554,6 +591,7 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
   RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
   const size_t gsm = sizeof(double) * rb * n;
   const size_t nsm = sizeof(double) * n * n;
+  const size_t tsm = sizeof(double) * (n * n + n);
   const int rblocks = (int)ceil_div((int64_t)n * n, 256);
   const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
   const double* src = Y;
@@ -563,9 +601,9 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
     RH_LAUNCH_CHECK();
     gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
     RH_LAUNCH_CHECK();
-    cholesky_kernel<<<1, 256, nsm, st>>>(C, n, R, flag);
+    cholesky_kernel<<<1, 256, nsm, st>>>(C, n, R, rdiag, flag);
     RH_LAUNCH_CHECK();
-    trsm_rows_kernel<<<tblocks, 256, nsm, st>>>(src, m, n, R, dst, flag);
+    trsm_rows_kernel<<<tblocks, 256, tsm, st>>>(src, m, n, R, rdiag, dst, flag);
     RH_LAUNCH_CHECK();
     src = Q1;
     dst = Q;
@@ -640,7 +678,7 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     nxt = t;
   }
   const int np = (n + 1) & ~1;
-  const size_t smj = sizeof(T) * 2 * (size_t)np * n;
+  const size_t smj = sizeof(T) * 4 * (size_t)np * n;
   RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
   {
     ProfileScope ps(PROF_JACOBI, 0, st);

@@ -154,12 +154,18 @@ def test_orthonormalize_rank_deficient(rh):
 # ---------------------------------------------------------------------------------
 # a2-a5: R-STHOSVD end to end
 # ---------------------------------------------------------------------------------
-def _compare(rh, X, ranks, p, seed, dtype, rho=None, tau=None, gate=None, err_tol=None, **kw):
+def _compare(rh, X, ranks, p, seed, dtype, rho=None, tau=None, gate=None, err_tol=None, alg="rsthosvd", **kw):
     Xd = dev(X, dtype)
-    T = rh.rsthosvd(Xd, list(X.shape), ranks, p=p, seed=seed, rho=rho, **kw)
+    if alg == "rsthosvd":
+        T = rh.rsthosvd(Xd, list(X.shape), ranks, p=p, seed=seed, rho=rho, **kw)
+    else:
+        T = rh.rhosvd(Xd, list(X.shape), ranks, p=p, seed=seed, **kw)
     torch.cuda.synchronize()
     Xe = X.astype(dtype).astype(np.float64)          # the exact input the GPU saw
-    out = otk.rsthosvd(Xe, ranks, p, seed, rho=rho, record=True, clamp=kw.get("clamp", False))
+    if alg == "rsthosvd":
+        out = otk.rsthosvd(Xe, ranks, p, seed, rho=rho, record=True, clamp=kw.get("clamp", False))
+    else:
+        out = otk.rhosvd(Xe, ranks, p, seed, record=True, clamp=kw.get("clamp", False))
     A = [mat(f) for f in T.factors]
     G = core_np(T)
     e_g = rel_error(Xe, G, A)
@@ -266,3 +272,67 @@ def test_rsthosvd_deterministic(rh):
     torch.cuda.synchronize()
     assert torch.equal(a.core, b.core)
     assert all(torch.equal(x, y) for x, y in zip(a.factors, b.factors))
+
+
+# ---------------------------------------------------------------------------------
+# a6: R-HOSVD (Alg. 2) and the core G = X x_n A_n^T
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_rhosvd_matches_oracle(rh, dtype):
+    X = lowrank_plus_noise_np([40, 35, 30], [6, 6, 6], 0.7, 1e-3, seed=13)
+    _compare(rh, X, [5, 6, 4], 5, 21, dtype, alg="rhosvd")
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_rhosvd_4way_many_tiles(rh, dtype):
+    X = lowrank_plus_noise_np([150, 40, 33, 9], [5, 5, 5, 4], 0.8, 1e-3, seed=14)
+    _compare(rh, X, [5, 5, 5, 3], 4, 3, dtype, alg="rhosvd")
+
+
+def test_rhosvd_hilbert_200(rh):
+    X = hilbert([200, 200, 200], offset=1)
+    T, e_g, e_o, _ = _compare(rh, X, [20, 20, 20], 5, 0, np.float64, alg="rhosvd")
+    assert e_g < 1e-12
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_core_ttm_matches_definition(rh, dtype):
+    from oracle.tensor import multi_ttm
+
+    rs = np.random.default_rng(15)
+    dims, ks = [70, 45, 33, 5], [7, 64, 3, 5]
+    X = rs.standard_normal(dims).astype(dtype)
+    A = [rs.standard_normal((dims[n], ks[n])) for n in range(4)]
+    G, kk = rh.core_ttm(dev(X, dtype), dims, [torch.from_numpy(a.T.copy()).cuda() for a in A])
+    Gg = np.reshape(G.cpu().numpy(), kk, order="F")
+    Ae = [a.astype(dtype).astype(np.float64) for a in A]      # factors in the tensor's precision
+    Gr = multi_ttm(X.astype(np.float64), Ae, transpose=True)
+    tol = 1e-12 if dtype == np.float64 else 2e-5
+    assert np.abs(Gg - Gr).max() <= tol * np.abs(Gr).max()
+
+
+# ---------------------------------------------------------------------------------
+# a7: direct residual
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_tucker_residual_matches_direct_error(rh, dtype):
+    X = lowrank_plus_noise_np([80, 70, 60], [8, 8, 8], 0.7, 1e-2, seed=16)
+    Xd = dev(X, dtype)
+    T = rh.rsthosvd(Xd, [80, 70, 60], [6, 7, 5], p=4, seed=2)
+    out = rh.tucker_residual(Xd, [80, 70, 60], T.factors, T.core).cpu().numpy()
+    Xe = X.astype(dtype).astype(np.float64)
+    e_ref = rel_error(Xe, core_np(T), [mat(f) for f in T.factors])
+    e_gpu = float(np.sqrt(out[0] / out[1]))
+    assert abs(out[1] - np.sum(Xe ** 2)) <= 1e-10 * np.sum(Xe ** 2)
+    # FP32: X_hat is formed in FP32 (relative rounding ~1e-7 per entry of the reconstruction)
+    assert abs(e_gpu - e_ref) <= (1e-12 if dtype == np.float64 else 2e-6)
+
+
+def test_tucker_residual_hilbert_tiny_error(rh):
+    X = hilbert([200, 200, 200], offset=1)
+    Xd = dev(X, np.float64)
+    T = rh.rsthosvd(Xd, [200, 200, 200], [20, 20, 20], p=5, seed=0, rho=[0, 1, 2])
+    out = rh.tucker_residual(Xd, [200, 200, 200], T.factors, T.core).cpu().numpy()
+    e_ref = rel_error(X, core_np(T), [mat(f) for f in T.factors])
+    assert e_ref < 1e-12
+    assert abs(float(np.sqrt(out[0] / out[1])) - e_ref) <= 1e-13
