@@ -62,7 +62,15 @@ enum {
   RH_EUNSUPPORTED = 6   /* valid request that this build does not implement               */
 };
 
-enum { RH_F64 = 0, RH_F32 = 1 };
+/* Element types of an input tensor.
+ *   RH_F64, RH_F32  plain arrays.
+ *   RH_BF16         one BF16 array (a tensor stored in BF16).
+ *   RH_BF16X2       an FP32 tensor held as two BF16 arrays, head h = bf16(x) and tail
+ *                   t = bf16(x - h) (16 significant bits, |x - h - t| <= 2^-16 |x|), stored one after
+ *                   the other in a single buffer of 2 N BF16 values (see rh_split_bf16x2).
+ * The BF16 forms use the tensor cores (tcgen05) for the first mode's sketch and mode product, with
+ * Omega rounded to BF16 (ties to even) and FP32 accumulation; later modes run in FP32. */
+enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3 };
 
 /* Options of the fixed-rank algorithms (Alg. 2, Alg. 3). */
 typedef struct rh_options {
@@ -115,7 +123,9 @@ rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0,
 /*
  * rhosvd_sketch -- range-finder sketch Y = X_(mode) Omega_mode (Alg. 1 step 1 applied to an
  * unfolding, as in Alg. 2 step 3 and Alg. 3 step 4).
- *   X       order-``order`` tensor with sizes dims[0..order-1], column-major, dtype RH_F64/RH_F32.
+ *   X       order-``order`` tensor with sizes dims[0..order-1], column-major, dtype RH_F64/RH_F32, or
+ *           RH_BF16/RH_BF16X2 for mode 0 (tensor cores; needs I_0 % 8 == 0, I_0 <= 1024; Omega in
+ *           BF16; norm2 is not computed for these and must be NULL).
  *   mode    0-based mode n;  ell  number of columns, 1 <= ell <= RH_MAX_ELL.
  *   Y       output, I_n x ell FP64, column-major (ld = I_n).
  *   norm2   optional (may be NULL): receives ||X||_F^2 (one FP64 value), accumulated
@@ -151,6 +161,12 @@ rh_status rhosvd_sketch_static(int32_t order, const int64_t* dims, int32_t dtype
                                double* norm2, void* stream);
 
 /*
+ * rh_split_bf16x2 -- write the RH_BF16X2 representation of an FP32 array: out[0..n) = bf16(x),
+ * out[n..2n) = bf16(x - bf16(x)) (ties to even).  n % 8 == 0 keeps the tail 16-byte aligned.
+ */
+rh_status rh_split_bf16x2(const float* X, int64_t n, uint16_t* out, void* stream);
+
+/*
  * rh_orthonormalize -- thin QR of a tall matrix, Y = Q R, returning Q (Alg. 1 step 2).
  *   Y  m x n FP64 column-major (read only), 1 <= n <= RH_MAX_ELL, n <= m.
  *   Q  m x n FP64 column-major output with orthonormal columns spanning range(Y).
@@ -175,6 +191,16 @@ rh_status rh_orthonormalize(int64_t m, int32_t n, const double* Y, double* Q, in
  */
 rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
                           int32_t k, const void* A, int32_t transpose, int32_t out_dtype, void* Y, void* stream);
+
+/*
+ * rh_mode_product_bf16 -- the first-mode product Y = X x_0 A^T on the tensor cores for a tensor in
+ * a BF16 form (RH_BF16 / RH_BF16X2): A is I_0 x k FP64 (1 <= k <= 64), split exactly into two BF16
+ * pieces; Y is k x (N / I_0) FP32 (layout c + k p), all four piece products with FP32
+ * accumulation.  Needs I_0 % 8 == 0.  Workspace: rh_mode_product_workspace_size.
+ */
+size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k);
+rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
+                               const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * rh_left_svd -- left singular vectors and singular values of the mode-n unfolding B_(n) of a tensor

@@ -36,8 +36,11 @@ def default_order(dims):
 def omega_matrix(seed, tensor_id, mode, nrows, ell, omega_round=None):
     """Omega_mode as an FP64 matrix (nrows x ell); FP32 normals promoted exactly.
 
-    ``omega_round='bf16'`` rounds each normal to BF16 first (the BF16 forms).
+    ``omega_round='bf16'`` rounds each normal to BF16 first (the BF16 forms); a dict maps
+    modes to their rounding (modes not in it use the FP32 normals).
     """
+    if isinstance(omega_round, dict):
+        omega_round = omega_round.get(mode)
     om = rng.omega(seed, tensor_id, mode, np.arange(nrows, dtype=np.int64), ell)
     if omega_round == "bf16":
         om = rng.round_bf16(om)

@@ -40,7 +40,7 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
-def _check_input(X, dims):
+def _check_input(X, dims, factor=1):
     torch = _torch()
     if not X.is_cuda:
         raise ValueError("X must be a CUDA tensor")
@@ -49,9 +49,12 @@ def _check_input(X, dims):
     n = 1
     for v in dims:
         n *= int(v)
-    if X.numel() != n:
-        raise ValueError(f"X has {X.numel()} elements but dims multiply to {n}")
+    if X.numel() != factor * n:
+        raise ValueError(f"X has {X.numel()} elements but dims multiply to {n} (x{factor})")
     return torch
+
+
+_FORMS = {"bf16": 2, "bf16x2": 3}
 
 
 def version():
@@ -80,6 +83,32 @@ def rhosvd_sketch(X, dims, mode, ell, seed=0, tensor_id=0, with_norm=False):
     check(lib().rhosvd_sketch(d, da, dt, _ptr(X), int(mode), int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF,
                               int(tensor_id), _ptr(Y), _ptr(nrm), _ptr(ws), ws_bytes, _stream(X.device)))
     return (Y, nrm) if with_norm else Y
+
+
+def split_bf16x2(X):
+    """RH_BF16X2 representation of a flat FP32 CUDA tensor: an int16 tensor of 2 N BF16 bit patterns."""
+    torch = _torch()
+    n = X.numel()
+    out = torch.empty(2 * n, dtype=torch.int16, device=X.device)
+    check(lib().rh_split_bf16x2(_ptr(X), n, _ptr(out), _stream(X.device)))
+    return out
+
+
+def rhosvd_sketch_bf16(Xb, dims, ell, seed=0, tensor_id=0, pieces=2):
+    """Tensor-core sketch of mode 0 for a BF16 (pieces=1, int16 bit patterns of N values) or
+    BF16X2 (pieces=2, 2 N values) tensor; returns the (ell, I_0) FP64 tensor of the I_0 x ell Y."""
+    torch = _torch()
+    d = len(dims)
+    da = i64_array(dims)
+    dt = _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
+    ws_bytes = lib().rhosvd_sketch_workspace_size(d, da, dt, 0, int(ell))
+    if ws_bytes == 0:
+        raise ValueError("unsupported BF16 sketch request")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=Xb.device)
+    Y = torch.empty((ell, int(dims[0])), dtype=torch.float64, device=Xb.device)
+    check(lib().rhosvd_sketch(d, da, dt, _ptr(Xb), 0, int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF, int(tensor_id),
+                              _ptr(Y), None, _ptr(ws), ws_bytes, _stream(Xb.device)))
+    return Y
 
 
 def orthonormalize(Y):
@@ -113,6 +142,26 @@ def mode_product(X, dims, mode, A, out_dtype=None, transpose=True):
     check(lib().rh_mode_product(len(dims), i64_array(dims), dt, _ptr(X), int(mode), k, _ptr(A.contiguous()),
                                 int(bool(transpose)), odt, _ptr(Y), _stream(X.device)))
     return Y, out_dims
+
+
+def mode_product_bf16(Xb, dims, A, pieces=2):
+    """First-mode product Y = X x_0 A^T on the tensor cores; Xb from split_bf16x2 (pieces=2) or BF16
+    bits (pieces=1); A a (k, I_0) FP64 tensor holding the column-major I_0 x k matrix.  Returns
+    (Y flat FP32 of k x N/I_0, layout c + k p)."""
+    torch = _torch()
+    d = len(dims)
+    da = i64_array(dims)
+    dt = _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
+    k = int(A.shape[0])
+    ws_bytes = lib().rh_mode_product_workspace_size(d, da, dt, 0, k)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=Xb.device)
+    n = 1
+    for v in dims[1:]:
+        n *= int(v)
+    Y = torch.empty(k * n, dtype=torch.float32, device=Xb.device)
+    check(lib().rh_mode_product_bf16(d, da, dt, _ptr(Xb), k, _ptr(A.contiguous()), _ptr(Y), _ptr(ws), ws_bytes,
+                                     _stream(Xb.device)))
+    return Y
 
 
 def left_svd(B, dims, mode):
@@ -196,7 +245,12 @@ class RsthosvdCall:
         torch = _torch()
         self.dims = [int(x) for x in dims]
         d = len(self.dims)
-        self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+        if isinstance(dtype, str):
+            self.dt = _FORMS[dtype]
+            self.factor = 2 if dtype == "bf16x2" else 1
+        else:
+            self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+            self.factor = 1
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
         self.da = i64_array(self.dims)
         self.ra = i32_array(ranks)
@@ -240,11 +294,11 @@ class RsthosvdCall:
                 cur[n] = k
         return out
 
-    def run(self, X):
-        _check_input(X, self.dims)
+    def run(self, X, norms=True):
+        _check_input(X, self.dims, self.factor)
         check(self._fn(len(self.dims), self.da, self.dt, _ptr(X), self.ra, ctypes.byref(self.opts), self.fptrs,
-                       _ptr(self.core), _ptr(self.norms), _ptr(self.info), _ptr(self.ws), self.ws_bytes,
-                       _stream(X.device)))
+                       _ptr(self.core), _ptr(self.norms) if norms else None, _ptr(self.info), _ptr(self.ws),
+                       self.ws_bytes, _stream(X.device)))
         return Tucker(self.factors, self.core, self.core_dims, self.norms, self.info)
 
 
@@ -261,9 +315,12 @@ def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True)
     return call.run(X)
 
 
-def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True):
-    """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``."""
-    call = RsthosvdCall(dims, X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
+def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None):
+    """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
+
+    ``form="bf16x2"`` (X from split_bf16x2) or ``form="bf16"`` (X holding BF16 bit patterns)
+    selects the tensor-core forms for the first mode."""
+    call = RsthosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
                         truncate=truncate, device=X.device)
     return call.run(X)
 

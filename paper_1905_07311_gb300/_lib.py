@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "librhosvd.so")
 
 RH_MAX_ORDER = 8
 RH_MAX_ELL = 64
-RH_F64, RH_F32 = 0, 1
+RH_F64, RH_F32, RH_BF16, RH_BF16X2 = 0, 1, 2, 3
 STATUS = {0: "RH_OK", 1: "RH_EINVAL", 2: "RH_ENOMEM", 3: "RH_ECUDA", 4: "RH_ENUMERIC", 5: "RH_ETIMEOUT",
           6: "RH_EUNSUPPORTED"}
 
@@ -49,8 +49,11 @@ SIGNATURES = {
     "rhosvd_sketch": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P, _SZ, _P]),
     "rhosvd_sketch_static": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P]),
     "rh_mode_product": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P]),
+    "rh_mode_product_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _I32]),
+    "rh_mode_product_bf16": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
     "rh_left_svd_workspace_size": (_SZ, [_I32, _P, _I32, _I32]),
     "rh_left_svd": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
+    "rh_split_bf16x2": (_I32, [_P, _I64, _P, _P]),
     "rh_orthonormalize_workspace_size": (_SZ, [_I64, _I32]),
     "rh_orthonormalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _SZ, _P]),
     "rsthosvd_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),

@@ -23,6 +23,23 @@ template <typename T>
 rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y,
                                double* norm2, cudaStream_t st);
 
+// ---- tensor-core sketch over BF16 pieces (sketch_tc.cu) --------------------------------
+bool sketch_tc_supported(const ModeView& v, int ell);
+int sketch_tc_ctas(const ModeView& v);
+rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
+                           uint32_t sid, float* part, int32_t* err, cudaStream_t st);
+rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
+// ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles
+rh_status launch_pieces_sumsq(const uint16_t* piece0, const uint16_t* piece1, int64_t n, double* part, double* out,
+                              cudaStream_t st);
+
+// ---- tensor-core mode product of the first mode (ttm_tc.cu) ---------------------------
+bool ttm_tc_supported(const ModeView& v, int ell);
+int ttm_tc_ctas(const ModeView& v);
+// qa: 128 x I BF16 scratch for the split Q; B: ell x M FP32 (layout c + ell p)
+rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
+                        uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
+
 // ---- mode-n product B = G x_n Q^T  (ttm.cu) ------------------------------------------
 // B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.
 template <typename T, typename TO>

@@ -13,6 +13,7 @@ namespace rh {
 namespace {
 
 bool dtype_ok(int32_t dtype) { return dtype == RH_F64 || dtype == RH_F32; }
+bool bf16_form(int32_t dtype) { return dtype == RH_BF16 || dtype == RH_BF16X2; }
 
 rh_status check_tensor(int32_t order, const int64_t* dims, int32_t dtype) {
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER, "order must be in [1, 8]");
@@ -59,11 +60,13 @@ struct Plan {
   std::vector<Step> steps;
   size_t max_I_ell = 0, max_tensor = 0, max_orth = 0, max_trunc = 0, max_part = 0, max_pnorm = 0;
   size_t fac_elems = 0;   // R-HOSVD: factor copies in the tensor's precision for the core chain
+  int32_t in_form = -1;   // RH_BF16 / RH_BF16X2 input (first mode on the tensor cores), else -1
+  size_t tc_part = 0, qa_elems = 0;
 };
 
 rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks, const rh_options& o,
                     Plan& pl) {
-  rh_status s = check_tensor(order, dims, dtype);
+  rh_status s = check_tensor(order, dims, bf16_form(dtype) ? RH_F32 : dtype);
   if (s != RH_OK) return s;
   RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
@@ -118,6 +121,19 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
     pl.steps.push_back(st);
   }
   (void)tsz;
+  if (bf16_form(dtype)) {
+    // the first processed mode runs on the tensor cores over the BF16 pieces
+    const Step& s0 = pl.steps[0];
+    if (s0.mode != 0 || !sketch_tc_supported(s0.v, s0.ell) || !ttm_tc_supported(s0.v, s0.ell)) {
+      set_error("unsupported: the BF16 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024, r + p <= 64");
+      return RH_EUNSUPPORTED;
+    }
+    pl.tc_part = (size_t)sketch_tc_ctas(s0.v) * s0.ell * s0.v.I;
+    pl.max_pnorm = std::max<size_t>(pl.max_pnorm, 1024);   // partials of the norm over the BF16 pieces
+    pl.qa_elems = (size_t)128 * s0.v.I;
+    pl.dtype = RH_F32;        // intermediates
+    pl.in_form = dtype;
+  }
   return RH_OK;
 }
 
@@ -185,6 +201,9 @@ struct Bufs {
   double* sv;
   void* Uc;
   void* fac;
+  float* tc_part;
+  uint16_t* qa;
+  int32_t* err;
 };
 
 Bufs carve(Arena& ar, const Plan& pl) {
@@ -205,30 +224,51 @@ Bufs carve(Arena& ar, const Plan& pl) {
   b.sv = ar.take<double>(RH_MAX_ELL);
   b.Uc = takeT(RH_MAX_ELL * RH_MAX_ELL);
   b.fac = pl.fac_elems ? takeT(pl.fac_elems) : nullptr;
+  b.tc_part = pl.tc_part ? ar.take<float>(pl.tc_part) : nullptr;
+  b.qa = pl.qa_elems ? ar.take<uint16_t>(pl.qa_elems) : nullptr;
+  b.err = ar.take<int32_t>(4);
   return b;
 }
 
 template <typename T>
-rh_status run_rsthosvd(const Plan& pl, const T* X, const rh_options& o, double* const* factors, double* core,
+rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, double* const* factors, double* core,
                        double* norms, int32_t* info, const Bufs& b, cudaStream_t st) {
+  const T* X = static_cast<const T*>(Xraw);
   const T* cur = X;
   int cur_buf = -1;  // -1: the input tensor
   rh_status s;
   const int nsteps = (int)pl.steps.size();
+  const bool tc0 = pl.in_form >= 0;
+  const uint16_t* piece0 = static_cast<const uint16_t*>(Xraw);
+  const uint16_t* piece1 = (pl.in_form == RH_BF16X2) ? piece0 + pl.steps[0].v.I * pl.steps[0].v.M() : nullptr;
+  if (tc0) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
   for (int j = 0; j < nsteps; ++j) {
     const Step& sp = pl.steps[j];
     const bool last = (j == nsteps - 1);
+    const bool tc = tc0 && j == 0;
     const uint32_t sid = ((uint32_t)o.tensor_id << 4) | (uint32_t)sp.mode;
     // Alg. 1 step 1: Y = G_(n) Omega_n   (+ ||X||^2 on the first pass)
     SketchBufs sb{b.part, b.part_norm};
     double* n2 = (j == 0) ? (norms ? norms : b.normx) : nullptr;
-    {
-      ProfileScope ps(PROF_SKETCH, j, st);
-      if ((s = launch_sketch<T>(sp.sk, cur, o.seed, sid, static_cast<T*>(sb.part), sb.part_norm, st)) != RH_OK)
+    if (tc) {
+      {
+        ProfileScope ps(PROF_SKETCH, j, st);
+        if ((s = launch_sketch_tc(sp.v, sp.ell, piece0, piece1, o.seed, sid, b.tc_part, b.err, st)) != RH_OK) return s;
+      }
+      SketchPlan rp = sp.sk;
+      rp.S = sketch_tc_ctas(sp.v);
+      if ((s = launch_sketch_reduce<float>(rp, b.tc_part, nullptr, b.Y, nullptr, st)) != RH_OK) return s;
+      if (norms && (s = launch_pieces_sumsq(piece0, piece1, sp.v.I * sp.v.M(), b.part_norm, norms, st)) != RH_OK)
+        return s;
+    } else {
+      {
+        ProfileScope ps(PROF_SKETCH, j, st);
+        if ((s = launch_sketch<T>(sp.sk, cur, o.seed, sid, static_cast<T*>(sb.part), sb.part_norm, st)) != RH_OK)
+          return s;
+      }
+      if ((s = launch_sketch_reduce<T>(sp.sk, static_cast<const T*>(sb.part), sb.part_norm, b.Y, n2, st)) != RH_OK)
         return s;
     }
-    if ((s = launch_sketch_reduce<T>(sp.sk, static_cast<const T*>(sb.part), sb.part_norm, b.Y, n2, st)) != RH_OK)
-      return s;
     // Alg. 1 step 2: Q = orth(Y)
     {
       ProfileScope ps(PROF_ORTH, j, st);
@@ -241,7 +281,15 @@ rh_status run_rsthosvd(const Plan& pl, const T* X, const rh_options& o, double* 
     const int wb = (cur_buf == 0) ? 1 : 0;
     T* B = static_cast<T*>(b.W[wb]);
     const bool direct_core = last && !o.truncate;
-    {
+    if (tc) {
+      ProfileScope ps(PROF_TTM, j, st);
+      if (direct_core) {
+        set_error("unsupported: single-mode untruncated BF16 request");
+        return RH_EUNSUPPORTED;
+      }
+      if ((s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st)) != RH_OK)
+        return s;
+    } else {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
         if ((s = launch_ttm<T, double>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, core, st)) != RH_OK) return s;
@@ -355,7 +403,23 @@ using namespace rh;
 
 extern "C" {
 
+static bool is_bf16_form(int32_t dtype) { return dtype == RH_BF16 || dtype == RH_BF16X2; }
+
+static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell) {
+  const ModeView v = mode_view(order, dims, 0);
+  Arena ar(nullptr);
+  ar.take<float>((size_t)sketch_tc_ctas(v) * ell * v.I);
+  ar.take<int32_t>(4);
+  return ar.used;
+}
+
 size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t ell) {
+  if (is_bf16_form(dtype)) {
+    if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode != 0 || ell < 1 || ell > RH_MAX_ELL) return 0;
+    for (int k = 0; k < order; ++k)
+      if (dims[k] < 1) return 0;
+    return sketch_tc_ws(order, dims, ell);
+  }
   if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || ell < 1 || ell > RH_MAX_ELL) return 0;
   const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
   Arena ar(nullptr);
@@ -367,6 +431,44 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
                         uint64_t seed, int32_t tensor_id, double* Y, double* norm2, void* workspace,
                         size_t workspace_bytes, void* stream) {
   clear_error();
+  if (is_bf16_form(dtype)) {
+    RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
+    for (int k = 0; k < order; ++k) RH_CHECK_ARG(dims[k] >= 1, "every dimension must be >= 1");
+    RH_CHECK_ARG(mode == 0, "the BF16 forms sketch mode 0 only");
+    RH_CHECK_ARG(ell >= 1 && ell <= RH_MAX_ELL, "ell must be in [1, 64]");
+    RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+    RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
+    RH_CHECK_ARG(norm2 == nullptr, "norm2 is not available for the BF16 forms");
+    const ModeView v = mode_view(order, dims, 0);
+    if (!sketch_tc_supported(v, ell)) {
+      set_error("unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024");
+      return RH_EUNSUPPORTED;
+    }
+    const size_t need = sketch_tc_ws(order, dims, ell);
+    if (workspace == nullptr || workspace_bytes < need) {
+      set_error("workspace too small: need " + std::to_string(need) + " bytes");
+      return RH_ENOMEM;
+    }
+    Arena ar(workspace);
+    const int S = sketch_tc_ctas(v);
+    float* part = ar.take<float>((size_t)S * ell * v.I);
+    int32_t* err = ar.take<int32_t>(4);
+    cudaStream_t st = (cudaStream_t)stream;
+    RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    const uint16_t* p0 = static_cast<const uint16_t*>(X);
+    const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
+    const uint32_t sid = ((uint32_t)tensor_id << 4);
+    rh_status s = launch_sketch_tc(v, ell, p0, p1, seed, sid, part, err, st);
+    if (s != RH_OK) return s;
+    SketchPlan rp;
+    rp.v = v;
+    rp.ell = ell;
+    rp.ellp = ell_pad_of(ell);
+    rp.gx = 0;
+    rp.S = S;
+    rp.chunk = 0;
+    return launch_sketch_reduce<float>(rp, part, nullptr, Y, nullptr, st);
+  }
   rh_status s = check_tensor(order, dims, dtype);
   if (s != RH_OK) return s;
   RH_CHECK_ARG(mode >= 0 && mode < order && mode < 16, "mode out of range");
@@ -388,9 +490,30 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
   return run_sketch<float>(pl, static_cast<const float*>(X), seed, sid, b, Y, norm2, st);
 }
 
+size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k) {
+  if (!bf16_form(dtype) || order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode != 0) return 0;
+  Arena ar(nullptr);
+  ar.take<uint16_t>((size_t)128 * dims[0]);
+  ar.take<int32_t>(4);
+  (void)k;
+  return ar.used;
+}
+
 rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
                           int32_t k, const void* A, int32_t transpose, int32_t out_dtype, void* Y, void* stream) {
   clear_error();
+  if (bf16_form(dtype)) {
+    RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
+    for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
+    RH_CHECK_ARG(mode == 0 && transpose == 1 && out_dtype == RH_F32, "BF16 forms: mode 0, transpose 1, FP32 output");
+    RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
+    const ModeView v = mode_view(order, dims, 0);
+    if (!ttm_tc_supported(v, k)) {
+      set_error("unsupported: the BF16 mode product needs I_0 % 8 == 0 and k <= 64");
+      return RH_EUNSUPPORTED;
+    }
+    RH_CHECK_ARG(false, "BF16 forms need scratch: use rh_mode_product_bf16");
+  }
   rh_status s = check_tensor(order, dims, dtype);
   if (s != RH_OK) return s;
   RH_CHECK_ARG(mode >= 0 && mode < order, "mode out of range");
@@ -410,6 +533,33 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
                                              k, static_cast<double*>(Y), st);
   return launch_ttm_strided<float, float>(v, static_cast<const float*>(X), static_cast<const float*>(A), qsi, qsc, k,
                                           static_cast<float*>(Y), st);
+}
+
+rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
+                               const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16 or RH_BF16X2");
+  RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
+  for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
+  RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
+  const ModeView v = mode_view(order, dims, 0);
+  if (!ttm_tc_supported(v, k)) {
+    set_error("unsupported: the BF16 mode product needs I_0 % 8 == 0 and 1 <= k <= 64");
+    return RH_EUNSUPPORTED;
+  }
+  const size_t need = rh_mode_product_workspace_size(order, dims, dtype, 0, k);
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  uint16_t* qa = ar.take<uint16_t>((size_t)128 * dims[0]);
+  int32_t* err = ar.take<int32_t>(4);
+  cudaStream_t st = (cudaStream_t)stream;
+  RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  const uint16_t* p0 = static_cast<const uint16_t*>(X);
+  const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
+  return launch_ttm_tc(v, k, p0, p1, A, qa, Y, err, st);
 }
 
 size_t rh_left_svd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode) {
@@ -440,6 +590,14 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
   if (dtype == RH_F64)
     return launch_trunc_svd<double>(tp, static_cast<const double*>(B), static_cast<double*>(workspace), U, sv, st);
   return launch_trunc_svd<float>(tp, static_cast<const float*>(B), static_cast<float*>(workspace), U, sv, st);
+}
+
+rh_status rh_split_bf16x2(const float* X, int64_t n, uint16_t* out, void* stream) {
+  clear_error();
+  RH_CHECK_ARG(n >= 0, "n must be >= 0");
+  RH_CHECK_ARG((X != nullptr && out != nullptr) || n == 0, "X and out must be non-NULL");
+  if (n == 0) return RH_OK;
+  return launch_split_bf16x2(X, n, out, out + n, (cudaStream_t)stream);
 }
 
 size_t rh_orthonormalize_workspace_size(int64_t m, int32_t n) {
@@ -489,9 +647,8 @@ rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void
   const Bufs b = carve(ar, pl);
   cudaStream_t st = (cudaStream_t)stream;
   if (info) RH_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * order, st));
-  if (dtype == RH_F64)
-    return run_rsthosvd<double>(pl, static_cast<const double*>(X), o, factors, core, norms, info, b, st);
-  return run_rsthosvd<float>(pl, static_cast<const float*>(X), o, factors, core, norms, info, b, st);
+  if (pl.dtype == RH_F64) return run_rsthosvd<double>(pl, X, o, factors, core, norms, info, b, st);
+  return run_rsthosvd<float>(pl, X, o, factors, core, norms, info, b, st);
 }
 
 size_t rhosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
@@ -537,7 +694,7 @@ size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t 
   Arena ar(nullptr);
   int64_t n = 1, ncore = 1;
   for (int k = 0; k < order; ++k) n *= dims[k];
-  const size_t esz = dtype == RH_F64 ? sizeof(double) : sizeof(float);
+  const size_t esz = dtype == RH_F64 ? sizeof(double) : (dtype == RH_BF16 ? 2 : sizeof(float));
   ar.take<char>((size_t)n * esz);
   std::vector<int64_t> kout(order, 0);
   for (const Step& sp : pl.steps) kout[sp.mode] = sp.ko;
@@ -570,7 +727,7 @@ rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const
   Arena ar(workspace);
   int64_t n = 1, ncore = 1;
   for (int k = 0; k < order; ++k) n *= dims[k];
-  const size_t esz = dtype == RH_F64 ? sizeof(double) : sizeof(float);
+  const size_t esz = dtype == RH_F64 ? sizeof(double) : (dtype == RH_BF16 ? 2 : sizeof(float));
   void* Xd = ar.take<char>((size_t)n * esz);
   std::vector<int64_t> kout(order, 0);
   for (const Step& sp : pl.steps) kout[sp.mode] = sp.ko;
@@ -584,10 +741,10 @@ rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const
   const Bufs b = carve(ar, pl);
   cudaStream_t st = (cudaStream_t)stream;
   RH_CUDA_TRY(cudaMemcpyAsync(Xd, X_host, (size_t)n * esz, cudaMemcpyHostToDevice, st));
-  if (dtype == RH_F64)
-    s = run_rsthosvd<double>(pl, static_cast<const double*>(Xd), o, fd.data(), cored, normsd, nullptr, b, st);
+  if (pl.dtype == RH_F64)
+    s = run_rsthosvd<double>(pl, Xd, o, fd.data(), cored, normsd, nullptr, b, st);
   else
-    s = run_rsthosvd<float>(pl, static_cast<const float*>(Xd), o, fd.data(), cored, normsd, nullptr, b, st);
+    s = run_rsthosvd<float>(pl, Xd, o, fd.data(), cored, normsd, nullptr, b, st);
   if (s != RH_OK) return s;
   for (int k = 0; k < order; ++k)
     RH_CUDA_TRY(cudaMemcpyAsync(factors_host[k], fd[k], sizeof(double) * dims[k] * kout[k], cudaMemcpyDeviceToHost, st));

@@ -1,0 +1,322 @@
+// Tensor-core (tcgen05) sketch Y = X_(1) Omega for the first mode of a tensor held as BF16
+// pieces (Alg. 1 step 1 on the unfolding whose rows are contiguous, i.e. the mode with L = 1).
+//
+// Input representation ("BF16 pieces"): X = X_1 + ... + X_np with each X_k a BF16 array of the
+// tensor's shape (np = 1: a BF16 tensor; np = 2: an FP32 tensor split exactly into a BF16 head
+// and a BF16 tail, 16 significant bits).  Omega is the library's Gaussian stream rounded to
+// BF16 (ties to even), so every product is exact and sums run in FP32 inside TMEM.
+//
+// Grid: persistent CTAs, each owning a contiguous range of 64-column chunks of X_(1) (split-K).
+// A CTA keeps the accumulators of all row tiles (I <= 128 * kMaxTiles rows x 64 columns, FP32)
+// in TMEM, so each Omega tile is generated once and used by every row tile.
+// Warp roles (192 threads): warp 0 issues TMA loads of the X pieces (128 x 64 tiles, MN-major
+// operand A, 128-byte swizzle); warp 1 owns TMEM and issues the MMAs (M = 128, N = 64, K = 16);
+// warps 2-5 generate the 64 x 64 Omega tile (K-major operand B, 128-byte swizzle) and, at the
+// end, read the accumulators back and write this CTA's partial sketch [I x ell] (FP32).
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "philox.cuh"
+#include "tc.cuh"
+
+namespace rh {
+namespace {
+
+constexpr int kRowsTile = 128;
+constexpr int kPChunk = 64;
+constexpr int kMaxTiles = 8;     // 8 x 64 FP32 columns = all 512 TMEM columns
+constexpr int kStages = 4;
+constexpr int kThreads = 192;
+constexpr uint32_t kHalfBox = 64 * 64 * 2;          // one TMA box: 64 rows x 64 columns, BF16
+constexpr uint32_t kPieceTile = 2 * kHalfBox;       // 128 x 64 BF16
+constexpr uint32_t kOmegaTile = 64 * 64 * 2;        // 64 x 64 BF16
+
+struct alignas(1024) SketchSmem {
+  uint8_t x[kStages][2][kPieceTile];   // [stage][piece][128 x 64]
+  uint8_t om[2][kOmegaTile];
+  uint64_t full[kStages], empty[kStages], om_full[2], om_empty[2], done;
+  uint32_t tmem_slot;
+};
+
+// byte offset of element (row, col) of a K-major 128B-swizzled tile whose rows hold 64 BF16
+__device__ __forceinline__ uint32_t sw128_off(int row, int col) {
+  const int chunk = (col >> 3) ^ (row & 7);
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (col & 7) * 2);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, int npieces,
+                     int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
+                     uint32_t sid, float* __restrict__ part, int32_t* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  SketchSmem& S = *reinterpret_cast<SketchSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nchunks = (M + kPChunk - 1) / kPChunk;
+  const int64_t c_begin = (int64_t)blockIdx.x * chunks_per_cta;
+  const int64_t c_end = c_begin + chunks_per_cta < nchunks ? c_begin + chunks_per_cta : nchunks;
+  const uint32_t tmem_cols = (uint32_t)(mtiles <= 1 ? 64 : (mtiles <= 2 ? 128 : (mtiles <= 4 ? 256 : 512)));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&S.full[s], 1);
+      tc::mbar_init(&S.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&S.om_full[b], 128);
+      tc::mbar_init(&S.om_empty[b], 1);
+    }
+    tc::mbar_init(&S.done, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&S.tmem_slot, tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = S.tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0 && c_begin < c_end) {
+      tc::prefetch_tmap(&map0);
+      if (npieces > 1) tc::prefetch_tmap(&map1);
+      uint32_t it = 0;
+      for (int64_t c = c_begin; c < c_end; ++c) {
+        const int32_t p0 = (int32_t)(c * kPChunk);
+        for (int m = 0; m < mtiles; ++m, ++it) {
+          const uint32_t s = it % kStages;
+          if (it >= kStages && !tc::mbar_wait(&S.empty[s], ((it / kStages) - 1) & 1, err, 1)) break;
+          tc::mbar_arrive_expect_tx(&S.full[s], kPieceTile * (uint32_t)npieces);
+          for (int pc = 0; pc < npieces; ++pc) {
+            const CUtensorMap* mp = pc == 0 ? &map0 : &map1;
+            tc::tma_load_2d(&S.x[s][pc][0], mp, m * kRowsTile, p0, &S.full[s]);
+            tc::tma_load_2d(&S.x[s][pc][kHalfBox], mp, m * kRowsTile + 64, p0, &S.full[s]);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0 && c_begin < c_end) {
+      constexpr uint32_t idesc = tc::idesc_bf16(128, 64, /*A MN-major*/ 1, /*B K-major*/ 0);
+      uint32_t it = 0, oc = 0;
+      bool first = true;
+      for (int64_t c = c_begin; c < c_end; ++c, ++oc) {
+        const uint32_t b = oc & 1;
+        if (!tc::mbar_wait(&S.om_full[b], (oc >> 1) & 1, err, 2)) break;
+        tc::tc_fence_after();
+        const uint32_t om_addr = tc::smem_u32(&S.om[b][0]);
+        for (int m = 0; m < mtiles; ++m, ++it) {
+          const uint32_t s = it % kStages;
+          if (!tc::mbar_wait(&S.full[s], (it / kStages) & 1, err, 3)) break;
+          tc::tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(m * 64);
+          for (int kk = 0; kk < kPChunk / 16; ++kk) {
+            const uint64_t bdesc = tc::sdesc_sw128(om_addr + kk * 32, 16, 1024);
+            for (int pc = 0; pc < npieces; ++pc) {
+              const uint64_t adesc = tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 2048, 8192, 1024);
+              tc::mma_bf16(d, adesc, bdesc, idesc, (first && kk == 0 && pc == 0) ? 0u : 1u);
+            }
+          }
+          tc::mma_commit(&S.empty[s]);
+        }
+        tc::mma_commit(&S.om_empty[b]);
+        first = false;
+      }
+      tc::mma_commit(&S.done);
+    }
+  } else {
+    // ---------------- Omega generators (warps 2..5) ----------------
+    const int t = threadIdx.x - 64;   // 0..127
+    uint32_t oc = 0;
+    for (int64_t c = c_begin; c < c_end; ++c, ++oc) {
+      const uint32_t b = oc & 1;
+      if (oc >= 2 && !tc::mbar_wait(&S.om_empty[b], ((oc >> 1) - 1) & 1, err, 4)) break;
+      uint8_t* om = &S.om[b][0];
+      const int p = t & 63;           // column of X_(1) within the chunk (K index)
+      const int64_t row = c * kPChunk + p;
+      for (int q = t >> 6; q < 16; q += 2) {
+        float4 v = rng::omega4(k0, k1, sid, row, (uint32_t)q);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n = 4 * q + j;    // column of Omega (N index); rows >= ell are unused but harmless
+          *reinterpret_cast<uint16_t*>(om + sw128_off(n, p)) = tc::bf16_rne(vv[j]);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&S.om_full[b]);
+    }
+    // ---------------- epilogue ----------------
+    if (c_begin < c_end && tc::mbar_wait(&S.done, 0, err, 5)) {
+      tc::tc_fence_after();
+      const int quad = warp & 3;      // TMEM lanes 32 quad .. 32 quad + 31
+      for (int m = 0; m < mtiles; ++m) {
+        const int64_t i = (int64_t)m * kRowsTile + quad * 32 + lane;
+        for (int cc = 0; cc < 4; ++cc) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(m * 64 + cc * 16), v);
+          if (i < I) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int col = cc * 16 + j;
+              if (col < ell) part[((int64_t)blockIdx.x * ell + col) * I + i] = v[j];
+            }
+          }
+        }
+      }
+    } else if (c_begin >= c_end) {
+      // no work: this CTA's partial is zero
+      for (int64_t e = t; e < (int64_t)ell * I; e += 128) part[(int64_t)blockIdx.x * ell * I + e] = 0.0f;
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+// X_1 = bf16(x), X_2 = bf16(x - X_1): an exact-to-16-bits split of an FP32 tensor.
+__global__ void split_bf16x2_kernel(const float* __restrict__ x, int64_t n, uint16_t* __restrict__ h,
+                                    uint16_t* __restrict__ l) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[e];
+    const uint16_t a = tc::bf16_rne(v);
+    h[e] = a;
+    l[e] = tc::bf16_rne(v - tc::bf16_to_f(a));
+  }
+}
+
+__global__ void pieces_sumsq_kernel(const uint16_t* __restrict__ a, const uint16_t* __restrict__ b, int64_t n,
+                                    double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)tc::bf16_to_f(a[e]);
+    if (b) v += (double)tc::bf16_to_f(b[e]);
+    s = fma(v, v, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_n_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < n; ++k) t += part[k];
+    *out = t;
+  }
+}
+
+// ---- tensor maps (driver entry point, no link-time dependency on libcuda) ----------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::mutex g_enc_mu;
+EncodeTiledFn g_enc = nullptr;
+
+rh_status get_encoder(EncodeTiledFn* fn) {
+  std::lock_guard<std::mutex> lk(g_enc_mu);
+  if (!g_enc) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+      set_error("cuTensorMapEncodeTiled is not available from the driver");
+      return RH_ECUDA;
+    }
+    g_enc = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *fn = g_enc;
+  return RH_OK;
+}
+
+}  // namespace
+
+// 2-D BF16 tensor map over a rows x cols column-major matrix (rows contiguous), box 64 x box_cols,
+// 128-byte swizzle, zero fill outside.
+rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_cols) {
+  EncodeTiledFn enc;
+  rh_status s = get_encoder(&enc);
+  if (s != RH_OK) return s;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)rows * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_cols};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return RH_ECUDA;
+  }
+  return RH_OK;
+}
+
+bool sketch_tc_supported(const ModeView& v, int ell) {
+  return v.L == 1 && v.I % 8 == 0 && v.I <= (int64_t)kRowsTile * kMaxTiles && ell >= 1 && ell <= 64 &&
+         v.M() < (int64_t(1) << 31);
+}
+
+int sketch_tc_ctas(const ModeView& v) {
+  const int64_t nchunks = ceil_div(v.M(), kPChunk);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nchunks));
+}
+
+size_t sketch_tc_smem() { return sizeof(SketchSmem) + 1024; }
+
+rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
+                           uint32_t sid, float* part, int32_t* err, cudaStream_t st) {
+  if (!sketch_tc_supported(v, ell)) {
+    set_error("tensor-core sketch: unsupported shape (needs the first mode, I % 8 == 0, I <= 1024, ell <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  CUtensorMap m0, m1;
+  rh_status s = make_bf16_map_2d(&m0, piece0, v.I, v.M(), 64);
+  if (s != RH_OK) return s;
+  const int np = piece1 ? 2 : 1;
+  if (piece1) {
+    if ((s = make_bf16_map_2d(&m1, piece1, v.I, v.M(), 64)) != RH_OK) return s;
+  } else {
+    m1 = m0;
+  }
+  const int ctas = sketch_tc_ctas(v);
+  const int64_t nchunks = ceil_div(v.M(), kPChunk);
+  const int64_t cpc = ceil_div(nchunks, ctas);
+  const int mtiles = (int)ceil_div(v.I, kRowsTile);
+  const size_t smem = sketch_tc_smem();
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<<<ctas, kThreads, smem, st>>>(m0, m1, np, v.I, v.M(), ell, mtiles, cpc,
+                                                 (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part, err);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_pieces_sumsq(const uint16_t* piece0, const uint16_t* piece1, int64_t n, double* part, double* out,
+                              cudaStream_t st) {
+  pieces_sumsq_kernel<<<1024, 256, 0, st>>>(piece0, piece1, n, part);
+  RH_LAUNCH_CHECK();
+  sum_n_kernel<<<1, 32, 0, st>>>(part, 1024, out);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * num_sms()));
+  split_bf16x2_kernel<<<blocks, 256, 0, st>>>(x, n, hi, lo);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+}  // namespace rh

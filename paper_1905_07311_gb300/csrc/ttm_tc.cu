@@ -1,0 +1,231 @@
+// Tensor-core (tcgen05) mode product for the first mode of a tensor held as BF16 pieces:
+// B = Q^T X_(1) (Alg. 1 step 3), with X_(1) of size I x M, rows contiguous, and Q of size
+// I x ell (ell <= 64) given in FP64.
+//
+// Q is split exactly into two BF16 pieces, Q = Q_h + Q_t (16 significant bits), stacked as the
+// 128 x I operand A = [Q_h^T; Q_t^T] (rows >= ell are zero).  For every BF16 piece X_k of X the
+// tensor cores accumulate D = A X_k (FP32, in TMEM), so rows c and 64 + c of D hold
+// Q_h^T X and Q_t^T X; the epilogue adds them.  All four products Q_a^T X_b are formed, each
+// exact, with FP32 accumulation.
+//
+// Persistent CTAs walk tiles of 128 columns of X_(1).  Per 64-row K-stage, TMA brings the
+// 128 x 64 slice of A and the 128 x 64 slices of the X pieces (K-major, 128-byte swizzle);
+// MMAs are M = 128, N = 128, K = 16.  The accumulator is double-buffered in TMEM so the
+// epilogue of one tile overlaps the MMAs of the next.  Warp roles (192 threads): warp 0 TMA,
+// warp 1 TMEM + MMA, warps 2-5 epilogue (warps 2, 3 read the tail rows and hand them to
+// warps 4, 5 through shared memory, which add the head rows and store B[c + ell p]).
+#include <string>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace rh {
+
+rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_cols);
+
+namespace {
+
+constexpr int kNTile = 128;   // columns of X_(1) per tile
+constexpr int kKStage = 64;   // rows of X_(1) per stage
+constexpr int kStages = 3;
+constexpr int kThreads = 192;
+constexpr uint32_t kATile = 128 * 64 * 2;      // A slice: 128 rows x 64 (BF16)
+constexpr uint32_t kXTile = kNTile * 64 * 2;   // X slice: 128 columns x 64 rows (BF16)
+
+struct alignas(1024) TtmSmem {
+  uint8_t a[kStages][kATile];
+  uint8_t x[kStages][2][kXTile];
+  float xchg[64][kNTile + 1];
+  uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
+  uint32_t tmem_slot;
+};
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
+                  const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
+                  float* __restrict__ B, int32_t* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  TtmSmem& S = *reinterpret_cast<TtmSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (M + kNTile - 1) / kNTile;
+  const int kstages = (int)((I + kKStage - 1) / kKStage);
+  const uint32_t tmem_cols = 256;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&S.full[s], 1);
+      tc::mbar_init(&S.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&S.tfull[b], 1);
+      tc::mbar_init(&S.tempty[b], 128);
+    }
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&S.tmem_slot, tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = S.tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::prefetch_tmap(&mapA);
+      tc::prefetch_tmap(&mapX0);
+      if (npieces > 1) tc::prefetch_tmap(&mapX1);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int32_t p0 = (int32_t)(t * kNTile);
+        for (int ks = 0; ks < kstages; ++ks, ++it) {
+          const uint32_t s = it % kStages;
+          if (it >= kStages && !tc::mbar_wait(&S.empty[s], ((it / kStages) - 1) & 1, err, 11)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&S.full[s], kATile + kXTile * (uint32_t)npieces);
+          tc::tma_load_2d(&S.a[s][0], &mapA, ks * kKStage, 0, &S.full[s]);
+          tc::tma_load_2d(&S.x[s][0][0], &mapX0, ks * kKStage, p0, &S.full[s]);
+          if (npieces > 1) tc::tma_load_2d(&S.x[s][1][0], &mapX1, ks * kKStage, p0, &S.full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16(128, kNTile, 0, 0);
+      uint32_t it = 0, tl = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const uint32_t b = tl & 1;
+        if (tl >= 2 && !tc::mbar_wait(&S.tempty[b], ((tl >> 1) - 1) & 1, err, 12)) break;
+        tc::tc_fence_after();
+        const uint32_t d = tmem + b * kNTile;
+        for (int ks = 0; ks < kstages; ++ks, ++it) {
+          const uint32_t s = it % kStages;
+          if (!tc::mbar_wait(&S.full[s], (it / kStages) & 1, err, 13)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a_addr = tc::smem_u32(&S.a[s][0]);
+          for (int kk = 0; kk < kKStage / 16; ++kk) {
+            const uint64_t adesc = tc::sdesc_sw128(a_addr + kk * 32, 16, 1024);
+            for (int pc = 0; pc < npieces; ++pc) {
+              const uint64_t bdesc = tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 32, 16, 1024);
+              tc::mma_bf16(d, adesc, bdesc, idesc, (ks == 0 && kk == 0 && pc == 0) ? 0u : 1u);
+            }
+          }
+          tc::mma_commit(&S.empty[s]);
+        }
+        tc::mma_commit(&S.tfull[b]);
+      }
+    }
+  } else {
+    // epilogue: warps 2..5 -> TMEM lane quadrants 2, 3, 0, 1
+    const int quad = warp & 3;
+    const bool tail = quad >= 2;        // rows 64..127: Q_t^T X
+    const int crow = (quad & 1) * 32 + lane;   // output row c (0..63)
+    uint32_t tl = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const uint32_t b = tl & 1;
+      if (!tc::mbar_wait(&S.tfull[b], (tl >> 1) & 1, err, 14)) break;
+      tc::tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + b * kNTile;
+      if (tail) {
+        for (int cc = 0; cc < kNTile / 16; ++cc) {
+          float v[16];
+          tc::tmem_ld16(base + cc * 16, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) S.xchg[crow][cc * 16 + j] = v[j];
+        }
+      }
+      named_sync(1, 128);
+      if (!tail) {
+        const int64_t p0 = t * kNTile;
+        for (int cc = 0; cc < kNTile / 16; ++cc) {
+          float v[16];
+          tc::tmem_ld16(base + cc * 16, v);
+          if (crow < ell) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int64_t p = p0 + cc * 16 + j;
+              if (p < M) B[crow + (int64_t)ell * p] = v[j] + S.xchg[crow][cc * 16 + j];
+            }
+          }
+        }
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&S.tempty[b]);
+      named_sync(1, 128);   // xchg is free again
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+// A = [bf16(Q)^T; bf16(Q - bf16(Q))^T] as a 128 x I row-major BF16 matrix; rows >= ell are zero.
+__global__ void q_pieces_kernel(const double* __restrict__ Q, int64_t I, int ell, uint16_t* __restrict__ A) {
+  const int64_t total = 128 * I;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % I;
+    const int r = (int)(e / I);
+    const int c = r & 63;
+    uint16_t out = 0;
+    if (c < ell) {
+      const float q = (float)Q[i + I * c];   // FP64 -> FP32 first (24 bits >= the 16 kept)
+      const uint16_t h = tc::bf16_rne(q);
+      out = (r < 64) ? h : tc::bf16_rne(q - tc::bf16_to_f(h));
+    }
+    A[e] = out;
+  }
+}
+
+}  // namespace
+
+bool ttm_tc_supported(const ModeView& v, int ell) {
+  return v.L == 1 && v.I % 8 == 0 && ell >= 1 && ell <= 64 && v.M() < (int64_t(1) << 31);
+}
+
+int ttm_tc_ctas(const ModeView& v) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(v.M(), kNTile)));
+}
+
+rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
+                        uint16_t* qa, float* B, int32_t* err, cudaStream_t st) {
+  if (!ttm_tc_supported(v, ell)) {
+    set_error("tensor-core mode product: unsupported shape (needs the first mode, I % 8 == 0, ell <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  {
+    const int64_t total = 128 * v.I;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
+    q_pieces_kernel<<<blocks, 256, 0, st>>>(Q, v.I, ell, qa);
+    RH_LAUNCH_CHECK();
+  }
+  CUtensorMap mA, m0, m1;
+  rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
+  if (s != RH_OK) return s;
+  if ((s = make_bf16_map_2d(&m0, piece0, v.I, v.M(), kNTile)) != RH_OK) return s;
+  const int np = piece1 ? 2 : 1;
+  if (piece1) {
+    if ((s = make_bf16_map_2d(&m1, piece1, v.I, v.M(), kNTile)) != RH_OK) return s;
+  } else {
+    m1 = m0;
+  }
+  const size_t smem = sizeof(TtmSmem) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<<<ttm_tc_ctas(v), kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+}  // namespace rh

@@ -1,0 +1,142 @@
+"""Tensor-core (tcgen05) paths through the C ABI against the oracle (needs a GB300).
+
+BF16 forms: X is held as BF16 pieces (one piece: a BF16 tensor; two pieces: head + tail of an
+FP32 tensor) and Omega is the library stream rounded to BF16 (ties to even), so every product is
+exact and only the FP32 accumulation rounds: |Y_gpu - Y| <= (K + 8) 2^-24 (|X_rep| |Omega_bf16|)
+with K the number of columns one CTA accumulates (at most ceil(M / 64 / CTAs) * 64), summed over
+CTAs in FP64.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import rng as orng  # noqa: E402
+from oracle.tensor import unfold  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_07311_gb300 import build
+
+    build.build()
+    import paper_1905_07311_gb300 as rh
+
+    return rh
+
+
+def bf16_bits_to_f64(b):
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_split_bf16x2_matches_definition(rh):
+    rs = np.random.default_rng(0)
+    x = (rs.standard_normal(4096) * np.exp(rs.uniform(-20, 20, 4096))).astype(np.float32)
+    out = rh.split_bf16x2(torch.from_numpy(x).cuda()).cpu().numpy().view(np.uint16)
+    h = orng.round_bf16(x)
+    t = orng.round_bf16((x - h).astype(np.float32))
+    assert np.array_equal(out[:4096], (h.view(np.uint32) >> 16).astype(np.uint16))
+    assert np.array_equal(out[4096:], (t.view(np.uint32) >> 16).astype(np.uint16))
+    rep = bf16_bits_to_f64(out[:4096]) + bf16_bits_to_f64(out[4096:])
+    assert np.all(np.abs(rep - x) <= 2.0 ** -16 * np.abs(x))
+
+
+@pytest.mark.parametrize("pieces", [1, 2])
+@pytest.mark.parametrize("shape", [(128, 300, 7), (200, 40, 40), (1024, 64, 33), (96, 1000), (8, 5000)])
+@pytest.mark.parametrize("ell", [1, 25, 64])
+def test_tc_sketch_matches_oracle(rh, pieces, shape, ell):
+    rs = np.random.default_rng(hash((shape, ell, pieces)) % 2 ** 32)
+    X = rs.standard_normal(shape).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    if pieces == 2:
+        Xb = rh.split_bf16x2(Xd)
+        bits = Xb.cpu().numpy().view(np.uint16)
+        n = X.size
+        rep = bf16_bits_to_f64(bits[:n]) + bf16_bits_to_f64(bits[n:])
+    else:
+        bits = (orng.round_bf16(X.ravel(order="F")).view(np.uint32) >> 16).astype(np.uint16)
+        Xb = torch.from_numpy(bits.view(np.int16).copy()).cuda()
+        rep = bf16_bits_to_f64(bits)
+    Xrep = np.reshape(rep, shape, order="F")
+    seed, tid = 77, 2
+    Y = rh.rhosvd_sketch_bf16(Xb, list(shape), ell, seed=seed, tensor_id=tid, pieces=pieces).cpu().numpy().T
+    Xm = unfold(Xrep, 0)
+    M = Xm.shape[1]
+    Om = orng.round_bf16(orng.omega(seed, tid, 0, np.arange(M), ell)).astype(np.float64)
+    Yr = Xm @ Om
+    bound = np.abs(Xm) @ np.abs(Om)
+    K = int(np.ceil(M / 64 / min(152, np.ceil(M / 64)))) * 64 + 64
+    assert np.all(np.abs(Y - Yr) <= (K + 8) * 2.0 ** -24 * bound + 1e-300), np.max(np.abs(Y - Yr) / (bound + 1e-30))
+
+
+@pytest.mark.parametrize("pieces", [1, 2])
+@pytest.mark.parametrize("shape,k", [((128, 300), 60), ((64, 129), 1), ((200, 7, 9), 25), ((1024, 300), 64)])
+def test_tc_mode_product_matches_definition(rh, pieces, shape, k):
+    """Y = A^T X_(1) with A split into two BF16 pieces: |Y - Y_rep| <= (I + 8) 2^-24 (|A_rep|^T |X_rep|)."""
+    rs = np.random.default_rng(5)
+    X = rs.standard_normal(shape).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    if pieces == 2:
+        Xb = rh.split_bf16x2(Xd)
+        bits = Xb.cpu().numpy().view(np.uint16)
+        rep = bf16_bits_to_f64(bits[:X.size]) + bf16_bits_to_f64(bits[X.size:])
+    else:
+        bits = (orng.round_bf16(X.ravel(order="F")).view(np.uint32) >> 16).astype(np.uint16)
+        Xb = torch.from_numpy(bits.view(np.int16).copy()).cuda()
+        rep = bf16_bits_to_f64(bits)
+    Xm = unfold(np.reshape(rep, shape, order="F"), 0)
+    A = rs.standard_normal((shape[0], k))
+    Af = A.astype(np.float32)
+    ah = orng.round_bf16(Af)
+    at = orng.round_bf16((Af - ah).astype(np.float32))
+    Arep = ah.astype(np.float64) + at.astype(np.float64)
+    Y = rh.mode_product_bf16(Xb, list(shape), torch.from_numpy(A.T.copy()).cuda(), pieces=pieces).cpu().numpy()
+    Yg = np.reshape(Y, (k, -1), order="F")
+    Yr = Arep.T @ Xm
+    bound = np.abs(Arep).T @ np.abs(Xm)
+    assert np.all(np.abs(Yg - Yr) <= (shape[0] + 8) * 2.0 ** -24 * bound + 1e-300), np.max(np.abs(Yg - Yr))
+
+
+# ---------------------------------------------------------------------------------
+# R-STHOSVD with the first mode on the tensor cores (BF16X2 form)
+# ---------------------------------------------------------------------------------
+# Gates: the GPU sees X_rep = head + tail exactly and rounds Omega_1 to BF16 (the oracle uses the
+# same values); the first mode product uses Q split into two BF16 pieces (|dQ| <= 2^-16 |Q|), a
+# perturbation of B of ~2^-16 relative.  It moves the leading-k factor subspace by ~2^-16 / tau
+# (tau = 0.05 -> 3e-4, gate 1e-3) and the relative Tucker error only at second order (the residual is
+# orthogonal to the perturbation of the projection), so the error gate stays 1e-5.
+@pytest.mark.parametrize("shape,ranks,p", [((128, 60, 50), (6, 5, 4), 5), ((256, 128, 96), (20, 20, 20), 10),
+                                           ((1024, 40, 30), (8, 6, 5), 4)])
+def test_rsthosvd_bf16x2_first_mode_matches_oracle(rh, shape, ranks, p):
+    from oracle import tucker as otk
+    from oracle.tensor import rel_error
+    from workloads import lowrank_plus_noise_np
+
+    X = lowrank_plus_noise_np(list(shape), [max(ranks) + 2] * 3, 0.8, 1e-3, seed=21).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    Xb = rh.split_bf16x2(Xd)
+    T = rh.rsthosvd(Xb, list(shape), list(ranks), p=p, seed=3, rho=[0, 1, 2], form="bf16x2")
+    torch.cuda.synchronize()
+    bits = Xb.cpu().numpy().view(np.uint16)
+    n = X.size
+    Xrep = np.reshape(bf16_bits_to_f64(bits[:n]) + bf16_bits_to_f64(bits[n:]), shape, order="F")
+    out = otk.rsthosvd(Xrep, list(ranks), p, 3, rho=[0, 1, 2], omega_round={0: "bf16"}, record=True)
+    A = [f.cpu().numpy().T for f in T.factors]
+    G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
+    e_g = rel_error(Xrep, G, A)
+    e_o = rel_error(Xrep, out["core"], out["factors"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    for rec in out["records"]:
+        m = rec["mode"]
+        sv = rec["sv_B"]
+        k = max(1, int(np.sum(sv >= 0.05 * sv[0])))
+        U = out["factors"][m][:, :k]
+        Qa, _ = np.linalg.qr(A[m])
+        assert np.linalg.norm(U - Qa @ (Qa.T @ U), 2) <= 1e-3, m
+    nx = float(T.norms.cpu().numpy()[0])
+    assert abs(nx - np.sum(Xrep ** 2)) <= 1e-10 * np.sum(Xrep ** 2)
