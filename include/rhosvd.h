@@ -68,9 +68,12 @@ enum {
  *   RH_BF16X2       an FP32 tensor held as two BF16 arrays, head h = bf16(x) and tail
  *                   t = bf16(x - h) (16 significant bits, |x - h - t| <= 2^-16 |x|), stored one after
  *                   the other in a single buffer of 2 N BF16 values (see rh_split_bf16x2).
+ *   RH_F32_BF16X2   a plain FP32 array, read as RH_BF16X2: the kernels of the first mode split
+ *                   each tile into head and tail in shared memory as they load it, so the results
+ *                   are bit-identical to RH_BF16X2 of rh_split_bf16x2(X) without the split pass.
  * The BF16 forms use the tensor cores (tcgen05) for the first mode's sketch and mode product, with
  * Omega rounded to BF16 (ties to even) and FP32 accumulation; later modes run in FP32. */
-enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3 };
+enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4 };
 
 /* Options of the fixed-rank algorithms (Alg. 2, Alg. 3). */
 typedef struct rh_options {
@@ -124,8 +127,10 @@ rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0,
  * rhosvd_sketch -- range-finder sketch Y = X_(mode) Omega_mode (Alg. 1 step 1 applied to an
  * unfolding, as in Alg. 2 step 3 and Alg. 3 step 4).
  *   X       order-``order`` tensor with sizes dims[0..order-1], column-major, dtype RH_F64/RH_F32, or
- *           RH_BF16/RH_BF16X2 for mode 0 (tensor cores; needs I_0 % 8 == 0, I_0 <= 1024; Omega in
- *           BF16; norm2 is not computed for these and must be NULL).
+ *           RH_BF16/RH_BF16X2/RH_F32_BF16X2 for mode 0 (tensor cores; needs I_0 % 8 == 0,
+ *           I_0 <= 1024; Omega in BF16).  norm2 is not computed for RH_BF16/RH_BF16X2 and must be
+ *           NULL; for RH_F32_BF16X2 it is ||head + tail||^2 (FP32 sums over 32 values per thread
+ *           and tile, FP64 above).
  *   mode    0-based mode n;  ell  number of columns, 1 <= ell <= RH_MAX_ELL.
  *   Y       output, I_n x ell FP64, column-major (ld = I_n).
  *   norm2   optional (may be NULL): receives ||X||_F^2 (one FP64 value), accumulated
@@ -194,7 +199,7 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
 
 /*
  * rh_mode_product_bf16 -- the first-mode product Y = X x_0 A^T on the tensor cores for a tensor in
- * a BF16 form (RH_BF16 / RH_BF16X2): A is I_0 x k FP64 (1 <= k <= 64), split exactly into two BF16
+ * a BF16 form (RH_BF16 / RH_BF16X2 / RH_F32_BF16X2): A is I_0 x k FP64 (1 <= k <= 64), split exactly into two BF16
  * pieces; Y is k x (N / I_0) FP32 (layout c + k p), all four piece products with FP32
  * accumulation.  Needs I_0 % 8 == 0.  Workspace: rh_mode_product_workspace_size.
  */
@@ -226,12 +231,16 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
  *   norms    optional device buffer of 2 FP64 values: ||X||_F^2 and ||G||_F^2.  For the
  *            orthonormal factors of Alg. 3, ||X - X_hat||^2 = ||X||^2 - ||G||^2 exactly
  *            (Thm. lem:st_mode_err); the difference is meaningful only above ~1e-6 relative.
- *   info     optional device int32 array of ``order`` values: 1 where mode n's QR took the
- *            Householder branch.
+ *   info     optional device int32 array of ``order`` values, bit flags per mode n:
+ *            1 = the QR of the sketch took the Householder branch; 2 = the truncation
+ *            SVD went through the Gram matrix (FP32 data only, see below).
  *   Size rule: ell_n <= min(I_n, prod of the other current sizes), else RH_EINVAL (or
  *   clamped, opts->clamp).  Steps per mode n (in order rho):
  *     sketch Y = G_(n) Omega_n; Q = orth(Y); B = Q^T G_(n) (mode-n product);
- *     B^T = Q_B R (tall-skinny Householder QR); one-sided Jacobi SVD of R gives U_B;
+ *     R with B B^T = R^T R: FP32 data first form W = B B^T (FP64 sums of FP32 partial
+ *     sums) and its Cholesky factor, kept when that succeeds and sigma_r^2 - sigma_{r+1}^2
+ *     >= 1e-5 sigma_1^2; otherwise (and for FP64 data) B^T = Q_B R by a tall-skinny
+ *     Householder QR; one-sided Jacobi SVD of R gives U_B;
  *     A_n = Q U_B(:, 1:r_n); G <- U_B(:, 1:r_n)^T B.
  */
 size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,

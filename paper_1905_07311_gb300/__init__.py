@@ -54,7 +54,15 @@ def _check_input(X, dims, factor=1):
     return torch
 
 
-_FORMS = {"bf16": 2, "bf16x2": 3}
+_FORMS = {"bf16": 2, "bf16x2": 3, "f32_bf16x2": 4}
+
+
+def _piece_form(pieces):
+    """dtype code of a tensor-core input: pieces=2 (split_bf16x2 output), 1 (BF16 bits) or "f32"
+    (a plain FP32 tensor split on the fly, RH_F32_BF16X2)."""
+    if pieces == "f32":
+        return _lib.RH_F32_BF16X2
+    return _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
 
 
 def version():
@@ -94,21 +102,23 @@ def split_bf16x2(X):
     return out
 
 
-def rhosvd_sketch_bf16(Xb, dims, ell, seed=0, tensor_id=0, pieces=2):
-    """Tensor-core sketch of mode 0 for a BF16 (pieces=1, int16 bit patterns of N values) or
-    BF16X2 (pieces=2, 2 N values) tensor; returns the (ell, I_0) FP64 tensor of the I_0 x ell Y."""
+def rhosvd_sketch_bf16(Xb, dims, ell, seed=0, tensor_id=0, pieces=2, with_norm=False):
+    """Tensor-core sketch of mode 0 for a BF16 (pieces=1, int16 bit patterns of N values),
+    BF16X2 (pieces=2, 2 N values) or FP32 (pieces="f32", split on the fly) tensor; returns the
+    (ell, I_0) FP64 tensor of the I_0 x ell Y (and ||X||^2 when with_norm, FP32 input only)."""
     torch = _torch()
     d = len(dims)
     da = i64_array(dims)
-    dt = _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
+    dt = _piece_form(pieces)
     ws_bytes = lib().rhosvd_sketch_workspace_size(d, da, dt, 0, int(ell))
     if ws_bytes == 0:
         raise ValueError("unsupported BF16 sketch request")
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=Xb.device)
     Y = torch.empty((ell, int(dims[0])), dtype=torch.float64, device=Xb.device)
+    nrm = torch.empty(1, dtype=torch.float64, device=Xb.device) if with_norm else None
     check(lib().rhosvd_sketch(d, da, dt, _ptr(Xb), 0, int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF, int(tensor_id),
-                              _ptr(Y), None, _ptr(ws), ws_bytes, _stream(Xb.device)))
-    return Y
+                              _ptr(Y), _ptr(nrm), _ptr(ws), ws_bytes, _stream(Xb.device)))
+    return (Y, nrm) if with_norm else Y
 
 
 def orthonormalize(Y):
@@ -145,13 +155,13 @@ def mode_product(X, dims, mode, A, out_dtype=None, transpose=True):
 
 
 def mode_product_bf16(Xb, dims, A, pieces=2):
-    """First-mode product Y = X x_0 A^T on the tensor cores; Xb from split_bf16x2 (pieces=2) or BF16
-    bits (pieces=1); A a (k, I_0) FP64 tensor holding the column-major I_0 x k matrix.  Returns
-    (Y flat FP32 of k x N/I_0, layout c + k p)."""
+    """First-mode product Y = X x_0 A^T on the tensor cores; Xb from split_bf16x2 (pieces=2), BF16
+    bits (pieces=1) or a plain FP32 tensor (pieces="f32"); A a (k, I_0) FP64 tensor holding the
+    column-major I_0 x k matrix.  Returns (Y flat FP32 of k x N/I_0, layout c + k p)."""
     torch = _torch()
     d = len(dims)
     da = i64_array(dims)
-    dt = _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
+    dt = _piece_form(pieces)
     k = int(A.shape[0])
     ws_bytes = lib().rh_mode_product_workspace_size(d, da, dt, 0, k)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=Xb.device)
@@ -318,8 +328,9 @@ def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True)
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None):
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 
-    ``form="bf16x2"`` (X from split_bf16x2) or ``form="bf16"`` (X holding BF16 bit patterns)
-    selects the tensor-core forms for the first mode."""
+    ``form="bf16x2"`` (X from split_bf16x2), ``form="bf16"`` (X holding BF16 bit patterns) or
+    ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly) selects the tensor-core forms for the
+    first mode."""
     call = RsthosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
                         truncate=truncate, device=X.device)
     return call.run(X)
@@ -341,7 +352,10 @@ class RsthosvdHostCall:
         ko = RsthosvdCall._out_ranks(dev_call, ranks, p, clamp, truncate, rho)
         self.dims = dev_call.dims
         d = len(self.dims)
-        self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+        if dtype == "f32_bf16x2":
+            self.dt = _lib.RH_F32_BF16X2
+        else:
+            self.dt = RH_F64 if dtype == torch.float64 else RH_F32
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
         self.da = i64_array(self.dims)
         self.ra = i32_array(ranks)

@@ -28,6 +28,11 @@ bool sketch_tc_supported(const ModeView& v, int ell);
 int sketch_tc_ctas(const ModeView& v);
 rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
                            uint32_t sid, float* part, int32_t* err, cudaStream_t st);
+// FP32 input split on the fly into the same two pieces; norm_part (sketch_tc_ctas doubles, may
+// be NULL) receives per-CTA sums of squares of the split values
+rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
+                               double* norm_part, int32_t* err, cudaStream_t st);
+rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st);
 rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 // ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles
 rh_status launch_pieces_sumsq(const uint16_t* piece0, const uint16_t* piece1, int64_t n, double* part, double* out,
@@ -39,6 +44,8 @@ int ttm_tc_ctas(const ModeView& v);
 // qa: 128 x I BF16 scratch for the split Q; B: ell x M FP32 (layout c + ell p)
 rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
                         uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
+rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
+                            int32_t* err, cudaStream_t st);
 
 // ---- mode-n product B = G x_n Q^T  (ttm.cu) ------------------------------------------
 // B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.
@@ -80,8 +87,13 @@ struct TruncPlan {
 TruncPlan plan_trunc(const ModeView& vb, int ell);
 template <typename T>
 size_t trunc_workspace_elems(const TruncPlan& pl);   // elements of T
+// FP32 data with a truncation rank r (1..ell) first try the Gram route: W = B B^T (FP64 sums of
+// FP32 tile sums), Cholesky W = R^T R, Jacobi on R.  It is kept when the Cholesky succeeds and
+// sigma_r^2 - sigma_{r+1}^2 >= 1e-5 sigma_1^2 (then *info |= 2, if info is given); otherwise
+// device-side flags run the tall-skinny QR route.  r = 0 (and FP64) take the QR route only.
 template <typename T>
-rh_status launch_trunc_svd(const TruncPlan& pl, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st);
+rh_status launch_trunc_svd(const TruncPlan& pl, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st, int r,
+                           int32_t* info);
 
 // A = Q * Ub(:, 0:r)  (I x r, FP64);  Uc = (T) Ub(:, 0:r) (ell x r)
 template <typename T>

@@ -13,7 +13,8 @@ namespace rh {
 namespace {
 
 bool dtype_ok(int32_t dtype) { return dtype == RH_F64 || dtype == RH_F32; }
-bool bf16_form(int32_t dtype) { return dtype == RH_BF16 || dtype == RH_BF16X2; }
+// forms whose first mode runs on the tensor cores over BF16 pieces
+bool bf16_form(int32_t dtype) { return dtype == RH_BF16 || dtype == RH_BF16X2 || dtype == RH_F32_BF16X2; }
 
 rh_status check_tensor(int32_t order, const int64_t* dims, int32_t dtype) {
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER, "order must be in [1, 8]");
@@ -60,7 +61,7 @@ struct Plan {
   std::vector<Step> steps;
   size_t max_I_ell = 0, max_tensor = 0, max_orth = 0, max_trunc = 0, max_part = 0, max_pnorm = 0;
   size_t fac_elems = 0;   // R-HOSVD: factor copies in the tensor's precision for the core chain
-  int32_t in_form = -1;   // RH_BF16 / RH_BF16X2 input (first mode on the tensor cores), else -1
+  int32_t in_form = -1;   // RH_BF16 / RH_BF16X2 / RH_F32_BF16X2 input (first mode on the tensor cores), else -1
   size_t tc_part = 0, qa_elems = 0;
 };
 
@@ -239,7 +240,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
   rh_status s;
   const int nsteps = (int)pl.steps.size();
   const bool tc0 = pl.in_form >= 0;
-  const uint16_t* piece0 = static_cast<const uint16_t*>(Xraw);
+  const bool f32in = pl.in_form == RH_F32_BF16X2;   // FP32 input split on the fly
+  const uint16_t* piece0 = f32in ? nullptr : static_cast<const uint16_t*>(Xraw);
   const uint16_t* piece1 = (pl.in_form == RH_BF16X2) ? piece0 + pl.steps[0].v.I * pl.steps[0].v.M() : nullptr;
   if (tc0) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
   for (int j = 0; j < nsteps; ++j) {
@@ -253,13 +255,21 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     if (tc) {
       {
         ProfileScope ps(PROF_SKETCH, j, st);
-        if ((s = launch_sketch_tc(sp.v, sp.ell, piece0, piece1, o.seed, sid, b.tc_part, b.err, st)) != RH_OK) return s;
+        if (f32in)
+          s = launch_sketch_tc_f32(sp.v, sp.ell, static_cast<const float*>(Xraw), o.seed, sid, b.tc_part,
+                                   norms ? b.part_norm : nullptr, b.err, st);
+        else
+          s = launch_sketch_tc(sp.v, sp.ell, piece0, piece1, o.seed, sid, b.tc_part, b.err, st);
+        if (s != RH_OK) return s;
       }
       SketchPlan rp = sp.sk;
       rp.S = sketch_tc_ctas(sp.v);
       if ((s = launch_sketch_reduce<float>(rp, b.tc_part, nullptr, b.Y, nullptr, st)) != RH_OK) return s;
-      if (norms && (s = launch_pieces_sumsq(piece0, piece1, sp.v.I * sp.v.M(), b.part_norm, norms, st)) != RH_OK)
-        return s;
+      if (norms) {
+        s = f32in ? launch_sum_n(b.part_norm, rp.S, norms, st)
+                  : launch_pieces_sumsq(piece0, piece1, sp.v.I * sp.v.M(), b.part_norm, norms, st);
+        if (s != RH_OK) return s;
+      }
     } else {
       {
         ProfileScope ps(PROF_SKETCH, j, st);
@@ -287,8 +297,12 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         set_error("unsupported: single-mode untruncated BF16 request");
         return RH_EUNSUPPORTED;
       }
-      if ((s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st)) != RH_OK)
-        return s;
+      if (f32in)
+        s = launch_ttm_tc_f32(sp.v, sp.ell, static_cast<const float*>(Xraw), b.Q, b.qa, reinterpret_cast<float*>(B),
+                              b.err, st);
+      else
+        s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
+      if (s != RH_OK) return s;
     } else {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
@@ -301,7 +315,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       // Alg. 1 steps 4-6: SVD of B, A_n = Q U_B(:, 1:r), G_(n) <- S V^T = U_B(:, 1:r)^T B
       {
         ProfileScope ps(PROF_TRUNC, j, st);
-        if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st)) != RH_OK) return s;
+        if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, sp.ko,
+                                      info ? info + sp.mode : nullptr)) != RH_OK) return s;
       }
       if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
                                          st)) != RH_OK)
@@ -370,7 +385,8 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
     }
     {
       ProfileScope ps(PROF_TRUNC, (int)j, st);
-      if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st)) != RH_OK) return s;
+      if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, sp.ko,
+                                      info ? info + sp.mode : nullptr)) != RH_OK) return s;
     }
     if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
                                        st)) != RH_OK)
@@ -403,13 +419,14 @@ using namespace rh;
 
 extern "C" {
 
-static bool is_bf16_form(int32_t dtype) { return dtype == RH_BF16 || dtype == RH_BF16X2; }
+static bool is_bf16_form(int32_t dtype) { return bf16_form(dtype); }
 
 static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell) {
   const ModeView v = mode_view(order, dims, 0);
   Arena ar(nullptr);
   ar.take<float>((size_t)sketch_tc_ctas(v) * ell * v.I);
   ar.take<int32_t>(4);
+  ar.take<double>((size_t)sketch_tc_ctas(v));
   return ar.used;
 }
 
@@ -438,7 +455,7 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     RH_CHECK_ARG(ell >= 1 && ell <= RH_MAX_ELL, "ell must be in [1, 64]");
     RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
     RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
-    RH_CHECK_ARG(norm2 == nullptr, "norm2 is not available for the BF16 forms");
+    RH_CHECK_ARG(norm2 == nullptr || dtype == RH_F32_BF16X2, "norm2 is not available for RH_BF16 / RH_BF16X2");
     const ModeView v = mode_view(order, dims, 0);
     if (!sketch_tc_supported(v, ell)) {
       set_error("unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024");
@@ -453,12 +470,20 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     const int S = sketch_tc_ctas(v);
     float* part = ar.take<float>((size_t)S * ell * v.I);
     int32_t* err = ar.take<int32_t>(4);
+    double* norm_part = ar.take<double>((size_t)S);
     cudaStream_t st = (cudaStream_t)stream;
     RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
-    const uint16_t* p0 = static_cast<const uint16_t*>(X);
-    const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
     const uint32_t sid = ((uint32_t)tensor_id << 4);
-    rh_status s = launch_sketch_tc(v, ell, p0, p1, seed, sid, part, err, st);
+    rh_status s;
+    if (dtype == RH_F32_BF16X2) {
+      s = launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part, norm2 ? norm_part : nullptr, err,
+                               st);
+      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st);
+    } else {
+      const uint16_t* p0 = static_cast<const uint16_t*>(X);
+      const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
+      s = launch_sketch_tc(v, ell, p0, p1, seed, sid, part, err, st);
+    }
     if (s != RH_OK) return s;
     SketchPlan rp;
     rp.v = v;
@@ -538,7 +563,7 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
 rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
                                const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
-  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16 or RH_BF16X2");
+  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16, RH_BF16X2 or RH_F32_BF16X2");
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
   for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
   RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
@@ -557,6 +582,7 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
   int32_t* err = ar.take<int32_t>(4);
   cudaStream_t st = (cudaStream_t)stream;
   RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  if (dtype == RH_F32_BF16X2) return launch_ttm_tc_f32(v, k, static_cast<const float*>(X), A, qa, Y, err, st);
   const uint16_t* p0 = static_cast<const uint16_t*>(X);
   const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
   return launch_ttm_tc(v, k, p0, p1, A, qa, Y, err, st);
@@ -588,8 +614,8 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
   const TruncPlan tp = plan_trunc(v, (int)v.I);
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == RH_F64)
-    return launch_trunc_svd<double>(tp, static_cast<const double*>(B), static_cast<double*>(workspace), U, sv, st);
-  return launch_trunc_svd<float>(tp, static_cast<const float*>(B), static_cast<float*>(workspace), U, sv, st);
+    return launch_trunc_svd<double>(tp, static_cast<const double*>(B), static_cast<double*>(workspace), U, sv, st, 0, nullptr);
+  return launch_trunc_svd<float>(tp, static_cast<const float*>(B), static_cast<float*>(workspace), U, sv, st, 0, nullptr);
 }
 
 rh_status rh_split_bf16x2(const float* X, int64_t n, uint16_t* out, void* stream) {

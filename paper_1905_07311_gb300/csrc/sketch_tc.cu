@@ -13,6 +13,11 @@
 // operand A, 128-byte swizzle); warp 1 owns TMEM and issues the MMAs (M = 128, N = 64, K = 16);
 // warps 2-5 generate the 64 x 64 Omega tile (K-major operand B, 128-byte swizzle) and, at the
 // end, read the accumulators back and write this CTA's partial sketch [I x ell] (FP32).
+//
+// FP32 input (448 threads): TMA brings FP32 tiles (four 32 x 64 boxes per 128 x 64 tile) and
+// warps 6-13 split them in shared memory into the same head / tail pieces that the separate
+// split produces, so the products, and the sketch, are bit-identical to the two-piece form;
+// they also accumulate ||head + tail||^2 for the norm of the input.
 #include <mutex>
 #include <string>
 
@@ -27,17 +32,31 @@ namespace {
 constexpr int kRowsTile = 128;
 constexpr int kPChunk = 64;
 constexpr int kMaxTiles = 8;     // 8 x 64 FP32 columns = all 512 TMEM columns
-constexpr int kStages = 4;
-constexpr int kThreads = 192;
 constexpr uint32_t kHalfBox = 64 * 64 * 2;          // one TMA box: 64 rows x 64 columns, BF16
 constexpr uint32_t kPieceTile = 2 * kHalfBox;       // 128 x 64 BF16
 constexpr uint32_t kOmegaTile = 64 * 64 * 2;        // 64 x 64 BF16
+constexpr uint32_t kF32Box = 32 * 64 * 4;           // FP32 TMA box: 32 rows x 64 columns
+constexpr uint32_t kF32Tile = 4 * kF32Box;          // 128 x 64 FP32
 
+// BF16 pieces in: 4 stages filled by TMA.  FP32 in: 3 stages of FP32 tiles filled by TMA,
+// split by four converter warps into 2 stages of BF16 pieces.
+template <bool F32IN>
+struct SketchCfg {
+  static constexpr int kPStages = F32IN ? 2 : 4;
+  static constexpr int kF32Stages = F32IN ? 3 : 1;
+  static constexpr int kThreads = F32IN ? 448 : 192;
+  static constexpr int kConv = 256;   // converter threads (warps 6..13)
+};
+
+template <bool F32IN>
 struct alignas(1024) SketchSmem {
-  uint8_t x[kStages][2][kPieceTile];   // [stage][piece][128 x 64]
+  uint8_t xf[SketchCfg<F32IN>::kF32Stages][F32IN ? kF32Tile : 1024];
+  uint8_t x[SketchCfg<F32IN>::kPStages][2][kPieceTile];   // [stage][piece][128 x 64]
   uint8_t om[2][kOmegaTile];
-  uint64_t full[kStages], empty[kStages], om_full[2], om_empty[2], done;
+  uint64_t f32full[SketchCfg<F32IN>::kF32Stages], f32empty[SketchCfg<F32IN>::kF32Stages];
+  uint64_t full[SketchCfg<F32IN>::kPStages], empty[SketchCfg<F32IN>::kPStages], om_full[2], om_empty[2], done;
   uint32_t tmem_slot;
+  double nrm[8];
 };
 
 // byte offset of element (row, col) of a K-major 128B-swizzled tile whose rows hold 64 BF16
@@ -46,12 +65,21 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int col) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (col & 7) * 2);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// F32IN = false: map0 / map1 are the BF16 pieces (box 64 x 64).  F32IN = true: map0 is the FP32
+// tensor (box 32 x 64), split on the fly; norm_part[blockIdx.x] receives this CTA's sum of
+// squares of the split values (head + tail).
+template <bool F32IN>
+__global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, int npieces,
                      int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
-                     uint32_t sid, float* __restrict__ part, int32_t* __restrict__ err) {
+                     uint32_t sid, float* __restrict__ part, double* __restrict__ norm_part,
+                     int32_t* __restrict__ err) {
+  using Cfg = SketchCfg<F32IN>;
+  constexpr int NS = Cfg::kPStages;
+  constexpr int NF = Cfg::kF32Stages;
   extern __shared__ uint8_t smem_raw[];
-  SketchSmem& S = *reinterpret_cast<SketchSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  SketchSmem<F32IN>& S =
+      *reinterpret_cast<SketchSmem<F32IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (M + kPChunk - 1) / kPChunk;
   const int64_t c_begin = (int64_t)blockIdx.x * chunks_per_cta;
@@ -59,9 +87,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_cols = (uint32_t)(mtiles <= 1 ? 64 : (mtiles <= 2 ? 128 : (mtiles <= 4 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&S.full[s], 1);
+    for (int s = 0; s < NS; ++s) {
+      tc::mbar_init(&S.full[s], F32IN ? Cfg::kConv : 1);
       tc::mbar_init(&S.empty[s], 1);
+    }
+    if (F32IN) {
+      for (int s = 0; s < NF; ++s) {
+        tc::mbar_init(&S.f32full[s], 1);
+        tc::mbar_init(&S.f32empty[s], Cfg::kConv);
+      }
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&S.om_full[b], 128);
@@ -83,18 +117,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0 && c_begin < c_end) {
       tc::prefetch_tmap(&map0);
-      if (npieces > 1) tc::prefetch_tmap(&map1);
+      if (!F32IN && npieces > 1) tc::prefetch_tmap(&map1);
       uint32_t it = 0;
       for (int64_t c = c_begin; c < c_end; ++c) {
         const int32_t p0 = (int32_t)(c * kPChunk);
         for (int m = 0; m < mtiles; ++m, ++it) {
-          const uint32_t s = it % kStages;
-          if (it >= kStages && !tc::mbar_wait(&S.empty[s], ((it / kStages) - 1) & 1, err, 1)) break;
-          tc::mbar_arrive_expect_tx(&S.full[s], kPieceTile * (uint32_t)npieces);
-          for (int pc = 0; pc < npieces; ++pc) {
-            const CUtensorMap* mp = pc == 0 ? &map0 : &map1;
-            tc::tma_load_2d(&S.x[s][pc][0], mp, m * kRowsTile, p0, &S.full[s]);
-            tc::tma_load_2d(&S.x[s][pc][kHalfBox], mp, m * kRowsTile + 64, p0, &S.full[s]);
+          if constexpr (F32IN) {
+            const uint32_t s = it % NF;
+            if (it >= NF && !tc::mbar_wait(&S.f32empty[s], ((it / NF) - 1) & 1, err, 1)) break;
+            tc::mbar_arrive_expect_tx(&S.f32full[s], kF32Tile);
+            for (int b = 0; b < 4; ++b)
+              tc::tma_load_2d(&S.xf[s][b * kF32Box], &map0, m * kRowsTile + 32 * b, p0, &S.f32full[s]);
+          } else {
+            const uint32_t s = it % NS;
+            if (it >= NS && !tc::mbar_wait(&S.empty[s], ((it / NS) - 1) & 1, err, 1)) break;
+            tc::mbar_arrive_expect_tx(&S.full[s], kPieceTile * (uint32_t)npieces);
+            for (int pc = 0; pc < npieces; ++pc) {
+              const CUtensorMap* mp = pc == 0 ? &map0 : &map1;
+              tc::tma_load_2d(&S.x[s][pc][0], mp, m * kRowsTile, p0, &S.full[s]);
+              tc::tma_load_2d(&S.x[s][pc][kHalfBox], mp, m * kRowsTile + 64, p0, &S.full[s]);
+            }
           }
         }
       }
@@ -111,8 +153,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tc_fence_after();
         const uint32_t om_addr = tc::smem_u32(&S.om[b][0]);
         for (int m = 0; m < mtiles; ++m, ++it) {
-          const uint32_t s = it % kStages;
-          if (!tc::mbar_wait(&S.full[s], (it / kStages) & 1, err, 3)) break;
+          const uint32_t s = it % NS;
+          if (!tc::mbar_wait(&S.full[s], (it / NS) & 1, err, 3)) break;
           tc::tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(m * 64);
           for (int kk = 0; kk < kPChunk / 16; ++kk) {
@@ -129,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc::mma_commit(&S.done);
     }
-  } else {
+  } else if (warp < 6) {
     // ---------------- Omega generators (warps 2..5) ----------------
     const int t = threadIdx.x - 64;   // 0..127
     uint32_t oc = 0;
@@ -172,6 +214,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (c_begin >= c_end) {
       // no work: this CTA's partial is zero
       for (int64_t e = t; e < (int64_t)ell * I; e += 128) part[(int64_t)blockIdx.x * ell * I + e] = 0.0f;
+    }
+  } else if constexpr (F32IN) {
+    // ---------------- converters (warps 6..13): FP32 tile -> BF16 head + tail ----------------
+    const int t = threadIdx.x - 192;   // 0..255
+    double acc = 0.0;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t c = c_begin; c < c_end && ok; ++c) {
+      for (int m = 0; m < mtiles; ++m, ++it) {
+        const uint32_t s = it % NF, ps = it % NS;
+        if (!tc::mbar_wait(&S.f32full[s], (it / NF) & 1, err, 6) ||
+            (it >= NS && !tc::mbar_wait(&S.empty[ps], ((it / NS) - 1) & 1, err, 7))) {
+          ok = false;
+          break;
+        }
+        acc += (double)tc::convert_tile<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+        tc::fence_proxy_async_smem();
+        tc::mbar_arrive(&S.f32empty[s]);
+        tc::mbar_arrive(&S.full[ps]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) S.nrm[warp - 6] = acc;
+    asm volatile("bar.sync 2, 256;" ::: "memory");
+    if (t == 0 && norm_part != nullptr) {
+      double sum = 0.0;
+      for (int w = 0; w < 8; ++w) sum += S.nrm[w];
+      norm_part[blockIdx.x] = sum;
     }
   }
   tc::tc_fence_before();
@@ -244,24 +315,28 @@ rh_status get_encoder(EncodeTiledFn* fn) {
 
 }  // namespace
 
-// 2-D BF16 tensor map over a rows x cols column-major matrix (rows contiguous), box 64 x box_cols,
-// 128-byte swizzle, zero fill outside.
-rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_cols) {
+// 2-D tensor map over a rows x cols column-major matrix (rows contiguous) of BF16 (esize 2) or
+// FP32 (esize 4) values; box (128 bytes of rows) x box_cols, 128-byte swizzle, zero fill outside.
+rh_status make_map_2d(CUtensorMap* map, const void* base, int esize, int64_t rows, int64_t cols, int box_cols) {
   EncodeTiledFn enc;
   rh_status s = get_encoder(&enc);
   if (s != RH_OK) return s;
   const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
-  const cuuint64_t strides[1] = {(cuuint64_t)rows * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)box_cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)rows * (cuuint64_t)esize};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_cols};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
     return RH_ECUDA;
   }
   return RH_OK;
+}
+
+rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_cols) {
+  return make_map_2d(map, base, 2, rows, cols, box_cols);
 }
 
 bool sketch_tc_supported(const ModeView& v, int ell) {
@@ -273,8 +348,6 @@ int sketch_tc_ctas(const ModeView& v) {
   const int64_t nchunks = ceil_div(v.M(), kPChunk);
   return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nchunks));
 }
-
-size_t sketch_tc_smem() { return sizeof(SketchSmem) + 1024; }
 
 rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
                            uint32_t sid, float* part, int32_t* err, cudaStream_t st) {
@@ -295,10 +368,33 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
   const int64_t nchunks = ceil_div(v.M(), kPChunk);
   const int64_t cpc = ceil_div(nchunks, ctas);
   const int mtiles = (int)ceil_div(v.I, kRowsTile);
-  const size_t smem = sketch_tc_smem();
-  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sketch_tc_kernel<<<ctas, kThreads, smem, st>>>(m0, m1, np, v.I, v.M(), ell, mtiles, cpc,
-                                                 (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part, err);
+  const size_t smem = sizeof(SketchSmem<false>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<false><<<ctas, SketchCfg<false>::kThreads, smem, st>>>(
+      m0, m1, np, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
+      nullptr, err);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
+                               double* norm_part, int32_t* err, cudaStream_t st) {
+  if (!sketch_tc_supported(v, ell)) {
+    set_error("tensor-core sketch: unsupported shape (needs the first mode, I % 8 == 0, I <= 1024, ell <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  CUtensorMap m0;
+  rh_status s = make_map_2d(&m0, X, 4, v.I, v.M(), 64);
+  if (s != RH_OK) return s;
+  const int ctas = sketch_tc_ctas(v);
+  const int64_t nchunks = ceil_div(v.M(), kPChunk);
+  const int64_t cpc = ceil_div(nchunks, ctas);
+  const int mtiles = (int)ceil_div(v.I, kRowsTile);
+  const size_t smem = sizeof(SketchSmem<true>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<true><<<ctas, SketchCfg<true>::kThreads, smem, st>>>(
+      m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
+      norm_part, err);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -308,6 +404,12 @@ rh_status launch_pieces_sumsq(const uint16_t* piece0, const uint16_t* piece1, in
   pieces_sumsq_kernel<<<1024, 256, 0, st>>>(piece0, piece1, n, part);
   RH_LAUNCH_CHECK();
   sum_n_kernel<<<1, 32, 0, st>>>(part, 1024, out);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st) {
+  sum_n_kernel<<<1, 32, 0, st>>>(part, n, out);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

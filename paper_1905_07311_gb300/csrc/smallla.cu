@@ -295,157 +295,173 @@ __device__ void smem_householder_r(T* A, int rows, int n, int ld, T* scratch, T*
 }
 
 // Level 0: block b holds rows [b rows0, ...) of B^T, with B^T[p, c] = B[(p % L) + L n (p / L) + L c].
+// CTAs loop over the blocks (the grid is capped), so a launch whose gate is off costs little.
 template <typename T>
 __global__ void __launch_bounds__(1024) tsqr_leaf_kernel(const T* __restrict__ B, int64_t L, int64_t R, int n,
-                                                         int rows0, int ld, T* __restrict__ Rout) {
+                                                         int rows0, int ld, T* __restrict__ Rout,
+                                                         const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* red = A + (int64_t)ld * n;
   __shared__ T scratch[33];
   const int64_t M = L * R;
-  const int64_t p0 = (int64_t)blockIdx.x * rows0;
-  const int rows = (int)(M - p0 < rows0 ? M - p0 : rows0);
-  if (L == 1) {
-    // B^T rows are contiguous: element (r, c) at n (p0 + r) + c; read the block linearly
-    const T* src = B + n * p0;
-    for (int e = threadIdx.x; e < rows0 * n; e += blockDim.x) {
-      const int r = e / n, c = e % n;
-      A[r + (int64_t)ld * c] = (r < rows) ? src[e] : T(0);
-    }
-  } else {
-    for (int r = threadIdx.x; r < rows0; r += blockDim.x) {
-      const int64_t p = p0 + r;
-      if (r < rows) {
-        const int64_t base = (p % L) + L * (int64_t)n * (p / L);
-        for (int c = 0; c < n; ++c) A[r + (int64_t)ld * c] = B[base + L * c];
-      } else {
-        for (int c = 0; c < n; ++c) A[r + (int64_t)ld * c] = T(0);
+  const int64_t nblk = (M + rows0 - 1) / rows0;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t p0 = blk * rows0;
+    const int rows = (int)(M - p0 < rows0 ? M - p0 : rows0);
+    __syncthreads();
+    if (L == 1) {
+      // B^T rows are contiguous: element (r, c) at n (p0 + r) + c; read the block linearly
+      const T* src = B + n * p0;
+      for (int e = threadIdx.x; e < rows0 * n; e += blockDim.x) {
+        const int r = e / n, c = e % n;
+        A[r + (int64_t)ld * c] = (r < rows) ? src[e] : T(0);
+      }
+    } else {
+      for (int r = threadIdx.x; r < rows0; r += blockDim.x) {
+        const int64_t p = p0 + r;
+        if (r < rows) {
+          const int64_t base = (p % L) + L * (int64_t)n * (p / L);
+          for (int c = 0; c < n; ++c) A[r + (int64_t)ld * c] = B[base + L * c];
+        } else {
+          for (int c = 0; c < n; ++c) A[r + (int64_t)ld * c] = T(0);
+        }
       }
     }
-  }
-  __syncthreads();
-  smem_householder_r(A, max(rows, n), n, ld, scratch, red);
-  T* o = Rout + (int64_t)blockIdx.x * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int j = e % n, k = e / n;
-    o[e] = (j <= k && j < rows) ? A[j + (int64_t)ld * k] : T(0);
+    __syncthreads();
+    smem_householder_r(A, max(rows, n), n, ld, scratch, red);
+    T* o = Rout + blk * n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int j = e % n, k = e / n;
+      o[e] = (j <= k && j < rows) ? A[j + (int64_t)ld * k] : T(0);
+    }
   }
 }
 
 // Higher level: block b stacks R's [b fan, b fan + fan) (each n x n) and re-triangularises.
 template <typename T>
 __global__ void __launch_bounds__(1024) tsqr_merge_kernel(const T* __restrict__ Rin, int64_t nin, int n, int fan,
-                                                          int ld, T* __restrict__ Rout) {
+                                                          int ld, T* __restrict__ Rout, const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* red = A + (int64_t)ld * n;
   __shared__ T scratch[33];
-  const int64_t b0 = (int64_t)blockIdx.x * fan;
-  const int cnt = (int)(nin - b0 < fan ? nin - b0 : fan);
-  const int rows = cnt * n;
-  for (int e = threadIdx.x; e < ld * n; e += blockDim.x) {
-    const int r = e % ld, c = e / ld;
-    const int q = r / n, j = r % n;
-    A[r + (int64_t)ld * c] = (q < cnt && r < fan * n) ? Rin[(b0 + q) * n * n + j + n * c] : T(0);
-  }
-  __syncthreads();
-  smem_householder_r(A, rows, n, ld, scratch, red);
-  T* o = Rout + (int64_t)blockIdx.x * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int j = e % n, k = e / n;
-    o[e] = (j <= k) ? A[j + (int64_t)ld * k] : T(0);
+  const int64_t nout = (nin + fan - 1) / fan;
+  for (int64_t blk = blockIdx.x; blk < nout; blk += gridDim.x) {
+    const int64_t b0 = blk * fan;
+    const int cnt = (int)(nin - b0 < fan ? nin - b0 : fan);
+    const int rows = cnt * n;
+    __syncthreads();
+    for (int e = threadIdx.x; e < ld * n; e += blockDim.x) {
+      const int r = e % ld, c = e / ld;
+      const int q = r / n, j = r % n;
+      A[r + (int64_t)ld * c] = (q < cnt && r < fan * n) ? Rin[(b0 + q) * n * n + j + n * c] : T(0);
+    }
+    __syncthreads();
+    smem_householder_r(A, rows, n, ld, scratch, red);
+    T* o = Rout + blk * n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int j = e % n, k = e / n;
+      o[e] = (j <= k) ? A[j + (int64_t)ld * k] : T(0);
+    }
   }
 }
 
 // One-sided Jacobi on the columns of R (n x n, n <= 64): R V = U S.  Writes Ub = V with columns
 // sorted by decreasing singular value and sv (both FP64).
-// Schedule: np = n rounded up to even "players" (a zero dummy when n is odd); warp w owns the
-// players at circle positions w and np-1-w.  In every round each warp rotates its pair, then
-// the players at positions 1..np-1 move one place round the circle (position 0 stays), which
-// pairs every two players once per sweep of np-1 rounds.  Columns travel between warps through
-// two alternating shared-memory buffers, so a round needs a single barrier.
+// Schedule: np = n rounded up to even "players" (a zero dummy when n is odd, which never
+// rotates); warp w owns the players at circle positions w and np-1-w.  In every round each warp
+// rotates its pair, then the players at positions 1..np-1 move one place round the circle
+// (position 0 stays), which pairs every two players once per sweep of np-1 rounds and brings
+// every player back to its starting position at the end of the sweep.  Columns travel between
+// warps through two alternating shared-memory buffers, so a round needs a single barrier; lane l
+// keeps entries l and l + 32 of a column and of its V column as one 4-vector.
 // Each player carries its squared norm: a round computes only the inner product g = a^T b and
 // updates the norms of the rotated pair in closed form (a'^2 = a^2 - t g, b'^2 = b^2 + t g);
-// the norms are re-measured at the start of every sweep.  The rotation angle t is computed in
-// FP32 (c = 1/sqrt(1+t^2), s = c t are then formed in T, so c^2 + s^2 = 1 to T's rounding).  A
-// rotation is applied when |g| > tol |a| |b|, tol = 8 max(n, 8) eps: the computed inner product
-// carries a rounding error up to n eps |a| |b|, so a threshold at that level is never met.
+// the norms are re-measured at the start of every sweep.  A rotation is applied when
+// |g| > tol |a| |b|, tol = 8 max(n, 8) eps: the computed inner product carries a rounding error
+// up to n eps |a| |b|, so a threshold at that level is never met.  The rotation
+// t = sign(z) / (|z| + sqrt(1 + z^2)), z = (b^2 - a^2) / (2 g), c = 1 / sqrt(1 + t^2), s = c t is
+// formed in T.
+template <typename T>
+struct alignas(4 * sizeof(T)) JacobiQuad {
+  T x0, x1, v0, v1;
+};
+
+__device__ __forceinline__ float jacobi_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double jacobi_rsqrt(double x) { return 1.0 / sqrt(x); }
+
 template <typename T>
 __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ Rin, int n, double* __restrict__ Ub,
-                                                          double* __restrict__ sv) {
+                                                          double* __restrict__ sv, const int32_t* __restrict__ gate,
+                                                          int32_t want) {
+  if (gate != nullptr && *gate != want) return;
+  using Q4 = JacobiQuad<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int np = (n + 1) & ~1;
   const int half = np / 2;
-  // buffer b (0/1): for each position q, the column (n values) and its V column (n values)
-  T* buf0 = reinterpret_cast<T*>(smem_raw);
-  T* buf1 = buf0 + (size_t)2 * np * n;
+  Q4* buf0 = reinterpret_cast<Q4*>(smem_raw);   // [position][lane]
+  Q4* buf1 = buf0 + (size_t)np * 32;
   __shared__ T nrm2[2][RH_MAX_ELL];
   __shared__ T sig[RH_MAX_ELL];
-  __shared__ int pid[2][RH_MAX_ELL];   // original column index held at each position
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
-    const int i = e % n, q = e / n;
-    buf0[(size_t)2 * n * q + i] = (q < n) ? Rin[i + n * q] : T(0);
-    buf0[(size_t)2 * n * q + n + i] = (q < n && i == q) ? T(1) : T(0);
+  for (int e = threadIdx.x; e < np * 32; e += blockDim.x) {
+    const int q = e >> 5, l = e & 31;
+    Q4 z;
+    const bool col = q < n;
+    z.x0 = (col && l < n) ? Rin[l + n * q] : T(0);
+    z.x1 = (col && l + 32 < n) ? Rin[l + 32 + n * q] : T(0);
+    z.v0 = (col && l == q) ? T(1) : T(0);
+    z.v1 = (col && l + 32 == q) ? T(1) : T(0);
+    buf0[e] = z;
   }
-  for (int q = threadIdx.x; q < np; q += blockDim.x) pid[0][q] = q;
   __syncthreads();
-  const float tol = (float)(8 * (n > 8 ? n : 8)) * ((sizeof(T) == 4) ? 5.9604645e-8f : 1.1102230246e-16f);
+  const T tol = T(8 * (n > 8 ? n : 8)) * ((sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16));
+  // fixed circle positions of this warp and where their players move after a round
+  const int qa = w, qb = np - 1 - w;
+  const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
+  const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
   int cur = 0;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    // re-measure the squared norms of all players
     {
-      const T* src = cur ? buf1 : buf0;
+      const Q4* src = cur ? buf1 : buf0;
       for (int q = w; q < np; q += nw) {
-        const T* x = src + (size_t)2 * n * q;
-        T a = T(0);
-        for (int i = lane; i < n; i += 32) a += x[i] * x[i];
-        a = warp_sum(a);
+        const Q4 z = src[q * 32 + lane];
+        const T a = warp_sum(z.x0 * z.x0 + z.x1 * z.x1);
         if (lane == 0) nrm2[cur][q] = a;
       }
       __syncthreads();
     }
     int rotated = 0;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
-      T* src = cur ? buf1 : buf0;
-      T* dst = cur ? buf0 : buf1;
+      const Q4* src = cur ? buf1 : buf0;
+      Q4* dst = cur ? buf0 : buf1;
       if (w < half) {
-        const int qa = w, qb = np - 1 - w;
-        const T* ca = src + (size_t)2 * n * qa;
-        const T* cb = src + (size_t)2 * n * qb;
-        T xa0 = lane < n ? ca[lane] : T(0), xa1 = lane + 32 < n ? ca[lane + 32] : T(0);
-        T xb0 = lane < n ? cb[lane] : T(0), xb1 = lane + 32 < n ? cb[lane + 32] : T(0);
-        T va0 = lane < n ? ca[n + lane] : T(0), va1 = lane + 32 < n ? ca[n + lane + 32] : T(0);
-        T vb0 = lane < n ? cb[n + lane] : T(0), vb1 = lane + 32 < n ? cb[n + lane + 32] : T(0);
+        Q4 A = src[qa * 32 + lane];
+        Q4 Bq = src[qb * 32 + lane];
         T al = nrm2[cur][qa], be = nrm2[cur][qb];
-        T ga = warp_sum(xa0 * xb0 + xa1 * xb1);
-        const bool dummy = (pid[cur][qa] >= n) || (pid[cur][qb] >= n);
-        const float gf = (float)ga, af = (float)al, bf = (float)be;
-        if (!dummy && gf != 0.0f && fabsf(gf) > tol * sqrtf(af) * sqrtf(bf)) {
-          const float zeta = (bf - af) / (2.0f * gf);
-          const float tf = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-          const T t = (T)tf;
-          const T c = T(1) / sqrt(T(1) + t * t);
+        const T g = warp_sum(A.x0 * Bq.x0 + A.x1 * Bq.x1);
+        if (g != T(0) && fabs(g) * jacobi_rsqrt(al) * jacobi_rsqrt(be) > tol) {
+          const T zeta = (be - al) / (T(2) * g);
+          const T az = fabs(zeta);
+          const T tm = az < T(1e18) ? T(1) / (az + sqrt(fma(az, az, T(1)))) : T(0.5) / az;
+          const T t = zeta < T(0) ? -tm : tm;
+          const T c = jacobi_rsqrt(fma(t, t, T(1)));
           const T sn = c * t;
           T u;
-          u = xa0; xa0 = c * u - sn * xb0; xb0 = sn * u + c * xb0;
-          u = xa1; xa1 = c * u - sn * xb1; xb1 = sn * u + c * xb1;
-          u = va0; va0 = c * u - sn * vb0; vb0 = sn * u + c * vb0;
-          u = va1; va1 = c * u - sn * vb1; vb1 = sn * u + c * vb1;
-          al = al - t * ga;
-          be = be + t * ga;
+          u = A.x0; A.x0 = c * u - sn * Bq.x0; Bq.x0 = sn * u + c * Bq.x0;
+          u = A.x1; A.x1 = c * u - sn * Bq.x1; Bq.x1 = sn * u + c * Bq.x1;
+          u = A.v0; A.v0 = c * u - sn * Bq.v0; Bq.v0 = sn * u + c * Bq.v0;
+          u = A.v1; A.v1 = c * u - sn * Bq.v1; Bq.v1 = sn * u + c * Bq.v1;
+          al = al - t * g;
+          be = be + t * g;
           rotated = 1;
         }
-        // positions after the move round the circle: 0 -> 0, np-1 -> 1, q -> q+1
-        const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
-        const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
-        T* da = dst + (size_t)2 * n * na;
-        T* db = dst + (size_t)2 * n * nb;
-        if (lane < n) { da[lane] = xa0; db[lane] = xb0; da[n + lane] = va0; db[n + lane] = vb0; }
-        if (lane + 32 < n) { da[lane + 32] = xa1; db[lane + 32] = xb1; da[n + lane + 32] = va1; db[n + lane + 32] = vb1; }
+        dst[na * 32 + lane] = A;
+        dst[nb * 32 + lane] = Bq;
         if (lane == 0) {
-          pid[cur ^ 1][na] = pid[cur][qa];
-          pid[cur ^ 1][nb] = pid[cur][qb];
           nrm2[cur ^ 1][na] = al;
           nrm2[cur ^ 1][nb] = be;
         }
@@ -455,22 +471,21 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ 
     }
     if (!__syncthreads_or(rotated)) break;
   }
-  T* fin = cur ? buf1 : buf0;
+  // every sweep ends with player q at position q
+  const Q4* fin = cur ? buf1 : buf0;
   for (int q = w; q < np; q += nw) {
-    const T* x = fin + (size_t)2 * n * q;
-    T s = T(0);
-    for (int i = lane; i < n; i += 32) s += x[i] * x[i];
-    s = warp_sum(s);
-    if (lane == 0) sig[q] = (pid[cur][q] < n) ? sqrt(s) : T(-1);
+    const Q4 z = fin[q * 32 + lane];
+    const T s = warp_sum(z.x0 * z.x0 + z.x1 * z.x1);
+    if (lane == 0) sig[q] = (q < n) ? sqrt(s) : T(-1);
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < np; q += blockDim.x) {
-    if (pid[cur][q] >= n) continue;
+  for (int q = w; q < n; q += nw) {
     int rank = 0;
-    for (int k = 0; k < np; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && pid[cur][k] < pid[cur][q]);
-    sv[rank] = (double)sig[q];
-    const T* v = fin + (size_t)2 * n * q + n;
-    for (int i = 0; i < n; ++i) Ub[i + n * rank] = (double)v[i];
+    for (int k = 0; k < n; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && k < q);
+    const Q4 z = fin[q * 32 + lane];
+    if (lane == 0) sv[rank] = (double)sig[q];
+    if (lane < n) Ub[lane + n * rank] = (double)z.v0;
+    if (lane + 32 < n) Ub[lane + 32 + n * rank] = (double)z.v1;
   }
 }
 
@@ -558,6 +573,171 @@ __global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* __
   if (threadIdx.x == 0) *out = s;
 }
 
+// Gram matrix W = B_(n) B_(n)^T (ell x ell) of a (L, ell, R) tensor, streamed once: CTAs walk
+// tiles of 128 unfolding columns staged in shared memory (row pp = column p of B_(n), 16-byte
+// aligned rows).  W is split into 4 x 4 blocks and thread t < NB (NB + 1) / 2 owns the t-th
+// block of the upper triangle (NB = ELLP / 4); it sums a tile's 128 products in FP32 and adds
+// the tile sum to FP64 accumulators.  Per-CTA FP64 partials (upper triangle) are reduced in a
+// fixed order.
+template <int ELLP>
+struct GramCfg {
+  static constexpr int NB = ELLP / 4;
+  static constexpr int NBLK = NB * (NB + 1) / 2;
+  static constexpr int THREADS = (NBLK + 31) / 32 * 32;
+  static constexpr int LDS = ELLP + 4;
+};
+
+template <int ELLP>
+__global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const float* __restrict__ B, int64_t L,
+                                                                        int64_t R, int ell, double* __restrict__ part,
+                                                                        const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate != 0) return;
+  using C = GramCfg<ELLP>;
+  __shared__ __align__(16) float Bs[128 * C::LDS];
+  const int tid = threadIdx.x;
+  int bi = 0, bj = tid;
+  while (bi < C::NB && bj >= C::NB - bi) {
+    bj -= C::NB - bi;
+    ++bi;
+  }
+  bj += bi;
+  const bool active = tid < C::NBLK;
+  const int64_t M = L * R;
+  const int64_t ntiles = (M + 127) / 128;
+  for (int e = tid; e < 128 * (C::LDS - ell); e += blockDim.x) {
+    const int w = C::LDS - ell;
+    Bs[(e / w) * C::LDS + ell + e % w] = 0.0f;
+  }
+  double accd[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * 128;
+    const int valid = (int)(M - p0 < 128 ? M - p0 : 128);
+    __syncthreads();
+    if (L == 1) {
+      // the tile is 128 x ell contiguous values starting 512 ell bytes into B: 16-byte aligned
+      const float* src = B + (int64_t)ell * p0;
+      const int nvalid = valid * ell;
+      for (int e4 = tid; e4 < 32 * ell; e4 += blockDim.x) {
+        const int e = 4 * e4;
+        float v[4];
+        if (e + 3 < nvalid) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(src) + e4);
+          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[k] = (e + k < nvalid) ? src[e + k] : 0.0f;
+        }
+        int pp = e / ell, c = e - pp * ell;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          Bs[pp * C::LDS + c] = v[k];
+          if (++c == ell) {
+            c = 0;
+            ++pp;
+          }
+        }
+      }
+    } else {
+      for (int pp = tid; pp < 128; pp += blockDim.x) {
+        if (pp < valid) {
+          const int64_t p = p0 + pp;
+          const float* src = B + (p % L) + L * (int64_t)ell * (p / L);
+          for (int c = 0; c < ell; ++c) Bs[pp * C::LDS + c] = src[L * c];
+        } else {
+          for (int c = 0; c < ell; ++c) Bs[pp * C::LDS + c] = 0.0f;
+        }
+      }
+    }
+    __syncthreads();
+    if (active) {
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+#pragma unroll 8
+      for (int pp = 0; pp < 128; ++pp) {
+        const float4 x = *reinterpret_cast<const float4*>(&Bs[pp * C::LDS + 4 * bi]);
+        const float4 y = *reinterpret_cast<const float4*>(&Bs[pp * C::LDS + 4 * bj]);
+        const float xa[4] = {x.x, x.y, x.z, x.w};
+        const float yb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) accd[a][b] += (double)acc[a][b];
+    }
+  }
+  if (!active) return;
+  double* o = part + (int64_t)blockIdx.x * ell * ell;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = 4 * bi + a, c = 4 * bj + b;
+      if (r <= c && c < ell) o[r + ell * c] = accd[a][b];
+    }
+}
+
+// W[r, c] = sum over CTAs of the upper-triangle partial at (min(r, c), max(r, c)).  A block of
+// 256 threads owns 32 consecutive entries of W: warp k sums partials k, k + 8, ... and the eight
+// warp sums are added in a fixed order.
+__global__ void __launch_bounds__(256) gram_b_reduce_kernel(const double* __restrict__ part, int nparts, int ell,
+                                                            double* __restrict__ W, const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate != 0) return;
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int nn = ell * ell;
+  const int e = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < nn) {
+    const int r = e % ell, c = e / ell;
+    const int u = r <= c ? e : c + ell * r;
+    for (int k = wp; k < nparts; k += 8) s += part[(int64_t)k * nn + u];
+  }
+  red[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && e < nn) {
+    double t = red[0][lane];
+    for (int k = 1; k < 8; ++k) t += red[k][lane];
+    W[e] = t;
+  }
+}
+
+// After the Gram route: fall back to the tall-skinny QR when the Cholesky factor broke down or
+// when the truncation gap sigma_r^2 - sigma_{r+1}^2 is below 1e-5 sigma_1^2, where the FP32
+// Gram cannot resolve the top-r subspace.
+__global__ void trunc_decide_kernel(const int32_t* __restrict__ chol_flag, const double* __restrict__ sv, int ell, int r,
+                                    int32_t* __restrict__ use_tsqr, int32_t* __restrict__ info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (*chol_flag) {
+    *use_tsqr = 1;
+    return;
+  }
+  const double s1 = sv[0];
+  const double sr = sv[r - 1];
+  const double sr1 = (r < ell) ? sv[r] : 0.0;
+  const bool ok = (r >= ell) || (s1 == 0.0) || (sr * sr - sr1 * sr1 >= 1e-5 * s1 * s1);
+  *use_tsqr = ok ? 0 : 1;
+  if (ok && info != nullptr) *info |= 2;
+}
+
+template <typename T>
+__global__ void cast_gated_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n,
+                                  const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate != 0) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -640,49 +820,96 @@ static void trunc_dims(TruncPlan& pl) {
 
 static int odd_ld(int rows) { return rows | 1; }
 
+static int gram_ctas() { return 4 * num_sms(); }
+
 template <typename T>
 size_t trunc_workspace_elems(const TruncPlan& pl0) {
   TruncPlan pl = pl0;
   trunc_dims<T>(pl);
   const int64_t nn = (int64_t)pl.ell * pl.ell;
   // two ping-pong buffers of R's
-  return (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+  size_t e = (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+  if (sizeof(T) == 4) {
+    // Gram route: CTA partials, W, R, rdiag, flags (in doubles), the FP32 copy of R
+    const size_t dbl = (size_t)gram_ctas() * nn + 2 * nn + pl.ell + 8;
+    e += 2 * dbl + nn + 64;
+  }
+  return e;
 }
 
 template <typename T>
-rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st) {
+rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st, int r,
+                           int32_t* info) {
   TruncPlan pl = pl0;
   trunc_dims<T>(pl);
   const int n = pl.ell;
   const int64_t nn = (int64_t)n * n;
   T* buf0 = ws;
   T* buf1 = ws + pl.nblk0 * nn;
+  const int np = (n + 1) & ~1;
+  const size_t smj = sizeof(T) * 4 * (size_t)np * 32 * 2;
+  RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
+  int32_t* use_tsqr = nullptr;
+  if (sizeof(T) == 4 && r >= 1 && r <= n) {
+    // Gram route (FP32 data): W = B B^T, R = chol(W)^T-factor, Jacobi on R; gated fallback below
+    const size_t tsqr_elems = (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+    double* dbase = reinterpret_cast<double*>(ws + ((tsqr_elems + 63) & ~size_t(63)));
+    const int ctas = gram_ctas();
+    double* part = dbase;
+    double* W = part + (size_t)ctas * nn;
+    double* Rd = W + nn;
+    double* rdiag = Rd + nn;
+    int32_t* flags = reinterpret_cast<int32_t*>(rdiag + n);
+    float* Rf = reinterpret_cast<float*>(flags + 16);
+    use_tsqr = flags + 1;
+    RH_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), st));
+    if (n <= 32)
+      gram_b_kernel<32><<<ctas, GramCfg<32>::THREADS, 0, st>>>(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n,
+                                                              part, nullptr);
+    else
+      gram_b_kernel<64><<<ctas, GramCfg<64>::THREADS, 0, st>>>(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n,
+                                                              part, nullptr);
+    RH_LAUNCH_CHECK();
+    gram_b_reduce_kernel<<<(int)ceil_div(nn, 32), 256, 0, st>>>(part, ctas, n, W, nullptr);
+    RH_LAUNCH_CHECK();
+    cholesky_kernel<<<1, 256, sizeof(double) * nn, st>>>(W, n, Rd, rdiag, flags);
+    RH_LAUNCH_CHECK();
+    cast_gated_kernel<float><<<(int)ceil_div(nn, 256), 256, 0, st>>>(Rd, Rf, nn, flags);
+    RH_LAUNCH_CHECK();
+    {
+      ProfileScope ps(PROF_JACOBI, 0, st);
+      jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(reinterpret_cast<const T*>(Rf), n, Ub, sv, flags, 0);
+      RH_LAUNCH_CHECK();
+    }
+    trunc_decide_kernel<<<1, 32, 0, st>>>(flags, sv, n, r, use_tsqr, info);
+    RH_LAUNCH_CHECK();
+  }
   const int ld0 = odd_ld(pl.rows0);
   const int ldm = odd_ld(pl.fan * n);
   const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
   const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
   RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
   RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-  tsqr_leaf_kernel<T><<<(unsigned)pl.nblk0, kTsqrThreads, sm0, st>>>(B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0);
+  const int64_t tsqr_grid_cap = 8 * (int64_t)num_sms();
+  tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, tsqr_grid_cap), kTsqrThreads, sm0, st>>>(
+      B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, use_tsqr);
   RH_LAUNCH_CHECK();
   int64_t cnt = pl.nblk0;
   T* cur = buf0;
   T* nxt = buf1;
   while (cnt > 1) {
     const int64_t nout = ceil_div(cnt, pl.fan);
-    tsqr_merge_kernel<T><<<(unsigned)nout, kTsqrThreads, smm, st>>>(cur, cnt, n, pl.fan, ldm, nxt);
+    tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, tsqr_grid_cap), kTsqrThreads, smm, st>>>(
+        cur, cnt, n, pl.fan, ldm, nxt, use_tsqr);
     RH_LAUNCH_CHECK();
     cnt = nout;
     T* t = cur;
     cur = nxt;
     nxt = t;
   }
-  const int np = (n + 1) & ~1;
-  const size_t smj = sizeof(T) * 4 * (size_t)np * n;
-  RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
   {
-    ProfileScope ps(PROF_JACOBI, 0, st);
-    jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(cur, n, Ub, sv);
+    ProfileScope ps(PROF_JACOBI, 1, st);
+    jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(cur, n, Ub, sv, use_tsqr, 1);
     RH_LAUNCH_CHECK();
   }
   return RH_OK;
@@ -716,8 +943,10 @@ rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st)
 
 template size_t trunc_workspace_elems<float>(const TruncPlan&);
 template size_t trunc_workspace_elems<double>(const TruncPlan&);
-template rh_status launch_trunc_svd<float>(const TruncPlan&, const float*, float*, double*, double*, cudaStream_t);
-template rh_status launch_trunc_svd<double>(const TruncPlan&, const double*, double*, double*, double*, cudaStream_t);
+template rh_status launch_trunc_svd<float>(const TruncPlan&, const float*, float*, double*, double*, cudaStream_t, int,
+                                           int32_t*);
+template rh_status launch_trunc_svd<double>(const TruncPlan&, const double*, double*, double*, double*, cudaStream_t,
+                                            int, int32_t*);
 template rh_status launch_factor_and_cast<float>(int64_t, int, int, const double*, const double*, double*, float*,
                                                  cudaStream_t);
 template rh_status launch_factor_and_cast<double>(int64_t, int, int, const double*, const double*, double*, double*,

@@ -138,5 +138,45 @@ __device__ __forceinline__ uint16_t bf16_rne(float x) {
 }
 __device__ __forceinline__ float bf16_to_f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
+// Two FP32 values rounded to BF16 (nearest, ties to even) and packed: lo in bits 0-15.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// Split a 32 KB tile of FP32 values staged by TMA (boxes of 32 values x kRowsPerBox rows, 128-byte
+// rows, 128-byte swizzle) into its BF16 head and tail, written as 128 rows of 64 values (128-byte
+// rows, 128-byte swizzle): box b, row r holds the values 32 (b & 1) .. 32 (b & 1) + 31 of output
+// row (b >> 1) kRowsPerBox + r.  Eight consecutive threads read one 128-byte FP32 row (4 values
+// each).  Returns the FP32 sum of (head + tail)^2 over the values this thread handled.
+template <int kRowsPerBox, int kThreadsConv>
+__device__ __forceinline__ float convert_tile(const uint8_t* f32, uint8_t* hi, uint8_t* lo, int t) {
+  float ss = 0.0f;
+#pragma unroll 4
+  for (int j = 0; j < 2048 / kThreadsConv; ++j) {
+    const int u = j * kThreadsConv + t;
+    const int k = u & 7, br = u >> 3;
+    const int b = br / kRowsPerBox, r = br % kRowsPerBox;
+    const float4 v = *reinterpret_cast<const float4*>(f32 + b * (kRowsPerBox * 128) + r * 128 + ((k ^ (r & 7)) << 4));
+    const uint32_t h01 = pack_bf16x2(v.x, v.y), h23 = pack_bf16x2(v.z, v.w);
+    const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
+    const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
+    const uint32_t t01 = pack_bf16x2(v.x - f0, v.y - f1), t23 = pack_bf16x2(v.z - f2, v.w - f3);
+    const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
+    const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
+    ss = fmaf(g0, g0, ss);
+    ss = fmaf(g1, g1, ss);
+    ss = fmaf(g2, g2, ss);
+    ss = fmaf(g3, g3, ss);
+    const int rho = (b >> 1) * kRowsPerBox + r;
+    const int ci = 4 * (b & 1) + (k >> 1);
+    const int off = rho * 128 + ((ci ^ (rho & 7)) << 4) + (k & 1) * 8;
+    *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
+    *reinterpret_cast<uint2*>(lo + off) = make_uint2(t01, t23);
+  }
+  return ss;
+}
+
 }  // namespace tc
 }  // namespace rh

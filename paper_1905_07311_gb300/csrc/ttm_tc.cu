@@ -14,6 +14,9 @@
 // epilogue of one tile overlaps the MMAs of the next.  Warp roles (192 threads): warp 0 TMA,
 // warp 1 TMEM + MMA, warps 2-5 epilogue (warps 2, 3 read the tail rows and hand them to
 // warps 4, 5 through shared memory, which add the head rows and store B[c + ell p]).
+// FP32 input (448 threads): TMA brings FP32 slices (two 32 x 128 boxes per stage) and warps
+// 6-13 split them in shared memory into the head / tail pieces, so B is bit-identical to the
+// two-piece form.
 #include <string>
 
 #include "common.cuh"
@@ -23,21 +26,36 @@
 namespace rh {
 
 rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_cols);
+rh_status make_map_2d(CUtensorMap* map, const void* base, int esize, int64_t rows, int64_t cols, int box_cols);
 
 namespace {
 
 constexpr int kNTile = 128;   // columns of X_(1) per tile
 constexpr int kKStage = 64;   // rows of X_(1) per stage
-constexpr int kStages = 3;
-constexpr int kThreads = 192;
 constexpr uint32_t kATile = 128 * 64 * 2;      // A slice: 128 rows x 64 (BF16)
 constexpr uint32_t kXTile = kNTile * 64 * 2;   // X slice: 128 columns x 64 rows (BF16)
+constexpr uint32_t kF32Box = kNTile * 32 * 4;  // FP32 TMA box: 32 rows x 128 columns
 
+// BF16 pieces in: 3 stages (A slice + pieces) filled by TMA.  FP32 in: 3 stages of FP32 slices
+// filled by TMA, split by four converter warps into 2 stages of pieces; the converters also
+// request the A slice of their stage.
+template <bool F32IN>
+struct TtmCfg {
+  static constexpr int kPStages = F32IN ? 2 : 3;
+  static constexpr int kF32Stages = F32IN ? 3 : 1;
+  static constexpr int kThreads = F32IN ? 448 : 192;
+  static constexpr int kConv = 256;   // converter threads (warps 6..13)
+};
+
+template <bool F32IN>
 struct alignas(1024) TtmSmem {
-  uint8_t a[kStages][kATile];
-  uint8_t x[kStages][2][kXTile];
+  uint8_t xf[TtmCfg<F32IN>::kF32Stages][F32IN ? 2 * kF32Box : 1024];
+  uint8_t a[TtmCfg<F32IN>::kPStages][kATile];
+  uint8_t x[TtmCfg<F32IN>::kPStages][2][kXTile];
   float xchg[64][kNTile + 1];
-  uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
+  uint64_t f32full[TtmCfg<F32IN>::kF32Stages], f32empty[TtmCfg<F32IN>::kF32Stages];
+  uint64_t full[TtmCfg<F32IN>::kPStages], empty[TtmCfg<F32IN>::kPStages], afull[TtmCfg<F32IN>::kPStages];
+  uint64_t tfull[2], tempty[2];
   uint32_t tmem_slot;
 };
 
@@ -45,21 +63,35 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// F32IN = false: mapX0 / mapX1 are the BF16 pieces (box 64 x 128).  F32IN = true: mapX0 is the
+// FP32 tensor (box 32 x 128), split on the fly into the same two pieces.
+template <bool F32IN>
+__global__ void __launch_bounds__(TtmCfg<F32IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
                   float* __restrict__ B, int32_t* __restrict__ err) {
+  using Cfg = TtmCfg<F32IN>;
+  constexpr int NS = Cfg::kPStages;
+  constexpr int NF = Cfg::kF32Stages;
   extern __shared__ uint8_t smem_raw[];
-  TtmSmem& S = *reinterpret_cast<TtmSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TtmSmem<F32IN>& S =
+      *reinterpret_cast<TtmSmem<F32IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (M + kNTile - 1) / kNTile;
   const int kstages = (int)((I + kKStage - 1) / kKStage);
   const uint32_t tmem_cols = 256;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&S.full[s], 1);
+    for (int s = 0; s < NS; ++s) {
+      tc::mbar_init(&S.full[s], F32IN ? Cfg::kConv : 1);
       tc::mbar_init(&S.empty[s], 1);
+      tc::mbar_init(&S.afull[s], 1);
+    }
+    if (F32IN) {
+      for (int s = 0; s < NF; ++s) {
+        tc::mbar_init(&S.f32full[s], 1);
+        tc::mbar_init(&S.f32empty[s], Cfg::kConv);
+      }
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&S.tfull[b], 1);
@@ -78,23 +110,36 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      tc::prefetch_tmap(&mapA);
       tc::prefetch_tmap(&mapX0);
-      if (npieces > 1) tc::prefetch_tmap(&mapX1);
+      if (!F32IN) {
+        tc::prefetch_tmap(&mapA);
+        if (npieces > 1) tc::prefetch_tmap(&mapX1);
+      }
       uint32_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int32_t p0 = (int32_t)(t * kNTile);
         for (int ks = 0; ks < kstages; ++ks, ++it) {
-          const uint32_t s = it % kStages;
-          if (it >= kStages && !tc::mbar_wait(&S.empty[s], ((it / kStages) - 1) & 1, err, 11)) {
-            ok = false;
-            break;
+          if constexpr (F32IN) {
+            const uint32_t s = it % NF;
+            if (it >= NF && !tc::mbar_wait(&S.f32empty[s], ((it / NF) - 1) & 1, err, 11)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&S.f32full[s], 2 * kF32Box);
+            tc::tma_load_2d(&S.xf[s][0], &mapX0, ks * kKStage, p0, &S.f32full[s]);
+            tc::tma_load_2d(&S.xf[s][kF32Box], &mapX0, ks * kKStage + 32, p0, &S.f32full[s]);
+          } else {
+            const uint32_t s = it % NS;
+            if (it >= NS && !tc::mbar_wait(&S.empty[s], ((it / NS) - 1) & 1, err, 11)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&S.full[s], kATile + kXTile * (uint32_t)npieces);
+            tc::tma_load_2d(&S.a[s][0], &mapA, ks * kKStage, 0, &S.full[s]);
+            tc::tma_load_2d(&S.x[s][0][0], &mapX0, ks * kKStage, p0, &S.full[s]);
+            if (npieces > 1) tc::tma_load_2d(&S.x[s][1][0], &mapX1, ks * kKStage, p0, &S.full[s]);
           }
-          tc::mbar_arrive_expect_tx(&S.full[s], kATile + kXTile * (uint32_t)npieces);
-          tc::tma_load_2d(&S.a[s][0], &mapA, ks * kKStage, 0, &S.full[s]);
-          tc::tma_load_2d(&S.x[s][0][0], &mapX0, ks * kKStage, p0, &S.full[s]);
-          if (npieces > 1) tc::tma_load_2d(&S.x[s][1][0], &mapX1, ks * kKStage, p0, &S.full[s]);
         }
       }
     }
@@ -109,8 +154,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tc_fence_after();
         const uint32_t d = tmem + b * kNTile;
         for (int ks = 0; ks < kstages; ++ks, ++it) {
-          const uint32_t s = it % kStages;
-          if (!tc::mbar_wait(&S.full[s], (it / kStages) & 1, err, 13)) {
+          const uint32_t s = it % NS;
+          if (!tc::mbar_wait(&S.full[s], (it / NS) & 1, err, 13) ||
+              (F32IN && !tc::mbar_wait(&S.afull[s], (it / NS) & 1, err, 15))) {
             ok = false;
             break;
           }
@@ -128,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mma_commit(&S.tfull[b]);
       }
     }
-  } else {
+  } else if (warp < 6) {
     // epilogue: warps 2..5 -> TMEM lane quadrants 2, 3, 0, 1
     const int quad = warp & 3;
     const bool tail = quad >= 2;        // rows 64..127: Q_t^T X
@@ -165,6 +211,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::tc_fence_before();
       tc::mbar_arrive(&S.tempty[b]);
       named_sync(1, 128);   // xchg is free again
+    }
+  } else if constexpr (F32IN) {
+    // converters (warps 6..13): FP32 slice -> BF16 head + tail; thread 0 also requests the A slice
+    const int t = threadIdx.x - 192;   // 0..255
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t tt = blockIdx.x; tt < ntiles && ok; tt += gridDim.x) {
+      for (int ks = 0; ks < kstages; ++ks, ++it) {
+        const uint32_t s = it % NF, ps = it % NS;
+        if (it >= NS && !tc::mbar_wait(&S.empty[ps], ((it / NS) - 1) & 1, err, 16)) {
+          ok = false;
+          break;
+        }
+        if (t == 0) {
+          tc::mbar_arrive_expect_tx(&S.afull[ps], kATile);
+          tc::tma_load_2d(&S.a[ps][0], &mapA, ks * kKStage, 0, &S.afull[ps]);
+        }
+        if (!tc::mbar_wait(&S.f32full[s], (it / NF) & 1, err, 17)) {
+          ok = false;
+          break;
+        }
+        (void)tc::convert_tile<128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+        tc::fence_proxy_async_smem();
+        tc::mbar_arrive(&S.f32empty[s]);
+        tc::mbar_arrive(&S.full[ps]);
+      }
     }
   }
   tc::tc_fence_before();
@@ -221,9 +293,33 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   } else {
     m1 = m0;
   }
-  const size_t smem = sizeof(TtmSmem) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<<<ttm_tc_ctas(v), kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err);
+  const size_t smem = sizeof(TtmSmem<false>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<false><<<ttm_tc_ctas(v), TtmCfg<false>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B,
+                                                                               err);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
+                            int32_t* err, cudaStream_t st) {
+  if (!ttm_tc_supported(v, ell)) {
+    set_error("tensor-core mode product: unsupported shape (needs the first mode, I % 8 == 0, ell <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  {
+    const int64_t total = 128 * v.I;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
+    q_pieces_kernel<<<blocks, 256, 0, st>>>(Q, v.I, ell, qa);
+    RH_LAUNCH_CHECK();
+  }
+  CUtensorMap mA, m0;
+  rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
+  if (s != RH_OK) return s;
+  if ((s = make_map_2d(&m0, X, 4, v.I, v.M(), kNTile)) != RH_OK) return s;
+  const size_t smem = sizeof(TtmSmem<true>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<true><<<ttm_tc_ctas(v), TtmCfg<true>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

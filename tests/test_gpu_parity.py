@@ -205,6 +205,31 @@ def test_rsthosvd_many_tiles(rh, dtype):
     _compare(rh, X, [20, 20, 20], 10, 1, dtype)
 
 
+def test_rsthosvd_f32_gram_route_taken(rh):
+    """Decay 0.9, r = 20 of 25: the truncation gap is far above 1e-5 sigma_1^2, so every mode's
+    truncation SVD goes through the Gram matrix (info bit 2) and still matches the oracle."""
+    X = lowrank_plus_noise_np([300, 200, 130], [25, 25, 25], 0.9, 1e-3, seed=5)
+    T, _, _, _ = _compare(rh, X, [20, 20, 20], 10, 1, np.float32)
+    assert [v & 2 for v in T.info.cpu().numpy().tolist()] == [2, 2, 2]
+
+
+def test_rsthosvd_f32_deep_truncation_falls_back_to_qr(rh):
+    """Decay 0.4 and r = 10: sigma_r^2 - sigma_{r+1}^2 is below 1e-5 sigma_1^2, where FP32 Gram
+    sums cannot resolve the retained subspace; the tall-skinny QR route must run instead."""
+    X = lowrank_plus_noise_np([90, 80, 70], [14, 14, 14], 0.4, 1e-7, seed=12)
+    T, e_g, e_o, _ = _compare(rh, X, [10, 10, 10], 4, 3, np.float32)
+    assert [v & 2 for v in T.info.cpu().numpy().tolist()] == [0, 0, 0]
+
+
+def test_rsthosvd_f32_rank_deficient_sketch(rh):
+    """Exact multilinear rank 4 with ell = 9: B B^T is singular up to rounding, so its FP32 Gram
+    may or may not be numerically definite (either truncation route may run); the result must
+    still recover the rank-4 tensor and match the oracle."""
+    X = lowrank_plus_noise_np([50, 45, 40], [4, 4, 4], 0.8, 0.0, seed=13)
+    T, e_g, _, _ = _compare(rh, X, [4, 4, 4], 5, 2, np.float32, gate=1e-3)
+    assert e_g < 1e-5
+
+
 def test_rsthosvd_hilbert_200_config(rh):
     """200^3 tensor 1/(i+j+k+1), rank 20, p = 5, seed 0, order 1,2,3; FP64."""
     X = hilbert([200, 200, 200], offset=1)

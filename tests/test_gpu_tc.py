@@ -140,3 +140,60 @@ def test_rsthosvd_bf16x2_first_mode_matches_oracle(rh, shape, ranks, p):
         assert np.linalg.norm(U - Qa @ (Qa.T @ U), 2) <= 1e-3, m
     nx = float(T.norms.cpu().numpy()[0])
     assert abs(nx - np.sum(Xrep ** 2)) <= 1e-10 * np.sum(Xrep ** 2)
+
+
+# ---------------------------------------------------------------------------------
+# RH_F32_BF16X2: an FP32 tensor split into head / tail inside the tensor-core kernels.  The pieces
+# and the order of every product and sum are those of the two-piece form, so the outputs must be
+# bit-identical to running the two-piece form on split_bf16x2(X).
+# ---------------------------------------------------------------------------------
+def _wide_f32(rs, shape):
+    """Normal values with magnitudes spread over 2^-29 .. 2^29 (exercises the head / tail split)."""
+    return (rs.standard_normal(shape) * np.exp(rs.uniform(-20, 20, shape))).astype(np.float32)
+
+
+@pytest.mark.parametrize("shape", [(128, 300, 7), (200, 40, 40), (1024, 64, 33), (96, 1000), (8, 5000),
+                                   (136, 77, 3)])
+@pytest.mark.parametrize("ell", [1, 25, 64])
+def test_f32_split_sketch_is_bit_identical_to_pieces(rh, shape, ell):
+    rs = np.random.default_rng(hash((shape, ell, "f32")) % 2 ** 32)
+    X = _wide_f32(rs, shape) if ell == 25 else rs.standard_normal(shape).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    Xb = rh.split_bf16x2(Xd)
+    Yp = rh.rhosvd_sketch_bf16(Xb, list(shape), ell, seed=9, tensor_id=4, pieces=2)
+    Yf, nrm = rh.rhosvd_sketch_bf16(Xd, list(shape), ell, seed=9, tensor_id=4, pieces="f32", with_norm=True)
+    assert torch.equal(Yp, Yf)
+    bits = Xb.cpu().numpy().view(np.uint16)
+    rep = bf16_bits_to_f64(bits[:X.size]) + bf16_bits_to_f64(bits[X.size:])
+    ref = float(np.sum(rep ** 2))
+    # FP32 sums of 32 squares per thread and tile (positive terms), FP64 above
+    assert abs(float(nrm.item()) - ref) <= 66 * 2.0 ** -24 * ref
+
+
+@pytest.mark.parametrize("shape,k", [((128, 300), 60), ((64, 129), 1), ((200, 7, 9), 25), ((1024, 300), 64),
+                                     ((136, 77, 3), 17)])
+def test_f32_split_mode_product_is_bit_identical_to_pieces(rh, shape, k):
+    rs = np.random.default_rng(6)
+    X = _wide_f32(rs, shape) if k == 25 else rs.standard_normal(shape).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    A = torch.from_numpy(rs.standard_normal((k, shape[0]))).cuda()
+    Yp = rh.mode_product_bf16(rh.split_bf16x2(Xd), list(shape), A, pieces=2)
+    Yf = rh.mode_product_bf16(Xd, list(shape), A, pieces="f32")
+    assert torch.equal(Yp, Yf)
+
+
+@pytest.mark.parametrize("shape,ranks,p", [((128, 60, 50), (6, 5, 4), 5), ((136, 45, 31), (5, 5, 5), 4),
+                                           ((1024, 40, 30), (8, 6, 5), 4)])
+def test_rsthosvd_f32_split_is_bit_identical_to_pieces(rh, shape, ranks, p):
+    from workloads import lowrank_plus_noise_np
+
+    X = lowrank_plus_noise_np(list(shape), [max(ranks) + 2] * 3, 0.8, 1e-3, seed=22).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    Tp = rh.rsthosvd(rh.split_bf16x2(Xd), list(shape), list(ranks), p=p, seed=3, rho=[0, 1, 2], form="bf16x2")
+    Tp = [t.clone() for t in Tp.factors] + [Tp.core.clone(), Tp.norms.clone()]
+    Tf = rh.rsthosvd(Xd, list(shape), list(ranks), p=p, seed=3, rho=[0, 1, 2], form="f32_bf16x2")
+    for a, b in zip(Tp[:3], Tf.factors):
+        assert torch.equal(a, b)
+    assert torch.equal(Tp[3], Tf.core)
+    assert Tp[4][1].item() == Tf.norms[1].item()
+    assert abs(Tp[4][0].item() - Tf.norms[0].item()) <= 66 * 2.0 ** -24 * Tp[4][0].item()
