@@ -11,7 +11,12 @@ weak scaling, no data-path collective).  Algorithmic flops per mode with current
 size N_c, M = N_c / I_n and ell = r + p: sketch 2 N_c ell + mode product 2 N_c ell +
 tall-skinny QR of B^T 4 M ell^2 + truncated-core product 2 M ell r.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Forms (--form): ``f32_bf16x2`` (default) reads the FP32 tensor once per first-mode kernel on the
+tensor cores, splitting every tile into its exact BF16 head and tail in shared memory (16
+significant bits of X, Omega rounded to BF16, FP32 accumulation; later modes FP32); ``f32`` is
+the FP32 form on the CUDA cores throughout.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--form F]
 """
 
 import argparse
@@ -212,7 +217,9 @@ def run_ours(args):
 
     L = _lib.lib()
     X = make_input(torch, device, seed_offset=rank)
-    call = rh.RsthosvdCall(DIMS, torch.float32, RANKS, p=P, seed=SEED, rho=RHO, device=device)
+    tc = args.form == "f32_bf16x2"
+    form = "f32_bf16x2" if tc else torch.float32
+    call = rh.RsthosvdCall(DIMS, form, RANKS, p=P, seed=SEED, rho=RHO, device=device)
     for _ in range(args.warmup):
         call.run(X)
     torch.cuda.synchronize()
@@ -261,24 +268,34 @@ def run_ours(args):
     dom_ms = sum(per[dom]) / len(per[dom])
     N = float(np.prod(DIMS))
     ell = RANKS[0] + P
+    # algorithmic bytes of one launch: X read once (+ B = Q^T X_(1) written by the mode product)
     dom_bytes = N * 4 + (N / DIMS[0]) * ell * 4 * (dom[0] == 1)
     dom_flops = 2.0 * N * ell
     peaks, src = measured_peaks()
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # FFMA lanes x 2 flops x clock
-    hbm_frac = dom_bytes / (dom_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
-    roofline = {"kernel": "sketch_kernel<float>" if dom[0] == 0 else "ttm_kernel<float>", "bound": "alu",
-                "achieved": round(dom_flops / (dom_ms * 1e-3) / 1e12, 3),
-                "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(dom_flops / (dom_ms * 1e-3) / 1e12 / fp32_peak, 4),
-                "traffic": traffic_for(dom[0]),
-                "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled SM clock)",
-                "hbm_frac_of_" + src: round(hbm_frac, 4), "avg_launch_ms": round(dom_ms, 4)}
+    hbm_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9
+    if tc:
+        kname = "sketch_tc_kernel<FP32 in>" if dom[0] == 0 else "ttm_tc_kernel<FP32 in>"
+        roofline = {"kernel": kname, "bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(hbm_gbs / peaks["hbm_gbs"], 4),
+                    "traffic": traffic_for(dom[0], tc=True),
+                    "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+                    else "fallback 6.8 TB/s", "algorithmic_bytes": dom_bytes, "avg_launch_ms": round(dom_ms, 4)}
+    else:
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # FFMA lanes x 2 flops x clock
+        roofline = {"kernel": "sketch_kernel<float>" if dom[0] == 0 else "ttm_kernel<float>", "bound": "alu",
+                    "achieved": round(dom_flops / (dom_ms * 1e-3) / 1e12, 3),
+                    "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                    "frac": round(dom_flops / (dom_ms * 1e-3) / 1e12 / fp32_peak, 4),
+                    "traffic": traffic_for(dom[0]),
+                    "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled "
+                                   "SM clock)",
+                    "hbm_frac_of_" + src: round(hbm_gbs / peaks["hbm_gbs"], 4), "avg_launch_ms": round(dom_ms, 4)}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
-        hc = rh.RsthosvdHostCall(DIMS, torch.float32, RANKS, p=P, seed=SEED, rho=RHO, device=device)
+        hc = rh.RsthosvdHostCall(DIMS, form, RANKS, p=P, seed=SEED, rho=RHO, device=device)
         Xh = X.cpu().pin_memory()
         hc.run(Xh)
         torch.cuda.synchronize()
@@ -305,6 +322,10 @@ def run_ours(args):
     extra = {}
     if rank == 0 and not args.no_fp64:
         extra = fp64_comparison(torch, rh, X, T, device)
+        ref = extra.get("fp64_gpu", {})
+        if "ms_per_step" in ref:
+            ref["speedup_of_ours"] = round(ref["ms_per_step"] / ms_step, 2)
+            ref["error_ratio_ours_over_fp64"] = round(extra["rel_error"] / ref["rel_error"], 6)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -313,7 +334,11 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "time_to_tucker_ms": round(ms_step, 4),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16x2" if tc else "f32",
+                "form": ("FP32 X split on the fly into exact BF16 head + tail (16 significant bits) for the "
+                         "first mode's tensor-core sketch and mode product, Omega in BF16, FP32 accumulation; "
+                         "later modes FP32 on the CUDA cores") if tc else "FP32 on the CUDA cores",
                 "data": "synthetic (seeded generator, inputs resident in HBM before timing)",
                 "config": {"workload": WORKLOAD, "dims": DIMS, "ranks": RANKS, "p": P, "seed": SEED,
                            "order": [n + 1 for n in RHO], "parallelism": f"independent tensor per GPU x{world}",
@@ -327,16 +352,20 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def traffic_for(kind):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+def traffic_for(kind, tc=False):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source
+    (the kernel's .cu file, and for the tensor-core kernels also the shared tc.cuh)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     import hashlib
 
-    want = {0: "sketch", 1: "ttm"}[kind]
-    src = os.path.join(ROOT, "paper_1905_07311_gb300", "csrc", f"{want}.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    want = {0: "sketch", 1: "ttm"}[kind] + ("_tc" if tc else "")
+    csrc = os.path.join(ROOT, "paper_1905_07311_gb300", "csrc")
+    blob = open(os.path.join(csrc, f"{want}.cu"), "rb").read()
+    if tc:
+        blob += open(os.path.join(csrc, "tc.cuh"), "rb").read()
+    h = hashlib.sha256(blob).hexdigest()[:16]
     with open(path) as f:
         for line in f:
             t = line.split()
@@ -420,6 +449,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-slab", type=int, default=None,
                     help="mode-3 extent of the CPU sample (default 384 for the baseline, 128 per reference step)")
+    ap.add_argument("--form", default="f32_bf16x2", choices=["f32_bf16x2", "f32"],
+                    help="f32_bf16x2: first mode on the tensor cores over the on-the-fly BF16 split of X "
+                         "(default); f32: CUDA-core FP32 throughout")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -71,8 +71,9 @@ rh_status launch_core_ttm(int d, const int64_t* dims, const T* X, const double* 
 
 // ---- small dense linear algebra (smallla.cu) --------------------------------------------
 size_t orth_workspace_elems(int64_t m, int n);   // doubles
+// df: run the two Cholesky factorizations of CholeskyQR2 in double-float (FP32 paths)
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
-                                cudaStream_t st);
+                                cudaStream_t st, bool df = false);
 
 // Truncation of B (mode-n unfolding of a L x ell x R tensor, entries of type T):
 // TSQR of B_(n)^T, one-sided Jacobi SVD of the ell x ell triangle -> U_B (ell x ell, FP64,

@@ -282,7 +282,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     // Alg. 1 step 2: Q = orth(Y)
     {
       ProfileScope ps(PROF_ORTH, j, st);
-      if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st)) !=
+      if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st,
+                                    sizeof(T) == 4)) !=
           RH_OK)
         return s;
     }
@@ -369,7 +370,8 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
       return s;
     {
       ProfileScope ps(PROF_ORTH, (int)j, st);
-      if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st)) !=
+      if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st,
+                                    sizeof(T) == 4)) !=
           RH_OK)
         return s;
     }

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace rh {
@@ -88,45 +89,66 @@ __global__ void gram_reduce_kernel(const double* __restrict__ Gpart, int nb, int
   C[e] = s;
 }
 
-// Cholesky C = R^T R (R upper) in one CTA of 256 threads; also writes rdiag = 1 / diag(R).
+// Cholesky C = R^T R (R upper) in one CTA of 1024 threads; also writes rdiag = 1 / diag(R).
 // flag <- 1 on a pivot <= 1e-14 C_kk (or not finite): CholeskyQR2 is then not accurate enough
-// and the Householder branch takes over.  Trailing update: thread t owns column j = t % 64
-// and rows i = t / 64, t / 64 + 4, ... (no index division in the loop).
-__global__ void __launch_bounds__(256) cholesky_kernel(const double* __restrict__ C, int n, double* __restrict__ R,
-                                                       double* __restrict__ rdiag, int32_t* __restrict__ flag) {
+// and the Householder branch takes over.
+// Right-looking on the unscaled Schur complement S (S_kj = R_kk R_kj after step k - 1):
+// S_ij -= S_ki S_kj / S_kk for k < i <= j, one barrier per step.  1 / sqrt(S_kk) of the next
+// step is computed by the thread that finishes S_{k+1,k+1}, which overlaps the rest of the
+// update.  Thread t owns column j = t % 64 and rows i = k + 1 + t / 64 + 16 q (q < 4); a thread
+// reads all its operands before it writes, so the FP64 updates of a step are independent.
+// R_kj = S_kj / sqrt(S_kk) is formed at the end.
+__global__ void __launch_bounds__(1024) cholesky_kernel(const double* __restrict__ C, int n, double* __restrict__ R,
+                                                        double* __restrict__ rdiag, int32_t* __restrict__ flag) {
   if (*flag) return;
   extern __shared__ double S[];  // n x n column-major working copy (upper part used)
+  __shared__ double rinv[RH_MAX_ELL];
+  __shared__ double cdiag[RH_MAX_ELL];   // diag(C): the pivot test must not wait on global memory
   __shared__ int bad;
-  __shared__ double rk_inv;
   const int t = threadIdx.x;
-  if (t == 0) bad = 0;
+  const int ld = n | 1;   // odd leading dimension: 8-byte accesses along a row hit distinct banks
   for (int e = t; e < n * n; e += blockDim.x) {
     const int j = e % n, k = e / n;
-    S[e] = (j <= k) ? C[e] : 0.0;
+    S[j + ld * k] = (j <= k) ? C[e] : 0.0;
+  }
+  for (int k = t; k < n; k += blockDim.x) cdiag[k] = C[k + n * k];
+  if (t == 0) {
+    bad = 0;
+    const double d = C[0];
+    if (!(d > 0.0) || !isfinite(d))
+      bad = 1;
+    else
+      rinv[0] = rsqrt(d);
   }
   __syncthreads();
   const int jc = t & 63, i0 = t >> 6;
-  for (int k = 0; k < n; ++k) {
-    if (t == 0) {
-      const double d = S[k + n * k];
-      if (!(d > 1e-14 * C[k + n * k]) || !isfinite(d)) {
-        bad = 1;
-      } else {
-        const double rkk = sqrt(d);
-        S[k + n * k] = rkk;
-        rk_inv = 1.0 / rkk;
-        rdiag[k] = rk_inv;
-      }
-    }
-    __syncthreads();
+  for (int k = 0; k < n - 1; ++k) {
     if (bad) break;  // uniform: read after the barrier
-    // row k of R: R[k, j] = S[k, j] / R[k, k] for j > k
-    if (jc > k && jc < n && i0 == 0) S[k + n * jc] *= rk_inv;
-    __syncthreads();
-    // trailing update S[i, j] -= R[k, i] R[k, j] for k < i <= j
     if (jc > k && jc < n) {
-      const double rkj = S[k + n * jc];
-      for (int i = k + 1 + i0; i <= jc; i += 4) S[i + n * jc] -= S[k + n * i] * rkj;
+      const double ri = rinv[k];
+      const double skj = S[k + ld * jc] * (ri * ri);
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = k + 1 + i0 + 16 * q;
+        a[q] = i <= jc ? S[k + ld * i] : 0.0;
+        b[q] = i <= jc ? S[i + ld * jc] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = k + 1 + i0 + 16 * q;
+        if (i <= jc) {
+          const double v = fma(-a[q], skj, b[q]);
+          S[i + ld * jc] = v;
+          if (i == k + 1 && jc == k + 1) {
+            // the next pivot is final: check it and prepare its reciprocal square root
+            if (!(v > 1e-14 * cdiag[k + 1]) || !isfinite(v))
+              bad = 1;
+            else
+              rinv[k + 1] = rsqrt(v);
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -136,8 +158,96 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const double* __restrict_
   }
   for (int e = t; e < n * n; e += blockDim.x) {
     const int j = e % n, k = e / n;
-    R[e] = (j <= k) ? S[e] : 0.0;
+    R[e] = (j <= k) ? S[j + ld * k] * rinv[j] : 0.0;
   }
+  for (int k = t; k < n; k += blockDim.x) rdiag[k] = rinv[k];
+}
+
+// The same factorization in double-float (about 48 bits) for the FP32 paths: C is scaled by a
+// power of two (largest diagonal in [1/4, 4)) so that FP32's exponent range suffices, the Schur
+// updates and 1 / sqrt(S_kk) run on the FP32 pipes, and R, rdiag are scaled back exactly.
+// Same outputs, layout, pivot test and flag as cholesky_kernel.
+__global__ void __launch_bounds__(1024) cholesky_df_kernel(const double* __restrict__ C, int n,
+                                                           double* __restrict__ R, double* __restrict__ rdiag,
+                                                           int32_t* __restrict__ flag) {
+  if (*flag) return;
+  using dfl::F2;
+  extern __shared__ __align__(16) unsigned char chol_raw[];
+  F2* S = reinterpret_cast<F2*>(chol_raw);   // n x n, upper part used
+  __shared__ F2 rinv[RH_MAX_ELL];
+  __shared__ float cdiag[RH_MAX_ELL];
+  __shared__ double scale_s;
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  if (t < 32) {
+    double m = 0.0;
+    for (int k = t; k < n; k += 32) m = fmax(m, C[k + n * k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (t == 0) {
+      int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+      e &= ~1;   // even, so that sqrt of the scale is a power of two too
+      scale_s = ldexp(1.0, -e);
+    }
+  }
+  __syncthreads();
+  const double sc = scale_s;
+  const int ld = n | 1;   // odd leading dimension: conflict-free 8-byte accesses along a row
+  for (int e = t; e < n * n; e += blockDim.x) {
+    const int j = e % n, k = e / n;
+    S[j + ld * k] = (j <= k) ? dfl::from_double(C[e] * sc) : F2{0.0f, 0.0f};
+  }
+  for (int k = t; k < n; k += blockDim.x) cdiag[k] = (float)(C[k + n * k] * sc);
+  __syncthreads();
+  if (t == 0) {
+    bad = 0;
+    const F2 d = S[0];
+    if (!(d.hi > 0.0f) || !isfinite(d.hi))
+      bad = 1;
+    else
+      rinv[0] = dfl::rsqrt(d);
+  }
+  __syncthreads();
+  const int jc = t & 63, i0 = t >> 6;
+  for (int k = 0; k < n - 1; ++k) {
+    if (bad) break;  // uniform: read after the barrier
+    if (jc > k && jc < n) {
+      const F2 ri = rinv[k];
+      const F2 skj = dfl::mul(S[k + ld * jc], dfl::mul(ri, ri));
+      F2 a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = k + 1 + i0 + 16 * q;
+        a[q] = i <= jc ? S[k + ld * i] : F2{0.0f, 0.0f};
+        b[q] = i <= jc ? S[i + ld * jc] : F2{0.0f, 0.0f};
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = k + 1 + i0 + 16 * q;
+        if (i <= jc) {
+          const F2 v = dfl::fms(b[q], a[q], skj);
+          S[i + ld * jc] = v;
+          if (i == k + 1 && jc == k + 1) {
+            if (!(v.hi > 1e-14f * cdiag[k + 1]) || !isfinite(v.hi))
+              bad = 1;
+            else
+              rinv[k + 1] = dfl::rsqrt(v);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (t == 0) *flag = 1;
+    return;
+  }
+  const double rs = sqrt(sc);   // exact: sc is an even power of two
+  for (int e = t; e < n * n; e += blockDim.x) {
+    const int j = e % n, k = e / n;
+    R[e] = (j <= k) ? dfl::to_double(dfl::mul(S[j + ld * k], rinv[j])) / rs : 0.0;
+  }
+  for (int k = t; k < n; k += blockDim.x) rdiag[k] = dfl::to_double(rinv[k]) * rs;
 }
 
 // Out = A R^{-1} row by row (forward substitution on x^T R = a^T); one warp per row, the
@@ -146,9 +256,10 @@ __global__ void trsm_rows_kernel(const double* __restrict__ A, int64_t m, int n,
                                  const double* __restrict__ rdiag, double* __restrict__ Out,
                                  const int32_t* __restrict__ flag) {
   if (*flag) return;
-  extern __shared__ double Rs[];  // n x n column-major, then n reciprocals
-  double* rd = Rs + n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[e] = R[e];
+  extern __shared__ double Rs[];  // n x n column-major (odd leading dimension ld), then n reciprocals
+  const int ld = n | 1;           // lanes read a row of R: an odd stride keeps the banks distinct
+  double* rd = Rs + ld * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[(e % n) + ld * (e / n)] = R[e];
   for (int e = threadIdx.x; e < n; e += blockDim.x) rd[e] = rdiag[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -161,8 +272,8 @@ __global__ void trsm_rows_kernel(const double* __restrict__ A, int64_t m, int n,
       if (lane == (c & 31)) {
         if (c < 32) y0 = xc; else y1 = xc;
       }
-      if (lane > c && lane < n) y0 -= xc * Rs[c + n * lane];
-      if (lane + 32 > c && lane + 32 < n) y1 -= xc * Rs[c + n * (lane + 32)];
+      if (lane > c && lane < n) y0 -= xc * Rs[c + ld * lane];
+      if (lane + 32 > c && lane + 32 < n) y1 -= xc * Rs[c + ld * (lane + 32)];
     }
     if (lane < n) Out[row + m * lane] = y0;
     if (lane + 32 < n) Out[row + m * (lane + 32)] = y1;
@@ -712,6 +823,255 @@ __global__ void __launch_bounds__(256) gram_b_reduce_kernel(const double* __rest
   }
 }
 
+// Diagonally pivoted Cholesky of the Gram matrix W (n x n, FP64 in, n <= 64) in one CTA, in
+// double-float after scaling W by a power of two: W = sum_k r_k r_k^T with r_k the k-th pivot
+// row of R in the original indexing.  Writes X(:, k) = r_k (FP32, n x n column-major), so
+// X X^T = W and the left singular vectors of X are the eigenvectors of W; choosing the largest
+// remaining diagonal at every step makes the columns of X graded and nearly orthogonal, which is
+// what makes one-sided Jacobi on X converge in few sweeps.  flag[0] <- 1 when the largest
+// remaining pivot is <= 1e-14 max diag(W) (numerically singular W) or not finite.  S keeps the
+// upper triangle (i <= j) of the Schur complement.
+__global__ void __launch_bounds__(1024) pivoted_cholesky_kernel(const double* __restrict__ W, int n,
+                                                                float* __restrict__ X,
+                                                                int32_t* __restrict__ flag) {
+  if (flag[0]) return;
+  using dfl::F2;
+  extern __shared__ __align__(16) unsigned char chol_raw[];
+  F2* S = reinterpret_cast<F2*>(chol_raw);
+  __shared__ int done[RH_MAX_ELL];
+  __shared__ int piv, bad;
+  __shared__ F2 rinv_s;
+  __shared__ double scale_s;
+  __shared__ float dmax_s;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (w == 0) {
+    double m = 0.0;
+    for (int i = lane; i < n; i += 32) m = fmax(m, W[i + n * i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+      e &= ~1;
+      scale_s = ldexp(1.0, -e);
+      dmax_s = (float)(m * ldexp(1.0, -e));   // in [1, 4)
+      bad = (m > 0.0 && isfinite(m)) ? 0 : 1;
+    }
+  }
+  __syncthreads();
+  const double sc = scale_s;
+  const int ld = n | 1;   // odd leading dimension: conflict-free 8-byte accesses along a row
+  for (int e = t; e < n * n; e += blockDim.x) S[(e % n) + ld * (e / n)] = dfl::from_double(W[e] * sc);
+  for (int e = t; e < n * n; e += blockDim.x) X[e] = 0.0f;
+  for (int i = t; i < RH_MAX_ELL; i += blockDim.x) done[i] = 0;
+  __syncthreads();
+  const float dmax = dmax_s;
+  const double unscale = 1.0 / sqrt(sc);
+  const int jc = t & 63, i0 = t >> 6;
+  for (int k = 0; k < n; ++k) {
+    if (bad) break;
+    if (w == 0) {
+      // argmax of the remaining diagonal (first index on ties), on the leading parts
+      float bv = -1.0f;
+      int bi = n;
+      for (int i = lane; i < n; i += 32) {
+        const float d = done[i] ? -1.0f : S[i + ld * i].hi;
+        if (d > bv) {
+          bv = d;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        if (!(bv > 1e-14f * dmax) || !isfinite(bv)) {
+          bad = 1;
+        } else {
+          piv = bi;
+          rinv_s = dfl::rsqrt(S[bi + ld * bi]);
+          done[bi] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (bad) break;  // uniform: read after the barrier
+    const int p = piv;
+    const F2 ri = rinv_s;
+    // column k of X: r_k(j) = S(p, j) / sqrt(S(p, p)) for the remaining j (and j = p)
+    for (int j = t; j < n; j += blockDim.x) {
+      const int a = p < j ? p : j, b = p < j ? j : p;
+      if (j == p || !done[j]) X[j + n * k] = (float)(dfl::to_double(dfl::mul(S[a + ld * b], ri)) * unscale);
+    }
+    // Schur update of the remaining upper triangle: S(i, j) -= S(p, i) S(p, j) / S(p, p).  Entries
+    // in row / column p (done now) are only read, the others only by their owner: no hazard.
+    if (jc < n && !done[jc]) {
+      const F2 spj = dfl::mul(S[(p < jc ? p : jc) + ld * (p < jc ? jc : p)], dfl::mul(ri, ri));
+      F2 a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + 16 * q;
+        const bool live = i <= jc && !done[i];
+        a[q] = live ? S[(p < i ? p : i) + ld * (p < i ? i : p)] : F2{0.0f, 0.0f};
+        b[q] = live ? S[i + ld * jc] : F2{0.0f, 0.0f};
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + 16 * q;
+        if (i <= jc && !done[i]) S[i + ld * jc] = dfl::fms(b[q], a[q], spj);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad && t == 0) flag[0] = 1;
+}
+
+// One-sided Jacobi on the columns of X (n x n, FP32, n <= 64) without accumulating the rotations:
+// at convergence X = U S, so U is read off by normalising the columns.  Same circle schedule and
+// rotation rule as jacobi_svd_kernel, but a warp rotates four pairs at once (eight lanes per pair,
+// each lane holding entries 4l..4l+3 and 32+4l..32+4l+3 of both columns as two 16-byte vectors).
+// Afterwards the columns are normalised, sorted by decreasing norm and made orthonormal to FP32
+// rounding by one polar correction U <- U (3 I - U^T U) / 2 (the Jacobi tolerance leaves
+// |u_i^T u_j| <= tol).  Writes Ub (n x n, FP64) and sv = the column norms (FP64), sorted.
+constexpr int kRowJacThreads = 256;
+
+__global__ void __launch_bounds__(kRowJacThreads) jacobi_rows_kernel(const float* __restrict__ Xin, int n,
+                                                                       double* __restrict__ Ub,
+                                                                       double* __restrict__ sv,
+                                                                       const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate != 0) return;
+  extern __shared__ __align__(16) float jsm[];
+  const int np = (n + 1) & ~1;
+  const int half = np / 2;
+  float* buf0 = jsm;                    // [position][64]
+  float* buf1 = buf0 + 64 * 64;
+  float* U = buf1 + 64 * 64;            // [64][65]: U(i, c) at i + 65 c
+  float* E = U + 64 * 65;               // [64][65]
+  __shared__ float nrm2[2][RH_MAX_ELL];
+  __shared__ float sig[RH_MAX_ELL];
+  __shared__ int rankof[RH_MAX_ELL];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int e = t; e < 64 * 64; e += blockDim.x) {
+    const int i = e & 63, q = e >> 6;
+    buf0[e] = (q < n && i < n) ? Xin[i + n * q] : 0.0f;
+  }
+  __syncthreads();
+  const float tol = (float)(8 * (n > 8 ? n : 8)) * 5.9604645e-8f;
+  const int grp = lane >> 3, l = lane & 7;
+  const int pr = 4 * w + grp;           // pair index of this lane group
+  const bool active = pr < half;
+  const int qa = pr, qb = np - 1 - pr;
+  const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
+  const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
+  int cur = 0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    {
+      const float* src = cur ? buf1 : buf0;
+      for (int q = w; q < np; q += blockDim.x >> 5) {
+        const float a = src[64 * q + lane], b = src[64 * q + 32 + lane];
+        float v = a * a + b * b;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) nrm2[cur][q] = v;
+      }
+      __syncthreads();
+    }
+    int rotated = 0;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      const float* src = cur ? buf1 : buf0;
+      float* dst = cur ? buf0 : buf1;
+      if (w * 4 < half) {
+        const int qa_ = active ? qa : 0, qb_ = active ? qb : 0;
+        float4 a0 = *reinterpret_cast<const float4*>(src + 64 * qa_ + 4 * l);
+        float4 a1 = *reinterpret_cast<const float4*>(src + 64 * qa_ + 32 + 4 * l);
+        float4 b0 = *reinterpret_cast<const float4*>(src + 64 * qb_ + 4 * l);
+        float4 b1 = *reinterpret_cast<const float4*>(src + 64 * qb_ + 32 + 4 * l);
+        float al = nrm2[cur][qa_], be = nrm2[cur][qb_];
+        float g = a0.x * b0.x + a0.y * b0.y + a0.z * b0.z + a0.w * b0.w + a1.x * b1.x + a1.y * b1.y + a1.z * b1.z +
+                  a1.w * b1.w;
+        g += __shfl_xor_sync(0xffffffffu, g, 1);
+        g += __shfl_xor_sync(0xffffffffu, g, 2);
+        g += __shfl_xor_sync(0xffffffffu, g, 4);
+        if (active && g != 0.0f && fabsf(g) * rsqrtf(al) * rsqrtf(be) > tol) {
+          const float zeta = (be - al) / (2.0f * g);
+          const float az = fabsf(zeta);
+          const float tm = az < 1e18f ? 1.0f / (az + sqrtf(fmaf(az, az, 1.0f))) : 0.5f / az;
+          const float tt = zeta < 0.0f ? -tm : tm;
+          const float c = rsqrtf(fmaf(tt, tt, 1.0f));
+          const float sn = c * tt;
+          float u;
+          u = a0.x; a0.x = c * u - sn * b0.x; b0.x = sn * u + c * b0.x;
+          u = a0.y; a0.y = c * u - sn * b0.y; b0.y = sn * u + c * b0.y;
+          u = a0.z; a0.z = c * u - sn * b0.z; b0.z = sn * u + c * b0.z;
+          u = a0.w; a0.w = c * u - sn * b0.w; b0.w = sn * u + c * b0.w;
+          u = a1.x; a1.x = c * u - sn * b1.x; b1.x = sn * u + c * b1.x;
+          u = a1.y; a1.y = c * u - sn * b1.y; b1.y = sn * u + c * b1.y;
+          u = a1.z; a1.z = c * u - sn * b1.z; b1.z = sn * u + c * b1.z;
+          u = a1.w; a1.w = c * u - sn * b1.w; b1.w = sn * u + c * b1.w;
+          al = al - tt * g;
+          be = be + tt * g;
+          rotated = 1;
+        }
+        if (active) {
+          *reinterpret_cast<float4*>(dst + 64 * na + 4 * l) = a0;
+          *reinterpret_cast<float4*>(dst + 64 * na + 32 + 4 * l) = a1;
+          *reinterpret_cast<float4*>(dst + 64 * nb + 4 * l) = b0;
+          *reinterpret_cast<float4*>(dst + 64 * nb + 32 + 4 * l) = b1;
+          if (l == 0) {
+            nrm2[cur ^ 1][na] = al;
+            nrm2[cur ^ 1][nb] = be;
+          }
+        }
+      }
+      cur ^= 1;
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) break;
+  }
+  // every sweep ends with player q at position q: columns are X's columns, rotated
+  const float* fin = cur ? buf1 : buf0;
+  for (int q = w; q < n; q += blockDim.x >> 5) {
+    const float a = fin[64 * q + lane], b = fin[64 * q + 32 + lane];
+    float v = a * a + b * b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sig[q] = sqrtf(v);
+  }
+  __syncthreads();
+  for (int q = t; q < n; q += blockDim.x) {
+    int rank = 0;
+    for (int k = 0; k < n; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && k < q);
+    rankof[q] = rank;
+    sv[rank] = (double)sig[q];
+  }
+  __syncthreads();
+  for (int e = t; e < n * n; e += blockDim.x) {
+    const int i = e % n, q = e / n;
+    const float s = sig[q];
+    U[i + 65 * rankof[q]] = s > 0.0f ? fin[64 * q + i] / s : (i == q ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  // polar correction: E = U^T U, U <- 1.5 U - 0.5 U E
+  for (int e = t; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    float acc = 0.0f;
+    for (int k = 0; k < n; ++k) acc = fmaf(U[k + 65 * i], U[k + 65 * j], acc);
+    E[i + 65 * j] = acc;
+  }
+  __syncthreads();
+  for (int e = t; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    float acc = 0.0f;
+    for (int k = 0; k < n; ++k) acc = fmaf(U[i + 65 * k], E[k + 65 * j], acc);
+    Ub[i + n * j] = (double)(1.5f * U[i + 65 * j] - 0.5f * acc);
+  }
+}
+
 // After the Gram route: fall back to the tall-skinny QR when the Cholesky factor broke down or
 // when the truncation gap sigma_r^2 - sigma_{r+1}^2 is below 1e-5 sigma_1^2, where the FP32
 // Gram cannot resolve the top-r subspace.
@@ -756,7 +1116,7 @@ size_t orth_workspace_elems(int64_t m, int n) {
 }
 
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool df) {
   const int rb = gram_rows(m);
   const int nb = (int)ceil_div(m, rb);
   double* Gpart = ws;
@@ -770,8 +1130,8 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
   RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
   RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
   const size_t gsm = sizeof(double) * rb * n;
-  const size_t nsm = sizeof(double) * n * n;
-  const size_t tsm = sizeof(double) * (n * n + n);
+  const size_t nsm = sizeof(double) * (n | 1) * n;
+  const size_t tsm = sizeof(double) * ((n | 1) * n + n);
   const int rblocks = (int)ceil_div((int64_t)n * n, 256);
   const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
   const double* src = Y;
@@ -781,7 +1141,10 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
     RH_LAUNCH_CHECK();
     gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
     RH_LAUNCH_CHECK();
-    cholesky_kernel<<<1, 256, nsm, st>>>(C, n, R, rdiag, flag);
+    if (df)
+      cholesky_df_kernel<<<1, 1024, nsm, st>>>(C, n, R, rdiag, flag);
+    else
+      cholesky_kernel<<<1, 1024, nsm, st>>>(C, n, R, rdiag, flag);
     RH_LAUNCH_CHECK();
     trsm_rows_kernel<<<tblocks, 256, tsm, st>>>(src, m, n, R, rdiag, dst, flag);
     RH_LAUNCH_CHECK();
@@ -872,13 +1235,13 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     RH_LAUNCH_CHECK();
     gram_b_reduce_kernel<<<(int)ceil_div(nn, 32), 256, 0, st>>>(part, ctas, n, W, nullptr);
     RH_LAUNCH_CHECK();
-    cholesky_kernel<<<1, 256, sizeof(double) * nn, st>>>(W, n, Rd, rdiag, flags);
-    RH_LAUNCH_CHECK();
-    cast_gated_kernel<float><<<(int)ceil_div(nn, 256), 256, 0, st>>>(Rd, Rf, nn, flags);
+    pivoted_cholesky_kernel<<<1, 1024, sizeof(float) * 2 * (n | 1) * n, st>>>(W, n, Rf, flags);
     RH_LAUNCH_CHECK();
     {
       ProfileScope ps(PROF_JACOBI, 0, st);
-      jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(reinterpret_cast<const T*>(Rf), n, Ub, sv, flags, 0);
+      const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
+      RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+      jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Rf, n, Ub, sv, flags);
       RH_LAUNCH_CHECK();
     }
     trunc_decide_kernel<<<1, 32, 0, st>>>(flags, sv, n, r, use_tsqr, info);

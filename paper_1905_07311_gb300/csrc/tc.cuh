@@ -149,20 +149,31 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // rows, 128-byte swizzle) into its BF16 head and tail, written as 128 rows of 64 values (128-byte
 // rows, 128-byte swizzle): box b, row r holds the values 32 (b & 1) .. 32 (b & 1) + 31 of output
 // row (b >> 1) kRowsPerBox + r.  Eight consecutive threads read one 128-byte FP32 row (4 values
-// each).  Returns the FP32 sum of (head + tail)^2 over the values this thread handled.
+// each); the four rows of a warp are boxes b, b ^ 1 of two consecutive rows, so its 8-byte stores
+// fill whole 128-byte output rows (no bank conflicts).  Returns the FP32 sum of (head + tail)^2
+// over the values this thread handled.
 template <int kRowsPerBox, int kThreadsConv>
-__device__ __forceinline__ float convert_tile(const uint8_t* f32, uint8_t* hi, uint8_t* lo, int t) {
-  float ss = 0.0f;
-#pragma unroll 4
-  for (int j = 0; j < 2048 / kThreadsConv; ++j) {
+__device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
+                                              uint8_t* __restrict__ lo, int t) {
+  constexpr int kUnits = 2048 / kThreadsConv;
+  float4 v[kUnits];
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {   // all loads first: kUnits independent 16-byte reads in flight
     const int u = j * kThreadsConv + t;
-    const int k = u & 7, br = u >> 3;
-    const int b = br / kRowsPerBox, r = br % kRowsPerBox;
-    const float4 v = *reinterpret_cast<const float4*>(f32 + b * (kRowsPerBox * 128) + r * 128 + ((k ^ (r & 7)) << 4));
-    const uint32_t h01 = pack_bf16x2(v.x, v.y), h23 = pack_bf16x2(v.z, v.w);
+    const int k = u & 7, g = u >> 3, rest = g >> 1;
+    const int b = 2 * (rest / kRowsPerBox) + (g & 1), r = rest % kRowsPerBox;
+    v[j] = *reinterpret_cast<const float4*>(f32 + b * (kRowsPerBox * 128) + r * 128 + ((k ^ (r & 7)) << 4));
+  }
+  float ss = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {
+    const int u = j * kThreadsConv + t;
+    const int k = u & 7, g = u >> 3, rest = g >> 1;
+    const int b = 2 * (rest / kRowsPerBox) + (g & 1), r = rest % kRowsPerBox;
+    const uint32_t h01 = pack_bf16x2(v[j].x, v[j].y), h23 = pack_bf16x2(v[j].z, v[j].w);
     const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
     const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
-    const uint32_t t01 = pack_bf16x2(v.x - f0, v.y - f1), t23 = pack_bf16x2(v.z - f2, v.w - f3);
+    const uint32_t t01 = pack_bf16x2(v[j].x - f0, v[j].y - f1), t23 = pack_bf16x2(v[j].z - f2, v[j].w - f3);
     const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
     const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
     ss = fmaf(g0, g0, ss);
