@@ -72,7 +72,11 @@ enum {
  *                   each tile into head and tail in shared memory as they load it, so the results
  *                   are bit-identical to RH_BF16X2 of rh_split_bf16x2(X) without the split pass.
  * The BF16 forms use the tensor cores (tcgen05) for the first mode's sketch and mode product, with
- * Omega rounded to BF16 (ties to even) and FP32 accumulation; later modes run in FP32. */
+ * Omega rounded to BF16 (ties to even) and FP32 accumulation; the intermediate cores are FP32.  In
+ * R-STHOSVD (truncating) the core after a mode is written with the next mode fastest when that
+ * mode is the smallest other one, and that mode then runs on the tensor cores too (its FP32 core
+ * split on the fly, Omega in BF16) if I_n % 8 == 0, I_n <= 1024 and r + p <= 64; the other modes
+ * run in FP32 on the CUDA cores.  info bit 4 marks the modes that ran on the tensor cores. */
 enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4 };
 
 /* Options of the fixed-rank algorithms (Alg. 2, Alg. 3). */
@@ -233,7 +237,8 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
  *            (Thm. lem:st_mode_err); the difference is meaningful only above ~1e-6 relative.
  *   info     optional device int32 array of ``order`` values, bit flags per mode n:
  *            1 = the QR of the sketch took the Householder branch; 2 = the truncation
- *            SVD went through the Gram matrix (FP32 data only, see below).
+ *            SVD went through the Gram matrix (FP32 data only, see below); 4 = the sketch and
+ *            mode product of mode n ran on the tensor cores (BF16 forms).
  *   Size rule: ell_n <= min(I_n, prod of the other current sizes), else RH_EINVAL (or
  *   clamped, opts->clamp).  Steps per mode n (in order rho):
  *     sketch Y = G_(n) Omega_n; Q = orth(Y); B = Q^T G_(n) (mode-n product);

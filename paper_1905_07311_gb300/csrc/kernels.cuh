@@ -62,6 +62,13 @@ template <typename T>
 rh_status launch_ttm_residual(const ModeView& v, const T* G, const T* Q, int64_t qsi, int64_t qsc, int ko,
                               const T* Xref, double* part, double* out, cudaStream_t st);
 
+// ---- truncated core of one mode (core_product.cu) ---------------------------------------
+// out[(p % Lp) + Lp (c + ko (p / Lp))] = sum_k U[k + ell c] B[k + ell p], p < M, c < ko
+// (B: ell x M FP32 with c fastest; ell, ko <= 64; M % Lp == 0).
+template <typename TO>
+rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, TO* out,
+                              cudaStream_t st);
+
 // ---- core G = X x_1 A_1^T ... x_d A_d^T (tucker.cu) ----------------------------------------
 // returns the elements of each of the two ping-pong buffers; *fac_elems = sum I_n k_n
 size_t core_chain_elems(int d, const int64_t* dims, const int32_t* ks, size_t* fac_elems);
@@ -71,9 +78,10 @@ rh_status launch_core_ttm(int d, const int64_t* dims, const T* X, const double* 
 
 // ---- small dense linear algebra (smallla.cu) --------------------------------------------
 size_t orth_workspace_elems(int64_t m, int n);   // doubles
-// df: run the two Cholesky factorizations of CholeskyQR2 in double-float (FP32 paths)
+// f32: FP32 data -- the second CholeskyQR pass (on the nearly orthonormal Q_1) in FP32 and the first
+// pass's Cholesky factor in double-float (the Householder branch still takes over on a breakdown)
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
-                                cudaStream_t st, bool df = false);
+                                cudaStream_t st, bool f32 = false);
 
 // Truncation of B (mode-n unfolding of a L x ell x R tensor, entries of type T):
 // TSQR of B_(n)^T, one-sided Jacobi SVD of the ell x ell triangle -> U_B (ell x ell, FP64,

@@ -53,6 +53,8 @@ struct Step {
   int ko;       // output width of the mode: r (truncate) or ell
   SketchPlan sk;
   TruncPlan tr;
+  bool tc = false;      // sketch and mode product on the tensor cores (FP32 core split on the fly)
+  int64_t out_lp = 0;   // core product into out[(p % out_lp) + out_lp (c + ko (p / out_lp))]; 0: mode product
 };
 
 struct Plan {
@@ -129,11 +131,55 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
       set_error("unsupported: the BF16 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024, r + p <= 64");
       return RH_EUNSUPPORTED;
     }
-    pl.tc_part = (size_t)sketch_tc_ctas(s0.v) * s0.ell * s0.v.I;
+    pl.steps[0].tc = true;
     pl.max_pnorm = std::max<size_t>(pl.max_pnorm, 1024);   // partials of the norm over the BF16 pieces
-    pl.qa_elems = (size_t)128 * s0.v.I;
     pl.dtype = RH_F32;        // intermediates
     pl.in_form = dtype;
+    if (o.truncate) {
+      // Later modes: the core product of a step whose B has its new mode fastest (unit-stride
+      // view) writes the next core either in the usual order or, when the next mode m is the
+      // smallest mode other than the one just processed, with m fastest (the Kolda column order
+      // of the next unfolding is kept, so Omega's rows still line up); that mode then has a
+      // unit-stride view as well and runs on the tensor cores when its shape allows.
+      std::vector<int64_t> sz(dims, dims + order);
+      for (int j = 0; j < order; ++j) {
+        Step& sp = pl.steps[j];
+        const int n = sp.mode;
+        sz[n] = sp.ko;   // sizes of the core after this step
+        if (sp.v.L != 1) continue;   // B is (L, ell, R): the mode product writes the usual order
+        if (j == order - 1) {
+          int64_t lp = 1;
+          for (int k = 0; k < n; ++k) lp *= sz[k];
+          sp.out_lp = lp;
+          break;
+        }
+        Step& nx = pl.steps[j + 1];
+        const int m = nx.mode;
+        const int smallest_other = (n == 0) ? 1 : 0;
+        if (m == smallest_other) {
+          int64_t lp = sz[m];
+          for (int k = 0; k < n; ++k)
+            if (k != m) lp *= sz[k];
+          sp.out_lp = lp;
+          nx.v = ModeView{1, nx.v.I, nx.v.L * nx.v.R};
+          nx.sk = plan_sketch(nx.v, nx.ell);
+          nx.tr = plan_trunc(ModeView{1, nx.ell, nx.v.R}, nx.ell);
+          nx.tc = sketch_tc_supported(nx.v, nx.ell) && ttm_tc_supported(nx.v, nx.ell);
+          pl.max_part = std::max(pl.max_part, nx.sk.part_elems());
+          pl.max_pnorm = std::max(pl.max_pnorm, nx.sk.norm_elems());
+          pl.max_trunc = std::max(pl.max_trunc, trunc_workspace_elems<float>(nx.tr));
+        } else {
+          int64_t lp = 1;
+          for (int k = 0; k < n; ++k) lp *= sz[k];
+          sp.out_lp = lp;
+        }
+      }
+    }
+    for (const Step& sp : pl.steps) {
+      if (!sp.tc) continue;
+      pl.tc_part = std::max(pl.tc_part, (size_t)sketch_tc_ctas(sp.v) * sp.ell * sp.v.I);
+      pl.qa_elems = std::max(pl.qa_elems, (size_t)128 * sp.v.I);
+    }
   }
   return RH_OK;
 }
@@ -231,6 +277,15 @@ Bufs carve(Arena& ar, const Plan& pl) {
   return b;
 }
 
+__global__ void info_or_kernel(int32_t* info, int32_t bits) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *info |= bits;
+}
+rh_status set_info_bits(int32_t* info, int32_t bits, cudaStream_t st) {
+  info_or_kernel<<<1, 32, 0, st>>>(info, bits);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
 template <typename T>
 rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, double* const* factors, double* core,
                        double* norms, int32_t* info, const Bufs& b, cudaStream_t st) {
@@ -247,25 +302,29 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
   for (int j = 0; j < nsteps; ++j) {
     const Step& sp = pl.steps[j];
     const bool last = (j == nsteps - 1);
-    const bool tc = tc0 && j == 0;
+    const bool tc = tc0 && sp.tc;
+    const bool first = (j == 0);
     const uint32_t sid = ((uint32_t)o.tensor_id << 4) | (uint32_t)sp.mode;
     // Alg. 1 step 1: Y = G_(n) Omega_n   (+ ||X||^2 on the first pass)
     SketchBufs sb{b.part, b.part_norm};
     double* n2 = (j == 0) ? (norms ? norms : b.normx) : nullptr;
+    // the input itself is split on the fly (FP32 input) or given as pieces; later cores are FP32
+    const bool in_pieces = tc && first && !f32in;
+    const float* tc_src = first ? static_cast<const float*>(Xraw) : reinterpret_cast<const float*>(cur);
     if (tc) {
       {
         ProfileScope ps(PROF_SKETCH, j, st);
-        if (f32in)
-          s = launch_sketch_tc_f32(sp.v, sp.ell, static_cast<const float*>(Xraw), o.seed, sid, b.tc_part,
-                                   norms ? b.part_norm : nullptr, b.err, st);
-        else
+        if (in_pieces)
           s = launch_sketch_tc(sp.v, sp.ell, piece0, piece1, o.seed, sid, b.tc_part, b.err, st);
+        else
+          s = launch_sketch_tc_f32(sp.v, sp.ell, tc_src, o.seed, sid, b.tc_part,
+                                   (first && norms) ? b.part_norm : nullptr, b.err, st);
         if (s != RH_OK) return s;
       }
       SketchPlan rp = sp.sk;
       rp.S = sketch_tc_ctas(sp.v);
       if ((s = launch_sketch_reduce<float>(rp, b.tc_part, nullptr, b.Y, nullptr, st)) != RH_OK) return s;
-      if (norms) {
+      if (first && norms) {
         s = f32in ? launch_sum_n(b.part_norm, rp.S, norms, st)
                   : launch_pieces_sumsq(piece0, piece1, sp.v.I * sp.v.M(), b.part_norm, norms, st);
         if (s != RH_OK) return s;
@@ -298,12 +357,12 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         set_error("unsupported: single-mode untruncated BF16 request");
         return RH_EUNSUPPORTED;
       }
-      if (f32in)
-        s = launch_ttm_tc_f32(sp.v, sp.ell, static_cast<const float*>(Xraw), b.Q, b.qa, reinterpret_cast<float*>(B),
-                              b.err, st);
-      else
+      if (in_pieces)
         s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
+      else
+        s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
       if (s != RH_OK) return s;
+      if (info && (s = set_info_bits(info + sp.mode, 4, st)) != RH_OK) return s;
     } else {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
@@ -324,7 +383,22 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         return s;
       const ModeView vb{sp.v.L, sp.ell, sp.v.R};
       ProfileScope ps(PROF_TTM_CORE, j, st);
-      if (last) {
+      if (sp.out_lp > 0) {
+        // B has the new mode fastest: G <- U_r^T B written in the order the next step reads
+        const float* Bf = reinterpret_cast<const float*>(B);
+        const float* Uf = reinterpret_cast<const float*>(b.Uc);
+        if (last) {
+          if ((s = launch_core_product<double>(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf, core, st)) != RH_OK)
+            return s;
+        } else {
+          const int wg = 1 - wb;
+          if ((s = launch_core_product<float>(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf,
+                                              static_cast<float*>(b.W[wg]), st)) != RH_OK)
+            return s;
+          cur = static_cast<const T*>(b.W[wg]);
+          cur_buf = wg;
+        }
+      } else if (last) {
         if ((s = launch_ttm<T, double>(vb, B, static_cast<const T*>(b.Uc), sp.ko, core, st)) != RH_OK) return s;
       } else {
         const int wg = 1 - wb;

@@ -44,8 +44,8 @@ template <bool F32IN>
 struct SketchCfg {
   static constexpr int kPStages = F32IN ? 2 : 4;
   static constexpr int kF32Stages = F32IN ? 3 : 1;
-  static constexpr int kThreads = F32IN ? 448 : 192;
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
+  static constexpr int kThreads = F32IN ? 192 + kConv : 192;
 };
 
 template <bool F32IN>
@@ -56,7 +56,7 @@ struct alignas(1024) SketchSmem {
   uint64_t f32full[SketchCfg<F32IN>::kF32Stages], f32empty[SketchCfg<F32IN>::kF32Stages];
   uint64_t full[SketchCfg<F32IN>::kPStages], empty[SketchCfg<F32IN>::kPStages], om_full[2], om_empty[2], done;
   uint32_t tmem_slot;
-  double nrm[8];
+  double nrm[16];
 };
 
 // byte offset of element (row, col) of a K-major 128B-swizzled tile whose rows hold 64 BF16
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
     }
   } else if constexpr (F32IN) {
     // ---------------- converters (warps 6..13): FP32 tile -> BF16 head + tail ----------------
-    const int t = threadIdx.x - 192;   // 0..255
+    const int t = threadIdx.x - 192;   // 0..kConv-1
     double acc = 0.0;
     uint32_t it = 0;
     bool ok = true;
@@ -238,10 +238,10 @@ __global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) S.nrm[warp - 6] = acc;
-    asm volatile("bar.sync 2, 256;" ::: "memory");
+    asm volatile("bar.sync 2, %0;" ::"n"(Cfg::kConv) : "memory");
     if (t == 0 && norm_part != nullptr) {
       double sum = 0.0;
-      for (int w = 0; w < 8; ++w) sum += S.nrm[w];
+      for (int w = 0; w < Cfg::kConv / 32; ++w) sum += S.nrm[w];
       norm_part[blockIdx.x] = sum;
     }
   }

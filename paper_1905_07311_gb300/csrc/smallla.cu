@@ -89,151 +89,167 @@ __global__ void gram_reduce_kernel(const double* __restrict__ Gpart, int nb, int
   C[e] = s;
 }
 
-// Cholesky C = R^T R (R upper) in one CTA of 1024 threads; also writes rdiag = 1 / diag(R).
-// flag <- 1 on a pivot <= 1e-14 C_kk (or not finite): CholeskyQR2 is then not accurate enough
-// and the Householder branch takes over.
-// Right-looking on the unscaled Schur complement S (S_kj = R_kk R_kj after step k - 1):
-// S_ij -= S_ki S_kj / S_kk for k < i <= j, one barrier per step.  1 / sqrt(S_kk) of the next
-// step is computed by the thread that finishes S_{k+1,k+1}, which overlaps the rest of the
-// update.  Thread t owns column j = t % 64 and rows i = k + 1 + t / 64 + 16 q (q < 4); a thread
-// reads all its operands before it writes, so the FP64 updates of a step are independent.
-// R_kj = S_kj / sqrt(S_kk) is formed at the end.
-__global__ void __launch_bounds__(1024) cholesky_kernel(const double* __restrict__ C, int n, double* __restrict__ R,
-                                                        double* __restrict__ rdiag, int32_t* __restrict__ flag) {
-  if (*flag) return;
-  extern __shared__ double S[];  // n x n column-major working copy (upper part used)
-  __shared__ double rinv[RH_MAX_ELL];
-  __shared__ double cdiag[RH_MAX_ELL];   // diag(C): the pivot test must not wait on global memory
-  __shared__ int bad;
-  const int t = threadIdx.x;
-  const int ld = n | 1;   // odd leading dimension: 8-byte accesses along a row hit distinct banks
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int j = e % n, k = e / n;
-    S[j + ld * k] = (j <= k) ? C[e] : 0.0;
+// Arithmetic of the small Cholesky factorizations: FP64, or double-float (about 48 bits on the FP32
+// pipes) for the FP32 paths.  Both scale the matrix by a power of two first (exact), so that the
+// pivot test, done on the leading FP32 part, stays in range.
+struct ArithF64 {
+  using V = double;
+  static constexpr bool kScale = true;   // exact in FP64; keeps the FP32 pivot test in range
+  static constexpr float kPivot = 1e-14f;
+  __device__ static V from(double d) { return d; }
+  __device__ static double to(V v) { return v; }
+  __device__ static V zero() { return 0.0; }
+  __device__ static V mul(V a, V b) { return a * b; }
+  __device__ static V fms(V x, V a, V b) { return fma(-a, b, x); }   // x - a b
+  __device__ static V rsq(V x) { return rsqrt(x); }
+  __device__ static float lead(V x) { return (float)x; }
+  __device__ static bool finite(V x) { return isfinite(x); }
+};
+struct ArithF32 {
+  using V = float;
+  static constexpr bool kScale = true;
+  // used on the Gram matrix of a nearly orthonormal Q_1 (pivots ~1): a small pivot means trouble
+  static constexpr float kPivot = 1e-5f;
+  __device__ static V from(double d) { return (float)d; }
+  __device__ static double to(V v) { return (double)v; }
+  __device__ static V zero() { return 0.0f; }
+  __device__ static V mul(V a, V b) { return a * b; }
+  __device__ static V fms(V x, V a, V b) { return fmaf(-a, b, x); }
+  __device__ static V rsq(V x) { return rsqrtf(x); }
+  __device__ static float lead(V x) { return x; }
+  __device__ static bool finite(V x) { return isfinite(x); }
+};
+struct ArithDF {
+  using V = dfl::F2;
+  static constexpr bool kScale = true;
+  static constexpr float kPivot = 1e-14f;
+  __device__ static V from(double d) { return dfl::from_double(d); }
+  __device__ static double to(V v) { return dfl::to_double(v); }
+  __device__ static V zero() { return V{0.0f, 0.0f}; }
+  __device__ static V mul(V a, V b) { return dfl::mul(a, b); }
+  __device__ static V fms(V x, V a, V b) { return dfl::fms(x, a, b); }
+  __device__ static V rsq(V x) { return dfl::rsqrt(x); }
+  __device__ static float lead(V x) { return x.hi; }
+  __device__ static bool finite(V x) { return isfinite(x.hi); }
+};
+
+// Trailing-triangle table: entry (i, j), 1 <= i <= j < n, sits at (n-i-1)(n-i)/2 + (j - i), so the
+// entries with i > k -- the ones updated at step k -- are the first (n-k-1)(n-k)/2.  Packed i << 8 | j.
+__device__ __forceinline__ void build_tri_table(uint16_t* tab, int n) {
+  for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+    const int base = (n - i - 1) * (n - i) / 2;
+    for (int j = i; j < n; ++j) tab[base + j - i] = (uint16_t)((i << 8) | j);
   }
-  for (int k = t; k < n; k += blockDim.x) cdiag[k] = C[k + n * k];
-  if (t == 0) {
-    bad = 0;
-    const double d = C[0];
-    if (!(d > 0.0) || !isfinite(d))
-      bad = 1;
-    else
-      rinv[0] = rsqrt(d);
-  }
-  __syncthreads();
-  const int jc = t & 63, i0 = t >> 6;
-  for (int k = 0; k < n - 1; ++k) {
-    if (bad) break;  // uniform: read after the barrier
-    if (jc > k && jc < n) {
-      const double ri = rinv[k];
-      const double skj = S[k + ld * jc] * (ri * ri);
-      double a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = k + 1 + i0 + 16 * q;
-        a[q] = i <= jc ? S[k + ld * i] : 0.0;
-        b[q] = i <= jc ? S[i + ld * jc] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = k + 1 + i0 + 16 * q;
-        if (i <= jc) {
-          const double v = fma(-a[q], skj, b[q]);
-          S[i + ld * jc] = v;
-          if (i == k + 1 && jc == k + 1) {
-            // the next pivot is final: check it and prepare its reciprocal square root
-            if (!(v > 1e-14 * cdiag[k + 1]) || !isfinite(v))
-              bad = 1;
-            else
-              rinv[k + 1] = rsqrt(v);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    if (t == 0) *flag = 1;
-    return;
-  }
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int j = e % n, k = e / n;
-    R[e] = (j <= k) ? S[j + ld * k] * rinv[j] : 0.0;
-  }
-  for (int k = t; k < n; k += blockDim.x) rdiag[k] = rinv[k];
 }
 
-// The same factorization in double-float (about 48 bits) for the FP32 paths: C is scaled by a
-// power of two (largest diagonal in [1/4, 4)) so that FP32's exponent range suffices, the Schur
-// updates and 1 / sqrt(S_kk) run on the FP32 pipes, and R, rdiag are scaled back exactly.
-// Same outputs, layout, pivot test and flag as cholesky_kernel.
-__global__ void __launch_bounds__(1024) cholesky_df_kernel(const double* __restrict__ C, int n,
-                                                           double* __restrict__ R, double* __restrict__ rdiag,
-                                                           int32_t* __restrict__ flag) {
-  if (*flag) return;
-  using dfl::F2;
-  extern __shared__ __align__(16) unsigned char chol_raw[];
-  F2* S = reinterpret_cast<F2*>(chol_raw);   // n x n, upper part used
-  __shared__ F2 rinv[RH_MAX_ELL];
-  __shared__ float cdiag[RH_MAX_ELL];
-  __shared__ double scale_s;
-  __shared__ int bad;
-  const int t = threadIdx.x;
-  if (t < 32) {
+// Largest diagonal entry of C and the power-of-two scale that brings it into [1, 4).  Warp 0;
+// result in *scale / *dmax.
+template <class Ar>
+__device__ __forceinline__ void diag_scale(const double* C, int n, double* scale, int* half_exp, float* dmax,
+                                           int* ok) {
+  if (threadIdx.x < 32) {
     double m = 0.0;
-    for (int k = t; k < n; k += 32) m = fmax(m, C[k + n * k]);
+    for (int k = threadIdx.x; k < n; k += 32) m = fmax(m, C[k + n * k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (t == 0) {
-      int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
-      e &= ~1;   // even, so that sqrt of the scale is a power of two too
-      scale_s = ldexp(1.0, -e);
+    if (threadIdx.x == 0) {
+      const bool good = m > 0.0 && isfinite(m);
+      int e = good ? ilogb(m) : 0;
+      e &= ~1;   // even, so that the square root of the scale is a power of two too
+      if (!Ar::kScale) e = 0;
+      *scale = ldexp(1.0, -e);
+      *half_exp = e / 2;
+      *dmax = (float)(m * *scale);
+      *ok = good ? 1 : 0;
     }
   }
+}
+
+constexpr int kCholThreads = 512;
+constexpr int kCholPer = 4096 / kCholThreads;   // matrix elements per thread in the load / store passes
+
+size_t chol_smem(int n, size_t velem) {
+  const size_t a = velem * (size_t)(n | 1) * n;
+  return ((a + 15) & ~size_t(15)) + sizeof(uint16_t) * (size_t)n * n / 2 + 16;
+}
+
+// Cholesky C = R^T R (R upper) in one CTA; also writes rdiag = 1 / diag(R).  flag <- 1 on a
+// pivot <= kPivot C_kk (1e-14 in FP64 / double-float, 1e-5 in FP32) or not finite: CholeskyQR2 is then not accurate enough and the Householder
+// branch takes over.  Right-looking on the unscaled Schur complement S (S_kj = R_kk R_kj after step
+// k - 1): S_ij -= S_ki S_kj / S_kk for k < i <= j, one barrier per step.  Thread 0 updates the next
+// pivot S_{k+1,k+1} first and prepares its 1 / sqrt; the other threads share the remaining
+// entries of the trailing triangle through the table (no idle predicated work).
+template <class Ar>
+__global__ void __launch_bounds__(kCholThreads) chol_kernel(const double* __restrict__ C, int n,
+                                                            double* __restrict__ R, double* __restrict__ rdiag,
+                                                            int32_t* __restrict__ flag) {
+  if (*flag) return;
+  using V = typename Ar::V;
+  extern __shared__ __align__(16) unsigned char chol_raw[];
+  const int ld = n | 1;   // odd leading dimension: 8-byte accesses along a row hit distinct banks
+  V* S = reinterpret_cast<V*>(chol_raw);
+  uint16_t* tab = reinterpret_cast<uint16_t*>(chol_raw + ((sizeof(V) * ld * n + 15) & ~size_t(15)));
+  __shared__ V rinv[RH_MAX_ELL];
+  __shared__ float cdiag[RH_MAX_ELL];
+  __shared__ double scale_s;
+  __shared__ float dmax_s;
+  __shared__ int hexp_s, ok_s, bad;
+  const int t = threadIdx.x;
+  diag_scale<Ar>(C, n, &scale_s, &hexp_s, &dmax_s, &ok_s);
+  build_tri_table(tab, n);
   __syncthreads();
   const double sc = scale_s;
-  const int ld = n | 1;   // odd leading dimension: conflict-free 8-byte accesses along a row
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int j = e % n, k = e / n;
-    S[j + ld * k] = (j <= k) ? dfl::from_double(C[e] * sc) : F2{0.0f, 0.0f};
+  {
+    double c[kCholPer];
+#pragma unroll
+    for (int q = 0; q < kCholPer; ++q) {   // all loads first
+      const int e = t + kCholThreads * q;
+      c[q] = (e < n * n && (e % n) <= (e / n)) ? C[e] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCholPer; ++q) {
+      const int e = t + kCholThreads * q;
+      if (e < n * n) S[(e % n) + ld * (e / n)] = Ar::from(c[q] * sc);
+    }
   }
   for (int k = t; k < n; k += blockDim.x) cdiag[k] = (float)(C[k + n * k] * sc);
   __syncthreads();
   if (t == 0) {
     bad = 0;
-    const F2 d = S[0];
-    if (!(d.hi > 0.0f) || !isfinite(d.hi))
+    const V d = S[0];
+    if (!(Ar::lead(d) > 0.0f) || !Ar::finite(d))
       bad = 1;
     else
-      rinv[0] = dfl::rsqrt(d);
+      rinv[0] = Ar::rsq(d);
   }
   __syncthreads();
-  const int jc = t & 63, i0 = t >> 6;
   for (int k = 0; k < n - 1; ++k) {
     if (bad) break;  // uniform: read after the barrier
-    if (jc > k && jc < n) {
-      const F2 ri = rinv[k];
-      const F2 skj = dfl::mul(S[k + ld * jc], dfl::mul(ri, ri));
-      F2 a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = k + 1 + i0 + 16 * q;
-        a[q] = i <= jc ? S[k + ld * i] : F2{0.0f, 0.0f};
-        b[q] = i <= jc ? S[i + ld * jc] : F2{0.0f, 0.0f};
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = k + 1 + i0 + 16 * q;
-        if (i <= jc) {
-          const F2 v = dfl::fms(b[q], a[q], skj);
-          S[i + ld * jc] = v;
-          if (i == k + 1 && jc == k + 1) {
-            if (!(v.hi > 1e-14f * cdiag[k + 1]) || !isfinite(v.hi))
-              bad = 1;
-            else
-              rinv[k + 1] = dfl::rsqrt(v);
-          }
-        }
+    const V ri = rinv[k];
+    const V ri2 = Ar::mul(ri, ri);
+    if (t == 0) {
+      const V a = S[k + ld * (k + 1)];
+      const V v = Ar::fms(S[(k + 1) + ld * (k + 1)], Ar::mul(a, ri2), a);
+      S[(k + 1) + ld * (k + 1)] = v;
+      if (!(Ar::lead(v) > Ar::kPivot * cdiag[k + 1]) || !Ar::finite(v))
+        bad = 1;
+      else
+        rinv[k + 1] = Ar::rsq(v);
+    } else {
+      // two table entries per pass, operands read before either result is written
+      const int T = (n - k - 1) * (n - k) / 2;
+      const int stride = blockDim.x - 1;
+      for (int e = t - 1; e < T; e += 2 * stride) {
+        const int e2 = e + stride;
+        const int ij = tab[e];
+        const int ij2 = e2 < T ? tab[e2] : ij;
+        const int i = ij >> 8, j = ij & 255, i2 = ij2 >> 8, j2 = ij2 & 255;
+        const V x1 = S[i + ld * j], a1 = S[k + ld * i], b1 = S[k + ld * j];
+        const V x2 = S[i2 + ld * j2], a2 = S[k + ld * i2], b2 = S[k + ld * j2];
+        const V v1 = Ar::fms(x1, Ar::mul(a1, ri2), b1);
+        const V v2 = Ar::fms(x2, Ar::mul(a2, ri2), b2);
+        if (!(i == k + 1 && j == k + 1)) S[i + ld * j] = v1;
+        if (e2 < T && !(i2 == k + 1 && j2 == k + 1)) S[i2 + ld * j2] = v2;
       }
     }
     __syncthreads();
@@ -242,33 +258,46 @@ __global__ void __launch_bounds__(1024) cholesky_df_kernel(const double* __restr
     if (t == 0) *flag = 1;
     return;
   }
-  const double rs = sqrt(sc);   // exact: sc is an even power of two
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int j = e % n, k = e / n;
-    R[e] = (j <= k) ? dfl::to_double(dfl::mul(S[j + ld * k], rinv[j])) / rs : 0.0;
+  // R = S diag(rinv) / sqrt(scale), rdiag = rinv sqrt(scale): exact powers of two
+  const double up = ldexp(1.0, hexp_s), down = ldexp(1.0, -hexp_s);
+  {
+    double r[kCholPer];
+#pragma unroll
+    for (int q = 0; q < kCholPer; ++q) {
+      const int e = t + kCholThreads * q;
+      const int j = e % n, k = e / n;
+      r[q] = (e < n * n && j <= k) ? Ar::to(Ar::mul(S[j + ld * k], rinv[j])) * up : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCholPer; ++q) {
+      const int e = t + kCholThreads * q;
+      if (e < n * n) R[e] = r[q];
+    }
   }
-  for (int k = t; k < n; k += blockDim.x) rdiag[k] = dfl::to_double(rinv[k]) * rs;
+  for (int k = t; k < n; k += blockDim.x) rdiag[k] = Ar::to(rinv[k]) * down;
 }
 
 // Out = A R^{-1} row by row (forward substitution on x^T R = a^T); one warp per row, the
 // diagonal applied through its precomputed reciprocals.
-__global__ void trsm_rows_kernel(const double* __restrict__ A, int64_t m, int n, const double* __restrict__ R,
-                                 const double* __restrict__ rdiag, double* __restrict__ Out,
+template <typename T>
+__global__ void trsm_rows_kernel(const T* __restrict__ A, int64_t m, int n, const double* __restrict__ R,
+                                 const double* __restrict__ rdiag, T* __restrict__ Out,
                                  const int32_t* __restrict__ flag) {
   if (*flag) return;
-  extern __shared__ double Rs[];  // n x n column-major (odd leading dimension ld), then n reciprocals
+  extern __shared__ __align__(16) unsigned char trsm_raw[];
+  T* Rs = reinterpret_cast<T*>(trsm_raw);   // n x n column-major (odd leading dimension ld), then n reciprocals
   const int ld = n | 1;           // lanes read a row of R: an odd stride keeps the banks distinct
-  double* rd = Rs + ld * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[(e % n) + ld * (e / n)] = R[e];
-  for (int e = threadIdx.x; e < n; e += blockDim.x) rd[e] = rdiag[e];
+  T* rd = Rs + ld * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[(e % n) + ld * (e / n)] = (T)R[e];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) rd[e] = (T)rdiag[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
-    double y0 = lane < n ? A[row + m * lane] : 0.0;
-    double y1 = lane + 32 < n ? A[row + m * (lane + 32)] : 0.0;
+    T y0 = lane < n ? A[row + m * lane] : T(0);
+    T y1 = lane + 32 < n ? A[row + m * (lane + 32)] : T(0);
     for (int c = 0; c < n; ++c) {
-      const double xc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31) * rd[c];
+      const T xc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31) * rd[c];
       if (lane == (c & 31)) {
         if (c < 32) y0 = xc; else y1 = xc;
       }
@@ -286,7 +315,7 @@ __global__ void householder_q_kernel(const double* __restrict__ Y, int64_t m, in
                                      double* __restrict__ beta, double* __restrict__ Q,
                                      const int32_t* __restrict__ flag, int32_t* __restrict__ info) {
   const bool run = (flag == nullptr) || (*flag != 0);
-  if (info != nullptr && threadIdx.x == 0) *info = run ? 1 : 0;
+  if (info != nullptr && threadIdx.x == 0) *info = (*info & ~1) | (run ? 1 : 0);
   if (!run) return;
   __shared__ double scratch[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -824,106 +853,121 @@ __global__ void __launch_bounds__(256) gram_b_reduce_kernel(const double* __rest
 }
 
 // Diagonally pivoted Cholesky of the Gram matrix W (n x n, FP64 in, n <= 64) in one CTA, in
-// double-float after scaling W by a power of two: W = sum_k r_k r_k^T with r_k the k-th pivot
-// row of R in the original indexing.  Writes X(:, k) = r_k (FP32, n x n column-major), so
-// X X^T = W and the left singular vectors of X are the eigenvectors of W; choosing the largest
-// remaining diagonal at every step makes the columns of X graded and nearly orthogonal, which is
-// what makes one-sided Jacobi on X converge in few sweeps.  flag[0] <- 1 when the largest
-// remaining pivot is <= 1e-14 max diag(W) (numerically singular W) or not finite.  S keeps the
-// upper triangle (i <= j) of the Schur complement.
-__global__ void __launch_bounds__(1024) pivoted_cholesky_kernel(const double* __restrict__ W, int n,
-                                                                float* __restrict__ X,
-                                                                int32_t* __restrict__ flag) {
+// double-float after scaling W by a power of two: W = sum_k r_k r_k^T with r_k the k-th pivot row
+// of R in the original indexing.  Writes X(:, k) = r_k (FP32, n x n column-major), so X X^T = W and
+// the left singular vectors of X are the eigenvectors of W; choosing the largest remaining diagonal
+// at every step makes the columns of X graded and nearly orthogonal, which is what makes one-sided
+// Jacobi on X converge in few sweeps.  flag[0] <- 1 when the largest remaining pivot is
+// <= 1e-14 max diag(W) (numerically singular W) or not finite.
+// S is kept in pivot positions (upper triangle, position -> original index in perm).  Step k: the
+// next pivot (largest remaining diagonal, first index on ties) is known from a 64-bit atomicMax of
+// (value, position) taken while the diagonal was updated; positions k and p are swapped
+// symmetrically; then column k of X is written and the trailing triangle updated through the
+// table of ArithDF / chol_kernel.  Two barriers per step.
+__global__ void __launch_bounds__(kCholThreads) pivoted_cholesky_kernel(const double* __restrict__ W, int n,
+                                                                        float* __restrict__ X,
+                                                                        int32_t* __restrict__ flag) {
   if (flag[0]) return;
-  using dfl::F2;
+  using Ar = ArithDF;
+  using V = Ar::V;
   extern __shared__ __align__(16) unsigned char chol_raw[];
-  F2* S = reinterpret_cast<F2*>(chol_raw);
-  __shared__ int done[RH_MAX_ELL];
-  __shared__ int piv, bad;
-  __shared__ F2 rinv_s;
+  const int ld = n | 1;
+  V* S = reinterpret_cast<V*>(chol_raw);
+  uint16_t* tab = reinterpret_cast<uint16_t*>(chol_raw + ((sizeof(V) * ld * n + 15) & ~size_t(15)));
+  __shared__ int perm[RH_MAX_ELL];
+  __shared__ unsigned long long key[2];
+  __shared__ V rinv_s;
   __shared__ double scale_s;
   __shared__ float dmax_s;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  if (w == 0) {
-    double m = 0.0;
-    for (int i = lane; i < n; i += 32) m = fmax(m, W[i + n * i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) {
-      int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
-      e &= ~1;
-      scale_s = ldexp(1.0, -e);
-      dmax_s = (float)(m * ldexp(1.0, -e));   // in [1, 4)
-      bad = (m > 0.0 && isfinite(m)) ? 0 : 1;
-    }
+  __shared__ int hexp_s, ok_s, bad;
+  const int t = threadIdx.x;
+  diag_scale<Ar>(W, n, &scale_s, &hexp_s, &dmax_s, &ok_s);
+  build_tri_table(tab, n);
+  if (t < RH_MAX_ELL) perm[t] = t;
+  if (t == 0) {
+    key[0] = 0ull;
+    key[1] = 0ull;
   }
   __syncthreads();
   const double sc = scale_s;
-  const int ld = n | 1;   // odd leading dimension: conflict-free 8-byte accesses along a row
-  for (int e = t; e < n * n; e += blockDim.x) S[(e % n) + ld * (e / n)] = dfl::from_double(W[e] * sc);
-  for (int e = t; e < n * n; e += blockDim.x) X[e] = 0.0f;
-  for (int i = t; i < RH_MAX_ELL; i += blockDim.x) done[i] = 0;
-  __syncthreads();
   const float dmax = dmax_s;
-  const double unscale = 1.0 / sqrt(sc);
-  const int jc = t & 63, i0 = t >> 6;
-  for (int k = 0; k < n; ++k) {
-    if (bad) break;
-    if (w == 0) {
-      // argmax of the remaining diagonal (first index on ties), on the leading parts
-      float bv = -1.0f;
-      int bi = n;
-      for (int i = lane; i < n; i += 32) {
-        const float d = done[i] ? -1.0f : S[i + ld * i].hi;
-        if (d > bv) {
-          bv = d;
-          bi = i;
-        }
-      }
+  {
+    double w[kCholPer];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) {
-          bv = ov;
-          bi = oi;
-        }
+    for (int q = 0; q < kCholPer; ++q) {   // all loads first
+      const int e = t + kCholThreads * q;
+      w[q] = (e < n * n && (e % n) <= (e / n)) ? W[e] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCholPer; ++q) {
+      const int e = t + kCholThreads * q;
+      if (e < n * n) {
+        S[(e % n) + ld * (e / n)] = Ar::from(w[q] * sc);
+        X[e] = 0.0f;
       }
-      if (lane == 0) {
-        if (!(bv > 1e-14f * dmax) || !isfinite(bv)) {
-          bad = 1;
-        } else {
-          piv = bi;
-          rinv_s = dfl::rsqrt(S[bi + ld * bi]);
-          done[bi] = 1;
-        }
+    }
+  }
+  __syncthreads();
+  auto pack = [](float v, int pos) -> unsigned long long {
+    const float c = (v > 0.0f && isfinite(v)) ? v : 0.0f;
+    return ((unsigned long long)__float_as_uint(c) << 32) | (unsigned long long)(63 - pos);
+  };
+  for (int i = t; i < n; i += blockDim.x) atomicMax(&key[0], pack(S[i + ld * i].hi, i));
+  if (t == 0) bad = ok_s ? 0 : 1;
+  __syncthreads();
+  const float unscale = ldexpf(1.0f, hexp_s);   // exact: 1 / sqrt(scale)
+  for (int k = 0; k < n; ++k) {
+    if (bad) break;  // uniform: read after the barrier
+    const unsigned long long kk = key[k & 1];
+    const int p = 63 - (int)(kk & 0xFFFFFFFFull);
+    // swap positions k and p (p >= k): S(k, j) <-> S(j, p) for k < j < p, S(k, j) <-> S(p, j) for j > p
+    if (t == 0) {
+      key[(k + 1) & 1] = 0ull;
+      const V dp = S[p + ld * p];
+      if (!(dp.hi > 1e-14f * dmax) || !Ar::finite(dp)) {
+        bad = 1;
+      } else {
+        S[p + ld * p] = S[k + ld * k];
+        S[k + ld * k] = dp;
+        const int q = perm[k];
+        perm[k] = perm[p];
+        perm[p] = q;
+        rinv_s = Ar::rsq(dp);
+      }
+    } else if (p != k) {
+      for (int j = k + t; j < n; j += blockDim.x - 1) {   // t >= 1: j > k
+        if (j == p) continue;
+        V* a = &S[k + ld * j];
+        V* b = (j < p) ? &S[j + ld * p] : &S[p + ld * j];
+        const V tmp = *a;
+        *a = *b;
+        *b = tmp;
       }
     }
     __syncthreads();
-    if (bad) break;  // uniform: read after the barrier
-    const int p = piv;
-    const F2 ri = rinv_s;
-    // column k of X: r_k(j) = S(p, j) / sqrt(S(p, p)) for the remaining j (and j = p)
-    for (int j = t; j < n; j += blockDim.x) {
-      const int a = p < j ? p : j, b = p < j ? j : p;
-      if (j == p || !done[j]) X[j + n * k] = (float)(dfl::to_double(dfl::mul(S[a + ld * b], ri)) * unscale);
-    }
-    // Schur update of the remaining upper triangle: S(i, j) -= S(p, i) S(p, j) / S(p, p).  Entries
-    // in row / column p (done now) are only read, the others only by their owner: no hazard.
-    if (jc < n && !done[jc]) {
-      const F2 spj = dfl::mul(S[(p < jc ? p : jc) + ld * (p < jc ? jc : p)], dfl::mul(ri, ri));
-      F2 a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + 16 * q;
-        const bool live = i <= jc && !done[i];
-        a[q] = live ? S[(p < i ? p : i) + ld * (p < i ? i : p)] : F2{0.0f, 0.0f};
-        b[q] = live ? S[i + ld * jc] : F2{0.0f, 0.0f};
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + 16 * q;
-        if (i <= jc && !done[i]) S[i + ld * jc] = dfl::fms(b[q], a[q], spj);
+    if (bad) break;
+    const V ri = rinv_s;
+    // column k of X: r_k(j) = S(k, j) / sqrt(S(k, k)) at position j >= k, original index perm[j]
+    for (int j = k + t; j < n; j += blockDim.x)
+      X[perm[j] + n * k] = Ar::mul(S[k + ld * j], ri).hi * unscale;
+    // trailing update; the updated diagonal proposes the next pivot
+    const V ri2 = Ar::mul(ri, ri);
+    const int T = (n - k - 1) * (n - k) / 2;
+    const int stride = blockDim.x;
+    for (int e = t; e < T; e += 2 * stride) {   // two entries per pass, operands read first
+      const int e2 = e + stride;
+      const int ij = tab[e];
+      const int ij2 = e2 < T ? tab[e2] : ij;
+      const int i = ij >> 8, j = ij & 255, i2 = ij2 >> 8, j2 = ij2 & 255;
+      const V x1 = S[i + ld * j], a1 = S[k + ld * i], b1 = S[k + ld * j];
+      const V x2 = S[i2 + ld * j2], a2 = S[k + ld * i2], b2 = S[k + ld * j2];
+      const V v1 = Ar::fms(x1, Ar::mul(a1, ri2), b1);
+      const V v2 = Ar::fms(x2, Ar::mul(a2, ri2), b2);
+      S[i + ld * j] = v1;
+      if (i == j) atomicMax(&key[(k + 1) & 1], pack(v1.hi, i));
+      if (e2 < T) {
+        S[i2 + ld * j2] = v2;
+        if (i2 == j2) atomicMax(&key[(k + 1) & 1], pack(v2.hi, i2));
       }
     }
     __syncthreads();
@@ -1072,6 +1116,13 @@ __global__ void __launch_bounds__(kRowJacThreads) jacobi_rows_kernel(const float
   }
 }
 
+__global__ void cast_f2d_gated_kernel(const float* __restrict__ src, double* __restrict__ dst, int64_t n,
+                                      const int32_t* __restrict__ gate) {
+  if (*gate) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
 // After the Gram route: fall back to the tall-skinny QR when the Cholesky factor broke down or
 // when the truncation gap sigma_r^2 - sigma_{r+1}^2 is below 1e-5 sigma_1^2, where the FP32
 // Gram cannot resolve the top-r subspace.
@@ -1115,8 +1166,11 @@ size_t orth_workspace_elems(int64_t m, int n) {
   return (size_t)(nb * n * n + n * n + n * n + n + m * n + m * n + n + 2) + 64;
 }
 
+rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
+                          const int32_t* gate, cudaStream_t st);
+
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
-                                cudaStream_t st, bool df) {
+                                cudaStream_t st, bool f32) {
   const int rb = gram_rows(m);
   const int nb = (int)ceil_div(m, rb);
   double* Gpart = ws;
@@ -1128,9 +1182,45 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
   double* beta = W + m * n;
   int32_t* flag = reinterpret_cast<int32_t*>(beta + n);
   RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+  if (f32) {
+    // FP32 data: CholeskyQR2 whose first pass keeps what its stability needs -- the Gram matrix in
+    // FP64, its Cholesky factor in double-float, the triangular solve in FP64 (Q_1 is then
+    // orthonormal to ~u_64 kappa(Y)) -- and whose second pass, on the nearly orthonormal Q_1, runs
+    // in FP32.  A breakdown hands over to the Householder branch below.  The FP32 copies live in
+    // the W region (only the Householder branch uses W, and it reads Y).
+    RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
+    const size_t gsm = sizeof(double) * rb * n;
+    const int rblocks = (int)ceil_div((int64_t)n * n, 256);
+    const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
+    gram_partial_kernel<<<nb, 256, gsm, st>>>(Y, m, n, rb, Gpart, flag);
+    RH_LAUNCH_CHECK();
+    gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
+    RH_LAUNCH_CHECK();
+    chol_kernel<ArithDF><<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(C, n, R, rdiag, flag);
+    RH_LAUNCH_CHECK();
+    trsm_rows_kernel<double><<<tblocks, 256, sizeof(double) * ((n | 1) * n + n), st>>>(Y, m, n, R, rdiag, Q1, flag);
+    RH_LAUNCH_CHECK();
+    float* Q1f = reinterpret_cast<float*>(W);
+    float* Q2f = Q1f + m * n;
+    const int cblocks = (int)std::min<int64_t>(ceil_div(m * n, 256), 4 * num_sms());
+    cast_gated_kernel<float><<<cblocks, 256, 0, st>>>(Q1, Q1f, m * n, flag);
+    RH_LAUNCH_CHECK();
+    rh_status s = launch_gram_f32(Q1f, m, 1, n, Gpart, C, flag, st);
+    if (s != RH_OK) return s;
+    chol_kernel<ArithF32><<<1, kCholThreads, chol_smem(n, sizeof(float)), st>>>(C, n, R, rdiag, flag);
+    RH_LAUNCH_CHECK();
+    trsm_rows_kernel<float><<<tblocks, 256, sizeof(float) * ((n | 1) * n + n), st>>>(Q1f, m, n, R, rdiag, Q2f, flag);
+    RH_LAUNCH_CHECK();
+    cast_f2d_gated_kernel<<<cblocks, 256, 0, st>>>(Q2f, Q, m * n, flag);
+    RH_LAUNCH_CHECK();
+    householder_q_kernel<<<1, 1024, 0, st>>>(Y, m, n, W, beta, Q, flag, info);
+    RH_LAUNCH_CHECK();
+    colsign_kernel<double><<<n, 256, 0, st>>>(Q, m, n, nullptr, 0);
+    RH_LAUNCH_CHECK();
+    return RH_OK;
+  }
   RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
   const size_t gsm = sizeof(double) * rb * n;
-  const size_t nsm = sizeof(double) * (n | 1) * n;
   const size_t tsm = sizeof(double) * ((n | 1) * n + n);
   const int rblocks = (int)ceil_div((int64_t)n * n, 256);
   const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
@@ -1141,12 +1231,9 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
     RH_LAUNCH_CHECK();
     gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
     RH_LAUNCH_CHECK();
-    if (df)
-      cholesky_df_kernel<<<1, 1024, nsm, st>>>(C, n, R, rdiag, flag);
-    else
-      cholesky_kernel<<<1, 1024, nsm, st>>>(C, n, R, rdiag, flag);
+    chol_kernel<ArithF64><<<1, kCholThreads, chol_smem(n, sizeof(double)), st>>>(C, n, R, rdiag, flag);
     RH_LAUNCH_CHECK();
-    trsm_rows_kernel<<<tblocks, 256, tsm, st>>>(src, m, n, R, rdiag, dst, flag);
+    trsm_rows_kernel<double><<<tblocks, 256, tsm, st>>>(src, m, n, R, rdiag, dst, flag);
     RH_LAUNCH_CHECK();
     src = Q1;
     dst = Q;
@@ -1183,7 +1270,23 @@ static void trunc_dims(TruncPlan& pl) {
 
 static int odd_ld(int rows) { return rows | 1; }
 
-static int gram_ctas() { return 4 * num_sms(); }
+int gram_ctas() { return 4 * num_sms(); }
+
+// W = B B^T (ell x ell, FP64, full) of the FP32 (L, ell, R) tensor B: FP32 sums over 128 columns,
+// FP64 across; part holds min(gram_ctas(), ceil(L R / 128)) ell^2 doubles.  Gated on *gate == 0.
+rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
+                          const int32_t* gate, cudaStream_t st) {
+  const int64_t ntiles = ceil_div(L * R, 128);
+  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(gram_ctas(), ntiles));
+  if (ell <= 32)
+    gram_b_kernel<32><<<ctas, GramCfg<32>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+  else
+    gram_b_kernel<64><<<ctas, GramCfg<64>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+  RH_LAUNCH_CHECK();
+  gram_b_reduce_kernel<<<(int)ceil_div((int64_t)ell * ell, 32), 256, 0, st>>>(part, ctas, ell, W, gate);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
 
 template <typename T>
 size_t trunc_workspace_elems(const TruncPlan& pl0) {
@@ -1226,16 +1329,11 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     float* Rf = reinterpret_cast<float*>(flags + 16);
     use_tsqr = flags + 1;
     RH_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), st));
-    if (n <= 32)
-      gram_b_kernel<32><<<ctas, GramCfg<32>::THREADS, 0, st>>>(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n,
-                                                              part, nullptr);
-    else
-      gram_b_kernel<64><<<ctas, GramCfg<64>::THREADS, 0, st>>>(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n,
-                                                              part, nullptr);
-    RH_LAUNCH_CHECK();
-    gram_b_reduce_kernel<<<(int)ceil_div(nn, 32), 256, 0, st>>>(part, ctas, n, W, nullptr);
-    RH_LAUNCH_CHECK();
-    pivoted_cholesky_kernel<<<1, 1024, sizeof(float) * 2 * (n | 1) * n, st>>>(W, n, Rf, flags);
+    (void)ctas;
+    rh_status s;
+    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st)) != RH_OK)
+      return s;
+    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(W, n, Rf, flags);
     RH_LAUNCH_CHECK();
     {
       ProfileScope ps(PROF_JACOBI, 0, st);

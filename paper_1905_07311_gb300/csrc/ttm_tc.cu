@@ -43,8 +43,8 @@ template <bool F32IN>
 struct TtmCfg {
   static constexpr int kPStages = F32IN ? 2 : 3;
   static constexpr int kF32Stages = F32IN ? 3 : 1;
-  static constexpr int kThreads = F32IN ? 448 : 192;
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
+  static constexpr int kThreads = F32IN ? 192 + kConv : 192;
 };
 
 template <bool F32IN>
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(TtmCfg<F32IN>::kThreads, 1)
     }
   } else if constexpr (F32IN) {
     // converters (warps 6..13): FP32 slice -> BF16 head + tail; thread 0 also requests the A slice
-    const int t = threadIdx.x - 192;   // 0..255
+    const int t = threadIdx.x - 192;   // 0..kConv-1
     uint32_t it = 0;
     bool ok = true;
     for (int64_t tt = blockIdx.x; tt < ntiles && ok; tt += gridDim.x) {

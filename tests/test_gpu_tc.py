@@ -103,29 +103,41 @@ def test_tc_mode_product_matches_definition(rh, pieces, shape, k):
 
 
 # ---------------------------------------------------------------------------------
-# R-STHOSVD with the first mode on the tensor cores (BF16X2 form)
+# R-STHOSVD on the tensor cores (BF16X2 form)
 # ---------------------------------------------------------------------------------
-# Gates: the GPU sees X_rep = head + tail exactly and rounds Omega_1 to BF16 (the oracle uses the
-# same values); the first mode product uses Q split into two BF16 pieces (|dQ| <= 2^-16 |Q|), a
-# perturbation of B of ~2^-16 relative.  It moves the leading-k factor subspace by ~2^-16 / tau
-# (tau = 0.05 -> 3e-4, gate 1e-3) and the relative Tucker error only at second order (the residual is
-# orthogonal to the perturbation of the projection), so the error gate stays 1e-5.
-@pytest.mark.parametrize("shape,ranks,p", [((128, 60, 50), (6, 5, 4), 5), ((256, 128, 96), (20, 20, 20), 10),
-                                           ((1024, 40, 30), (8, 6, 5), 4)])
-def test_rsthosvd_bf16x2_first_mode_matches_oracle(rh, shape, ranks, p):
+# Gates: the GPU sees X_rep = head + tail exactly and rounds Omega_n to BF16 on every mode that ran
+# on the tensor cores (info bit 4; the oracle rounds the same modes); a mode product on the tensor
+# cores uses Q split into two BF16 pieces (|dQ| <= 2^-16 |Q|) and, after the first mode, the FP32
+# core split into 16 significant bits: perturbations of B of ~2^-16 relative.  They move the
+# leading-k factor subspace by ~2^-16 / tau (tau = 0.05 -> 3e-4, gate 1e-3) and the relative Tucker
+# error only at second order (the residual is orthogonal to the perturbation of the projection), so
+# the error gate stays 1e-5.
+@pytest.mark.parametrize("shape,ranks,p,rho", [((128, 60, 50), (6, 5, 4), 5, [0, 1, 2]),
+                                               ((256, 128, 96), (20, 20, 20), 10, [0, 1, 2]),
+                                               ((1024, 40, 30), (8, 6, 5), 4, [0, 1, 2]),
+                                               ((256, 96, 48), (12, 10, 8), 6, [0, 2, 1]),
+                                               ((64, 48, 40, 16), (6, 5, 4, 3), 3, [0, 1, 2, 3]),
+                                               ((64, 40, 24, 16), (6, 5, 4, 3), 3, [0, 1, 3, 2])])
+def test_rsthosvd_bf16x2_matches_oracle(rh, shape, ranks, p, rho):
     from oracle import tucker as otk
     from oracle.tensor import rel_error
     from workloads import lowrank_plus_noise_np
 
-    X = lowrank_plus_noise_np(list(shape), [max(ranks) + 2] * 3, 0.8, 1e-3, seed=21).astype(np.float32)
+    d = len(shape)
+    X = lowrank_plus_noise_np(list(shape), [max(ranks) + 2] * d, 0.8, 1e-3, seed=21).astype(np.float32)
     Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
     Xb = rh.split_bf16x2(Xd)
-    T = rh.rsthosvd(Xb, list(shape), list(ranks), p=p, seed=3, rho=[0, 1, 2], form="bf16x2")
+    T = rh.rsthosvd(Xb, list(shape), list(ranks), p=p, seed=3, rho=rho, form="bf16x2")
     torch.cuda.synchronize()
+    info = T.info.cpu().numpy().tolist()
+    assert info[0] & 4, info          # the first mode always runs on the tensor cores
+    if shape == (256, 128, 96):
+        assert info[1] & 4, info      # mode 2 follows with a unit-stride core (I_2 = 128)
     bits = Xb.cpu().numpy().view(np.uint16)
     n = X.size
     Xrep = np.reshape(bf16_bits_to_f64(bits[:n]) + bf16_bits_to_f64(bits[n:]), shape, order="F")
-    out = otk.rsthosvd(Xrep, list(ranks), p, 3, rho=[0, 1, 2], omega_round={0: "bf16"}, record=True)
+    rnd = {m: "bf16" for m in range(d) if info[m] & 4}
+    out = otk.rsthosvd(Xrep, list(ranks), p, 3, rho=rho, omega_round=rnd, record=True)
     A = [f.cpu().numpy().T for f in T.factors]
     G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
     e_g = rel_error(Xrep, G, A)
