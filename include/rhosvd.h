@@ -292,6 +292,38 @@ rh_status rh_tucker_residual(int32_t order, const int64_t* dims, int32_t dtype, 
                              void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * adaptive_rank -- adaptive-rank randomized HOSVD (variant 0, Alg. 4) or STHOSVD (variant 1,
+ * Alg. 5) to a target relative error: every mode's factor comes from the adaptive range finder
+ * of Sec. 4 with the absolute tolerance tau = eps ||X||_F / sqrt(d).  Reading of the range finder
+ * (the paper names it without listing it): blocks of ``block`` columns of the mode's Gaussian
+ * stream are added until ||G_(n) - Q Q^T G_(n)||_F <= tau or max_ranks[n] columns are reached, then
+ * opts->p more columns of the same stream; the SVD of B = Q^T G_(n) is trimmed to the smallest r
+ * with sum_{i>r} sigma_i^2 + ||G_(n) - Q B||^2 <= tau^2.  One sketch of width max_ranks[n] + p
+ * serves every block size (the leading columns of its thin QR span the leading blocks).
+ *   X          tensor (order, dims, RH_F64 or RH_F32), column-major, device.
+ *   max_ranks  host array: cap on the range-finder size per mode (max_ranks[n] + p <= 64 after
+ *              clamping to min(I_n, prod of the other sizes)).
+ *   opts       p (trim oversampling), seed, tensor_id, rho (variant 1; rho[0] < 0: decreasing
+ *              I_n).  truncate and clamp are ignored.
+ *   factors    host array of device pointers, factors[n] holds I_n x ell_n FP64 with
+ *              ell_n = min(max_ranks[n] + p, I_n, prod of the other input sizes) (the trim runs over
+ *              up to ell_n rows, so ranks[n] can exceed max_ranks[n]); the first ranks[n] columns
+ *              receive A_n (orthonormal, column signs as in rsthosvd).
+ *   core       device buffer of prod(ell_n) FP64; receives the ranks[0] x ... core, column-major.
+ *   ranks      HOST array of ``order`` values receiving the chosen ranks.
+ *   norms      optional device buffer of 2 FP64: ||X||^2 and ||G||^2.
+ *   Synchronous: the chosen sizes drive the later launches, so the call synchronises ``stream``
+ *   once per mode and returns when the result is complete.  Workspace:
+ *   adaptive_rank_workspace_size.
+ */
+size_t adaptive_rank_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t variant,
+                                    const int32_t* max_ranks, const rh_options* opts);
+rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const void* X, double eps,
+                        int32_t variant, int32_t block, const int32_t* max_ranks, const rh_options* opts,
+                        double* const* factors, double* core, int32_t* ranks, double* norms, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
+/*
  * rsthosvd_host -- the same R-STHOSVD with HOST buffers: enqueues the copy of X to the
  * device, the decomposition and the copies of the factors, the core and the norms back
  * to the host, all on ``stream``; the results are valid once the stream is synchronised.

@@ -325,6 +325,49 @@ def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True)
     return call.run(X)
 
 
+def adaptive(X, dims, eps, variant="sthosvd", block=8, max_ranks=None, p=10, seed=0, rho=None, tensor_id=0):
+    """Adaptive-rank R-HOSVD (``variant="hosvd"``, Alg. 4) or R-STHOSVD (``"sthosvd"``, Alg. 5) of the
+    flat column-major tensor X to relative error ``eps`` (tolerance eps ||X|| / sqrt(d) per mode).
+    ``max_ranks`` caps the range finder per mode (default min(I_n, 64 - p)).  Synchronous; returns a
+    Tucker whose factors are (r_n, I_n) views and whose ``ranks`` attribute lists the chosen ranks."""
+    torch = _check_input(X, dims)
+    d = len(dims)
+    dims = [int(v) for v in dims]
+    if max_ranks is None:
+        max_ranks = [max(1, min(v, 64 - int(p))) for v in dims]
+    vcode = {"hosvd": 0, "sthosvd": 1}[variant]
+    dt = _dtype_code(X)
+    da, ma = i64_array(dims), i32_array(max_ranks)
+    opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho)
+    ws_bytes = lib().adaptive_rank_workspace_size(d, da, dt, vcode, ma, ctypes.byref(opts))
+    if ws_bytes == 0:
+        raise ValueError("invalid adaptive request (check dtype, max_ranks + p <= 64)")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=X.device)
+    ntot = 1
+    for v in dims:
+        ntot *= v
+    ells = [min(int(max_ranks[n]) + int(p), dims[n], ntot // dims[n]) for n in range(d)]
+    full = [torch.zeros((ells[n], dims[n]), dtype=torch.float64, device=X.device) for n in range(d)]
+    ncore = 1
+    for k in ells:
+        ncore *= k
+    core = torch.zeros(ncore, dtype=torch.float64, device=X.device)
+    norms = torch.zeros(2, dtype=torch.float64, device=X.device)
+    ranks = (ctypes.c_int32 * d)()
+    fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in full])
+    check(lib().adaptive_rank(d, da, dt, _ptr(X), float(eps), vcode, int(block), ma, ctypes.byref(opts), fptrs,
+                              _ptr(core), ranks, _ptr(norms), _ptr(ws), ws_bytes, _stream(X.device)))
+    rk = [int(ranks[n]) for n in range(d)]
+    # factor n occupies the first r_n columns of its I_n x max_ranks[n] column-major buffer
+    factors = [full[n].reshape(-1)[: rk[n] * dims[n]].reshape(rk[n], dims[n]) for n in range(d)]
+    nc = 1
+    for r in rk:
+        nc *= r
+    T = Tucker(factors, core[:nc], rk, norms, torch.zeros(d, dtype=torch.int32, device=X.device))
+    T.ranks = rk
+    return T
+
+
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None):
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 

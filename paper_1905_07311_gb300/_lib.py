@@ -62,6 +62,9 @@ SIGNATURES = {
     "rhosvd": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
     "core_ttm_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
     "core_ttm": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    "adaptive_rank_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _P, ctypes.POINTER(RhOptions)]),
+    "adaptive_rank": (_I32, [_I32, _P, _I32, _P, ctypes.c_double, _I32, _I32, _P, ctypes.POINTER(RhOptions), _P, _P,
+                             _P, _P, _P, _SZ, _P]),
     "rh_tucker_residual_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
     "rh_tucker_residual": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),

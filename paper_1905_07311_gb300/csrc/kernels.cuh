@@ -104,6 +104,20 @@ template <typename T>
 rh_status launch_trunc_svd(const TruncPlan& pl, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st, int r,
                            int32_t* info);
 
+// Staged truncation (adaptive variants).  Stage 1, the factor of the whole ell x M matrix B:
+// gram (FP32 data) -> W = B B^T in W (part: gram partials, see launch_gram_f32); otherwise the
+// tall-skinny QR triangle R of B^T (inside ws, *R points at it).  rownorm2[c] = ||row c of B||^2.
+// Stage 2, the SVD of the leading k rows of B from that factor: U_B (k x k) and sv (k), through
+// the pivoted Cholesky of W[0:k, 0:k] and the row Jacobi (flag <- 1 on a Cholesky breakdown), or
+// through the Jacobi SVD of R[0:k, 0:k] (Wk, Xf, Rk: k x k scratch).
+template <typename T>
+rh_status launch_trunc_factor(const TruncPlan& pl, const T* B, T* ws, bool gram, double* part, double* W, T** R,
+                              double* rownorm2, cudaStream_t st);
+template <typename T>
+rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, const T* R, double* Wk, float* Xf,
+                                   T* Rk, double* Ub, double* sv, int32_t* flag, cudaStream_t st);
+int gram_ctas();
+
 // A = Q * Ub(:, 0:r)  (I x r, FP64);  Uc = (T) Ub(:, 0:r) (ell x r)
 template <typename T>
 rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, const double* Ub, double* A, T* Uc,

@@ -1116,6 +1116,29 @@ __global__ void __launch_bounds__(kRowJacThreads) jacobi_rows_kernel(const float
   }
 }
 
+// dst (k x k) = the leading k x k block of the column-major n x n src
+template <typename TS, typename TD>
+__global__ void copy_leading_kernel(const TS* __restrict__ src, int n, int k, TD* __restrict__ dst) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
+    dst[e] = (TD)src[(e % k) + n * (e / k)];
+}
+// d[c] = W[c, c]
+__global__ void diag_kernel(const double* __restrict__ W, int n, double* __restrict__ d) {
+  for (int c = threadIdx.x; c < n; c += blockDim.x) d[c] = W[c + n * c];
+}
+// d[c] = sum_i R[i, c]^2 (the squared norm of row c of B when B^T = Q_B R)
+template <typename T>
+__global__ void colnorm2_kernel(const T* __restrict__ R, int n, double* __restrict__ d) {
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) {
+    const double v = (double)R[i + n * c];
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  if (threadIdx.x == 0) d[c] = s;
+}
+
 __global__ void cast_f2d_gated_kernel(const float* __restrict__ src, double* __restrict__ dst, int64_t n,
                                       const int32_t* __restrict__ gate) {
   if (*gate) return;
@@ -1376,6 +1399,78 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
   return RH_OK;
 }
 
+// ---- staged truncation (adaptive variants) ----------------------------------------------
+template <typename T>
+rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram, double* part, double* W, T** R,
+                              double* rownorm2, cudaStream_t st) {
+  TruncPlan pl = pl0;
+  trunc_dims<T>(pl);
+  const int n = pl.ell;
+  const int64_t nn = (int64_t)n * n;
+  if (gram) {
+    rh_status s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st);
+    if (s != RH_OK) return s;
+    diag_kernel<<<1, 64, 0, st>>>(W, n, rownorm2);
+    RH_LAUNCH_CHECK();
+    return RH_OK;
+  }
+  T* buf0 = ws;
+  T* buf1 = ws + pl.nblk0 * nn;
+  const int ld0 = odd_ld(pl.rows0);
+  const int ldm = odd_ld(pl.fan * n);
+  const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
+  const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
+  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+  const int64_t cap = 8 * (int64_t)num_sms();
+  tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, cap), kTsqrThreads, sm0, st>>>(
+      B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, nullptr);
+  RH_LAUNCH_CHECK();
+  int64_t cnt = pl.nblk0;
+  T* cur = buf0;
+  T* nxt = buf1;
+  while (cnt > 1) {
+    const int64_t nout = ceil_div(cnt, pl.fan);
+    tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, cap), kTsqrThreads, smm, st>>>(cur, cnt, n, pl.fan,
+                                                                                           ldm, nxt, nullptr);
+    RH_LAUNCH_CHECK();
+    cnt = nout;
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  *R = cur;
+  colnorm2_kernel<T><<<n, 32, 0, st>>>(cur, n, rownorm2);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+template <typename T>
+rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, const T* R, double* Wk, float* Xf,
+                                   T* Rk, double* Ub, double* sv, int32_t* flag, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, ceil_div((int64_t)k * k, 256));
+  if (gram) {
+    RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+    copy_leading_kernel<double, double><<<blocks, 256, 0, st>>>(W, n, k, Wk);
+    RH_LAUNCH_CHECK();
+    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(k, sizeof(dfl::F2)), st>>>(Wk, k, Xf, flag);
+    RH_LAUNCH_CHECK();
+    const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
+    RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Xf, k, Ub, sv, flag);
+    RH_LAUNCH_CHECK();
+    return RH_OK;
+  }
+  copy_leading_kernel<T, T><<<blocks, 256, 0, st>>>(R, n, k, Rk);
+  RH_LAUNCH_CHECK();
+  const int np = (k + 1) & ~1;
+  const size_t smj = sizeof(T) * 4 * (size_t)np * 32 * 2;
+  RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
+  jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(Rk, k, Ub, sv, nullptr, 0);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
 template <typename T>
 rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, const double* Ub, double* A, T* Uc,
                                  cudaStream_t st) {
@@ -1408,6 +1503,14 @@ template rh_status launch_trunc_svd<float>(const TruncPlan&, const float*, float
                                            int32_t*);
 template rh_status launch_trunc_svd<double>(const TruncPlan&, const double*, double*, double*, double*, cudaStream_t,
                                             int, int32_t*);
+template rh_status launch_trunc_factor<float>(const TruncPlan&, const float*, float*, bool, double*, double*, float**,
+                                             double*, cudaStream_t);
+template rh_status launch_trunc_factor<double>(const TruncPlan&, const double*, double*, bool, double*, double*,
+                                              double**, double*, cudaStream_t);
+template rh_status launch_trunc_leading_svd<float>(int, int, bool, const double*, const float*, double*, float*, float*,
+                                                  double*, double*, int32_t*, cudaStream_t);
+template rh_status launch_trunc_leading_svd<double>(int, int, bool, const double*, const double*, double*, float*,
+                                                   double*, double*, double*, int32_t*, cudaStream_t);
 template rh_status launch_factor_and_cast<float>(int64_t, int, int, const double*, const double*, double*, float*,
                                                  cudaStream_t);
 template rh_status launch_factor_and_cast<double>(int64_t, int, int, const double*, const double*, double*, double*,
