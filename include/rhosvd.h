@@ -324,6 +324,49 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
                         size_t workspace_bytes, void* stream);
 
 /*
+ * rhosvd_sketch_coo -- the range-finder sketch Y = X_(mode) Omega_mode of a sparse tensor given as
+ * COO entries, without densifying (Alg. 6 step 4; Sec. 5).  Entry k is (idx[0][k], ..., idx[d-1][k])
+ * with value vals[k]; it adds vals[k] Omega_mode(p, :) to row idx[mode][k] of Y, p the Kolda
+ * column index of the entry in the mode-``mode`` unfolding (the Omega stream of rhosvd_sketch).
+ *   idx   host array of ``order`` DEVICE pointers to int32 arrays of nnz 0-based indices
+ *         (deduplicated; duplicates are summed).  vals: device FP32 array of nnz values.
+ *   Y     device, I_mode x ell FP64, column-major.
+ *   The entries are stably sorted by their mode index and each row's sum is formed in a fixed
+ *   order (FP32 sums over at most 512 entries, FP64 above): the result is deterministic.  The call
+ *   synchronises ``stream`` once (the work split is built on the host from the row counts).
+ *   Needs nnz < 2^31 and every I_n < 2^31; ell <= 64.  Workspace: rhosvd_sketch_coo_workspace_size.
+ */
+size_t rhosvd_sketch_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, int32_t mode, int32_t ell);
+rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
+                            const float* vals, int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id, double* Y,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sp_sthosvd_coo -- structure-preserving STHOSVD of a COO tensor (Alg. 6).  Per mode n in the order
+ * rho: Y = G_(n) Omega_n from the nonzeros; Y = QR; P_n = ell_n rows of Q chosen by strong RRQR
+ * with eta = 2 (column-pivoted QR of Q^T, then swaps while some |A_ij| > 2 on an unselected row,
+ * largest first, lowest (i, j) on ties); A_n = Q (P_n^T Q)^{-1}; G_(n) <- P_n^T G_(n), i.e. the
+ * nonzeros whose mode-n index is selected, renumbered to their position in the sorted selection.
+ * The core is the dense ell_1 x ... x ell_d array of the surviving entries (entries of X).
+ *   ell_n = ranks[n] + opts->p must be < min(I_n, prod of the other current sizes) (Alg. 6's strict
+ *   rule; opts->clamp lowers ell_n to that bound minus one instead of failing) and <= 64.
+ *   idx, vals   as rhosvd_sketch_coo (not modified; the call works on a copy).
+ *   factors     host array of device pointers, factors[n] receives A_n, I_n x ell_n FP64.
+ *   selected    optional host array of device pointers, selected[n] receives P_n (ell_n int32,
+ *               increasing); NULL or NULL entries skip it.
+ *   core        device, prod(ell_n) FP64, column-major.  norms: optional device 2 FP64:
+ *               ||X||^2 and ||G||^2.
+ *   The selection runs on the host in FP64; the call synchronises ``stream`` several times per
+ *   mode and returns when the result is complete.  Workspace: sp_sthosvd_coo_workspace_size.
+ */
+size_t sp_sthosvd_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks,
+                                     const rh_options* opts);
+rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
+                         const float* vals, const int32_t* ranks, const rh_options* opts, double* const* factors,
+                         int32_t* const* selected, double* core, double* norms, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/*
  * rsthosvd_host -- the same R-STHOSVD with HOST buffers: enqueues the copy of X to the
  * device, the decomposition and the copies of the factors, the core and the norms back
  * to the host, all on ``stream``; the results are valid once the stream is synchronised.

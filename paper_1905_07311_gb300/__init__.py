@@ -368,6 +368,85 @@ def adaptive(X, dims, eps, variant="sthosvd", block=8, max_ranks=None, p=10, see
     return T
 
 
+def _coo_args(idx, vals):
+    torch = _torch()
+    cols = [c.contiguous() for c in idx]
+    for c in cols:
+        if c.dtype != torch.int32 or not c.is_cuda:
+            raise ValueError("COO indices must be int32 CUDA tensors")
+    if vals.dtype != torch.float32 or not vals.is_cuda:
+        raise ValueError("COO values must be a float32 CUDA tensor")
+    return cols, (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols]), vals.contiguous()
+
+
+def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0):
+    """Y = X_(mode) Omega_mode of the COO tensor (``idx``: list of d int32 CUDA index tensors, ``vals``
+    FP32); returns the (ell, I_mode) FP64 tensor holding the column-major I_mode x ell Y."""
+    torch = _torch()
+    cols, iptr, vals = _coo_args(idx, vals)
+    d = len(dims)
+    da = i64_array(dims)
+    nnz = int(vals.numel())
+    ws_bytes = lib().rhosvd_sketch_coo_workspace_size(d, da, nnz, int(mode), int(ell))
+    if ws_bytes == 0:
+        raise ValueError("invalid COO sketch request")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=vals.device)
+    Y = torch.empty((int(ell), int(dims[mode])), dtype=torch.float64, device=vals.device)
+    check(lib().rhosvd_sketch_coo(d, da, nnz, iptr, _ptr(vals), int(mode), int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                  int(tensor_id), _ptr(Y), _ptr(ws), ws_bytes, _stream(vals.device)))
+    return Y
+
+
+class SpTucker(Tucker):
+    """SP-STHOSVD result: factors (ell_n, I_n), selected row indices per mode, dense core."""
+
+
+def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False):
+    """Alg. 6 (SP-STHOSVD) of a COO tensor; returns an SpTucker with ``selected``."""
+    torch = _torch()
+    cols, iptr, vals = _coo_args(idx, vals)
+    d = len(dims)
+    dims = [int(v) for v in dims]
+    da, ra = i64_array(dims), i32_array(ranks)
+    nnz = int(vals.numel())
+    opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp)
+    ws_bytes = lib().sp_sthosvd_coo_workspace_size(d, da, nnz, ra, ctypes.byref(opts))
+    if ws_bytes == 0:
+        check(lib().sp_sthosvd_coo(d, da, nnz, iptr, _ptr(vals), ra, ctypes.byref(opts), None, None, None, None, None,
+                                   0, None))
+        raise ValueError("invalid SP-STHOSVD request")
+    # ell_n as the library computes it (same order and size rule)
+    order = list(rho) if rho is not None else sorted(range(d), key=lambda n: (-dims[n], n))
+    cur = list(dims)
+    ells = [0] * d
+    for n in order:
+        M = 1
+        for k in range(d):
+            if k != n:
+                M *= cur[k]
+        ell = int(ranks[n]) + int(p)
+        lim = min(cur[n], M)
+        if ell >= lim:
+            ell = lim - 1
+        ells[n] = ell
+        cur[n] = ell
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=vals.device)
+    factors = [torch.empty((ells[n], dims[n]), dtype=torch.float64, device=vals.device) for n in range(d)]
+    selected = [torch.empty(ells[n], dtype=torch.int32, device=vals.device) for n in range(d)]
+    ncore = 1
+    for e in ells:
+        ncore *= e
+    core = torch.empty(ncore, dtype=torch.float64, device=vals.device)
+    norms = torch.empty(2, dtype=torch.float64, device=vals.device)
+    fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in factors])
+    sptrs = (ctypes.c_void_p * d)(*[s_.data_ptr() for s_ in selected])
+    check(lib().sp_sthosvd_coo(d, da, nnz, iptr, _ptr(vals), ra, ctypes.byref(opts), fptrs, sptrs, _ptr(core),
+                               _ptr(norms), _ptr(ws), ws_bytes, _stream(vals.device)))
+    T = SpTucker(factors, core, ells, norms, torch.zeros(d, dtype=torch.int32, device=vals.device))
+    T.selected = selected
+    return T
+
+
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None):
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 

@@ -65,6 +65,10 @@ SIGNATURES = {
     "adaptive_rank_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _P, ctypes.POINTER(RhOptions)]),
     "adaptive_rank": (_I32, [_I32, _P, _I32, _P, ctypes.c_double, _I32, _I32, _P, ctypes.POINTER(RhOptions), _P, _P,
                              _P, _P, _P, _SZ, _P]),
+    "rhosvd_sketch_coo_workspace_size": (_SZ, [_I32, _P, _I64, _I32, _I32]),
+    "rhosvd_sketch_coo": (_I32, [_I32, _P, _I64, _P, _P, _I32, _I32, ctypes.c_uint64, _I32, _P, _P, _SZ, _P]),
+    "sp_sthosvd_coo_workspace_size": (_SZ, [_I32, _P, _I64, _P, ctypes.POINTER(RhOptions)]),
+    "sp_sthosvd_coo": (_I32, [_I32, _P, _I64, _P, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
     "rh_tucker_residual_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
     "rh_tucker_residual": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),

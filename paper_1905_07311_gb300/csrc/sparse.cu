@@ -1,0 +1,659 @@
+// Structure-preserving STHOSVD on a COO tensor (Alg. 6, SP-STHOSVD, Sec. 5).
+//
+// Per mode n in the processing order, on the current sparse core G (COO, 0-based, deduplicated):
+//   Y = G_(n) Omega_n       sketch straight from the nonzeros (step 4): nonzero (i_1..i_d, v)
+//                           adds v Omega_n(p, :) to row i_n, p its Kolda column index
+//   Y = Q R                 thin QR (step 5, CholeskyQR2 / Householder)
+//   P_n = sRRQR(Q^T)        ell_n rows of Q, max |A_ij| <= eta = 2 (step 6)
+//   A_n = Q (P_n^T Q)^{-1}  (step 7)
+//   G_(n) <- P_n^T G_(n)    keep the nonzeros whose mode-n index is selected and renumber it to
+//                           its position in the sorted selection (step 8): G stays sparse
+// and finally the dense ell_1 x ... x ell_d core of the surviving entries.
+//
+// The sketch is deterministic: the nonzeros are stably sorted by i_n (CUB radix sort), each row's
+// run is cut into work items of at most kItem nonzeros, a warp turns an item into a partial row
+// (FP32 sums of products, two nonzeros per pass: lanes 0-15 and 16-31, lane q generating Omega
+// columns 4q..4q+3 with the library's Philox / Box-Muller), and the partials of a row are added in
+// FP64 in item order.  The item list is built on the host from the row counts, and the selection
+// (strong RRQR: column-pivoted QR of Q^T, then swaps while some |A_ij| > eta, the largest entry first,
+// lowest (i, j) on ties) runs on the host in FP64, so the call synchronises its stream per mode.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "philox.cuh"
+
+namespace rh {
+namespace {
+
+constexpr int kItem = 512;   // nonzeros per work item of the sketch
+
+__global__ void iota_kernel(int32_t* __restrict__ a, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    a[e] = (int32_t)e;
+}
+
+__global__ void count_kernel(const int32_t* __restrict__ key, int64_t n, int32_t* __restrict__ cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[key[e]], 1);
+}
+
+struct SpIdx {
+  const int32_t* idx[RH_MAX_ORDER];
+  int64_t stride[RH_MAX_ORDER];   // Kolda stride of each mode in the mode-n unfolding (0 for n)
+};
+
+// Warp per work item (row, [begin, end) of the sorted nonzeros): partial row of Y in FP64.
+__global__ void __launch_bounds__(256) sp_sketch_items_kernel(SpIdx ix, int d, const float* __restrict__ vals,
+                                                              const int32_t* __restrict__ perm,
+                                                              const int3* __restrict__ items, int nitems, int ell,
+                                                              uint32_t k0, uint32_t k1, uint32_t sid,
+                                                              double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int q = lane & 15, half = lane >> 4;
+  const int nq = (ell + 3) >> 2;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const int3 item = items[it];   // x: row (unused here), y: begin, z: end
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int j = item.y + half; j < item.z; j += 2) {
+      const int e = perm[j];
+      int64_t p = 0;
+      for (int k = 0; k < d; ++k) p += (int64_t)ix.idx[k][e] * ix.stride[k];
+      const float v = vals[e];
+      if (q < nq) {
+        const float4 w = rng::omega4(k0, k1, sid, p, (uint32_t)q);
+        acc[0] = fmaf(v, w.x, acc[0]);
+        acc[1] = fmaf(v, w.y, acc[1]);
+        acc[2] = fmaf(v, w.z, acc[2]);
+        acc[3] = fmaf(v, w.w, acc[3]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+    if (half == 0 && q < nq) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * q + c < ell) part[(int64_t)it * ell + 4 * q + c] = (double)acc[c];
+    }
+  }
+}
+
+// Y[r, c] = sum of the partials of row r's items, in item order (rows without items: 0)
+__global__ void sp_sketch_reduce_kernel(const double* __restrict__ part, const int32_t* __restrict__ row_items,
+                                        int64_t I, int ell, double* __restrict__ Y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * ell; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % I;
+    const int c = (int)(e / I);
+    double s = 0.0;
+    for (int it = row_items[r]; it < row_items[r + 1]; ++it) s += part[(int64_t)it * ell + c];
+    Y[r + I * c] = s;
+  }
+}
+
+__global__ void keep_flags_kernel(const int32_t* __restrict__ key, int64_t n, const int32_t* __restrict__ pos,
+                                  int32_t* __restrict__ flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    flag[e] = pos[key[e]] >= 0 ? 1 : 0;
+}
+
+// stable compaction of the kept nonzeros; mode n's index is renumbered through pos
+__global__ void compact_kernel(SpIdx in, int d, int n, const float* __restrict__ vals, int64_t nnz,
+                               const int32_t* __restrict__ flag, const int32_t* __restrict__ dest,
+                               const int32_t* __restrict__ pos, SpIdx out, float* __restrict__ out_vals) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[e]) continue;
+    const int64_t t = dest[e];
+    for (int k = 0; k < d; ++k) {
+      const int32_t v = in.idx[k][e];
+      const_cast<int32_t*>(out.idx[k])[t] = (k == n) ? pos[v] : v;
+    }
+    out_vals[t] = vals[e];
+  }
+}
+
+__global__ void scatter_core_kernel(SpIdx ix, int d, const float* __restrict__ vals, int64_t nnz,
+                                    double* __restrict__ core) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t off = 0;
+    for (int k = 0; k < d; ++k) off += (int64_t)ix.idx[k][e] * ix.stride[k];
+    core[off] = (double)vals[e];
+  }
+}
+
+__global__ void sumsq_f32_kernel(const float* __restrict__ v, int64_t n, double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s = fma((double)v[e], (double)v[e], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < n; ++k) t += part[k];
+    *out = t;
+  }
+}
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * num_sms())); }
+
+// ---- host: strong RRQR subset selection on Q^T (FP64) ----------------------------------------
+// inv (ell x ell, column-major) of the rows sel of Q (I x ell, column-major); false if singular
+bool invert_rows(const std::vector<double>& Q, int64_t I, int ell, const std::vector<int>& sel,
+                 std::vector<double>& inv) {
+  std::vector<double> M((size_t)ell * ell);
+  for (int a = 0; a < ell; ++a)
+    for (int c = 0; c < ell; ++c) M[a + (size_t)ell * c] = Q[sel[a] + I * c];
+  inv.assign((size_t)ell * ell, 0.0);
+  for (int a = 0; a < ell; ++a) inv[a + (size_t)ell * a] = 1.0;
+  for (int c = 0; c < ell; ++c) {   // Gauss-Jordan, partial pivoting
+    int pr = c;
+    for (int a = c + 1; a < ell; ++a)
+      if (std::fabs(M[a + (size_t)ell * c]) > std::fabs(M[pr + (size_t)ell * c])) pr = a;
+    if (M[pr + (size_t)ell * c] == 0.0) return false;
+    if (pr != c)
+      for (int k = 0; k < ell; ++k) {
+        std::swap(M[c + (size_t)ell * k], M[pr + (size_t)ell * k]);
+        std::swap(inv[c + (size_t)ell * k], inv[pr + (size_t)ell * k]);
+      }
+    const double piv = 1.0 / M[c + (size_t)ell * c];
+    for (int k = 0; k < ell; ++k) {
+      M[c + (size_t)ell * k] *= piv;
+      inv[c + (size_t)ell * k] *= piv;
+    }
+    for (int a = 0; a < ell; ++a) {
+      if (a == c) continue;
+      const double f = M[a + (size_t)ell * c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < ell; ++k) {
+        M[a + (size_t)ell * k] -= f * M[c + (size_t)ell * k];
+        inv[a + (size_t)ell * k] -= f * inv[c + (size_t)ell * k];
+      }
+    }
+  }
+  return true;
+}
+
+// A = Q inv (I x ell)
+void apply_inv(const std::vector<double>& Q, int64_t I, int ell, const std::vector<double>& inv,
+               std::vector<double>& A) {
+  A.assign((size_t)I * ell, 0.0);
+  for (int c = 0; c < ell; ++c)
+    for (int k = 0; k < ell; ++k) {
+      const double f = inv[k + (size_t)ell * c];
+      if (f == 0.0) continue;
+      const double* q = &Q[(size_t)I * k];
+      double* a = &A[(size_t)I * c];
+      for (int64_t i = 0; i < I; ++i) a[i] += q[i] * f;
+    }
+}
+
+rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, double eta, std::vector<int>& sel_out,
+                            std::vector<double>& A) {
+  // column-pivoted Householder QR of Q^T (ell x I): column i of W is row i of Q
+  std::vector<double> W((size_t)ell * I);
+  for (int64_t i = 0; i < I; ++i)
+    for (int c = 0; c < ell; ++c) W[c + (size_t)ell * i] = Q[i + I * c];
+  std::vector<char> taken(I, 0);
+  std::vector<int> sel;
+  std::vector<double> v(ell);
+  for (int s = 0; s < ell; ++s) {
+    int64_t best = -1;
+    double bn = -1.0;
+    for (int64_t i = 0; i < I; ++i) {
+      if (taken[i]) continue;
+      double nrm = 0.0;
+      for (int a = s; a < ell; ++a) nrm += W[a + (size_t)ell * i] * W[a + (size_t)ell * i];
+      if (nrm > bn) {
+        bn = nrm;
+        best = i;
+      }
+    }
+    taken[best] = 1;
+    sel.push_back((int)best);
+    // Householder reflector of W[s:, best], applied to every column
+    double alpha = 0.0;
+    for (int a = s; a < ell; ++a) alpha += W[a + (size_t)ell * best] * W[a + (size_t)ell * best];
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    const double x0 = W[s + (size_t)ell * best];
+    const double beta = x0 >= 0 ? -alpha : alpha;
+    for (int a = s; a < ell; ++a) v[a] = W[a + (size_t)ell * best];
+    v[s] -= beta;
+    double vv = 0.0;
+    for (int a = s; a < ell; ++a) vv += v[a] * v[a];
+    if (vv == 0.0) continue;
+    for (int64_t i = 0; i < I; ++i) {
+      double dot = 0.0;
+      for (int a = s; a < ell; ++a) dot += v[a] * W[a + (size_t)ell * i];
+      const double f = 2.0 * dot / vv;
+      for (int a = s; a < ell; ++a) W[a + (size_t)ell * i] -= f * v[a];
+    }
+  }
+  // swaps while some |A_ij| > eta on an unselected row (largest first, lowest (i, j) on ties)
+  std::vector<double> inv;
+  for (int sw = 0; sw < 100000; ++sw) {
+    if (!invert_rows(Q, I, ell, sel, inv)) {
+      set_error("SP-STHOSVD: the selected rows of Q are singular");
+      return RH_ENUMERIC;
+    }
+    apply_inv(Q, I, ell, inv, A);
+    std::vector<char> in(I, 0);
+    for (int x : sel) in[x] = 1;
+    double amax = 0.0;
+    int64_t bi = -1;
+    int bj = -1;
+    for (int64_t i = 0; i < I; ++i) {
+      if (in[i]) continue;
+      for (int j = 0; j < ell; ++j) {
+        const double a = std::fabs(A[i + (size_t)I * j]);
+        if (a > amax) {
+          amax = a;
+          bi = i;
+          bj = j;
+        }
+      }
+    }
+    if (amax <= eta) break;
+    sel[bj] = (int)bi;
+  }
+  std::sort(sel.begin(), sel.end());
+  if (!invert_rows(Q, I, ell, sel, inv)) {
+    set_error("SP-STHOSVD: the selected rows of Q are singular");
+    return RH_ENUMERIC;
+  }
+  apply_inv(Q, I, ell, inv, A);
+  sel_out = sel;
+  return RH_OK;
+}
+
+struct SpBufs {
+  int32_t *keys_in, *keys_out, *perm_in, *perm_out, *cnt, *flag, *dest, *pos, *row_items;
+  int3* items;
+  double *part, *Y, *Q, *orth, *norm_part;
+  int32_t* idx[2][RH_MAX_ORDER];
+  float* vals[2];
+  void* cub_tmp;
+  size_t cub_bytes;
+  int32_t* info;
+};
+
+struct SpSizes {
+  int64_t nnz, I_max, items_max;
+  int ell_max;
+  size_t orth, cub_bytes;
+};
+
+size_t cub_bytes_for(int64_t nnz) {
+  size_t a = 0, b = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, a, (const int32_t*)nullptr, (int32_t*)nullptr, (const int32_t*)nullptr,
+                                  (int32_t*)nullptr, (int)std::max<int64_t>(nnz, 1), 0, 31, (cudaStream_t)0);
+  cub::DeviceScan::ExclusiveSum(nullptr, b, (const int32_t*)nullptr, (int32_t*)nullptr,
+                                (int)std::max<int64_t>(nnz, 1), (cudaStream_t)0);
+  return std::max(a, b);
+}
+
+SpBufs carve_sp(Arena& ar, int d, const SpSizes& z) {
+  SpBufs b;
+  const size_t n = (size_t)std::max<int64_t>(z.nnz, 1);
+  b.keys_in = ar.take<int32_t>(n);
+  b.keys_out = ar.take<int32_t>(n);
+  b.perm_in = ar.take<int32_t>(n);
+  b.perm_out = ar.take<int32_t>(n);
+  b.flag = ar.take<int32_t>(n);
+  b.dest = ar.take<int32_t>(n);
+  b.cnt = ar.take<int32_t>((size_t)z.I_max + 1);
+  b.pos = ar.take<int32_t>((size_t)z.I_max + 1);
+  b.row_items = ar.take<int32_t>((size_t)z.I_max + 1);
+  b.items = ar.take<int3>((size_t)z.items_max);
+  b.part = ar.take<double>((size_t)z.items_max * z.ell_max);
+  b.Y = ar.take<double>((size_t)z.I_max * z.ell_max);
+  b.Q = ar.take<double>((size_t)z.I_max * z.ell_max);
+  b.orth = ar.take<double>(z.orth);
+  b.norm_part = ar.take<double>(1024);
+  for (int s = 0; s < 2; ++s) {
+    for (int k = 0; k < d; ++k) b.idx[s][k] = ar.take<int32_t>(n);
+    b.vals[s] = ar.take<float>(n);
+  }
+  b.cub_bytes = z.cub_bytes;
+  b.cub_tmp = ar.take<char>(z.cub_bytes);
+  b.info = ar.take<int32_t>(4);
+  return b;
+}
+
+int bits_for(int64_t v) {
+  int b = 1;
+  while (b < 31 && (int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+// Y = G_(n) Omega_n (I x ell, FP64, column-major) from the COO nonzeros (Alg. 6 step 4): stable sort
+// by i_n, work items of at most kItem nonzeros per row, warp partials, FP64 sums in item order.
+rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int ell, int64_t cnnz, const int32_t* key,
+                         const float* vals, uint64_t seed, int32_t tensor_id, int64_t items_max, const SpBufs& b,
+                         double* Y, cudaStream_t st) {
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  // (a) stable sort of the nonzeros by i_n; row counts (an empty tensor has no items: Y = 0)
+  size_t tb = b.cub_bytes;
+  RH_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * (I + 1), st));
+  if (cnnz > 0) {
+    iota_kernel<<<grid_for(cnnz), 256, 0, st>>>(b.perm_in, cnnz);
+    RH_LAUNCH_CHECK();
+    RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, key, b.keys_out, b.perm_in, b.perm_out,
+                                                (int)cnnz, 0, bits_for(I), st));
+    count_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, b.cnt);
+    RH_LAUNCH_CHECK();
+  }
+  std::vector<int32_t> cnt(I);
+  RH_CUDA_TRY(cudaMemcpyAsync(cnt.data(), b.cnt, sizeof(int32_t) * I, cudaMemcpyDeviceToHost, st));
+  RH_CUDA_TRY(cudaStreamSynchronize(st));
+  // (b) work items: each row's run cut into pieces of at most kItem nonzeros
+  std::vector<int3> items;
+  std::vector<int32_t> row_items(I + 1, 0);
+  int64_t off = 0;
+  for (int64_t r = 0; r < I; ++r) {
+    row_items[r] = (int32_t)items.size();
+    for (int64_t a = 0; a < cnt[r]; a += kItem)
+      items.push_back(make_int3((int)r, (int)(off + a), (int)(off + std::min<int64_t>(cnt[r], a + kItem))));
+    off += cnt[r];
+  }
+  row_items[I] = (int32_t)items.size();
+  if ((int64_t)items.size() > items_max) {
+    set_error("SP-STHOSVD: internal item count exceeds the plan");
+    return RH_ENUMERIC;
+  }
+  if (!items.empty())
+    RH_CUDA_TRY(cudaMemcpyAsync(b.items, items.data(), sizeof(int3) * items.size(), cudaMemcpyHostToDevice, st));
+  RH_CUDA_TRY(cudaMemcpyAsync(b.row_items, row_items.data(), sizeof(int32_t) * (I + 1), cudaMemcpyHostToDevice, st));
+  // (c) sketch Y = G_(n) Omega_n (step 4)
+  const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)n;
+  if (!items.empty()) {
+    const int nwarps = (int)std::min<int64_t>((int64_t)items.size(), 64LL * num_sms());
+    sp_sketch_items_kernel<<<(int)ceil_div(nwarps, 8), 256, 0, st>>>(ix, order, vals, b.perm_out, b.items,
+                                                                       (int)items.size(), ell, k0, k1, sid, b.part);
+    RH_LAUNCH_CHECK();
+  }
+  sp_sketch_reduce_kernel<<<grid_for(I * ell), 256, 0, st>>>(b.part, b.row_items, I, ell, Y);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status sp_plan(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks, const rh_options& o,
+                  std::vector<int>& rho, std::vector<int>& ells, SpSizes& z) {
+  RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
+  RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
+  RH_CHECK_ARG(nnz >= 1 && nnz < (int64_t(1) << 31), "nnz must be in [1, 2^31)");
+  RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
+  RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  for (int k = 0; k < order; ++k) {
+    RH_CHECK_ARG(dims[k] >= 1 && dims[k] < (int64_t(1) << 31), "every dimension must be in [1, 2^31)");
+    RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");
+  }
+  rho.resize(order);
+  if (o.rho[0] < 0) {
+    std::iota(rho.begin(), rho.end(), 0);
+    std::stable_sort(rho.begin(), rho.end(), [&](int a, int c) { return dims[a] > dims[c]; });
+  } else {
+    std::vector<int> seen(order, 0);
+    for (int k = 0; k < order; ++k) {
+      RH_CHECK_ARG(o.rho[k] >= 0 && o.rho[k] < order && !seen[o.rho[k]], "rho must be a permutation of 0..order-1");
+      seen[o.rho[k]] = 1;
+      rho[k] = o.rho[k];
+    }
+  }
+  std::vector<int64_t> cur(dims, dims + order);
+  ells.assign(order, 0);
+  z.nnz = nnz;
+  z.I_max = 1;
+  z.ell_max = 1;
+  z.orth = 1;
+  for (int j = 0; j < order; ++j) {
+    const int n = rho[j];
+    int64_t M = 1;
+    for (int k = 0; k < order; ++k)
+      if (k != n) M *= cur[k];
+    int64_t ell = (int64_t)ranks[n] + o.p;
+    const int64_t lim = std::min<int64_t>(cur[n], M);
+    if (ell >= lim) {   // Alg. 6 requires r + p < min(I_n, prod of the other sizes)
+      if (!o.clamp) {
+        set_error("invalid argument: r_n + p = " + std::to_string(ell) + " must be < min(I_n, prod of the other " +
+                  "sizes) = " + std::to_string(lim) + " for mode " + std::to_string(n));
+        return RH_EINVAL;
+      }
+      ell = lim - 1;
+    }
+    if (ell < 1) {
+      set_error("invalid argument: mode " + std::to_string(n) + " is too small for SP-STHOSVD");
+      return RH_EINVAL;
+    }
+    if (ell > RH_MAX_ELL) {
+      set_error("unsupported: r_n + p exceeds RH_MAX_ELL (64)");
+      return RH_EUNSUPPORTED;
+    }
+    ells[n] = (int)ell;
+    z.I_max = std::max(z.I_max, cur[n]);
+    z.ell_max = std::max(z.ell_max, (int)ell);
+    z.orth = std::max(z.orth, orth_workspace_elems(cur[n], (int)ell));
+    cur[n] = ell;
+  }
+  z.items_max = nnz / kItem + z.I_max + 1;
+  z.cub_bytes = cub_bytes_for(nnz);
+  return RH_OK;
+}
+
+}  // namespace
+}  // namespace rh
+
+using namespace rh;
+
+extern "C" {
+
+size_t sp_sthosvd_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks,
+                                     const rh_options* opts) {
+  rh_options o;
+  rh_options_default(&o);
+  if (opts) o = *opts;
+  std::vector<int> rho, ells;
+  SpSizes z;
+  if (sp_plan(order, dims, nnz, ranks, o, rho, ells, z) != RH_OK) return 0;
+  Arena ar(nullptr);
+  carve_sp(ar, order, z);
+  return ar.used;
+}
+
+rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
+                         const float* vals, const int32_t* ranks, const rh_options* opts, double* const* factors,
+                         int32_t* const* selected, double* core, double* norms, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  clear_error();
+  rh_options o;
+  rh_options_default(&o);
+  if (opts) o = *opts;
+  std::vector<int> rho, ells;
+  SpSizes z;
+  rh_status s = sp_plan(order, dims, nnz, ranks, o, rho, ells, z);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(idx != nullptr && vals != nullptr && factors != nullptr && core != nullptr,
+               "idx, vals, factors and core must be non-NULL");
+  for (int k = 0; k < order; ++k) {
+    RH_CHECK_ARG(idx[k] != nullptr && factors[k] != nullptr, "every idx[n] and factors[n] must be non-NULL");
+  }
+  Arena meas(nullptr);
+  carve_sp(meas, order, z);
+  if (workspace == nullptr || workspace_bytes < meas.used) {
+    set_error("workspace too small: need " + std::to_string(meas.used) + " bytes");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  SpBufs b = carve_sp(ar, order, z);
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t k0 = (uint32_t)(o.seed & 0xFFFFFFFFu), k1 = (uint32_t)(o.seed >> 32);
+
+  // the working copy of the tensor (set 0) and ||X||^2
+  for (int k = 0; k < order; ++k)
+    RH_CUDA_TRY(cudaMemcpyAsync(b.idx[0][k], idx[k], sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
+  RH_CUDA_TRY(cudaMemcpyAsync(b.vals[0], vals, sizeof(float) * nnz, cudaMemcpyDeviceToDevice, st));
+  if (norms) {
+    const int nb = (int)std::min<int64_t>(ceil_div(nnz, 256), 1024);
+    sumsq_f32_kernel<<<nb, 256, 0, st>>>(b.vals[0], nnz, b.norm_part);
+    RH_LAUNCH_CHECK();
+    sum_parts_kernel<<<1, 32, 0, st>>>(b.norm_part, nb, norms);
+    RH_LAUNCH_CHECK();
+  }
+  std::vector<int64_t> cur(dims, dims + order);
+  int set = 0;
+  int64_t cnnz = nnz;
+  for (int j = 0; j < order; ++j) {
+    const int n = rho[j];
+    const int ell = ells[n];
+    const int64_t I = cur[n];
+    SpIdx ix;
+    int64_t stride = 1;
+    for (int k = 0; k < order; ++k) {
+      ix.idx[k] = b.idx[set][k];
+      if (k == n) {
+        ix.stride[k] = 0;
+      } else {
+        ix.stride[k] = stride;
+        stride *= cur[k];
+      }
+    }
+    for (int k = order; k < RH_MAX_ORDER; ++k) {
+      ix.idx[k] = nullptr;
+      ix.stride[k] = 0;
+    }
+    if ((s = sp_sketch_mode(ix, order, n, I, ell, cnnz, b.idx[set][n], b.vals[set], o.seed, o.tensor_id, z.items_max,
+                            b, b.Y, st)) != RH_OK)
+      return s;
+    // (d) thin QR (step 5)
+    RH_CUDA_TRY(cudaMemsetAsync(b.info, 0, sizeof(int32_t), st));
+    if ((s = launch_orthonormalize(I, ell, b.Y, b.Q, b.info, b.orth, st, false)) != RH_OK) return s;
+    // (e) strong RRQR selection and A_n = Q (P^T Q)^{-1} on the host (steps 6-7)
+    std::vector<double> Qh((size_t)I * ell);
+    RH_CUDA_TRY(cudaMemcpyAsync(Qh.data(), b.Q, sizeof(double) * I * ell, cudaMemcpyDeviceToHost, st));
+    RH_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> sel;
+    std::vector<double> A;
+    if ((s = srrqr_select_host(Qh, I, ell, 2.0, sel, A)) != RH_OK) return s;
+    RH_CUDA_TRY(cudaMemcpyAsync(factors[n], A.data(), sizeof(double) * I * ell, cudaMemcpyHostToDevice, st));
+    if (selected && selected[n])
+      RH_CUDA_TRY(cudaMemcpyAsync(selected[n], sel.data(), sizeof(int32_t) * ell, cudaMemcpyHostToDevice, st));
+    // (f) G_(n) <- P^T G_(n): keep the selected slices, renumber mode n (step 8)
+    std::vector<int32_t> pos(I, -1);
+    for (int a = 0; a < ell; ++a) pos[sel[a]] = a;
+    RH_CUDA_TRY(cudaMemcpyAsync(b.pos, pos.data(), sizeof(int32_t) * I, cudaMemcpyHostToDevice, st));
+    if (cnnz > 0) {
+      keep_flags_kernel<<<grid_for(cnnz), 256, 0, st>>>(b.idx[set][n], cnnz, b.pos, b.flag);
+      RH_LAUNCH_CHECK();
+      size_t tb = b.cub_bytes;
+      RH_CUDA_TRY(cub::DeviceScan::ExclusiveSum(b.cub_tmp, tb, b.flag, b.dest, (int)cnnz, st));
+      int32_t last_dest = 0, last_flag = 0;
+      RH_CUDA_TRY(cudaMemcpyAsync(&last_dest, b.dest + cnnz - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      RH_CUDA_TRY(cudaMemcpyAsync(&last_flag, b.flag + cnnz - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      SpIdx out;
+      for (int k = 0; k < RH_MAX_ORDER; ++k) {
+        out.idx[k] = k < order ? b.idx[1 - set][k] : nullptr;
+        out.stride[k] = 0;
+      }
+      compact_kernel<<<grid_for(cnnz), 256, 0, st>>>(ix, order, n, b.vals[set], cnnz, b.flag, b.dest, b.pos, out,
+                                                      b.vals[1 - set]);
+      RH_LAUNCH_CHECK();
+      RH_CUDA_TRY(cudaStreamSynchronize(st));
+      cnnz = (int64_t)last_dest + last_flag;
+    }
+    set = 1 - set;
+    cur[n] = ell;
+  }
+  // dense ell_1 x ... x ell_d core of the surviving entries
+  int64_t ncore = 1;
+  for (int k = 0; k < order; ++k) ncore *= cur[k];
+  RH_CUDA_TRY(cudaMemsetAsync(core, 0, sizeof(double) * ncore, st));
+  if (cnnz > 0) {
+    SpIdx ix;
+    int64_t stride = 1;
+    for (int k = 0; k < RH_MAX_ORDER; ++k) {
+      ix.idx[k] = k < order ? b.idx[set][k] : nullptr;
+      ix.stride[k] = k < order ? stride : 0;
+      if (k < order) stride *= cur[k];
+    }
+    scatter_core_kernel<<<grid_for(cnnz), 256, 0, st>>>(ix, order, b.vals[set], cnnz, core);
+    RH_LAUNCH_CHECK();
+  }
+  if (norms) {
+    if ((s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
+  }
+  RH_CUDA_TRY(cudaStreamSynchronize(st));
+  return RH_OK;
+}
+
+size_t rhosvd_sketch_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, int32_t mode, int32_t ell) {
+  if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode < 0 || mode >= order || mode >= 16) return 0;
+  if (nnz < 0 || nnz >= (int64_t(1) << 31) || ell < 1 || ell > RH_MAX_ELL) return 0;
+  for (int k = 0; k < order; ++k)
+    if (dims[k] < 1 || dims[k] >= (int64_t(1) << 31)) return 0;
+  SpSizes z;
+  z.nnz = nnz;
+  z.I_max = dims[mode];
+  z.ell_max = ell;
+  z.orth = 1;
+  z.items_max = nnz / kItem + z.I_max + 1;
+  z.cub_bytes = cub_bytes_for(nnz);
+  Arena ar(nullptr);
+  carve_sp(ar, order, z);
+  return ar.used;
+}
+
+rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
+                            const float* vals, int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id, double* Y,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  const size_t need = rhosvd_sketch_coo_workspace_size(order, dims, nnz, mode, ell);
+  RH_CHECK_ARG(need > 0, "bad order, dims, nnz, mode or ell");
+  RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  RH_CHECK_ARG(idx != nullptr && Y != nullptr && (nnz == 0 || vals != nullptr), "idx, vals and Y must be non-NULL");
+  for (int k = 0; k < order; ++k) RH_CHECK_ARG(nnz == 0 || idx[k] != nullptr, "every idx[n] must be non-NULL");
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    return RH_ENOMEM;
+  }
+  SpSizes z;
+  z.nnz = nnz;
+  z.I_max = dims[mode];
+  z.ell_max = ell;
+  z.orth = 1;
+  z.items_max = nnz / kItem + z.I_max + 1;
+  z.cub_bytes = cub_bytes_for(nnz);
+  Arena ar(workspace);
+  const SpBufs b = carve_sp(ar, order, z);
+  SpIdx ix;
+  int64_t stride = 1;
+  for (int k = 0; k < RH_MAX_ORDER; ++k) {
+    ix.idx[k] = k < order ? idx[k] : nullptr;
+    ix.stride[k] = 0;
+    if (k < order && k != mode) {
+      ix.stride[k] = stride;
+      stride *= dims[k];
+    }
+  }
+  return sp_sketch_mode(ix, order, mode, dims[mode], ell, nnz, nnz ? idx[mode] : nullptr, vals, seed, tensor_id,
+                        z.items_max, b, Y, (cudaStream_t)stream);
+}
+
+}  // extern "C"
