@@ -71,6 +71,10 @@ enum {
  *   RH_F32_BF16X2   a plain FP32 array, read as RH_BF16X2: the kernels of the first mode split
  *                   each tile into head and tail in shared memory as they load it, so the results
  *                   are bit-identical to RH_BF16X2 of rh_split_bf16x2(X) without the split pass.
+ *                   In rsthosvd a first mode that the tensor-core kernels do not cover (not mode 0,
+ *                   or I_0 % 8 != 0, I_0 > 1024) runs in FP32 on the CUDA cores instead of being
+ *                   rejected, so the form accepts any FP32 tensor (info bit 4 shows which modes
+ *                   ran on the tensor cores).
  * The BF16 forms use the tensor cores (tcgen05) for the first mode's sketch and mode product, with
  * Omega rounded to BF16 (ties to even) and FP32 accumulation; the intermediate cores are FP32.  In
  * R-STHOSVD (truncating) the core after a mode is written with the next mode fastest when that
@@ -253,6 +257,37 @@ size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype
 rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
                    const rh_options* opts, double* const* factors, double* core, double* norms,
                    int32_t* info, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rsthosvd_batched -- R-STHOSVD (Alg. 3) applied independently to each of ``count`` tensors of
+ * different orders and sizes in one call (each tensor is decomposed exactly as by rsthosvd).
+ *   orders   host array of ``count`` tensor orders (1 .. 8).
+ *   dims     host array of sum(orders) sizes, tensor i's sizes after those of tensors 0 .. i-1.
+ *   ranks    host array laid out like dims.
+ *   X        host array of ``count`` device pointers (all tensors of one dtype, column-major).
+ *   factors  host array of sum(orders) device pointers, laid out like dims (FP64 as in rsthosvd).
+ *   cores    host array of ``count`` device pointers (FP64 cores as in rsthosvd).
+ *   norms    optional device buffer of 2 * count FP64 values (tensor i at 2 i); info optional
+ *            device int32 array laid out like dims.
+ *   opts     shared by every tensor; tensor i draws Omega with tensor_id = opts->tensor_id + i.
+ *            The processing order must be the default (opts->rho[0] < 0).
+ *   streams  number of internal streams (0 = min(8, count), at most 32).  The caller's stream is
+ *            forked into them with an event, tensors are placed largest first (by element count)
+ *            on the least-loaded stream, and every stream is joined back into ``stream`` before
+ *            the call returns; no host synchronisation, so the call is CUDA-graph capturable.
+ *   workspace  one slice per internal stream, each the largest rsthosvd_workspace_size of the
+ *            batch (rounded to 256 B); rsthosvd_batched_workspace_size returns the total (0 on an
+ *            invalid request).  The placement, and so the result, does not depend on timing:
+ *            each tensor's result equals that of a single rsthosvd call.
+ *   Errors: RH_EINVAL names the first invalid tensor; a failing tensor stops the enqueueing of
+ *   later tensors (earlier ones still run) and its message is returned.
+ */
+size_t rsthosvd_batched_workspace_size(int32_t count, const int32_t* orders, const int64_t* dims, int32_t dtype,
+                                       const int32_t* ranks, const rh_options* opts, int32_t streams);
+rh_status rsthosvd_batched(int32_t count, const int32_t* orders, const int64_t* dims, int32_t dtype,
+                           const void* const* X, const int32_t* ranks, const rh_options* opts,
+                           double* const* factors, double* const* cores, double* norms, int32_t* info,
+                           int32_t streams, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * rhosvd -- R-HOSVD (Alg. 2): RandSVD (Alg. 1) of every unfolding X_(n) of the input with its own

@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import RH_F32, RH_F64, RhError, check, i32_array, i64_array, lib, make_options
 
 __all__ = ["omega", "rhosvd_sketch", "orthonormalize", "mode_product", "left_svd", "core_ttm", "tucker_residual",
-           "rsthosvd", "rhosvd", "RhError", "version"]
+           "rsthosvd", "rhosvd", "rsthosvd_batched", "RsthosvdBatchedCall", "RhError", "version"]
 
 
 def _torch():
@@ -456,6 +456,85 @@ def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, tr
     call = RsthosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
                         truncate=truncate, device=X.device)
     return call.run(X)
+
+
+class RsthosvdBatchedCall:
+    """A prepared ``rsthosvd_batched`` call over tensors of shapes ``dims_list`` (one list of sizes
+    per tensor) and ``ranks_list``; all tensors share ``dtype`` and the options, tensor i draws its
+    Omega with tensor_id + i.  ``run(Xs)`` enqueues the whole batch on the current stream and
+    returns one Tucker per tensor (views of buffers allocated once here)."""
+
+    def __init__(self, dims_list, ranks_list, dtype, p=5, seed=0, tensor_id=0, clamp=False, truncate=True,
+                 streams=0, device="cuda"):
+        torch = _torch()
+        if len(dims_list) != len(ranks_list) or not dims_list:
+            raise ValueError("dims_list and ranks_list must be non-empty and of equal length")
+        self.count = len(dims_list)
+        self.dims_list = [[int(x) for x in d] for d in dims_list]
+        if isinstance(dtype, str):
+            self.dt = _FORMS[dtype]
+            if dtype == "bf16x2":
+                raise ValueError("batched calls take float32/float64 or the f32_bf16x2 and bf16 forms")
+        else:
+            self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, clamp=clamp, truncate=truncate)
+        self.orders = i32_array([len(d) for d in self.dims_list])
+        self.da = i64_array([x for d in self.dims_list for x in d])
+        self.ra = i32_array([int(r) for rk in ranks_list for r in rk])
+        self.streams = int(streams)
+        self.ws_bytes = lib().rsthosvd_batched_workspace_size(self.count, self.orders, self.da, self.dt, self.ra,
+                                                              ctypes.byref(self.opts), self.streams)
+        if self.ws_bytes == 0:
+            check(lib().rsthosvd_batched(self.count, self.orders, self.da, self.dt, None, self.ra,
+                                         ctypes.byref(self.opts), None, None, None, None, self.streams, None, 0,
+                                         None))
+            raise ValueError("invalid batched request")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.core_dims, self.factors, self.cores = [], [], []
+        probe = RsthosvdCall.__new__(RsthosvdCall)
+        for dims, ranks in zip(self.dims_list, ranks_list):
+            probe.dims = dims
+            ko = RsthosvdCall._out_ranks(probe, ranks, p, clamp, truncate, None)
+            self.core_dims.append(ko)
+            self.factors.append([torch.empty((ko[n], dims[n]), dtype=torch.float64, device=device)
+                                 for n in range(len(dims))])
+            ncore = 1
+            for k in ko:
+                ncore *= k
+            self.cores.append(torch.empty(ncore, dtype=torch.float64, device=device))
+        nf = sum(len(d) for d in self.dims_list)
+        self.norms = torch.empty(2 * self.count, dtype=torch.float64, device=device)
+        self.info = torch.zeros(nf, dtype=torch.int32, device=device)
+        self.fptrs = (ctypes.c_void_p * nf)(*[f.data_ptr() for fs in self.factors for f in fs])
+        self.cptrs = (ctypes.c_void_p * self.count)(*[c.data_ptr() for c in self.cores])
+        self.device = torch.device(device)
+
+    def run(self, Xs, norms=True):
+        if len(Xs) != self.count:
+            raise ValueError(f"expected {self.count} tensors, got {len(Xs)}")
+        factor = 1
+        for X, dims in zip(Xs, self.dims_list):
+            _check_input(X, dims, factor)
+        xptrs = (ctypes.c_void_p * self.count)(*[X.data_ptr() for X in Xs])
+        check(lib().rsthosvd_batched(self.count, self.orders, self.da, self.dt, xptrs, self.ra, ctypes.byref(self.opts),
+                                     self.fptrs, self.cptrs, _ptr(self.norms) if norms else None, _ptr(self.info),
+                                     self.streams, _ptr(self.ws), self.ws_bytes, _stream(self.device)))
+        out, off = [], 0
+        for i, dims in enumerate(self.dims_list):
+            d = len(dims)
+            out.append(Tucker(self.factors[i], self.cores[i], self.core_dims[i], self.norms[2 * i:2 * i + 2],
+                              self.info[off:off + d]))
+            off += d
+        return out
+
+
+def rsthosvd_batched(Xs, dims_list, ranks_list, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, form=None,
+                     streams=0):
+    """R-STHOSVD (Alg. 3) of every tensor in ``Xs`` (flat column-major, sizes ``dims_list[i]``) in
+    one batched call; returns a list of Tucker results."""
+    call = RsthosvdBatchedCall(dims_list, ranks_list, form or Xs[0].dtype, p=p, seed=seed, tensor_id=tensor_id,
+                               clamp=clamp, truncate=truncate, streams=streams, device=Xs[0].device)
+    return call.run(Xs)
 
 
 class RsthosvdHostCall:

@@ -71,6 +71,9 @@ SIGNATURES = {
     "sp_sthosvd_coo": (_I32, [_I32, _P, _I64, _P, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
     "rh_tucker_residual_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
     "rh_tucker_residual": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "rsthosvd_batched_workspace_size": (_SZ, [_I32, _P, _P, _I32, _P, ctypes.POINTER(RhOptions), _I32]),
+    "rsthosvd_batched": (_I32, [_I32, _P, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _I32, _P,
+                                _SZ, _P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
     "rsthosvd_host": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _SZ, _P]),
 }

@@ -125,13 +125,16 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
   }
   (void)tsz;
   if (bf16_form(dtype)) {
-    // the first processed mode runs on the tensor cores over the BF16 pieces
+    // The first processed mode runs on the tensor cores over the BF16 pieces.  FP32 input split
+    // on the fly can also take the FP32 CUDA-core path for a first mode the tensor-core kernels
+    // do not cover (later modes still go to the tensor cores where their shape allows).
     const Step& s0 = pl.steps[0];
-    if (s0.mode != 0 || !sketch_tc_supported(s0.v, s0.ell) || !ttm_tc_supported(s0.v, s0.ell)) {
+    const bool s0_tc = s0.mode == 0 && sketch_tc_supported(s0.v, s0.ell) && ttm_tc_supported(s0.v, s0.ell);
+    if (!s0_tc && dtype != RH_F32_BF16X2) {
       set_error("unsupported: the BF16 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024, r + p <= 64");
       return RH_EUNSUPPORTED;
     }
-    pl.steps[0].tc = true;
+    pl.steps[0].tc = s0_tc;
     pl.max_pnorm = std::max<size_t>(pl.max_pnorm, 1024);   // partials of the norm over the BF16 pieces
     pl.dtype = RH_F32;        // intermediates
     pl.in_form = dtype;

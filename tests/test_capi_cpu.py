@@ -118,3 +118,48 @@ def test_omega_and_sketch_argument_checks(L):
     assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 2, 4, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 1
     assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 0, 65, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 1
     assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 0, 4, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 2
+
+
+def _batched_ws(L, dims_list, ranks_list, streams=0, **kw):
+    from paper_1905_07311_gb300 import _lib
+
+    o = _lib.make_options(**kw)
+    return L.rsthosvd_batched_workspace_size(len(dims_list), _lib.i32_array([len(d) for d in dims_list]),
+                                             _lib.i64_array([x for d in dims_list for x in d]), 0,
+                                             _lib.i32_array([r for rk in ranks_list for r in rk]), ctypes.byref(o),
+                                             streams)
+
+
+def test_batched_workspace_is_one_slice_per_stream(L):
+    dims_list = [[30, 20, 10], [40, 12, 11, 9], [16, 16, 16]]
+    ranks_list = [[4, 4, 4], [3, 3, 3, 3], [5, 5, 5]]
+    one = max(_ws(L, d, r, p=5) for d, r in zip(dims_list, ranks_list))
+    slice_ = (one + 255) // 256 * 256
+    assert _batched_ws(L, dims_list, ranks_list, streams=1, p=5) == slice_
+    assert _batched_ws(L, dims_list, ranks_list, streams=2, p=5) == 2 * slice_
+    # streams are capped at the tensor count, 0 = min(8, count)
+    assert _batched_ws(L, dims_list, ranks_list, streams=16, p=5) == 3 * slice_
+    assert _batched_ws(L, dims_list, ranks_list, streams=0, p=5) == 3 * slice_
+
+
+def test_batched_argument_checks(L):
+    from paper_1905_07311_gb300 import _lib
+
+    dims_list = [[30, 20, 10], [10, 40, 40]]
+    ranks_list = [[4, 4, 4], [8, 4, 4]]                 # tensor 1 breaks r + p <= I_n at p = 5
+    assert _batched_ws(L, dims_list, ranks_list, p=5) == 0
+    assert _batched_ws(L, dims_list, ranks_list, p=5, clamp=True) > 0
+    o = _lib.make_options(p=5)
+    xs = (ctypes.c_void_p * 2)(1, 1)
+    fs = (ctypes.c_void_p * 6)(*([1] * 6))
+    cs = (ctypes.c_void_p * 2)(1, 1)
+    code = L.rsthosvd_batched(2, _lib.i32_array([3, 3]), _lib.i64_array([30, 20, 10, 10, 40, 40]), 0, xs,
+                              _lib.i32_array([4, 4, 4, 8, 4, 4]), ctypes.byref(o), fs, cs, None, None, 0, None, 0,
+                              None)
+    assert code == 1 and L.rh_last_error().decode().startswith("tensor 1:")
+    # an order outside [1, 8], no tensors, or too many streams
+    assert _batched_ws(L, [[4] * 9], [[1] * 9], p=1) == 0
+    assert L.rsthosvd_batched_workspace_size(0, None, None, 0, None, None, 0) == 0
+    assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], streams=64, p=5) > 0    # capped at count = 1
+    # a custom processing order is not accepted for a batch
+    assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], p=5, rho=[2, 1, 0]) == 0

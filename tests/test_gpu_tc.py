@@ -209,3 +209,39 @@ def test_rsthosvd_f32_split_is_bit_identical_to_pieces(rh, shape, ranks, p):
     assert torch.equal(Tp[3], Tf.core)
     assert Tp[4][1].item() == Tf.norms[1].item()
     assert abs(Tp[4][0].item() - Tf.norms[0].item()) <= 66 * 2.0 ** -24 * Tp[4][0].item()
+
+
+# A first mode outside the tensor-core kernels (I_0 % 8 != 0, or another mode processed first)
+# runs in FP32 on the CUDA cores under RH_F32_BF16X2; the modes after it still go to the tensor
+# cores where the core has a unit-stride view.  The oracle sees the exact FP32 input and rounds
+# Omega to BF16 on exactly the modes that report info bit 4.  Tolerances as for the two-piece form.
+@pytest.mark.parametrize("shape,ranks,p,rho,tc_modes", [((90, 64, 40), (6, 5, 4), 5, [0, 1, 2], [1]),
+                                                        ((60, 128, 50), (5, 6, 4), 5, None, []),
+                                                        ((17, 24, 23, 16), (4, 4, 4, 4), 3, [0, 1, 2, 3], [1])])
+def test_rsthosvd_f32_split_first_mode_on_cuda_cores(rh, shape, ranks, p, rho, tc_modes):
+    from oracle import tucker as otk
+    from oracle.tensor import rel_error
+    from workloads import lowrank_plus_noise_np
+
+    d = len(shape)
+    X = lowrank_plus_noise_np(list(shape), [max(ranks) + 2] * d, 0.8, 1e-3, seed=23).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    T = rh.rsthosvd(Xd, list(shape), list(ranks), p=p, seed=5, rho=rho, form="f32_bf16x2", clamp=True)
+    torch.cuda.synchronize()
+    info = T.info.cpu().numpy().tolist()
+    assert [m for m in range(d) if info[m] & 4] == tc_modes, info
+    Xe = X.astype(np.float64)
+    rnd = {m: "bf16" for m in tc_modes}
+    out = otk.rsthosvd(Xe, list(ranks), p, 5, rho=rho, omega_round=rnd, record=True, clamp=True)
+    A = [f.cpu().numpy().T for f in T.factors]
+    G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
+    e_g = rel_error(Xe, G, A)
+    e_o = rel_error(Xe, out["core"], out["factors"])
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+    for rec in out["records"]:
+        m = rec["mode"]
+        sv = rec["sv_B"]
+        k = max(1, int(np.sum(sv >= 0.05 * sv[0])))
+        U = out["factors"][m][:, :k]
+        Qa, _ = np.linalg.qr(A[m])
+        assert np.linalg.norm(U - Qa @ (Qa.T @ U), 2) <= 1e-3, m

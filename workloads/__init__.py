@@ -135,3 +135,19 @@ def zipf_coo(dims, nnz, s, lam, seed, batch=None):
         rem = rem % mult[n]
     vals = np.log(1.0 + rs.poisson(lam, nnz).astype(np.float64) + 1.0).astype(np.float32)
     return idx, vals
+
+
+def batch_recipe(count=512, seed=4, orders=(3, 4, 5), size_range=(16, 96), rank_range=(4, 16)):
+    """Shapes and ranks of the batched workload: ``count`` tensors, order uniform in ``orders``, every
+    mode size uniform in ``size_range``, every rank uniform in ``rank_range`` capped at the mode size
+    (and at the size rule r + p <= prod of the other sizes is left to the caller's clamp).  Each
+    tensor i is then ``lowrank_plus_noise`` with core sizes = its ranks, decay 0.9, noise 1e-3 and
+    seed ``seed * 100003 + i``.  Returns a list of (dims, ranks, data_seed)."""
+    rs = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        d = int(rs.choice(orders))
+        dims = [int(v) for v in rs.integers(size_range[0], size_range[1] + 1, size=d)]
+        ranks = [int(min(r, I)) for r, I in zip(rs.integers(rank_range[0], rank_range[1] + 1, size=d), dims)]
+        out.append((dims, ranks, int(seed) * 100003 + i))
+    return out
