@@ -75,13 +75,28 @@ enum {
  *                   or I_0 % 8 != 0, I_0 > 1024) runs in FP32 on the CUDA cores instead of being
  *                   rejected, so the form accepts any FP32 tensor (info bit 4 shows which modes
  *                   ran on the tensor cores).
+ *   RH_FP8_E4M3     a tensor stored in FP8 E4M3 (OCP FP8: bias 7, max 448, no infinities) with one
+ *                   FP32 scale per 128 bytes of storage.  Buffer layout (see rh_fp8_layout): the
+ *                   E4M3 bytes column-major with the mode-1 fibres at a stride of ld = I_1 rounded up
+ *                   to 16 (padding bytes are ignored), ld x prod_{k>1} I_k bytes, then, from the next
+ *                   16-byte boundary, the FP32 scales: element (i, p) of X_(1) has the value
+ *                   fl32(e4m3[i + ld p] * scales[(i + ld p) / 128]) (FP32 product, ties to even).
+ *                   The kernels of the first mode dequantize each tile in shared memory and split it
+ *                   as RH_F32_BF16X2 does, so the results are bit-identical to RH_F32_BF16X2 on the
+ *                   dequantized FP32 tensor; the first mode must run on the tensor cores.
  * The BF16 forms use the tensor cores (tcgen05) for the first mode's sketch and mode product, with
  * Omega rounded to BF16 (ties to even) and FP32 accumulation; the intermediate cores are FP32.  In
  * R-STHOSVD (truncating) the core after a mode is written with the next mode fastest when that
  * mode is the smallest other one, and that mode then runs on the tensor cores too (its FP32 core
  * split on the fly, Omega in BF16) if I_n % 8 == 0, I_n <= 1024 and r + p <= 64; the other modes
  * run in FP32 on the CUDA cores.  info bit 4 marks the modes that ran on the tensor cores. */
-enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4 };
+enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4, RH_FP8_E4M3 = 5 };
+
+/* rh_fp8_layout -- storage of an RH_FP8_E4M3 tensor with sizes dims (see above): *ld = the stride
+ * of the mode-1 fibres in bytes, *scale_offset = the byte offset of the scales, *nscales = their
+ * count, *bytes = the whole buffer.  Any output pointer may be NULL.  RH_EINVAL on bad sizes. */
+rh_status rh_fp8_layout(int32_t order, const int64_t* dims, int64_t* ld, size_t* scale_offset, size_t* nscales,
+                        size_t* bytes);
 
 /* Options of the fixed-rank algorithms (Alg. 2, Alg. 3). */
 typedef struct rh_options {

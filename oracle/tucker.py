@@ -256,14 +256,21 @@ def adapt_range_finder(Gm, tol, b, p, omega_cols, cap=None):
     return A, {"k": k_found, "ell": Q.shape[1], "rank": r, "sv_B": s, "res2": res2}
 
 
-def _omega_cols_fn(seed, tensor_id, mode, nrows):
+def _omega_cols_fn(seed, tensor_id, mode, nrows, omega_round=None):
     cache = {}
+    if isinstance(omega_round, dict):
+        omega_round = omega_round.get(mode)
 
     def cols(c0, c1):
         need = c1
         if cache.get("ell", 0) < need:
             ell = max(need, 2 * cache.get("ell", 0), 8)
-            cache["om"] = rng.omega(seed, tensor_id, mode, np.arange(nrows, dtype=np.int64), ell).astype(np.float64)
+            om = rng.omega(seed, tensor_id, mode, np.arange(nrows, dtype=np.int64), ell)
+            if omega_round == "bf16":
+                om = rng.round_bf16(om)
+            elif omega_round is not None:
+                raise ValueError(omega_round)
+            cache["om"] = om.astype(np.float64)
             cache["ell"] = ell
         return cache["om"][:, c0:c1]
 
@@ -285,11 +292,12 @@ def adaptive_rhosvd(X, eps, b, p, seed, tensor_id=0, max_ranks=None):
     return {"core": multi_ttm(X, A, transpose=True), "factors": A, "infos": infos}
 
 
-def adaptive_rsthosvd(X, eps, b, p, seed, rho=None, tensor_id=0, max_ranks=None):
+def adaptive_rsthosvd(X, eps, b, p, seed, rho=None, tensor_id=0, max_ranks=None, omega_round=None):
     """Alg. 5: G = X; for j in rho: A = AdaptRangeFinder(G_(j), eps ||X|| / sqrt(d), b); G <- A^T G_(j).
 
     The tolerance is absolute, eps ||X||_F / sqrt(d) with the norm of the input X,
-    so that the successive iterates obey the bound stated before Alg. 5.
+    so that the successive iterates obey the bound stated before Alg. 5.  ``omega_round`` as in
+    omega_matrix (per-mode BF16 rounding of the normals).
     """
     X = np.asarray(X, dtype=np.float64)
     d = X.ndim
@@ -301,7 +309,8 @@ def adaptive_rsthosvd(X, eps, b, p, seed, rho=None, tensor_id=0, max_ranks=None)
     for n in rho:
         Gm = unfold(G, n)
         cap = None if max_ranks is None else max_ranks[n]
-        A[n], info = adapt_range_finder(Gm, tol, b, p, _omega_cols_fn(seed, tensor_id, n, Gm.shape[1]), cap)
+        A[n], info = adapt_range_finder(Gm, tol, b, p, _omega_cols_fn(seed, tensor_id, n, Gm.shape[1], omega_round),
+                                        cap)
         infos.append(info)
         G = ttm(G, A[n].T, n)
     return {"core": G, "factors": A, "infos": infos, "rho": rho}

@@ -12,7 +12,7 @@ import ctypes
 from . import _lib
 from ._lib import RH_F32, RH_F64, RhError, check, i32_array, i64_array, lib, make_options
 
-__all__ = ["omega", "rhosvd_sketch", "orthonormalize", "mode_product", "left_svd", "core_ttm", "tucker_residual",
+__all__ = ["fp8_layout", "omega", "rhosvd_sketch", "orthonormalize", "mode_product", "left_svd", "core_ttm", "tucker_residual",
            "rsthosvd", "rhosvd", "rsthosvd_batched", "RsthosvdBatchedCall", "RhError", "version"]
 
 
@@ -54,19 +54,31 @@ def _check_input(X, dims, factor=1):
     return torch
 
 
-_FORMS = {"bf16": 2, "bf16x2": 3, "f32_bf16x2": 4}
+_FORMS = {"bf16": 2, "bf16x2": 3, "f32_bf16x2": 4, "fp8_e4m3": 5}
 
 
 def _piece_form(pieces):
-    """dtype code of a tensor-core input: pieces=2 (split_bf16x2 output), 1 (BF16 bits) or "f32"
-    (a plain FP32 tensor split on the fly, RH_F32_BF16X2)."""
+    """dtype code of a tensor-core input: pieces=2 (split_bf16x2 output), 1 (BF16 bits), "f32"
+    (a plain FP32 tensor split on the fly, RH_F32_BF16X2) or "fp8" (an RH_FP8_E4M3 buffer)."""
     if pieces == "f32":
         return _lib.RH_F32_BF16X2
+    if pieces == "fp8":
+        return _lib.RH_FP8_E4M3
     return _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
 
 
 def version():
     return lib().rh_version().decode()
+
+
+def fp8_layout(dims):
+    """Storage of an RH_FP8_E4M3 tensor with sizes ``dims``: dict with ``ld`` (stride of the mode-1
+    fibres in bytes), ``scale_offset`` (byte offset of the FP32 scales), ``nscales`` and ``bytes``."""
+    ld = ctypes.c_int64()
+    off, ns, nb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    check(lib().rh_fp8_layout(len(dims), i64_array(dims), ctypes.byref(ld), ctypes.byref(off), ctypes.byref(ns),
+                              ctypes.byref(nb)))
+    return {"ld": ld.value, "scale_offset": off.value, "nscales": ns.value, "bytes": nb.value}
 
 
 def omega(seed, tensor_id, mode, row0, nrows, ell, device="cuda"):
@@ -305,7 +317,12 @@ class RsthosvdCall:
         return out
 
     def run(self, X, norms=True):
-        _check_input(X, self.dims, self.factor)
+        if self.dt == _lib.RH_FP8_E4M3:
+            nb = fp8_layout(self.dims)["bytes"]
+            if not X.is_cuda or not X.is_contiguous() or X.numel() * X.element_size() != nb:
+                raise ValueError(f"an RH_FP8_E4M3 tensor of sizes {self.dims} is a contiguous CUDA buffer of {nb} bytes")
+        else:
+            _check_input(X, self.dims, self.factor)
         check(self._fn(len(self.dims), self.da, self.dt, _ptr(X), self.ra, ctypes.byref(self.opts), self.fptrs,
                        _ptr(self.core), _ptr(self.norms) if norms else None, _ptr(self.info), _ptr(self.ws),
                        self.ws_bytes, _stream(X.device)))
@@ -325,18 +342,25 @@ def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True)
     return call.run(X)
 
 
-def adaptive(X, dims, eps, variant="sthosvd", block=8, max_ranks=None, p=10, seed=0, rho=None, tensor_id=0):
+def adaptive(X, dims, eps, variant="sthosvd", block=8, max_ranks=None, p=10, seed=0, rho=None, tensor_id=0,
+             form=None):
     """Adaptive-rank R-HOSVD (``variant="hosvd"``, Alg. 4) or R-STHOSVD (``"sthosvd"``, Alg. 5) of the
     flat column-major tensor X to relative error ``eps`` (tolerance eps ||X|| / sqrt(d) per mode).
-    ``max_ranks`` caps the range finder per mode (default min(I_n, 64 - p)).  Synchronous; returns a
-    Tucker whose factors are (r_n, I_n) views and whose ``ranks`` attribute lists the chosen ranks."""
-    torch = _check_input(X, dims)
+    ``max_ranks`` caps the range finder per mode (default min(I_n, 64 - p)).  ``form`` selects a
+    low-precision storage form of X as in rsthosvd (Alg. 5 only; its first mode runs on the tensor
+    cores).  Synchronous; returns a Tucker whose factors are (r_n, I_n) views and whose ``ranks``
+    attribute lists the chosen ranks."""
+    torch = _torch()
+    if form is None:
+        _check_input(X, dims)
+    elif not X.is_cuda or not X.is_contiguous():
+        raise ValueError("X must be a contiguous CUDA tensor")
     d = len(dims)
     dims = [int(v) for v in dims]
     if max_ranks is None:
         max_ranks = [max(1, min(v, 64 - int(p))) for v in dims]
     vcode = {"hosvd": 0, "sthosvd": 1}[variant]
-    dt = _dtype_code(X)
+    dt = _FORMS[form] if form is not None else _dtype_code(X)
     da, ma = i64_array(dims), i32_array(max_ranks)
     opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho)
     ws_bytes = lib().adaptive_rank_workspace_size(d, da, dt, vcode, ma, ctypes.byref(opts))
@@ -450,9 +474,9 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, c
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None):
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 
-    ``form="bf16x2"`` (X from split_bf16x2), ``form="bf16"`` (X holding BF16 bit patterns) or
-    ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly) selects the tensor-core forms for the
-    first mode."""
+    ``form="bf16x2"`` (X from split_bf16x2), ``form="bf16"`` (X holding BF16 bit patterns),
+    ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly) or ``form="fp8_e4m3"`` (X a uint8
+    buffer in the layout of fp8_layout) selects the tensor-core forms for the first mode."""
     call = RsthosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
                         truncate=truncate, device=X.device)
     return call.run(X)
@@ -553,8 +577,8 @@ class RsthosvdHostCall:
         ko = RsthosvdCall._out_ranks(dev_call, ranks, p, clamp, truncate, rho)
         self.dims = dev_call.dims
         d = len(self.dims)
-        if dtype == "f32_bf16x2":
-            self.dt = _lib.RH_F32_BF16X2
+        if isinstance(dtype, str):
+            self.dt = _FORMS[dtype]
         else:
             self.dt = RH_F64 if dtype == torch.float64 else RH_F32
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
@@ -575,7 +599,10 @@ class RsthosvdHostCall:
         n = 1
         for v in self.dims:
             n *= v
-        self.h2d_bytes = n * (8 if self.dt == RH_F64 else 4)
+        if self.dt == _lib.RH_FP8_E4M3:
+            self.h2d_bytes = fp8_layout(self.dims)["bytes"]
+        else:
+            self.h2d_bytes = n * {RH_F64: 8, _lib.RH_BF16: 2}.get(self.dt, 4)
         self.d2h_bytes = 8 * (sum(self.dims[k] * ko[k] for k in range(d)) + ncore + 2)
         self.device = torch.device(device)
 

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "librhosvd.so")
 
 RH_MAX_ORDER = 8
 RH_MAX_ELL = 64
-RH_F64, RH_F32, RH_BF16, RH_BF16X2, RH_F32_BF16X2 = 0, 1, 2, 3, 4
+RH_F64, RH_F32, RH_BF16, RH_BF16X2, RH_F32_BF16X2, RH_FP8_E4M3 = 0, 1, 2, 3, 4, 5
 STATUS = {0: "RH_OK", 1: "RH_EINVAL", 2: "RH_ENOMEM", 3: "RH_ECUDA", 4: "RH_ENUMERIC", 5: "RH_ETIMEOUT",
           6: "RH_EUNSUPPORTED"}
 
@@ -71,6 +71,7 @@ SIGNATURES = {
     "sp_sthosvd_coo": (_I32, [_I32, _P, _I64, _P, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
     "rh_tucker_residual_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
     "rh_tucker_residual": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "rh_fp8_layout": (_I32, [_I32, _P, _P, _P, _P, _P]),
     "rsthosvd_batched_workspace_size": (_SZ, [_I32, _P, _P, _I32, _P, ctypes.POINTER(RhOptions), _I32]),
     "rsthosvd_batched": (_I32, [_I32, _P, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _I32, _P,
                                 _SZ, _P]),

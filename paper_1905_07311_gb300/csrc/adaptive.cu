@@ -36,6 +36,13 @@ __global__ void pad_rows_kernel(const T* __restrict__ Uc, int k, int r, int ell,
 
 struct AdaptSizes {
   size_t part = 0, pnorm = 0, I_ell = 0, orth = 0, tensor = 0, trunc = 0, fac = 0, chain = 0;
+  size_t tc_part = 0, qa = 0, tc_norm = 0;   // tensor-core first mode (low-precision input forms)
+};
+
+// The stored input of a low-precision form, read by the tensor-core kernels on the first mode.
+struct TcInput {
+  int32_t form = -1;   // RH_BF16, RH_BF16X2, RH_F32_BF16X2 or RH_FP8_E4M3; -1: none
+  const void* X = nullptr;
 };
 
 struct AdaptBufs {
@@ -50,6 +57,10 @@ struct AdaptBufs {
   float* Xf;
   void *Rk, *Uc, *Ucpad, *fac, *chain[2];
   int32_t* flag;
+  float* tc_part;
+  uint16_t* qa;
+  double* tc_norm;
+  int32_t* err;
 };
 
 size_t tsize(int32_t dtype) { return dtype == RH_F64 ? sizeof(double) : sizeof(float); }
@@ -76,6 +87,13 @@ rh_status adapt_sizes(int32_t order, const int64_t* dims, int32_t dtype, int32_t
     z.trunc = std::max(z.trunc, dtype == RH_F64 ? trunc_workspace_elems<double>(tp) : trunc_workspace_elems<float>(tp));
   }
   z.tensor = std::max<size_t>(z.tensor, (size_t)std::accumulate(dims, dims + order, int64_t(1), std::multiplies<int64_t>()));
+  if (dtype != RH_F64 && dtype != RH_F32) {
+    const ModeView v0 = mode_view(order, dims, 0);
+    z.tc_part = (size_t)sketch_tc_ctas(v0) * ells[0] * v0.I;
+    z.qa = (size_t)128 * v0.I;
+    z.tc_norm = (size_t)sketch_tc_ctas(v0);
+    z.pnorm = std::max<size_t>(z.pnorm, 1024);   // partial sums of the norm of BF16 pieces
+  }
   if (variant == 0) {
     size_t fe = 0;
     z.chain = core_chain_elems(order, dims, ells.data(), &fe);   // the kept ranks are at most ell_n
@@ -85,6 +103,7 @@ rh_status adapt_sizes(int32_t order, const int64_t* dims, int32_t dtype, int32_t
 }
 
 AdaptBufs carve_adapt(Arena& ar, const AdaptSizes& z, int32_t dtype, int32_t variant) {
+  dtype = dtype == RH_F64 ? RH_F64 : RH_F32;   // intermediates of the low-precision forms are FP32
   const size_t ts = tsize(dtype);
   auto takeT = [&](size_t n) -> void* { return (void*)ar.take<char>(n * ts); };
   AdaptBufs b;
@@ -114,6 +133,10 @@ AdaptBufs carve_adapt(Arena& ar, const AdaptSizes& z, int32_t dtype, int32_t var
   b.chain[0] = variant == 0 ? takeT(z.chain) : nullptr;
   b.chain[1] = variant == 0 ? takeT(z.chain) : nullptr;
   b.flag = ar.take<int32_t>(4);
+  b.tc_part = z.tc_part ? ar.take<float>(z.tc_part) : nullptr;
+  b.qa = z.qa ? ar.take<uint16_t>(z.qa) : nullptr;
+  b.tc_norm = z.tc_norm ? ar.take<double>(z.tc_norm) : nullptr;
+  b.err = ar.take<int32_t>(4);
   return b;
 }
 
@@ -131,22 +154,72 @@ int trim_rank(const std::vector<double>& sv, double res2, double tau2) {
 // then set to eps^2 ||G||^2 / d from this pass's norm (G = X on the first mode of either variant).
 // Writes A_n (I x r) into factor; leaves B (ell x M in the view (L, ell, R)) and U_r padded to ell
 // rows (Ucpad) for the caller's core update.
+// Sketch of the first mode (with ||X||^2) on the tensor cores, straight from the stored form.
+rh_status tc_sketch(const ModeView& v, int ell, const TcInput& in, uint64_t seed, uint32_t sid, const AdaptBufs& bf,
+                    cudaStream_t st) {
+  rh_status s;
+  const int S = sketch_tc_ctas(v);
+  RH_CUDA_TRY(cudaMemsetAsync(bf.err, 0, sizeof(int32_t), st));
+  const uint16_t* p0 = static_cast<const uint16_t*>(in.X);
+  const uint16_t* p1 = in.form == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
+  if (in.form == RH_F32_BF16X2) {
+    s = launch_sketch_tc_f32(v, ell, static_cast<const float*>(in.X), seed, sid, bf.tc_part, bf.tc_norm, bf.err, st);
+  } else if (in.form == RH_FP8_E4M3) {
+    const int64_t dims2[2] = {v.I, v.M()};
+    const Fp8Layout f8 = fp8_layout(2, dims2);
+    const uint8_t* x8 = static_cast<const uint8_t*>(in.X);
+    s = launch_sketch_tc_fp8(v, ell, x8, reinterpret_cast<const float*>(x8 + f8.scale_off), f8.ld, seed, sid,
+                             bf.tc_part, bf.tc_norm, bf.err, st);
+  } else {
+    s = launch_sketch_tc(v, ell, p0, p1, seed, sid, bf.tc_part, bf.err, st);
+  }
+  if (s != RH_OK) return s;
+  SketchPlan rp = plan_sketch(v, ell);
+  rp.S = S;
+  if ((s = launch_sketch_reduce<float>(rp, bf.tc_part, nullptr, bf.Y, nullptr, st)) != RH_OK) return s;
+  if (in.form == RH_F32_BF16X2 || in.form == RH_FP8_E4M3) return launch_sum_n(bf.tc_norm, S, bf.norm2, st);
+  return launch_pieces_sumsq(p0, p1, v.I * v.M(), bf.pnorm, bf.norm2, st);
+}
+
+rh_status tc_mode_product(const ModeView& v, int ell, const TcInput& in, const AdaptBufs& bf, float* B,
+                          cudaStream_t st) {
+  if (in.form == RH_F32_BF16X2)
+    return launch_ttm_tc_f32(v, ell, static_cast<const float*>(in.X), bf.Q, bf.qa, B, bf.err, st);
+  if (in.form == RH_FP8_E4M3) {
+    const int64_t dims2[2] = {v.I, v.M()};
+    const Fp8Layout f8 = fp8_layout(2, dims2);
+    const uint8_t* x8 = static_cast<const uint8_t*>(in.X);
+    return launch_ttm_tc_fp8(v, ell, x8, reinterpret_cast<const float*>(x8 + f8.scale_off), f8.ld, bf.Q, bf.qa, B,
+                             bf.err, st);
+  }
+  const uint16_t* p0 = static_cast<const uint16_t*>(in.X);
+  const uint16_t* p1 = in.form == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
+  return launch_ttm_tc(v, ell, p0, p1, bf.Q, bf.qa, B, bf.err, st);
+}
+
 template <typename T>
-rh_status adapt_mode(const ModeView& v, const T* G, int cap, int p, int b_blk, double eps, int d, double* tau2,
-                     uint64_t seed, uint32_t sid, const AdaptBufs& bf, double* factor, int* r_out, int* ell_out,
-                     double* g2_out, cudaStream_t st) {
+rh_status adapt_mode(const ModeView& v, const T* G, const TcInput* tci, int cap, int p, int b_blk, double eps, int d,
+                     double* tau2, uint64_t seed, uint32_t sid, const AdaptBufs& bf, double* factor, int* r_out,
+                     int* ell_out, double* g2_out, cudaStream_t st) {
   rh_status s;
   const int ell = (int)std::min<int64_t>((int64_t)cap + p, std::min<int64_t>(v.I, v.M()));
   const int kmax = (int)std::min<int64_t>(cap, std::min<int64_t>(v.I, v.M()));
-  // sketch (with ||G||^2), thin QR, mode product B = Q^T G_(n)
-  const SketchPlan sk = plan_sketch(v, ell);
-  if ((s = launch_sketch<T>(sk, G, seed, sid, static_cast<T*>(bf.part), bf.pnorm, st)) != RH_OK) return s;
-  if ((s = launch_sketch_reduce<T>(sk, static_cast<const T*>(bf.part), bf.pnorm, bf.Y, bf.norm2, st)) != RH_OK)
-    return s;
-  if ((s = launch_orthonormalize(v.I, ell, bf.Y, bf.Q, nullptr, bf.orth, st, sizeof(T) == 4)) != RH_OK) return s;
-  if ((s = launch_cast<T>(bf.Q, static_cast<T*>(bf.Qc), v.I * ell, st)) != RH_OK) return s;
+  // sketch (with ||G||^2), thin QR, mode product B = Q^T G_(n); the first mode of a low-precision
+  // form reads the stored tensor on the tensor cores (Omega in BF16, B in FP32)
   T* B = static_cast<T*>(bf.B);
-  if ((s = launch_ttm<T, T>(v, G, static_cast<const T*>(bf.Qc), ell, B, st)) != RH_OK) return s;
+  if (tci) {
+    if ((s = tc_sketch(v, ell, *tci, seed, sid, bf, st)) != RH_OK) return s;
+    if ((s = launch_orthonormalize(v.I, ell, bf.Y, bf.Q, nullptr, bf.orth, st, true)) != RH_OK) return s;
+    if ((s = tc_mode_product(v, ell, *tci, bf, reinterpret_cast<float*>(B), st)) != RH_OK) return s;
+  } else {
+    const SketchPlan sk = plan_sketch(v, ell);
+    if ((s = launch_sketch<T>(sk, G, seed, sid, static_cast<T*>(bf.part), bf.pnorm, st)) != RH_OK) return s;
+    if ((s = launch_sketch_reduce<T>(sk, static_cast<const T*>(bf.part), bf.pnorm, bf.Y, bf.norm2, st)) != RH_OK)
+      return s;
+    if ((s = launch_orthonormalize(v.I, ell, bf.Y, bf.Q, nullptr, bf.orth, st, sizeof(T) == 4)) != RH_OK) return s;
+    if ((s = launch_cast<T>(bf.Q, static_cast<T*>(bf.Qc), v.I * ell, st)) != RH_OK) return s;
+    if ((s = launch_ttm<T, T>(v, G, static_cast<const T*>(bf.Qc), ell, B, st)) != RH_OK) return s;
+  }
   // factor of the whole B: Gram matrix (FP32 data) or the tall-skinny QR triangle; row norms of B
   const TruncPlan tp = plan_trunc(ModeView{v.L, (int64_t)ell, v.R}, ell);
   bool gram = sizeof(T) == 4;
@@ -157,7 +230,13 @@ rh_status adapt_mode(const ModeView& v, const T* G, int cap, int p, int b_blk, d
   double g2 = 0.0;
   RH_CUDA_TRY(cudaMemcpyAsync(d2.data(), bf.d, sizeof(double) * ell, cudaMemcpyDeviceToHost, st));
   RH_CUDA_TRY(cudaMemcpyAsync(&g2, bf.norm2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  int32_t tc_err = 0;
+  if (tci) RH_CUDA_TRY(cudaMemcpyAsync(&tc_err, bf.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   RH_CUDA_TRY(cudaStreamSynchronize(st));
+  if (tc_err != 0) {
+    set_error("a tensor-core kernel gave up waiting (code " + std::to_string(tc_err) + ")");
+    return RH_ETIMEOUT;
+  }
   if (*tau2 < 0.0) *tau2 = eps * eps * g2 / d;
   const double t2 = *tau2;
   // blocked growth: k = b, 2b, ... (the last block capped at kmax) until ||G - Q_k B_k||^2 <= tau^2
@@ -204,9 +283,10 @@ rh_status adapt_mode(const ModeView& v, const T* G, int cap, int p, int b_blk, d
 }
 
 template <typename T>
-rh_status run_adaptive(int32_t order, const int64_t* dims, const T* X, double eps, int32_t variant, int32_t b_blk,
-                       const int32_t* caps, const rh_options& o, double* const* factors, double* core,
-                       int32_t* ranks, double* norms, const AdaptBufs& bf, cudaStream_t st) {
+rh_status run_adaptive(int32_t order, const int64_t* dims, const T* X, const TcInput* tci, double eps,
+                       int32_t variant, int32_t b_blk, const int32_t* caps, const rh_options& o,
+                       double* const* factors, double* core, int32_t* ranks, double* norms, const AdaptBufs& bf,
+                       cudaStream_t st) {
   rh_status s;
   std::vector<int> rho(order);
   if (variant == 1 && o.rho[0] >= 0) {
@@ -225,8 +305,8 @@ rh_status run_adaptive(int32_t order, const int64_t* dims, const T* X, double ep
     const uint32_t sid = ((uint32_t)o.tensor_id << 4) | (uint32_t)n;
     int r = 0, ell = 0;
     double g2 = 0.0;
-    if ((s = adapt_mode<T>(v, variant == 1 ? G : X, caps[n], o.p, b_blk, eps, order, &tau2, o.seed, sid, bf, factors[n],
-                           &r, &ell, &g2, st)) != RH_OK)
+    if ((s = adapt_mode<T>(v, variant == 1 ? G : X, j == 0 ? tci : nullptr, caps[n], o.p, b_blk, eps, order, &tau2,
+                           o.seed, sid, bf, factors[n], &r, &ell, &g2, st)) != RH_OK)
       return s;
     if (j == 0) nx2 = g2;
     ranks[n] = r;
@@ -268,6 +348,50 @@ rh_status run_adaptive(int32_t order, const int64_t* dims, const T* X, double ep
 }  // namespace
 }  // namespace rh
 
+namespace rh {
+namespace {
+
+bool lowp_form(int32_t dtype) {
+  return dtype == RH_BF16 || dtype == RH_BF16X2 || dtype == RH_F32_BF16X2 || dtype == RH_FP8_E4M3;
+}
+
+// How a low-precision form runs: its first mode on the tensor cores (*tc = true) when mode 0 is
+// processed first and the tensor-core kernels cover it; an FP32-split input may instead run as
+// plain FP32 (*as_f32 = true); anything else is unsupported.
+rh_status lowp_plan(int32_t order, const int64_t* dims, int32_t dtype, int32_t variant, const int32_t* caps,
+                    const rh_options& o, bool* tc, bool* as_f32) {
+  *tc = false;
+  *as_f32 = false;
+  if (!lowp_form(dtype)) return RH_OK;
+  if (variant != 1) {
+    set_error("unsupported: the BF16 and E4M3 forms take the sequential variant (Alg. 5) only");
+    return RH_EUNSUPPORTED;
+  }
+  int first = 0;
+  if (o.rho[0] >= 0) {
+    first = o.rho[0];
+  } else {
+    for (int k = 1; k < order; ++k)
+      if (dims[k] > dims[first]) first = k;
+  }
+  const ModeView v0 = mode_view(order, dims, 0);
+  const int ell0 = (int)std::min<int64_t>((int64_t)caps[0] + o.p, std::min<int64_t>(v0.I, v0.M()));
+  if (first == 0 && sketch_tc_supported(v0, ell0) && ttm_tc_supported(v0, ell0)) {
+    *tc = true;
+    return RH_OK;
+  }
+  if (dtype == RH_F32_BF16X2) {
+    *as_f32 = true;
+    return RH_OK;
+  }
+  set_error("unsupported: the BF16 and E4M3 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024 and "
+            "max_ranks[0] + p <= 64");
+  return RH_EUNSUPPORTED;
+}
+
+}  // namespace
+}  // namespace rh
+
 using namespace rh;
 
 extern "C" {
@@ -275,13 +399,16 @@ extern "C" {
 size_t adaptive_rank_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t variant,
                                     const int32_t* max_ranks, const rh_options* opts) {
   if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || max_ranks == nullptr) return 0;
-  if (dtype != RH_F64 && dtype != RH_F32) return 0;
+  if (dtype != RH_F64 && dtype != RH_F32 && !lowp_form(dtype)) return 0;
   if (variant != 0 && variant != 1) return 0;
   for (int k = 0; k < order; ++k)
     if (dims[k] < 1 || max_ranks[k] < 1) return 0;
   rh_options o;
   rh_options_default(&o);
   if (opts) o = *opts;
+  bool tc = false, as_f32 = false;
+  if (lowp_plan(order, dims, dtype, variant, max_ranks, o, &tc, &as_f32) != RH_OK) return 0;
+  if (as_f32) dtype = RH_F32;
   AdaptSizes z;
   if (adapt_sizes(order, dims, dtype, variant, max_ranks, o.p, z) != RH_OK) return 0;
   Arena ar(nullptr);
@@ -296,7 +423,7 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
   clear_error();
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
   for (int k = 0; k < order; ++k) RH_CHECK_ARG(dims[k] >= 1, "every dimension must be >= 1");
-  RH_CHECK_ARG(dtype == RH_F64 || dtype == RH_F32, "dtype must be RH_F64 or RH_F32");
+  RH_CHECK_ARG(dtype == RH_F64 || dtype == RH_F32 || lowp_form(dtype), "dtype must be a dense input form");
   RH_CHECK_ARG(variant == 0 || variant == 1, "variant must be 0 (Alg. 4) or 1 (Alg. 5)");
   RH_CHECK_ARG(eps > 0.0 && std::isfinite(eps), "eps must be positive");
   RH_CHECK_ARG(block >= 1, "block must be >= 1");
@@ -319,8 +446,12 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
       seen[o.rho[k]] = 1;
     }
   }
+  bool tc = false, as_f32 = false;
+  rh_status s = lowp_plan(order, dims, dtype, variant, max_ranks, o, &tc, &as_f32);
+  if (s != RH_OK) return s;
+  if (as_f32) dtype = RH_F32;
   AdaptSizes z;
-  rh_status s = adapt_sizes(order, dims, dtype, variant, max_ranks, o.p, z);
+  s = adapt_sizes(order, dims, dtype, variant, max_ranks, o.p, z);
   if (s != RH_OK) return s;
   Arena meas(nullptr);
   carve_adapt(meas, z, dtype, variant);
@@ -332,10 +463,13 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
   const AdaptBufs bf = carve_adapt(ar, z, dtype, variant);
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == RH_F64)
-    return run_adaptive<double>(order, dims, static_cast<const double*>(X), eps, variant, block, max_ranks, o, factors,
-                                core, ranks, norms, bf, st);
-  return run_adaptive<float>(order, dims, static_cast<const float*>(X), eps, variant, block, max_ranks, o, factors,
-                             core, ranks, norms, bf, st);
+    return run_adaptive<double>(order, dims, static_cast<const double*>(X), nullptr, eps, variant, block, max_ranks, o,
+                                factors, core, ranks, norms, bf, st);
+  TcInput tin;
+  tin.form = dtype;
+  tin.X = X;
+  return run_adaptive<float>(order, dims, static_cast<const float*>(X), tc ? &tin : nullptr, eps, variant, block,
+                             max_ranks, o, factors, core, ranks, norms, bf, st);
 }
 
 }  // extern "C"

@@ -107,4 +107,24 @@ inline ModeView mode_view(int order, const int64_t* dims, int n) {
 
 inline int ell_pad_of(int ell) { return ell <= 32 ? 32 : 64; }
 
+// Storage of an RH_FP8_E4M3 tensor: E4M3 bytes column-major with the mode-1 fibres at a stride
+// of ld = I_1 rounded up to 16 (zero padding), i.e. ld x M bytes (M = prod of the other sizes),
+// then, from the next 16-byte boundary, one FP32 scale per 128 consecutive bytes of that array:
+// element (i, p) is e4m3[i + ld p] * scales[(i + ld p) / 128].
+struct Fp8Layout {
+  int64_t ld = 0;
+  size_t scale_off = 0, nscales = 0, bytes = 0;
+};
+inline Fp8Layout fp8_layout(int order, const int64_t* dims) {
+  Fp8Layout f;
+  int64_t m = 1;
+  for (int k = 1; k < order; ++k) m *= dims[k];
+  f.ld = (dims[0] + 15) / 16 * 16;
+  const size_t data = (size_t)f.ld * (size_t)m;
+  f.scale_off = (data + 15) / 16 * 16;
+  f.nscales = (data + 127) / 128;
+  f.bytes = f.scale_off + 4 * f.nscales;
+  return f;
+}
+
 }  // namespace rh

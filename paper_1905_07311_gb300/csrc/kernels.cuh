@@ -32,6 +32,11 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
 // be NULL) receives per-CTA sums of squares of the split values
 rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
                                double* norm_part, int32_t* err, cudaStream_t st);
+// E4M3 input (leading dimension ld, one FP32 scale per 128 bytes of storage), dequantized and
+// split on the fly into the same two pieces as FP32 input
+rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
+                               uint64_t seed, uint32_t sid, float* part, double* norm_part, int32_t* err,
+                               cudaStream_t st);
 rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st);
 rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 // ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles
@@ -46,6 +51,8 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
                         uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
                             int32_t* err, cudaStream_t st);
+rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
+                            const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
 
 // ---- mode-n product B = G x_n Q^T  (ttm.cu) ------------------------------------------
 // B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.

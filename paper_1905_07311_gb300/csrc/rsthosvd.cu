@@ -14,7 +14,20 @@ namespace {
 
 bool dtype_ok(int32_t dtype) { return dtype == RH_F64 || dtype == RH_F32; }
 // forms whose first mode runs on the tensor cores over BF16 pieces
-bool bf16_form(int32_t dtype) { return dtype == RH_BF16 || dtype == RH_BF16X2 || dtype == RH_F32_BF16X2; }
+// input forms whose first mode runs on the tensor cores over BF16 pieces
+bool bf16_form(int32_t dtype) {
+  return dtype == RH_BF16 || dtype == RH_BF16X2 || dtype == RH_F32_BF16X2 || dtype == RH_FP8_E4M3;
+}
+// FP32 or E4M3 input converted to BF16 pieces inside the tensor-core kernels
+bool converted_form(int32_t dtype) { return dtype == RH_F32_BF16X2 || dtype == RH_FP8_E4M3; }
+
+// bytes of an input tensor buffer in the given form
+size_t input_bytes(int32_t order, const int64_t* dims, int32_t dtype) {
+  if (dtype == RH_FP8_E4M3) return fp8_layout(order, dims).bytes;
+  size_t n = 1;
+  for (int k = 0; k < order; ++k) n *= (size_t)dims[k];
+  return n * (dtype == RH_F64 ? 8 : (dtype == RH_BF16 ? 2 : 4));
+}
 
 rh_status check_tensor(int32_t order, const int64_t* dims, int32_t dtype) {
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER, "order must be in [1, 8]");
@@ -63,8 +76,9 @@ struct Plan {
   std::vector<Step> steps;
   size_t max_I_ell = 0, max_tensor = 0, max_orth = 0, max_trunc = 0, max_part = 0, max_pnorm = 0;
   size_t fac_elems = 0;   // R-HOSVD: factor copies in the tensor's precision for the core chain
-  int32_t in_form = -1;   // RH_BF16 / RH_BF16X2 / RH_F32_BF16X2 input (first mode on the tensor cores), else -1
+  int32_t in_form = -1;   // a bf16_form input (first mode on the tensor cores when possible), else -1
   size_t tc_part = 0, qa_elems = 0;
+  std::vector<int64_t> dims0;   // the input sizes
 };
 
 rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks, const rh_options& o,
@@ -89,6 +103,7 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
   }
   pl.d = order;
   pl.dtype = dtype;
+  pl.dims0.assign(dims, dims + order);
   std::vector<int64_t> cur(dims, dims + order);
   const size_t tsz = (dtype == RH_F64) ? sizeof(double) : sizeof(float);
   for (int j = 0; j < order; ++j) {
@@ -131,7 +146,8 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
     const Step& s0 = pl.steps[0];
     const bool s0_tc = s0.mode == 0 && sketch_tc_supported(s0.v, s0.ell) && ttm_tc_supported(s0.v, s0.ell);
     if (!s0_tc && dtype != RH_F32_BF16X2) {
-      set_error("unsupported: the BF16 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024, r + p <= 64");
+      set_error("unsupported: the BF16 and E4M3 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024, "
+                "r + p <= 64");
       return RH_EUNSUPPORTED;
     }
     pl.steps[0].tc = s0_tc;
@@ -299,7 +315,11 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
   const int nsteps = (int)pl.steps.size();
   const bool tc0 = pl.in_form >= 0;
   const bool f32in = pl.in_form == RH_F32_BF16X2;   // FP32 input split on the fly
-  const uint16_t* piece0 = f32in ? nullptr : static_cast<const uint16_t*>(Xraw);
+  const bool fp8in = pl.in_form == RH_FP8_E4M3;     // E4M3 input dequantized and split on the fly
+  const Fp8Layout f8 = fp8in ? fp8_layout(pl.d, pl.dims0.data()) : Fp8Layout{};
+  const uint8_t* x8 = static_cast<const uint8_t*>(Xraw);
+  const float* scales8 = fp8in ? reinterpret_cast<const float*>(x8 + f8.scale_off) : nullptr;
+  const uint16_t* piece0 = (f32in || fp8in) ? nullptr : static_cast<const uint16_t*>(Xraw);
   const uint16_t* piece1 = (pl.in_form == RH_BF16X2) ? piece0 + pl.steps[0].v.I * pl.steps[0].v.M() : nullptr;
   if (tc0) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
   for (int j = 0; j < nsteps; ++j) {
@@ -312,13 +332,17 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     SketchBufs sb{b.part, b.part_norm};
     double* n2 = (j == 0) ? (norms ? norms : b.normx) : nullptr;
     // the input itself is split on the fly (FP32 input) or given as pieces; later cores are FP32
-    const bool in_pieces = tc && first && !f32in;
+    const bool in_pieces = tc && first && !f32in && !fp8in;
+    const bool in_fp8 = tc && first && fp8in;
     const float* tc_src = first ? static_cast<const float*>(Xraw) : reinterpret_cast<const float*>(cur);
     if (tc) {
       {
         ProfileScope ps(PROF_SKETCH, j, st);
         if (in_pieces)
           s = launch_sketch_tc(sp.v, sp.ell, piece0, piece1, o.seed, sid, b.tc_part, b.err, st);
+        else if (in_fp8)
+          s = launch_sketch_tc_fp8(sp.v, sp.ell, x8, scales8, f8.ld, o.seed, sid, b.tc_part,
+                                   norms ? b.part_norm : nullptr, b.err, st);
         else
           s = launch_sketch_tc_f32(sp.v, sp.ell, tc_src, o.seed, sid, b.tc_part,
                                    (first && norms) ? b.part_norm : nullptr, b.err, st);
@@ -328,8 +352,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       rp.S = sketch_tc_ctas(sp.v);
       if ((s = launch_sketch_reduce<float>(rp, b.tc_part, nullptr, b.Y, nullptr, st)) != RH_OK) return s;
       if (first && norms) {
-        s = f32in ? launch_sum_n(b.part_norm, rp.S, norms, st)
-                  : launch_pieces_sumsq(piece0, piece1, sp.v.I * sp.v.M(), b.part_norm, norms, st);
+        s = (f32in || fp8in) ? launch_sum_n(b.part_norm, rp.S, norms, st)
+                             : launch_pieces_sumsq(piece0, piece1, sp.v.I * sp.v.M(), b.part_norm, norms, st);
         if (s != RH_OK) return s;
       }
     } else {
@@ -362,6 +386,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       }
       if (in_pieces)
         s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
+      else if (in_fp8)
+        s = launch_ttm_tc_fp8(sp.v, sp.ell, x8, scales8, f8.ld, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
       else
         s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
       if (s != RH_OK) return s;
@@ -509,6 +535,19 @@ static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell) {
   return ar.used;
 }
 
+rh_status rh_fp8_layout(int32_t order, const int64_t* dims, int64_t* ld, size_t* scale_offset, size_t* nscales,
+                        size_t* bytes) {
+  clear_error();
+  rh_status s = check_tensor(order, dims, RH_F32);
+  if (s != RH_OK) return s;
+  const Fp8Layout f = fp8_layout(order, dims);
+  if (ld) *ld = f.ld;
+  if (scale_offset) *scale_offset = f.scale_off;
+  if (nscales) *nscales = f.nscales;
+  if (bytes) *bytes = f.bytes;
+  return RH_OK;
+}
+
 size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t ell) {
   if (is_bf16_form(dtype)) {
     if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode != 0 || ell < 1 || ell > RH_MAX_ELL) return 0;
@@ -534,7 +573,7 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     RH_CHECK_ARG(ell >= 1 && ell <= RH_MAX_ELL, "ell must be in [1, 64]");
     RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
     RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
-    RH_CHECK_ARG(norm2 == nullptr || dtype == RH_F32_BF16X2, "norm2 is not available for RH_BF16 / RH_BF16X2");
+    RH_CHECK_ARG(norm2 == nullptr || converted_form(dtype), "norm2 is not available for RH_BF16 / RH_BF16X2");
     const ModeView v = mode_view(order, dims, 0);
     if (!sketch_tc_supported(v, ell)) {
       set_error("unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024");
@@ -557,6 +596,12 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     if (dtype == RH_F32_BF16X2) {
       s = launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part, norm2 ? norm_part : nullptr, err,
                                st);
+      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st);
+    } else if (dtype == RH_FP8_E4M3) {
+      const Fp8Layout f8 = fp8_layout(order, dims);
+      const uint8_t* x8 = static_cast<const uint8_t*>(X);
+      s = launch_sketch_tc_fp8(v, ell, x8, reinterpret_cast<const float*>(x8 + f8.scale_off), f8.ld, seed, sid, part,
+                               norm2 ? norm_part : nullptr, err, st);
       if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st);
     } else {
       const uint16_t* p0 = static_cast<const uint16_t*>(X);
@@ -642,7 +687,7 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
 rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
                                const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
-  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16, RH_BF16X2 or RH_F32_BF16X2");
+  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16, RH_BF16X2, RH_F32_BF16X2 or RH_FP8_E4M3");
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
   for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
   RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
@@ -662,6 +707,11 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
   cudaStream_t st = (cudaStream_t)stream;
   RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
   if (dtype == RH_F32_BF16X2) return launch_ttm_tc_f32(v, k, static_cast<const float*>(X), A, qa, Y, err, st);
+  if (dtype == RH_FP8_E4M3) {
+    const Fp8Layout f8 = fp8_layout(order, dims);
+    const uint8_t* x8 = static_cast<const uint8_t*>(X);
+    return launch_ttm_tc_fp8(v, k, x8, reinterpret_cast<const float*>(x8 + f8.scale_off), f8.ld, A, qa, Y, err, st);
+  }
   const uint16_t* p0 = static_cast<const uint16_t*>(X);
   const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
   return launch_ttm_tc(v, k, p0, p1, A, qa, Y, err, st);
@@ -799,8 +849,7 @@ size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t 
   Arena ar(nullptr);
   int64_t n = 1, ncore = 1;
   for (int k = 0; k < order; ++k) n *= dims[k];
-  const size_t esz = dtype == RH_F64 ? sizeof(double) : (dtype == RH_BF16 ? 2 : sizeof(float));
-  ar.take<char>((size_t)n * esz);
+  ar.take<char>(input_bytes(order, dims, dtype));
   std::vector<int64_t> kout(order, 0);
   for (const Step& sp : pl.steps) kout[sp.mode] = sp.ko;
   for (int k = 0; k < order; ++k) {
@@ -832,8 +881,8 @@ rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const
   Arena ar(workspace);
   int64_t n = 1, ncore = 1;
   for (int k = 0; k < order; ++k) n *= dims[k];
-  const size_t esz = dtype == RH_F64 ? sizeof(double) : (dtype == RH_BF16 ? 2 : sizeof(float));
-  void* Xd = ar.take<char>((size_t)n * esz);
+  const size_t xbytes = input_bytes(order, dims, dtype);
+  void* Xd = ar.take<char>(xbytes);
   std::vector<int64_t> kout(order, 0);
   for (const Step& sp : pl.steps) kout[sp.mode] = sp.ko;
   std::vector<double*> fd(order);
@@ -845,7 +894,7 @@ rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const
   double* normsd = ar.take<double>(2);
   const Bufs b = carve(ar, pl);
   cudaStream_t st = (cudaStream_t)stream;
-  RH_CUDA_TRY(cudaMemcpyAsync(Xd, X_host, (size_t)n * esz, cudaMemcpyHostToDevice, st));
+  RH_CUDA_TRY(cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, st));
   if (pl.dtype == RH_F64)
     s = run_rsthosvd<double>(pl, Xd, o, fd.data(), cored, normsd, nullptr, b, st);
   else

@@ -180,21 +180,56 @@ __global__ void __launch_bounds__(kNT, 2)
   }
 }
 
+// Y(i, c) = sum over the S splits of part[k][c][i], in FP64.  CTA (bx, c) owns rows
+// i in [32 bx, 32 bx + 32) of column c; warp w sums the splits k = w, w + 8, ... (each warp
+// load is 32 consecutive rows, one 128-byte line for FP32), and warp 0 adds the 8 warp sums in
+// a fixed order, so the result does not depend on timing.  CTA (0, 0) also sums the per-CTA
+// squared norms with a fixed-shape tree.
+constexpr int kRedWarps = 8;
+
 template <typename T>
-__global__ void sketch_reduce_kernel(const T* __restrict__ part, int S, int64_t I, int ell, double* __restrict__ Y,
-                                     const double* __restrict__ part_norm, int nnorm, double* __restrict__ norm2) {
-  const int64_t total = I * ell;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t % I;
-    const int64_t c = t / I;
-    double s = 0.0;
-    for (int k = 0; k < S; ++k) s += (double)part[((int64_t)k * ell + c) * I + i];
-    Y[i + I * c] = s;
+__global__ void __launch_bounds__(32 * kRedWarps) sketch_reduce_kernel(const T* __restrict__ part, int S, int64_t I,
+                                                                        int ell, double* __restrict__ Y,
+                                                                        const double* __restrict__ part_norm,
+                                                                        int nnorm, double* __restrict__ norm2) {
+  __shared__ double red[kRedWarps][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t c = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (i < I) {
+    const T* src = part + c * I + i;
+    const int64_t step = (int64_t)ell * I;
+    int k = w;
+    // two independent chains per lane, combined in a fixed order
+    double s1 = 0.0;
+    for (; k + kRedWarps < S; k += 2 * kRedWarps) {
+      s += (double)src[(int64_t)k * step];
+      s1 += (double)src[(int64_t)(k + kRedWarps) * step];
+    }
+    if (k < S) s += (double)src[(int64_t)k * step];
+    s += s1;
   }
-  if (norm2 != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < nnorm; ++k) s += part_norm[k];
-    *norm2 = s;
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && i < I) {
+    double t = red[0][lane];
+#pragma unroll
+    for (int j = 1; j < kRedWarps; ++j) t += red[j][lane];
+    Y[i + I * c] = t;
+  }
+  if (norm2 != nullptr && blockIdx.x == 0 && blockIdx.y == 0) {
+    __syncthreads();
+    double t = 0.0;
+    for (int k = threadIdx.x; k < nnorm; k += blockDim.x) t += part_norm[k];
+    double* flat = &red[0][0];
+    flat[threadIdx.x] = t;   // 256 <= 8 * 33
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) flat[threadIdx.x] += flat[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *norm2 = flat[0];
   }
 }
 
@@ -208,8 +243,12 @@ SketchPlan plan_sketch(const ModeView& v, int ell) {
   pl.gx = (int)ceil_div(v.I, kTI);
   const int64_t M = v.M();
   const int64_t ksteps = ceil_div(M, kKP);
+  // about 4 CTAs per SM, but at least kMinChunk columns per CTA: a small tensor is not spread
+  // over more splits than its size pays for (every split adds I x ell partial sums to reduce)
+  constexpr int64_t kMinChunk = 1024;
   const int64_t target = 4LL * num_sms();
   int64_t S = std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, pl.gx), ksteps));
+  S = std::max<int64_t>(1, std::min<int64_t>(S, ceil_div(M, kMinChunk)));
   pl.chunk = ceil_div(ceil_div(M, S), kKP) * kKP;
   pl.S = (int)ceil_div(M, pl.chunk);
   return pl;
@@ -237,11 +276,13 @@ rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_
 template <typename T>
 rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y, double* norm2,
                                cudaStream_t st) {
-  const int64_t total = pl.v.I * pl.ell;
-  const int threads = 256;
-  const int blocks = (int)std::min<int64_t>(ceil_div(total, threads), 4096);
-  sketch_reduce_kernel<T><<<blocks, threads, 0, st>>>(part, pl.S, pl.v.I, pl.ell, Y, part_norm,
-                                                      (int)pl.norm_elems(), norm2);
+  if (pl.ell > 65535) {
+    set_error("sketch reduce: too many columns");
+    return RH_EUNSUPPORTED;
+  }
+  const dim3 grid((unsigned)ceil_div(pl.v.I, 32), (unsigned)pl.ell);
+  sketch_reduce_kernel<T><<<grid, 32 * kRedWarps, 0, st>>>(part, pl.S, pl.v.I, pl.ell, Y, part_norm,
+                                                           (int)pl.norm_elems(), norm2);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

@@ -38,23 +38,28 @@ constexpr uint32_t kOmegaTile = 64 * 64 * 2;        // 64 x 64 BF16
 constexpr uint32_t kF32Box = 32 * 64 * 4;           // FP32 TMA box: 32 rows x 64 columns
 constexpr uint32_t kF32Tile = 4 * kF32Box;          // 128 x 64 FP32
 
-// BF16 pieces in: 4 stages filled by TMA.  FP32 in: 3 stages of FP32 tiles filled by TMA,
-// split by four converter warps into 2 stages of BF16 pieces.
-template <bool F32IN>
+constexpr uint32_t kFp8Tile = 128 * 64;           // E4M3 TMA box: 128 rows (bytes) x 64 columns
+
+// BF16 pieces in: 4 stages filled by TMA.  FP32 in: 3 stages of FP32 tiles filled by TMA, split
+// by eight converter warps into 2 stages of BF16 pieces.  E4M3 in: 4 stages of byte tiles,
+// dequantized and split the same way.
+template <int IN>
 struct SketchCfg {
-  static constexpr int kPStages = F32IN ? 2 : 4;
-  static constexpr int kF32Stages = F32IN ? 3 : 1;
+  static constexpr bool kConvIn = IN != tc::kInPieces;
+  static constexpr int kPStages = kConvIn ? 2 : 4;
+  static constexpr int kF32Stages = IN == tc::kInF32 ? 3 : (IN == tc::kInFp8 ? 4 : 1);
+  static constexpr uint32_t kStageBytes = IN == tc::kInF32 ? kF32Tile : (IN == tc::kInFp8 ? kFp8Tile : 1024);
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
-  static constexpr int kThreads = F32IN ? 192 + kConv : 192;
+  static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
 };
 
-template <bool F32IN>
+template <int IN>
 struct alignas(1024) SketchSmem {
-  uint8_t xf[SketchCfg<F32IN>::kF32Stages][F32IN ? kF32Tile : 1024];
-  uint8_t x[SketchCfg<F32IN>::kPStages][2][kPieceTile];   // [stage][piece][128 x 64]
+  uint8_t xf[SketchCfg<IN>::kF32Stages][SketchCfg<IN>::kStageBytes];
+  uint8_t x[SketchCfg<IN>::kPStages][2][kPieceTile];   // [stage][piece][128 x 64]
   uint8_t om[2][kOmegaTile];
-  uint64_t f32full[SketchCfg<F32IN>::kF32Stages], f32empty[SketchCfg<F32IN>::kF32Stages];
-  uint64_t full[SketchCfg<F32IN>::kPStages], empty[SketchCfg<F32IN>::kPStages], om_full[2], om_empty[2], done;
+  uint64_t f32full[SketchCfg<IN>::kF32Stages], f32empty[SketchCfg<IN>::kF32Stages];
+  uint64_t full[SketchCfg<IN>::kPStages], empty[SketchCfg<IN>::kPStages], om_full[2], om_empty[2], done;
   uint32_t tmem_slot;
   double nrm[16];
 };
@@ -65,21 +70,23 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int col) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (col & 7) * 2);
 }
 
-// F32IN = false: map0 / map1 are the BF16 pieces (box 64 x 64).  F32IN = true: map0 is the FP32
-// tensor (box 32 x 64), split on the fly; norm_part[blockIdx.x] receives this CTA's sum of
-// squares of the split values (head + tail).
-template <bool F32IN>
-__global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
+// IN = kInPieces: map0 / map1 are the BF16 pieces (box 64 x 64).  IN = kInF32: map0 is the FP32
+// tensor (box 32 x 64), split on the fly.  IN = kInFp8: map0 is the E4M3 tensor (box 128 x 64
+// bytes, leading dimension ld), dequantized with ``scales`` and split on the fly.  With converted
+// input, norm_part[blockIdx.x] receives this CTA's sum of squares of the split values (head + tail).
+template <int IN>
+__global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, int npieces,
                      int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
                      uint32_t sid, float* __restrict__ part, double* __restrict__ norm_part,
-                     int32_t* __restrict__ err) {
-  using Cfg = SketchCfg<F32IN>;
+                     int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld) {
+  using Cfg = SketchCfg<IN>;
+  constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
   constexpr int NF = Cfg::kF32Stages;
   extern __shared__ uint8_t smem_raw[];
-  SketchSmem<F32IN>& S =
-      *reinterpret_cast<SketchSmem<F32IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  SketchSmem<IN>& S =
+      *reinterpret_cast<SketchSmem<IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (M + kPChunk - 1) / kPChunk;
   const int64_t c_begin = (int64_t)blockIdx.x * chunks_per_cta;
@@ -125,9 +132,14 @@ __global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
           if constexpr (F32IN) {
             const uint32_t s = it % NF;
             if (it >= NF && !tc::mbar_wait(&S.f32empty[s], ((it / NF) - 1) & 1, err, 1)) break;
-            tc::mbar_arrive_expect_tx(&S.f32full[s], kF32Tile);
-            for (int b = 0; b < 4; ++b)
-              tc::tma_load_2d(&S.xf[s][b * kF32Box], &map0, m * kRowsTile + 32 * b, p0, &S.f32full[s]);
+            if constexpr (IN == tc::kInFp8) {
+              tc::mbar_arrive_expect_tx(&S.f32full[s], kFp8Tile);
+              tc::tma_load_2d(&S.xf[s][0], &map0, m * kRowsTile, p0, &S.f32full[s]);
+            } else {
+              tc::mbar_arrive_expect_tx(&S.f32full[s], kF32Tile);
+              for (int b = 0; b < 4; ++b)
+                tc::tma_load_2d(&S.xf[s][b * kF32Box], &map0, m * kRowsTile + 32 * b, p0, &S.f32full[s]);
+            }
           } else {
             const uint32_t s = it % NS;
             if (it >= NS && !tc::mbar_wait(&S.empty[s], ((it / NS) - 1) & 1, err, 1)) break;
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
       for (int64_t e = t; e < (int64_t)ell * I; e += 128) part[(int64_t)blockIdx.x * ell * I + e] = 0.0f;
     }
   } else if constexpr (F32IN) {
-    // ---------------- converters (warps 6..13): FP32 tile -> BF16 head + tail ----------------
+    // ---------------- converters (warps 6..13): FP32 / E4M3 tile -> BF16 head + tail -----------
     const int t = threadIdx.x - 192;   // 0..kConv-1
     double acc = 0.0;
     uint32_t it = 0;
@@ -229,7 +241,12 @@ __global__ void __launch_bounds__(SketchCfg<F32IN>::kThreads, 1)
           ok = false;
           break;
         }
-        acc += (double)tc::convert_tile<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+        if constexpr (IN == tc::kInFp8)
+          acc += (double)tc::convert_fp8_tile<128, 64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t,
+                                                                   scales, ld, (int64_t)m * kRowsTile,
+                                                                   c * kPChunk, I, M);
+        else
+          acc += (double)tc::convert_tile<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&S.f32empty[s]);
         tc::mbar_arrive(&S.full[ps]);
@@ -339,6 +356,27 @@ rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int
   return make_map_2d(map, base, 2, rows, cols, box_cols);
 }
 
+// 2-D tensor map over bytes: rows x cols, column-major with leading dimension ld (a multiple of
+// 16), box box_rows x box_cols, no swizzle, zero fill outside rows x cols.
+rh_status make_u8_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t ld, int64_t cols, int box_rows,
+                         int box_cols) {
+  EncodeTiledFn enc;
+  rh_status s = get_encoder(&enc);
+  if (s != RH_OK) return s;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld};
+  const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (bytes) failed with code " + std::to_string((int)r));
+    return RH_ECUDA;
+  }
+  return RH_OK;
+}
+
 bool sketch_tc_supported(const ModeView& v, int ell) {
   return v.L == 1 && v.I % 8 == 0 && v.I <= (int64_t)kRowsTile * kMaxTiles && ell >= 1 && ell <= 64 &&
          v.M() < (int64_t(1) << 31);
@@ -368,11 +406,12 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
   const int64_t nchunks = ceil_div(v.M(), kPChunk);
   const int64_t cpc = ceil_div(nchunks, ctas);
   const int mtiles = (int)ceil_div(v.I, kRowsTile);
-  const size_t smem = sizeof(SketchSmem<false>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sketch_tc_kernel<false><<<ctas, SketchCfg<false>::kThreads, smem, st>>>(
+  constexpr int IN = tc::kInPieces;
+  const size_t smem = sizeof(SketchSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m1, np, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      nullptr, err);
+      nullptr, err, nullptr, 0);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -390,11 +429,37 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
   const int64_t nchunks = ceil_div(v.M(), kPChunk);
   const int64_t cpc = ceil_div(nchunks, ctas);
   const int mtiles = (int)ceil_div(v.I, kRowsTile);
-  const size_t smem = sizeof(SketchSmem<true>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sketch_tc_kernel<true><<<ctas, SketchCfg<true>::kThreads, smem, st>>>(
+  constexpr int IN = tc::kInF32;
+  const size_t smem = sizeof(SketchSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err);
+      norm_part, err, nullptr, 0);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
+                               uint64_t seed, uint32_t sid, float* part, double* norm_part, int32_t* err,
+                               cudaStream_t st) {
+  if (!sketch_tc_supported(v, ell) || ld < v.I || ld % 16 != 0) {
+    set_error("tensor-core sketch: unsupported E4M3 shape (needs the first mode, I % 8 == 0, I <= 1024, "
+              "ell <= 64, a leading dimension that is a multiple of 16)");
+    return RH_EUNSUPPORTED;
+  }
+  CUtensorMap m0;
+  rh_status s = make_u8_map_2d(&m0, X, v.I, ld, v.M(), 128, 64);
+  if (s != RH_OK) return s;
+  const int ctas = sketch_tc_ctas(v);
+  const int64_t nchunks = ceil_div(v.M(), kPChunk);
+  const int64_t cpc = ceil_div(nchunks, ctas);
+  const int mtiles = (int)ceil_div(v.I, kRowsTile);
+  constexpr int IN = tc::kInFp8;
+  const size_t smem = sizeof(SketchSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
+      m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
+      norm_part, err, scales, ld);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

@@ -27,6 +27,8 @@ namespace rh {
 
 rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_cols);
 rh_status make_map_2d(CUtensorMap* map, const void* base, int esize, int64_t rows, int64_t cols, int box_cols);
+rh_status make_u8_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t ld, int64_t cols, int box_rows,
+                         int box_cols);
 
 namespace {
 
@@ -36,25 +38,30 @@ constexpr uint32_t kATile = 128 * 64 * 2;      // A slice: 128 rows x 64 (BF16)
 constexpr uint32_t kXTile = kNTile * 64 * 2;   // X slice: 128 columns x 64 rows (BF16)
 constexpr uint32_t kF32Box = kNTile * 32 * 4;  // FP32 TMA box: 32 rows x 128 columns
 
+constexpr uint32_t kFp8Box = kNTile * 64;      // E4M3 TMA box: 64 rows (bytes) x 128 columns
+
 // BF16 pieces in: 3 stages (A slice + pieces) filled by TMA.  FP32 in: 3 stages of FP32 slices
-// filled by TMA, split by four converter warps into 2 stages of pieces; the converters also
-// request the A slice of their stage.
-template <bool F32IN>
+// filled by TMA, split by eight converter warps into 2 stages of pieces; the converters also
+// request the A slice of their stage.  E4M3 in: 4 stages of byte slices, dequantized and split
+// the same way.
+template <int IN>
 struct TtmCfg {
-  static constexpr int kPStages = F32IN ? 2 : 3;
-  static constexpr int kF32Stages = F32IN ? 3 : 1;
+  static constexpr bool kConvIn = IN != tc::kInPieces;
+  static constexpr int kPStages = kConvIn ? 2 : 3;
+  static constexpr int kF32Stages = IN == tc::kInF32 ? 3 : (IN == tc::kInFp8 ? 4 : 1);
+  static constexpr uint32_t kStageBytes = IN == tc::kInF32 ? 2 * kF32Box : (IN == tc::kInFp8 ? kFp8Box : 1024);
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
-  static constexpr int kThreads = F32IN ? 192 + kConv : 192;
+  static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
 };
 
-template <bool F32IN>
+template <int IN>
 struct alignas(1024) TtmSmem {
-  uint8_t xf[TtmCfg<F32IN>::kF32Stages][F32IN ? 2 * kF32Box : 1024];
-  uint8_t a[TtmCfg<F32IN>::kPStages][kATile];
-  uint8_t x[TtmCfg<F32IN>::kPStages][2][kXTile];
+  uint8_t xf[TtmCfg<IN>::kF32Stages][TtmCfg<IN>::kStageBytes];
+  uint8_t a[TtmCfg<IN>::kPStages][kATile];
+  uint8_t x[TtmCfg<IN>::kPStages][2][kXTile];
   float xchg[64][kNTile + 1];
-  uint64_t f32full[TtmCfg<F32IN>::kF32Stages], f32empty[TtmCfg<F32IN>::kF32Stages];
-  uint64_t full[TtmCfg<F32IN>::kPStages], empty[TtmCfg<F32IN>::kPStages], afull[TtmCfg<F32IN>::kPStages];
+  uint64_t f32full[TtmCfg<IN>::kF32Stages], f32empty[TtmCfg<IN>::kF32Stages];
+  uint64_t full[TtmCfg<IN>::kPStages], empty[TtmCfg<IN>::kPStages], afull[TtmCfg<IN>::kPStages];
   uint64_t tfull[2], tempty[2];
   uint32_t tmem_slot;
 };
@@ -63,19 +70,21 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// F32IN = false: mapX0 / mapX1 are the BF16 pieces (box 64 x 128).  F32IN = true: mapX0 is the
-// FP32 tensor (box 32 x 128), split on the fly into the same two pieces.
-template <bool F32IN>
-__global__ void __launch_bounds__(TtmCfg<F32IN>::kThreads, 1)
+// IN = kInPieces: mapX0 / mapX1 are the BF16 pieces (box 64 x 128).  IN = kInF32: mapX0 is the
+// FP32 tensor (box 32 x 128), split on the fly into the same two pieces.  IN = kInFp8: mapX0 is
+// the E4M3 tensor (box 64 x 128 bytes, leading dimension ld), dequantized with ``scales`` and split.
+template <int IN>
+__global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
-                  float* __restrict__ B, int32_t* __restrict__ err) {
-  using Cfg = TtmCfg<F32IN>;
+                  float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld) {
+  using Cfg = TtmCfg<IN>;
+  constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
   constexpr int NF = Cfg::kF32Stages;
   extern __shared__ uint8_t smem_raw[];
-  TtmSmem<F32IN>& S =
-      *reinterpret_cast<TtmSmem<F32IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TtmSmem<IN>& S =
+      *reinterpret_cast<TtmSmem<IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (M + kNTile - 1) / kNTile;
   const int kstages = (int)((I + kKStage - 1) / kKStage);
@@ -126,9 +135,14 @@ __global__ void __launch_bounds__(TtmCfg<F32IN>::kThreads, 1)
               ok = false;
               break;
             }
-            tc::mbar_arrive_expect_tx(&S.f32full[s], 2 * kF32Box);
-            tc::tma_load_2d(&S.xf[s][0], &mapX0, ks * kKStage, p0, &S.f32full[s]);
-            tc::tma_load_2d(&S.xf[s][kF32Box], &mapX0, ks * kKStage + 32, p0, &S.f32full[s]);
+            if constexpr (IN == tc::kInFp8) {
+              tc::mbar_arrive_expect_tx(&S.f32full[s], kFp8Box);
+              tc::tma_load_2d(&S.xf[s][0], &mapX0, ks * kKStage, p0, &S.f32full[s]);
+            } else {
+              tc::mbar_arrive_expect_tx(&S.f32full[s], 2 * kF32Box);
+              tc::tma_load_2d(&S.xf[s][0], &mapX0, ks * kKStage, p0, &S.f32full[s]);
+              tc::tma_load_2d(&S.xf[s][kF32Box], &mapX0, ks * kKStage + 32, p0, &S.f32full[s]);
+            }
           } else {
             const uint32_t s = it % NS;
             if (it >= NS && !tc::mbar_wait(&S.empty[s], ((it / NS) - 1) & 1, err, 11)) {
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(TtmCfg<F32IN>::kThreads, 1)
       named_sync(1, 128);   // xchg is free again
     }
   } else if constexpr (F32IN) {
-    // converters (warps 6..13): FP32 slice -> BF16 head + tail; thread 0 also requests the A slice
+    // converters (warps 6..13): FP32 / E4M3 slice -> BF16 head + tail; thread 0 also requests the A slice
     const int t = threadIdx.x - 192;   // 0..kConv-1
     uint32_t it = 0;
     bool ok = true;
@@ -232,7 +246,11 @@ __global__ void __launch_bounds__(TtmCfg<F32IN>::kThreads, 1)
           ok = false;
           break;
         }
-        (void)tc::convert_tile<128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+        if constexpr (IN == tc::kInFp8)
+          (void)tc::convert_fp8_tile<64, 128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t, scales, ld,
+                                                          (int64_t)ks * kKStage, tt * kNTile, I, M);
+        else
+          (void)tc::convert_tile<128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&S.f32empty[s]);
         tc::mbar_arrive(&S.full[ps]);
@@ -293,10 +311,11 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   } else {
     m1 = m0;
   }
-  const size_t smem = sizeof(TtmSmem<false>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<false><<<ttm_tc_ctas(v), TtmCfg<false>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B,
-                                                                               err);
+  constexpr int IN = tc::kInPieces;
+  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
+                                                                         nullptr, 0);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -317,9 +336,37 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
   if (s != RH_OK) return s;
   if ((s = make_map_2d(&m0, X, 4, v.I, v.M(), kNTile)) != RH_OK) return s;
-  const size_t smem = sizeof(TtmSmem<true>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<true><<<ttm_tc_ctas(v), TtmCfg<true>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err);
+  constexpr int IN = tc::kInF32;
+  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
+                                                                         nullptr, 0);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
+                            const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st) {
+  if (!ttm_tc_supported(v, ell) || ld < v.I || ld % 16 != 0) {
+    set_error("tensor-core mode product: unsupported E4M3 shape (needs the first mode, I % 8 == 0, ell <= 64, "
+              "a leading dimension that is a multiple of 16)");
+    return RH_EUNSUPPORTED;
+  }
+  {
+    const int64_t total = 128 * v.I;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
+    q_pieces_kernel<<<blocks, 256, 0, st>>>(Q, v.I, ell, qa);
+    RH_LAUNCH_CHECK();
+  }
+  CUtensorMap mA, m0;
+  rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
+  if (s != RH_OK) return s;
+  if ((s = make_u8_map_2d(&m0, X, v.I, ld, v.M(), 64, kNTile)) != RH_OK) return s;
+  constexpr int IN = tc::kInFp8;
+  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
+                                                                         scales, ld);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

@@ -151,3 +151,92 @@ def batch_recipe(count=512, seed=4, orders=(3, 4, 5), size_range=(16, 96), rank_
         ranks = [int(min(r, I)) for r, I in zip(rs.integers(rank_range[0], rank_range[1] + 1, size=d), dims)]
         out.append((dims, ranks, int(seed) * 100003 + i))
     return out
+
+
+# ---- low-precision storage of an input tensor (the form the caller hands over) ---------------
+# E4M3 with one FP32 scale per 128 bytes: codes column-major with the mode-1 fibres padded to a
+# multiple of 16 bytes, then the scales from the next 16-byte boundary.  Block scale = amax / 448
+# in FP32 (1 for an all-zero block), codes = nearest E4M3 value of x / scale (ties to the even
+# code), saturated at +-448.
+
+def _e4m3_finite_magnitudes():
+    v = []
+    for code in range(127):   # 0x00 .. 0x7E; 0x7F is NaN
+        e, m = code >> 3, code & 7
+        v.append(m * 2.0 ** -9 if e == 0 else (1 + m / 8) * 2.0 ** (e - 7))
+    return np.array(v)
+
+
+def fp8_storage_layout(dims):
+    dims = [int(v) for v in dims]
+    m = int(np.prod(dims[1:], dtype=np.int64)) if len(dims) > 1 else 1
+    ld = -(-dims[0] // 16) * 16
+    off = -(-(ld * m) // 16) * 16
+    nscales = -(-(ld * m) // 128)
+    return ld, m, off, nscales, off + 4 * nscales
+
+
+def fp8_quantize_np(X):
+    """Block-scaled E4M3 buffer (uint8 ndarray) of the numpy tensor X (shape = its sizes)."""
+    X = np.asarray(X, dtype=np.float32)
+    ld, m, off, nscales, total = fp8_storage_layout(X.shape)
+    P = np.zeros((ld, m), dtype=np.float32)
+    P[:X.shape[0], :] = np.reshape(X, (X.shape[0], m), order="F")
+    flat = np.zeros(nscales * 128, dtype=np.float32)
+    flat[:ld * m] = P.ravel(order="F")
+    blocks = flat.reshape(nscales, 128)
+    amax = np.abs(blocks).max(axis=1)
+    scale = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    y = (blocks / scale[:, None]).astype(np.float32).astype(np.float64)
+    mag = np.minimum(np.abs(y), 448.0)
+    tab = _e4m3_finite_magnitudes()
+    hi = np.clip(np.searchsorted(tab, mag), 0, 126)
+    lo = np.clip(hi - 1, 0, 126)
+    dlo, dhi = mag - tab[lo], tab[hi] - mag
+    pick_hi = (dhi < dlo) | ((dhi == dlo) & (hi % 2 == 0))
+    code = np.where(pick_hi, hi, lo).astype(np.uint8)
+    code = code | np.where(y < 0, 0x80, 0).astype(np.uint8)
+    buf = np.zeros(total, dtype=np.uint8)
+    buf[:ld * m] = code.ravel()[:ld * m]
+    buf[off:] = scale.view(np.uint8)
+    return buf
+
+
+def fp8_quantize_torch(X, dims):
+    """Block-scaled E4M3 buffer (uint8 torch tensor on X's device) of the flat column-major
+    FP32 torch tensor X with sizes dims (torch's float8_e4m3fn rounding, ties to even)."""
+    import torch
+
+    ld, m, off, nscales, total = fp8_storage_layout(dims)
+    I0 = int(dims[0])
+    buf = torch.zeros(total, dtype=torch.uint8, device=X.device)
+    codes = buf[:ld * m].view(m, ld)
+    scales = torch.empty(nscales, dtype=torch.float32, device=X.device)
+    Xv = X.view(m, I0)
+    # columns in slabs so the FP32 temporaries stay small; a slab covers whole 128-byte blocks
+    step = max(1, (1 << 26) // ld)
+    step = max(128, step // 128 * 128)
+    for c0 in range(0, m, step):
+        c1 = min(m, c0 + step)
+        P = torch.zeros((c1 - c0, ld), dtype=torch.float32, device=X.device)
+        P[:, :I0] = Xv[c0:c1]
+        flat = P.reshape(-1)
+        b0 = c0 * ld // 128
+        nb = -(-flat.numel() // 128)
+        fpad = torch.zeros(nb * 128, dtype=torch.float32, device=X.device)
+        fpad[:flat.numel()] = flat
+        blk = fpad.view(nb, 128)
+        amax = blk.abs().amax(dim=1)
+        sc = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax))
+        q = (blk / sc[:, None]).clamp_(-448.0, 448.0).to(torch.float8_e4m3fn).view(torch.uint8).reshape(-1)
+        codes.view(-1)[c0 * ld:c1 * ld] = q[:flat.numel()]
+        scales[b0:b0 + nb] = sc
+    buf[off:] = scales.view(torch.uint8)
+    return buf
+
+
+def bf16_bits_np(X):
+    """BF16 bit patterns (uint16, ties to even) of the numpy tensor X in column-major order."""
+    x = np.asarray(X, dtype=np.float32).ravel(order="F").view(np.uint32).astype(np.uint64)
+    r = (x + 0x7FFF + ((x >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
