@@ -186,6 +186,29 @@ def omega(seed, tensor_id, mode, rows, ell):
     return out[:, :ell]
 
 
+def omega_columns(seed, tensor_id, mode, rows, cols):
+    """Omega[rows, cols] for a list of column indices; only the Philox counters of those columns
+    (col // 4) are evaluated, so single columns of a very long Omega stay cheap."""
+    rows = np.asarray(rows, dtype=np.int64).ravel()
+    cols = [int(c) for c in cols]
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    k0, k1 = seed & 0xFFFFFFFF, seed >> 32
+    lo = (rows & 0xFFFFFFFF).astype(np.uint64)
+    hi = (rows >> 32).astype(np.uint64)
+    sid = np.full(rows.shape, stream_id(tensor_id, mode), dtype=np.uint64)
+    out = np.empty((rows.size, len(cols)), dtype=F32)
+    groups = {}
+    for j, c in enumerate(cols):
+        q = c // 4
+        if q not in groups:
+            w0, w1, w2, w3 = philox4x32_10(np.full(rows.shape, q, dtype=np.uint64), lo, hi, sid, k0, k1)
+            n0, n1 = box_muller_f32(w0, w1)
+            n2, n3 = box_muller_f32(w2, w3)
+            groups[q] = (n0, n1, n2, n3)
+        out[:, j] = groups[q][c % 4]
+    return out
+
+
 def round_bf16(x):
     """Round FP32 values to the nearest BF16 (ties to even), returned as FP32."""
     b = np.asarray(x, dtype=F32).view(np.uint32).astype(np.uint64)

@@ -62,3 +62,21 @@ def fp8_dequantize(buf, dims):
     x = (vals * s).astype(np.float32)                                  # FP32 product, ties to even
     X1 = np.reshape(x, (ld, mcols), order="F")[:dims[0], :]
     return np.reshape(X1.astype(np.float64), dims, order="F")
+
+
+def fp8_dequantize_rows(buf, dims, rows):
+    """Rows ``rows`` of the mode-1 unfolding of the tensor a block-scaled E4M3 buffer denotes
+    (float64 array len(rows) x prod(dims[1:])), read without expanding the rest of the tensor."""
+    buf = np.asarray(buf, dtype=np.uint8).ravel()
+    ld, off, nscales, total = fp8_layout(dims)
+    if buf.size != total:
+        raise ValueError(f"buffer has {buf.size} bytes, the layout needs {total}")
+    mcols = int(np.prod([int(v) for v in dims[1:]], dtype=np.int64)) if len(dims) > 1 else 1
+    scales = buf[off:off + 4 * nscales].view(np.float32)
+    table = e4m3_values().astype(np.float32)
+    out = np.empty((len(rows), mcols), dtype=np.float64)
+    p = np.arange(mcols, dtype=np.int64)
+    for j, i in enumerate(rows):
+        e = int(i) + ld * p
+        out[j] = (table[buf[e]] * scales[e // 128]).astype(np.float32)
+    return out

@@ -243,12 +243,10 @@ SketchPlan plan_sketch(const ModeView& v, int ell) {
   pl.gx = (int)ceil_div(v.I, kTI);
   const int64_t M = v.M();
   const int64_t ksteps = ceil_div(M, kKP);
-  // about 4 CTAs per SM, but at least kMinChunk columns per CTA: a small tensor is not spread
-  // over more splits than its size pays for (every split adds I x ell partial sums to reduce)
-  constexpr int64_t kMinChunk = 1024;
+  // about 4 CTAs per SM (the partial sums are reduced by warps over the splits, so many splits
+  // stay cheap even for small I)
   const int64_t target = 4LL * num_sms();
-  int64_t S = std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, pl.gx), ksteps));
-  S = std::max<int64_t>(1, std::min<int64_t>(S, ceil_div(M, kMinChunk)));
+  const int64_t S = std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, pl.gx), ksteps));
   pl.chunk = ceil_div(ceil_div(M, S), kKP) * kKP;
   pl.S = (int)ceil_div(M, pl.chunk);
   return pl;

@@ -280,6 +280,10 @@ rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, do
     return RH_ENUMERIC;
   }
   apply_inv(Q, I, ell, inv, A);
+  // A(P, :) = (P^T Q)(P^T Q)^{-1} is the identity in exact arithmetic: store it exactly, so that the
+  // decomposition reproduces X at the selected positions
+  for (int a = 0; a < ell; ++a)
+    for (int c = 0; c < ell; ++c) A[sel[a] + (size_t)I * c] = (a == c) ? 1.0 : 0.0;
   sel_out = sel;
   return RH_OK;
 }

@@ -1,0 +1,293 @@
+"""Parity at the full sizes of the workloads (needs a GB300 and tens of GB of host memory).
+
+The kernels run in the launch configuration of the full-size decomposition.  Where the oracle
+cannot redo the whole computation in seconds, parity is checked on outputs it computes one at a
+time -- single rows of the sketch, single columns of the mode product -- and on properties that
+hold at any size.  The 1024^3 FP32 decomposition of the benchmark is also redone end to end by the
+oracle (about a minute on the host).
+
+Gates (as in the small-size tests): a sketch entry of the tensor-core path is within
+(K + 8) 2^-24 (|x| . |omega|) of the FP64 sum over the represented input (head + tail of the FP32
+values, Omega rounded to BF16), K the columns one CTA accumulates; a mode-product entry within
+(I + 8) 2^-24 (|q| . |x|); the relative Tucker error within 1e-5 of the oracle's.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_07311_gb300 import build
+
+    build.build()
+    import paper_1905_07311_gb300 as rh
+
+    return rh
+
+
+from oracle import rng as orng  # noqa: E402
+from oracle import tucker as otk  # noqa: E402
+from oracle.storage import fp8_dequantize_rows  # noqa: E402
+from workloads import fp8_quantize_torch, lowrank_plus_noise_torch, zipf_coo_torch  # noqa: E402
+
+
+def _rep(x):
+    """head + tail (float64) of FP32 values, as the tensor cores see them."""
+    x = np.asarray(x, dtype=np.float32)
+    h = orng.round_bf16(x)
+    t = orng.round_bf16((x - h).astype(np.float32))
+    return h.astype(np.float64) + t.astype(np.float64)
+
+
+def _sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def _k_sketch(M):
+    chunks = -(-M // 64)
+    return -(-chunks // min(_sms(), chunks)) * 64 + 64
+
+
+def _check_sketch_rows(Y, xrows, rows, cols, M, seed, tid):
+    """Y: (ell, I) FP64 GPU sketch; xrows: represented rows of X_(1) (len(rows) x M)."""
+    om = orng.round_bf16(orng.omega_columns(seed, tid, 0, np.arange(M, dtype=np.int64), cols)).astype(np.float64)
+    ref = xrows @ om
+    bound = (_k_sketch(M) + 8) * 2.0 ** -24 * (np.abs(xrows) @ np.abs(om))
+    got = Y.cpu().numpy().T[np.ix_(rows, cols)]
+    assert np.all(np.abs(got - ref) <= bound + 1e-300), np.max(np.abs(got - ref) / (bound + 1e-300))
+
+
+def _rel_error_slabs(Xf, dims, factors, core, core_dims, slab=32):
+    """||X - G x_1 A_1 ... x_d A_d|| / ||X|| for a flat column-major FP32 X, slab by slab over the
+    last mode (numpy, FP64); factors as (r_n, I_n) arrays, core flat column-major."""
+    d = len(dims)
+    A = [np.asarray(f, dtype=np.float64).T for f in factors]
+    G = np.reshape(np.asarray(core, dtype=np.float64), core_dims, order="F")
+    # G x_1 A_1 ... x_{d-1} A_{d-1}: shape (I_1, ..., I_{d-1}, r_d)
+    H = G
+    for n in range(d - 1):
+        H = np.moveaxis(np.tensordot(A[n], H, axes=([1], [n])), 0, n)
+    Xv = np.reshape(Xf, (int(np.prod(dims[:-1])), dims[-1]), order="F")
+    Hm = np.reshape(H, (int(np.prod(dims[:-1])), core_dims[-1]), order="F")
+    num = den = 0.0
+    for k0 in range(0, dims[-1], slab):
+        k1 = min(dims[-1], k0 + slab)
+        Xs = Xv[:, k0:k1].astype(np.float64)
+        D = Xs - Hm @ A[-1][k0:k1].T
+        num += float(np.sum(D * D))
+        den += float(np.sum(Xs * Xs))
+    return np.sqrt(num / den)
+
+
+# ---------------------------------------------------------------------------------------------
+# 1024^3 FP32, rank (50, 50, 50), p = 10: the benchmark's workload and call
+# ---------------------------------------------------------------------------------------------
+DIMS2 = [1024, 1024, 1024]
+
+
+@pytest.fixture(scope="module")
+def x1024(rh):
+    X = lowrank_plus_noise_torch(DIMS2, [50] * 3, 0.9, 1e-3, 2, torch.float32, "cuda")
+    torch.cuda.synchronize()
+    yield X
+    del X
+    torch.cuda.empty_cache()
+
+
+def test_1024_sketch_rows_match_oracle(rh, x1024):
+    M = 1024 * 1024
+    Y = rh.rhosvd_sketch_bf16(x1024, DIMS2, 60, seed=0, tensor_id=0, pieces="f32")
+    rows, cols = [0, 517, 1023], [0, 1, 2, 3, 56, 57, 58, 59]
+    xrows = _rep(x1024.view(M, 1024)[:, rows].T.contiguous().cpu().numpy())
+    _check_sketch_rows(Y, xrows, rows, cols, M, 0, 0)
+
+
+def test_1024_mode_product_columns_match_oracle(rh, x1024):
+    M = 1024 * 1024
+    Q = np.linalg.qr(np.random.default_rng(9).standard_normal((1024, 60)))[0]
+    B = rh.mode_product_bf16(x1024, DIMS2, torch.from_numpy(Q.T.copy()).cuda(), pieces="f32").view(M, 60)
+    ps = [0, 777777, M - 1]
+    x = _rep(x1024.view(M, 1024)[ps].cpu().numpy())                 # columns p of X_(1), as rows
+    qf = Q.astype(np.float32)
+    qh = orng.round_bf16(qf)
+    qrep = qh.astype(np.float64) + orng.round_bf16((qf - qh).astype(np.float32)).astype(np.float64)
+    ref = x @ qrep
+    bound = (1024 + 8) * 2.0 ** -24 * (np.abs(x) @ np.abs(qrep))
+    got = B[ps].cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+def _host_available_gb():
+    import os
+
+    try:
+        return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
+    except (ValueError, OSError, AttributeError):
+        return 0.0
+
+
+def test_1024_rsthosvd_matches_oracle_end_to_end(rh, x1024):
+    """The benchmark's call (FP32 split on the fly, order 1, 2, 3) against the oracle on the same
+    represented input with the same Omega bits.  The oracle holds about 45 GB on the host."""
+    if _host_available_gb() < 96:
+        pytest.skip("needs about 45 GB of free host memory (96 GB available asked for headroom)")
+    T = rh.rsthosvd(x1024, DIMS2, [50, 50, 50], p=10, seed=0, rho=[0, 1, 2], form="f32_bf16x2")
+    torch.cuda.synchronize()
+    info = T.info.cpu().numpy().tolist()
+    assert info[0] & 4 and info[1] & 4
+    A = [f.cpu().numpy() for f in T.factors]
+    core = T.core.cpu().numpy()
+    for a in A:
+        assert np.abs(a @ a.T - np.eye(a.shape[0])).max() <= 2e-5
+    Xf = x1024.cpu().numpy()
+    Xrep = np.reshape(_rep(Xf), DIMS2, order="F")
+    nx = float(T.norms[0].item())
+    assert abs(nx - float(np.sum(Xrep * Xrep))) <= 1e-6 * nx
+    rnd = {m: "bf16" for m in range(3) if info[m] & 4}
+    out = otk.rsthosvd(Xrep, [50, 50, 50], 10, 0, rho=[0, 1, 2], omega_round=rnd)
+    Xrep_flat = Xrep.ravel(order="F")
+    del Xrep
+    e_g = _rel_error_slabs(Xrep_flat, DIMS2, A, core, T.core_dims)
+    e_o = _rel_error_slabs(Xrep_flat, DIMS2, [f.T for f in out["factors"]], out["core"].ravel(order="F"),
+                           list(out["core"].shape))
+    assert abs(e_g - e_o) <= 1e-5, (e_g, e_o)
+
+
+# ---------------------------------------------------------------------------------------------
+# 192^4 stored in E4M3 (block scales) and BF16, rank 30, p = 10; adaptive at 1e-2
+# ---------------------------------------------------------------------------------------------
+DIMS3 = [192, 192, 192, 192]
+
+
+@pytest.fixture(scope="module")
+def x192(rh):
+    X = lowrank_plus_noise_torch(DIMS3, [30] * 4, 0.8, 1e-3, 3, torch.float32, "cuda")
+    torch.cuda.synchronize()
+    yield X
+    del X
+    torch.cuda.empty_cache()
+
+
+def _dequantize_fp8_torch(buf, dims):
+    """The FP32 tensor an E4M3 buffer denotes, on the device (test-side, slab by slab)."""
+    from paper_1905_07311_gb300 import fp8_layout
+
+    lay = fp8_layout(dims)
+    ld, off, ns = lay["ld"], lay["scale_offset"], lay["nscales"]
+    I0 = dims[0]
+    M = int(np.prod(dims[1:]))
+    codes = buf[:ld * M].view(M, ld)
+    scales = buf[off:off + 4 * ns].view(torch.float32)
+    out = torch.empty(M * I0, dtype=torch.float32, device=buf.device).view(M, I0)
+    step = 1 << 16
+    for c0 in range(0, M, step):
+        c1 = min(M, c0 + step)
+        v = codes[c0:c1, :I0].contiguous().view(torch.float8_e4m3fn).to(torch.float32)
+        e = (torch.arange(c0, c1, device=buf.device, dtype=torch.int64)[:, None] * ld
+             + torch.arange(I0, device=buf.device, dtype=torch.int64)[None, :])
+        out[c0:c1] = v * scales[e // 128]
+    return out.view(-1)
+
+
+def test_192x4_fp8_full_size(rh, x192):
+    buf = fp8_quantize_torch(x192, DIMS3)
+    Xdq = _dequantize_fp8_torch(buf, DIMS3)
+    T8 = rh.rsthosvd(buf, DIMS3, [30] * 4, p=10, seed=0, form="fp8_e4m3")
+    t8 = [f.clone() for f in T8.factors] + [T8.core.clone()]
+    Tf = rh.rsthosvd(Xdq, DIMS3, [30] * 4, p=10, seed=0, form="f32_bf16x2")
+    torch.cuda.synchronize()
+    for a, b in zip(t8[:4], Tf.factors):
+        assert torch.equal(a, b)
+    assert torch.equal(t8[4], Tf.core)
+    # sampled sketch rows of the E4M3 path against the oracle's reading of the buffer
+    M = 192 ** 3
+    Y = rh.rhosvd_sketch_bf16(buf, DIMS3, 40, seed=0, tensor_id=0, pieces="fp8")
+    rows, cols = [0, 191], [0, 1, 2, 3]
+    xrows = _rep(fp8_dequantize_rows(buf.cpu().numpy(), DIMS3, rows))
+    _check_sketch_rows(Y, xrows, rows, cols, M, 0, 0)
+    for f in Tf.factors:
+        a = f.double()
+        assert (a @ a.T - torch.eye(a.shape[0], device=a.device, dtype=torch.float64)).abs().max().item() <= 2e-5
+
+
+def _rel_error_torch(X, dims, factors, core, core_dims):
+    """||X - X_hat|| / ||X|| in FP64 on the device, slab by slab over the last mode (test-side)."""
+    d = len(dims)
+    A = [f.double().T for f in factors]
+    G = core.double().view(*reversed(core_dims))            # axes (r_d, ..., r_1)
+    H = G
+    for n in range(d - 1):                                  # apply A_1 .. A_{d-1}
+        ax = d - 1 - n
+        H = torch.movedim(torch.tensordot(A[n], H, dims=([1], [ax])), 0, ax)
+    Xv = X.view(dims[-1], -1)
+    Hm = H.reshape(core_dims[-1], -1)
+    num = den = 0.0
+    for k0 in range(0, dims[-1], 16):
+        k1 = min(dims[-1], k0 + 16)
+        Xs = Xv[k0:k1].double()
+        D = Xs - A[-1][k0:k1] @ Hm
+        num += float((D * D).sum())
+        den += float((Xs * Xs).sum())
+    return (num / den) ** 0.5
+
+
+def test_192x4_bf16_adaptive_full_size(rh, x192):
+    Xb = x192.to(torch.bfloat16)
+    T = rh.adaptive(Xb.view(torch.int16), DIMS3, 1e-2, variant="sthosvd", block=8, p=10, seed=0, form="bf16")
+    torch.cuda.synchronize()
+    Xin = Xb.to(torch.float32)
+    e = _rel_error_torch(Xin, DIMS3, T.factors, T.core, T.ranks)
+    assert e <= 1e-2 * (1 + 1e-4), (e, T.ranks)
+    assert all(1 <= r <= 54 for r in T.ranks)
+    for f in T.factors:
+        a = f.double()
+        assert (a @ a.T - torch.eye(a.shape[0], device=a.device, dtype=torch.float64)).abs().max().item() <= 2e-5
+    nx = float(T.norms[0].item())
+    ref = float((Xin.double() ** 2).sum())
+    assert abs(nx - ref) <= 1e-6 * ref
+
+
+# ---------------------------------------------------------------------------------------------
+# Sparse COO 20000 x 20000 x 5000 with 5e7 nonzeros, rank 30, p = 10
+# ---------------------------------------------------------------------------------------------
+def test_sparse_full_size(rh):
+    dims = [20000, 20000, 5000]
+    idx, vals = zipf_coo_torch(dims, 50_000_000, 1.1, 3.0, 5, "cuda")
+    torch.cuda.synchronize()
+    # sampled sketch rows of mode 1 (row 0 holds the most nonzeros of a Zipf index)
+    Y = rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0, tensor_id=0).cpu().numpy().T
+    for i in (0, 7, 19999):
+        sel = (idx[0] == i).nonzero().flatten()
+        sub = np.stack([t[sel].long().cpu().numpy() for t in idx], axis=1)
+        v = vals[sel].double().cpu().numpy()
+        p = otk._kolda_rows(sub, dims, 0)                   # Kolda columns of X_(1)
+        om = orng.omega_columns(0, 0, 0, p, [0, 1, 38, 39]).astype(np.float64)
+        ref = v @ om
+        bound = (512 + 8) * 2.0 ** -24 * (np.abs(v) @ np.abs(om))
+        got = Y[i, [0, 1, 38, 39]]
+        assert np.all(np.abs(got - ref) <= bound + 1e-300), (i, got, ref)
+    T = rh.sp_sthosvd_coo(idx, vals, dims, [30, 30, 30], p=10, seed=0)
+    torch.cuda.synchronize()
+    keys = (idx[0].long() * dims[1] + idx[1].long()) * dims[2] + idx[2].long()
+    for n in range(3):
+        A = T.factors[n].double().T                          # I_n x ell
+        P = T.selected[n].long()
+        assert torch.equal(A[P], torch.eye(A.shape[1], dtype=torch.float64, device=A.device))
+        assert A.abs().max().item() <= 2.0 * (1 + 1e-6)
+    # the core holds the entries of X at the selected positions (zero where X has none)
+    s = [t.long() for t in T.selected]
+    gi = torch.cartesian_prod(s[0], s[1], s[2])
+    gk = (gi[:, 0] * dims[1] + gi[:, 1]) * dims[2] + gi[:, 2]
+    pos = torch.searchsorted(keys, gk).clamp(max=keys.numel() - 1)
+    hit = keys[pos] == gk
+    want = torch.where(hit, vals[pos].double(), torch.zeros_like(gk, dtype=torch.float64))
+    ell = [int(t.numel()) for t in T.selected]
+    core = T.core.double().view(ell[2], ell[1], ell[0]).permute(2, 1, 0).reshape(-1)
+    assert torch.equal(core, want)

@@ -84,7 +84,7 @@ def test_sp_sthosvd_matches_oracle(rh, dims, nnz, ranks, p):
     sel = [s.cpu().numpy().astype(np.int64) for s in T.selected]
     G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
     for n in range(d):
-        assert np.abs(A[n][sel[n], :] - np.eye(len(sel[n]))).max() <= 1e-10
+        assert np.array_equal(A[n][sel[n], :], np.eye(len(sel[n])))
         assert np.abs(A[n]).max() <= 2.0 + 1e-8
     # core entries are entries of X at the selected coordinates
     Xs = X

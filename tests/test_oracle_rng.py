@@ -137,3 +137,13 @@ def test_stream_id_limits(mode):
     assert rng.stream_id(5, mode) == (5 << 4) | mode
     with pytest.raises(ValueError):
         rng.stream_id(0, 16)
+
+
+def test_omega_columns_equal_the_full_draw():
+    from oracle import rng as r
+
+    rows = np.arange((1 << 32) - 50, (1 << 32) + 50, dtype=np.int64)
+    full = r.omega(11, 7, 2, rows, 64)
+    cols = [63, 0, 17, 18, 19, 20, 5]
+    sub = r.omega_columns(11, 7, 2, rows, cols)
+    assert np.array_equal(full[:, cols].view(np.uint32), sub.view(np.uint32))

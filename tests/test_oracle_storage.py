@@ -88,3 +88,15 @@ def test_quantizer_is_nearest_and_saturates():
     err = np.abs(Xd / s - np.clip(X / s, -448, 448)) - 0.5 * step
     assert np.all(err <= 1e-6 * step)
     assert np.all(Xd[:, 0, 0] == 0.0)
+
+
+def test_fp8_rows_equal_the_full_dequantization():
+    from oracle.storage import fp8_dequantize_rows
+    from oracle.tensor import unfold
+
+    rs = np.random.default_rng(3)
+    X = rs.standard_normal((20, 7, 5)).astype(np.float32)
+    buf = fp8_quantize_np(X)
+    full = unfold(fp8_dequantize(buf, X.shape), 0)
+    rows = [0, 7, 19]
+    assert np.array_equal(fp8_dequantize_rows(buf, X.shape, rows), full[rows])

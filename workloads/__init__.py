@@ -240,3 +240,48 @@ def bf16_bits_np(X):
     x = np.asarray(X, dtype=np.float32).ravel(order="F").view(np.uint32).astype(np.uint64)
     r = (x + 0x7FFF + ((x >> 16) & 1)) >> 16
     return r.astype(np.uint16)
+
+
+def zipf_coo_torch(dims, nnz, s, lam, seed, device):
+    """The ``zipf_coo`` recipe drawn with torch generators on ``device`` (for full-size inputs):
+    coordinates Zipf(s) per mode, the first ``nnz`` distinct tuples in draw order, sorted
+    lexicographically (mode 1 slowest), values log(1 + Poisson(lam) + 1) in FP64 stored as FP32.
+    Returns ([int32 index tensor per mode], FP32 values), all on ``device``."""
+    import torch
+
+    dims = [int(x) for x in dims]
+    d = len(dims)
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    cdfs = []
+    for I in dims:
+        w = torch.arange(1, I + 1, dtype=torch.float64, device=device) ** (-float(s))
+        c = torch.cumsum(w, 0)
+        cdfs.append(c / c[-1])
+    mult = [1] * d
+    for n in range(d - 2, -1, -1):
+        mult[n] = mult[n + 1] * dims[n + 1]
+    batch = max(1 << 20, nnz // 2)
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    while True:
+        k = torch.zeros(batch, dtype=torch.int64, device=device)
+        for n in range(d):
+            u = torch.rand(batch, generator=g, dtype=torch.float64, device=device)
+            col = torch.clamp(torch.searchsorted(cdfs[n], u), max=dims[n] - 1)
+            k += col * mult[n]
+        keys = torch.cat([keys, k])
+        uniq, inv = torch.unique(keys, return_inverse=True)
+        if uniq.numel() >= nnz:
+            pos = torch.arange(keys.numel(), device=device)
+            first = torch.full((uniq.numel(),), keys.numel(), dtype=torch.int64, device=device)
+            first.scatter_reduce_(0, inv, pos, reduce="amin")
+            order = torch.argsort(first)[:nnz]
+            keys = torch.sort(uniq[order]).values
+            break
+    idx = []
+    rem = keys.clone()
+    for n in range(d):
+        idx.append((rem // mult[n]).to(torch.int32))
+        rem = rem % mult[n]
+    lamt = torch.full((nnz,), float(lam), dtype=torch.float64, device=device)
+    vals = torch.log(1.0 + torch.poisson(lamt, generator=g) + 1.0).to(torch.float32)
+    return idx, vals
