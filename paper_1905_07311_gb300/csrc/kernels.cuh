@@ -51,6 +51,12 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
                         uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
                             int32_t* err, cudaStream_t st);
+// G <- U^T B on the tensor cores for a truncated core (Alg. 1 step 6): B ell x M FP32 (layout
+// c + ell p, split on the fly), U ell x ko FP32 (split into two BF16 pieces in qa, 128 x ceil8(ell)),
+// out[(p % Lp) + Lp (c + ko (p / Lp))] FP32.  Needs ell % 4 == 0, ell, ko <= 64.
+bool core_product_tc_supported(int ell, int ko, int64_t M);
+rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, uint16_t* qa,
+                                 float* out, int32_t* err, cudaStream_t st);
 rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                             const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
 

@@ -68,6 +68,7 @@ struct Step {
   TruncPlan tr;
   bool tc = false;      // sketch and mode product on the tensor cores (FP32 core split on the fly)
   int64_t out_lp = 0;   // core product into out[(p % out_lp) + out_lp (c + ko (p / out_lp))]; 0: mode product
+  bool cp_tc = false;   // that core product on the tensor cores (B and U_r split into BF16 pieces)
 };
 
 struct Plan {
@@ -194,7 +195,13 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
         }
       }
     }
-    for (const Step& sp : pl.steps) {
+    for (size_t j = 0; j < pl.steps.size(); ++j) {
+      Step& sp = pl.steps[j];
+      // the truncated core of a non-final mode on the tensor cores (the final core is FP64)
+      if (sp.out_lp > 0 && j + 1 < pl.steps.size() && core_product_tc_supported(sp.ell, sp.ko, sp.v.M())) {
+        sp.cp_tc = true;
+        pl.qa_elems = std::max(pl.qa_elems, (size_t)128 * ((sp.ell + 7) / 8 * 8));
+      }
       if (!sp.tc) continue;
       pl.tc_part = std::max(pl.tc_part, (size_t)sketch_tc_ctas(sp.v) * sp.ell * sp.v.I);
       pl.qa_elems = std::max(pl.qa_elems, (size_t)128 * sp.v.I);
@@ -421,9 +428,13 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
             return s;
         } else {
           const int wg = 1 - wb;
-          if ((s = launch_core_product<float>(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf,
-                                              static_cast<float*>(b.W[wg]), st)) != RH_OK)
-            return s;
+          if (sp.cp_tc)
+            s = launch_core_product_tc(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf, b.qa, static_cast<float*>(b.W[wg]),
+                                       b.err, st);
+          else
+            s = launch_core_product<float>(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf, static_cast<float*>(b.W[wg]),
+                                           st);
+          if (s != RH_OK) return s;
           cur = static_cast<const T*>(b.W[wg]);
           cur_buf = wg;
         }

@@ -42,13 +42,13 @@ constexpr uint32_t kFp8Box = kNTile * 64;      // E4M3 TMA box: 64 rows (bytes) 
 
 // BF16 pieces in: 3 stages (A slice + pieces) filled by TMA.  FP32 in: 3 stages of FP32 slices
 // filled by TMA, split by eight converter warps into 2 stages of pieces; the converters also
-// request the A slice of their stage.  E4M3 in: 4 stages of byte slices, dequantized and split
+// request the A slice of their stage.  E4M3 in: 8 stages of byte slices, dequantized and split
 // the same way.
 template <int IN>
 struct TtmCfg {
   static constexpr bool kConvIn = IN != tc::kInPieces;
   static constexpr int kPStages = kConvIn ? 2 : 3;
-  static constexpr int kF32Stages = IN == tc::kInF32 ? 3 : (IN == tc::kInFp8 ? 4 : 1);
+  static constexpr int kF32Stages = IN == tc::kInF32 ? 3 : (IN == tc::kInFp8 ? 8 : 1);
   static constexpr uint32_t kStageBytes = IN == tc::kInF32 ? 2 * kF32Box : (IN == tc::kInFp8 ? kFp8Box : 1024);
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
   static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
@@ -77,7 +77,8 @@ template <int IN>
 __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
-                  float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld) {
+                  float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld,
+                  int64_t Lp) {
   using Cfg = TtmCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -208,22 +209,51 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
         }
       }
       named_sync(1, 128);
-      if (!tail) {
-        const int64_t p0 = t * kNTile;
-        for (int cc = 0; cc < kNTile / 16; ++cc) {
-          float v[16];
-          tc::tmem_ld16(base + cc * 16, v);
-          if (crow < ell) {
+      const int64_t p0 = t * kNTile;
+      if (Lp == 1) {
+        // B[c + ell p]: the threads of a warp hold consecutive rows c, so the stores are coalesced
+        if (!tail) {
+          for (int cc = 0; cc < kNTile / 16; ++cc) {
+            float v[16];
+            tc::tmem_ld16(base + cc * 16, v);
+            if (crow < ell) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int64_t p = p0 + cc * 16 + j;
-              if (p < M) B[crow + (int64_t)ell * p] = v[j] + S.xchg[crow][cc * 16 + j];
+              for (int j = 0; j < 16; ++j) {
+                const int64_t p = p0 + cc * 16 + j;
+                if (p < M) B[crow + (int64_t)ell * p] = v[j] + S.xchg[crow][cc * 16 + j];
+              }
             }
           }
         }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&S.tempty[b]);
+      } else {
+        // B[(p % Lp) + Lp (c + ell (p / Lp))]: sum the halves in shared memory, then each warp
+        // writes whole rows c with its lanes along p
+        if (!tail) {
+          for (int cc = 0; cc < kNTile / 16; ++cc) {
+            float v[16];
+            tc::tmem_ld16(base + cc * 16, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) S.xchg[crow][cc * 16 + j] += v[j];
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&S.tempty[b]);
+        named_sync(1, 128);
+        const int wq = warp - 2;   // 0..3
+        int64_t q0 = (p0 + lane) / Lp, r0 = (p0 + lane) - q0 * Lp;
+        for (int jj = lane; jj < kNTile; jj += 32) {
+          const int64_t p = p0 + jj;
+          if (p < M)
+            for (int c = wq; c < ell; c += 4) B[r0 + Lp * ((int64_t)c + (int64_t)ell * q0)] = S.xchg[c][jj];
+          r0 += 32;
+          while (r0 >= Lp) {
+            r0 -= Lp;
+            ++q0;
+          }
+        }
       }
-      tc::tc_fence_before();
-      tc::mbar_arrive(&S.tempty[b]);
       named_sync(1, 128);   // xchg is free again
     }
   } else if constexpr (F32IN) {
@@ -262,15 +292,17 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
   if (warp == 1) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
-// A = [bf16(Q)^T; bf16(Q - bf16(Q))^T] as a 128 x I row-major BF16 matrix; rows >= ell are zero.
-__global__ void q_pieces_kernel(const double* __restrict__ Q, int64_t I, int ell, uint16_t* __restrict__ A) {
-  const int64_t total = 128 * I;
+// A = [bf16(Q)^T; bf16(Q - bf16(Q))^T] as a 128 x I row-major BF16 matrix with leading dimension
+// ldA >= I (ldA % 8 == 0 for the tensor map); rows >= ell and columns >= I are zero.
+template <typename TQ>
+__global__ void q_pieces_kernel(const TQ* __restrict__ Q, int64_t I, int ell, int64_t ldA, uint16_t* __restrict__ A) {
+  const int64_t total = 128 * ldA;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % I;
-    const int r = (int)(e / I);
+    const int64_t i = e % ldA;
+    const int r = (int)(e / ldA);
     const int c = r & 63;
     uint16_t out = 0;
-    if (c < ell) {
+    if (c < ell && i < I) {
       const float q = (float)Q[i + I * c];   // FP64 -> FP32 first (24 bits >= the 16 kept)
       const uint16_t h = tc::bf16_rne(q);
       out = (r < 64) ? h : tc::bf16_rne(q - tc::bf16_to_f(h));
@@ -298,7 +330,7 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   {
     const int64_t total = 128 * v.I;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
-    q_pieces_kernel<<<blocks, 256, 0, st>>>(Q, v.I, ell, qa);
+    q_pieces_kernel<double><<<blocks, 256, 0, st>>>(Q, v.I, ell, v.I, qa);
     RH_LAUNCH_CHECK();
   }
   CUtensorMap mA, m0, m1;
@@ -315,7 +347,7 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0);
+                                                                         nullptr, 0, 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -329,7 +361,7 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   {
     const int64_t total = 128 * v.I;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
-    q_pieces_kernel<<<blocks, 256, 0, st>>>(Q, v.I, ell, qa);
+    q_pieces_kernel<double><<<blocks, 256, 0, st>>>(Q, v.I, ell, v.I, qa);
     RH_LAUNCH_CHECK();
   }
   CUtensorMap mA, m0;
@@ -340,7 +372,37 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0);
+                                                                         nullptr, 0, 1);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+bool core_product_tc_supported(int ell, int ko, int64_t M) {
+  return ell >= 1 && ell <= 64 && ell % 4 == 0 && ko >= 1 && ko <= 64 && M >= 1 && M < (int64_t(1) << 31);
+}
+
+rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, uint16_t* qa,
+                                 float* out, int32_t* err, cudaStream_t st) {
+  if (!core_product_tc_supported(ell, ko, M) || Lp < 1 || M % Lp != 0) {
+    set_error("tensor-core core product: unsupported shape (needs ell % 4 == 0, ell, r <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  const int64_t ldA = (ell + 7) / 8 * 8;
+  {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(128 * ldA, 256), 2 * num_sms()));
+    q_pieces_kernel<float><<<blocks, 256, 0, st>>>(U, ell, ko, ldA, qa);
+    RH_LAUNCH_CHECK();
+  }
+  CUtensorMap mA, m0;
+  rh_status s = make_bf16_map_2d(&mA, qa, ldA, 128, 128);
+  if (s != RH_OK) return s;
+  if ((s = make_map_2d(&m0, B, 4, ell, M, kNTile)) != RH_OK) return s;
+  const ModeView v{1, (int64_t)ell, M};
+  constexpr int IN = tc::kInF32;
+  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err, nullptr,
+                                                                         0, Lp);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -355,7 +417,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   {
     const int64_t total = 128 * v.I;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
-    q_pieces_kernel<<<blocks, 256, 0, st>>>(Q, v.I, ell, qa);
+    q_pieces_kernel<double><<<blocks, 256, 0, st>>>(Q, v.I, ell, v.I, qa);
     RH_LAUNCH_CHECK();
   }
   CUtensorMap mA, m0;
@@ -366,7 +428,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         scales, ld);
+                                                                         scales, ld, 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

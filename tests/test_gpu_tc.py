@@ -117,7 +117,12 @@ def test_tc_mode_product_matches_definition(rh, pieces, shape, k):
                                                ((1024, 40, 30), (8, 6, 5), 4, [0, 1, 2]),
                                                ((256, 96, 48), (12, 10, 8), 6, [0, 2, 1]),
                                                ((64, 48, 40, 16), (6, 5, 4, 3), 3, [0, 1, 2, 3]),
-                                               ((64, 40, 24, 16), (6, 5, 4, 3), 3, [0, 1, 3, 2])])
+                                               ((64, 40, 24, 16), (6, 5, 4, 3), 3, [0, 1, 3, 2]),
+                                               # ell % 4 == 0: truncated cores on the tensor cores, written
+                                               # with the next mode fastest (Lp = 72) and in the usual
+                                               # order (Lp = 20 < 32), ragged last tiles
+                                               ((256, 72, 50), (20, 12, 10), 8, [0, 1, 2]),
+                                               ((96, 40, 24, 36), (12, 8, 8, 8), 4, [0, 1, 2, 3])])
 def test_rsthosvd_bf16x2_matches_oracle(rh, shape, ranks, p, rho):
     from oracle import tucker as otk
     from oracle.tensor import rel_error
