@@ -110,9 +110,13 @@ typedef struct rh_options {
                                  /* 1: ell_n = min(r_n + p, I_n, prod_{k!=n} I_k)                */
   int32_t truncate;              /* 1: rank r_n via the SVD of B (Alg. 1 steps 4-6, default)     */
                                  /* 0: keep all ell_n columns, A_n = Q_n, G <- Q_n^T G           */
+  int32_t svd_route;             /* SVD of B for FP32 data: 0 = automatic (FP32 Gram, double-    */
+                                 /* float Gram, tall-skinny QR, see rsthosvd); 1 = always the    */
+                                 /* tall-skinny Householder QR of B^T (FP64 data always use it)  */
 } rh_options;
 
-/* Fill ``opts`` with defaults: seed 0, tensor_id 0, p 5, rho decreasing, clamp 0, truncate 1. */
+/* Fill ``opts`` with defaults: seed 0, tensor_id 0, p 5, rho decreasing, clamp 0, truncate 1,
+ * svd_route 0. */
 void rh_options_default(rh_options* opts);
 
 /* Version string and the message of the last failure on this thread ("" after success). */
@@ -257,14 +261,17 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
  *   info     optional device int32 array of ``order`` values, bit flags per mode n:
  *            1 = the QR of the sketch took the Householder branch; 2 = the truncation
  *            SVD went through the Gram matrix (FP32 data only, see below); 4 = the sketch and
- *            mode product of mode n ran on the tensor cores (BF16 forms).
+ *            mode product of mode n ran on the tensor cores (BF16 forms); 8 = the truncation
+ *            SVD went through the double-float Gram matrix.
  *   Size rule: ell_n <= min(I_n, prod of the other current sizes), else RH_EINVAL (or
  *   clamped, opts->clamp).  Steps per mode n (in order rho):
  *     sketch Y = G_(n) Omega_n; Q = orth(Y); B = Q^T G_(n) (mode-n product);
  *     R with B B^T = R^T R: FP32 data first form W = B B^T (FP64 sums of FP32 partial
- *     sums) and its Cholesky factor, kept when that succeeds and sigma_r^2 - sigma_{r+1}^2
- *     >= 1e-5 sigma_1^2; otherwise (and for FP64 data) B^T = Q_B R by a tall-skinny
- *     Householder QR; one-sided Jacobi SVD of R gives U_B;
+ *     sums) and its pivoted Cholesky factor, kept when that succeeds and sigma_r^2 -
+ *     sigma_{r+1}^2 >= 1e-5 sigma_1^2; otherwise W again with every product exact and the
+ *     sums in double-float (~2^-44 relative), kept when its Cholesky succeeds; otherwise (and
+ *     for FP64 data) B^T = Q_B R by a tall-skinny Householder QR; one-sided Jacobi SVD of the
+ *     factor gives U_B;
  *     A_n = Q U_B(:, 1:r_n); G <- U_B(:, 1:r_n)^T B.
  */
 size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,

@@ -263,7 +263,7 @@ class RsthosvdCall:
     ALG = "rsthosvd"
 
     def __init__(self, dims, dtype, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True,
-                 device="cuda"):
+                 device="cuda", svd_route=0):
         torch = _torch()
         self.dims = [int(x) for x in dims]
         d = len(self.dims)
@@ -273,7 +273,8 @@ class RsthosvdCall:
         else:
             self.dt = RH_F64 if dtype == torch.float64 else RH_F32
             self.factor = 1
-        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate)
+        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate,
+                                 svd_route=svd_route)
         self.da = i64_array(self.dims)
         self.ra = i32_array(ranks)
         self._fn = getattr(lib(), self.ALG)
@@ -335,15 +336,15 @@ class RhosvdCall(RsthosvdCall):
     ALG = "rhosvd"
 
 
-def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True):
+def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, svd_route=0):
     """R-HOSVD (Alg. 2) of the flat column-major tensor X with sizes ``dims``."""
     call = RhosvdCall(dims, X.dtype, ranks, p=p, seed=seed, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
-                      device=X.device)
+                      device=X.device, svd_route=svd_route)
     return call.run(X)
 
 
 def adaptive(X, dims, eps, variant="sthosvd", block=8, max_ranks=None, p=10, seed=0, rho=None, tensor_id=0,
-             form=None):
+             form=None, svd_route=0):
     """Adaptive-rank R-HOSVD (``variant="hosvd"``, Alg. 4) or R-STHOSVD (``"sthosvd"``, Alg. 5) of the
     flat column-major tensor X to relative error ``eps`` (tolerance eps ||X|| / sqrt(d) per mode).
     ``max_ranks`` caps the range finder per mode (default min(I_n, 64 - p)).  ``form`` selects a
@@ -362,7 +363,7 @@ def adaptive(X, dims, eps, variant="sthosvd", block=8, max_ranks=None, p=10, see
     vcode = {"hosvd": 0, "sthosvd": 1}[variant]
     dt = _FORMS[form] if form is not None else _dtype_code(X)
     da, ma = i64_array(dims), i32_array(max_ranks)
-    opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho)
+    opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, svd_route=svd_route)
     ws_bytes = lib().adaptive_rank_workspace_size(d, da, dt, vcode, ma, ctypes.byref(opts))
     if ws_bytes == 0:
         raise ValueError("invalid adaptive request (check dtype, max_ranks + p <= 64)")
@@ -471,14 +472,16 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, c
     return T
 
 
-def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None):
+def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None,
+             svd_route=0):
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 
     ``form="bf16x2"`` (X from split_bf16x2), ``form="bf16"`` (X holding BF16 bit patterns),
     ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly) or ``form="fp8_e4m3"`` (X a uint8
-    buffer in the layout of fp8_layout) selects the tensor-core forms for the first mode."""
+    buffer in the layout of fp8_layout) selects the tensor-core forms for the first mode.
+    ``svd_route=1`` keeps the SVD of B on the tall-skinny QR (see rh_options.svd_route)."""
     call = RsthosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
-                        truncate=truncate, device=X.device)
+                        truncate=truncate, device=X.device, svd_route=svd_route)
     return call.run(X)
 
 

@@ -20,7 +20,8 @@ STATUS = {0: "RH_OK", 1: "RH_EINVAL", 2: "RH_ENOMEM", 3: "RH_ECUDA", 4: "RH_ENUM
 
 class RhOptions(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("tensor_id", ctypes.c_int32), ("p", ctypes.c_int32),
-                ("rho", ctypes.c_int32 * RH_MAX_ORDER), ("clamp", ctypes.c_int32), ("truncate", ctypes.c_int32)]
+                ("rho", ctypes.c_int32 * RH_MAX_ORDER), ("clamp", ctypes.c_int32), ("truncate", ctypes.c_int32),
+                ("svd_route", ctypes.c_int32)]
 
 
 class RhError(RuntimeError):
@@ -110,7 +111,7 @@ def i32_array(vals):
     return (ctypes.c_int32 * len(vals))(*[int(v) for v in vals])
 
 
-def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True):
+def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True, svd_route=0):
     o = RhOptions()
     lib().rh_options_default(ctypes.byref(o))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
@@ -121,4 +122,5 @@ def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True)
             o.rho[k] = int(m)
     o.clamp = int(bool(clamp))
     o.truncate = int(bool(truncate))
+    o.svd_route = int(svd_route)
     return o

@@ -200,7 +200,7 @@ rh_status tc_mode_product(const ModeView& v, int ell, const TcInput& in, const A
 template <typename T>
 rh_status adapt_mode(const ModeView& v, const T* G, const TcInput* tci, int cap, int p, int b_blk, double eps, int d,
                      double* tau2, uint64_t seed, uint32_t sid, const AdaptBufs& bf, double* factor, int* r_out,
-                     int* ell_out, double* g2_out, cudaStream_t st) {
+                     int* ell_out, double* g2_out, cudaStream_t st, bool qr_only) {
   rh_status s;
   const int ell = (int)std::min<int64_t>((int64_t)cap + p, std::min<int64_t>(v.I, v.M()));
   const int kmax = (int)std::min<int64_t>(cap, std::min<int64_t>(v.I, v.M()));
@@ -222,7 +222,7 @@ rh_status adapt_mode(const ModeView& v, const T* G, const TcInput* tci, int cap,
   }
   // factor of the whole B: Gram matrix (FP32 data) or the tall-skinny QR triangle; row norms of B
   const TruncPlan tp = plan_trunc(ModeView{v.L, (int64_t)ell, v.R}, ell);
-  bool gram = sizeof(T) == 4;
+  bool gram = sizeof(T) == 4 && !qr_only;
   T* R = nullptr;
   if ((s = launch_trunc_factor<T>(tp, B, static_cast<T*>(bf.trunc), gram, bf.gpart, bf.W, &R, bf.d, st)) != RH_OK)
     return s;
@@ -254,7 +254,10 @@ rh_status adapt_mode(const ModeView& v, const T* G, const TcInput* tci, int cap,
   for (int i = 0; i < kp; ++i) pk += d2[i];
   const double res2 = std::max(0.0, g2 - pk);
   std::vector<double> sv(kp);
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  // routes for FP32 data: FP32 Gram (kept when its Cholesky succeeds and the truncation gap is
+  // resolved), double-float Gram (kept when its Cholesky succeeds), tall-skinny QR of B^T
+  bool df = false;
+  for (int attempt = 0; attempt < 3; ++attempt) {
     if ((s = launch_trunc_leading_svd<T>(ell, kp, gram, bf.W, R, bf.Wk, bf.Xf, static_cast<T*>(bf.Rk), bf.Ub, bf.sv,
                                          bf.flag, st)) != RH_OK)
       return s;
@@ -265,10 +268,13 @@ rh_status adapt_mode(const ModeView& v, const T* G, const TcInput* tci, int cap,
     if (!gram) break;
     const int r = trim_rank(sv, res2, t2);
     const bool gap_ok = r >= kp || sv[0] == 0.0 || (sv[r - 1] * sv[r - 1] - sv[r] * sv[r] >= 1e-5 * sv[0] * sv[0]);
-    if (!flag && gap_ok) break;
-    // the FP32 Gram matrix cannot resolve this truncation: tall-skinny QR of B^T instead
-    gram = false;
-    if ((s = launch_trunc_factor<T>(tp, B, static_cast<T*>(bf.trunc), false, bf.gpart, bf.W, &R, bf.d, st)) != RH_OK)
+    if (!flag && (gap_ok || df)) break;
+    if (!df)
+      df = true;       // the FP32 Gram matrix cannot resolve this truncation: the double-float one can
+    else
+      gram = false;    // the double-float Cholesky broke down: tall-skinny QR of B^T
+    if ((s = launch_trunc_factor<T>(tp, B, static_cast<T*>(bf.trunc), gram, bf.gpart, bf.W, &R, bf.d, st, df)) !=
+        RH_OK)
       return s;
   }
   const int r = trim_rank(sv, res2, t2);
@@ -306,7 +312,7 @@ rh_status run_adaptive(int32_t order, const int64_t* dims, const T* X, const TcI
     int r = 0, ell = 0;
     double g2 = 0.0;
     if ((s = adapt_mode<T>(v, variant == 1 ? G : X, j == 0 ? tci : nullptr, caps[n], o.p, b_blk, eps, order, &tau2,
-                           o.seed, sid, bf, factors[n], &r, &ell, &g2, st)) != RH_OK)
+                           o.seed, sid, bf, factors[n], &r, &ell, &g2, st, o.svd_route != 0)) != RH_OK)
       return s;
     if (j == 0) nx2 = g2;
     ranks[n] = r;
@@ -438,6 +444,7 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
   rh_options_default(&o);
   if (opts) o = *opts;
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
+  RH_CHECK_ARG(o.svd_route == 0 || o.svd_route == 1, "svd_route must be 0 or 1");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
   if (variant == 1 && o.rho[0] >= 0) {
     std::vector<int> seen(order, 0);

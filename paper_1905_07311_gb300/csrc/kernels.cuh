@@ -125,7 +125,7 @@ rh_status launch_trunc_svd(const TruncPlan& pl, const T* B, T* ws, double* Ub, d
 // through the Jacobi SVD of R[0:k, 0:k] (Wk, Xf, Rk: k x k scratch).
 template <typename T>
 rh_status launch_trunc_factor(const TruncPlan& pl, const T* B, T* ws, bool gram, double* part, double* W, T** R,
-                              double* rownorm2, cudaStream_t st);
+                              double* rownorm2, cudaStream_t st, bool df = false);
 template <typename T>
 rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, const T* R, double* Wk, float* Xf,
                                    T* Rk, double* Ub, double* sv, int32_t* flag, cudaStream_t st);

@@ -52,6 +52,7 @@ void rh_options_default(rh_options* o) {
   for (int i = 0; i < RH_MAX_ORDER; ++i) o->rho[i] = -1;
   o->clamp = 0;
   o->truncate = 1;
+  o->svd_route = 0;
 }
 
 rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0, int64_t nrows, int32_t ell,

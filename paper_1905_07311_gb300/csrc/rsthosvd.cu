@@ -89,6 +89,7 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
   RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  RH_CHECK_ARG(o.svd_route == 0 || o.svd_route == 1, "svd_route must be 0 or 1");
   for (int k = 0; k < order; ++k) RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");
   std::vector<int> rho(order);
   if (o.rho[0] < 0) {
@@ -218,6 +219,7 @@ rh_status make_plan_hosvd(int32_t order, const int64_t* dims, int32_t dtype, con
   RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  RH_CHECK_ARG(o.svd_route == 0 || o.svd_route == 1, "svd_route must be 0 or 1");
   for (int k = 0; k < order; ++k) RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");
   pl.d = order;
   pl.dtype = dtype;
@@ -411,7 +413,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       // Alg. 1 steps 4-6: SVD of B, A_n = Q U_B(:, 1:r), G_(n) <- S V^T = U_B(:, 1:r)^T B
       {
         ProfileScope ps(PROF_TRUNC, j, st);
-        if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, sp.ko,
+        // r = 0 keeps the truncation SVD on the tall-skinny QR (svd_route 1)
+        if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, o.svd_route ? 0 : sp.ko,
                                       info ? info + sp.mode : nullptr)) != RH_OK) return s;
       }
       if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
@@ -501,7 +504,7 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
     }
     {
       ProfileScope ps(PROF_TRUNC, (int)j, st);
-      if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, sp.ko,
+      if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, o.svd_route ? 0 : sp.ko,
                                       info ? info + sp.mode : nullptr)) != RH_OK) return s;
     }
     if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),

@@ -12,6 +12,8 @@
 //   factor          A_n = Q U_B(:, 1:r) (Alg. 1 step 5).
 #include <math.h>
 
+#include <utility>
+
 #include "common.cuh"
 #include "dfloat.cuh"
 #include "kernels.cuh"
@@ -509,6 +511,166 @@ __global__ void __launch_bounds__(1024) tsqr_merge_kernel(const T* __restrict__ 
   }
 }
 
+// ---- FP32 tall-skinny QR with one row per thread ----------------------------------------------
+// Householder QR of a block of up to 256 rows of B^T (n <= NC columns), every row held in the
+// registers of one thread (the column loop is unrolled, so register indices are static).  Per
+// column k: ||x||^2 of column k from the diagonal down (warp shuffles, 8 warp partials), the
+// reflector v = x + sign(x_k) ||x|| e_k, the products v_r a_r[j] staged in shared memory and summed
+// by columns (segments of NC rows, then the segment partials), and the update
+// a_r[j] -= beta w_j v_r with beta = 1 / (||x|| (||x|| + |x_k|)).  Four barriers per column, all
+// with 256 threads.  Leaf blocks read 256 rows of B^T from the (L, n, R) view of B; merge blocks
+// stack ``fan`` upper triangles (n x n, column-major) of the previous level, fan n <= 256.
+constexpr int kRowsQR = 256;
+
+// ---- FP32 tall-skinny QR, 256-row blocks in shared memory -------------------------------------
+// Householder QR of a block of up to 256 rows of B^T (n <= NC columns) held row-major in shared
+// memory (odd leading dimension: conflict-free row and column access).  Per column k: ||x||^2 of
+// column k from the diagonal down (warp shuffles, 8 warp partials), the reflector
+// v = x + sign(x_k) ||x|| e_k, the products w_j = sum_r v_r A(r, j) summed by (segment, column)
+// threads (256 / NC segments of NC rows) and then over segments, and the row update
+// A(r, j) -= beta w_j v_r with beta = 1 / (||x|| (||x|| + |x_k|)).  Four barriers per column, all
+// loops rolled (small code).  Leaf blocks read 256 rows of B^T from the (L, n, R) view of B; merge
+// blocks stack ``fan`` upper triangles (n x n, column-major) of the previous level, fan n <= 256.
+template <int NC>
+__global__ void __launch_bounds__(kRowsQR) tsqr_rows_kernel(const float* __restrict__ B, int64_t L, int64_t R, int n,
+                                                            const float* __restrict__ Rin, int64_t nin, int fan,
+                                                            float* __restrict__ Rout,
+                                                            const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  constexpr int LD = NC + 1;
+  constexpr int SEG = kRowsQR / NC;   // row segments of the column sums, NC rows each
+  extern __shared__ float qsm[];
+  float* A = qsm;                      // [256][LD]
+  float* Vs = A + kRowsQR * LD;        // [256]: v
+  float* Sg = Vs + kRowsQR;            // [SEG][NC]
+  float* Wv = Sg + SEG * NC;           // [NC]: beta w_j
+  __shared__ float red[kRowsQR / 32];
+  __shared__ float sh_alpha;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int cj = t % NC, cseg = t / NC;
+  const bool leaf = (Rin == nullptr);
+  const int64_t M = L * R;
+  const int64_t nblk = leaf ? (M + kRowsQR - 1) / kRowsQR : (nin + fan - 1) / fan;
+  float* Arow = A + t * LD;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    __syncthreads();   // shared buffers are free (previous block)
+    if (leaf) {
+      const int64_t p0 = blk * kRowsQR;
+      const int rows = (int)(M - p0 < kRowsQR ? M - p0 : kRowsQR);
+      if (L == 1) {
+        // the block's rows of B^T are n consecutive floats each: a coalesced copy
+        const float* src = B + (int64_t)n * p0;
+        for (int e = t; e < kRowsQR * n; e += kRowsQR) {
+          const int r = e / n, c = e - r * n;
+          A[r * LD + c] = (r < rows) ? src[e] : 0.0f;
+        }
+      } else {
+        const bool ok = t < rows;
+        const int64_t p = p0 + t;
+        const int64_t base = ok ? (p % L) + L * (int64_t)n * (p / L) : 0;
+        for (int c = 0; c < n; ++c) Arow[c] = ok ? B[base + L * c] : 0.0f;
+      }
+    } else {
+      const int64_t b0 = blk * fan;
+      const int cnt = (int)(nin - b0 < fan ? nin - b0 : fan);
+      const int q = t / n, j = t - q * n;
+      const bool ok = q < cnt;
+      const float* src = Rin + (b0 + (ok ? q : 0)) * (int64_t)n * n + j;
+      for (int c = 0; c < n; ++c) Arow[c] = ok ? src[(int64_t)n * c] : 0.0f;
+    }
+    for (int k = 0; k < n; ++k) {
+      __syncthreads();   // the previous column's updates are visible
+      const float xk = (t >= k) ? Arow[k] : 0.0f;
+      float sq = xk * xk;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) red[wid] = sq;
+      if (t == k) sh_alpha = xk;
+      __syncthreads();
+      float ss = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kRowsQR / 32; ++w) ss += red[w];
+      const float alpha = sh_alpha;
+      const float nrm = sqrtf(ss);
+      if (!(nrm > 0.0f)) continue;   // uniform: every thread sums the same partials
+      const float sg = alpha >= 0.0f ? 1.0f : -1.0f;
+      const float beta = 1.0f / (nrm * (nrm + fabsf(alpha)));
+      const float v = (t == k) ? alpha + sg * nrm : xk;
+      Vs[t] = v;
+      __syncthreads();
+      if (cj > k && cj < n) {
+        const int r0 = cseg * NC;
+        // v vanishes above the diagonal; eight independent chains keep the loads in flight
+        const int rb = r0 > k ? r0 : k;
+        float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        int r = rb;
+        for (; r + 7 < r0 + NC; r += 8) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[q] = fmaf(Vs[r + q], A[(r + q) * LD + cj], acc[q]);
+        }
+        for (; r < r0 + NC; ++r) acc[0] = fmaf(Vs[r], A[r * LD + cj], acc[0]);
+        Sg[cseg * NC + cj] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+      }
+      __syncthreads();
+      if (t > k && t < n) {
+        float w = 0.0f;
+        for (int q = 0; q < SEG; ++q) w += Sg[q * NC + t];   // every segment wrote its partial
+        Wv[t] = beta * w;
+      }
+      __syncthreads();
+      if (t >= k) {
+#pragma unroll 4
+        for (int j = k + 1; j < n; ++j) Arow[j] = fmaf(-Wv[j], v, Arow[j]);
+      }
+      if (t == k)
+        Arow[k] = -sg * nrm;
+      else if (t > k)
+        Arow[k] = 0.0f;
+    }
+    __syncthreads();
+    if (t < n) {
+      float* o = Rout + blk * (int64_t)n * n;
+      for (int c = 0; c < n; ++c) o[t + (int64_t)n * c] = (c >= t) ? A[t * LD + c] : 0.0f;
+    }
+  }
+}
+
+size_t tsqr_rows_smem(int nc) {
+  return sizeof(float) * ((size_t)kRowsQR * (nc + 1) + (size_t)kRowsQR + (size_t)kRowsQR + nc);
+}
+
+// R of B^T (M x n FP32) by levels of tsqr_rows_kernel; buf0 / buf1 hold ceil(M / 256) and
+// ceil(M / 256 / fan) n x n triangles; returns the final triangle's buffer in *out.
+rh_status launch_tsqr_rows(const float* B, int64_t L, int64_t R, int n, float* buf0, float* buf1,
+                           const int32_t* gate, float** out, cudaStream_t st) {
+  if (n < 1 || n > 64) {
+    set_error("tall-skinny QR: n must be in [1, 64]");
+    return RH_EUNSUPPORTED;
+  }
+  const int nc = n <= 32 ? 32 : 64;
+  const size_t smem = tsqr_rows_smem(nc);
+  auto kern = nc == 32 ? tsqr_rows_kernel<32> : tsqr_rows_kernel<64>;
+  RH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t cap = 4 * (int64_t)num_sms();
+  const int fan = kRowsQR / n;
+  int64_t cnt = ceil_div(L * R, kRowsQR);
+  kern<<<(unsigned)std::min<int64_t>(cnt, cap), kRowsQR, smem, st>>>(B, L, R, n, nullptr, 0, fan, buf0, gate);
+  RH_LAUNCH_CHECK();
+  float* cur = buf0;
+  float* nxt = buf1;
+  while (cnt > 1) {
+    const int64_t nout = ceil_div(cnt, fan);
+    kern<<<(unsigned)std::min<int64_t>(nout, cap), kRowsQR, smem, st>>>(nullptr, 1, 1, n, cur, cnt, fan, nxt, gate);
+    RH_LAUNCH_CHECK();
+    cnt = nout;
+    float* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  *out = cur;
+  return RH_OK;
+}
+
 // One-sided Jacobi on the columns of R (n x n, n <= 64): R V = U S.  Writes Ub = V with columns
 // sorted by decreasing singular value and sv (both FP64).
 // Schedule: np = n rounded up to even "players" (a zero dummy when n is odd, which never
@@ -727,7 +889,11 @@ struct GramCfg {
   static constexpr int LDS = ELLP + 4;
 };
 
-template <int ELLP>
+// DF = true: every product is formed exactly (p = x y, e = fma(x, y, -p)) and summed in double-float
+// (TwoSum of the running sum and p, the rounding errors and e collected in a second FP32 term), so a
+// tile's partial carries ~2^-44 relative error instead of the FP32 sum's ~128 u; the Gram matrix is
+// then accurate enough for the Cholesky-Jacobi route at any condition number below ~1e6.
+template <int ELLP, bool DF>
 __global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const float* __restrict__ B, int64_t L,
                                                                         int64_t R, int ell, double* __restrict__ part,
                                                                         const int32_t* __restrict__ gate) {
@@ -794,11 +960,14 @@ __global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const fl
     }
     __syncthreads();
     if (active) {
-      float acc[4][4];
+      float acc[4][4], err[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b] = 0.0f;
+          err[a][b] = 0.0f;
+        }
 #pragma unroll 8
       for (int pp = 0; pp < 128; ++pp) {
         const float4 x = *reinterpret_cast<const float4*>(&Bs[pp * C::LDS + 4 * bi]);
@@ -808,12 +977,24 @@ __global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const fl
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+          for (int b = 0; b < 4; ++b) {
+            if constexpr (DF) {
+              const float pr = __fmul_rn(xa[a], yb[b]);
+              const float pe = fmaf(xa[a], yb[b], -pr);           // x y = pr + pe exactly
+              const float sm = __fadd_rn(acc[a][b], pr);
+              const float bb = __fsub_rn(sm, acc[a][b]);
+              const float se = __fadd_rn(__fsub_rn(acc[a][b], __fsub_rn(sm, bb)), __fsub_rn(pr, bb));
+              acc[a][b] = sm;                                      // acc + pr = sm + se exactly
+              err[a][b] = __fadd_rn(err[a][b], __fadd_rn(se, pe));
+            } else {
+              acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+            }
+          }
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) accd[a][b] += (double)acc[a][b];
+        for (int b = 0; b < 4; ++b) accd[a][b] += DF ? (double)acc[a][b] + (double)err[a][b] : (double)acc[a][b];
     }
   }
   if (!active) return;
@@ -866,7 +1047,8 @@ __global__ void __launch_bounds__(256) gram_b_reduce_kernel(const double* __rest
 // table of ArithDF / chol_kernel.  Two barriers per step.
 __global__ void __launch_bounds__(kCholThreads) pivoted_cholesky_kernel(const double* __restrict__ W, int n,
                                                                         float* __restrict__ X,
-                                                                        int32_t* __restrict__ flag) {
+                                                                        int32_t* __restrict__ flag,
+                                                                        int32_t* __restrict__ clear_on_success) {
   if (flag[0]) return;
   using Ar = ArithDF;
   using V = Ar::V;
@@ -973,6 +1155,7 @@ __global__ void __launch_bounds__(kCholThreads) pivoted_cholesky_kernel(const do
     __syncthreads();
   }
   if (bad && t == 0) flag[0] = 1;
+  if (!bad && t == 0 && clear_on_success != nullptr) *clear_on_success = 0;
 }
 
 // One-sided Jacobi on the columns of X (n x n, FP32, n <= 64) without accumulating the rotations:
@@ -987,8 +1170,11 @@ constexpr int kRowJacThreads = 256;
 __global__ void __launch_bounds__(kRowJacThreads) jacobi_rows_kernel(const float* __restrict__ Xin, int n,
                                                                        double* __restrict__ Ub,
                                                                        double* __restrict__ sv,
-                                                                       const int32_t* __restrict__ gate) {
+                                                                       const int32_t* __restrict__ gate,
+                                                                       int32_t* __restrict__ info_or = nullptr,
+                                                                       int32_t info_bits = 0) {
   if (gate != nullptr && *gate != 0) return;
+  if (info_or != nullptr && threadIdx.x == 0) *info_or |= info_bits;
   extern __shared__ __align__(16) float jsm[];
   const int np = (n + 1) & ~1;
   const int half = np / 2;
@@ -1149,11 +1335,15 @@ __global__ void cast_f2d_gated_kernel(const float* __restrict__ src, double* __r
 // After the Gram route: fall back to the tall-skinny QR when the Cholesky factor broke down or
 // when the truncation gap sigma_r^2 - sigma_{r+1}^2 is below 1e-5 sigma_1^2, where the FP32
 // Gram cannot resolve the top-r subspace.
+// Decides the first (FP32 Gram) route; arm[0] = 0 arms the second (double-float Gram) route exactly
+// when the first is rejected, arm[0] = 1 keeps it off.
 __global__ void trunc_decide_kernel(const int32_t* __restrict__ chol_flag, const double* __restrict__ sv, int ell, int r,
-                                    int32_t* __restrict__ use_tsqr, int32_t* __restrict__ info) {
+                                    int32_t* __restrict__ use_tsqr, int32_t* __restrict__ info,
+                                    int32_t* __restrict__ arm) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (*chol_flag) {
     *use_tsqr = 1;
+    if (arm != nullptr) arm[0] = 0;
     return;
   }
   const double s1 = sv[0];
@@ -1161,6 +1351,7 @@ __global__ void trunc_decide_kernel(const int32_t* __restrict__ chol_flag, const
   const double sr1 = (r < ell) ? sv[r] : 0.0;
   const bool ok = (r >= ell) || (s1 == 0.0) || (sr * sr - sr1 * sr1 >= 1e-5 * s1 * s1);
   *use_tsqr = ok ? 0 : 1;
+  if (arm != nullptr) arm[0] = ok ? 1 : 0;
   if (ok && info != nullptr) *info |= 2;
 }
 
@@ -1190,7 +1381,7 @@ size_t orth_workspace_elems(int64_t m, int n) {
 }
 
 rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
-                          const int32_t* gate, cudaStream_t st);
+                          const int32_t* gate, cudaStream_t st, bool df = false);
 
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
                                 cudaStream_t st, bool f32) {
@@ -1282,6 +1473,13 @@ constexpr int kTsqrThreads = 1024;
 template <typename T>
 static void trunc_dims(TruncPlan& pl) {
   const int n = pl.ell;
+  if (sizeof(T) == 4) {
+    // FP32: tsqr_rows_kernel, 256 rows per block, 256 / n triangles per merge
+    pl.rows0 = kRowsQR;
+    pl.fan = std::max(2, kRowsQR / n);
+    pl.nblk0 = ceil_div(pl.v.M(), kRowsQR);
+    return;
+  }
   const int budget = smem_budget() - (int)sizeof(T) * (kTsqrThreads + 64);
   int rows0 = budget / (int)(sizeof(T) * n) - 1;
   rows0 = std::min(rows0, 512);
@@ -1293,18 +1491,31 @@ static void trunc_dims(TruncPlan& pl) {
 
 static int odd_ld(int rows) { return rows | 1; }
 
-int gram_ctas() { return 4 * num_sms(); }
+int gram_ctas() { return 8 * num_sms(); }
 
 // W = B B^T (ell x ell, FP64, full) of the FP32 (L, ell, R) tensor B: FP32 sums over 128 columns,
 // FP64 across; part holds min(gram_ctas(), ceil(L R / 128)) ell^2 doubles.  Gated on *gate == 0.
 rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
-                          const int32_t* gate, cudaStream_t st) {
+                          const int32_t* gate, cudaStream_t st, bool df) {
   const int64_t ntiles = ceil_div(L * R, 128);
   const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(gram_ctas(), ntiles));
-  if (ell <= 32)
-    gram_b_kernel<32><<<ctas, GramCfg<32>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
-  else
-    gram_b_kernel<64><<<ctas, GramCfg<64>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+  if (!df) {
+    if (ell <= 32)
+      gram_b_kernel<32, false><<<ctas, GramCfg<32>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+    else
+      gram_b_kernel<64, false><<<ctas, GramCfg<64>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+  } else {
+    // the double-float sums are ALU-bound: blocks of 4 x 4 entries over the columns actually used
+    switch ((ell + 7) / 8) {
+#define RH_GDF(E) \
+  case E / 8: gram_b_kernel<E, true><<<ctas, GramCfg<E>::THREADS, 0, st>>>(B, L, R, ell, part, gate); break
+      RH_GDF(8); RH_GDF(16); RH_GDF(24); RH_GDF(32); RH_GDF(40); RH_GDF(48); RH_GDF(56); RH_GDF(64);
+#undef RH_GDF
+      default:
+        set_error("Gram matrix: ell must be in [1, 64]");
+        return RH_EUNSUPPORTED;
+    }
+  }
   RH_LAUNCH_CHECK();
   gram_b_reduce_kernel<<<(int)ceil_div((int64_t)ell * ell, 32), 256, 0, st>>>(part, ctas, ell, W, gate);
   RH_LAUNCH_CHECK();
@@ -1351,45 +1562,67 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     int32_t* flags = reinterpret_cast<int32_t*>(rdiag + n);
     float* Rf = reinterpret_cast<float*>(flags + 16);
     use_tsqr = flags + 1;
-    RH_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), st));
+    int32_t* flags2 = flags + 4;   // second route: [0] = skip / Cholesky failure
+    RH_CUDA_TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int32_t), st));
     (void)ctas;
     rh_status s;
     if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st)) != RH_OK)
       return s;
-    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(W, n, Rf, flags);
+    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(W, n, Rf, flags, nullptr);
     RH_LAUNCH_CHECK();
+    const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
+    RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     {
       ProfileScope ps(PROF_JACOBI, 0, st);
-      const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
-      RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
       jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Rf, n, Ub, sv, flags);
       RH_LAUNCH_CHECK();
     }
-    trunc_decide_kernel<<<1, 32, 0, st>>>(flags, sv, n, r, use_tsqr, info);
+    trunc_decide_kernel<<<1, 32, 0, st>>>(flags, sv, n, r, use_tsqr, info, flags2);
     RH_LAUNCH_CHECK();
+    // Second route when the first is rejected: the same factorization of a double-float Gram
+    // matrix (no gap test: its error is ~2^-44 ||W||).  Its Cholesky clears use_tsqr when it
+    // succeeds, so the tall-skinny QR below only runs when it breaks down too.
+    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, flags2, st, true)) !=
+        RH_OK)
+      return s;
+    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(W, n, Rf, flags2, use_tsqr);
+    RH_LAUNCH_CHECK();
+    {
+      ProfileScope ps(PROF_JACOBI, 2, st);
+      jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Rf, n, Ub, sv, flags2, info, 8);
+      RH_LAUNCH_CHECK();
+    }
   }
-  const int ld0 = odd_ld(pl.rows0);
-  const int ldm = odd_ld(pl.fan * n);
-  const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
-  const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
-  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-  const int64_t tsqr_grid_cap = 8 * (int64_t)num_sms();
-  tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, tsqr_grid_cap), kTsqrThreads, sm0, st>>>(
-      B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, use_tsqr);
-  RH_LAUNCH_CHECK();
-  int64_t cnt = pl.nblk0;
   T* cur = buf0;
-  T* nxt = buf1;
-  while (cnt > 1) {
-    const int64_t nout = ceil_div(cnt, pl.fan);
-    tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, tsqr_grid_cap), kTsqrThreads, smm, st>>>(
-        cur, cnt, n, pl.fan, ldm, nxt, use_tsqr);
+  if constexpr (sizeof(T) == 4) {
+    float* fin = nullptr;
+    rh_status s = launch_tsqr_rows(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, reinterpret_cast<float*>(buf0),
+                                   reinterpret_cast<float*>(buf1), use_tsqr, &fin, st);
+    if (s != RH_OK) return s;
+    cur = reinterpret_cast<T*>(fin);
+  } else {
+    const int ld0 = odd_ld(pl.rows0);
+    const int ldm = odd_ld(pl.fan * n);
+    const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
+    const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
+    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    const int64_t tsqr_grid_cap = 8 * (int64_t)num_sms();
+    tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, tsqr_grid_cap), kTsqrThreads, sm0, st>>>(
+        B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, use_tsqr);
     RH_LAUNCH_CHECK();
-    cnt = nout;
-    T* t = cur;
-    cur = nxt;
-    nxt = t;
+    int64_t cnt = pl.nblk0;
+    T* nxt = buf1;
+    while (cnt > 1) {
+      const int64_t nout = ceil_div(cnt, pl.fan);
+      tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, tsqr_grid_cap), kTsqrThreads, smm, st>>>(
+          cur, cnt, n, pl.fan, ldm, nxt, use_tsqr);
+      RH_LAUNCH_CHECK();
+      cnt = nout;
+      T* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
   }
   {
     ProfileScope ps(PROF_JACOBI, 1, st);
@@ -1402,13 +1635,13 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
 // ---- staged truncation (adaptive variants) ----------------------------------------------
 template <typename T>
 rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram, double* part, double* W, T** R,
-                              double* rownorm2, cudaStream_t st) {
+                              double* rownorm2, cudaStream_t st, bool df) {
   TruncPlan pl = pl0;
   trunc_dims<T>(pl);
   const int n = pl.ell;
   const int64_t nn = (int64_t)n * n;
   if (gram) {
-    rh_status s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st);
+    rh_status s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st, df);
     if (s != RH_OK) return s;
     diag_kernel<<<1, 64, 0, st>>>(W, n, rownorm2);
     RH_LAUNCH_CHECK();
@@ -1416,28 +1649,36 @@ rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram
   }
   T* buf0 = ws;
   T* buf1 = ws + pl.nblk0 * nn;
-  const int ld0 = odd_ld(pl.rows0);
-  const int ldm = odd_ld(pl.fan * n);
-  const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
-  const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
-  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-  RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-  const int64_t cap = 8 * (int64_t)num_sms();
-  tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, cap), kTsqrThreads, sm0, st>>>(
-      B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, nullptr);
-  RH_LAUNCH_CHECK();
-  int64_t cnt = pl.nblk0;
   T* cur = buf0;
-  T* nxt = buf1;
-  while (cnt > 1) {
-    const int64_t nout = ceil_div(cnt, pl.fan);
-    tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, cap), kTsqrThreads, smm, st>>>(cur, cnt, n, pl.fan,
-                                                                                           ldm, nxt, nullptr);
+  if constexpr (sizeof(T) == 4) {
+    float* fin = nullptr;
+    rh_status s = launch_tsqr_rows(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, reinterpret_cast<float*>(buf0),
+                                   reinterpret_cast<float*>(buf1), nullptr, &fin, st);
+    if (s != RH_OK) return s;
+    cur = reinterpret_cast<T*>(fin);
+  } else {
+    const int ld0 = odd_ld(pl.rows0);
+    const int ldm = odd_ld(pl.fan * n);
+    const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
+    const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
+    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    const int64_t cap = 8 * (int64_t)num_sms();
+    tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, cap), kTsqrThreads, sm0, st>>>(
+        B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, nullptr);
     RH_LAUNCH_CHECK();
-    cnt = nout;
-    T* t = cur;
-    cur = nxt;
-    nxt = t;
+    int64_t cnt = pl.nblk0;
+    T* nxt = buf1;
+    while (cnt > 1) {
+      const int64_t nout = ceil_div(cnt, pl.fan);
+      tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, cap), kTsqrThreads, smm, st>>>(cur, cnt, n, pl.fan,
+                                                                                             ldm, nxt, nullptr);
+      RH_LAUNCH_CHECK();
+      cnt = nout;
+      T* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
   }
   *R = cur;
   colnorm2_kernel<T><<<n, 32, 0, st>>>(cur, n, rownorm2);
@@ -1453,7 +1694,7 @@ rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, con
     RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
     copy_leading_kernel<double, double><<<blocks, 256, 0, st>>>(W, n, k, Wk);
     RH_LAUNCH_CHECK();
-    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(k, sizeof(dfl::F2)), st>>>(Wk, k, Xf, flag);
+    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(k, sizeof(dfl::F2)), st>>>(Wk, k, Xf, flag, nullptr);
     RH_LAUNCH_CHECK();
     const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
     RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
@@ -1504,9 +1745,9 @@ template rh_status launch_trunc_svd<float>(const TruncPlan&, const float*, float
 template rh_status launch_trunc_svd<double>(const TruncPlan&, const double*, double*, double*, double*, cudaStream_t,
                                             int, int32_t*);
 template rh_status launch_trunc_factor<float>(const TruncPlan&, const float*, float*, bool, double*, double*, float**,
-                                             double*, cudaStream_t);
+                                             double*, cudaStream_t, bool);
 template rh_status launch_trunc_factor<double>(const TruncPlan&, const double*, double*, bool, double*, double*,
-                                              double**, double*, cudaStream_t);
+                                              double**, double*, cudaStream_t, bool);
 template rh_status launch_trunc_leading_svd<float>(int, int, bool, const double*, const float*, double*, float*, float*,
                                                   double*, double*, int32_t*, cudaStream_t);
 template rh_status launch_trunc_leading_svd<double>(int, int, bool, const double*, const double*, double*, float*,

@@ -163,3 +163,12 @@ def test_batched_argument_checks(L):
     assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], streams=64, p=5) > 0    # capped at count = 1
     # a custom processing order is not accepted for a batch
     assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], p=5, rho=[2, 1, 0]) == 0
+
+
+def test_svd_route_option(L):
+    from paper_1905_07311_gb300 import _lib
+
+    assert _lib.make_options().svd_route == 0
+    assert _ws(L, [30, 20, 10], [4, 4, 4], p=5, svd_route=1) > 0
+    code, msg = _call_invalid(L, [30, 20, 10], [4, 4, 4], p=5, svd_route=2)
+    assert code == 1 and "svd_route" in msg

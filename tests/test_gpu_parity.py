@@ -213,12 +213,41 @@ def test_rsthosvd_f32_gram_route_taken(rh):
     assert [v & 2 for v in T.info.cpu().numpy().tolist()] == [2, 2, 2]
 
 
-def test_rsthosvd_f32_deep_truncation_falls_back_to_qr(rh):
+def test_rsthosvd_f32_deep_truncation_takes_the_double_float_gram(rh):
     """Decay 0.4 and r = 10: sigma_r^2 - sigma_{r+1}^2 is below 1e-5 sigma_1^2, where FP32 Gram
-    sums cannot resolve the retained subspace; the tall-skinny QR route must run instead."""
+    sums cannot resolve the retained subspace; the double-float Gram matrix (~2^-44) can, so its
+    route runs (info bit 8) and matches the oracle."""
     X = lowrank_plus_noise_np([90, 80, 70], [14, 14, 14], 0.4, 1e-7, seed=12)
     T, e_g, e_o, _ = _compare(rh, X, [10, 10, 10], 4, 3, np.float32)
-    assert [v & 2 for v in T.info.cpu().numpy().tolist()] == [0, 0, 0]
+    assert [v & 10 for v in T.info.cpu().numpy().tolist()] == [8, 8, 8]
+
+
+def test_rsthosvd_f32_double_float_gram_wide(rh):
+    """ell = 40 (Gram blocks sized to 40 columns), decay 0.8: sigma_34^2 - sigma_35^2 ~ 1e-7
+    sigma_1^2 rejects the FP32 Gram matrix, sigma_40^2 ~ 3e-8 sigma_1^2 is well inside what the
+    double-float one resolves.  (With a steeper spectrum, e.g. decay 0.55, sigma_40^2 ~ 5e-21
+    sigma_1^2 is singular even in double-float and the tall-skinny QR takes over.)"""
+    X = lowrank_plus_noise_np([300, 200, 130], [44, 44, 44], 0.8, 1e-4, seed=14)
+    T, e_g, e_o, _ = _compare(rh, X, [34, 34, 34], 6, 7, np.float32)
+    assert [v & 10 for v in T.info.cpu().numpy().tolist()] == [8, 8, 8]
+
+
+def test_rsthosvd_f32_numerically_singular_gram_falls_back_to_qr(rh):
+    """Decay 0.55, ell = 40: sigma_40^2 ~ 5e-21 sigma_1^2, the double-float Cholesky breaks down
+    and the tall-skinny QR of B^T runs (neither Gram bit)."""
+    X = lowrank_plus_noise_np([300, 200, 130], [44, 44, 44], 0.55, 1e-7, seed=14)
+    T, e_g, e_o, _ = _compare(rh, X, [34, 34, 34], 6, 7, np.float32)
+    assert [v & 10 for v in T.info.cpu().numpy().tolist()] == [0, 0, 0]
+
+
+@pytest.mark.parametrize("shape,core,ranks,p,decay", [([90, 80, 70], 14, 10, 4, 0.4),
+                                                      ([300, 200, 130], 44, 34, 6, 0.55)])
+def test_rsthosvd_f32_tall_skinny_qr_route(rh, shape, core, ranks, p, decay):
+    """svd_route = 1: the Householder QR of B^T (256-row blocks and merge levels; 32- and
+    64-column instantiations, unit-stride and strided views of B) for every mode."""
+    X = lowrank_plus_noise_np(shape, [core] * 3, decay, 1e-7, seed=15)
+    T, e_g, e_o, _ = _compare(rh, X, [ranks] * 3, p, 7, np.float32, svd_route=1)
+    assert [v & 10 for v in T.info.cpu().numpy().tolist()] == [0, 0, 0]
 
 
 def test_rsthosvd_f32_rank_deficient_sketch(rh):
