@@ -17,6 +17,7 @@ significant bits of X, Omega rounded to BF16, FP32 accumulation; later modes FP3
 the FP32 form on the CUDA cores throughout.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--form F]
+       python bench.py --workload hilbert200|lowp192|batched|sparse [--steps K] [--warmup W]
 """
 
 import argparse
@@ -441,6 +442,271 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------------
+# Further workloads (--workload): the configurations the tests check for parity, measured with the
+# same rules (inputs resident, CUDA events on the launching stream, clocks sampled, warm-up).
+# ---------------------------------------------------------------------------------
+NAMES = {0: "sketch", 1: "mode_product", 2: "qr", 3: "trunc_svd", 4: "core_product", 5: "jacobi"}
+
+
+def _timed(torch, L, fn, steps, warmup, device, profile=True):
+    """Median-free device timing of ``steps`` calls of fn after ``warmup``; returns
+    (ms per call, {stage: ms per call}, launches per call, clocks)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    clocks = Clocks(device.index or 0)
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if profile:
+        L.rh_profile_enable(1)
+    n0 = L.rh_kernel_launches()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = (L.rh_kernel_launches() - n0) / steps
+    per = {}
+    if profile:
+        L.rh_profile_enable(0)
+        cap = 200000
+        kinds, tags, ms = (ctypes.c_int32 * cap)(), (ctypes.c_int32 * cap)(), (ctypes.c_float * cap)()
+        nrec = min(L.rh_profile_collect(kinds, tags, ms, cap), cap)
+        for i in range(nrec):
+            per.setdefault(f"{NAMES.get(kinds[i], kinds[i])}[{tags[i]}]", []).append(ms[i])
+    breakdown = {k: round(sum(v) / steps, 4) for k, v in sorted(per.items())}
+    return e0.elapsed_time(e1) / steps, breakdown, launches, clk
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def _hbm_roof(kernel, nbytes, ms, peaks, src):
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": None,
+            "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", "algorithmic_bytes": nbytes,
+            "avg_launch_ms": round(ms, 4)}
+
+
+def wl_hilbert200(torch, rh, L, args, device, peaks, src):
+    """200^3 FP64 tensor 1/(i+j+k+1), rank (20, 20, 20), p = 5, seed 0, order 1, 2, 3."""
+    from workloads import hilbert
+
+    dims, ranks = [200, 200, 200], [20, 20, 20]
+    Xn = hilbert(dims, offset=1)
+    X = torch.from_numpy(np.ascontiguousarray(Xn.ravel(order="F"))).to(device)
+    call = rh.RsthosvdCall(dims, torch.float64, ranks, p=5, seed=0, rho=[0, 1, 2], device=device)
+    ms, br, launches, clk = _timed(torch, L, lambda: call.run(X), args.steps, args.warmup, device)
+    T = call.run(X)
+    G = torch.from_numpy(np.reshape(T.core.cpu().numpy(), T.core_dims, order="F"))
+    A = [f.cpu().double().T for f in T.factors]
+    Xh = G
+    for n in range(3):
+        Xh = torch.movedim(torch.tensordot(A[n], Xh, dims=([1], [n])), 0, n)
+    Xt = torch.from_numpy(Xn)
+    err = float(torch.linalg.vector_norm(Xt - Xh) / torch.linalg.vector_norm(Xt))
+    # the first-mode sketch on the CUDA cores is FP64-FMA bound: 2 N ell flops at the nominal
+    # FP64 rate of the part (no measured FP64 peak is available)
+    sk = br.get("sketch[0]", ms)
+    fl = 2.0 * 200 ** 3 * 25
+    roof = {"kernel": "sketch_kernel<double>", "bound": "alu", "achieved": round(fl / (sk * 1e-3) / 1e12, 4),
+            "peak": 1.25, "unit": "TFLOP/s", "frac": round(fl / (sk * 1e-3) / 1e12 / 1.25, 4), "traffic": None,
+            "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)", "algorithmic_flops": fl,
+            "avg_launch_ms": sk}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import tucker
+
+        t0 = time.perf_counter()
+        out = tucker.rsthosvd(Xn, ranks, 5, 0, rho=[0, 1, 2])
+        dt = time.perf_counter() - t0
+        Gd, Ad = tucker.sthosvd(Xn, ranks, rho=[0, 1, 2])
+        from oracle.tensor import rel_error
+
+        cpu = {"value": round(dt * 1e3, 3), "unit": "ms", "cores": _cores(), "kind": "oracle",
+               "sample": "oracle R-STHOSVD (numpy FP64) on the whole 200^3 tensor",
+               "oracle_rel_error": rel_error(Xn, out["core"], out["factors"]),
+               "sthosvd_rel_error": rel_error(Xn, Gd, Ad)}
+    return {"metric": "R-STHOSVD time-to-Tucker, 200^3 Hilbert-type FP64, rank 20", "value": round(ms, 4),
+            "unit": "ms", "higher_is_better": False, "dtype": "f64", "rel_error": err,
+            "config": {"workload": "dense 3-way FP64 200x200x200, X(i,j,k) = 1/(i+j+k+1), rank (20,20,20), p=5, "
+                                   "seed 0, order 1,2,3", "l2": "input 64 MB (fits L2); no flush"},
+            "roofline": roof, "breakdown_ms": br, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+
+
+def wl_lowp192(torch, rh, L, args, device, peaks, src):
+    """192^4 with a 30^4 core (decay 0.8), noise 1e-3, stored in BF16 and E4M3 (block scales);
+    R-STHOSVD rank 30, p = 10; adaptive Alg. 5 at 1e-2 (block 8, p = 10) on the BF16 storage."""
+    from workloads import fp8_quantize_torch, lowrank_plus_noise_torch
+
+    dims, ranks = [192] * 4, [30] * 4
+    X = lowrank_plus_noise_torch(dims, ranks, 0.8, 1e-3, 3, torch.float32, device)
+    N = X.numel()
+    stored = {"fp8_e4m3": fp8_quantize_torch(X, dims), "bf16": X.to(torch.bfloat16).view(torch.int16),
+              "f32_bf16x2": X}
+    nbytes = {"fp8_e4m3": stored["fp8_e4m3"].numel(), "bf16": 2 * N, "f32_bf16x2": 4 * N}
+    forms = {}
+    for form, Xs in stored.items():
+        call = rh.RsthosvdCall(dims, form, ranks, p=10, seed=0, device=device)
+        ms, br, launches, clk = _timed(torch, L, lambda: call.run(Xs), args.steps, args.warmup, device)
+        sk = br.get("sketch[0]", ms)
+        forms[form] = {"ms": round(ms, 4), "sketch0_GBs": round(nbytes[form] / (sk * 1e-3) / 1e9, 1),
+                       "breakdown_ms": br, "gpu_launches": launches, "clocks": clk,
+                       "info": call.info.cpu().numpy().tolist()}
+    # adaptive on the BF16 storage
+    Xb = stored["bf16"]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    rh.adaptive(Xb, dims, 1e-2, variant="sthosvd", block=8, p=10, seed=0, form="bf16")
+    torch.cuda.synchronize()
+    t0.record()
+    Ta = rh.adaptive(Xb, dims, 1e-2, variant="sthosvd", block=8, p=10, seed=0, form="bf16")
+    t1.record()
+    torch.cuda.synchronize()
+    adapt = {"ms": round(t0.elapsed_time(t1), 3), "ranks": Ta.ranks, "eps": 1e-2,
+             "note": "synchronous call (one host read of the sizes per mode)"}
+    f8 = forms["fp8_e4m3"]
+    roof = _hbm_roof("sketch_tc_kernel<E4M3 in>", nbytes["fp8_e4m3"], f8["breakdown_ms"].get("sketch[0]"), peaks,
+                     src)
+    cpu = None
+    if not args.no_cpu:
+        from oracle import tucker
+
+        sub = X.view(192, 192, 192, 192)[:8].contiguous().view(-1)   # X[:, :, :, :8] in column-major terms
+        Xs = np.reshape(sub.double().cpu().numpy(), [192, 192, 192, 8], order="F")
+        t = time.perf_counter()
+        tucker.rsthosvd(Xs, [30, 30, 30, 8], 10, 0, clamp=True)
+        dt = time.perf_counter() - t
+        cpu = {"value": round(dt * 1e3, 1), "unit": "ms", "cores": _cores(), "kind": "oracle",
+               "sample": "oracle R-STHOSVD (numpy FP64) on the 192x192x192x8 slab X[:, :, :, :8] (1/24 of the "
+                         "tensor), ranks (30, 30, 30, 8), p = 10, ell clamped to the slab"}
+    return {"metric": "R-STHOSVD time-to-Tucker, 192^4 stored in BF16 (E4M3 and FP32 forms alongside)",
+            "value": forms["bf16"]["ms"], "unit": "ms", "higher_is_better": False, "dtype": "bf16",
+            "config": {"workload": "dense 4-way 192^4, core 30^4 decay 0.8, noise 1e-3, seed 3; rank (30,30,30,30), "
+                                   "p=10; storage BF16 / E4M3 with per-128-byte FP32 scales / FP32 split on the fly",
+                       "l2": "inputs 1.4-5.4 GB (larger than L2); no flush"},
+            "forms": forms, "adaptive_bf16": adapt, "roofline": roof, "cpu_baseline": cpu}
+
+
+def wl_batched(torch, rh, L, args, device, peaks, src):
+    """The batched workload's order-3 and order-4 tensors (339 of 512, 8.0 GB FP32), one
+    rsthosvd_batched call captured in a CUDA graph and replayed."""
+    from workloads import batch_recipe, lowrank_plus_noise_torch
+
+    rec = [b for b in batch_recipe() if len(b[0]) in (3, 4)]
+    Xs = [lowrank_plus_noise_torch(d, r, 0.9, 1e-3, sd, torch.float32, device) for d, r, sd in rec]
+    nbytes = sum(4 * x.numel() for x in Xs)
+    call = rh.RsthosvdBatchedCall([b[0] for b in rec], [b[1] for b in rec], torch.float32, p=5, seed=4, clamp=True,
+                                  streams=args.streams, device=device)
+    call.run(Xs)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream(device=device)
+    s.wait_stream(torch.cuda.current_stream(device))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        call.run(Xs)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            call.run(Xs)
+    ms, _, _, clk = _timed(torch, L, g.replay, args.steps, args.warmup, device, profile=False)
+    n0 = L.rh_kernel_launches()
+    call.run(Xs)
+    torch.cuda.synchronize()
+    launches = L.rh_kernel_launches() - n0
+    tps = len(Xs) / (ms * 1e-3)
+    # roofline of the whole call: each tensor is read twice (sketch and mode product of mode 1)
+    roof = _hbm_roof("rsthosvd_batched (whole call)", 2 * nbytes, ms, peaks, src)
+    cpu = None
+    if not args.no_cpu:
+        from oracle import tucker
+
+        t = time.perf_counter()
+        for (d, r, _), X in list(zip(rec, Xs))[:6]:
+            Xn = np.reshape(X.double().cpu().numpy(), d, order="F")
+            tucker.rsthosvd(Xn, r, 5, 4, clamp=True)
+        dt = time.perf_counter() - t
+        cpu = {"value": round(6 / dt, 3), "unit": "tensors/s", "cores": _cores(), "kind": "oracle",
+               "sample": "oracle R-STHOSVD (numpy FP64) of the first 6 tensors of the same set"}
+    return {"metric": "batched R-STHOSVD throughput (order-3 and order-4 tensors of the batch)",
+            "value": round(tps, 1), "unit": "tensors/s", "higher_is_better": True, "dtype": "f32",
+            "ms_per_step": round(ms, 3),
+            "config": {"workload": f"{len(Xs)} tensors, order 3-4, sizes U[16,96], ranks U[4,16] capped, low rank + "
+                                   f"1e-3 noise, seed 4, p=5 clamped; {nbytes / 1e9:.2f} GB FP32",
+                       "streams": args.streams, "graph": True, "l2": "inputs 8 GB (larger than L2); no flush"},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+
+
+def wl_sparse(torch, rh, L, args, device, peaks, src):
+    """COO 20000 x 20000 x 5000 with 5e7 nonzeros (Zipf 1.1, log-count values), SP-STHOSVD rank 30,
+    p = 10.  The sketch is not HBM- or tensor-bound: its roof is max(COO bytes / HBM, Omega
+    normals / the measured rate of the library's Omega generator)."""
+    from workloads import zipf_coo_torch
+
+    dims, nnz = [20000, 20000, 5000], 50_000_000
+    idx, vals = zipf_coo_torch(dims, nnz, 1.1, 3.0, 5, device)
+    torch.cuda.synchronize()
+    ms, br, launches, clk = _timed(torch, L, lambda: rh.sp_sthosvd_coo(idx, vals, dims, [30] * 3, p=10, seed=0),
+                                   args.steps, args.warmup, device, profile=False)
+    ms_sk, _, _, _ = _timed(torch, L, lambda: rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0),
+                            args.steps, args.warmup, device, profile=False)
+    # Omega generator rate (normals per second) on a long stream
+    rows = 1 << 24
+    out = torch.empty((40, rows), dtype=torch.float32, device=device)
+    o_ms, _, _, _ = _timed(torch, L, lambda: L.rh_omega(0, 0, 0, 0, rows, 40, ctypes.c_void_p(out.data_ptr()),
+                                                        ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)),
+                           args.steps, args.warmup, device, profile=False)
+    rate = 40.0 * rows / (o_ms * 1e-3)
+    sk_bytes = nnz * 16.0
+    t_roof = max(sk_bytes / (peaks["hbm_gbs"] * 1e9), nnz * 40.0 / rate) * 1e3
+    roof = {"kernel": "rhosvd_sketch_coo (mode 1, ell 40)", "bound": "alu", "achieved": round(t_roof / ms_sk, 4),
+            "peak": 1.0, "unit": "fraction of max(COO bytes / HBM, normals / Omega rate)",
+            "frac": round(t_roof / ms_sk, 4), "traffic": None,
+            "peak_source": f"Omega generator measured at {rate / 1e9:.1f} G normals/s (rh_omega, 2^24 x 40), "
+                           f"HBM {peaks['hbm_gbs']} GB/s ({src})",
+            "roof_ms": round(t_roof, 4), "avg_launch_ms": round(ms_sk, 4)}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import tucker
+
+        m = 1_000_000
+        sub = np.stack([t[:m].cpu().numpy().astype(np.int64) for t in idx], axis=1)
+        v = vals[:m].double().cpu().numpy()
+        t = time.perf_counter()
+        tucker.coo_sketch(sub, v, dims, 0, 40, 0)
+        dt = time.perf_counter() - t
+        cpu = {"value": round(m / dt / 1e6, 3), "unit": "M nonzeros/s (sketch, ell 40)", "cores": _cores(),
+               "kind": "oracle", "sample": "oracle COO sketch of the first 1e6 nonzeros, mode 1, ell 40"}
+    return {"metric": "SP-STHOSVD time-to-Tucker, COO 20000x20000x5000, 5e7 nonzeros", "value": round(ms, 3),
+            "unit": "ms", "higher_is_better": False, "dtype": "f32", "sketch_mode1_ms": round(ms_sk, 4),
+            "config": {"workload": "COO 20000x20000x5000, 5e7 distinct Zipf(1.1) coordinates, values "
+                                   "log(1+Poisson(3)+1), seed 5; rank (30,30,30), p=10", "l2": "800 MB of COO; no flush"},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+
+
+def run_workload(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    from paper_1905_07311_gb300 import build
+
+    build.build()
+    import paper_1905_07311_gb300 as rh
+    from paper_1905_07311_gb300 import _lib
+
+    L = _lib.lib()
+    peaks, src = measured_peaks()
+    fn = {"hilbert200": wl_hilbert200, "lowp192": wl_lowp192, "batched": wl_batched, "sparse": wl_sparse}[args.workload]
+    line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    line.update(fn(torch, rh, L, args, device, peaks, src))
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -457,7 +723,15 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--dims", type=int, nargs=3, default=None,
                     help="smaller cube for profiling captures (default 1024 1024 1024)")
+    ap.add_argument("--workload", default="dense1024",
+                    choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse"],
+                    help="dense1024: the benchmark line (default); the others measure the further configurations "
+                         "and print one JSON line each")
+    ap.add_argument("--streams", type=int, default=8, help="internal streams of the batched workload")
     args = ap.parse_args()
+    if args.workload != "dense1024":
+        run_workload(args)
+        return
     if args.dims:
         global DIMS, WORKLOAD
         DIMS = list(args.dims)

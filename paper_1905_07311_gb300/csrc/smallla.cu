@@ -726,6 +726,10 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ 
   const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
   const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
   int cur = 0;
+  // columns whose norm is below n u ||R||_F are rounding noise: they cannot be made orthogonal to
+  // the relative tolerance, so pairs involving one are not rotated (otherwise a spectrum that
+  // reaches the rounding level, like the Hilbert tensor's, never meets the stopping test)
+  __shared__ T floor2_s;
   for (int sweep = 0; sweep < 40; ++sweep) {
     {
       const Q4* src = cur ? buf1 : buf0;
@@ -735,7 +739,15 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ 
         if (lane == 0) nrm2[cur][q] = a;
       }
       __syncthreads();
+      if (sweep == 0 && threadIdx.x == 0) {
+        T fro2 = T(0);
+        for (int q = 0; q < n; ++q) fro2 += nrm2[cur][q];
+        const T nu = T(n) * ((sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16));
+        floor2_s = nu * nu * fro2;
+      }
+      __syncthreads();
     }
+    const T floor2 = floor2_s;
     int rotated = 0;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       const Q4* src = cur ? buf1 : buf0;
@@ -745,7 +757,7 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ 
         Q4 Bq = src[qb * 32 + lane];
         T al = nrm2[cur][qa], be = nrm2[cur][qb];
         const T g = warp_sum(A.x0 * Bq.x0 + A.x1 * Bq.x1);
-        if (g != T(0) && fabs(g) * jacobi_rsqrt(al) * jacobi_rsqrt(be) > tol) {
+        if (g != T(0) && (al < be ? al : be) > floor2 && fabs(g) * jacobi_rsqrt(al) * jacobi_rsqrt(be) > tol) {
           const T zeta = (be - al) / (T(2) * g);
           const T az = fabs(zeta);
           const T tm = az < T(1e18) ? T(1) / (az + sqrt(fma(az, az, T(1)))) : T(0.5) / az;

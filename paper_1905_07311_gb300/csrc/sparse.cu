@@ -12,9 +12,9 @@
 //
 // The sketch is deterministic: the nonzeros are stably sorted by i_n (CUB radix sort), each row's
 // run is cut into work items of at most kItem nonzeros, a warp turns an item into a partial row
-// (FP32 sums of products, two nonzeros per pass: lanes 0-15 and 16-31, lane q generating Omega
-// columns 4q..4q+3 with the library's Philox / Box-Muller), and the partials of a row are added in
-// FP64 in item order.  The item list is built on the host from the row counts, and the selection
+// (FP32 sums of products; ceil(ell / 4) lanes per nonzero, lane q generating Omega columns
+// 4q..4q+3 with the library's Philox / Box-Muller, 32 / ceil(ell / 4) nonzeros per pass, the
+// groups combined in a fixed order), and the partials of a row are added in FP64 in item order.  The item list is built on the host from the row counts, and the selection
 // (strong RRQR: column-pivoted QR of Q^T, then swaps while some |A_ij| > eta, the largest entry first,
 // lowest (i, j) on ties) runs on the host in FP64, so the call synchronises its stream per mode.
 #include <cub/cub.cuh>
@@ -58,17 +58,21 @@ __global__ void __launch_bounds__(256) sp_sketch_items_kernel(SpIdx ix, int d, c
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int q = lane & 15, half = lane >> 4;
+  // nq lanes per nonzero (lane q generates Omega columns 4q..4q+3), npass = 32 / nq nonzeros
+  // per pass of the warp: ell = 40 keeps 30 of 32 lanes busy
   const int nq = (ell + 3) >> 2;
+  const int npass = 32 / nq;
+  const int g = lane / nq, q = lane - g * nq;
+  const bool active = g < npass;
   for (int it = warp; it < nitems; it += nwarps) {
     const int3 item = items[it];   // x: row (unused here), y: begin, z: end
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int j = item.y + half; j < item.z; j += 2) {
-      const int e = perm[j];
-      int64_t p = 0;
-      for (int k = 0; k < d; ++k) p += (int64_t)ix.idx[k][e] * ix.stride[k];
-      const float v = vals[e];
-      if (q < nq) {
+    if (active) {
+      for (int j = item.y + g; j < item.z; j += npass) {
+        const int e = perm[j];
+        int64_t p = 0;
+        for (int k = 0; k < d; ++k) p += (int64_t)ix.idx[k][e] * ix.stride[k];
+        const float v = vals[e];
         const float4 w = rng::omega4(k0, k1, sid, p, (uint32_t)q);
         acc[0] = fmaf(v, w.x, acc[0]);
         acc[1] = fmaf(v, w.y, acc[1]);
@@ -76,9 +80,16 @@ __global__ void __launch_bounds__(256) sp_sketch_items_kernel(SpIdx ix, int d, c
         acc[3] = fmaf(v, w.w, acc[3]);
       }
     }
+    // group 0 adds the other groups' sums in a fixed order
+    for (int s = 1; s < npass; ++s) {
+      const int src = (lane + s * nq) & 31;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
-    if (half == 0 && q < nq) {
+      for (int c = 0; c < 4; ++c) {
+        const float o = __shfl_sync(0xffffffffu, acc[c], src);
+        if (g == 0) acc[c] += o;
+      }
+    }
+    if (g == 0) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (4 * q + c < ell) part[(int64_t)it * ell + 4 * q + c] = (double)acc[c];
