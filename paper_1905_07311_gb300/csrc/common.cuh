@@ -107,6 +107,71 @@ inline ModeView mode_view(int order, const int64_t* dims, int n) {
 
 inline int ell_pad_of(int ell) { return ell <= 32 ? 32 : 64; }
 
+// Division of 32-bit unsigned integers by an invariant divisor d >= 1 with one multiply-high and
+// shifts (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// n / d = (t + ((n - t) >> 1)) >> (l - 1) for l >= 1, and n / 1 = n.
+struct FastDiv {
+  uint32_t d = 1, m = 0;
+  int l = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t dv) : d(dv) {
+    while ((uint64_t(1) << l) < d) ++l;
+    m = l ? (uint32_t)((((uint64_t)1 << 32) * ((uint64_t(1) << l) - d)) / d + 1) : 0u;
+  }
+  __host__ __device__ uint32_t div(uint32_t n) const {
+    if (l == 0) return n;
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(m, n);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)m * n) >> 32);
+#endif
+    return (t + ((n - t) >> 1)) >> (l - 1);
+  }
+};
+
+// Where a truncated core G <- U_r^T B (B: ell x M, column p = Kolda column of the unfolding of
+// mode n) stores element (c, p): the next mode m first, then the other modes in increasing order,
+// with the new index c of mode n (ko values) in its place.  With p's digits in increasing mode
+// order, i_m = (p / S) % I is mode m's digit and r = (p % S) + S (p / (S I)) the rest;
+//   out(c, p) = i_m + I ((r % Ln) + Ln (c + ko (r / Ln))) = base(p) + c I Ln.
+// S = I = 1 is the usual column-major order with c inserted after the modes before n (Ln of them).
+// For M < 2^31 the divisions use FastDiv (make() prepares them).
+struct CoreOut {
+  int64_t S = 1, I = 1, Ln = 1;
+  bool fast = false;
+  FastDiv fS, fI, fLn;
+  static CoreOut make(int64_t S, int64_t I, int64_t Ln, int64_t M) {
+    CoreOut c;
+    c.S = S;
+    c.I = I;
+    c.Ln = Ln;
+    c.fast = M < (int64_t(1) << 31) && S < (int64_t(1) << 31) && I < (int64_t(1) << 31) && Ln < (int64_t(1) << 31);
+    if (c.fast) {
+      c.fS = FastDiv((uint32_t)S);
+      c.fI = FastDiv((uint32_t)I);
+      c.fLn = FastDiv((uint32_t)Ln);
+    }
+    return c;
+  }
+  __host__ __device__ int64_t base(int64_t p, int ko) const {
+    if (fast) {
+      const uint32_t pp = (uint32_t)p;
+      const uint32_t q = fS.div(pp), q2 = fI.div(q);
+      const uint32_t im = q - q2 * (uint32_t)I;
+      const uint32_t r = (pp - q * (uint32_t)S) + (uint32_t)S * q2;
+      const uint32_t rq = fLn.div(r);
+      return (int64_t)im + I * ((int64_t)(r - rq * (uint32_t)Ln) + Ln * (int64_t)ko * rq);
+    }
+    const int64_t q = p / S, im = q % I;
+    const int64_t r = (p - q * S) + S * (q / I);
+    const int64_t rq = r / Ln;
+    return im + I * ((r - rq * Ln) + Ln * (int64_t)ko * rq);
+  }
+  __host__ __device__ int64_t cstride() const { return I * Ln; }
+  __host__ __device__ bool plain() const { return S == 1 && I == 1 && Ln == 1; }
+};
+
 // Storage of an RH_FP8_E4M3 tensor: E4M3 bytes column-major with the mode-1 fibres at a stride
 // of ld = I_1 rounded up to 16 (zero padding), i.e. ld x M bytes (M = prod of the other sizes),
 // then, from the next 16-byte boundary, one FP32 scale per 128 consecutive bytes of that array:

@@ -1,12 +1,8 @@
 // Truncated core of one R-STHOSVD mode (Alg. 1 step 6 inside Alg. 3): G_(n) <- U_r^T B with
 // B = Q^T G_(n) the ell x M mode product (column p at B + ell p) and U_r the leading r columns of
-// U_B (ell x r, column-major).  The output can be written in any order that keeps the Kolda
-// column order of B and inserts the new mode-n index at one position:
-//   out[(p % Lp) + Lp (c + ko (p / Lp))],
-// Lp = 1 .. M.  With Lp = the product of the sizes of the modes before n (in increasing mode
-// order) this is the usual column-major core; with Lp = I_m for the next mode m (the smallest
-// mode other than n) it stores the core with mode m fastest, so the next unfolding is read with
-// unit stride.
+// U_B (ell x r, column-major).  The output order is a CoreOut: the usual column-major core, or the
+// core with the next mode m first and the other modes in increasing order, so that the next
+// unfolding is read with unit stride and its Kolda column order (Omega's rows) is unchanged.
 //
 // A CTA takes 128 consecutive columns: the 128 x ell slice of B is read with 16-byte loads and
 // stored transposed in shared memory, U_r stays in shared memory, and each of the 256 threads
@@ -22,7 +18,7 @@ constexpr int kCpLd = kCpTile + 4;
 
 template <typename TO>
 __global__ void __launch_bounds__(256) core_product_kernel(const float* __restrict__ B, int ell, int ko, int64_t M,
-                                                           int64_t Lp, const float* __restrict__ U,
+                                                           CoreOut co, const float* __restrict__ U,
                                                            TO* __restrict__ out) {
   extern __shared__ __align__(16) float cp_smem[];
   float* Bt = cp_smem;                      // [64][kCpLd]: Bt[k][p]
@@ -84,16 +80,16 @@ __global__ void __launch_bounds__(256) core_product_kernel(const float* __restri
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(uu[a], xx[b], acc[a][b]);
     }
+    const int64_t cs = co.cstride();
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int c = 4 * cg + a;
-      if (c >= ko) continue;
+    for (int b = 0; b < 8; ++b) {
+      const int pp = (b < 4 ? 4 * pl + b : 64 + 4 * pl + (b - 4));
+      if (pp >= valid) continue;
+      const int64_t base = co.base(p0 + pp, ko);
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const int pp = (b < 4 ? 4 * pl + b : 64 + 4 * pl + (b - 4));
-        if (pp >= valid) continue;
-        const int64_t p = p0 + pp;
-        out[(p % Lp) + Lp * ((int64_t)c + (int64_t)ko * (p / Lp))] = (TO)acc[a][b];
+      for (int a = 0; a < 4; ++a) {
+        const int c = 4 * cg + a;
+        if (c < ko) out[base + cs * c] = (TO)acc[a][b];
       }
     }
   }
@@ -104,9 +100,9 @@ __global__ void __launch_bounds__(256) core_product_kernel(const float* __restri
 size_t core_product_smem() { return sizeof(float) * (64 * kCpLd + 64 * 64); }
 
 template <typename TO>
-rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, TO* out,
+rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, TO* out,
                               cudaStream_t st) {
-  if (ell < 1 || ell > 64 || ko < 1 || ko > 64 || Lp < 1 || M % Lp != 0) {
+  if (ell < 1 || ell > 64 || ko < 1 || ko > 64 || co.S < 1 || co.I < 1 || co.Ln < 1 || M % (co.S * co.I) != 0) {
     set_error("core product: bad shape");
     return RH_EINVAL;
   }
@@ -114,14 +110,14 @@ rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, int64_
   RH_CUDA_TRY(cudaFuncSetAttribute(core_product_kernel<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t ntiles = ceil_div(M, kCpTile);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 3 * (int64_t)num_sms()));
-  core_product_kernel<TO><<<grid, 256, smem, st>>>(B, ell, ko, M, Lp, U, out);
+  core_product_kernel<TO><<<grid, 256, smem, st>>>(B, ell, ko, M, co, U, out);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
 
-template rh_status launch_core_product<float>(const float*, int, int, int64_t, int64_t, const float*, float*,
+template rh_status launch_core_product<float>(const float*, int, int, int64_t, CoreOut, const float*, float*,
                                               cudaStream_t);
-template rh_status launch_core_product<double>(const float*, int, int, int64_t, int64_t, const float*, double*,
+template rh_status launch_core_product<double>(const float*, int, int, int64_t, CoreOut, const float*, double*,
                                                cudaStream_t);
 
 }  // namespace rh

@@ -53,9 +53,9 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
                             int32_t* err, cudaStream_t st);
 // G <- U^T B on the tensor cores for a truncated core (Alg. 1 step 6): B ell x M FP32 (layout
 // c + ell p, split on the fly), U ell x ko FP32 (split into two BF16 pieces in qa, 128 x ceil8(ell)),
-// out[(p % Lp) + Lp (c + ko (p / Lp))] FP32.  Needs ell % 4 == 0, ell, ko <= 64.
+// out[co.base(p) + c co.cstride()] FP32 (see CoreOut).  Needs ell % 4 == 0, ell, ko <= 64.
 bool core_product_tc_supported(int ell, int ko, int64_t M);
-rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, uint16_t* qa,
+rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, uint16_t* qa,
                                  float* out, int32_t* err, cudaStream_t st);
 rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                             const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
@@ -76,10 +76,10 @@ rh_status launch_ttm_residual(const ModeView& v, const T* G, const T* Q, int64_t
                               const T* Xref, double* part, double* out, cudaStream_t st);
 
 // ---- truncated core of one mode (core_product.cu) ---------------------------------------
-// out[(p % Lp) + Lp (c + ko (p / Lp))] = sum_k U[k + ell c] B[k + ell p], p < M, c < ko
-// (B: ell x M FP32 with c fastest; ell, ko <= 64; M % Lp == 0).
+// out[co.base(p) + c co.cstride()] = sum_k U[k + ell c] B[k + ell p], p < M, c < ko
+// (B: ell x M FP32 with c fastest; ell, ko <= 64; M % (co.S co.I) == 0).
 template <typename TO>
-rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, TO* out,
+rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, TO* out,
                               cudaStream_t st);
 
 // ---- core G = X x_1 A_1^T ... x_d A_d^T (tucker.cu) ----------------------------------------

@@ -67,7 +67,8 @@ struct Step {
   SketchPlan sk;
   TruncPlan tr;
   bool tc = false;      // sketch and mode product on the tensor cores (FP32 core split on the fly)
-  int64_t out_lp = 0;   // core product into out[(p % out_lp) + out_lp (c + ko (p / out_lp))]; 0: mode product
+  bool cp = false;      // truncated core by the core product (B has the new mode fastest) in the order cout
+  CoreOut cout;
   bool cp_tc = false;   // that core product on the tensor cores (B and U_r split into BF16 pieces)
 };
 
@@ -158,48 +159,48 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
     pl.in_form = dtype;
     if (o.truncate) {
       // Later modes: the core product of a step whose B has its new mode fastest (unit-stride
-      // view) writes the next core either in the usual order or, when the next mode m is the
-      // smallest mode other than the one just processed, with m fastest (the Kolda column order
-      // of the next unfolding is kept, so Omega's rows still line up); that mode then has a
-      // unit-stride view as well and runs on the tensor cores when its shape allows.
-      std::vector<int64_t> sz(dims, dims + order);
+      // view) writes the next core with the next mode m first and the other modes in increasing
+      // order (CoreOut), so the next unfolding keeps its Kolda column order (Omega's rows line up)
+      // and is read with unit stride; it runs on the tensor cores when its shape allows.  The
+      // final core is written in the usual column-major order.
+      std::vector<int64_t> sz(dims, dims + order);   // sizes of the current core
       for (int j = 0; j < order; ++j) {
         Step& sp = pl.steps[j];
         const int n = sp.mode;
-        sz[n] = sp.ko;   // sizes of the core after this step
-        if (sp.v.L != 1) continue;   // B is (L, ell, R): the mode product writes the usual order
-        if (j == order - 1) {
-          int64_t lp = 1;
-          for (int k = 0; k < n; ++k) lp *= sz[k];
-          sp.out_lp = lp;
-          break;
+        std::vector<int64_t> after = sz;
+        after[n] = sp.ko;
+        if (sp.v.L == 1) {
+          sp.cp = true;
+          if (j == order - 1) {
+            int64_t ln = 1;
+            for (int k = 0; k < n; ++k) ln *= after[k];
+            sp.cout = CoreOut::make(1, 1, ln, sp.v.M());
+          } else {
+            Step& nx = pl.steps[j + 1];
+            const int m = nx.mode;
+            int64_t S = 1, Ln = 1, Mn = 1;
+            for (int k = 0; k < order; ++k) {
+              if (k != n && k < m) S *= sz[k];          // stride of mode m in the columns of G_(n)
+              if (k < n && k != m) Ln *= after[k];      // modes before n in the new order
+              if (k != m) Mn *= after[k];
+            }
+            sp.cout = CoreOut::make(S, sz[m], Ln, sp.v.M());
+            nx.v = ModeView{1, sz[m], Mn};
+            nx.sk = plan_sketch(nx.v, nx.ell);
+            nx.tr = plan_trunc(ModeView{1, nx.ell, Mn}, nx.ell);
+            nx.tc = sketch_tc_supported(nx.v, nx.ell) && ttm_tc_supported(nx.v, nx.ell);
+            pl.max_part = std::max(pl.max_part, nx.sk.part_elems());
+            pl.max_pnorm = std::max(pl.max_pnorm, nx.sk.norm_elems());
+            pl.max_trunc = std::max(pl.max_trunc, trunc_workspace_elems<float>(nx.tr));
+          }
         }
-        Step& nx = pl.steps[j + 1];
-        const int m = nx.mode;
-        const int smallest_other = (n == 0) ? 1 : 0;
-        if (m == smallest_other) {
-          int64_t lp = sz[m];
-          for (int k = 0; k < n; ++k)
-            if (k != m) lp *= sz[k];
-          sp.out_lp = lp;
-          nx.v = ModeView{1, nx.v.I, nx.v.L * nx.v.R};
-          nx.sk = plan_sketch(nx.v, nx.ell);
-          nx.tr = plan_trunc(ModeView{1, nx.ell, nx.v.R}, nx.ell);
-          nx.tc = sketch_tc_supported(nx.v, nx.ell) && ttm_tc_supported(nx.v, nx.ell);
-          pl.max_part = std::max(pl.max_part, nx.sk.part_elems());
-          pl.max_pnorm = std::max(pl.max_pnorm, nx.sk.norm_elems());
-          pl.max_trunc = std::max(pl.max_trunc, trunc_workspace_elems<float>(nx.tr));
-        } else {
-          int64_t lp = 1;
-          for (int k = 0; k < n; ++k) lp *= sz[k];
-          sp.out_lp = lp;
-        }
+        sz = after;
       }
     }
     for (size_t j = 0; j < pl.steps.size(); ++j) {
       Step& sp = pl.steps[j];
       // the truncated core of a non-final mode on the tensor cores (the final core is FP64)
-      if (sp.out_lp > 0 && j + 1 < pl.steps.size() && core_product_tc_supported(sp.ell, sp.ko, sp.v.M())) {
+      if (sp.cp && j + 1 < pl.steps.size() && core_product_tc_supported(sp.ell, sp.ko, sp.v.M())) {
         sp.cp_tc = true;
         pl.qa_elems = std::max(pl.qa_elems, (size_t)128 * ((sp.ell + 7) / 8 * 8));
       }
@@ -422,20 +423,20 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         return s;
       const ModeView vb{sp.v.L, sp.ell, sp.v.R};
       ProfileScope ps(PROF_TTM_CORE, j, st);
-      if (sp.out_lp > 0) {
+      if (sp.cp) {
         // B has the new mode fastest: G <- U_r^T B written in the order the next step reads
         const float* Bf = reinterpret_cast<const float*>(B);
         const float* Uf = reinterpret_cast<const float*>(b.Uc);
         if (last) {
-          if ((s = launch_core_product<double>(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf, core, st)) != RH_OK)
+          if ((s = launch_core_product<double>(Bf, sp.ell, sp.ko, sp.v.M(), sp.cout, Uf, core, st)) != RH_OK)
             return s;
         } else {
           const int wg = 1 - wb;
           if (sp.cp_tc)
-            s = launch_core_product_tc(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf, b.qa, static_cast<float*>(b.W[wg]),
+            s = launch_core_product_tc(Bf, sp.ell, sp.ko, sp.v.M(), sp.cout, Uf, b.qa, static_cast<float*>(b.W[wg]),
                                        b.err, st);
           else
-            s = launch_core_product<float>(Bf, sp.ell, sp.ko, sp.v.M(), sp.out_lp, Uf, static_cast<float*>(b.W[wg]),
+            s = launch_core_product<float>(Bf, sp.ell, sp.ko, sp.v.M(), sp.cout, Uf, static_cast<float*>(b.W[wg]),
                                            st);
           if (s != RH_OK) return s;
           cur = static_cast<const T*>(b.W[wg]);

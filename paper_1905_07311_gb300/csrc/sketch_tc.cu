@@ -6,7 +6,7 @@
 // and a BF16 tail, 16 significant bits).  Omega is the library's Gaussian stream rounded to
 // BF16 (ties to even), so every product is exact and sums run in FP32 inside TMEM.
 //
-// Grid: persistent CTAs, each owning a contiguous range of 64-column chunks of X_(1) (split-K).
+// Grid: persistent CTAs, each taking every gridDim.x-th 64-column chunk of X_(1) (split-K).
 // A CTA keeps the accumulators of all row tiles (I <= 128 * kMaxTiles rows x 64 columns, FP32)
 // in TMEM, so each Omega tile is generated once and used by every row tile.
 // Warp roles (192 threads): warp 0 issues TMA loads of the X pieces (128 x 64 tiles, MN-major
@@ -14,10 +14,10 @@
 // warps 2-5 generate the 64 x 64 Omega tile (K-major operand B, 128-byte swizzle) and, at the
 // end, read the accumulators back and write this CTA's partial sketch [I x ell] (FP32).
 //
-// FP32 input (448 threads): TMA brings FP32 tiles (four 32 x 64 boxes per 128 x 64 tile) and
-// warps 6-13 split them in shared memory into the same head / tail pieces that the separate
-// split produces, so the products, and the sketch, are bit-identical to the two-piece form;
-// they also accumulate ||head + tail||^2 for the norm of the input.
+// FP32 input (448 threads): TMA brings FP32 tiles (one unswizzled 128 x 64 box: 512-byte column
+// segments) and warps 6-13 split them in shared memory into the same head / tail pieces that the
+// separate split produces, so the products, and the sketch, are bit-identical to the two-piece
+// form; they also accumulate ||head + tail||^2 for the norm of the input.
 #include <mutex>
 #include <string>
 
@@ -89,8 +89,9 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
       *reinterpret_cast<SketchSmem<IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (M + kPChunk - 1) / kPChunk;
-  const int64_t c_begin = (int64_t)blockIdx.x * chunks_per_cta;
-  const int64_t c_end = c_begin + chunks_per_cta < nchunks ? c_begin + chunks_per_cta : nchunks;
+  // chunks are dealt round-robin (c = blockIdx.x, blockIdx.x + gridDim.x, ...)
+  (void)chunks_per_cta;
+  const int64_t c_begin = blockIdx.x, c_step = gridDim.x, c_end = nchunks;
   const uint32_t tmem_cols = (uint32_t)(mtiles <= 1 ? 64 : (mtiles <= 2 ? 128 : (mtiles <= 4 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
       tc::prefetch_tmap(&map0);
       if (!F32IN && npieces > 1) tc::prefetch_tmap(&map1);
       uint32_t it = 0;
-      for (int64_t c = c_begin; c < c_end; ++c) {
+      for (int64_t c = c_begin; c < c_end; c += c_step) {
         const int32_t p0 = (int32_t)(c * kPChunk);
         for (int m = 0; m < mtiles; ++m, ++it) {
           if constexpr (F32IN) {
@@ -137,8 +138,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
               tc::tma_load_2d(&S.xf[s][0], &map0, m * kRowsTile, p0, &S.f32full[s]);
             } else {
               tc::mbar_arrive_expect_tx(&S.f32full[s], kF32Tile);
-              for (int b = 0; b < 4; ++b)
-                tc::tma_load_2d(&S.xf[s][b * kF32Box], &map0, m * kRowsTile + 32 * b, p0, &S.f32full[s]);
+              tc::tma_load_2d(&S.xf[s][0], &map0, m * kRowsTile, p0, &S.f32full[s]);   // 128 x 64, unswizzled
             }
           } else {
             const uint32_t s = it % NS;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
       constexpr uint32_t idesc = tc::idesc_bf16(128, 64, /*A MN-major*/ 1, /*B K-major*/ 0);
       uint32_t it = 0, oc = 0;
       bool first = true;
-      for (int64_t c = c_begin; c < c_end; ++c, ++oc) {
+      for (int64_t c = c_begin; c < c_end; c += c_step, ++oc) {
         const uint32_t b = oc & 1;
         if (!tc::mbar_wait(&S.om_full[b], (oc >> 1) & 1, err, 2)) break;
         tc::tc_fence_after();
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     // ---------------- Omega generators (warps 2..5) ----------------
     const int t = threadIdx.x - 64;   // 0..127
     uint32_t oc = 0;
-    for (int64_t c = c_begin; c < c_end; ++c, ++oc) {
+    for (int64_t c = c_begin; c < c_end; c += c_step, ++oc) {
       const uint32_t b = oc & 1;
       if (oc >= 2 && !tc::mbar_wait(&S.om_empty[b], ((oc >> 1) - 1) & 1, err, 4)) break;
       uint8_t* om = &S.om[b][0];
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     double acc = 0.0;
     uint32_t it = 0;
     bool ok = true;
-    for (int64_t c = c_begin; c < c_end && ok; ++c) {
+    for (int64_t c = c_begin; c < c_end && ok; c += c_step) {
       for (int m = 0; m < mtiles; ++m, ++it) {
         const uint32_t s = it % NF, ps = it % NS;
         if (!tc::mbar_wait(&S.f32full[s], (it / NF) & 1, err, 6) ||
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
                                                                    scales, ld, (int64_t)m * kRowsTile,
                                                                    c * kPChunk, I, M);
         else
-          acc += (double)tc::convert_tile<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+          acc += (double)tc::convert_tile_plain<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&S.f32empty[s]);
         tc::mbar_arrive(&S.full[ps]);
@@ -356,6 +356,27 @@ rh_status make_bf16_map_2d(CUtensorMap* map, const void* base, int64_t rows, int
   return make_map_2d(map, base, 2, rows, cols, box_cols);
 }
 
+// 2-D tensor map over a rows x cols column-major FP32 / BF16 matrix, box box_rows x box_cols, no
+// swizzle (rows of box_rows * esize bytes, at most 256 elements), zero fill outside.
+rh_status make_map_2d_plain(CUtensorMap* map, const void* base, int esize, int64_t rows, int64_t cols, int box_rows,
+                            int box_cols) {
+  EncodeTiledFn enc;
+  rh_status s = get_encoder(&enc);
+  if (s != RH_OK) return s;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)rows * (cuuint64_t)esize};
+  const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (plain) failed with code " + std::to_string((int)r));
+    return RH_ECUDA;
+  }
+  return RH_OK;
+}
+
 // 2-D tensor map over bytes: rows x cols, column-major with leading dimension ld (a multiple of
 // 16), box box_rows x box_cols, no swizzle, zero fill outside rows x cols.
 rh_status make_u8_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64_t ld, int64_t cols, int box_rows,
@@ -423,7 +444,7 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
     return RH_EUNSUPPORTED;
   }
   CUtensorMap m0;
-  rh_status s = make_map_2d(&m0, X, 4, v.I, v.M(), 64);
+  rh_status s = make_map_2d_plain(&m0, X, 4, v.I, v.M(), kRowsTile, 64);
   if (s != RH_OK) return s;
   const int ctas = sketch_tc_ctas(v);
   const int64_t nchunks = ceil_div(v.M(), kPChunk);

@@ -189,6 +189,42 @@ __device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, u
   return ss;
 }
 
+// As convert_tile, for a tile staged unswizzled: kPRows columns of 128 consecutive FP32 rows each
+// (value (i, p) at byte 512 p + 4 i, one TMA box of 512-byte rows); the output pieces are the same
+// (value (p, i) at (i / 64) kPRows 128 + 128 p + ((i % 64 / 8) ^ (p % 8)) 16 + 2 (i % 8)).  A warp
+// reads one 512-byte column (conflict-free) and writes two 128-byte output rows.
+template <int kPRows, int kThreadsConv>
+__device__ __forceinline__ float convert_tile_plain(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
+                                                    uint8_t* __restrict__ lo, int t) {
+  constexpr int kUnits = kPRows * 32 / kThreadsConv;
+  float4 v[kUnits];
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {
+    const int u = j * kThreadsConv + t;
+    v[j] = *reinterpret_cast<const float4*>(f32 + (u >> 5) * 512 + (u & 31) * 16);
+  }
+  float ss = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {
+    const int u = j * kThreadsConv + t;
+    const int p = u >> 5, i = (u & 31) * 4;
+    const uint32_t h01 = pack_bf16x2(v[j].x, v[j].y), h23 = pack_bf16x2(v[j].z, v[j].w);
+    const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
+    const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
+    const uint32_t t01 = pack_bf16x2(v[j].x - f0, v[j].y - f1), t23 = pack_bf16x2(v[j].z - f2, v[j].w - f3);
+    const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
+    const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
+    ss = fmaf(g0, g0, ss);
+    ss = fmaf(g1, g1, ss);
+    ss = fmaf(g2, g2, ss);
+    ss = fmaf(g3, g3, ss);
+    const int off = (i >> 6) * (kPRows * 128) + p * 128 + ((((i & 63) >> 3) ^ (p & 7)) << 4) + ((i >> 2) & 1) * 8;
+    *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
+    *reinterpret_cast<uint2*>(lo + off) = make_uint2(t01, t23);
+  }
+  return ss;
+}
+
 // Input kinds of the tensor-core sketch and mode product: BF16 pieces loaded by TMA as they are,
 // FP32 values or E4M3 bytes (with per-128-element scales) converted in shared memory.
 constexpr int kInPieces = 0, kInF32 = 1, kInFp8 = 2;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
                   float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld,
-                  int64_t Lp) {
+                  CoreOut co) {
   using Cfg = TtmCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
       }
       named_sync(1, 128);
       const int64_t p0 = t * kNTile;
-      if (Lp == 1) {
+      if (co.plain()) {
         // B[c + ell p]: the threads of a warp hold consecutive rows c, so the stores are coalesced
         if (!tail) {
           for (int cc = 0; cc < kNTile / 16; ++cc) {
@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
         tc::tc_fence_before();
         tc::mbar_arrive(&S.tempty[b]);
       } else {
-        // B[(p % Lp) + Lp (c + ell (p / Lp))]: sum the halves in shared memory, then each warp
-        // writes whole rows c with its lanes along p
+        // B[co.base(p) + c co.cstride()] (CoreOut): sum the halves in shared memory, then each
+        // warp writes whole rows c with its lanes along p
         if (!tail) {
           for (int cc = 0; cc < kNTile / 16; ++cc) {
             float v[16];
@@ -242,15 +242,12 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
         tc::mbar_arrive(&S.tempty[b]);
         named_sync(1, 128);
         const int wq = warp - 2;   // 0..3
-        int64_t q0 = (p0 + lane) / Lp, r0 = (p0 + lane) - q0 * Lp;
+        const int64_t cs = co.cstride();
         for (int jj = lane; jj < kNTile; jj += 32) {
           const int64_t p = p0 + jj;
-          if (p < M)
-            for (int c = wq; c < ell; c += 4) B[r0 + Lp * ((int64_t)c + (int64_t)ell * q0)] = S.xchg[c][jj];
-          r0 += 32;
-          while (r0 >= Lp) {
-            r0 -= Lp;
-            ++q0;
+          if (p < M) {
+            const int64_t base = co.base(p, ell);
+            for (int c = wq; c < ell; c += 4) B[base + cs * c] = S.xchg[c][jj];
           }
         }
       }
@@ -347,7 +344,7 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, 1);
+                                                                         nullptr, 0, CoreOut{});
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -372,7 +369,7 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, 1);
+                                                                         nullptr, 0, CoreOut{});
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -381,9 +378,9 @@ bool core_product_tc_supported(int ell, int ko, int64_t M) {
   return ell >= 1 && ell <= 64 && ell % 4 == 0 && ko >= 1 && ko <= 64 && M >= 1 && M < (int64_t(1) << 31);
 }
 
-rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, int64_t Lp, const float* U, uint16_t* qa,
+rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, uint16_t* qa,
                                  float* out, int32_t* err, cudaStream_t st) {
-  if (!core_product_tc_supported(ell, ko, M) || Lp < 1 || M % Lp != 0) {
+  if (!core_product_tc_supported(ell, ko, M) || co.S < 1 || co.I < 1 || co.Ln < 1 || M % (co.S * co.I) != 0) {
     set_error("tensor-core core product: unsupported shape (needs ell % 4 == 0, ell, r <= 64)");
     return RH_EUNSUPPORTED;
   }
@@ -402,7 +399,7 @@ rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, int
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err, nullptr,
-                                                                         0, Lp);
+                                                                         0, co);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -428,7 +425,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         scales, ld, 1);
+                                                                         scales, ld, CoreOut{});
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
