@@ -81,9 +81,10 @@ enum {
  *                   to 16 (padding bytes are ignored), ld x prod_{k>1} I_k bytes, then, from the next
  *                   16-byte boundary, the FP32 scales: element (i, p) of X_(1) has the value
  *                   fl32(e4m3[i + ld p] * scales[(i + ld p) / 128]) (FP32 product, ties to even).
- *                   The kernels of the first mode dequantize each tile in shared memory and split it
- *                   as RH_F32_BF16X2 does, so the results are bit-identical to RH_F32_BF16X2 on the
- *                   dequantized FP32 tensor; the first mode must run on the tensor cores.
+ *                   The kernels of the first mode dequantize each tile in shared memory and round it
+ *                   to one BF16 piece (ties to even; E4M3 holds 4 significant bits, so a second piece
+ *                   would add nothing but work), so the results are bit-identical to RH_BF16 on
+ *                   bf16 of the dequantized values; the first mode must run on the tensor cores.
  * The BF16 forms use the tensor cores (tcgen05) for the first mode's sketch and mode product, with
  * Omega rounded to BF16 (ties to even) and FP32 accumulation; the intermediate cores are FP32.  In
  * R-STHOSVD (truncating) the core after a mode is written with the next mode fastest when that

@@ -71,8 +71,9 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int col) {
 }
 
 // IN = kInPieces: map0 / map1 are the BF16 pieces (box 64 x 64).  IN = kInF32: map0 is the FP32
-// tensor (box 32 x 64), split on the fly.  IN = kInFp8: map0 is the E4M3 tensor (box 128 x 64
-// bytes, leading dimension ld), dequantized with ``scales`` and split on the fly.  With converted
+// tensor (one unswizzled 128 x 64 box), split on the fly.  IN = kInFp8: map0 is the E4M3 tensor
+// (box 128 x 64 bytes, leading dimension ld), dequantized with ``scales`` and rounded to one BF16
+// piece on the fly (npieces = 1).  With converted
 // input, norm_part[blockIdx.x] receives this CTA's sum of squares of the split values (head + tail).
 template <int IN>
 __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
@@ -242,9 +243,8 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
           break;
         }
         if constexpr (IN == tc::kInFp8)
-          acc += (double)tc::convert_fp8_tile<128, 64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t,
-                                                                   scales, ld, (int64_t)m * kRowsTile,
-                                                                   c * kPChunk, I, M);
+          acc += (double)tc::convert_fp8_tile<128, 64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], nullptr, t, scales,
+                                                                   ld, (int64_t)m * kRowsTile, c * kPChunk, I, M);
         else
           acc += (double)tc::convert_tile_plain<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         tc::fence_proxy_async_smem();
@@ -479,7 +479,7 @@ rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, con
   const size_t smem = sizeof(SketchSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
-      m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
+      m0, m0, 1, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
       norm_part, err, scales, ld);
   RH_LAUNCH_CHECK();
   return RH_OK;

@@ -241,14 +241,15 @@ __device__ __forceinline__ float e4m3_to_f32(uint32_t b) {
 }
 
 // Dequantize a tile of E4M3 values staged by TMA (kPRows rows of kRowBytes bytes, no swizzle; a
-// row is one column p of the unfolding, its bytes consecutive rows i) and split it into BF16 head
-// and tail exactly as convert_tile does for FP32 input.  The value of storage element (i, p) of the
-// tensor (leading dimension ld) is x = fl32(e4m3 * s) with s = scales[(i + ld p) / 128]; elements
-// outside the tensor (i >= I or p >= M, zero-filled by TMA) take s = 0.  Output layout as in
-// convert_tile: value (p, i) at byte (i / 64) kPRows 128 + 128 p + ((i % 64 / 8) ^ (p % 8)) 16 +
-// 2 (i % 8).  Each unit is 16 consecutive bytes of one row; ld % 16 == 0 puts its 16 elements in
-// one scale block.  Returns the FP32 sum of (head + tail)^2 over this thread's values.
-template <int kRowBytes, int kPRows, int kThreadsConv>
+// row is one column p of the unfolding, its bytes consecutive rows i) and round it to one BF16
+// piece, bf16(x) (ties to even), written in the layout of convert_tile (or, with kTwoPieces, split
+// into head and tail exactly as convert_tile does for FP32 input).  The value of storage element
+// (i, p) of the tensor (leading dimension ld) is x = fl32(e4m3 * s) with s = scales[(i + ld p) /
+// 128]; elements outside the tensor (i >= I or p >= M, zero-filled by TMA) take s = 0.  Output:
+// value (p, i) at byte (i / 64) kPRows 128 + 128 p + ((i % 64 / 8) ^ (p % 8)) 16 + 2 (i % 8).  Each
+// unit is 16 consecutive bytes of one row; ld % 16 == 0 puts its 16 elements in one scale block.
+// Returns the FP32 sum of the squares of the values written (bf16(x), or head + tail).
+template <int kRowBytes, int kPRows, int kThreadsConv, bool kTwoPieces = false>
 __device__ __forceinline__ float convert_fp8_tile(const uint8_t* __restrict__ src, uint8_t* __restrict__ hi,
                                                   uint8_t* __restrict__ lo, int t, const float* __restrict__ scales,
                                                   int64_t ld, int64_t i0, int64_t p0, int64_t I, int64_t M) {
@@ -272,6 +273,7 @@ __device__ __forceinline__ float convert_fp8_tile(const uint8_t* __restrict__ sr
     const int p = u / kUnitsPerRow, il = (u % kUnitsPerRow) * 16;
     const uint32_t w[4] = {raw[j].x, raw[j].y, raw[j].z, raw[j].w};
     uint32_t h[8], tl[8];
+    (void)tl;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const uint32_t word = w[q >> 1] >> (16 * (q & 1));
@@ -279,18 +281,25 @@ __device__ __forceinline__ float convert_fp8_tile(const uint8_t* __restrict__ sr
       const float x1 = __fmul_rn(e4m3_to_f32((word >> 8) & 0xFFu), sc[j]);
       h[q] = pack_bf16x2(x0, x1);
       const float f0 = __uint_as_float(h[q] << 16), f1 = __uint_as_float(h[q] & 0xFFFF0000u);
-      tl[q] = pack_bf16x2(x0 - f0, x1 - f1);
-      const float g0 = f0 + __uint_as_float(tl[q] << 16), g1 = f1 + __uint_as_float(tl[q] & 0xFFFF0000u);
-      ss = fmaf(g0, g0, ss);
-      ss = fmaf(g1, g1, ss);
+      if constexpr (kTwoPieces) {
+        tl[q] = pack_bf16x2(x0 - f0, x1 - f1);
+        const float g0 = f0 + __uint_as_float(tl[q] << 16), g1 = f1 + __uint_as_float(tl[q] & 0xFFFF0000u);
+        ss = fmaf(g0, g0, ss);
+        ss = fmaf(g1, g1, ss);
+      } else {
+        ss = fmaf(f0, f0, ss);
+        ss = fmaf(f1, f1, ss);
+      }
     }
     const int base = (il >> 6) * (kPRows * 128) + p * 128;
     const int c0 = (il & 63) >> 3;
     const int o0 = base + ((c0 ^ (p & 7)) << 4), o1 = base + (((c0 + 1) ^ (p & 7)) << 4);
     *reinterpret_cast<uint4*>(hi + o0) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(hi + o1) = make_uint4(h[4], h[5], h[6], h[7]);
-    *reinterpret_cast<uint4*>(lo + o0) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
-    *reinterpret_cast<uint4*>(lo + o1) = make_uint4(tl[4], tl[5], tl[6], tl[7]);
+    if constexpr (kTwoPieces) {
+      *reinterpret_cast<uint4*>(lo + o0) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+      *reinterpret_cast<uint4*>(lo + o1) = make_uint4(tl[4], tl[5], tl[6], tl[7]);
+    }
   }
   return ss;
 }

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
           break;
         }
         if constexpr (IN == tc::kInFp8)
-          (void)tc::convert_fp8_tile<64, 128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t, scales, ld,
+          (void)tc::convert_fp8_tile<64, 128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], nullptr, t, scales, ld,
                                                           (int64_t)ks * kKStage, tt * kNTile, I, M);
         else
           (void)tc::convert_tile<128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
@@ -424,7 +424,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   constexpr int IN = tc::kInFp8;
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
+  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 1, v.I, v.M(), ell, B, err,
                                                                          scales, ld, CoreOut{});
   RH_LAUNCH_CHECK();
   return RH_OK;

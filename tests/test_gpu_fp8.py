@@ -1,14 +1,14 @@
 """Low-precision storage forms on the tensor cores (needs a GB300).
 
 E4M3 with per-128-byte FP32 scales (RH_FP8_E4M3): the kernels of the first mode dequantize each
-tile, x = fl32(e4m3 * scale), and split it into BF16 head + tail exactly as the FP32 form does, so
-* the sketch, the mode product and the whole R-STHOSVD must be bit-identical to the FP32-split
-  form (RH_F32_BF16X2) run on the dequantized FP32 tensor (the norm ||X||^2 only up to the order
-  of its FP32 partial sums: relative 1e-6);
-* against the oracle on the tensor the bytes denote (oracle.storage), the gates of the
-  two-piece form apply: relative Tucker error within 1e-5 absolute of the oracle's on the
-  represented input with the same BF16-rounded Omega, and within 2 % of it relative, which is the
-  agreement asked of the low-precision forms.
+tile, x = fl32(e4m3 * scale), and round it to one BF16 piece (ties to even), so
+* the sketch, the mode product and the whole R-STHOSVD must be bit-identical to the BF16 form
+  (RH_BF16) run on bf16(x) (the norm ||X||^2 only up to the order of its FP32 partial sums:
+  relative 1e-6);
+* against the oracle: relative Tucker error within 1e-5 absolute of the oracle's on the values
+  the tensor cores see, bf16(x), with the same BF16-rounded Omega, and within 2 % of the oracle's
+  on the tensor the bytes denote (oracle.storage), which is the agreement asked of the
+  low-precision forms.
 BF16 storage (RH_BF16): the oracle reads the BF16 values exactly; same gates.
 """
 
@@ -56,36 +56,48 @@ def _fp8(X):
     return torch.from_numpy(buf).cuda(), fp8_dequantize(buf, X.shape)
 
 
+def _bf16_of(X):
+    """(int16 CUDA tensor of the BF16 bits, float64 values) of bf16(X) (ties to even), column-major."""
+    x = np.asarray(X, dtype=np.float32)
+    r = orng.round_bf16(x)
+    bits = (np.ascontiguousarray(r.ravel(order="F")).view(np.uint32) >> 16).astype(np.uint16)
+    return torch.from_numpy(bits.view(np.int16).copy()).cuda(), r.astype(np.float64)
+
+
 @pytest.mark.parametrize("shape", [(128, 300, 7), (200, 40, 40), (1024, 64, 33), (96, 1000), (8, 5000)])
 @pytest.mark.parametrize("ell", [1, 25, 64])
-def test_fp8_sketch_bit_identical_to_f32_split(rh, shape, ell):
+def test_fp8_sketch_bit_identical_to_bf16_of_dequantized(rh, shape, ell):
     rs = np.random.default_rng(hash((shape, ell)) % 2 ** 32)
     X = (rs.standard_normal(shape) * np.exp(rs.uniform(-4, 4, shape))).astype(np.float32)
     buf, Xdq = _fp8(X)
+    Xb, Xbv = _bf16_of(Xdq)
     Y8, n8 = rh.rhosvd_sketch_bf16(buf, list(shape), ell, seed=5, tensor_id=3, pieces="fp8", with_norm=True)
-    Yf, nf = rh.rhosvd_sketch_bf16(_flat32(Xdq), list(shape), ell, seed=5, tensor_id=3, pieces="f32", with_norm=True)
-    assert torch.equal(Y8, Yf)
-    ref = float(np.sum(_rep_bf16x2(Xdq) ** 2))
-    assert abs(n8.item() - ref) <= 1e-6 * ref and abs(n8.item() - nf.item()) <= 1e-6 * ref
+    Yb = rh.rhosvd_sketch_bf16(Xb, list(shape), ell, seed=5, tensor_id=3, pieces=1)
+    assert torch.equal(Y8, Yb)
+    ref = float(np.sum(Xbv ** 2))
+    assert abs(n8.item() - ref) <= 1e-6 * ref
 
 
 @pytest.mark.parametrize("shape,k", [((128, 300), 60), ((200, 129), 1), ((200, 7, 9), 25), ((1024, 300), 64),
                                      ((8, 77, 3), 17)])
-def test_fp8_mode_product_bit_identical_to_f32_split(rh, shape, k):
+def test_fp8_mode_product_bit_identical_to_bf16_of_dequantized(rh, shape, k):
     rs = np.random.default_rng(7)
     X = rs.standard_normal(shape).astype(np.float32)
     buf, Xdq = _fp8(X)
+    Xb, _ = _bf16_of(Xdq)
     A = torch.from_numpy(rs.standard_normal((k, shape[0]))).cuda()
     Y8 = rh.mode_product_bf16(buf, list(shape), A, pieces="fp8")
-    Yf = rh.mode_product_bf16(_flat32(Xdq), list(shape), A, pieces="f32")
-    assert torch.equal(Y8, Yf)
+    Yb = rh.mode_product_bf16(Xb, list(shape), A, pieces=1)
+    assert torch.equal(Y8, Yb)
 
 
-def _check_vs_oracle(T, Xin, ranks, p, seed, rho):
+def _check_vs_oracle(T, Xin, ranks, p, seed, rho, Xseen=None):
+    """Xin: the tensor the storage denotes; Xseen: the values the first mode's tensor cores read
+    (default: the head + tail split of Xin)."""
     d = Xin.ndim
     info = T.info.cpu().numpy().tolist()
     rnd = {m: "bf16" for m in range(d) if info[m] & 4}
-    Xrep = _rep_bf16x2(Xin)
+    Xrep = _rep_bf16x2(Xin) if Xseen is None else Xseen
     A = [f.cpu().numpy().T for f in T.factors]
     G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
     e_g = rel_error(Xrep, G, A)
@@ -108,9 +120,10 @@ def test_rsthosvd_fp8(rh, shape, ranks, p, rho):
     d = len(shape)
     X = lowrank_plus_noise_np(list(shape), [max(ranks) + 2] * d, 0.8, 1e-3, seed=31).astype(np.float32)
     buf, Xdq = _fp8(X)
+    Xb, Xbv = _bf16_of(Xdq)
     T8 = rh.rsthosvd(buf, list(shape), list(ranks), p=p, seed=4, rho=rho, form="fp8_e4m3")
     T8c = [f.clone() for f in T8.factors] + [T8.core.clone(), T8.norms.clone(), T8.info.clone()]
-    Tf = rh.rsthosvd(_flat32(Xdq), list(shape), list(ranks), p=p, seed=4, rho=rho, form="f32_bf16x2")
+    Tf = rh.rsthosvd(Xb, list(shape), list(ranks), p=p, seed=4, rho=rho, form="bf16")
     torch.cuda.synchronize()
     for a, b in zip(T8c[:d], Tf.factors):
         assert torch.equal(a, b)
@@ -119,7 +132,7 @@ def test_rsthosvd_fp8(rh, shape, ranks, p, rho):
     assert T8c[d + 1][1].item() == Tf.norms[1].item()
     assert abs(T8c[d + 1][0].item() - Tf.norms[0].item()) <= 1e-6 * Tf.norms[0].item()
     assert T8.info.cpu().numpy()[0] & 4
-    _check_vs_oracle(T8, Xdq, ranks, p, 4, rho)
+    _check_vs_oracle(T8, Xdq, ranks, p, 4, rho, Xseen=np.reshape(Xbv, Xdq.shape))
 
 
 @pytest.mark.parametrize("form", ["fp8_e4m3", "bf16"])
@@ -127,15 +140,17 @@ def test_hilbert_200_low_precision_storage(rh, form):
     """The 200^3 tensor 1/(i+j+k+1) stored in E4M3 (block scales) or BF16; rank 20, p = 5, seed 0,
     order 1, 2, 3 (the FP64 configuration of the same tensor)."""
     X = hilbert([200, 200, 200], offset=1).astype(np.float32)
+    Xseen = None
     if form == "fp8_e4m3":
         Xb, Xin = _fp8(X)
+        Xseen = np.reshape(_bf16_of(Xin)[1], X.shape)
     else:
         bits = bf16_bits_np(X)
         Xb = torch.from_numpy(bits.view(np.int16).copy()).cuda()
         Xin = np.reshape((bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64), X.shape, order="F")
     T = rh.rsthosvd(Xb, [200, 200, 200], [20, 20, 20], p=5, seed=0, rho=[0, 1, 2], form=form)
     torch.cuda.synchronize()
-    e_g, e_ref = _check_vs_oracle(T, Xin, [20, 20, 20], 5, 0, [0, 1, 2])
+    e_g, e_ref = _check_vs_oracle(T, Xin, [20, 20, 20], 5, 0, [0, 1, 2], Xseen=Xseen)
     # the error against the original tensor is the storage's quantisation error, not the method's
     A = [f.cpu().numpy().T for f in T.factors]
     G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
@@ -156,6 +171,7 @@ def test_adaptive_sthosvd_low_precision(rh, form, eps, block):
     X = lowrank_plus_noise_np(shape, [14, 12, 10], 0.7, 1e-4, seed=33).astype(np.float32)
     if form == "fp8_e4m3":
         Xb, Xin = _fp8(X)
+        Xin = np.reshape(_bf16_of(Xin)[1], X.shape)   # the values the tensor cores read
     elif form == "bf16":
         bits = bf16_bits_np(X)
         Xb = torch.from_numpy(bits.view(np.int16).copy()).cuda()
