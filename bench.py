@@ -594,8 +594,10 @@ def wl_lowp192(torch, rh, L, args, device, peaks, src):
 
 
 def wl_batched(torch, rh, L, args, device, peaks, src):
-    """The batched workload's order-3 and order-4 tensors (339 of 512, 8.0 GB FP32), one
-    rsthosvd_batched call captured in a CUDA graph and replayed."""
+    """The batched workload's order-3 and order-4 tensors (339 of 512, 8.0 GB FP32).  Grouped engine
+    (--streams 0): a batched plan (each tensor's launches recorded once, one grouped launch per stage)
+    whose run is captured in a CUDA graph and replayed; stream engine (--streams N): one
+    rsthosvd_batched call captured and replayed."""
     from workloads import batch_recipe, lowrank_plus_noise_torch
 
     rec = [b for b in batch_recipe() if len(b[0]) in (3, 4)]
@@ -603,19 +605,21 @@ def wl_batched(torch, rh, L, args, device, peaks, src):
     nbytes = sum(4 * x.numel() for x in Xs)
     call = rh.RsthosvdBatchedCall([b[0] for b in rec], [b[1] for b in rec], torch.float32, p=5, seed=4, clamp=True,
                                   streams=args.streams, device=device)
-    call.run(Xs)
+    plan = call.plan(Xs) if args.streams == 0 else None
+    step = plan.run if plan is not None else (lambda: call.run(Xs))
+    step()
     torch.cuda.synchronize()
     s = torch.cuda.Stream(device=device)
     s.wait_stream(torch.cuda.current_stream(device))
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
-        call.run(Xs)
+        step()
         torch.cuda.synchronize()
         with torch.cuda.graph(g, stream=s):
-            call.run(Xs)
+            step()
     ms, _, _, clk = _timed(torch, L, g.replay, args.steps, args.warmup, device, profile=False)
     n0 = L.rh_kernel_launches()
-    call.run(Xs)
+    step()
     torch.cuda.synchronize()
     launches = L.rh_kernel_launches() - n0
     tps = len(Xs) / (ms * 1e-3)
@@ -637,7 +641,8 @@ def wl_batched(torch, rh, L, args, device, peaks, src):
             "ms_per_step": round(ms, 3),
             "config": {"workload": f"{len(Xs)} tensors, order 3-4, sizes U[16,96], ranks U[4,16] capped, low rank + "
                                    f"1e-3 noise, seed 4, p=5 clamped; {nbytes / 1e9:.2f} GB FP32",
-                       "streams": args.streams, "graph": True, "l2": "inputs 8 GB (larger than L2); no flush"},
+                       "engine": "grouped (batched plan)" if args.streams == 0 else f"{args.streams} streams",
+                       "graph": True, "l2": "inputs 8 GB (larger than L2); no flush"},
             "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
 
 
@@ -727,7 +732,9 @@ def main():
                     choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse"],
                     help="dense1024: the benchmark line (default); the others measure the further configurations "
                          "and print one JSON line each")
-    ap.add_argument("--streams", type=int, default=8, help="internal streams of the batched workload")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="batched workload: 0 = grouped engine (one launch per stage for the batch), "
+                         "N >= 1 = N internal streams")
     args = ap.parse_args()
     if args.workload != "dense1024":
         run_workload(args)

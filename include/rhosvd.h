@@ -294,16 +294,24 @@ rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void
  *            device int32 array laid out like dims.
  *   opts     shared by every tensor; tensor i draws Omega with tensor_id = opts->tensor_id + i.
  *            The processing order must be the default (opts->rho[0] < 0).
- *   streams  number of internal streams (0 = min(8, count), at most 32).  The caller's stream is
- *            forked into them with an event, tensors are placed largest first (by element count)
- *            on the least-loaded stream, and every stream is joined back into ``stream`` before
- *            the call returns; no host synchronisation, so the call is CUDA-graph capturable.
- *   workspace  one slice per internal stream, each the largest rsthosvd_workspace_size of the
- *            batch (rounded to 256 B); rsthosvd_batched_workspace_size returns the total (0 on an
- *            invalid request).  The placement, and so the result, does not depend on timing:
- *            each tensor's result equals that of a single rsthosvd call.
- *   Errors: RH_EINVAL names the first invalid tensor; a failing tensor stops the enqueueing of
- *   later tensors (earlier ones still run) and its message is returned.
+ *   streams  0 = the grouped engine when every request is FP32 or FP64 data with truncation
+ *            (opts->truncate): each tensor's launch sequence is recorded on the host and the same
+ *            stage of all tensors runs as one launch (about 30 launches per mode for the whole
+ *            batch; the per-tensor argument tables are copied into the workspace by stream-ordered
+ *            kernels that carry them in their parameters).  Otherwise, and for streams >= 1, that
+ *            many internal streams (0 = min(8, count), at most 32): the caller's stream is forked
+ *            into them with an event, tensors are placed largest first (by element count) on the
+ *            least-loaded stream, and every stream is joined back into ``stream`` before the call
+ *            returns.  Either way no host synchronisation, so the call is CUDA-graph capturable.
+ *   workspace  grouped engine: one slice per tensor (its rsthosvd_workspace_size rounded to 256 B)
+ *            and the launch tables; streams: one slice per internal stream, each the largest
+ *            rsthosvd_workspace_size of the batch.  rsthosvd_batched_workspace_size returns the
+ *            total for the engine that ``streams`` selects (0 on an invalid request).  Neither
+ *            engine's result depends on timing: each tensor's result equals, bit for bit, that of a
+ *            single rsthosvd call.
+ *   Errors: RH_EINVAL names the first invalid tensor; on the stream engine a failing tensor stops
+ *   the enqueueing of later tensors (earlier ones still run); the grouped engine validates every
+ *   tensor before it launches anything.
  */
 size_t rsthosvd_batched_workspace_size(int32_t count, const int32_t* orders, const int64_t* dims, int32_t dtype,
                                        const int32_t* ranks, const rh_options* opts, int32_t streams);
@@ -311,6 +319,27 @@ rh_status rsthosvd_batched(int32_t count, const int32_t* orders, const int64_t* 
                            const void* const* X, const int32_t* ranks, const rh_options* opts,
                            double* const* factors, double* const* cores, double* norms, int32_t* info,
                            int32_t streams, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Batched plan -- the grouped engine of rsthosvd_batched for a fixed set of requests, buffers and
+ * workspace, recorded once and run many times.  create takes the arguments of rsthosvd_batched
+ * (workspace of rsthosvd_batched_workspace_size(..., streams = 0) bytes, of which the plan uses the
+ * per-tensor slices), records every tensor's program, and copies the launch tables into device
+ * memory the plan owns (one synchronous copy).  run enqueues the grouped launches on ``stream``
+ * (no host synchronisation; capturable); every run recomputes all outputs from the current
+ * contents of X.  The buffers named at create must stay valid while the plan is used.  destroy
+ * frees the tables (it synchronises the device through cudaFree).  RH_EUNSUPPORTED when a request
+ * is not FP32 / FP64 with truncation.
+ */
+typedef struct rh_batched_plan_s* rh_batched_plan;
+rh_status rsthosvd_batched_plan_create(int32_t count, const int32_t* orders, const int64_t* dims, int32_t dtype,
+                                      const void* const* X, const int32_t* ranks, const rh_options* opts,
+                                      double* const* factors, double* const* cores, double* norms, int32_t* info,
+                                      void* workspace, size_t workspace_bytes, rh_batched_plan* plan);
+rh_status rsthosvd_batched_plan_run(rh_batched_plan plan, void* stream);
+/* number of grouped launches one run enqueues (-1 for a NULL plan) */
+int64_t rsthosvd_batched_plan_launches(rh_batched_plan plan);
+void rsthosvd_batched_plan_destroy(rh_batched_plan plan);
 
 /*
  * rhosvd -- R-HOSVD (Alg. 2): RandSVD (Alg. 1) of every unfolding X_(n) of the input with its own

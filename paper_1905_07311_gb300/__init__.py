@@ -492,7 +492,7 @@ class RsthosvdBatchedCall:
     returns one Tucker per tensor (views of buffers allocated once here)."""
 
     def __init__(self, dims_list, ranks_list, dtype, p=5, seed=0, tensor_id=0, clamp=False, truncate=True,
-                 streams=0, device="cuda"):
+                 streams=0, device="cuda", svd_route=0):
         torch = _torch()
         if len(dims_list) != len(ranks_list) or not dims_list:
             raise ValueError("dims_list and ranks_list must be non-empty and of equal length")
@@ -504,7 +504,8 @@ class RsthosvdBatchedCall:
                 raise ValueError("batched calls take float32/float64 or the f32_bf16x2 and bf16 forms")
         else:
             self.dt = RH_F64 if dtype == torch.float64 else RH_F32
-        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, clamp=clamp, truncate=truncate)
+        self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
+                                 svd_route=svd_route)
         self.orders = i32_array([len(d) for d in self.dims_list])
         self.da = i64_array([x for d in self.dims_list for x in d])
         self.ra = i32_array([int(r) for rk in ranks_list for r in rk])
@@ -546,6 +547,9 @@ class RsthosvdBatchedCall:
         check(lib().rsthosvd_batched(self.count, self.orders, self.da, self.dt, xptrs, self.ra, ctypes.byref(self.opts),
                                      self.fptrs, self.cptrs, _ptr(self.norms) if norms else None, _ptr(self.info),
                                      self.streams, _ptr(self.ws), self.ws_bytes, _stream(self.device)))
+        return self._results()
+
+    def _results(self):
         out, off = [], 0
         for i, dims in enumerate(self.dims_list):
             d = len(dims)
@@ -554,13 +558,55 @@ class RsthosvdBatchedCall:
             off += d
         return out
 
+    def plan(self, Xs, norms=True):
+        """A recorded grouped run over these tensors (``rsthosvd_batched_plan_*``): ``plan.run()``
+        enqueues it on the current stream and returns the Tucker results (the call's buffers)."""
+        return BatchedPlan(self, Xs, norms)
+
+
+class BatchedPlan:
+    """``rsthosvd_batched_plan``: the grouped engine recorded once for fixed tensors and outputs."""
+
+    def __init__(self, call, Xs, norms=True):
+        if len(Xs) != call.count:
+            raise ValueError(f"expected {call.count} tensors, got {len(Xs)}")
+        for X, dims in zip(Xs, call.dims_list):
+            _check_input(X, dims, 1)
+        self.call = call
+        self.Xs = list(Xs)   # the plan reads these buffers on every run
+        xptrs = (ctypes.c_void_p * call.count)(*[X.data_ptr() for X in Xs])
+        h = ctypes.c_void_p()
+        check(lib().rsthosvd_batched_plan_create(call.count, call.orders, call.da, call.dt, xptrs, call.ra,
+                                                 ctypes.byref(call.opts), call.fptrs, call.cptrs,
+                                                 _ptr(call.norms) if norms else None, _ptr(call.info), _ptr(call.ws),
+                                                 call.ws_bytes, ctypes.byref(h)))
+        self.h = h
+        self.launches = int(lib().rsthosvd_batched_plan_launches(h))
+
+    def run(self):
+        check(lib().rsthosvd_batched_plan_run(self.h, _stream(self.call.device)))
+        return self.call._results()
+
+    def close(self):
+        if self.h:
+            lib().rsthosvd_batched_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 def rsthosvd_batched(Xs, dims_list, ranks_list, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, form=None,
-                     streams=0):
+                     streams=0, svd_route=0):
     """R-STHOSVD (Alg. 3) of every tensor in ``Xs`` (flat column-major, sizes ``dims_list[i]``) in
-    one batched call; returns a list of Tucker results."""
+    one batched call; returns a list of Tucker results.  ``streams=0`` runs FP32 / FP64 truncated
+    requests on the grouped engine (one launch per stage for the whole batch)."""
     call = RsthosvdBatchedCall(dims_list, ranks_list, form or Xs[0].dtype, p=p, seed=seed, tensor_id=tensor_id,
-                               clamp=clamp, truncate=truncate, streams=streams, device=Xs[0].device)
+                               clamp=clamp, truncate=truncate, streams=streams, device=Xs[0].device,
+                               svd_route=svd_route)
     return call.run(Xs)
 
 

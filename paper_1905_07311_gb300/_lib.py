@@ -76,6 +76,11 @@ SIGNATURES = {
     "rsthosvd_batched_workspace_size": (_SZ, [_I32, _P, _P, _I32, _P, ctypes.POINTER(RhOptions), _I32]),
     "rsthosvd_batched": (_I32, [_I32, _P, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _I32, _P,
                                 _SZ, _P]),
+    "rsthosvd_batched_plan_create": (_I32, [_I32, _P, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P,
+                                            _P, _SZ, ctypes.POINTER(_P)]),
+    "rsthosvd_batched_plan_run": (_I32, [_P, _P]),
+    "rsthosvd_batched_plan_launches": (_I64, [_P]),
+    "rsthosvd_batched_plan_destroy": (None, [_P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
     "rsthosvd_host": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _SZ, _P]),
 }

@@ -192,4 +192,122 @@ inline Fp8Layout fp8_layout(int order, const int64_t* dims) {
   return f;
 }
 
+
+// ---- launches: direct, or recorded for a grouped launch ---------------------------------------
+// A kernel that can run grouped is an Op: a plain argument struct Args, a device body(Grid, Args)
+// written against the block coordinates in Grid (not blockIdx / gridDim), and its block size
+// kThreads (and kMinBlocks for the launch bounds).  single_kernel<Op> is the ordinary launch (the
+// hardware grid); group_kernel<Op> runs the same body for many independent problems in one launch:
+// the blocks of problem t are [start[t], start[t+1]), read as t's own gx x gy grid (x fastest),
+// and get t's Args, so each problem computes exactly what its own launch would.
+struct Grid {
+  uint32_t bx, by, gx, gy;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ Grid hw_grid() { return Grid{blockIdx.x, blockIdx.y, gridDim.x, gridDim.y}; }
+
+// The problem whose block range holds this block: the t with start[t] <= blockIdx.x < start[t+1]
+// (start[0] = 0 and start[n] = the launch's block count, so empty ranges are never chosen).
+__device__ __forceinline__ int group_find(const int32_t* __restrict__ start, int n) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(start + mid) <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks) single_kernel(const typename Op::Args a) {
+  Op::body(hw_grid(), a);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks)
+    group_kernel(const typename Op::Args* __restrict__ args, const int32_t* __restrict__ start,
+                 const uint2* __restrict__ gdim, int n) {
+  const int t = group_find(start, n);
+  const uint2 d = gdim[t];
+  const uint32_t lb = blockIdx.x - (uint32_t)start[t];
+  const typename Op::Args a = args[t];
+  Op::body(Grid{lb % d.x, lb / d.x, d.x, d.y}, a);
+}
+#endif
+
+struct KernelRef {
+  const void* single;   // single_kernel<Op>
+  const void* group;    // group_kernel<Op>
+  uint32_t args_bytes;
+  int threads;
+  size_t smem_single = 0, smem_group = 0;   // dynamic shared memory opted in so far (host)
+};
+
+#ifdef __CUDACC__
+template <class Op>
+KernelRef* kref() {
+  static KernelRef r{reinterpret_cast<const void*>(&single_kernel<Op>), reinterpret_cast<const void*>(&group_kernel<Op>),
+                     (uint32_t)sizeof(typename Op::Args), Op::kThreads};
+  return &r;
+}
+#endif
+
+// Launch sites of the per-tensor R-STHOSVD program, numbered in the order one step runs them.  A
+// recorded program must visit (step, site, sub) in increasing order; launches of different
+// problems with the same key and kernel become one grouped launch (grouped.cu).
+enum LaunchSite : int {
+  SITE_ENTRY = 0,
+  SITE_SKETCH = 10,
+  SITE_SKETCH_REDUCE,
+  SITE_ORTH_ZERO = 20,
+  SITE_ORTH_GRAM,
+  SITE_ORTH_GRAM_REDUCE,
+  SITE_ORTH_CHOL,
+  SITE_ORTH_TRSM,
+  SITE_ORTH_CAST,
+  SITE_ORTH_GRAM2,
+  SITE_ORTH_GRAM2_REDUCE,
+  SITE_ORTH_CHOL2,
+  SITE_ORTH_TRSM2,
+  SITE_ORTH_CAST2,
+  SITE_ORTH_HOUSEHOLDER,
+  SITE_ORTH_SIGN,
+  SITE_CAST_Q = 40,
+  SITE_MODE_PRODUCT = 45,
+  SITE_TRUNC_ZERO = 50,
+  SITE_TRUNC_GRAM,
+  SITE_TRUNC_GRAM_REDUCE,
+  SITE_TRUNC_PCHOL,
+  SITE_TRUNC_JACOBI,
+  SITE_TRUNC_DECIDE,
+  SITE_TRUNC_GRAM_DF,
+  SITE_TRUNC_GRAM_DF_REDUCE,
+  SITE_TRUNC_PCHOL2,
+  SITE_TRUNC_JACOBI2,
+  SITE_TRUNC_TSQR,          // sub = level of the reduction tree
+  SITE_TRUNC_JACOBI_SVD,
+  SITE_FACTOR = 70,
+  SITE_FACTOR_SIGN,
+  SITE_CORE = 80,
+  SITE_FINAL = 90,
+  SITE_OTHER = 1000         // launches of entry points that never run grouped
+};
+
+// Direct launch (the caller's stream), or, while this thread records a tape, an entry of it.
+rh_status emit_raw(KernelRef* k, int site, int sub, dim3 grid, size_t smem, cudaStream_t st, const void* args);
+#ifdef __CUDACC__
+template <class Op>
+rh_status emit(int site, int sub, dim3 grid, size_t smem, cudaStream_t st, const typename Op::Args& a) {
+  return emit_raw(kref<Op>(), site, sub, grid, smem, st, &a);
+}
+#endif
+// Zero fill of bytes at p (cudaMemsetAsync, or a recorded fill).
+rh_status emit_memset(int site, int sub, void* p, size_t bytes, cudaStream_t st);
+bool recording();
+void record_step(int step);
+
 }  // namespace rh

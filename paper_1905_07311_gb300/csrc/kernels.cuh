@@ -8,9 +8,10 @@ namespace rh {
 // ---- sketch Y = G_(n) Omega_n  (sketch.cu) -----------------------------------------
 struct SketchPlan {
   ModeView v;
-  int ell, ellp;
+  int ell, ellp;      // ellp: Omega columns computed (padded ell)
   int gx, S;
   int64_t chunk;
+  int ti = 0;         // small-row kernel (I <= 128, ell <= 32): rows per CTA; 0 = the general kernel
   size_t part_elems() const { return (size_t)S * ell * v.I; }
   size_t norm_elems() const { return (size_t)S * gx; }
 };
@@ -63,7 +64,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
 // ---- mode-n product B = G x_n Q^T  (ttm.cu) ------------------------------------------
 // B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.
 template <typename T, typename TO>
-rh_status launch_ttm(const ModeView& v, const T* G, const T* Q, int ko, TO* B, cudaStream_t st);
+rh_status launch_ttm(const ModeView& v, const T* G, const T* Q, int ko, TO* B, cudaStream_t st, int site = SITE_OTHER);
 // general factor layout: Q(i, c) = Q[i qsi + c qsc]; any ko >= 1
 template <typename T, typename TO>
 rh_status launch_ttm_strided(const ModeView& v, const T* G, const T* Q, int64_t qsi, int64_t qsc, int ko, TO* B,

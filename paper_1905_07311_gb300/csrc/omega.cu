@@ -4,6 +4,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "grouped.cuh"
 #include "philox.cuh"
 
 namespace rh {
@@ -14,7 +15,10 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 void clear_error() { g_last_error.clear(); }
 
 static std::atomic<uint64_t> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  note_direct_launch();
+}
 
 // out[i + nrows * c] = Omega(row0 + i, c); one thread per (row, group of 4 columns).
 __global__ void omega_kernel(uint32_t k0, uint32_t k1, uint32_t sid, int64_t row0, int64_t nrows, int ell,

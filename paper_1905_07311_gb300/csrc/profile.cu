@@ -37,7 +37,7 @@ bool profiling() {
 
 ProfileScope::ProfileScope(int kind, int tag, cudaStream_t st) : st_(st) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_on) return;
+  if (!g_on || recording()) return;   // a recorded program is timed as a whole
   Rec r{kind, tag, get_event(), get_event()};
   if (!r.a || !r.b) return;
   if (cudaEventRecord(r.a, st) != cudaSuccess) return;

@@ -333,6 +333,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
   const uint16_t* piece1 = (pl.in_form == RH_BF16X2) ? piece0 + pl.steps[0].v.I * pl.steps[0].v.M() : nullptr;
   if (tc0) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
   for (int j = 0; j < nsteps; ++j) {
+    record_step(j);
     const Step& sp = pl.steps[j];
     const bool last = (j == nsteps - 1);
     const bool tc = tc0 && sp.tc;
@@ -405,9 +406,12 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     } else {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
-        if ((s = launch_ttm<T, double>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, core, st)) != RH_OK) return s;
+        if ((s = launch_ttm<T, double>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, core, st, SITE_MODE_PRODUCT)) !=
+            RH_OK)
+          return s;
       } else {
-        if ((s = launch_ttm<T, T>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) return s;
+        if ((s = launch_ttm<T, T>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, B, st, SITE_MODE_PRODUCT)) != RH_OK)
+          return s;
       }
     }
     if (o.truncate) {
@@ -443,10 +447,12 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
           cur_buf = wg;
         }
       } else if (last) {
-        if ((s = launch_ttm<T, double>(vb, B, static_cast<const T*>(b.Uc), sp.ko, core, st)) != RH_OK) return s;
+        if ((s = launch_ttm<T, double>(vb, B, static_cast<const T*>(b.Uc), sp.ko, core, st, SITE_CORE)) != RH_OK)
+          return s;
       } else {
         const int wg = 1 - wb;
-        if ((s = launch_ttm<T, T>(vb, B, static_cast<const T*>(b.Uc), sp.ko, static_cast<T*>(b.W[wg]), st)) != RH_OK)
+        if ((s = launch_ttm<T, T>(vb, B, static_cast<const T*>(b.Uc), sp.ko, static_cast<T*>(b.W[wg]), st, SITE_CORE)) !=
+            RH_OK)
           return s;
         cur = static_cast<const T*>(b.W[wg]);
         cur_buf = wg;
@@ -460,6 +466,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     }
   }
   if (norms) {
+    record_step(nsteps);
     int64_t ncore = 1;
     // final core sizes
     std::vector<int64_t> dims_out(pl.d, 0);
@@ -797,6 +804,22 @@ size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype
   return ar.used;
 }
 
+}  // extern "C"
+
+namespace rh {
+// A request whose whole R-STHOSVD program goes through emit (FP32 or FP64 data on the CUDA cores,
+// truncated), so that it can be recorded for a grouped launch.
+bool rsthosvd_groupable(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
+                        const rh_options* opts) {
+  const rh_options o = opts_or_default(opts);
+  Plan pl;
+  if (make_plan(order, dims, dtype, ranks, o, pl) != RH_OK) return false;
+  return (dtype == RH_F32 || dtype == RH_F64) && pl.in_form < 0 && o.truncate;
+}
+}  // namespace rh
+
+extern "C" {
+
 rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* X, const int32_t* ranks,
                    const rh_options* opts, double* const* factors, double* core, double* norms, int32_t* info,
                    void* workspace, size_t workspace_bytes, void* stream) {
@@ -816,7 +839,8 @@ rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void
   Arena ar(workspace);
   const Bufs b = carve(ar, pl);
   cudaStream_t st = (cudaStream_t)stream;
-  if (info) RH_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * order, st));
+  record_step(-1);
+  if (info && (s = emit_memset(SITE_ENTRY, 0, info, sizeof(int32_t) * order, st)) != RH_OK) return s;
   if (pl.dtype == RH_F64) return run_rsthosvd<double>(pl, X, o, factors, core, norms, info, b, st);
   return run_rsthosvd<float>(pl, X, o, factors, core, norms, info, b, st);
 }

@@ -46,10 +46,33 @@ __device__ __forceinline__ int swz(int k, int col) {
   return col ^ ((k & 7) * Vec<T>::n);
 }
 
+template <typename T>
+struct SketchArgs {
+  const T* G;
+  int64_t L, I, R;
+  int ell;
+  int64_t chunk;
+  uint32_t k0, k1, sid;
+  T* part;
+  double* part_norm;
+};
+
 template <typename T, int ELLP, bool KCONTIG>
-__global__ void __launch_bounds__(kNT, 2)
-    sketch_kernel(const T* __restrict__ G, int64_t L, int64_t I, int64_t R, int ell, int64_t chunk, uint32_t k0,
-                  uint32_t k1, uint32_t sid, T* __restrict__ part, double* __restrict__ part_norm) {
+struct SketchOp {
+  using Args = SketchArgs<T>;
+  static constexpr int kThreads = kNT, kMinBlocks = 2;
+  __device__ static void body(const Grid g, const Args& args);
+};
+
+template <typename T, int ELLP, bool KCONTIG>
+__device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, const Args& args) {
+  const T* __restrict__ G = args.G;
+  const int64_t L = args.L, I = args.I, R = args.R;
+  const int ell = args.ell;
+  const int64_t chunk = args.chunk;
+  const uint32_t k0 = args.k0, k1 = args.k1, sid = args.sid;
+  T* __restrict__ part = args.part;
+  double* __restrict__ part_norm = args.part_norm;
   constexpr int CG = ELLP / 4;      // groups of 4 Omega columns
   constexpr int IG = kNT / CG;      // groups of rows
   constexpr int TM = kTI / IG;      // rows per thread
@@ -65,9 +88,9 @@ __global__ void __launch_bounds__(kNT, 2)
   const int tid = threadIdx.x;
   const int tc = tid % CG;
   const int ti = tid / CG;
-  const int64_t i0 = (int64_t)blockIdx.x * kTI;
+  const int64_t i0 = (int64_t)g.bx * kTI;
   const int64_t M = L * R;
-  const int64_t pb = (int64_t)blockIdx.y * chunk;
+  const int64_t pb = (int64_t)g.by * chunk;
   const int64_t pe = min(M, pb + chunk);
 
   T acc[TM][4];
@@ -165,7 +188,7 @@ __global__ void __launch_bounds__(kNT, 2)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int c = 4 * tc + b;
-      if (c < ell) part[((int64_t)blockIdx.y * ell + c) * I + i] = acc2[a][b] + acc[a][b];
+      if (c < ell) part[((int64_t)g.by * ell + c) * I + i] = acc2[a][b] + acc[a][b];
     }
   }
   // -- partial ||G||^2 of the elements this CTA loaded
@@ -176,7 +199,210 @@ __global__ void __launch_bounds__(kNT, 2)
   if (tid == 0) {
     double s = 0.0;
     for (int k = 0; k < kNT / 32; ++k) s += red[k];
-    part_norm[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    part_norm[(int64_t)g.by * g.gx + g.bx] = s;
+  }
+}
+
+// Small-row sketch (I <= 128, ell <= 32): the CTA keeps every row of its columns (TI >= I rows,
+// TI in {32, 64, 128}), so each Omega row is generated once, and only the ceil(ell / 4) quads of
+// it that are used.  A k-step covers KP = NTE / TI columns -- a tile of NTE elements (4096 FP32,
+// 2048 FP64: 16 KB) whatever I is -- and the next tile is loaded into registers while the current
+// one is multiplied.  The 256 threads are KS slices x TI/4 row groups x E/4 column groups; slice
+// ks sums the columns kk = ks, ks + KS, ... of each tile and the slices are added at the end in a
+// fixed order, so the result is deterministic.
+template <typename T>
+struct SketchSmallArgs {
+  const T* G;
+  int64_t L, I, R;
+  int ell;
+  int64_t chunk;
+  uint32_t k0, k1, sid;
+  T* part;
+  double* part_norm;
+  FastDiv fI, fL;   // division by I (unit-stride view) and by L (strided view)
+};
+
+template <typename T>
+struct SmallTile {
+  static constexpr int NTE = sizeof(T) == 4 ? 4096 : 2048;   // tile elements (16 KB)
+};
+
+template <typename T, int TI, int E, bool KC>
+struct SketchSmallOp {
+  using Args = SketchSmallArgs<T>;
+  static constexpr int kThreads = 256, kMinBlocks = 2;
+  static constexpr int NTE = SmallTile<T>::NTE;
+  static constexpr int KP = NTE / TI;              // columns per k-step
+  static constexpr int IG = TI / 4, CG = E / 4;    // groups of 4 rows, of 4 columns
+  static constexpr int KS = 256 / (IG * CG);       // column slices
+  static constexpr int PER = NTE / 256;            // tile elements each thread loads
+  static_assert(KS >= 1 && IG * CG * KS == 256, "thread split");
+  static_assert(KP % 8 == 0 && KP % KS == 0, "tile shape");
+  __device__ static void body(const Grid g, const Args& args);
+};
+
+template <typename T, int TI, int E, bool KC>
+__device__ __forceinline__ void SketchSmallOp<T, TI, E, KC>::body(const Grid g, const Args& args) {
+  using Op = SketchSmallOp<T, TI, E, KC>;
+  constexpr int KP = Op::KP, CG = Op::CG, IG = Op::IG, KS = Op::KS, PER = Op::PER;
+  constexpr int VN = Vec<T>::n;
+  using V = typename Vec<T>::type;
+  constexpr int TERMS = KP / KS;                   // products per accumulator per k-step
+  constexpr int FLUSH = TERMS >= 512 ? 1 : 512 / TERMS;
+  union Smem {
+    struct {
+      T Xs[KP][TI];
+      float Os[KP][E];
+    } t;
+    T red[4096];
+  };
+  __shared__ __align__(16) Smem sm;
+  __shared__ double nred[8];
+
+  const T* __restrict__ G = args.G;
+  const int64_t L = args.L, I = args.I, R = args.R;
+  const int ell = args.ell;
+  const int64_t M = L * R;
+  const int64_t pb = (int64_t)g.by * args.chunk;
+  const int64_t pe = min(M, pb + args.chunk);
+  const int tid = threadIdx.x;
+  const int cg = tid % CG, ig = (tid / CG) % IG, ks = tid / (CG * IG);
+  const int nq = (ell + 3) / 4;
+  const int Ii = (int)I;
+
+  // -- loads of one tile into registers.  Unit-stride view: the tile is the contiguous run
+  // G[I p0, I (p0 + KP)), element e at (kp, ii) = (e / I, e % I).  Strided view: each warp covers
+  // 8 consecutive columns x 4 rows (32-byte runs), so a thread keeps one or two columns.
+  T xr[PER];
+  auto load_tile = [&](int64_t p0) {
+    if (KC) {
+      const int64_t lim = (min(pe, p0 + KP) - p0) * I;
+      const T* src = G + I * p0;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int e = tid + 256 * j;
+        xr[j] = (e < lim) ? __ldg(src + e) : T(0);
+      }
+    } else {
+      const int lane = tid & 31;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int w = (tid >> 5) + 8 * j;
+        const int kp = (lane & 7) + 8 * (w % (KP / 8));
+        const int ii = (lane >> 3) + 4 * (w / (KP / 8));
+        const int64_t p = p0 + kp;
+        T x = T(0);
+        if (p < pe && ii < Ii) {
+          const uint32_t q = args.fL.div((uint32_t)p);
+          x = __ldg(G + ((int64_t)((uint32_t)p - q * (uint32_t)L) + L * I * (int64_t)q + L * (int64_t)ii));
+        }
+        xr[j] = x;
+      }
+    }
+  };
+  auto store_tile = [&]() {
+    T ss = T(0);
+    if (KC) {
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int e = tid + 256 * j;
+        if (e < KP * Ii) {
+          const int kp = (int)args.fI.div((uint32_t)e), ii = e - kp * Ii;
+          sm.t.Xs[kp][swz<T>(kp, ii)] = xr[j];
+        }
+        ss += xr[j] * xr[j];
+      }
+      // rows ii in [I, TI) of the tile stay zero (written once before the loop)
+    } else {
+      const int lane = tid & 31;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int w = (tid >> 5) + 8 * j;
+        const int kp = (lane & 7) + 8 * (w % (KP / 8));
+        const int ii = (lane >> 3) + 4 * (w / (KP / 8));
+        sm.t.Xs[kp][swz<T>(kp, ii)] = xr[j];
+        ss += xr[j] * xr[j];
+      }
+    }
+    return ss;
+  };
+
+  if (KC) {
+    for (int e = tid; e < KP * TI; e += 256) (&sm.t.Xs[0][0])[e] = T(0);
+    __syncthreads();
+  }
+  T acc[4][4], acc2[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = acc2[a][b] = T(0);
+  double nrm = 0.0;
+  if (pb < pe) load_tile(pb);
+  int step = 0;
+  for (int64_t p0 = pb; p0 < pe; p0 += KP, ++step) {
+    nrm += (double)store_tile();
+    // Omega tile: quads q < nq of columns p0 .. p0 + KP - 1; the padded quads are zero
+    for (int t = tid; t < KP * CG; t += 256) {
+      const int kp = t / CG, q = t % CG;
+      const int64_t p = p0 + kp;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < pe && q < nq) v = rng::omega4(args.k0, args.k1, args.sid, p, (uint32_t)q);
+      *reinterpret_cast<float4*>(&sm.t.Os[kp][4 * q]) = v;
+    }
+    __syncthreads();
+    if (p0 + KP < pe) load_tile(p0 + KP);   // in flight during the products below
+#pragma unroll 4
+    for (int kk = ks; kk < KP; kk += KS) {
+      T xv[4];
+#pragma unroll
+      for (int a = 0; a < 4; a += VN) {
+        const V v = *reinterpret_cast<const V*>(&sm.t.Xs[kk][swz<T>(kk, 4 * ig + a)]);
+        if constexpr (VN == 4) {
+          xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
+        } else {
+          xv[a] = v.x; xv[a + 1] = v.y;
+        }
+      }
+      const float4 o = *reinterpret_cast<const float4*>(&sm.t.Os[kk][4 * cg]);
+      const T ov[4] = {T(o.x), T(o.y), T(o.z), T(o.w)};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xv[a], ov[b], acc[a][b]);
+    }
+    if (sizeof(T) == 4 && (step % FLUSH) == FLUSH - 1) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc2[a][b] += acc[a][b];
+          acc[a][b] = T(0);
+        }
+    }
+    __syncthreads();
+  }
+  // -- slices: red[ks][c][i], summed over ks in order; then part[by][c][i]
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sm.red[(ks * E + 4 * cg + b) * TI + 4 * ig + a] = acc2[a][b] + acc[a][b];
+  __syncthreads();
+  for (int t = tid; t < TI * E; t += 256) {
+    const int i = t % TI, c = t / TI;
+    T v = sm.red[c * TI + i];
+#pragma unroll
+    for (int k = 1; k < KS; ++k) v += sm.red[(k * E + c) * TI + i];
+    if (i < Ii && c < ell) args.part[((int64_t)g.by * ell + c) * I + i] = v;
+  }
+  // -- partial ||G||^2 of the elements this CTA loaded
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((tid & 31) == 0) nred[tid >> 5] = nrm;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += nred[k];
+    args.part_norm[(int64_t)g.by * g.gx + g.bx] = t;
   }
 }
 
@@ -188,14 +414,38 @@ __global__ void __launch_bounds__(kNT, 2)
 constexpr int kRedWarps = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kRedWarps) sketch_reduce_kernel(const T* __restrict__ part, int S, int64_t I,
-                                                                        int ell, double* __restrict__ Y,
-                                                                        const double* __restrict__ part_norm,
-                                                                        int nnorm, double* __restrict__ norm2) {
+struct SketchReduceArgs {
+  const T* part;
+  int S;
+  int64_t I;
+  int ell;
+  double* Y;
+  const double* part_norm;
+  int nnorm;
+  double* norm2;
+};
+
+template <typename T>
+struct SketchReduceOp {
+  using Args = SketchReduceArgs<T>;
+  static constexpr int kThreads = 32 * kRedWarps, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+
+template <typename T>
+__device__ __forceinline__ void SketchReduceOp<T>::body(const Grid g, const Args& args) {
+  const T* __restrict__ part = args.part;
+  const int S = args.S;
+  const int64_t I = args.I;
+  const int ell = args.ell;
+  double* __restrict__ Y = args.Y;
+  const double* __restrict__ part_norm = args.part_norm;
+  const int nnorm = args.nnorm;
+  double* __restrict__ norm2 = args.norm2;
   __shared__ double red[kRedWarps][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t c = blockIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t c = g.by;
+  const int64_t i = (int64_t)g.bx * 32 + lane;
   double s = 0.0;
   if (i < I) {
     const T* src = part + c * I + i;
@@ -218,7 +468,7 @@ __global__ void __launch_bounds__(32 * kRedWarps) sketch_reduce_kernel(const T* 
     for (int j = 1; j < kRedWarps; ++j) t += red[j][lane];
     Y[i + I * c] = t;
   }
-  if (norm2 != nullptr && blockIdx.x == 0 && blockIdx.y == 0) {
+  if (norm2 != nullptr && g.bx == 0 && g.by == 0) {
     __syncthreads();
     double t = 0.0;
     for (int k = threadIdx.x; k < nnorm; k += blockDim.x) t += part_norm[k];
@@ -239,9 +489,21 @@ SketchPlan plan_sketch(const ModeView& v, int ell) {
   SketchPlan pl;
   pl.v = v;
   pl.ell = ell;
+  const int64_t M = v.M();
+  if (v.I <= 128 && ell <= 32 && M < (int64_t(1) << 31)) {
+    // small-row kernel: one row tile; at least 8 k-steps per CTA, about 6 CTAs per SM at most
+    pl.ti = v.I <= 32 ? 32 : (v.I <= 64 ? 64 : 128);
+    pl.ellp = ell <= 8 ? 8 : (ell <= 16 ? 16 : 32);
+    pl.gx = 1;
+    const int64_t kp = 4096 / pl.ti;   // FP32 tile columns (a multiple of the FP64 ones)
+    const int64_t ksteps = ceil_div(M, kp);
+    const int64_t S = std::max<int64_t>(1, std::min<int64_t>(6LL * num_sms(), ceil_div(ksteps, 8)));
+    pl.chunk = ceil_div(ksteps, S) * kp;
+    pl.S = (int)ceil_div(M, pl.chunk);
+    return pl;
+  }
   pl.ellp = ell_pad_of(ell);
   pl.gx = (int)ceil_div(v.I, kTI);
-  const int64_t M = v.M();
   const int64_t ksteps = ceil_div(M, kKP);
   // about 4 CTAs per SM (the partial sums are reduced by warps over the splits, so many splits
   // stay cheap even for small I)
@@ -252,23 +514,39 @@ SketchPlan plan_sketch(const ModeView& v, int ell) {
   return pl;
 }
 
+template <typename T, int TI, int E>
+static rh_status emit_sketch_small(const SketchPlan& pl, const SketchSmallArgs<T>& a, cudaStream_t st) {
+  const dim3 grid(1, pl.S);
+  return pl.v.L == 1 ? emit<SketchSmallOp<T, TI, E, true>>(SITE_SKETCH, 0, grid, 0, st, a)
+                     : emit<SketchSmallOp<T, TI, E, false>>(SITE_SKETCH, 0, grid, 0, st, a);
+}
+
+template <typename T, int TI>
+static rh_status emit_sketch_small_e(const SketchPlan& pl, const SketchSmallArgs<T>& a, cudaStream_t st) {
+  if (pl.ellp == 8) return emit_sketch_small<T, TI, 8>(pl, a, st);
+  if (pl.ellp == 16) return emit_sketch_small<T, TI, 16>(pl, a, st);
+  return emit_sketch_small<T, TI, 32>(pl, a, st);
+}
+
 template <typename T>
 rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_t sid, T* part, double* part_norm,
                         cudaStream_t st) {
-  const dim3 grid(pl.gx, pl.S);
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
-  const bool kc = (pl.v.L == 1);
-#define RH_SK(E, KC)                                                                                     \
-  sketch_kernel<T, E, KC><<<grid, kNT, 0, st>>>(G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, \
-                                                part_norm)
-  if (pl.ellp == 32) {
-    if (kc) RH_SK(32, true); else RH_SK(32, false);
-  } else {
-    if (kc) RH_SK(64, true); else RH_SK(64, false);
+  if (pl.ti > 0) {
+    const SketchSmallArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm,
+                               FastDiv((uint32_t)pl.v.I), FastDiv((uint32_t)pl.v.L)};
+    if (pl.ti == 32) return emit_sketch_small_e<T, 32>(pl, a, st);
+    if (pl.ti == 64) return emit_sketch_small_e<T, 64>(pl, a, st);
+    return emit_sketch_small_e<T, 128>(pl, a, st);
   }
-#undef RH_SK
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  const dim3 grid(pl.gx, pl.S);
+  const bool kc = (pl.v.L == 1);
+  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm};
+  if (pl.ellp == 32)
+    return kc ? emit<SketchOp<T, 32, true>>(SITE_SKETCH, 0, grid, 0, st, a)
+              : emit<SketchOp<T, 32, false>>(SITE_SKETCH, 0, grid, 0, st, a);
+  return kc ? emit<SketchOp<T, 64, true>>(SITE_SKETCH, 0, grid, 0, st, a)
+            : emit<SketchOp<T, 64, false>>(SITE_SKETCH, 0, grid, 0, st, a);
 }
 
 template <typename T>
@@ -279,10 +557,8 @@ rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double
     return RH_EUNSUPPORTED;
   }
   const dim3 grid((unsigned)ceil_div(pl.v.I, 32), (unsigned)pl.ell);
-  sketch_reduce_kernel<T><<<grid, 32 * kRedWarps, 0, st>>>(part, pl.S, pl.v.I, pl.ell, Y, part_norm,
-                                                           (int)pl.norm_elems(), norm2);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return emit<SketchReduceOp<T>>(SITE_SKETCH_REDUCE, 0, grid, 0, st,
+                                 SketchReduceArgs<T>{part, pl.S, pl.v.I, pl.ell, Y, part_norm, (int)pl.norm_elems(), norm2});
 }
 
 template rh_status launch_sketch<float>(const SketchPlan&, const float*, uint64_t, uint32_t, float*, double*,

@@ -20,6 +20,13 @@
 
 namespace rh {
 
+// One launch of an Op through emit (direct, or recorded for a grouped launch); returns on failure.
+#define RH_EMIT(OP, SITE, SUB, GRID, SMEM, ...)                                                 \
+  do {                                                                                        \
+    const rh_status rh_emit_s_ = emit<OP>(SITE, SUB, dim3(GRID), SMEM, st, typename OP::Args{__VA_ARGS__}); \
+    if (rh_emit_s_ != RH_OK) return rh_emit_s_;                                               \
+  } while (0)
+
 namespace {
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -54,11 +61,29 @@ __device__ T block_sum(T v, T* scratch /* >= 33 */) {
 // CholeskyQR2
 // ---------------------------------------------------------------------------------
 // Gpart[b] = A_b^T A_b over row block b (rows [b rb, b rb + rb)), upper triangle j <= k.
-__global__ void gram_partial_kernel(const double* __restrict__ A, int64_t m, int n, int rb,
-                                    double* __restrict__ Gpart, const int32_t* __restrict__ flag) {
+struct GramPartialOp {
+  struct Args {
+    const double* A;
+    int64_t m;
+    int n;
+    int rb;
+    double* Gpart;
+    const int32_t* flag;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void GramPartialOp::body(const Grid g, const Args& args) {
+  const double* __restrict__ A = args.A;
+  int64_t m = args.m;
+  int n = args.n;
+  int rb = args.rb;
+  double* __restrict__ Gpart = args.Gpart;
+  const int32_t* __restrict__ flag = args.flag;
+
   if (flag != nullptr && *flag) return;
   extern __shared__ double As[];  // rb x n, row-major
-  const int64_t r0 = (int64_t)blockIdx.x * rb;
+  const int64_t r0 = (int64_t)g.bx * rb;
   const int rows = (int)(m - r0 < rb ? m - r0 : rb);
   for (int t = threadIdx.x; t < rb * n; t += blockDim.x) {
     const int r = t % rb, c = t / rb;
@@ -74,15 +99,31 @@ __global__ void gram_partial_kernel(const double* __restrict__ A, int64_t m, int
     const int j = e - k * (k + 1) / 2;
     double s = 0.0;
     for (int r = 0; r < rows; ++r) s = fma(As[r * n + j], As[r * n + k], s);
-    Gpart[(int64_t)blockIdx.x * n * n + j + n * k] = s;
+    Gpart[(int64_t)g.bx * n * n + j + n * k] = s;
   }
 }
 
 // C = sum_b Gpart[b] (fixed order), upper triangle; one thread per entry.
-__global__ void gram_reduce_kernel(const double* __restrict__ Gpart, int nb, int n, double* __restrict__ C,
-                                   const int32_t* __restrict__ flag) {
+struct GramReduceOp {
+  struct Args {
+    const double* Gpart;
+    int nb;
+    int n;
+    double* C;
+    const int32_t* flag;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void GramReduceOp::body(const Grid g, const Args& args) {
+  const double* __restrict__ Gpart = args.Gpart;
+  int nb = args.nb;
+  int n = args.n;
+  double* __restrict__ C = args.C;
+  const int32_t* __restrict__ flag = args.flag;
+
   if (flag != nullptr && *flag) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = g.bx * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
   const int j = e % n, k = e / n;
   if (j > k) return;
@@ -182,9 +223,25 @@ size_t chol_smem(int n, size_t velem) {
 // pivot S_{k+1,k+1} first and prepares its 1 / sqrt; the other threads share the remaining
 // entries of the trailing triangle through the table (no idle predicated work).
 template <class Ar>
-__global__ void __launch_bounds__(kCholThreads) chol_kernel(const double* __restrict__ C, int n,
-                                                            double* __restrict__ R, double* __restrict__ rdiag,
-                                                            int32_t* __restrict__ flag) {
+struct CholOp {
+  struct Args {
+    const double* C;
+    int n;
+    double* R;
+    double* rdiag;
+    int32_t* flag;
+  };
+  static constexpr int kThreads = kCholThreads, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <class Ar>
+__device__ __forceinline__ void CholOp<Ar>::body(const Grid g, const Args& args) {
+  const double* __restrict__ C = args.C;
+  int n = args.n;
+  double* __restrict__ R = args.R;
+  double* __restrict__ rdiag = args.rdiag;
+  int32_t* __restrict__ flag = args.flag;
+
   if (*flag) return;
   using V = typename Ar::V;
   extern __shared__ __align__(16) unsigned char chol_raw[];
@@ -282,9 +339,29 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double* __rest
 // Out = A R^{-1} row by row (forward substitution on x^T R = a^T); one warp per row, the
 // diagonal applied through its precomputed reciprocals.
 template <typename T>
-__global__ void trsm_rows_kernel(const T* __restrict__ A, int64_t m, int n, const double* __restrict__ R,
-                                 const double* __restrict__ rdiag, T* __restrict__ Out,
-                                 const int32_t* __restrict__ flag) {
+struct TrsmRowsOp {
+  struct Args {
+    const T* A;
+    int64_t m;
+    int n;
+    const double* R;
+    const double* rdiag;
+    T* Out;
+    const int32_t* flag;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void TrsmRowsOp<T>::body(const Grid g, const Args& args) {
+  const T* __restrict__ A = args.A;
+  int64_t m = args.m;
+  int n = args.n;
+  const double* __restrict__ R = args.R;
+  const double* __restrict__ rdiag = args.rdiag;
+  T* __restrict__ Out = args.Out;
+  const int32_t* __restrict__ flag = args.flag;
+
   if (*flag) return;
   extern __shared__ __align__(16) unsigned char trsm_raw[];
   T* Rs = reinterpret_cast<T*>(trsm_raw);   // n x n column-major (odd leading dimension ld), then n reciprocals
@@ -294,8 +371,8 @@ __global__ void trsm_rows_kernel(const T* __restrict__ A, int64_t m, int n, cons
   for (int e = threadIdx.x; e < n; e += blockDim.x) rd[e] = (T)rdiag[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
+  const int64_t warps = (int64_t)g.gx * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)g.bx * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
     T y0 = lane < n ? A[row + m * lane] : T(0);
     T y1 = lane + 32 < n ? A[row + m * (lane + 32)] : T(0);
     for (int c = 0; c < n; ++c) {
@@ -313,9 +390,30 @@ __global__ void trsm_rows_kernel(const T* __restrict__ A, int64_t m, int n, cons
 
 // Householder QR of Y (m x n) with explicit thin Q, one CTA; runs only when *flag is set
 // (or always when flag == nullptr).  W is an m x n FP64 scratch copy; beta has n slots.
-__global__ void householder_q_kernel(const double* __restrict__ Y, int64_t m, int n, double* __restrict__ W,
-                                     double* __restrict__ beta, double* __restrict__ Q,
-                                     const int32_t* __restrict__ flag, int32_t* __restrict__ info) {
+struct HouseholderQOp {
+  struct Args {
+    const double* Y;
+    int64_t m;
+    int n;
+    double* W;
+    double* beta;
+    double* Q;
+    const int32_t* flag;
+    int32_t* info;
+  };
+  static constexpr int kThreads = 1024, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void HouseholderQOp::body(const Grid g, const Args& args) {
+  const double* __restrict__ Y = args.Y;
+  int64_t m = args.m;
+  int n = args.n;
+  double* __restrict__ W = args.W;
+  double* __restrict__ beta = args.beta;
+  double* __restrict__ Q = args.Q;
+  const int32_t* __restrict__ flag = args.flag;
+  int32_t* __restrict__ info = args.info;
+
   const bool run = (flag == nullptr) || (*flag != 0);
   if (info != nullptr && threadIdx.x == 0) *info = (*info & ~1) | (run ? 1 : 0);
   if (!run) return;
@@ -439,9 +537,31 @@ __device__ void smem_householder_r(T* A, int rows, int n, int ld, T* scratch, T*
 // Level 0: block b holds rows [b rows0, ...) of B^T, with B^T[p, c] = B[(p % L) + L n (p / L) + L c].
 // CTAs loop over the blocks (the grid is capped), so a launch whose gate is off costs little.
 template <typename T>
-__global__ void __launch_bounds__(1024) tsqr_leaf_kernel(const T* __restrict__ B, int64_t L, int64_t R, int n,
-                                                         int rows0, int ld, T* __restrict__ Rout,
-                                                         const int32_t* __restrict__ gate) {
+struct TsqrLeafOp {
+  struct Args {
+    const T* B;
+    int64_t L;
+    int64_t R;
+    int n;
+    int rows0;
+    int ld;
+    T* Rout;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = 1024, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void TsqrLeafOp<T>::body(const Grid g, const Args& args) {
+  const T* __restrict__ B = args.B;
+  int64_t L = args.L;
+  int64_t R = args.R;
+  int n = args.n;
+  int rows0 = args.rows0;
+  int ld = args.ld;
+  T* __restrict__ Rout = args.Rout;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
@@ -449,7 +569,7 @@ __global__ void __launch_bounds__(1024) tsqr_leaf_kernel(const T* __restrict__ B
   __shared__ T scratch[33];
   const int64_t M = L * R;
   const int64_t nblk = (M + rows0 - 1) / rows0;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+  for (int64_t blk = g.bx; blk < nblk; blk += g.gx) {
     const int64_t p0 = blk * rows0;
     const int rows = (int)(M - p0 < rows0 ? M - p0 : rows0);
     __syncthreads();
@@ -483,15 +603,36 @@ __global__ void __launch_bounds__(1024) tsqr_leaf_kernel(const T* __restrict__ B
 
 // Higher level: block b stacks R's [b fan, b fan + fan) (each n x n) and re-triangularises.
 template <typename T>
-__global__ void __launch_bounds__(1024) tsqr_merge_kernel(const T* __restrict__ Rin, int64_t nin, int n, int fan,
-                                                          int ld, T* __restrict__ Rout, const int32_t* __restrict__ gate) {
+struct TsqrMergeOp {
+  struct Args {
+    const T* Rin;
+    int64_t nin;
+    int n;
+    int fan;
+    int ld;
+    T* Rout;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = 1024, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void TsqrMergeOp<T>::body(const Grid g, const Args& args) {
+  const T* __restrict__ Rin = args.Rin;
+  int64_t nin = args.nin;
+  int n = args.n;
+  int fan = args.fan;
+  int ld = args.ld;
+  T* __restrict__ Rout = args.Rout;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* red = A + (int64_t)ld * n;
   __shared__ T scratch[33];
   const int64_t nout = (nin + fan - 1) / fan;
-  for (int64_t blk = blockIdx.x; blk < nout; blk += gridDim.x) {
+  for (int64_t blk = g.bx; blk < nout; blk += g.gx) {
     const int64_t b0 = blk * fan;
     const int cnt = (int)(nin - b0 < fan ? nin - b0 : fan);
     const int rows = cnt * n;
@@ -532,10 +673,33 @@ constexpr int kRowsQR = 256;
 // loops rolled (small code).  Leaf blocks read 256 rows of B^T from the (L, n, R) view of B; merge
 // blocks stack ``fan`` upper triangles (n x n, column-major) of the previous level, fan n <= 256.
 template <int NC>
-__global__ void __launch_bounds__(kRowsQR) tsqr_rows_kernel(const float* __restrict__ B, int64_t L, int64_t R, int n,
-                                                            const float* __restrict__ Rin, int64_t nin, int fan,
-                                                            float* __restrict__ Rout,
-                                                            const int32_t* __restrict__ gate) {
+struct TsqrRowsOp {
+  struct Args {
+    const float* B;
+    int64_t L;
+    int64_t R;
+    int n;
+    const float* Rin;
+    int64_t nin;
+    int fan;
+    float* Rout;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = kRowsQR, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <int NC>
+__device__ __forceinline__ void TsqrRowsOp<NC>::body(const Grid g, const Args& args) {
+  const float* __restrict__ B = args.B;
+  int64_t L = args.L;
+  int64_t R = args.R;
+  int n = args.n;
+  const float* __restrict__ Rin = args.Rin;
+  int64_t nin = args.nin;
+  int fan = args.fan;
+  float* __restrict__ Rout = args.Rout;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (gate != nullptr && *gate == 0) return;
   constexpr int LD = NC + 1;
   constexpr int SEG = kRowsQR / NC;   // row segments of the column sums, NC rows each
@@ -552,7 +716,7 @@ __global__ void __launch_bounds__(kRowsQR) tsqr_rows_kernel(const float* __restr
   const int64_t M = L * R;
   const int64_t nblk = leaf ? (M + kRowsQR - 1) / kRowsQR : (nin + fan - 1) / fan;
   float* Arow = A + t * LD;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+  for (int64_t blk = g.bx; blk < nblk; blk += g.gx) {
     __syncthreads();   // shared buffers are free (previous block)
     if (leaf) {
       const int64_t p0 = blk * kRowsQR;
@@ -642,26 +806,31 @@ size_t tsqr_rows_smem(int nc) {
 // R of B^T (M x n FP32) by levels of tsqr_rows_kernel; buf0 / buf1 hold ceil(M / 256) and
 // ceil(M / 256 / fan) n x n triangles; returns the final triangle's buffer in *out.
 rh_status launch_tsqr_rows(const float* B, int64_t L, int64_t R, int n, float* buf0, float* buf1,
-                           const int32_t* gate, float** out, cudaStream_t st) {
+                           const int32_t* gate, float** out, cudaStream_t st, int site = SITE_OTHER) {
   if (n < 1 || n > 64) {
     set_error("tall-skinny QR: n must be in [1, 64]");
     return RH_EUNSUPPORTED;
   }
   const int nc = n <= 32 ? 32 : 64;
   const size_t smem = tsqr_rows_smem(nc);
-  auto kern = nc == 32 ? tsqr_rows_kernel<32> : tsqr_rows_kernel<64>;
-  RH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t cap = 4 * (int64_t)num_sms();
   const int fan = kRowsQR / n;
   int64_t cnt = ceil_div(L * R, kRowsQR);
-  kern<<<(unsigned)std::min<int64_t>(cnt, cap), kRowsQR, smem, st>>>(B, L, R, n, nullptr, 0, fan, buf0, gate);
-  RH_LAUNCH_CHECK();
+  auto level = [&](int sub, int64_t blocks, const float* Bs, int64_t Ls, int64_t Rs, const float* Rin, int64_t nin,
+                   float* Rout) -> rh_status {
+    const dim3 grid((unsigned)std::min<int64_t>(blocks, cap));
+    if (nc == 32)
+      return emit<TsqrRowsOp<32>>(site, sub, grid, smem, st,
+                                  TsqrRowsOp<32>::Args{Bs, Ls, Rs, n, Rin, nin, fan, Rout, gate});
+    return emit<TsqrRowsOp<64>>(site, sub, grid, smem, st, TsqrRowsOp<64>::Args{Bs, Ls, Rs, n, Rin, nin, fan, Rout, gate});
+  };
+  rh_status s = level(0, cnt, B, L, R, nullptr, 0, buf0);
+  if (s != RH_OK) return s;
   float* cur = buf0;
   float* nxt = buf1;
-  while (cnt > 1) {
+  for (int lv = 1; cnt > 1; ++lv) {
     const int64_t nout = ceil_div(cnt, fan);
-    kern<<<(unsigned)std::min<int64_t>(nout, cap), kRowsQR, smem, st>>>(nullptr, 1, 1, n, cur, cnt, fan, nxt, gate);
-    RH_LAUNCH_CHECK();
+    if ((s = level(lv, nout, nullptr, 1, 1, cur, cnt, nxt)) != RH_OK) return s;
     cnt = nout;
     float* tmp = cur;
     cur = nxt;
@@ -696,9 +865,27 @@ __device__ __forceinline__ float jacobi_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double jacobi_rsqrt(double x) { return 1.0 / sqrt(x); }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ Rin, int n, double* __restrict__ Ub,
-                                                          double* __restrict__ sv, const int32_t* __restrict__ gate,
-                                                          int32_t want) {
+struct JacobiSvdOp {
+  struct Args {
+    const T* Rin;
+    int n;
+    double* Ub;
+    double* sv;
+    const int32_t* gate;
+    int32_t want;
+  };
+  static constexpr int kThreads = 1024, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& args) {
+  const T* __restrict__ Rin = args.Rin;
+  int n = args.n;
+  double* __restrict__ Ub = args.Ub;
+  double* __restrict__ sv = args.sv;
+  const int32_t* __restrict__ gate = args.gate;
+  int32_t want = args.want;
+
   if (gate != nullptr && *gate != want) return;
   using Q4 = JacobiQuad<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -818,10 +1005,31 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const T* __restrict__ 
 }
 
 template <typename T>
-__global__ void factor_cast_kernel(int64_t I, int ell, int r, const double* __restrict__ Q,
-                                   const double* __restrict__ Ub, double* __restrict__ A, T* __restrict__ Uc) {
+struct FactorCastOp {
+  struct Args {
+    int64_t I;
+    int ell;
+    int r;
+    const double* Q;
+    const double* Ub;
+    double* A;
+    T* Uc;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void FactorCastOp<T>::body(const Grid g, const Args& args) {
+  int64_t I = args.I;
+  int ell = args.ell;
+  int r = args.r;
+  const double* __restrict__ Q = args.Q;
+  const double* __restrict__ Ub = args.Ub;
+  double* __restrict__ A = args.A;
+  T* __restrict__ Uc = args.Uc;
+
   const int64_t total = I * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = g.bx * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)g.gx * blockDim.x) {
     const int64_t i = e % I;
     const int k = (int)(e / I);
     double s = 0.0;
@@ -829,8 +1037,8 @@ __global__ void factor_cast_kernel(int64_t I, int ell, int r, const double* __re
     A[e] = s;
   }
   if (Uc != nullptr) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)ell * r;
-         e += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t e = g.bx * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)ell * r;
+         e += (int64_t)g.gx * blockDim.x)
       Uc[e] = (T)Ub[e];
   }
 }
@@ -839,11 +1047,29 @@ __global__ void factor_cast_kernel(int64_t I, int ell, int r, const double* __re
 // largest-magnitude entry (first index on ties) is positive; apply the same flip to
 // column k of ``other`` (rows_o x n, leading dimension rows_o) when given.  One CTA per column.
 template <typename T>
-__global__ void colsign_kernel(double* __restrict__ A, int64_t m, int n, T* __restrict__ other, int rows_o) {
+struct ColsignOp {
+  struct Args {
+    double* A;
+    int64_t m;
+    int n;
+    T* other;
+    int rows_o;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void ColsignOp<T>::body(const Grid g, const Args& args) {
+  double* __restrict__ A = args.A;
+  int64_t m = args.m;
+  int n = args.n;
+  T* __restrict__ other = args.other;
+  int rows_o = args.rows_o;
+
   __shared__ double sv[32];
   __shared__ int64_t si[32];
   __shared__ double sgn;
-  const int k = blockIdx.x;
+  const int k = g.bx;
   double* a = A + m * (int64_t)k;
   double best = -1.0;
   int64_t bi = 0;
@@ -888,12 +1114,39 @@ __global__ void colsign_kernel(double* __restrict__ A, int64_t m, int n, T* __re
 }
 
 template <typename T>
-__global__ void cast_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+struct CastOp {
+  struct Args {
+    const double* src;
+    T* dst;
+    int64_t n;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void CastOp<T>::body(const Grid g, const Args& args) {
+  const double* __restrict__ src = args.src;
+  T* __restrict__ dst = args.dst;
+  int64_t n = args.n;
+
+  for (int64_t e = g.bx * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)g.gx * blockDim.x)
     dst[e] = (T)src[e];
 }
 
-__global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+struct SumsqOp {
+  struct Args {
+    const double* x;
+    int64_t n;
+    double* out;
+  };
+  static constexpr int kThreads = 1024, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void SumsqOp::body(const Grid g, const Args& args) {
+  const double* __restrict__ x = args.x;
+  int64_t n = args.n;
+  double* __restrict__ out = args.out;
+
   __shared__ double scratch[33];
   double s = 0.0;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s = fma(x[e], x[e], s);
@@ -920,9 +1173,27 @@ struct GramCfg {
 // tile's partial carries ~2^-44 relative error instead of the FP32 sum's ~128 u; the Gram matrix is
 // then accurate enough for the Cholesky-Jacobi route at any condition number below ~1e6.
 template <int ELLP, bool DF>
-__global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const float* __restrict__ B, int64_t L,
-                                                                        int64_t R, int ell, double* __restrict__ part,
-                                                                        const int32_t* __restrict__ gate) {
+struct GramBOp {
+  struct Args {
+    const float* B;
+    int64_t L;
+    int64_t R;
+    int ell;
+    double* part;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = GramCfg<ELLP>::THREADS, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <int ELLP, bool DF>
+__device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args& args) {
+  const float* __restrict__ B = args.B;
+  int64_t L = args.L;
+  int64_t R = args.R;
+  int ell = args.ell;
+  double* __restrict__ part = args.part;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (gate != nullptr && *gate != 0) return;
   using C = GramCfg<ELLP>;
   __shared__ __align__(16) float Bs[128 * C::LDS];
@@ -945,7 +1216,7 @@ __global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const fl
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int64_t t = g.bx; t < ntiles; t += g.gx) {
     const int64_t p0 = t * 128;
     const int valid = (int)(M - p0 < 128 ? M - p0 : 128);
     __syncthreads();
@@ -1024,7 +1295,7 @@ __global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const fl
     }
   }
   if (!active) return;
-  double* o = part + (int64_t)blockIdx.x * ell * ell;
+  double* o = part + (int64_t)g.bx * ell * ell;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1037,13 +1308,29 @@ __global__ void __launch_bounds__(GramCfg<ELLP>::THREADS) gram_b_kernel(const fl
 // W[r, c] = sum over CTAs of the upper-triangle partial at (min(r, c), max(r, c)).  A block of
 // 256 threads owns 32 consecutive entries of W: warp k sums partials k, k + 8, ... and the eight
 // warp sums are added in a fixed order.
-__global__ void __launch_bounds__(256) gram_b_reduce_kernel(const double* __restrict__ part, int nparts, int ell,
-                                                            double* __restrict__ W, const int32_t* __restrict__ gate) {
+struct GramBReduceOp {
+  struct Args {
+    const double* part;
+    int nparts;
+    int ell;
+    double* W;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void GramBReduceOp::body(const Grid g, const Args& args) {
+  const double* __restrict__ part = args.part;
+  int nparts = args.nparts;
+  int ell = args.ell;
+  double* __restrict__ W = args.W;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (gate != nullptr && *gate != 0) return;
   __shared__ double red[8][32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int nn = ell * ell;
-  const int e = blockIdx.x * 32 + lane;
+  const int e = g.bx * 32 + lane;
   double s = 0.0;
   if (e < nn) {
     const int r = e % ell, c = e / ell;
@@ -1071,10 +1358,24 @@ __global__ void __launch_bounds__(256) gram_b_reduce_kernel(const double* __rest
 // (value, position) taken while the diagonal was updated; positions k and p are swapped
 // symmetrically; then column k of X is written and the trailing triangle updated through the
 // table of ArithDF / chol_kernel.  Two barriers per step.
-__global__ void __launch_bounds__(kCholThreads) pivoted_cholesky_kernel(const double* __restrict__ W, int n,
-                                                                        float* __restrict__ X,
-                                                                        int32_t* __restrict__ flag,
-                                                                        int32_t* __restrict__ clear_on_success) {
+struct PivotedCholeskyOp {
+  struct Args {
+    const double* W;
+    int n;
+    float* X;
+    int32_t* flag;
+    int32_t* clear_on_success;
+  };
+  static constexpr int kThreads = kCholThreads, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void PivotedCholeskyOp::body(const Grid g, const Args& args) {
+  const double* __restrict__ W = args.W;
+  int n = args.n;
+  float* __restrict__ X = args.X;
+  int32_t* __restrict__ flag = args.flag;
+  int32_t* __restrict__ clear_on_success = args.clear_on_success;
+
   if (flag[0]) return;
   using Ar = ArithDF;
   using V = Ar::V;
@@ -1193,12 +1494,28 @@ __global__ void __launch_bounds__(kCholThreads) pivoted_cholesky_kernel(const do
 // |u_i^T u_j| <= tol).  Writes Ub (n x n, FP64) and sv = the column norms (FP64), sorted.
 constexpr int kRowJacThreads = 256;
 
-__global__ void __launch_bounds__(kRowJacThreads) jacobi_rows_kernel(const float* __restrict__ Xin, int n,
-                                                                       double* __restrict__ Ub,
-                                                                       double* __restrict__ sv,
-                                                                       const int32_t* __restrict__ gate,
-                                                                       int32_t* __restrict__ info_or = nullptr,
-                                                                       int32_t info_bits = 0) {
+struct JacobiRowsOp {
+  struct Args {
+    const float* Xin;
+    int n;
+    double* Ub;
+    double* sv;
+    const int32_t* gate;
+    int32_t* info_or;
+    int32_t info_bits;
+  };
+  static constexpr int kThreads = kRowJacThreads, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& args) {
+  const float* __restrict__ Xin = args.Xin;
+  int n = args.n;
+  double* __restrict__ Ub = args.Ub;
+  double* __restrict__ sv = args.sv;
+  const int32_t* __restrict__ gate = args.gate;
+  int32_t* __restrict__ info_or = args.info_or;
+  int32_t info_bits = args.info_bits;
+
   if (gate != nullptr && *gate != 0) return;
   if (info_or != nullptr && threadIdx.x == 0) *info_or |= info_bits;
   extern __shared__ __align__(16) float jsm[];
@@ -1355,10 +1672,24 @@ __global__ void colnorm2_kernel(const T* __restrict__ R, int n, double* __restri
   if (threadIdx.x == 0) d[c] = s;
 }
 
-__global__ void cast_f2d_gated_kernel(const float* __restrict__ src, double* __restrict__ dst, int64_t n,
-                                      const int32_t* __restrict__ gate) {
+struct CastF2dGatedOp {
+  struct Args {
+    const float* src;
+    double* dst;
+    int64_t n;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void CastF2dGatedOp::body(const Grid g, const Args& args) {
+  const float* __restrict__ src = args.src;
+  double* __restrict__ dst = args.dst;
+  int64_t n = args.n;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (*gate) return;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t e = g.bx * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)g.gx * blockDim.x)
     dst[e] = (double)src[e];
 }
 
@@ -1367,10 +1698,29 @@ __global__ void cast_f2d_gated_kernel(const float* __restrict__ src, double* __r
 // Gram cannot resolve the top-r subspace.
 // Decides the first (FP32 Gram) route; arm[0] = 0 arms the second (double-float Gram) route exactly
 // when the first is rejected, arm[0] = 1 keeps it off.
-__global__ void trunc_decide_kernel(const int32_t* __restrict__ chol_flag, const double* __restrict__ sv, int ell, int r,
-                                    int32_t* __restrict__ use_tsqr, int32_t* __restrict__ info,
-                                    int32_t* __restrict__ arm) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+struct TruncDecideOp {
+  struct Args {
+    const int32_t* chol_flag;
+    const double* sv;
+    int ell;
+    int r;
+    int32_t* use_tsqr;
+    int32_t* info;
+    int32_t* arm;
+  };
+  static constexpr int kThreads = 32, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void TruncDecideOp::body(const Grid g, const Args& args) {
+  const int32_t* __restrict__ chol_flag = args.chol_flag;
+  const double* __restrict__ sv = args.sv;
+  int ell = args.ell;
+  int r = args.r;
+  int32_t* __restrict__ use_tsqr = args.use_tsqr;
+  int32_t* __restrict__ info = args.info;
+  int32_t* __restrict__ arm = args.arm;
+
+  if (threadIdx.x != 0 || g.bx != 0) return;
   if (*chol_flag) {
     *use_tsqr = 1;
     if (arm != nullptr) arm[0] = 0;
@@ -1386,10 +1736,25 @@ __global__ void trunc_decide_kernel(const int32_t* __restrict__ chol_flag, const
 }
 
 template <typename T>
-__global__ void cast_gated_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n,
-                                  const int32_t* __restrict__ gate) {
+struct CastGatedOp {
+  struct Args {
+    const double* src;
+    T* dst;
+    int64_t n;
+    const int32_t* gate;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void CastGatedOp<T>::body(const Grid g, const Args& args) {
+  const double* __restrict__ src = args.src;
+  T* __restrict__ dst = args.dst;
+  int64_t n = args.n;
+  const int32_t* __restrict__ gate = args.gate;
+
   if (gate != nullptr && *gate != 0) return;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t e = g.bx * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)g.gx * blockDim.x)
     dst[e] = (T)src[e];
 }
 
@@ -1411,7 +1776,7 @@ size_t orth_workspace_elems(int64_t m, int n) {
 }
 
 rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
-                          const int32_t* gate, cudaStream_t st, bool df = false);
+                          const int32_t* gate, cudaStream_t st, bool df = false, int site = SITE_OTHER);
 
 rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, int32_t* info, double* ws,
                                 cudaStream_t st, bool f32) {
@@ -1425,67 +1790,48 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
   double* W = Q1 + m * n;
   double* beta = W + m * n;
   int32_t* flag = reinterpret_cast<int32_t*>(beta + n);
-  RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+  rh_status s = emit_memset(SITE_ORTH_ZERO, 0, flag, sizeof(int32_t), st);
+  if (s != RH_OK) return s;
+  if ((s = emit_memset(SITE_ORTH_ZERO, 1, C, sizeof(double) * n * n, st)) != RH_OK) return s;
+  const size_t gsm = sizeof(double) * rb * n;
+  const int rblocks = (int)ceil_div((int64_t)n * n, 256);
+  const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
   if (f32) {
     // FP32 data: CholeskyQR2 whose first pass keeps what its stability needs -- the Gram matrix in
     // FP64, its Cholesky factor in double-float, the triangular solve in FP64 (Q_1 is then
     // orthonormal to ~u_64 kappa(Y)) -- and whose second pass, on the nearly orthonormal Q_1, runs
     // in FP32.  A breakdown hands over to the Householder branch below.  The FP32 copies live in
     // the W region (only the Householder branch uses W, and it reads Y).
-    RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
-    const size_t gsm = sizeof(double) * rb * n;
-    const int rblocks = (int)ceil_div((int64_t)n * n, 256);
-    const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
-    gram_partial_kernel<<<nb, 256, gsm, st>>>(Y, m, n, rb, Gpart, flag);
-    RH_LAUNCH_CHECK();
-    gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
-    RH_LAUNCH_CHECK();
-    chol_kernel<ArithDF><<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(C, n, R, rdiag, flag);
-    RH_LAUNCH_CHECK();
-    trsm_rows_kernel<double><<<tblocks, 256, sizeof(double) * ((n | 1) * n + n), st>>>(Y, m, n, R, rdiag, Q1, flag);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(GramPartialOp, SITE_ORTH_GRAM, 0, nb, gsm, Y, m, n, rb, Gpart, flag);
+    RH_EMIT(GramReduceOp, SITE_ORTH_GRAM_REDUCE, 0, rblocks, 0, Gpart, nb, n, C, flag);
+    RH_EMIT(CholOp<ArithDF>, SITE_ORTH_CHOL, 0, 1, chol_smem(n, sizeof(dfl::F2)), C, n, R, rdiag, flag);
+    RH_EMIT(TrsmRowsOp<double>, SITE_ORTH_TRSM, 0, tblocks, sizeof(double) * ((n | 1) * n + n), Y, m, n, R, rdiag, Q1,
+            flag);
     float* Q1f = reinterpret_cast<float*>(W);
     float* Q2f = Q1f + m * n;
     const int cblocks = (int)std::min<int64_t>(ceil_div(m * n, 256), 4 * num_sms());
-    cast_gated_kernel<float><<<cblocks, 256, 0, st>>>(Q1, Q1f, m * n, flag);
-    RH_LAUNCH_CHECK();
-    rh_status s = launch_gram_f32(Q1f, m, 1, n, Gpart, C, flag, st);
-    if (s != RH_OK) return s;
-    chol_kernel<ArithF32><<<1, kCholThreads, chol_smem(n, sizeof(float)), st>>>(C, n, R, rdiag, flag);
-    RH_LAUNCH_CHECK();
-    trsm_rows_kernel<float><<<tblocks, 256, sizeof(float) * ((n | 1) * n + n), st>>>(Q1f, m, n, R, rdiag, Q2f, flag);
-    RH_LAUNCH_CHECK();
-    cast_f2d_gated_kernel<<<cblocks, 256, 0, st>>>(Q2f, Q, m * n, flag);
-    RH_LAUNCH_CHECK();
-    householder_q_kernel<<<1, 1024, 0, st>>>(Y, m, n, W, beta, Q, flag, info);
-    RH_LAUNCH_CHECK();
-    colsign_kernel<double><<<n, 256, 0, st>>>(Q, m, n, nullptr, 0);
-    RH_LAUNCH_CHECK();
-    return RH_OK;
+    RH_EMIT(CastGatedOp<float>, SITE_ORTH_CAST, 0, cblocks, 0, Q1, Q1f, m * n, flag);
+    if ((s = launch_gram_f32(Q1f, m, 1, n, Gpart, C, flag, st, false, SITE_ORTH_GRAM2)) != RH_OK) return s;
+    RH_EMIT(CholOp<ArithF32>, SITE_ORTH_CHOL2, 0, 1, chol_smem(n, sizeof(float)), C, n, R, rdiag, flag);
+    RH_EMIT(TrsmRowsOp<float>, SITE_ORTH_TRSM2, 0, tblocks, sizeof(float) * ((n | 1) * n + n), Q1f, m, n, R, rdiag,
+            Q2f, flag);
+    RH_EMIT(CastF2dGatedOp, SITE_ORTH_CAST2, 0, cblocks, 0, Q2f, Q, m * n, flag);
+  } else {
+    const size_t tsm = sizeof(double) * ((n | 1) * n + n);
+    const double* src = Y;
+    double* dst = Q1;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int so = pass == 0 ? 0 : SITE_ORTH_GRAM2 - SITE_ORTH_GRAM;   // the second pass's sites
+      RH_EMIT(GramPartialOp, SITE_ORTH_GRAM + so, 0, nb, gsm, src, m, n, rb, Gpart, flag);
+      RH_EMIT(GramReduceOp, SITE_ORTH_GRAM_REDUCE + so, 0, rblocks, 0, Gpart, nb, n, C, flag);
+      RH_EMIT(CholOp<ArithF64>, SITE_ORTH_CHOL + so, 0, 1, chol_smem(n, sizeof(double)), C, n, R, rdiag, flag);
+      RH_EMIT(TrsmRowsOp<double>, SITE_ORTH_TRSM + so, 0, tblocks, tsm, src, m, n, R, rdiag, dst, flag);
+      src = Q1;
+      dst = Q;
+    }
   }
-  RH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * n * n, st));
-  const size_t gsm = sizeof(double) * rb * n;
-  const size_t tsm = sizeof(double) * ((n | 1) * n + n);
-  const int rblocks = (int)ceil_div((int64_t)n * n, 256);
-  const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
-  const double* src = Y;
-  double* dst = Q1;
-  for (int pass = 0; pass < 2; ++pass) {
-    gram_partial_kernel<<<nb, 256, gsm, st>>>(src, m, n, rb, Gpart, flag);
-    RH_LAUNCH_CHECK();
-    gram_reduce_kernel<<<rblocks, 256, 0, st>>>(Gpart, nb, n, C, flag);
-    RH_LAUNCH_CHECK();
-    chol_kernel<ArithF64><<<1, kCholThreads, chol_smem(n, sizeof(double)), st>>>(C, n, R, rdiag, flag);
-    RH_LAUNCH_CHECK();
-    trsm_rows_kernel<double><<<tblocks, 256, tsm, st>>>(src, m, n, R, rdiag, dst, flag);
-    RH_LAUNCH_CHECK();
-    src = Q1;
-    dst = Q;
-  }
-  householder_q_kernel<<<1, 1024, 0, st>>>(Y, m, n, W, beta, Q, flag, info);
-  RH_LAUNCH_CHECK();
-  colsign_kernel<double><<<n, 256, 0, st>>>(Q, m, n, nullptr, 0);
-  RH_LAUNCH_CHECK();
+  RH_EMIT(HouseholderQOp, SITE_ORTH_HOUSEHOLDER, 0, 1, 0, Y, m, n, W, beta, Q, flag, info);
+  RH_EMIT(ColsignOp<double>, SITE_ORTH_SIGN, 0, n, 0, Q, m, n, nullptr, 0);
   return RH_OK;
 }
 
@@ -1526,19 +1872,24 @@ int gram_ctas() { return 8 * num_sms(); }
 // W = B B^T (ell x ell, FP64, full) of the FP32 (L, ell, R) tensor B: FP32 sums over 128 columns,
 // FP64 across; part holds min(gram_ctas(), ceil(L R / 128)) ell^2 doubles.  Gated on *gate == 0.
 rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
-                          const int32_t* gate, cudaStream_t st, bool df) {
+                          const int32_t* gate, cudaStream_t st, bool df, int site) {
   const int64_t ntiles = ceil_div(L * R, 128);
   const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(gram_ctas(), ntiles));
   if (!df) {
+    using G32 = GramBOp<32, false>;
+    using G64 = GramBOp<64, false>;
     if (ell <= 32)
-      gram_b_kernel<32, false><<<ctas, GramCfg<32>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+      RH_EMIT(G32, site, 0, ctas, 0, B, L, R, ell, part, gate);
     else
-      gram_b_kernel<64, false><<<ctas, GramCfg<64>::THREADS, 0, st>>>(B, L, R, ell, part, gate);
+      RH_EMIT(G64, site, 0, ctas, 0, B, L, R, ell, part, gate);
   } else {
     // the double-float sums are ALU-bound: blocks of 4 x 4 entries over the columns actually used
     switch ((ell + 7) / 8) {
 #define RH_GDF(E) \
-  case E / 8: gram_b_kernel<E, true><<<ctas, GramCfg<E>::THREADS, 0, st>>>(B, L, R, ell, part, gate); break
+  case E / 8: {                                                           \
+    using GE = GramBOp<E, true>;                                          \
+    RH_EMIT(GE, site, 0, ctas, 0, B, L, R, ell, part, gate);              \
+  } break
       RH_GDF(8); RH_GDF(16); RH_GDF(24); RH_GDF(32); RH_GDF(40); RH_GDF(48); RH_GDF(56); RH_GDF(64);
 #undef RH_GDF
       default:
@@ -1546,9 +1897,8 @@ rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double*
         return RH_EUNSUPPORTED;
     }
   }
-  RH_LAUNCH_CHECK();
-  gram_b_reduce_kernel<<<(int)ceil_div((int64_t)ell * ell, 32), 256, 0, st>>>(part, ctas, ell, W, gate);
-  RH_LAUNCH_CHECK();
+  RH_EMIT(GramBReduceOp, site == SITE_OTHER ? SITE_OTHER : site + 1, 0, (int)ceil_div((int64_t)ell * ell, 32), 0,
+          part, ctas, ell, W, gate);
   return RH_OK;
 }
 
@@ -1567,6 +1917,34 @@ size_t trunc_workspace_elems(const TruncPlan& pl0) {
   return e;
 }
 
+// R of B^T (M x n) by the FP64 tree: a Householder QR per block of rows0 rows, then merges of fan
+// triangles per level; *out points at the final triangle (buf0 or buf1).
+template <typename T>
+static rh_status launch_tsqr_tree(const TruncPlan& pl, const T* B, T* buf0, T* buf1, const int32_t* gate, T** out,
+                                  cudaStream_t st, int site) {
+  const int n = pl.ell;
+  const int ld0 = odd_ld(pl.rows0);
+  const int ldm = odd_ld(pl.fan * n);
+  const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
+  const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
+  const int64_t cap = 8 * (int64_t)num_sms();
+  RH_EMIT(TsqrLeafOp<T>, site, 0, (unsigned)std::min<int64_t>(pl.nblk0, cap), sm0, B, pl.v.L, pl.v.R, n, pl.rows0, ld0,
+          buf0, gate);
+  int64_t cnt = pl.nblk0;
+  T* cur = buf0;
+  T* nxt = buf1;
+  for (int lv = 1; cnt > 1; ++lv) {
+    const int64_t nout = ceil_div(cnt, pl.fan);
+    RH_EMIT(TsqrMergeOp<T>, site, lv, (unsigned)std::min<int64_t>(nout, cap), smm, cur, cnt, n, pl.fan, ldm, nxt, gate);
+    cnt = nout;
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  *out = cur;
+  return RH_OK;
+}
+
 template <typename T>
 rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st, int r,
                            int32_t* info) {
@@ -1578,7 +1956,6 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
   T* buf1 = ws + pl.nblk0 * nn;
   const int np = (n + 1) & ~1;
   const size_t smj = sizeof(T) * 4 * (size_t)np * 32 * 2;
-  RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
   int32_t* use_tsqr = nullptr;
   if (sizeof(T) == 4 && r >= 1 && r <= n) {
     // Gram route (FP32 data): W = B B^T, R = chol(W)^T-factor, Jacobi on R; gated fallback below
@@ -1593,71 +1970,45 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     float* Rf = reinterpret_cast<float*>(flags + 16);
     use_tsqr = flags + 1;
     int32_t* flags2 = flags + 4;   // second route: [0] = skip / Cholesky failure
-    RH_CUDA_TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int32_t), st));
     (void)ctas;
-    rh_status s;
-    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st)) != RH_OK)
+    rh_status s = emit_memset(SITE_TRUNC_ZERO, 0, flags, 8 * sizeof(int32_t), st);
+    if (s != RH_OK) return s;
+    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st, false,
+                             SITE_TRUNC_GRAM)) != RH_OK)
       return s;
-    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(W, n, Rf, flags, nullptr);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(PivotedCholeskyOp, SITE_TRUNC_PCHOL, 0, 1, chol_smem(n, sizeof(dfl::F2)), W, n, Rf, flags, nullptr);
     const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
-    RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     {
       ProfileScope ps(PROF_JACOBI, 0, st);
-      jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Rf, n, Ub, sv, flags);
-      RH_LAUNCH_CHECK();
+      RH_EMIT(JacobiRowsOp, SITE_TRUNC_JACOBI, 0, 1, smr, Rf, n, Ub, sv, flags, nullptr, 0);
     }
-    trunc_decide_kernel<<<1, 32, 0, st>>>(flags, sv, n, r, use_tsqr, info, flags2);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(TruncDecideOp, SITE_TRUNC_DECIDE, 0, 1, 0, flags, sv, n, r, use_tsqr, info, flags2);
     // Second route when the first is rejected: the same factorization of a double-float Gram
     // matrix (no gap test: its error is ~2^-44 ||W||).  Its Cholesky clears use_tsqr when it
     // succeeds, so the tall-skinny QR below only runs when it breaks down too.
-    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, flags2, st, true)) !=
-        RH_OK)
+    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, flags2, st, true,
+                             SITE_TRUNC_GRAM_DF)) != RH_OK)
       return s;
-    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(n, sizeof(dfl::F2)), st>>>(W, n, Rf, flags2, use_tsqr);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(PivotedCholeskyOp, SITE_TRUNC_PCHOL2, 0, 1, chol_smem(n, sizeof(dfl::F2)), W, n, Rf, flags2, use_tsqr);
     {
       ProfileScope ps(PROF_JACOBI, 2, st);
-      jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Rf, n, Ub, sv, flags2, info, 8);
-      RH_LAUNCH_CHECK();
+      RH_EMIT(JacobiRowsOp, SITE_TRUNC_JACOBI2, 0, 1, smr, Rf, n, Ub, sv, flags2, info, 8);
     }
   }
   T* cur = buf0;
   if constexpr (sizeof(T) == 4) {
     float* fin = nullptr;
     rh_status s = launch_tsqr_rows(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, reinterpret_cast<float*>(buf0),
-                                   reinterpret_cast<float*>(buf1), use_tsqr, &fin, st);
+                                   reinterpret_cast<float*>(buf1), use_tsqr, &fin, st, SITE_TRUNC_TSQR);
     if (s != RH_OK) return s;
     cur = reinterpret_cast<T*>(fin);
   } else {
-    const int ld0 = odd_ld(pl.rows0);
-    const int ldm = odd_ld(pl.fan * n);
-    const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
-    const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
-    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    const int64_t tsqr_grid_cap = 8 * (int64_t)num_sms();
-    tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, tsqr_grid_cap), kTsqrThreads, sm0, st>>>(
-        B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, use_tsqr);
-    RH_LAUNCH_CHECK();
-    int64_t cnt = pl.nblk0;
-    T* nxt = buf1;
-    while (cnt > 1) {
-      const int64_t nout = ceil_div(cnt, pl.fan);
-      tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, tsqr_grid_cap), kTsqrThreads, smm, st>>>(
-          cur, cnt, n, pl.fan, ldm, nxt, use_tsqr);
-      RH_LAUNCH_CHECK();
-      cnt = nout;
-      T* t = cur;
-      cur = nxt;
-      nxt = t;
-    }
+    rh_status s = launch_tsqr_tree<T>(pl, B, buf0, buf1, use_tsqr, &cur, st, SITE_TRUNC_TSQR);
+    if (s != RH_OK) return s;
   }
   {
     ProfileScope ps(PROF_JACOBI, 1, st);
-    jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(cur, n, Ub, sv, use_tsqr, 1);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(JacobiSvdOp<T>, SITE_TRUNC_JACOBI_SVD, 0, 1, smj, cur, n, Ub, sv, use_tsqr, 1);
   }
   return RH_OK;
 }
@@ -1671,7 +2022,8 @@ rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram
   const int n = pl.ell;
   const int64_t nn = (int64_t)n * n;
   if (gram) {
-    rh_status s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st, df);
+    rh_status s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st, df,
+                                  SITE_OTHER);
     if (s != RH_OK) return s;
     diag_kernel<<<1, 64, 0, st>>>(W, n, rownorm2);
     RH_LAUNCH_CHECK();
@@ -1683,32 +2035,12 @@ rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram
   if constexpr (sizeof(T) == 4) {
     float* fin = nullptr;
     rh_status s = launch_tsqr_rows(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, reinterpret_cast<float*>(buf0),
-                                   reinterpret_cast<float*>(buf1), nullptr, &fin, st);
+                                   reinterpret_cast<float*>(buf1), nullptr, &fin, st, SITE_OTHER);
     if (s != RH_OK) return s;
     cur = reinterpret_cast<T*>(fin);
   } else {
-    const int ld0 = odd_ld(pl.rows0);
-    const int ldm = odd_ld(pl.fan * n);
-    const size_t sm0 = sizeof(T) * ((size_t)ld0 * n + kTsqrThreads + 64);
-    const size_t smm = sizeof(T) * ((size_t)ldm * n + kTsqrThreads + 64);
-    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
-    RH_CUDA_TRY(cudaFuncSetAttribute(tsqr_merge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    const int64_t cap = 8 * (int64_t)num_sms();
-    tsqr_leaf_kernel<T><<<(unsigned)std::min<int64_t>(pl.nblk0, cap), kTsqrThreads, sm0, st>>>(
-        B, pl.v.L, pl.v.R, n, pl.rows0, ld0, buf0, nullptr);
-    RH_LAUNCH_CHECK();
-    int64_t cnt = pl.nblk0;
-    T* nxt = buf1;
-    while (cnt > 1) {
-      const int64_t nout = ceil_div(cnt, pl.fan);
-      tsqr_merge_kernel<T><<<(unsigned)std::min<int64_t>(nout, cap), kTsqrThreads, smm, st>>>(cur, cnt, n, pl.fan,
-                                                                                             ldm, nxt, nullptr);
-      RH_LAUNCH_CHECK();
-      cnt = nout;
-      T* t = cur;
-      cur = nxt;
-      nxt = t;
-    }
+    rh_status s = launch_tsqr_tree<T>(pl, B, buf0, buf1, nullptr, &cur, st, SITE_OTHER);
+    if (s != RH_OK) return s;
   }
   *R = cur;
   colnorm2_kernel<T><<<n, 32, 0, st>>>(cur, n, rownorm2);
@@ -1724,21 +2056,16 @@ rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, con
     RH_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
     copy_leading_kernel<double, double><<<blocks, 256, 0, st>>>(W, n, k, Wk);
     RH_LAUNCH_CHECK();
-    pivoted_cholesky_kernel<<<1, kCholThreads, chol_smem(k, sizeof(dfl::F2)), st>>>(Wk, k, Xf, flag, nullptr);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(PivotedCholeskyOp, SITE_OTHER, 0, 1, chol_smem(k, sizeof(dfl::F2)), Wk, k, Xf, flag, nullptr);
     const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
-    RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    jacobi_rows_kernel<<<1, kRowJacThreads, smr, st>>>(Xf, k, Ub, sv, flag);
-    RH_LAUNCH_CHECK();
+    RH_EMIT(JacobiRowsOp, SITE_OTHER, 0, 1, smr, Xf, k, Ub, sv, flag, nullptr, 0);
     return RH_OK;
   }
   copy_leading_kernel<T, T><<<blocks, 256, 0, st>>>(R, n, k, Rk);
   RH_LAUNCH_CHECK();
   const int np = (k + 1) & ~1;
   const size_t smj = sizeof(T) * 4 * (size_t)np * 32 * 2;
-  RH_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
-  jacobi_svd_kernel<T><<<1, 1024, smj, st>>>(Rk, k, Ub, sv, nullptr, 0);
-  RH_LAUNCH_CHECK();
+  RH_EMIT(JacobiSvdOp<T>, SITE_OTHER, 0, 1, smj, Rk, k, Ub, sv, nullptr, 0);
   return RH_OK;
 }
 
@@ -1747,24 +2074,20 @@ rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, con
                                  cudaStream_t st) {
   const int64_t total = std::max<int64_t>(I * r, (int64_t)ell * r);
   const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 8 * num_sms());
-  factor_cast_kernel<T><<<blocks, 256, 0, st>>>(I, ell, r, Q, Ub, A, Uc);
-  RH_LAUNCH_CHECK();
-  colsign_kernel<T><<<r, 256, 0, st>>>(A, I, r, Uc, ell);
-  RH_LAUNCH_CHECK();
+  RH_EMIT(FactorCastOp<T>, SITE_FACTOR, 0, blocks, 0, I, ell, r, Q, Ub, A, Uc);
+  RH_EMIT(ColsignOp<T>, SITE_FACTOR_SIGN, 0, r, 0, A, I, r, Uc, ell);
   return RH_OK;
 }
 
 template <typename T>
 rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-  cast_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>(src, dst, n);
-  RH_LAUNCH_CHECK();
+  RH_EMIT(CastOp<T>, SITE_CAST_Q, 0, std::max(blocks, 1), 0, src, dst, n);
   return RH_OK;
 }
 
 rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st) {
-  sumsq_kernel<<<1, 1024, 0, st>>>(x, n, out);
-  RH_LAUNCH_CHECK();
+  RH_EMIT(SumsqOp, SITE_FINAL, 0, 1, 0, x, n, out);
   return RH_OK;
 }
 

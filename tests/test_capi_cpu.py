@@ -120,12 +120,12 @@ def test_omega_and_sketch_argument_checks(L):
     assert L.rhosvd_sketch(2, dims, 0, ctypes.c_void_p(1), 0, 4, 0, 0, ctypes.c_void_p(1), None, None, 0, None) == 2
 
 
-def _batched_ws(L, dims_list, ranks_list, streams=0, **kw):
+def _batched_ws(L, dims_list, ranks_list, streams=0, dtype=0, **kw):
     from paper_1905_07311_gb300 import _lib
 
     o = _lib.make_options(**kw)
     return L.rsthosvd_batched_workspace_size(len(dims_list), _lib.i32_array([len(d) for d in dims_list]),
-                                             _lib.i64_array([x for d in dims_list for x in d]), 0,
+                                             _lib.i64_array([x for d in dims_list for x in d]), dtype,
                                              _lib.i32_array([r for rk in ranks_list for r in rk]), ctypes.byref(o),
                                              streams)
 
@@ -137,9 +137,48 @@ def test_batched_workspace_is_one_slice_per_stream(L):
     slice_ = (one + 255) // 256 * 256
     assert _batched_ws(L, dims_list, ranks_list, streams=1, p=5) == slice_
     assert _batched_ws(L, dims_list, ranks_list, streams=2, p=5) == 2 * slice_
-    # streams are capped at the tensor count, 0 = min(8, count)
+    # streams are capped at the tensor count
     assert _batched_ws(L, dims_list, ranks_list, streams=16, p=5) == 3 * slice_
-    assert _batched_ws(L, dims_list, ranks_list, streams=0, p=5) == 3 * slice_
+    # streams = 0 with FP64 / FP32 truncated requests: the grouped engine, one slice per tensor
+    # plus the launch tables (recorded on the host: a few KB per tensor)
+    slices = sum((_ws(L, d, r, dtype=dt, p=5) + 255) // 256 * 256 for d, r in zip(dims_list, ranks_list)
+                 for dt in [0])
+    g = _batched_ws(L, dims_list, ranks_list, streams=0, p=5)
+    assert slices < g < slices + (1 << 20)
+    slices32 = sum((_ws(L, d, r, dtype=1, p=5) + 255) // 256 * 256 for d, r in zip(dims_list, ranks_list))
+    g32 = _batched_ws(L, dims_list, ranks_list, streams=0, dtype=1, p=5)
+    assert slices32 < g32 < slices32 + (1 << 20)
+    # requests outside the grouped engine (a converted input form, or no truncation) keep the
+    # stream engine at streams = 0: min(8, count) slices
+    one4 = max(_ws(L, d, r, dtype=4, p=5) for d, r in zip(dims_list, ranks_list))
+    assert _batched_ws(L, dims_list, ranks_list, streams=0, dtype=4, p=5) == 3 * ((one4 + 255) // 256 * 256)
+    one_nt = max(_ws(L, d, r, p=5, truncate=False) for d, r in zip(dims_list, ranks_list))
+    assert _batched_ws(L, dims_list, ranks_list, streams=0, p=5, truncate=False) == 3 * ((one_nt + 255) // 256 * 256)
+
+
+def test_batched_plan_argument_checks(L):
+    from paper_1905_07311_gb300 import _lib
+
+    dims = _lib.i64_array([30, 20, 10, 16, 16, 16])
+    orders = _lib.i32_array([3, 3])
+    ranks = _lib.i32_array([4, 4, 4, 5, 5, 5])
+    xs = (ctypes.c_void_p * 2)(1, 1)
+    fs = (ctypes.c_void_p * 6)(*([1] * 6))
+    cs = (ctypes.c_void_p * 2)(1, 1)
+    h = ctypes.c_void_p()
+    o = _lib.make_options(p=5)
+    # no plan pointer
+    assert L.rsthosvd_batched_plan_create(2, orders, dims, 1, xs, ranks, ctypes.byref(o), fs, cs, None, None,
+                                          None, 0, None) == 1
+    # a converted input form is not on the grouped engine
+    assert L.rsthosvd_batched_plan_create(2, orders, dims, 4, xs, ranks, ctypes.byref(o), fs, cs, None, None,
+                                          None, 0, ctypes.byref(h)) == 6
+    assert "grouped engine" in L.rh_last_error().decode() and not h.value
+    # workspace too small (checked before anything touches the device)
+    assert L.rsthosvd_batched_plan_create(2, orders, dims, 1, xs, ranks, ctypes.byref(o), fs, cs, None, None,
+                                          ctypes.c_void_p(1 << 20), 16, ctypes.byref(h)) == 2
+    assert L.rsthosvd_batched_plan_launches(None) == -1
+    L.rsthosvd_batched_plan_destroy(None)
 
 
 def test_batched_argument_checks(L):
