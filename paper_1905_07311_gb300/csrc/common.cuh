@@ -289,6 +289,7 @@ enum LaunchSite : int {
   SITE_TRUNC_PCHOL2,
   SITE_TRUNC_JACOBI2,
   SITE_TRUNC_TSQR,          // sub = level of the reduction tree
+  SITE_TRUNC_PIVQR,
   SITE_TRUNC_JACOBI_SVD,
   SITE_FACTOR = 70,
   SITE_FACTOR_SIGN,

@@ -873,6 +873,7 @@ struct JacobiSvdOp {
     double* sv;
     const int32_t* gate;
     int32_t want;
+    const int32_t* piv;   // non-NULL: preconditioned mode (see below)
   };
   static constexpr int kThreads = 1024, kMinBlocks = 1;
   __device__ static void body(const Grid g, const Args& args);
@@ -885,6 +886,7 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
   double* __restrict__ sv = args.sv;
   const int32_t* __restrict__ gate = args.gate;
   int32_t want = args.want;
+  const int32_t* __restrict__ piv = args.piv;
 
   if (gate != nullptr && *gate != want) return;
   using Q4 = JacobiQuad<T>;
@@ -900,8 +902,11 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
     const int q = e >> 5, l = e & 31;
     Q4 z;
     const bool col = q < n;
-    z.x0 = (col && l < n) ? Rin[l + n * q] : T(0);
-    z.x1 = (col && l + 32 < n) ? Rin[l + 32 + n * q] : T(0);
+    // preconditioned mode: the players are the rows of Rin (the columns of X = Rin^T)
+    const int64_t s0 = piv ? q + (int64_t)n * l : l + (int64_t)n * q;
+    const int64_t s1 = piv ? q + (int64_t)n * (l + 32) : l + 32 + (int64_t)n * q;
+    z.x0 = (col && l < n) ? Rin[s0] : T(0);
+    z.x1 = (col && l + 32 < n) ? Rin[s1] : T(0);
     z.v0 = (col && l == q) ? T(1) : T(0);
     z.v1 = (col && l + 32 == q) ? T(1) : T(0);
     buf0[e] = z;
@@ -918,7 +923,7 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
   // reaches the rounding level, like the Hilbert tensor's, never meets the stopping test; a floor
   // as high as the tolerance itself was measured to move the leading subspace of the 200^3
   // Hilbert tensor by 1.6e-10)
-  __shared__ T floor2_s;
+  __shared__ T floor2_s, abs2_s;
   for (int sweep = 0; sweep < 40; ++sweep) {
     {
       const Q4* src = cur ? buf1 : buf0;
@@ -931,12 +936,14 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
       if (sweep == 0 && threadIdx.x == 0) {
         T fro2 = T(0);
         for (int q = 0; q < n; ++q) fro2 += nrm2[cur][q];
-        const T nu = T(n) * ((sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16));
+        const T u = (sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16);
+        const T nu = T(n) * u;
         floor2_s = nu * nu * fro2;
+        abs2_s = T(16) * u * u * fro2;   // (4 u ||R||_F)^2
       }
       __syncthreads();
     }
-    const T floor2 = floor2_s;
+    const T floor2 = floor2_s, abs2 = abs2_s;
     int rotated = 0;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       const Q4* src = cur ? buf1 : buf0;
@@ -947,11 +954,17 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
         T al = nrm2[cur][qa], be = nrm2[cur][qb];
         const T g = warp_sum(A.x0 * Bq.x0 + A.x1 * Bq.x1);
         // the decision and the rotation are the same for the whole warp: lane 0 evaluates them
-        // (divisions and square roots are few and slow in FP64 on this part) and broadcasts
+        // (divisions and square roots are few and slow in FP64 on this part) and broadcasts.
+        // Preconditioned mode: the test is on squares (no square roots), and a pair whose inner
+        // product is within the absolute rounding noise 4 u ||R|| min(|a|, |b|) of the rotated
+        // columns is left alone (such columns cannot be made orthogonal to the relative tolerance;
+        // for a column with |a| >= 1e-5 ||R|| the coupling left is below 4.4e-11)
         T t = T(0), c = T(1), sn = T(0);
         int rot = 0;
-        if (lane == 0 && g != T(0) && (al < be ? al : be) > floor2 &&
-            fabs(g) * jacobi_rsqrt(al) * jacobi_rsqrt(be) > tol) {
+        const T mn = al < be ? al : be;
+        const bool go = piv ? (g * g > tol * tol * al * be && g * g > abs2 * mn)
+                            : (g != T(0) && fabs(g) * jacobi_rsqrt(al) * jacobi_rsqrt(be) > tol);
+        if (lane == 0 && mn > floor2 && go) {
           const T zeta = (be - al) / (T(2) * g);
           const T az = fabs(zeta);
           const T tm = az < T(1e18) ? T(1) / (az + sqrt(fma(az, az, T(1)))) : T(0.5) / az;
@@ -968,8 +981,10 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
           T u;
           u = A.x0; A.x0 = c * u - sn * Bq.x0; Bq.x0 = sn * u + c * Bq.x0;
           u = A.x1; A.x1 = c * u - sn * Bq.x1; Bq.x1 = sn * u + c * Bq.x1;
-          u = A.v0; A.v0 = c * u - sn * Bq.v0; Bq.v0 = sn * u + c * Bq.v0;
-          u = A.v1; A.v1 = c * u - sn * Bq.v1; Bq.v1 = sn * u + c * Bq.v1;
+          if (piv == nullptr) {   // the preconditioned mode outputs the columns, not V
+            u = A.v0; A.v0 = c * u - sn * Bq.v0; Bq.v0 = sn * u + c * Bq.v0;
+            u = A.v1; A.v1 = c * u - sn * Bq.v1; Bq.v1 = sn * u + c * Bq.v1;
+          }
           al = al - t * g;
           be = be + t * g;
           rotated = 1;
@@ -994,14 +1009,155 @@ __device__ __forceinline__ void JacobiSvdOp<T>::body(const Grid g, const Args& a
     if (lane == 0) sig[q] = (q < n) ? sqrt(s) : T(-1);
   }
   __syncthreads();
+  if (piv == nullptr) {
+    for (int q = w; q < n; q += nw) {
+      int rank = 0;
+      for (int k = 0; k < n; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && k < q);
+      const Q4 z = fin[q * 32 + lane];
+      if (lane == 0) sv[rank] = (double)sig[q];
+      if (lane < n) Ub[lane + n * rank] = (double)z.v0;
+      if (lane + 32 < n) Ub[lane + 32 + n * rank] = (double)z.v1;
+    }
+    return;
+  }
+  // Preconditioned mode: X V = U' S with X = R2^T, so the left singular vectors are the rotated
+  // columns divided by their norms.  They are staged in rank order in the free buffer, made
+  // orthonormal by one modified Gram-Schmidt pass in that order (a no-op up to rounding for the
+  // converged columns; columns at the rounding floor are completed with unit vectors), and row l
+  // is written to row piv[l] (U_B = Pi U').
+  T* Us = reinterpret_cast<T*>(cur ? buf0 : buf1);   // [rank][64]
   for (int q = w; q < n; q += nw) {
     int rank = 0;
     for (int k = 0; k < n; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && k < q);
     const Q4 z = fin[q * 32 + lane];
+    const T inv = sig[q] > T(0) ? T(1) / sig[q] : T(0);
     if (lane == 0) sv[rank] = (double)sig[q];
-    if (lane < n) Ub[lane + n * rank] = (double)z.v0;
-    if (lane + 32 < n) Ub[lane + 32 + n * rank] = (double)z.v1;
+    Us[rank * 64 + lane] = z.x0 * inv;
+    Us[rank * 64 + lane + 32] = z.x1 * inv;
   }
+  __syncthreads();
+  if (w == 0) {
+    for (int k = 0; k < n; ++k) {
+      T u0 = Us[k * 64 + lane], u1 = Us[k * 64 + lane + 32];
+      for (int j = 0; j < k; ++j) {
+        const T d = warp_sum(Us[j * 64 + lane] * u0 + Us[j * 64 + lane + 32] * u1);
+        u0 -= d * Us[j * 64 + lane];
+        u1 -= d * Us[j * 64 + lane + 32];
+      }
+      T nn2 = warp_sum(u0 * u0 + u1 * u1);
+      for (int m = 0; m < n && nn2 < T(0.25); ++m) {
+        // complete with e_m minus its projection on the columns before
+        u0 = (lane == m) ? T(1) : T(0);
+        u1 = (lane + 32 == m) ? T(1) : T(0);
+        for (int j = 0; j < k; ++j) {
+          const T d = warp_sum(Us[j * 64 + lane] * u0 + Us[j * 64 + lane + 32] * u1);
+          u0 -= d * Us[j * 64 + lane];
+          u1 -= d * Us[j * 64 + lane + 32];
+        }
+        nn2 = warp_sum(u0 * u0 + u1 * u1);
+      }
+      const T inv = T(1) / sqrt(nn2);
+      Us[k * 64 + lane] = (lane < n) ? u0 * inv : T(0);
+      Us[k * 64 + lane + 32] = (lane + 32 < n) ? u1 * inv : T(0);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int l = e % n, k = e / n;
+    Ub[piv[l] + n * k] = (double)Us[k * 64 + l];
+  }
+}
+
+// Householder QR with column pivoting of an n x n matrix (n <= 64), one CTA: Rin P = Q R2, with
+// R2 upper triangular (written n x n, zeros below the diagonal) and piv[j] the column of Rin in
+// position j.  At step k the column of largest norm over rows k..n-1 moves to position k, and the
+// reflector I - v v^T / (v^T v), v = x - alpha e_1, alpha = -sign(x_1) ||x||, zeroes it below row k.
+template <typename T>
+struct PivQrOp {
+  struct Args {
+    const T* Rin;
+    int n;
+    T* R2;
+    int32_t* piv;
+    const int32_t* gate;
+    int32_t want;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T>
+__device__ __forceinline__ void PivQrOp<T>::body(const Grid g, const Args& args) {
+  if (args.gate != nullptr && *args.gate != args.want) return;
+  constexpr int LD = 65;
+  __shared__ T A[64 * LD];   // column-major, leading dimension 65
+  __shared__ T cn[64];
+  __shared__ int pv[64];
+  __shared__ int jmax_s;
+  const int n = args.n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[(e % n) + LD * (e / n)] = args.Rin[e];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) pv[j] = j;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // norms of the trailing parts of the columns j >= k, one warp per column
+    for (int j = k + w; j < n; j += nw) {
+      T s = T(0);
+      for (int i = k + lane; i < n; i += 32) s += A[i + LD * j] * A[i + LD * j];
+      s = warp_sum(s);
+      if (lane == 0) cn[j] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int jm = k;
+      for (int j = k + 1; j < n; ++j)
+        if (cn[j] > cn[jm]) jm = j;
+      jmax_s = jm;
+    }
+    __syncthreads();
+    const int jm = jmax_s;
+    if (jm != k) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const T t = A[i + LD * k];
+        A[i + LD * k] = A[i + LD * jm];
+        A[i + LD * jm] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int t = pv[k];
+        pv[k] = pv[jm];
+        pv[jm] = t;
+        const T c = cn[k];
+        cn[k] = cn[jm];
+        cn[jm] = c;
+      }
+    }
+    __syncthreads();
+    const T nx2 = cn[k];
+    if (nx2 > T(0) && k < n - 1) {
+      const T x1 = A[k + LD * k];
+      const T alpha = x1 >= T(0) ? -sqrt(nx2) : sqrt(nx2);
+      const T v1 = x1 - alpha;                // v = (v1, A[k+1.., k])
+      const T vtv = nx2 - x1 * x1 + v1 * v1;
+      // apply to the columns j > k, one warp per column
+      for (int j = k + 1 + w; j < n; j += nw) {
+        T s = (lane == 0) ? v1 * A[k + LD * j] : T(0);
+        for (int i = k + 1 + lane; i < n; i += 32) s += A[i + LD * k] * A[i + LD * j];
+        s = warp_sum(s);
+        const T f = T(2) * s / vtv;
+        if (lane == 0) A[k + LD * j] -= f * v1;
+        for (int i = k + 1 + lane; i < n; i += 32) A[i + LD * j] -= f * A[i + LD * k];
+      }
+      __syncthreads();
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + LD * k] = T(0);
+      if (threadIdx.x == 0) A[k + LD * k] = alpha;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    args.R2[e] = (i <= j) ? A[i + LD * j] : T(0);
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) args.piv[j] = pv[j];
 }
 
 template <typename T>
@@ -2006,9 +2162,17 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     rh_status s = launch_tsqr_tree<T>(pl, B, buf0, buf1, use_tsqr, &cur, st, SITE_TRUNC_TSQR);
     if (s != RH_OK) return s;
   }
+  // Preconditioning (Drmac and Veselic): the column-pivoted QR of the tall-skinny triangle,
+  // R P = Q2 R2, makes B^T P = (Q_B Q2) R2 a pivoted QR of B^T, and the one-sided Jacobi on R2^T
+  // then converges in a few sweeps and keeps the small singular values' vectors accurate, where the
+  // Jacobi on the unpivoted R of a graded spectrum runs to its sweep cap.  R2 and the permutation
+  // sit after the two triangle buffers.
+  T* R2 = buf1 + ceil_div(pl.nblk0, pl.fan) * nn;
+  int32_t* piv = reinterpret_cast<int32_t*>(R2 + nn);
+  RH_EMIT(PivQrOp<T>, SITE_TRUNC_PIVQR, 0, 1, 0, cur, n, R2, piv, use_tsqr, 1);
   {
     ProfileScope ps(PROF_JACOBI, 1, st);
-    RH_EMIT(JacobiSvdOp<T>, SITE_TRUNC_JACOBI_SVD, 0, 1, smj, cur, n, Ub, sv, use_tsqr, 1);
+    RH_EMIT(JacobiSvdOp<T>, SITE_TRUNC_JACOBI_SVD, 0, 1, smj, R2, n, Ub, sv, use_tsqr, 1, piv);
   }
   return RH_OK;
 }
@@ -2065,7 +2229,7 @@ rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, con
   RH_LAUNCH_CHECK();
   const int np = (k + 1) & ~1;
   const size_t smj = sizeof(T) * 4 * (size_t)np * 32 * 2;
-  RH_EMIT(JacobiSvdOp<T>, SITE_OTHER, 0, 1, smj, Rk, k, Ub, sv, nullptr, 0);
+  RH_EMIT(JacobiSvdOp<T>, SITE_OTHER, 0, 1, smj, Rk, k, Ub, sv, nullptr, 0, nullptr);
   return RH_OK;
 }
 
