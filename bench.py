@@ -600,7 +600,10 @@ def wl_batched(torch, rh, L, args, device, peaks, src):
     rsthosvd_batched call captured and replayed."""
     from workloads import batch_recipe, lowrank_plus_noise_torch
 
-    rec = [b for b in batch_recipe() if len(b[0]) in (3, 4)]
+    orders = tuple(int(v) for v in args.batch_orders.split(","))
+    rec = [b for b in batch_recipe() if len(b[0]) in orders]
+    if args.batch_count > 0:
+        rec = rec[:args.batch_count]
     Xs = [lowrank_plus_noise_torch(d, r, 0.9, 1e-3, sd, torch.float32, device) for d, r, sd in rec]
     nbytes = sum(4 * x.numel() for x in Xs)
     call = rh.RsthosvdBatchedCall([b[0] for b in rec], [b[1] for b in rec], torch.float32, p=5, seed=4, clamp=True,
@@ -639,7 +642,8 @@ def wl_batched(torch, rh, L, args, device, peaks, src):
     return {"metric": "batched R-STHOSVD throughput (order-3 and order-4 tensors of the batch)",
             "value": round(tps, 1), "unit": "tensors/s", "higher_is_better": True, "dtype": "f32",
             "ms_per_step": round(ms, 3),
-            "config": {"workload": f"{len(Xs)} tensors, order 3-4, sizes U[16,96], ranks U[4,16] capped, low rank + "
+            "config": {"workload": f"{len(Xs)} tensors, order {args.batch_orders}, sizes U[16,96], ranks U[4,16] capped, "
+                                   "low rank + "
                                    f"1e-3 noise, seed 4, p=5 clamped; {nbytes / 1e9:.2f} GB FP32",
                        "engine": "grouped (batched plan)" if args.streams == 0 else f"{args.streams} streams",
                        "graph": True, "l2": "inputs 8 GB (larger than L2); no flush"},
@@ -732,6 +736,10 @@ def main():
                     choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse"],
                     help="dense1024: the benchmark line (default); the others measure the further configurations "
                          "and print one JSON line each")
+    ap.add_argument("--batch-orders", default="3,4",
+                    help="batched workload: tensor orders taken from the 512-tensor recipe (comma list)")
+    ap.add_argument("--batch-count", type=int, default=0,
+                    help="batched workload: first N tensors of those orders (0 = all)")
     ap.add_argument("--streams", type=int, default=0,
                     help="batched workload: 0 = grouped engine (one launch per stage for the batch), "
                          "N >= 1 = N internal streams")
