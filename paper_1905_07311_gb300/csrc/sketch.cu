@@ -451,14 +451,14 @@ __device__ __forceinline__ void SketchReduceOp<T>::body(const Grid g, const Args
     const T* src = part + c * I + i;
     const int64_t step = (int64_t)ell * I;
     int k = w;
-    // two independent chains per lane, combined in a fixed order
-    double s1 = 0.0;
-    for (; k + kRedWarps < S; k += 2 * kRedWarps) {
-      s += (double)src[(int64_t)k * step];
-      s1 += (double)src[(int64_t)(k + kRedWarps) * step];
+    // eight independent chains per lane (loads in flight together), combined in a fixed order
+    double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (; k + 7 * kRedWarps < S; k += 8 * kRedWarps) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) c[j] += (double)src[(int64_t)(k + j * kRedWarps) * step];
     }
-    if (k < S) s += (double)src[(int64_t)k * step];
-    s += s1;
+    for (; k < S; k += kRedWarps) c[0] += (double)src[(int64_t)k * step];
+    s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
   }
   red[w][lane] = s;
   __syncthreads();

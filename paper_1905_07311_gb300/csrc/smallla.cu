@@ -29,6 +29,21 @@ namespace rh {
 
 namespace {
 
+// Asynchronous global -> shared copies (cp.async): 4 or 16 bytes, zero-filled when !ok.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1304,8 +1319,19 @@ __device__ __forceinline__ void SumsqOp::body(const Grid g, const Args& args) {
   double* __restrict__ out = args.out;
 
   __shared__ double scratch[33];
-  double s = 0.0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s = fma(x[e], x[e], s);
+  // eight independent chains per thread (loads in flight together), combined in a fixed order
+  double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const int64_t st = blockDim.x;
+  int64_t e = threadIdx.x;
+  for (; e + 7 * st < n; e += 8 * st) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const double v = x[e + j * st];
+      c[j] = fma(v, v, c[j]);
+    }
+  }
+  for (; e < n; e += st) c[0] = fma(x[e], x[e], c[0]);
+  double s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
   s = block_sum(s, scratch);
   if (threadIdx.x == 0) *out = s;
 }
@@ -1322,6 +1348,7 @@ struct GramCfg {
   static constexpr int NBLK = NB * (NB + 1) / 2;
   static constexpr int THREADS = (NBLK + 31) / 32 * 32;
   static constexpr int LDS = ELLP + 4;
+  static constexpr size_t SMEM = 2 * 128 * LDS * sizeof(float);   // two tiles (dynamic)
 };
 
 // DF = true: every product is formed exactly (p = x y, e = fma(x, y, -p)) and summed in double-float
@@ -1338,7 +1365,7 @@ struct GramBOp {
     double* part;
     const int32_t* gate;
   };
-  static constexpr int kThreads = GramCfg<ELLP>::THREADS, kMinBlocks = 1;
+  static constexpr int kThreads = GramCfg<ELLP>::THREADS, kMinBlocks = 3;
   __device__ static void body(const Grid g, const Args& args);
 };
 template <int ELLP, bool DF>
@@ -1352,7 +1379,7 @@ __device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args
 
   if (gate != nullptr && *gate != 0) return;
   using C = GramCfg<ELLP>;
-  __shared__ __align__(16) float Bs[128 * C::LDS];
+  extern __shared__ __align__(16) float gram_sm[];   // two tiles of 128 x LDS
   const int tid = threadIdx.x;
   int bi = 0, bj = tid;
   while (bi < C::NB && bj >= C::NB - bi) {
@@ -1363,55 +1390,75 @@ __device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args
   const bool active = tid < C::NBLK;
   const int64_t M = L * R;
   const int64_t ntiles = (M + 127) / 128;
-  for (int e = tid; e < 128 * (C::LDS - ell); e += blockDim.x) {
+  for (int e = tid; e < 2 * 128 * (C::LDS - ell); e += blockDim.x) {
     const int w = C::LDS - ell;
-    Bs[(e / w) * C::LDS + ell + e % w] = 0.0f;
+    gram_sm[(e / w) * C::LDS + ell + e % w] = 0.0f;   // padding columns of both tiles
   }
-  double accd[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
-  for (int64_t t = g.bx; t < ntiles; t += g.gx) {
+  // asynchronous copy of tile t into Bs: rows pp = columns p0 + pp of B_(n), zero past M
+  const int nthr = blockDim.x;
+  auto issue = [&](int64_t t, float* Bs) {
     const int64_t p0 = t * 128;
     const int valid = (int)(M - p0 < 128 ? M - p0 : 128);
-    __syncthreads();
     if (L == 1) {
       // the tile is 128 x ell contiguous values starting 512 ell bytes into B: 16-byte aligned
       const float* src = B + (int64_t)ell * p0;
       const int nvalid = valid * ell;
-      for (int e4 = tid; e4 < 32 * ell; e4 += blockDim.x) {
-        const int e = 4 * e4;
-        float v[4];
-        if (e + 3 < nvalid) {
-          const float4 q = __ldg(reinterpret_cast<const float4*>(src) + e4);
-          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) v[k] = (e + k < nvalid) ? src[e + k] : 0.0f;
+      if ((ell & 3) == 0) {
+        const int q4 = ell / 4, dq = nthr / q4, rq = nthr - dq * q4;
+        int pp = tid / q4, cq = tid - pp * q4;
+        for (int e4 = tid; e4 < 32 * ell; e4 += nthr) {
+          const bool ok = 4 * e4 < nvalid;
+          cp_async16(&Bs[pp * C::LDS + 4 * cq], ok ? src + 4 * e4 : B, ok);
+          pp += dq;
+          cq += rq;
+          if (cq >= q4) {
+            cq -= q4;
+            ++pp;
+          }
         }
-        int pp = e / ell, c = e - pp * ell;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          Bs[pp * C::LDS + c] = v[k];
-          if (++c == ell) {
-            c = 0;
+      } else {
+        const int de = nthr / ell, re = nthr - de * ell;
+        int pp = tid / ell, c = tid - pp * ell;
+        for (int e = tid; e < 128 * ell; e += nthr) {
+          const bool ok = e < nvalid;
+          cp_async4(&Bs[pp * C::LDS + c], ok ? src + e : B, ok);
+          pp += de;
+          c += re;
+          if (c >= ell) {
+            c -= ell;
             ++pp;
           }
         }
       }
     } else {
-      for (int pp = tid; pp < 128; pp += blockDim.x) {
-        if (pp < valid) {
-          const int64_t p = p0 + pp;
-          const float* src = B + (p % L) + L * (int64_t)ell * (p / L);
-          for (int c = 0; c < ell; ++c) Bs[pp * C::LDS + c] = src[L * c];
-        } else {
-          for (int c = 0; c < ell; ++c) Bs[pp * C::LDS + c] = 0.0f;
-        }
+      for (int pp = tid; pp < 128; pp += nthr) {
+        const bool ok = pp < valid;
+        const int64_t p = p0 + pp;
+        const float* src = ok ? B + (p % L) + L * (int64_t)ell * (p / L) : B;
+        for (int c = 0; c < ell; ++c) cp_async4(&Bs[pp * C::LDS + c], ok ? src + L * c : B, ok);
       }
     }
+    cp_async_commit();
+  };
+  double accd[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
+  float* bufs[2] = {gram_sm, gram_sm + 128 * C::LDS};
+  int cur = 0;
+  __syncthreads();   // padding written before any tile lands next to it
+  if ((int64_t)g.bx < ntiles) issue(g.bx, bufs[0]);
+  for (int64_t t = g.bx; t < ntiles; t += g.gx) {
+    // the next tile streams in while this one is multiplied
+    if (t + g.gx < ntiles) {
+      issue(t + g.gx, bufs[cur ^ 1]);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncthreads();
+    const float* Bs = bufs[cur];
     if (active) {
       float acc[4][4], err[4][4];
 #pragma unroll
@@ -1449,6 +1496,8 @@ __device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args
 #pragma unroll
         for (int b = 0; b < 4; ++b) accd[a][b] += DF ? (double)acc[a][b] + (double)err[a][b] : (double)acc[a][b];
     }
+    __syncthreads();   // this tile's buffer is refilled two tiles later
+    cur ^= 1;
   }
   if (!active) return;
   double* o = part + (int64_t)g.bx * ell * ell;
@@ -2035,16 +2084,16 @@ rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double*
     using G32 = GramBOp<32, false>;
     using G64 = GramBOp<64, false>;
     if (ell <= 32)
-      RH_EMIT(G32, site, 0, ctas, 0, B, L, R, ell, part, gate);
+      RH_EMIT(G32, site, 0, ctas, GramCfg<32>::SMEM, B, L, R, ell, part, gate);
     else
-      RH_EMIT(G64, site, 0, ctas, 0, B, L, R, ell, part, gate);
+      RH_EMIT(G64, site, 0, ctas, GramCfg<64>::SMEM, B, L, R, ell, part, gate);
   } else {
     // the double-float sums are ALU-bound: blocks of 4 x 4 entries over the columns actually used
     switch ((ell + 7) / 8) {
 #define RH_GDF(E) \
   case E / 8: {                                                           \
     using GE = GramBOp<E, true>;                                          \
-    RH_EMIT(GE, site, 0, ctas, 0, B, L, R, ell, part, gate);              \
+    RH_EMIT(GE, site, 0, ctas, GramCfg<E>::SMEM, B, L, R, ell, part, gate); \
   } break
       RH_GDF(8); RH_GDF(16); RH_GDF(24); RH_GDF(32); RH_GDF(40); RH_GDF(48); RH_GDF(56); RH_GDF(64);
 #undef RH_GDF
