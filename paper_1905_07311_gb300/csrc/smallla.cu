@@ -245,6 +245,7 @@ struct CholOp {
     double* R;
     double* rdiag;
     int32_t* flag;
+    double skip_tol;   // > 0: *flag <- 2 and no factorization when max |C - I| <= skip_tol
   };
   static constexpr int kThreads = kCholThreads, kMinBlocks = 1;
   __device__ static void body(const Grid g, const Args& args);
@@ -258,6 +259,21 @@ __device__ __forceinline__ void CholOp<Ar>::body(const Grid g, const Args& args)
   int32_t* __restrict__ flag = args.flag;
 
   if (*flag) return;
+  if (args.skip_tol > 0.0) {
+    // the Gram matrix of an already orthonormal basis: the second CholeskyQR pass is not needed
+    __shared__ int far_s;
+    if (threadIdx.x == 0) far_s = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e % n, j = e / n;
+      if (i <= j && fabs(C[e] - (i == j ? 1.0 : 0.0)) > args.skip_tol) far_s = 1;
+    }
+    __syncthreads();
+    if (!far_s) {
+      if (threadIdx.x == 0) *flag = 2;
+      return;
+    }
+  }
   using V = typename Ar::V;
   extern __shared__ __align__(16) unsigned char chol_raw[];
   const int ld = n | 1;   // odd leading dimension: 8-byte accesses along a row hit distinct banks
@@ -429,7 +445,7 @@ __device__ __forceinline__ void HouseholderQOp::body(const Grid g, const Args& a
   const int32_t* __restrict__ flag = args.flag;
   int32_t* __restrict__ info = args.info;
 
-  const bool run = (flag == nullptr) || (*flag != 0);
+  const bool run = (flag == nullptr) || (*flag == 1);   // 2: the second pass was skipped
   if (info != nullptr && threadIdx.x == 0) *info = (*info & ~1) | (run ? 1 : 0);
   if (!run) return;
   __shared__ double scratch[33];
@@ -2009,15 +2025,17 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
     // the W region (only the Householder branch uses W, and it reads Y).
     RH_EMIT(GramPartialOp, SITE_ORTH_GRAM, 0, nb, gsm, Y, m, n, rb, Gpart, flag);
     RH_EMIT(GramReduceOp, SITE_ORTH_GRAM_REDUCE, 0, rblocks, 0, Gpart, nb, n, C, flag);
-    RH_EMIT(CholOp<ArithDF>, SITE_ORTH_CHOL, 0, 1, chol_smem(n, sizeof(dfl::F2)), C, n, R, rdiag, flag);
-    RH_EMIT(TrsmRowsOp<double>, SITE_ORTH_TRSM, 0, tblocks, sizeof(double) * ((n | 1) * n + n), Y, m, n, R, rdiag, Q1,
+    // the first pass writes Q itself: when Q_1^T Q_1 is within 1e-6 of I (u_64 kappa(Y)^2 small) the
+    // FP32 second pass is skipped (flag 2) and Q_1 is the result
+    RH_EMIT(CholOp<ArithDF>, SITE_ORTH_CHOL, 0, 1, chol_smem(n, sizeof(dfl::F2)), C, n, R, rdiag, flag, 0.0);
+    RH_EMIT(TrsmRowsOp<double>, SITE_ORTH_TRSM, 0, tblocks, sizeof(double) * ((n | 1) * n + n), Y, m, n, R, rdiag, Q,
             flag);
     float* Q1f = reinterpret_cast<float*>(W);
     float* Q2f = Q1f + m * n;
     const int cblocks = (int)std::min<int64_t>(ceil_div(m * n, 256), 4 * num_sms());
-    RH_EMIT(CastGatedOp<float>, SITE_ORTH_CAST, 0, cblocks, 0, Q1, Q1f, m * n, flag);
+    RH_EMIT(CastGatedOp<float>, SITE_ORTH_CAST, 0, cblocks, 0, Q, Q1f, m * n, flag);
     if ((s = launch_gram_f32(Q1f, m, 1, n, Gpart, C, flag, st, false, SITE_ORTH_GRAM2)) != RH_OK) return s;
-    RH_EMIT(CholOp<ArithF32>, SITE_ORTH_CHOL2, 0, 1, chol_smem(n, sizeof(float)), C, n, R, rdiag, flag);
+    RH_EMIT(CholOp<ArithF32>, SITE_ORTH_CHOL2, 0, 1, chol_smem(n, sizeof(float)), C, n, R, rdiag, flag, 1e-6);
     RH_EMIT(TrsmRowsOp<float>, SITE_ORTH_TRSM2, 0, tblocks, sizeof(float) * ((n | 1) * n + n), Q1f, m, n, R, rdiag,
             Q2f, flag);
     RH_EMIT(CastF2dGatedOp, SITE_ORTH_CAST2, 0, cblocks, 0, Q2f, Q, m * n, flag);
@@ -2029,7 +2047,7 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
       const int so = pass == 0 ? 0 : SITE_ORTH_GRAM2 - SITE_ORTH_GRAM;   // the second pass's sites
       RH_EMIT(GramPartialOp, SITE_ORTH_GRAM + so, 0, nb, gsm, src, m, n, rb, Gpart, flag);
       RH_EMIT(GramReduceOp, SITE_ORTH_GRAM_REDUCE + so, 0, rblocks, 0, Gpart, nb, n, C, flag);
-      RH_EMIT(CholOp<ArithF64>, SITE_ORTH_CHOL + so, 0, 1, chol_smem(n, sizeof(double)), C, n, R, rdiag, flag);
+      RH_EMIT(CholOp<ArithF64>, SITE_ORTH_CHOL + so, 0, 1, chol_smem(n, sizeof(double)), C, n, R, rdiag, flag, 0.0);
       RH_EMIT(TrsmRowsOp<double>, SITE_ORTH_TRSM + so, 0, tblocks, tsm, src, m, n, R, rdiag, dst, flag);
       src = Q1;
       dst = Q;
