@@ -278,11 +278,44 @@ __global__ void split_bf16x2_kernel(const float* __restrict__ x, int64_t n, uint
   }
 }
 
+// ||a + b||^2 of BF16 pieces: head + tail is exact in FP32 (16 significant bits), each square is
+// formed exactly as p + e (p = v v, e = fma(v, v, -p)) and summed in double-float (TwoSum on the
+// high part, the rounding errors and e collected in the low part: ~2^-44 relative), converted to
+// FP64 once per thread -- FP64 itself runs at a small fraction of the FP32 rate on this part.
+// 16-byte loads when both pieces are 16-byte aligned.
 __global__ void pieces_sumsq_kernel(const uint16_t* __restrict__ a, const uint16_t* __restrict__ b, int64_t n,
                                     double* __restrict__ part) {
   __shared__ double red[32];
   double s = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = (reinterpret_cast<uintptr_t>(a) % 16 == 0) && (b == nullptr || reinterpret_cast<uintptr_t>(b) % 16 == 0);
+  int64_t done = 0;
+  if (vec) {
+    float sh = 0.0f, sl = 0.0f;
+    const int64_t n8 = n / 8;
+    for (int64_t q = tid; q < n8; q += nth) {
+      const uint4 ha = __ldg(reinterpret_cast<const uint4*>(a) + q);
+      uint4 hb = make_uint4(0u, 0u, 0u, 0u);
+      if (b) hb = __ldg(reinterpret_cast<const uint4*>(b) + q);
+      const uint32_t wa[4] = {ha.x, ha.y, ha.z, ha.w}, wb[4] = {hb.x, hb.y, hb.z, hb.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t ua = (k & 1) ? (wa[k >> 1] & 0xFFFF0000u) : (wa[k >> 1] << 16);
+        const uint32_t ub = (k & 1) ? (wb[k >> 1] & 0xFFFF0000u) : (wb[k >> 1] << 16);
+        const float v = __fadd_rn(__uint_as_float(ua), __uint_as_float(ub));
+        const float pr = __fmul_rn(v, v);
+        const float pe = fmaf(v, v, -pr);
+        const float t = __fadd_rn(sh, pr);
+        const float bb = __fsub_rn(t, sh);
+        const float se = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(pr, bb));
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(se, pe));
+      }
+    }
+    s = (double)sh + (double)sl;
+    done = n8 * 8;
+  }
+  for (int64_t e = done + tid; e < n; e += nth) {
     double v = (double)tc::bf16_to_f(a[e]);
     if (b) v += (double)tc::bf16_to_f(b[e]);
     s = fma(v, v, s);
