@@ -187,19 +187,24 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
   } else if (warp < 6) {
     // ---------------- Omega generators (warps 2..5) ----------------
     const int t = threadIdx.x - 64;   // 0..127
+    const int p = t & 63;             // column of X_(1) within the chunk (K index)
+    // only the ceil(ell / 4) quads of Omega that reach the output are generated; the N columns
+    // past them are zeroed once in both buffers (their accumulator columns are never read)
+    const int nq = (ell + 3) / 4;
+    for (int b = 0; b < 2; ++b)
+      for (int n = 4 * nq + (t >> 6); n < 64; n += 2) *reinterpret_cast<uint16_t*>(&S.om[b][0] + sw128_off(n, p)) = 0;
     uint32_t oc = 0;
     for (int64_t c = c_begin; c < c_end; c += c_step, ++oc) {
       const uint32_t b = oc & 1;
       if (oc >= 2 && !tc::mbar_wait(&S.om_empty[b], ((oc >> 1) - 1) & 1, err, 4)) break;
       uint8_t* om = &S.om[b][0];
-      const int p = t & 63;           // column of X_(1) within the chunk (K index)
       const int64_t row = c * kPChunk + p;
-      for (int q = t >> 6; q < 16; q += 2) {
+      for (int q = t >> 6; q < nq; q += 2) {
         float4 v = rng::omega4(k0, k1, sid, row, (uint32_t)q);
         const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int n = 4 * q + j;    // column of Omega (N index); rows >= ell are unused but harmless
+          const int n = 4 * q + j;    // column of Omega (N index); columns ell .. 4 nq - 1 are unused
           *reinterpret_cast<uint16_t*>(om + sw128_off(n, p)) = tc::bf16_rne(vv[j]);
         }
       }
