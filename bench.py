@@ -127,6 +127,17 @@ def dist_setup():
     return world, rank, local
 
 
+def job_time_and_value(torch, dist, ms_local, flops_per_rank, world, device):
+    """Whole-job time and throughput over the ranks: every rank decomposes its own tensor (weak
+    scaling), the job takes as long as its slowest rank (max over ranks), and the value counts the
+    work of all ranks.  Returns (ms per step, TFLOP/s); ``dist`` is None for a single process."""
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * flops_per_rank / (ms * 1e-3) / 1e12
+
+
 def make_input(torch, device, seed_offset=0):
     from workloads import lowrank_plus_noise_torch
 
@@ -279,14 +290,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms_step = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item())
-
     flops = algorithmic_flops(DIMS, RANKS, P, RHO)
-    value = world * flops / (ms_step * 1e-3) / 1e12
+    ms_step, value = job_time_and_value(torch, dist if world > 1 else None, e0.elapsed_time(e1) / args.steps, flops,
+                                        world, device)
 
     # ---- dominant kernel and its roofline ----
     per = {}
@@ -338,12 +344,9 @@ def run_ours(args):
             hc.run(Xh)
         f1.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = f0.elapsed_time(f1) / ke
-        te = torch.tensor([ms_e2e], dtype=torch.float64, device=device)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        ms_e2e = float(te.item())
-        e2e = {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+        ms_e2e, v_e2e = job_time_and_value(torch, dist if world > 1 else None, f0.elapsed_time(f1) / ke, flops,
+                                           world, device)
+        e2e = {"value": round(v_e2e, 3), "unit": "TFLOP/s",
                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": hc.h2d_bytes,
                "d2h_bytes_per_step": hc.d2h_bytes}
         del Xh, hc
