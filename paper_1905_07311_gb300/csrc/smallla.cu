@@ -1556,7 +1556,15 @@ __device__ __forceinline__ void GramBReduceOp::body(const Grid g, const Args& ar
   if (e < nn) {
     const int r = e % ell, c = e / ell;
     const int u = r <= c ? e : c + ell * r;
-    for (int k = wp; k < nparts; k += 8) s += part[(int64_t)k * nn + u];
+    // eight independent chains (loads in flight together), combined in a fixed order
+    double ch[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int k = wp;
+    for (; k + 56 < nparts; k += 64) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ch[j] += part[(int64_t)(k + 8 * j) * nn + u];
+    }
+    for (; k < nparts; k += 8) ch[0] += part[(int64_t)k * nn + u];
+    s = ((ch[0] + ch[1]) + (ch[2] + ch[3])) + ((ch[4] + ch[5]) + (ch[6] + ch[7]));
   }
   red[wp][lane] = s;
   __syncthreads();
@@ -2090,7 +2098,9 @@ static void trunc_dims(TruncPlan& pl) {
 
 static int odd_ld(int rows) { return rows | 1; }
 
-int gram_ctas() { return 8 * num_sms(); }
+// one wave of the ell <= 64 Gram kernel (3 CTAs per SM): fewer per-CTA partials (ell^2 doubles each)
+// for the reduce to read, and no tail wave
+int gram_ctas() { return 3 * num_sms(); }
 
 // W = B B^T (ell x ell, FP64, full) of the FP32 (L, ell, R) tensor B: FP32 sums over 128 columns,
 // FP64 across; part holds min(gram_ctas(), ceil(L R / 128)) ell^2 doubles.  Gated on *gate == 0.
