@@ -238,8 +238,9 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
 /*
  * rh_left_svd -- left singular vectors and singular values of the mode-n unfolding B_(n) of a tensor
  * whose mode n is short (I_mode <= RH_MAX_ELL): the thin SVD of Alg. 1 step 4 applied to
- * B = Q^T X.  B_(n)^T is triangularised by a tree of Householder QRs (no Gram matrix) and the
- * I_mode x I_mode triangle is diagonalised by one-sided Jacobi, in B's precision.
+ * B = Q^T X.  B_(n)^T is triangularised by a tree of Householder QRs (no Gram matrix); the
+ * I_mode x I_mode triangle R gets a column-pivoted QR, R P = Q_2 R_2 (Drmac-Veselic
+ * preconditioning), and R_2^T is diagonalised by one-sided Jacobi, all in B's precision.
  *   U   I_mode x I_mode FP64, column-major, columns ordered by decreasing singular value
  *       (column signs arbitrary);  sv  I_mode FP64 singular values, decreasing.
  */
@@ -271,8 +272,9 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
  *     sums) and its pivoted Cholesky factor, kept when that succeeds and sigma_r^2 -
  *     sigma_{r+1}^2 >= 1e-5 sigma_1^2; otherwise W again with every product exact and the
  *     sums in double-float (~2^-44 relative), kept when its Cholesky succeeds; otherwise (and
- *     for FP64 data) B^T = Q_B R by a tall-skinny Householder QR; one-sided Jacobi SVD of the
- *     factor gives U_B;
+ *     for FP64 data) B^T = Q_B R by a tall-skinny Householder QR, R P = Q_2 R_2 by a
+ *     column-pivoted QR and one-sided Jacobi on R_2^T.  In every branch the one-sided
+ *     Jacobi SVD of the final factor gives U_B;
  *     A_n = Q U_B(:, 1:r_n); G <- U_B(:, 1:r_n)^T B.
  */
 size_t rsthosvd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
