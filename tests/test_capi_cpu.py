@@ -211,3 +211,105 @@ def test_svd_route_option(L):
     assert _ws(L, [30, 20, 10], [4, 4, 4], p=5, svd_route=1) > 0
     code, msg = _call_invalid(L, [30, 20, 10], [4, 4, 4], p=5, svd_route=2)
     assert code == 1 and "svd_route" in msg
+
+
+def _err(L):
+    return L.rh_last_error().decode()
+
+
+def test_every_entry_point_validates_before_the_device(L):
+    """Each call below fails on its arguments alone (RH_EINVAL = 1, RH_ENOMEM = 2,
+    RH_EUNSUPPORTED = 6); on this machine any device call would instead give RH_ECUDA = 3."""
+    from paper_1905_07311_gb300 import _lib
+
+    P = ctypes.c_void_p
+    one, big = P(1), 1 << 30
+    d3 = _lib.i64_array([30, 20, 10])
+    ks = _lib.i32_array([4, 4, 4])
+    ptr3 = (P * 3)(1, 1, 1)
+    o = ctypes.byref(_lib.make_options(p=5))
+    r3 = _lib.i32_array([0, 0, 0])
+
+    # thin QR (Alg. 1 step 2): 1 <= n <= min(m, 64)
+    assert L.rh_orthonormalize(4, 5, one, one, None, one, big, None) == 1
+    assert L.rh_orthonormalize(100, 65, one, one, None, one, big, None) == 1
+    assert L.rh_orthonormalize(100, 5, None, one, None, one, big, None) == 1
+    assert L.rh_orthonormalize(100, 5, one, one, None, one, 1, None) == 2
+    assert L.rh_orthonormalize_workspace_size(4, 5) == 0 < L.rh_orthonormalize_workspace_size(100, 5)
+    # mode product (Sec. 2.1)
+    assert L.rh_mode_product(3, d3, 1, one, 3, 4, one, 1, 1, one, None) == 1      # mode out of range
+    assert L.rh_mode_product(3, d3, 1, one, 0, 0, one, 1, 1, one, None) == 1      # k = 0
+    assert L.rh_mode_product(3, d3, 1, None, 0, 4, one, 1, 1, one, None) == 1
+    assert L.rh_mode_product(3, d3, 0, one, 0, 4, one, 1, 1, one, None) == 1      # FP64 in, FP32 out
+    assert L.rh_mode_product_bf16(3, d3, 1, one, 4, one, one, one, big, None) == 1
+    assert L.rh_mode_product_bf16(3, _lib.i64_array([32, 20, 10]), 2, one, 65, one, one, one, big, None) == 6
+    assert L.rh_mode_product_bf16(3, d3, 2, one, 4, one, one, one, big, None) == 6   # I_0 % 8 != 0
+    # left SVD of a short mode (Alg. 1 step 4)
+    assert L.rh_left_svd(3, _lib.i64_array([65, 20, 10]), 1, one, 0, one, one, one, big, None) == 1
+    assert L.rh_left_svd(3, d3, 1, None, 2, one, one, one, big, None) == 1
+    assert L.rh_left_svd(3, d3, 1, one, 2, one, one, one, 1, None) == 2
+    # BF16 split
+    assert L.rh_split_bf16x2(one, -1, one, None) == 1
+    assert L.rh_split_bf16x2(None, 8, one, None) == 1
+    assert L.rh_split_bf16x2(None, 0, None, None) == 0                            # nothing to do
+    # core and direct residual
+    assert L.core_ttm(3, d3, 1, one, ptr3, _lib.i32_array([0, 4, 4]), one, one, big, None) == 1
+    assert L.core_ttm(3, d3, 1, None, ptr3, ks, one, one, big, None) == 1
+    assert L.core_ttm(3, d3, 1, one, ptr3, ks, one, one, 1, None) == 2 and "need" in _err(L)
+    assert L.rh_tucker_residual(3, d3, 1, one, ptr3, ks, None, one, one, big, None) == 1
+    assert L.rh_tucker_residual(3, d3, 1, one, ptr3, ks, one, one, one, 1, None) == 2
+    # adaptive rank (Alg. 4 / 5)
+    assert L.adaptive_rank(3, d3, 1, one, 0.0, 0, 4, ks, o, ptr3, one, r3, None, one, big, None) == 1
+    assert L.adaptive_rank(3, d3, 1, one, 0.1, 2, 4, ks, o, ptr3, one, r3, None, one, big, None) == 1
+    assert L.adaptive_rank(3, d3, 1, one, 0.1, 0, 0, ks, o, ptr3, one, r3, None, one, big, None) == 1
+    assert L.adaptive_rank(3, d3, 2, one, 0.1, 0, 4, ks, o, ptr3, one, r3, None, one, big, None) == 6
+    assert "Alg. 5" in _err(L)
+    assert L.adaptive_rank(3, _lib.i64_array([100, 100, 100]), 1, one, 0.1, 0, 4, _lib.i32_array([60, 4, 4]), o,
+                           ptr3, one, r3, None, one, big, None) == 6
+    assert L.adaptive_rank(3, d3, 1, one, 0.1, 0, 4, ks, o, ptr3, one, r3, None, one, 1, None) == 2
+    # sparse sketch and SP-STHOSVD (Alg. 6)
+    assert L.rhosvd_sketch_coo(3, d3, -1, ptr3, one, 0, 4, 0, 0, one, one, big, None) == 1
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 3, 4, 0, 0, one, one, big, None) == 1
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 65, 0, 0, one, one, big, None) == 1
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 4, 0, 0, one, one, 1, None) == 2
+    strict = _lib.i32_array([4, 4, 5])     # mode 2 (processed last): ell = 10 is not < I_2 = 10
+    assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, strict, o, ptr3, None, one, None, one, big, None) == 1
+    assert "must be < min" in _err(L)
+    assert L.sp_sthosvd_coo_workspace_size(3, d3, 10, strict, o) == 0
+    assert L.sp_sthosvd_coo_workspace_size(3, d3, 10, strict, ctypes.byref(_lib.make_options(p=5, clamp=True))) > 0
+    assert L.sp_sthosvd_coo(3, d3, 10, ptr3, None, ks, o, ptr3, None, one, None, one, big, None) == 1
+    assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, ks, o, ptr3, None, one, None, one, 1, None) == 2
+    # host-buffer R-STHOSVD and R-HOSVD (Alg. 3, Alg. 2)
+    bad = _lib.i32_array([26, 4, 4])       # r_0 + p = 31 > I_0 = 30
+    assert L.rsthosvd_host(3, d3, 1, one, bad, o, ptr3, one, None, one, big, None) == 1
+    assert L.rsthosvd_host(3, d3, 1, None, ks, o, ptr3, one, None, one, big, None) == 1
+    assert L.rsthosvd_host(3, d3, 1, one, ks, o, ptr3, one, None, one, 1, None) == 2
+    assert L.rsthosvd_host_workspace_size(3, d3, 1, ks, o) > L.rsthosvd_workspace_size(3, d3, 1, ks, o)
+    assert L.rhosvd(3, d3, 1, one, bad, o, ptr3, one, None, None, one, big, None) == 1
+    assert L.rhosvd(3, d3, 1, one, ks, o, ptr3, one, None, None, one, 1, None) == 2
+    assert L.rhosvd_sketch_static(3, d3, 1, one, 0, 65, 0, 0, one, None, None) == 1
+    # plans and profiling with nothing to act on
+    assert L.rsthosvd_batched_plan_launches(None) == -1
+    assert L.rsthosvd_batched_plan_run(None, None) == 1
+    L.rsthosvd_batched_plan_destroy(None)
+    assert L.rh_profile_collect(None, None, None, 0) == 0
+
+
+def test_fp8_layout_sizes(L):
+    """Block-scaled E4M3 storage: the mode-1 fibres at a stride ld = I_1 rounded up to 16 bytes,
+    then, from the next 16-byte boundary, one FP32 scale per 128 bytes of storage."""
+    from paper_1905_07311_gb300 import _lib
+
+    def layout(dims):
+        ld, so, ns, by = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        assert L.rh_fp8_layout(len(dims), _lib.i64_array(dims), ctypes.byref(ld), ctypes.byref(so),
+                               ctypes.byref(ns), ctypes.byref(by)) == 0
+        return ld.value, so.value, ns.value, by.value
+
+    ld, so, ns, by = layout([128, 48, 40])
+    assert ld == 128 and so == 128 * 48 * 40 and ns == so // 128 and by == so + 4 * ns
+    ld, so, ns, by = layout([30, 7, 3])        # ragged: 30 -> 32 bytes per fibre, 672 bytes of data
+    assert ld == 32 and so == 672 and ns == 6 and by == 672 + 4 * 6
+    ld, so, ns, by = layout([5, 3])            # 48 bytes of data, one partly used scale block
+    assert ld == 16 and so == 48 and ns == 1 and by == 52
+    assert L.rh_fp8_layout(3, _lib.i64_array([128, 0, 40]), None, None, None, None) == 1
