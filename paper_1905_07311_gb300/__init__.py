@@ -13,7 +13,8 @@ from . import _lib
 from ._lib import RH_F32, RH_F64, RhError, check, i32_array, i64_array, lib, make_options
 
 __all__ = ["fp8_layout", "omega", "rhosvd_sketch", "orthonormalize", "mode_product", "left_svd", "core_ttm", "tucker_residual",
-           "rsthosvd", "rhosvd", "rsthosvd_batched", "RsthosvdBatchedCall", "RhError", "version"]
+           "rsthosvd", "rhosvd", "rsthosvd_batched", "RsthosvdBatchedCall", "srrqr_select", "sp_sthosvd_coo",
+           "rhosvd_sketch_coo", "RhError", "version"]
 
 
 def _torch():
@@ -420,6 +421,21 @@ def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0):
     check(lib().rhosvd_sketch_coo(d, da, nnz, iptr, _ptr(vals), int(mode), int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                   int(tensor_id), _ptr(Y), _ptr(ws), ws_bytes, _stream(vals.device)))
     return Y
+
+
+def srrqr_select(Q, eta=2.0):
+    """Row selection and A = Q (P^T Q)^{-1} of Alg. 6 steps 6-7 for a host FP64 tensor Q (I x ell),
+    computed by the library's host step (no device call).  Returns (selected int32 tensor, increasing;
+    A as an (ell, I) FP64 tensor holding the column-major I x ell A)."""
+    torch = _torch()
+    if Q.device.type != "cpu" or Q.dtype != torch.float64 or Q.dim() != 2:
+        raise ValueError("Q must be a 2-D float64 host tensor")
+    I, ell = (int(v) for v in Q.shape)
+    Qf = Q.t().contiguous()            # (ell, I) row-major = I x ell column-major
+    sel = torch.empty(ell, dtype=torch.int32)
+    A = torch.empty((ell, I), dtype=torch.float64)
+    check(lib().rh_srrqr_select(I, ell, _ptr(Qf), float(eta), _ptr(sel), _ptr(A)))
+    return sel, A
 
 
 class SpTucker(Tucker):

@@ -237,6 +237,10 @@ rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, do
         best = i;
       }
     }
+    if (best < 0) {   // every remaining norm is NaN
+      set_error("SP-STHOSVD: Q holds non-finite values");
+      return RH_ENUMERIC;
+    }
     taken[best] = 1;
     sel.push_back((int)best);
     // Householder reflector of W[s:, best], applied to every column
@@ -615,6 +619,23 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
     if ((s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
   }
   RH_CUDA_TRY(cudaStreamSynchronize(st));
+  return RH_OK;
+}
+
+rh_status rh_srrqr_select(int64_t I, int32_t ell, const double* Q, double eta, int32_t* selected, double* A) {
+  clear_error();
+  RH_CHECK_ARG(I >= 1 && ell >= 1 && ell <= I, "need 1 <= ell <= I");
+  RH_CHECK_ARG(I <= (int64_t(1) << 31) - 1 && (uint64_t)I * (uint64_t)ell <= (uint64_t(1) << 40),
+               "I x ell too large for the host selection");
+  RH_CHECK_ARG(eta >= 1.0, "eta must be >= 1");
+  RH_CHECK_ARG(Q != nullptr && selected != nullptr && A != nullptr, "Q, selected and A must be non-NULL");
+  const std::vector<double> Qh(Q, Q + (size_t)I * ell);
+  std::vector<int> sel;
+  std::vector<double> Ah;
+  const rh_status s = srrqr_select_host(Qh, I, ell, eta, sel, Ah);
+  if (s != RH_OK) return s;
+  for (int a = 0; a < ell; ++a) selected[a] = sel[a];
+  std::copy(Ah.begin(), Ah.end(), A);
   return RH_OK;
 }
 
