@@ -424,6 +424,9 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
  *   order (FP32 sums over at most 512 entries, FP64 above): the result is deterministic.  The call
  *   synchronises ``stream`` once (the work split is built on the host from the row counts).
  *   Needs nnz < 2^31 and every I_n < 2^31; ell <= 64.  Workspace: rhosvd_sketch_coo_workspace_size.
+ *   Indices of mode ``mode`` outside [0, I_mode) are counted on the device and the call returns
+ *   RH_EINVAL after its synchronisation (Y undefined); they are never used as addresses.  Indices of
+ *   the other modes only select rows of Omega and are not checked.
  */
 size_t rhosvd_sketch_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, int32_t mode, int32_t ell);
 rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
@@ -447,6 +450,8 @@ rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, con
  *               ||X||^2 and ||G||^2.
  *   The selection runs on the host in FP64; the call synchronises ``stream`` several times per
  *   mode and returns when the result is complete.  Workspace: sp_sthosvd_coo_workspace_size.
+ *   An index outside [0, I_n) is detected when mode n's nonzeros are counted (before any kernel
+ *   addresses memory with it) and the call returns RH_EINVAL; the outputs are then undefined.
  */
 size_t sp_sthosvd_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks,
                                      const rh_options* opts);

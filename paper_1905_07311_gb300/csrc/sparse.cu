@@ -39,9 +39,13 @@ __global__ void iota_kernel(int32_t* __restrict__ a, int64_t n) {
     a[e] = (int32_t)e;
 }
 
-__global__ void count_kernel(const int32_t* __restrict__ key, int64_t n, int32_t* __restrict__ cnt) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[key[e]], 1);
+// Row counts of the keys; a key outside [0, I) is counted in cnt[I] (the host turns that into
+// RH_EINVAL before any kernel uses the key as an address).
+__global__ void count_kernel(const int32_t* __restrict__ key, int64_t n, int64_t I, int32_t* __restrict__ cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = key[e];
+    atomicAdd(&cnt[(k >= 0 && k < I) ? (int64_t)k : I], 1);
+  }
 }
 
 struct SpIdx {
@@ -377,12 +381,17 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int ell, 
     RH_LAUNCH_CHECK();
     RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, key, b.keys_out, b.perm_in, b.perm_out,
                                                 (int)cnnz, 0, bits_for(I), st));
-    count_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, b.cnt);
+    count_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, I, b.cnt);
     RH_LAUNCH_CHECK();
   }
-  std::vector<int32_t> cnt(I);
-  RH_CUDA_TRY(cudaMemcpyAsync(cnt.data(), b.cnt, sizeof(int32_t) * I, cudaMemcpyDeviceToHost, st));
+  std::vector<int32_t> cnt(I + 1);
+  RH_CUDA_TRY(cudaMemcpyAsync(cnt.data(), b.cnt, sizeof(int32_t) * (I + 1), cudaMemcpyDeviceToHost, st));
   RH_CUDA_TRY(cudaStreamSynchronize(st));
+  if (cnt[I] != 0) {
+    set_error("invalid argument: " + std::to_string(cnt[I]) + " indices of mode " + std::to_string(n) +
+              " lie outside [0, " + std::to_string(I) + ")");
+    return RH_EINVAL;
+  }
   // (b) work items: each row's run cut into pieces of at most kItem nonzeros
   std::vector<int3> items;
   std::vector<int32_t> row_items(I + 1, 0);

@@ -118,3 +118,23 @@ def test_sp_sthosvd_exact_recovery(rh):
     A = [f.cpu().numpy().T.copy() for f in T.factors]
     G = np.reshape(T.core.cpu().numpy(), T.core_dims, order="F")
     assert rel_error(X.astype(np.float64), G, A) <= 1e-5
+
+
+@pytest.mark.parametrize("bad", [30, -1])
+def test_out_of_range_index_is_an_error(rh, bad):
+    """An index outside [0, I_n) of the mode being counted is reported (RH_EINVAL) instead of being
+    used as an address; the context stays usable."""
+    dims = [30, 20, 10]
+    idx, vals = zipf_coo(dims, 2000, 1.1, 3.0, seed=45)
+    idx = idx.copy()
+    idx[17, 0] = bad
+    cols, v = coo_dev(idx, vals)
+    with pytest.raises(rh.RhError, match="outside"):
+        rh.rhosvd_sketch_coo(cols, v, dims, 0, 8, seed=1)
+    with pytest.raises(rh.RhError, match="outside"):
+        rh.sp_sthosvd_coo(cols, v, dims, [3, 3, 3], p=2, seed=1)
+    idx[17, 0] = 0
+    cols, v = coo_dev(idx, vals)
+    Y = rh.rhosvd_sketch_coo(cols, v, dims, 0, 8, seed=1)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Y).all()
