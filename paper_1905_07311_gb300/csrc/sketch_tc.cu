@@ -357,7 +357,8 @@ rh_status get_encoder(EncodeTiledFn* fn) {
   if (!g_enc) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q);
+    // the cuTensorMapEncodeTiled ABI as introduced in CUDA 12.0
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
       set_error("cuTensorMapEncodeTiled is not available from the driver");
       return RH_ECUDA;

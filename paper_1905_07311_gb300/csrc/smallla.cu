@@ -156,7 +156,6 @@ struct ArithF64 {
   static constexpr float kPivot = 1e-14f;
   __device__ static V from(double d) { return d; }
   __device__ static double to(V v) { return v; }
-  __device__ static V zero() { return 0.0; }
   __device__ static V mul(V a, V b) { return a * b; }
   __device__ static V fms(V x, V a, V b) { return fma(-a, b, x); }   // x - a b
   __device__ static V rsq(V x) { return rsqrt(x); }
@@ -170,7 +169,6 @@ struct ArithF32 {
   static constexpr float kPivot = 1e-5f;
   __device__ static V from(double d) { return (float)d; }
   __device__ static double to(V v) { return (double)v; }
-  __device__ static V zero() { return 0.0f; }
   __device__ static V mul(V a, V b) { return a * b; }
   __device__ static V fms(V x, V a, V b) { return fmaf(-a, b, x); }
   __device__ static V rsq(V x) { return rsqrtf(x); }
@@ -183,7 +181,6 @@ struct ArithDF {
   static constexpr float kPivot = 1e-14f;
   __device__ static V from(double d) { return dfl::from_double(d); }
   __device__ static double to(V v) { return dfl::to_double(v); }
-  __device__ static V zero() { return V{0.0f, 0.0f}; }
   __device__ static V mul(V a, V b) { return dfl::mul(a, b); }
   __device__ static V fms(V x, V a, V b) { return dfl::fms(x, a, b); }
   __device__ static V rsq(V x) { return dfl::rsqrt(x); }

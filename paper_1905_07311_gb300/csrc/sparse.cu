@@ -532,7 +532,6 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
   Arena ar(workspace);
   SpBufs b = carve_sp(ar, order, z);
   cudaStream_t st = (cudaStream_t)stream;
-  const uint32_t k0 = (uint32_t)(o.seed & 0xFFFFFFFFu), k1 = (uint32_t)(o.seed >> 32);
 
   // the working copy of the tensor (set 0) and ||X||^2
   for (int k = 0; k < order; ++k)
