@@ -10,6 +10,8 @@ Each function follows the algorithm it names step by step, in the paper's order:
 * ``adaptive_rhosvd``    Alg. 4,  ``adaptive_rsthosvd`` Alg. 5
 * ``srrqr_select``       strong RRQR subset selection with eta = 2 (Alg. 6, step 4)
 * ``sp_sthosvd``         Alg. 6 (SP-STHOSVD), dense or COO input
+* ``sp_hosvd``           SP-HOSVD, Alg. 6 with independent modes (Sec. 5 remark 1)
+* ``randsvd(q=...)``     Alg. 1 with randomized subspace iteration (Sec. 5 remark 2, Sec. 6)
 
 Library primitives used as single steps: numpy matmul, ``numpy.linalg.qr``
 (Householder), ``numpy.linalg.svd``, ``scipy.linalg.qr`` with column pivoting.
@@ -87,14 +89,25 @@ def canon_qr(Y):
 # ---------------------------------------------------------------------------------
 # Alg. 1 -- RandSVD
 # ---------------------------------------------------------------------------------
-def randsvd(Xm, r, Omega):
+def randsvd(Xm, r, Omega, q=0):
     """Alg. 1: Y = X Omega; Y = QR; B = Q^T X; B = U_B S V^T; U = Q U_B(:, 1:r).
+
+    ``q`` > 0 adds q steps of randomized subspace iteration to the range finder (the variant
+    named in Sec. 5's remark on range finding and used with q = 1 for the Olivetti data in
+    Sec. 6; Halko, Martinsson and Tropp 2011, Alg. 4.3): Q spans (X X^T)^q X Omega.  Read here
+    in the re-orthonormalised form of the same reference (a thin QR after every application of
+    X^T and of X), which spans the same subspace in exact arithmetic and keeps the directions
+    below sigma_1 * u^(1/(2q+1)) that the plain power loses.
 
     Column signs of Q and of U follow ``canon_signs``; the flip of U's column k is
     applied to U_B(:, k) and V(:, k) as well, so U S V^T is unchanged.
     """
     Y = Xm @ Omega                                  # step 1
     Q = canon_qr(Y)                                 # step 2 (thin, Householder)
+    for _ in range(int(q)):                         # subspace iteration
+        W = canon_qr(Xm.T @ Q)
+        Y = Xm @ W
+        Q = canon_qr(Y)
     B = Q.T @ Xm                                    # step 3
     Ub, s, Vt = np.linalg.svd(B, full_matrices=False)   # step 4
     U = Q @ Ub[:, :r]                               # step 5
@@ -137,8 +150,9 @@ def sthosvd(X, ranks, rho=None):
 # ---------------------------------------------------------------------------------
 # Alg. 2 / Alg. 3
 # ---------------------------------------------------------------------------------
-def rhosvd(X, ranks, p, seed, tensor_id=0, omega_round=None, clamp=False, record=False):
-    """Alg. 2 (R-HOSVD): RandSVD of every X_(j) with its own Omega_j, then G = X x_j A_j^T."""
+def rhosvd(X, ranks, p, seed, tensor_id=0, omega_round=None, clamp=False, record=False, q=0):
+    """Alg. 2 (R-HOSVD): RandSVD of every X_(j) with its own Omega_j, then G = X x_j A_j^T.
+    ``q``: subspace-iteration steps of every RandSVD (see ``randsvd``)."""
     X = np.asarray(X, dtype=np.float64)
     d = X.ndim
     N = X.size
@@ -149,7 +163,7 @@ def rhosvd(X, ranks, p, seed, tensor_id=0, omega_round=None, clamp=False, record
         M = N // I
         ell = _ell(ranks[n], p, I, M, clamp)
         Om = omega_matrix(seed, tensor_id, n, M, ell, omega_round)     # step 2
-        U, s, V, info = randsvd(unfold(X, n), min(ranks[n], ell), Om)     # step 3
+        U, s, V, info = randsvd(unfold(X, n), min(ranks[n], ell), Om, q)  # step 3
         A[n] = U                                                         # step 4
         recs.append(dict(mode=n, ell=ell, **info))
     G = multi_ttm(X, A, transpose=True)                                 # step 6
@@ -160,13 +174,14 @@ def rhosvd(X, ranks, p, seed, tensor_id=0, omega_round=None, clamp=False, record
 
 
 def rsthosvd(X, ranks, p, seed, rho=None, tensor_id=0, omega_round=None, clamp=False, record=False,
-             truncate=True):
+             truncate=True, q=0):
     """Alg. 3 (R-STHOSVD).
 
     G = X; for j = 1..d: Omega_{rho_j} over the current other-mode extent;
     [U, S, V] = RandSVD(G_(rho_j), r, p, Omega); A_{rho_j} = U; G_(rho_j) <- S V^T.
     ``truncate=False`` stops RandSVD after step 3: A_{rho_j} = Q, G_(rho_j) <- Q^T G_(rho_j)
-    (the untruncated core G = X x_1 Q_1^T ... of the range finder).
+    (the untruncated core G = X x_1 Q_1^T ... of the range finder).  ``q``: subspace-iteration
+    steps of every RandSVD, on the current core's unfolding (see ``randsvd``).
     """
     X = np.asarray(X, dtype=np.float64)
     d = X.ndim
@@ -187,12 +202,15 @@ def rsthosvd(X, ranks, p, seed, rho=None, tensor_id=0, omega_round=None, clamp=F
             Gm = unfold(G, n)
             Y = Gm @ Om
             Q = canon_qr(Y)
+            for _ in range(int(q)):
+                Y = Gm @ canon_qr(Gm.T @ Q)
+                Q = canon_qr(Y)
             A[n] = Q
             shape[n] = ell
             G = fold(Q.T @ Gm, n, shape)
             recs.append(dict(mode=n, ell=ell, Y=Y, Q=Q, sv_B=np.linalg.svd(Q.T @ Gm, compute_uv=False)))
             continue
-        U, s, V, info = randsvd(unfold(G, n), r, Om)                     # step 4
+        U, s, V, info = randsvd(unfold(G, n), r, Om, q)                  # step 4
         A[n] = U                                                         # step 5
         shape[n] = r
         G = fold(s[:, None] * V.T, n, shape)                             # step 6
@@ -375,6 +393,32 @@ def sp_sthosvd(X, ranks, p, seed, rho=None, tensor_id=0, eta=2.0, record=False):
     if record:
         out["records"] = recs
     return out
+
+
+def sp_hosvd(X, ranks, p, seed, tensor_id=0, eta=2.0):
+    """SP-HOSVD (Sec. 5, first remark after Alg. 6): the modes of Alg. 6 handled independently.
+
+    For every mode j of the input: Y = X_(j) Omega_j; Y = QR; P_j by strong RRQR on Q^T;
+    A_j = Q (P_j^T Q)^{-1}.  The core is G = X x_1 P_1^T ... x_d P_d^T, the entries of X at the
+    selected coordinates.  Alg. 6's strict size rule r_j + p < min(I_j, prod_{i != j} I_i) on the
+    input sizes; Omega_j is the stream of R-HOSVD's mode j.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    d = X.ndim
+    A = [None] * d
+    sel = [None] * d
+    for n in range(d):
+        I = X.shape[n]
+        M = X.size // I
+        ell = _ell(ranks[n], p, I, M, clamp=False, strict=True)
+        Om = omega_matrix(seed, tensor_id, n, M, ell)
+        Y = unfold(X, n) @ Om
+        Q, _ = np.linalg.qr(Y)
+        P = srrqr_select(Q, eta)
+        A[n] = Q @ np.linalg.inv(Q[P, :])
+        sel[n] = P
+    G = X[np.ix_(*sel)]
+    return {"core": G, "factors": A, "selected": sel}
 
 
 def _kolda_rows(idx, dims, n):
