@@ -461,23 +461,29 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
                          size_t workspace_bytes, void* stream);
 
 /*
- * rh_srrqr_select -- the row selection and interpolatory factor of Alg. 6 steps 6-7 on one
- * orthonormal basis, the host step that sp_sthosvd_coo runs for each mode (exposed for callers that
- * form Q themselves, and for testing).  Host memory only; no device call.
+ * rh_subset_select -- the row selection and interpolatory factor of Alg. 6 steps 6-7 on one basis:
+ * the host step that sp_sthosvd_coo runs for each mode (with RH_SELECT_SRRQR, eta = 2), and the
+ * other selections of Sec. 5's remark on subset selection.  Host memory only; no device call.
  *   Q         host, I x ell FP64 column-major (full column rank; sp_sthosvd_coo passes the thin-QR
  *             factor of the sketch).  Not modified.
- *   eta       strong-RRQR bound, >= 1 (sp_sthosvd_coo uses 2): the result has |A_ij| <= eta on
- *             every unselected row (or 100000 swaps were made).
- *   selected  host, ell int32 receiving P, the chosen rows of Q, increasing.  Selection: column-
- *             pivoted Householder QR of Q^T (largest remaining column norm, lowest index on ties),
- *             then, while some unselected |A_ij| > eta, row i replaces selected row j for the largest
- *             |A_ij| (lowest (i, j) on ties).
+ *   method    RH_SELECT_SRRQR: column-pivoted Householder QR of Q^T (largest remaining column norm,
+ *               lowest index on ties), then, while some unselected |A_ij| > eta, row i replaces
+ *               selected row j for the largest |A_ij| (lowest (i, j) on ties; at most 100000
+ *               swaps), so |A_ij| <= eta on every unselected row;
+ *             RH_SELECT_CPQR: the pivots of that column-pivoted QR alone (no bound on A);
+ *             RH_SELECT_DEIM: the DEIM greedy (Chaturantabut-Sorensen; Sorensen-Embree): the largest
+ *               |Q(i, 0)|, then for j = 1 .. ell-1 the largest |r_i| of r = Q(:, j) - Q(:, 0:j) c with
+ *               Q(P, 0:j) c = Q(P, j) (lowest index on ties).
+ *   eta       strong-RRQR bound, >= 1 (RH_SELECT_SRRQR only).
+ *   selected  host, ell int32 receiving P, the chosen rows of Q, increasing.
  *   A         host, I x ell FP64 column-major receiving A = Q (P^T Q)^{-1}, with the rows P stored as
  *             the exact identity.
- *   RH_EINVAL: ell < 1, ell > I, eta < 1, NULL pointers.  RH_ENUMERIC: P^T Q singular, or Q holds
- *   non-finite values that stop the pivoting.
+ *   RH_EINVAL: ell < 1, ell > I, unknown method, eta < 1 with RH_SELECT_SRRQR, NULL pointers.
+ *   RH_ENUMERIC: P^T Q singular, a vanishing DEIM residual, or non-finite values in Q.
  */
-rh_status rh_srrqr_select(int64_t I, int32_t ell, const double* Q, double eta, int32_t* selected, double* A);
+enum { RH_SELECT_SRRQR = 0, RH_SELECT_CPQR = 1, RH_SELECT_DEIM = 2 };
+rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, int32_t* selected,
+                           double* A);
 
 /*
  * rsthosvd_host -- the same R-STHOSVD with HOST buffers: enqueues the copy of X to the

@@ -8,7 +8,8 @@ Each function follows the algorithm it names step by step, in the paper's order:
 * ``rsthosvd``           Alg. 3 (R-STHOSVD)
 * ``adapt_range_finder`` Sec. 4 (blocked randomized QB with an error indicator)
 * ``adaptive_rhosvd``    Alg. 4,  ``adaptive_rsthosvd`` Alg. 5
-* ``srrqr_select``       strong RRQR subset selection with eta = 2 (Alg. 6, step 4)
+* ``srrqr_select``       strong RRQR subset selection with eta = 2 (Alg. 6, step 4);
+  ``cpqr_select``, ``deim_select`` the other selections of Sec. 5
 * ``sp_sthosvd``         Alg. 6 (SP-STHOSVD), dense or COO input
 * ``sp_hosvd``           SP-HOSVD, Alg. 6 with independent modes (Sec. 5 remark 1)
 * ``randsvd(q=...)``     Alg. 1 with randomized subspace iteration (Sec. 5 remark 2, Sec. 6)
@@ -337,6 +338,28 @@ def adaptive_rsthosvd(X, eps, b, p, seed, rho=None, tensor_id=0, max_ranks=None,
 # ---------------------------------------------------------------------------------
 # Sec. 5 -- structure-preserving STHOSVD
 # ---------------------------------------------------------------------------------
+def cpqr_select(Q):
+    """Subset selection by column-pivoted QR of Q^T alone (Sec. 5 remark 3): the first ell pivots of
+    scipy's pivoted Householder QR, sorted.  No bound on |A_ij| (it can fail on adversarial inputs)."""
+    ell = Q.shape[1]
+    _, _, piv = scipy.linalg.qr(Q.T, pivoting=True, mode="economic")
+    return np.array(sorted(int(x) for x in piv[:ell]), dtype=np.int64)
+
+
+def deim_select(Q):
+    """Subset selection by DEIM (Sec. 5 selection operators; Chaturantabut and Sorensen 2010,
+    Sorensen and Embree 2016): p_1 = argmax |Q(:, 1)|; for j = 2..ell interpolate column j at the
+    indices so far, Q(P, 1:j-1) c = Q(P, j), and take p_j = argmax |Q(:, j) - Q(:, 1:j-1) c|
+    (first index on ties).  Returns the indices sorted."""
+    I, ell = Q.shape
+    p = [int(np.argmax(np.abs(Q[:, 0])))]
+    for j in range(1, ell):
+        c = np.linalg.solve(Q[p, :j], Q[p, j])
+        r = Q[:, j] - Q[:, :j] @ c
+        p.append(int(np.argmax(np.abs(r))))
+    return np.array(sorted(p), dtype=np.int64)
+
+
 def srrqr_select(Q, eta=2.0, max_swaps=100000):
     """Strong RRQR subset selection on Q^T (Alg. 6, step 4) with k = ell = rank.
 

@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import RH_F32, RH_F64, RhError, check, i32_array, i64_array, lib, make_options
 
 __all__ = ["fp8_layout", "omega", "rhosvd_sketch", "orthonormalize", "mode_product", "left_svd", "core_ttm", "tucker_residual",
-           "rsthosvd", "rhosvd", "rsthosvd_batched", "RsthosvdBatchedCall", "srrqr_select", "sp_sthosvd_coo",
+           "rsthosvd", "rhosvd", "rsthosvd_batched", "RsthosvdBatchedCall", "subset_select", "sp_sthosvd_coo",
            "rhosvd_sketch_coo", "RhError", "version"]
 
 
@@ -423,18 +423,24 @@ def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0):
     return Y
 
 
-def srrqr_select(Q, eta=2.0):
+SELECT_METHODS = {"srrqr": 0, "cpqr": 1, "deim": 2}
+
+
+def subset_select(Q, method="srrqr", eta=2.0):
     """Row selection and A = Q (P^T Q)^{-1} of Alg. 6 steps 6-7 for a host FP64 tensor Q (I x ell),
-    computed by the library's host step (no device call).  Returns (selected int32 tensor, increasing;
-    A as an (ell, I) FP64 tensor holding the column-major I x ell A)."""
+    computed by the library's host step (no device call).  ``method``: "srrqr" (strong RRQR with
+    bound ``eta``, the one SP-STHOSVD uses), "cpqr" (column-pivoted QR alone) or "deim".  Returns
+    (selected int32 tensor, increasing; A as an (ell, I) FP64 tensor holding the column-major I x ell A)."""
     torch = _torch()
     if Q.device.type != "cpu" or Q.dtype != torch.float64 or Q.dim() != 2:
         raise ValueError("Q must be a 2-D float64 host tensor")
+    if method not in SELECT_METHODS:
+        raise ValueError(f"method must be one of {sorted(SELECT_METHODS)}")
     I, ell = (int(v) for v in Q.shape)
     Qf = Q.t().contiguous()            # (ell, I) row-major = I x ell column-major
     sel = torch.empty(ell, dtype=torch.int32)
     A = torch.empty((ell, I), dtype=torch.float64)
-    check(lib().rh_srrqr_select(I, ell, _ptr(Qf), float(eta), _ptr(sel), _ptr(A)))
+    check(lib().rh_subset_select(I, ell, _ptr(Qf), SELECT_METHODS[method], float(eta), _ptr(sel), _ptr(A)))
     return sel, A
 
 

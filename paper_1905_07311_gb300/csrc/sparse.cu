@@ -169,7 +169,7 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int n, double*
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * num_sms())); }
 
-// ---- host: strong RRQR subset selection on Q^T (FP64) ----------------------------------------
+// ---- host: subset selection on Q (FP64): strong RRQR, column-pivoted QR, DEIM ------------------
 // inv (ell x ell, column-major) of the rows sel of Q (I x ell, column-major); false if singular
 bool invert_rows(const std::vector<double>& Q, int64_t I, int ell, const std::vector<int>& sel,
                  std::vector<double>& inv) {
@@ -220,14 +220,14 @@ void apply_inv(const std::vector<double>& Q, int64_t I, int ell, const std::vect
     }
 }
 
-rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, double eta, std::vector<int>& sel_out,
-                            std::vector<double>& A) {
-  // column-pivoted Householder QR of Q^T (ell x I): column i of W is row i of Q
+// Column-pivoted Householder QR of Q^T (ell x I; column i is row i of Q): the ell pivots, in order
+// (largest remaining column norm, lowest index on ties).
+rh_status cpqr_rows_host(const std::vector<double>& Q, int64_t I, int ell, std::vector<int>& sel) {
   std::vector<double> W((size_t)ell * I);
   for (int64_t i = 0; i < I; ++i)
     for (int c = 0; c < ell; ++c) W[c + (size_t)ell * i] = Q[i + I * c];
   std::vector<char> taken(I, 0);
-  std::vector<int> sel;
+  sel.clear();
   std::vector<double> v(ell);
   for (int s = 0; s < ell; ++s) {
     int64_t best = -1;
@@ -242,7 +242,7 @@ rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, do
       }
     }
     if (best < 0) {   // every remaining norm is NaN
-      set_error("SP-STHOSVD: Q holds non-finite values");
+      set_error("subset selection: Q holds non-finite values");
       return RH_ENUMERIC;
     }
     taken[best] = 1;
@@ -266,11 +266,87 @@ rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, do
       for (int a = s; a < ell; ++a) W[a + (size_t)ell * i] -= f * v[a];
     }
   }
-  // swaps while some |A_ij| > eta on an unselected row (largest first, lowest (i, j) on ties)
-  std::vector<double> inv;
+  return RH_OK;
+}
+
+// Solves the j x j system M c = b in place (M column-major, Gaussian elimination with partial
+// pivoting); false if a pivot is zero or not finite.
+bool solve_small(std::vector<double>& M, int j, std::vector<double>& b) {
+  for (int c = 0; c < j; ++c) {
+    int pr = c;
+    for (int a = c + 1; a < j; ++a)
+      if (std::fabs(M[a + (size_t)j * c]) > std::fabs(M[pr + (size_t)j * c])) pr = a;
+    const double pv = M[pr + (size_t)j * c];
+    if (pv == 0.0 || !std::isfinite(pv)) return false;
+    if (pr != c) {
+      for (int k = 0; k < j; ++k) std::swap(M[c + (size_t)j * k], M[pr + (size_t)j * k]);
+      std::swap(b[c], b[pr]);
+    }
+    for (int a = c + 1; a < j; ++a) {
+      const double f = M[a + (size_t)j * c] / pv;
+      if (f == 0.0) continue;
+      for (int k = c; k < j; ++k) M[a + (size_t)j * k] -= f * M[c + (size_t)j * k];
+      b[a] -= f * b[c];
+    }
+  }
+  for (int c = j - 1; c >= 0; --c) {
+    double t = b[c];
+    for (int k = c + 1; k < j; ++k) t -= M[c + (size_t)j * k] * b[k];
+    b[c] = t / M[c + (size_t)j * c];
+  }
+  return true;
+}
+
+// DEIM (Chaturantabut and Sorensen 2010; Sorensen and Embree 2016): the first index is the largest
+// |Q(i, 0)|; index j is the largest |r| of the residual r = Q(:, j) - Q(:, 0:j) c of interpolating
+// column j at the indices chosen so far, Q(P, 0:j) c = Q(P, j) (lowest index on ties).
+rh_status deim_rows_host(const std::vector<double>& Q, int64_t I, int ell, std::vector<int>& sel) {
+  sel.clear();
+  std::vector<double> M, c;
+  for (int j = 0; j < ell; ++j) {
+    const double* qj = &Q[(size_t)I * j];
+    std::vector<double> r(qj, qj + I);
+    if (j > 0) {
+      M.assign((size_t)j * j, 0.0);
+      c.assign(j, 0.0);
+      for (int a = 0; a < j; ++a) {
+        for (int k = 0; k < j; ++k) M[a + (size_t)j * k] = Q[sel[a] + (size_t)I * k];
+        c[a] = qj[sel[a]];
+      }
+      if (!solve_small(M, j, c)) {
+        set_error("subset selection: DEIM met a singular interpolation matrix (Q is rank deficient)");
+        return RH_ENUMERIC;
+      }
+      for (int k = 0; k < j; ++k) {
+        const double f = c[k];
+        const double* qk = &Q[(size_t)I * k];
+        for (int64_t i = 0; i < I; ++i) r[i] -= qk[i] * f;
+      }
+    }
+    int64_t best = -1;
+    double bm = -1.0;
+    for (int64_t i = 0; i < I; ++i)
+      if (std::fabs(r[i]) > bm) {
+        bm = std::fabs(r[i]);
+        best = i;
+      }
+    if (best < 0 || bm == 0.0) {
+      set_error(best < 0 ? "subset selection: Q holds non-finite values"
+                         : "subset selection: DEIM residual vanished (Q is rank deficient)");
+      return RH_ENUMERIC;
+    }
+    sel.push_back((int)best);
+  }
+  return RH_OK;
+}
+
+// sRRQR swaps on a start selection: while some |A_ij| > eta on an unselected row, row i replaces
+// selected row j for the largest |A_ij| (lowest (i, j) on ties); at most 100000 swaps.
+rh_status srrqr_swaps_host(const std::vector<double>& Q, int64_t I, int ell, double eta, std::vector<int>& sel) {
+  std::vector<double> inv, A;
   for (int sw = 0; sw < 100000; ++sw) {
     if (!invert_rows(Q, I, ell, sel, inv)) {
-      set_error("SP-STHOSVD: the selected rows of Q are singular");
+      set_error("subset selection: the selected rows of Q are singular");
       return RH_ENUMERIC;
     }
     apply_inv(Q, I, ell, inv, A);
@@ -293,18 +369,32 @@ rh_status srrqr_select_host(const std::vector<double>& Q, int64_t I, int ell, do
     if (amax <= eta) break;
     sel[bj] = (int)bi;
   }
+  return RH_OK;
+}
+
+// Sorts the selection and forms A = Q (P^T Q)^{-1}, storing A(P, :) as the exact identity (it is one in
+// exact arithmetic), so that a decomposition with this factor reproduces the selected entries.
+rh_status interp_factor_host(const std::vector<double>& Q, int64_t I, int ell, std::vector<int>& sel,
+                             std::vector<double>& A) {
   std::sort(sel.begin(), sel.end());
+  std::vector<double> inv;
   if (!invert_rows(Q, I, ell, sel, inv)) {
-    set_error("SP-STHOSVD: the selected rows of Q are singular");
+    set_error("subset selection: the selected rows of Q are singular");
     return RH_ENUMERIC;
   }
   apply_inv(Q, I, ell, inv, A);
-  // A(P, :) = (P^T Q)(P^T Q)^{-1} is the identity in exact arithmetic: store it exactly, so that the
-  // decomposition reproduces X at the selected positions
   for (int a = 0; a < ell; ++a)
     for (int c = 0; c < ell; ++c) A[sel[a] + (size_t)I * c] = (a == c) ? 1.0 : 0.0;
-  sel_out = sel;
   return RH_OK;
+}
+
+// Row selection P and A = Q (P^T Q)^{-1} of Alg. 6 steps 6-7 (method: RH_SELECT_*).
+rh_status subset_select_host(const std::vector<double>& Q, int64_t I, int ell, int method, double eta,
+                             std::vector<int>& sel, std::vector<double>& A) {
+  rh_status s = method == RH_SELECT_DEIM ? deim_rows_host(Q, I, ell, sel) : cpqr_rows_host(Q, I, ell, sel);
+  if (s != RH_OK) return s;
+  if (method == RH_SELECT_SRRQR && (s = srrqr_swaps_host(Q, I, ell, eta, sel)) != RH_OK) return s;
+  return interp_factor_host(Q, I, ell, sel, A);
 }
 
 struct SpBufs {
@@ -578,7 +668,7 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
     RH_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<int> sel;
     std::vector<double> A;
-    if ((s = srrqr_select_host(Qh, I, ell, 2.0, sel, A)) != RH_OK) return s;
+    if ((s = subset_select_host(Qh, I, ell, RH_SELECT_SRRQR, 2.0, sel, A)) != RH_OK) return s;
     RH_CUDA_TRY(cudaMemcpyAsync(factors[n], A.data(), sizeof(double) * I * ell, cudaMemcpyHostToDevice, st));
     if (selected && selected[n])
       RH_CUDA_TRY(cudaMemcpyAsync(selected[n], sel.data(), sizeof(int32_t) * ell, cudaMemcpyHostToDevice, st));
@@ -630,17 +720,20 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
   return RH_OK;
 }
 
-rh_status rh_srrqr_select(int64_t I, int32_t ell, const double* Q, double eta, int32_t* selected, double* A) {
+rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, int32_t* selected,
+                           double* A) {
   clear_error();
   RH_CHECK_ARG(I >= 1 && ell >= 1 && ell <= I, "need 1 <= ell <= I");
   RH_CHECK_ARG(I <= (int64_t(1) << 31) - 1 && (uint64_t)I * (uint64_t)ell <= (uint64_t(1) << 40),
                "I x ell too large for the host selection");
-  RH_CHECK_ARG(eta >= 1.0, "eta must be >= 1");
+  RH_CHECK_ARG(method == RH_SELECT_SRRQR || method == RH_SELECT_CPQR || method == RH_SELECT_DEIM,
+               "method must be RH_SELECT_SRRQR, RH_SELECT_CPQR or RH_SELECT_DEIM");
+  RH_CHECK_ARG(method != RH_SELECT_SRRQR || eta >= 1.0, "eta must be >= 1");
   RH_CHECK_ARG(Q != nullptr && selected != nullptr && A != nullptr, "Q, selected and A must be non-NULL");
   const std::vector<double> Qh(Q, Q + (size_t)I * ell);
   std::vector<int> sel;
   std::vector<double> Ah;
-  const rh_status s = srrqr_select_host(Qh, I, ell, eta, sel, Ah);
+  const rh_status s = subset_select_host(Qh, I, ell, method, eta, sel, Ah);
   if (s != RH_OK) return s;
   for (int a = 0; a < ell; ++a) selected[a] = sel[a];
   std::copy(Ah.begin(), Ah.end(), A);

@@ -176,3 +176,47 @@ def test_sp_hosvd_size_rule_is_strict():
         tucker.sp_hosvd(X, [3, 3, 5], 3, seed=1)                 # mode 2: ell = 8 = I_2
     out = tucker.sp_hosvd(X, [3, 3, 4], 3, seed=1)              # ell = 7 < 8
     assert [P.size for P in out["selected"]] == [6, 6, 7]
+
+
+# ---- the other subset selections (Sec. 5 remark 3) --------------------------------------------
+def _lu_pivot_rows(Q):
+    """Rows chosen by Gaussian elimination with partial pivoting on Q (LAPACK getrf's swaps)."""
+    import scipy.linalg
+
+    _, piv = scipy.linalg.lu_factor(Q)
+    perm = np.arange(Q.shape[0])
+    for i, pv in enumerate(piv):
+        perm[i], perm[pv] = perm[pv], perm[i]
+    return np.sort(perm[: Q.shape[1]])
+
+
+def _greedy_residual_rows(Q):
+    """Column-pivoted QR of Q^T by its definition: repeatedly take the row of Q with the largest
+    norm after projecting out the span of the rows taken so far."""
+    chosen = []
+    for _ in range(Q.shape[1]):
+        if chosen:
+            B, _ = np.linalg.qr(Q[chosen, :].T)
+            R = Q - (Q @ B) @ B.T
+        else:
+            R = Q
+        nrm = np.sum(R * R, axis=1)
+        nrm[chosen] = -1.0
+        chosen.append(int(np.argmax(nrm)))
+    return np.sort(np.array(chosen))
+
+
+@pytest.mark.parametrize("I,ell,seed", [(40, 6, 1), (120, 20, 2), (64, 63, 3), (9, 1, 4)])
+def test_deim_is_partial_pivoting(I, ell, seed):
+    """DEIM's greedy equals the row pivots of LU with partial pivoting of Q (Sorensen and Embree
+    2016): the residual at step j is column j of the Schur complement."""
+    Q = np.linalg.qr(np.random.default_rng(seed).standard_normal((I, ell)))[0]
+    assert np.array_equal(tucker.deim_select(Q), _lu_pivot_rows(Q))
+
+
+@pytest.mark.parametrize("I,ell,seed", [(40, 6, 5), (120, 20, 6), (64, 63, 7)])
+def test_cpqr_is_the_greedy_residual_selection(I, ell, seed):
+    Q = np.linalg.qr(np.random.default_rng(seed).standard_normal((I, ell)))[0]
+    assert np.array_equal(tucker.cpqr_select(Q), _greedy_residual_rows(Q))
+    # and sRRQR starts from it: with eta = infinity no swap is made
+    assert np.array_equal(tucker.srrqr_select(Q, eta=np.inf), tucker.cpqr_select(Q))

@@ -1,7 +1,8 @@
-"""The host step of SP-STHOSVD (Alg. 6 steps 6-7: strong-RRQR row selection and the interpolatory
-factor A = Q (P^T Q)^{-1}) through the C ABI, on CPU: the library runs it on the host, so it is
-compared with the oracle here on identical inputs.  The selection is index work and must equal the
-oracle's exactly; A follows from it and is checked against its definition.
+"""The host step of SP-STHOSVD (Alg. 6 steps 6-7: row selection and the interpolatory factor
+A = Q (P^T Q)^{-1}) through the C ABI, on CPU, for the three selections the library offers (strong
+RRQR, the one Alg. 6 uses; column-pivoted QR and DEIM, Sec. 5's alternatives): the library runs them
+on the host, so they are compared with the oracle here on identical inputs.  The selection is index
+work and must equal the oracle's exactly; A follows from it and is checked against its definition.
 """
 
 import numpy as np
@@ -30,9 +31,13 @@ def _basis(I, ell, seed, row_scale=None):
     return np.linalg.qr(g)[0]
 
 
-def _select(rh, Q, eta):
-    sel, A = rh.srrqr_select(torch.from_numpy(np.ascontiguousarray(Q)), eta)
+def _select(rh, Q, eta, method="srrqr"):
+    sel, A = rh.subset_select(torch.from_numpy(np.ascontiguousarray(Q)), method, eta)
     return sel.numpy().astype(np.int64), A.numpy().T
+
+
+ORACLE = {"srrqr": lambda Q, eta: otk.srrqr_select(Q, eta=eta), "cpqr": lambda Q, eta: otk.cpqr_select(Q),
+          "deim": lambda Q, eta: otk.deim_select(Q)}
 
 
 def _check_valid(Q, sel, A, eta):
@@ -40,7 +45,7 @@ def _check_valid(Q, sel, A, eta):
     assert np.all(np.diff(sel) > 0) and sel[0] >= 0 and sel[-1] < I
     assert np.array_equal(A[sel, :], np.eye(ell))                   # stored exactly
     rest = np.setdiff1d(np.arange(I), sel)
-    if rest.size:
+    if rest.size and eta is not None:
         assert np.abs(A[rest, :]).max() <= eta * (1 + 1e-12)
     ref = np.linalg.solve(Q[sel, :].T, Q.T).T                       # Q (P^T Q)^{-1}, another route
     cond = np.linalg.cond(Q[sel, :])
@@ -49,11 +54,11 @@ def _check_valid(Q, sel, A, eta):
 
 @pytest.mark.parametrize("I,ell,seed", [(50, 5, 1), (200, 20, 2), (64, 63, 3), (300, 40, 4), (1000, 64, 5),
                                         (9, 1, 6)])
-@pytest.mark.parametrize("eta", [2.0, 1.0])
-def test_selection_equals_the_oracle(rh, I, ell, seed, eta):
+@pytest.mark.parametrize("method,eta", [("srrqr", 2.0), ("srrqr", 1.0), ("cpqr", None), ("deim", None)])
+def test_selection_equals_the_oracle(rh, I, ell, seed, method, eta):
     Q = _basis(I, ell, seed)
-    sel, A = _select(rh, Q, eta)
-    assert np.array_equal(sel, otk.srrqr_select(Q, eta=eta))
+    sel, A = _select(rh, Q, 2.0 if eta is None else eta, method)
+    assert np.array_equal(sel, ORACLE[method](Q, eta))
     _check_valid(Q, sel, A, eta)
 
 
@@ -72,17 +77,18 @@ def test_swaps_run(rh):
     assert moved > 0
 
 
-def test_closed_forms(rh):
+@pytest.mark.parametrize("method", ["srrqr", "cpqr", "deim"])
+def test_closed_forms(rh, method):
     # ell = I: every row, A = I
     Q = _basis(7, 7, 8)
-    sel, A = _select(rh, Q, 2.0)
+    sel, A = _select(rh, Q, 2.0, method)
     assert np.array_equal(sel, np.arange(7)) and np.array_equal(A, np.eye(7))
     # a basis supported on rows {3, 10, 17}: those rows are chosen and A is Q (P^T Q)^{-1} = E_P
     I, rows = 20, [3, 10, 17]
     Q = np.zeros((I, 3))
     R = np.linalg.qr(np.random.default_rng(9).standard_normal((3, 3)))[0]
     Q[rows, :] = R
-    sel, A = _select(rh, Q, 2.0)
+    sel, A = _select(rh, Q, 2.0, method)
     assert list(sel) == rows
     E = np.zeros((I, 3))
     E[rows, :] = np.eye(3)
@@ -92,14 +98,26 @@ def test_closed_forms(rh):
 def test_failures_are_reported(rh):
     Q = _basis(30, 4, 10)
     Q[:, 2] = 0.0                                   # rank-deficient: P^T Q is singular
-    with pytest.raises(rh.RhError, match="singular"):
-        rh.srrqr_select(torch.from_numpy(Q), 2.0)
+    for method in ("srrqr", "cpqr"):
+        with pytest.raises(rh.RhError, match="singular"):
+            rh.subset_select(torch.from_numpy(Q), method)
+    with pytest.raises(rh.RhError, match="rank deficient"):
+        rh.subset_select(torch.from_numpy(Q), "deim")
     Q = np.full((30, 4), np.nan)
-    with pytest.raises(rh.RhError, match="non-finite"):
-        rh.srrqr_select(torch.from_numpy(Q), 2.0)
+    for method in ("srrqr", "cpqr", "deim"):
+        with pytest.raises(rh.RhError, match="non-finite|rank deficient"):
+            rh.subset_select(torch.from_numpy(Q), method)
     with pytest.raises(rh.RhError, match="eta"):
-        rh.srrqr_select(torch.from_numpy(_basis(30, 4, 11)), 0.5)
+        rh.subset_select(torch.from_numpy(_basis(30, 4, 11)), "srrqr", 0.5)
+    sel, _ = rh.subset_select(torch.from_numpy(_basis(30, 4, 11)), "deim", 0.5)   # eta unused
+    assert sel.numel() == 4
     with pytest.raises(rh.RhError, match="ell <= I"):
-        rh.srrqr_select(torch.from_numpy(_basis(30, 4, 12).T.copy()), 2.0)
+        rh.subset_select(torch.from_numpy(_basis(30, 4, 12).T.copy()))
     with pytest.raises(ValueError):
-        rh.srrqr_select(torch.zeros((4, 2), dtype=torch.float32), 2.0)
+        rh.subset_select(torch.zeros((4, 2), dtype=torch.float32))
+    with pytest.raises(ValueError):
+        rh.subset_select(torch.from_numpy(_basis(30, 4, 12)), "leverage")
+    from paper_1905_07311_gb300 import _lib
+    import ctypes
+    one = ctypes.c_void_p(1)
+    assert _lib.lib().rh_subset_select(30, 4, one, 3, 2.0, one, one) == 1       # unknown method
