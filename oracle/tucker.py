@@ -12,6 +12,7 @@ Each function follows the algorithm it names step by step, in the paper's order:
   ``cpqr_select``, ``deim_select`` the other selections of Sec. 5
 * ``sp_sthosvd``         Alg. 6 (SP-STHOSVD), dense or COO input
 * ``sp_hosvd``           SP-HOSVD, Alg. 6 with independent modes (Sec. 5 remark 1)
+* ``orthonormalize_tucker`` the orthonormalising post-processing of Sec. 5
 * ``randsvd(q=...)``     Alg. 1 with randomized subspace iteration (Sec. 5 remark 2, Sec. 6)
 
 Library primitives used as single steps: numpy matmul, ``numpy.linalg.qr``
@@ -442,6 +443,18 @@ def sp_hosvd(X, ranks, p, seed, tensor_id=0, eta=2.0):
         sel[n] = P
     G = X[np.ix_(*sel)]
     return {"core": G, "factors": A, "selected": sel}
+
+
+def orthonormalize_tucker(core, factors):
+    """Post-processing of Sec. 5 for the non-orthonormal factors of Alg. 6 and SP-HOSVD: a thin QR
+    of every factor, A_j = Q_j R_j, and the aggregation of the triangles into the core,
+    G <- G x_1 R_1 ... x_d R_d.  The approximation G x_j A_j is unchanged."""
+    Qs, G = [], np.asarray(core, dtype=np.float64)
+    for n, A in enumerate(factors):
+        Q, R = np.linalg.qr(A)
+        Qs.append(Q)
+        G = ttm(G, R, n)
+    return G, Qs
 
 
 def _kolda_rows(idx, dims, n):

@@ -220,3 +220,29 @@ def test_cpqr_is_the_greedy_residual_selection(I, ell, seed):
     assert np.array_equal(tucker.cpqr_select(Q), _greedy_residual_rows(Q))
     # and sRRQR starts from it: with eta = infinity no swap is made
     assert np.array_equal(tucker.srrqr_select(Q, eta=np.inf), tucker.cpqr_select(Q))
+
+
+# ---- orthonormalising post-processing (Sec. 5) -------------------------------------------------
+@pytest.mark.parametrize("alg", ["sp_sthosvd", "sp_hosvd"])
+def test_orthonormalize_keeps_the_approximation(alg):
+    X = _sparse_tensor(3)
+    out = getattr(tucker, alg)(X, [3, 3, 3], 3, seed=4)
+    G, Qs = tucker.orthonormalize_tucker(out["core"], out["factors"])
+    before = multi_ttm(out["core"], out["factors"])
+    after = multi_ttm(G, Qs)
+    assert frob(after - before) <= 1e-12 * frob(before)
+    for Q, A in zip(Qs, out["factors"]):
+        assert Q.shape == A.shape
+        assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 1e-14 * 10 * Q.shape[1]
+        assert np.abs(_proj(Q) - _proj(A)).max() < 1e-12                 # same column spaces
+    # orthonormal factors: the norm of the approximation is the norm of the core
+    assert abs(frob(after) - frob(G)) <= 1e-12 * frob(G)
+
+
+def test_orthonormalize_of_an_orthonormal_tucker_only_flips_signs():
+    X = lowrank_plus_noise_np([14, 12, 10], [4, 4, 4], 0.7, 1e-2, seed=11)
+    out = tucker.rsthosvd(X, [4, 4, 4], 3, seed=12)
+    G, Qs = tucker.orthonormalize_tucker(out["core"], out["factors"])
+    for Q, A in zip(Qs, out["factors"]):
+        assert np.allclose(np.abs(Q), np.abs(A), atol=1e-13)
+    assert np.allclose(np.abs(G), np.abs(out["core"]), atol=1e-12 * np.abs(out["core"]).max())
