@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/rhosvd.h"
@@ -80,13 +81,16 @@ class ProfileScope {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// SM count of the device current at the first call (initialised once, thread-safe); 152 (GB300)
+// when no device answers, as in workspace queries on a machine without a GPU.
 inline int num_sms() {
-  static int n = -1;
-  if (n < 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 148;
-  }
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v <= 0)
+      v = 152;
+    return v;
+  }();
   return n;
 }
 
@@ -244,7 +248,7 @@ struct KernelRef {
   const void* group;    // group_kernel<Op>
   uint32_t args_bytes;
   int threads;
-  size_t smem_single = 0, smem_group = 0;   // dynamic shared memory opted in so far (host)
+  std::atomic<size_t> smem_single{0}, smem_group{0};   // dynamic shared memory opted in so far (host)
 };
 
 #ifdef __CUDACC__
