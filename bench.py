@@ -220,7 +220,7 @@ def run_ours(args):
     device = torch.device("cuda", local)
     from paper_1905_07311_gb300 import build
 
-    if rank == 0 or not build.up_to_date():
+    if local == 0:          # one build per node; the other ranks wait for it at the barrier
         build.build()
     if world > 1:
         dist.barrier()
