@@ -313,3 +313,33 @@ def test_fp8_layout_sizes(L):
     ld, so, ns, by = layout([5, 3])            # 48 bytes of data, one partly used scale block
     assert ld == 16 and so == 48 and ns == 1 and by == 52
     assert L.rh_fp8_layout(3, _lib.i64_array([128, 0, 40]), None, None, None, None) == 1
+
+
+def test_header_is_plain_c_and_links(L):
+    """include/rhosvd.h is a C header: a C99 program (strict, warnings as errors) includes it,
+    links against the library and answers a workspace query without a device."""
+    import shutil
+
+    from paper_1905_07311_gb300 import _lib
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    out = os.path.join(ROOT, "_build", "c_abi_check")
+    os.makedirs(out, exist_ok=True)
+    src = os.path.join(out, "main.c")
+    with open(src, "w") as f:
+        f.write('#include "rhosvd.h"\n#include <stdio.h>\n'
+                "int main(void) {\n"
+                "  rh_options o;\n  rh_options_default(&o);\n"
+                "  int64_t dims[3] = {30, 20, 10};\n  int32_t ranks[3] = {4, 4, 4};\n"
+                "  size_t ws = rsthosvd_workspace_size(3, dims, RH_F32, ranks, &o);\n"
+                '  printf("%zu %d\\n", ws, (int)RH_SELECT_DEIM);\n'
+                "  return ws > 0 ? 0 : 1;\n}\n")
+    exe = os.path.join(out, "main")
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    src, "-L", libdir, "-lrhosvd", f"-Wl,-rpath,{libdir}", "-o", exe], check=True)
+    res = subprocess.run([exe], capture_output=True, text=True, check=True)
+    ws, deim = res.stdout.split()
+    assert int(ws) == _ws(L, [30, 20, 10], [4, 4, 4], dtype=1) and int(deim) == 2
