@@ -11,7 +11,7 @@ Each function follows the algorithm it names step by step, in the paper's order:
 * ``srrqr_select``       strong RRQR subset selection with eta = 2 (Alg. 6, step 4);
   ``cpqr_select``, ``deim_select`` the other selections of Sec. 5
 * ``sp_sthosvd``         Alg. 6 (SP-STHOSVD), dense or COO input
-* ``sp_hosvd``           SP-HOSVD, Alg. 6 with independent modes (Sec. 5 remark 1)
+* ``sp_hosvd``           SP-HOSVD, Alg. 6 with independent modes (Sec. 5 remark 1), dense or COO input
 * ``orthonormalize_tucker`` the orthonormalising post-processing of Sec. 5
 * ``randsvd(q=...)``     Alg. 1 with randomized subspace iteration (Sec. 5 remark 2, Sec. 6)
 
@@ -514,6 +514,36 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p, seed, rho=None, tensor_id=0, eta=2
     if idx.shape[0]:
         core[tuple(idx.T)] = vals
     return {"core": core, "factors": A, "selected": sel, "rho": rho}
+
+
+def sp_hosvd_coo(idx, vals, dims, ranks, p, seed, tensor_id=0, eta=2.0):
+    """SP-HOSVD (Sec. 5 remark 1) of a COO tensor: every mode's sketch from the input's nonzeros
+    (``coo_sketch``), thin QR, strong-RRQR selection and A_j = Q (P_j^T Q)^{-1}; the core keeps the
+    nonzeros whose every coordinate is selected, renumbered to positions in the sorted selections."""
+    idx = np.asarray(idx, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    dims = [int(x) for x in dims]
+    d = len(dims)
+    N = int(np.prod(dims))
+    A = [None] * d
+    sel = [None] * d
+    keep = np.ones(idx.shape[0], dtype=bool)
+    new = idx.copy()
+    for n in range(d):
+        ell = _ell(ranks[n], p, dims[n], N // dims[n], clamp=False, strict=True)
+        Y = coo_sketch(idx, vals, dims, n, ell, seed, tensor_id)
+        Q, _ = np.linalg.qr(Y)
+        P = srrqr_select(Q, eta)
+        A[n] = Q @ np.linalg.inv(Q[P, :])
+        sel[n] = P
+        pos = np.full(dims[n], -1, dtype=np.int64)
+        pos[P] = np.arange(P.size)
+        new[:, n] = pos[idx[:, n]]
+        keep &= new[:, n] >= 0
+    core = np.zeros([s_.size for s_ in sel])
+    if keep.any():
+        core[tuple(new[keep].T)] = vals[keep]
+    return {"core": core, "factors": A, "selected": sel}
 
 
 # ---------------------------------------------------------------------------------

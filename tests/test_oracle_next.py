@@ -246,3 +246,15 @@ def test_orthonormalize_of_an_orthonormal_tucker_only_flips_signs():
     for Q, A in zip(Qs, out["factors"]):
         assert np.allclose(np.abs(Q), np.abs(A), atol=1e-13)
     assert np.allclose(np.abs(G), np.abs(out["core"]), atol=1e-12 * np.abs(out["core"]).max())
+
+
+def test_sp_hosvd_coo_equals_dense():
+    X = _sparse_tensor(4)
+    idx = np.argwhere(X != 0)
+    vals = X[X != 0]
+    out = tucker.sp_hosvd(X, [3, 3, 3], 3, seed=2)
+    oc = tucker.sp_hosvd_coo(idx, vals, X.shape, [3, 3, 3], 3, seed=2)
+    for n in range(3):
+        assert np.array_equal(oc["selected"][n], out["selected"][n])
+        assert np.allclose(oc["factors"][n], out["factors"][n], atol=1e-10)
+    assert np.array_equal(oc["core"], out["core"])
