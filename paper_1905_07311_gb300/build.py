@@ -19,7 +19,9 @@ OUT = os.path.join(PKG, "librhosvd.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+# Host code (the subset selection of the sparse path, plans) must give the same results on x86 and
+# Arm hosts: no contraction of a*b + c into FMA there (device code keeps nvcc's own FMA rules).
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]
 
 
@@ -35,7 +37,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "rhosvd.h")]
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "rhosvd.h")]
+            + [os.path.abspath(__file__)])   # the flags live here
 
 
 def up_to_date():
