@@ -463,7 +463,8 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
 /*
  * rh_subset_select -- the row selection and interpolatory factor of Alg. 6 steps 6-7 on one basis:
  * the host step that sp_sthosvd_coo runs for each mode (with RH_SELECT_SRRQR, eta = 2), and the
- * other selections of Sec. 5's remark on subset selection.  Host memory only; no device call.
+ * other selections of Sec. 5's remark on subset selection (column-pivoted QR, DEIM, uniform and
+ * leverage-score sampling).  Host memory only; no device call.
  *   Q         host, I x ell FP64 column-major (full column rank; sp_sthosvd_coo passes the thin-QR
  *             factor of the sketch).  Not modified.
  *   method    RH_SELECT_SRRQR: column-pivoted Householder QR of Q^T (largest remaining column norm,
@@ -473,17 +474,24 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
  *             RH_SELECT_CPQR: the pivots of that column-pivoted QR alone (no bound on A);
  *             RH_SELECT_DEIM: the DEIM greedy (Chaturantabut-Sorensen; Sorensen-Embree): the largest
  *               |Q(i, 0)|, then for j = 1 .. ell-1 the largest |r_i| of r = Q(:, j) - Q(:, 0:j) c with
- *               Q(P, 0:j) c = Q(P, j) (lowest index on ties).
+ *               Q(P, 0:j) c = Q(P, j) (lowest index on ties);
+ *             RH_SELECT_UNIFORM / RH_SELECT_LEVERAGE: ell rows sampled without replacement with
+ *               weights 1 or ||Q(i, :)||^2 (the leverage scores of range(Q)): draw k takes the first
+ *               untaken row (increasing i) whose running weight sum exceeds u_k times the untaken
+ *               total (FP64 sums), u_k = ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53 from the Philox4x32-10
+ *               words of counter (k, stream, 0, 0x53454C45) under key (seed lo, seed hi).
  *   eta       strong-RRQR bound, >= 1 (RH_SELECT_SRRQR only).
+ *   seed, stream  key and counter word of the sampling methods (ignored by the others).
  *   selected  host, ell int32 receiving P, the chosen rows of Q, increasing.
  *   A         host, I x ell FP64 column-major receiving A = Q (P^T Q)^{-1}, with the rows P stored as
  *             the exact identity.
  *   RH_EINVAL: ell < 1, ell > I, unknown method, eta < 1 with RH_SELECT_SRRQR, NULL pointers.
- *   RH_ENUMERIC: P^T Q singular, a vanishing DEIM residual, or non-finite values in Q.
+ *   RH_ENUMERIC: P^T Q singular, a vanishing DEIM residual, no sampling weight left, or non-finite
+ *   values in Q.
  */
-enum { RH_SELECT_SRRQR = 0, RH_SELECT_CPQR = 1, RH_SELECT_DEIM = 2 };
-rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, int32_t* selected,
-                           double* A);
+enum { RH_SELECT_SRRQR = 0, RH_SELECT_CPQR = 1, RH_SELECT_DEIM = 2, RH_SELECT_UNIFORM = 3, RH_SELECT_LEVERAGE = 4 };
+rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, uint64_t seed,
+                           uint32_t stream, int32_t* selected, double* A);
 
 /*
  * rsthosvd_host -- the same R-STHOSVD with HOST buffers: enqueues the copy of X to the

@@ -9,7 +9,7 @@ Each function follows the algorithm it names step by step, in the paper's order:
 * ``adapt_range_finder`` Sec. 4 (blocked randomized QB with an error indicator)
 * ``adaptive_rhosvd``    Alg. 4,  ``adaptive_rsthosvd`` Alg. 5
 * ``srrqr_select``       strong RRQR subset selection with eta = 2 (Alg. 6, step 4);
-  ``cpqr_select``, ``deim_select`` the other selections of Sec. 5
+  ``cpqr_select``, ``deim_select``, ``sample_select`` the other selections of Sec. 5
 * ``sp_sthosvd``         Alg. 6 (SP-STHOSVD), dense or COO input
 * ``sp_hosvd``           SP-HOSVD, Alg. 6 with independent modes (Sec. 5 remark 1), dense or COO input
 * ``orthonormalize_tucker`` the orthonormalising post-processing of Sec. 5
@@ -359,6 +359,54 @@ def deim_select(Q):
         r = Q[:, j] - Q[:, :j] @ c
         p.append(int(np.argmax(np.abs(r))))
     return np.array(sorted(p), dtype=np.int64)
+
+
+def sample_select(Q, leverage, seed, stream=0):
+    """Subset selection by sampling (Sec. 5 remark 3: uniform or leverage-score sampling), read as
+    ell rows drawn without replacement with weights 1 or ||Q(i, :)||^2: draw k takes the first
+    untaken row (increasing i) whose running weight sum exceeds u_k times the untaken total (FP64
+    sums in row order); u_k = ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53 from the Philox4x32-10 words of
+    counter (k, stream, 0, 0x53454C45) under key (seed lo, seed hi).  Returns the rows sorted."""
+    I, ell = Q.shape
+    if leverage:
+        w = []
+        for i in range(I):
+            s_ = 0.0
+            for c in range(ell):
+                s_ = s_ + float(Q[i, c]) * float(Q[i, c])
+            w.append(s_)
+    else:
+        w = [1.0] * I
+    taken = [False] * I
+    out = []
+    k0, k1 = int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF
+    for k in range(ell):
+        words = rng.philox4x32_10(np.uint32(k), np.uint32(stream), np.uint32(0), np.uint32(0x53454C45),
+                                  np.uint32(k0), np.uint32(k1))
+        w0, w1 = int(np.asarray(words[0]).ravel()[0]), int(np.asarray(words[1]).ravel()[0])
+        u = ((w0 >> 5) * 67108864.0 + (w1 >> 6)) * 2.0 ** -53
+        T = 0.0
+        for i in range(I):
+            if not taken[i]:
+                T = T + w[i]
+        if not T > 0.0:
+            raise ValueError("no sampling weight left")
+        t = u * T
+        pick, last, c = -1, -1, 0.0
+        for i in range(I):
+            if taken[i]:
+                continue
+            c = c + w[i]
+            if w[i] > 0.0:
+                last = i
+            if c > t:
+                pick = i
+                break
+        if pick < 0:
+            pick = last
+        taken[pick] = True
+        out.append(pick)
+    return np.array(sorted(out), dtype=np.int64)
 
 
 def srrqr_select(Q, eta=2.0, max_swaps=100000):

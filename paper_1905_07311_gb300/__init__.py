@@ -423,13 +423,14 @@ def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0):
     return Y
 
 
-SELECT_METHODS = {"srrqr": 0, "cpqr": 1, "deim": 2}
+SELECT_METHODS = {"srrqr": 0, "cpqr": 1, "deim": 2, "uniform": 3, "leverage": 4}
 
 
-def subset_select(Q, method="srrqr", eta=2.0):
+def subset_select(Q, method="srrqr", eta=2.0, seed=0, stream=0):
     """Row selection and A = Q (P^T Q)^{-1} of Alg. 6 steps 6-7 for a host FP64 tensor Q (I x ell),
     computed by the library's host step (no device call).  ``method``: "srrqr" (strong RRQR with
-    bound ``eta``, the one SP-STHOSVD uses), "cpqr" (column-pivoted QR alone) or "deim".  Returns
+    bound ``eta``, the one SP-STHOSVD uses), "cpqr" (column-pivoted QR alone), "deim", or the
+    sampling selections "uniform" and "leverage" (drawn from ``seed`` and ``stream``).  Returns
     (selected int32 tensor, increasing; A as an (ell, I) FP64 tensor holding the column-major I x ell A)."""
     torch = _torch()
     if Q.device.type != "cpu" or Q.dtype != torch.float64 or Q.dim() != 2:
@@ -440,7 +441,8 @@ def subset_select(Q, method="srrqr", eta=2.0):
     Qf = Q.t().contiguous()            # (ell, I) row-major = I x ell column-major
     sel = torch.empty(ell, dtype=torch.int32)
     A = torch.empty((ell, I), dtype=torch.float64)
-    check(lib().rh_subset_select(I, ell, _ptr(Qf), SELECT_METHODS[method], float(eta), _ptr(sel), _ptr(A)))
+    check(lib().rh_subset_select(I, ell, _ptr(Qf), SELECT_METHODS[method], float(eta),
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream) & 0xFFFFFFFF, _ptr(sel), _ptr(A)))
     return sel, A
 
 

@@ -81,7 +81,7 @@ SIGNATURES = {
     "rsthosvd_batched_plan_run": (_I32, [_P, _P]),
     "rsthosvd_batched_plan_launches": (_I64, [_P]),
     "rsthosvd_batched_plan_destroy": (None, [_P]),
-    "rh_subset_select": (_I32, [_I64, _I32, _P, _I32, ctypes.c_double, _P, _P]),
+    "rh_subset_select": (_I32, [_I64, _I32, _P, _I32, ctypes.c_double, _U64, ctypes.c_uint32, _P, _P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
     "rsthosvd_host": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _SZ, _P]),
 }

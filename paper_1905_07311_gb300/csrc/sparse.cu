@@ -388,10 +388,79 @@ rh_status interp_factor_host(const std::vector<double>& Q, int64_t I, int ell, s
   return RH_OK;
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11) on the host: ten rounds of two 32 x 32 -> 64-bit
+// multiplications by 0xD2511F53 and 0xCD9E8D57, the key bumped by the Weyl constants 0x9E3779B9 and
+// 0xBB67AE85 between rounds.
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1, n3 = (uint32_t)p0;
+    c[0] = n0;
+    c[1] = n1;
+    c[2] = n2;
+    c[3] = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Sampling selections (uniform or leverage-score weights): ell rows without replacement, draw k taking
+// the first untaken row whose running weight sum exceeds u_k times the untaken total (sums in FP64,
+// increasing row order); u_k = ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53 from Philox4x32-10 with counter
+// (k, stream, 0, 0x53454C45) and key (seed lo, seed hi).
+rh_status sample_rows_host(const std::vector<double>& Q, int64_t I, int ell, bool leverage, uint64_t seed,
+                           uint32_t stream, std::vector<int>& sel) {
+  std::vector<double> w(I, 1.0);
+  if (leverage)
+    for (int64_t i = 0; i < I; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < ell; ++c) {
+        const double q = Q[i + (size_t)I * c];
+        s = s + q * q;
+      }
+      w[i] = s;
+    }
+  std::vector<char> taken(I, 0);
+  sel.clear();
+  for (int k = 0; k < ell; ++k) {
+    uint32_t ctr[4] = {(uint32_t)k, stream, 0u, 0x53454C45u};
+    philox_host(ctr, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    const double u = ((double)(ctr[0] >> 5) * 67108864.0 + (double)(ctr[1] >> 6)) * 0x1p-53;
+    double T = 0.0;
+    for (int64_t i = 0; i < I; ++i)
+      if (!taken[i]) T = T + w[i];
+    if (!(T > 0.0)) {
+      set_error("subset selection: no sampling weight left (Q has too few nonzero rows or non-finite values)");
+      return RH_ENUMERIC;
+    }
+    const double t = u * T;
+    int64_t pick = -1, last = -1;
+    double c = 0.0;
+    for (int64_t i = 0; i < I; ++i) {
+      if (taken[i]) continue;
+      c = c + w[i];
+      if (w[i] > 0.0) last = i;
+      if (c > t) {
+        pick = i;
+        break;
+      }
+    }
+    if (pick < 0) pick = last;   // t rounded up to the total
+    taken[pick] = 1;
+    sel.push_back((int)pick);
+  }
+  return RH_OK;
+}
+
 // Row selection P and A = Q (P^T Q)^{-1} of Alg. 6 steps 6-7 (method: RH_SELECT_*).
 rh_status subset_select_host(const std::vector<double>& Q, int64_t I, int ell, int method, double eta,
-                             std::vector<int>& sel, std::vector<double>& A) {
-  rh_status s = method == RH_SELECT_DEIM ? deim_rows_host(Q, I, ell, sel) : cpqr_rows_host(Q, I, ell, sel);
+                             std::vector<int>& sel, std::vector<double>& A, uint64_t seed = 0, uint32_t stream = 0) {
+  rh_status s;
+  if (method == RH_SELECT_UNIFORM || method == RH_SELECT_LEVERAGE)
+    s = sample_rows_host(Q, I, ell, method == RH_SELECT_LEVERAGE, seed, stream, sel);
+  else
+    s = method == RH_SELECT_DEIM ? deim_rows_host(Q, I, ell, sel) : cpqr_rows_host(Q, I, ell, sel);
   if (s != RH_OK) return s;
   if (method == RH_SELECT_SRRQR && (s = srrqr_swaps_host(Q, I, ell, eta, sel)) != RH_OK) return s;
   return interp_factor_host(Q, I, ell, sel, A);
@@ -720,20 +789,20 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
   return RH_OK;
 }
 
-rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, int32_t* selected,
-                           double* A) {
+rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, uint64_t seed,
+                           uint32_t stream, int32_t* selected, double* A) {
   clear_error();
   RH_CHECK_ARG(I >= 1 && ell >= 1 && ell <= I, "need 1 <= ell <= I");
   RH_CHECK_ARG(I <= (int64_t(1) << 31) - 1 && (uint64_t)I * (uint64_t)ell <= (uint64_t(1) << 40),
                "I x ell too large for the host selection");
-  RH_CHECK_ARG(method == RH_SELECT_SRRQR || method == RH_SELECT_CPQR || method == RH_SELECT_DEIM,
-               "method must be RH_SELECT_SRRQR, RH_SELECT_CPQR or RH_SELECT_DEIM");
+  RH_CHECK_ARG(method >= RH_SELECT_SRRQR && method <= RH_SELECT_LEVERAGE,
+               "method must be one of RH_SELECT_SRRQR, _CPQR, _DEIM, _UNIFORM, _LEVERAGE");
   RH_CHECK_ARG(method != RH_SELECT_SRRQR || eta >= 1.0, "eta must be >= 1");
   RH_CHECK_ARG(Q != nullptr && selected != nullptr && A != nullptr, "Q, selected and A must be non-NULL");
   const std::vector<double> Qh(Q, Q + (size_t)I * ell);
   std::vector<int> sel;
   std::vector<double> Ah;
-  const rh_status s = subset_select_host(Qh, I, ell, method, eta, sel, Ah);
+  const rh_status s = subset_select_host(Qh, I, ell, method, eta, sel, Ah, seed, stream);
   if (s != RH_OK) return s;
   for (int a = 0; a < ell; ++a) selected[a] = sel[a];
   std::copy(Ah.begin(), Ah.end(), A);

@@ -258,3 +258,35 @@ def test_sp_hosvd_coo_equals_dense():
         assert np.array_equal(oc["selected"][n], out["selected"][n])
         assert np.allclose(oc["factors"][n], out["factors"][n], atol=1e-10)
     assert np.array_equal(oc["core"], out["core"])
+
+
+def test_uniform_sampling_draws_every_subset_equally():
+    """Uniform sampling without replacement makes every ell-subset equally likely: C(5, 2) = 10
+    subsets, 3000 seeds, each count within 5 standard deviations of 300."""
+    import itertools
+
+    Q = np.linalg.qr(np.random.default_rng(1).standard_normal((5, 2)))[0]
+    counts = {c: 0 for c in itertools.combinations(range(5), 2)}
+    for seed in range(3000):
+        counts[tuple(int(x) for x in tucker.sample_select(Q, False, seed))] += 1
+    sd = math.sqrt(3000 * 0.1 * 0.9)
+    assert all(abs(v - 300) <= 5 * sd for v in counts.values()), counts
+
+
+def test_leverage_sampling_follows_its_law():
+    """Weights w_i = ||Q(i, :)||^2 (sum ell): a pair {a, b} is drawn with probability
+    w_a/T w_b/(T - w_a) + w_b/T w_a/(T - w_b), T = sum w = 2, checked on 4000 seeds."""
+    import itertools
+
+    Q = np.linalg.qr(np.random.default_rng(2).standard_normal((4, 2)) * np.array([[3.0], [1.0], [0.5], [0.2]]))[0]
+    w = np.sum(Q * Q, axis=1)
+    T = w.sum()
+    assert abs(T - 2.0) < 1e-12
+    n = 4000
+    counts = {c: 0 for c in itertools.combinations(range(4), 2)}
+    for seed in range(n):
+        counts[tuple(int(x) for x in tucker.sample_select(Q, True, seed, stream=5))] += 1
+    for (a, b), v in counts.items():
+        prob = w[a] / T * w[b] / (T - w[a]) + w[b] / T * w[a] / (T - w[b])
+        sd = math.sqrt(n * prob * (1 - prob))
+        assert abs(v - n * prob) <= 5 * sd + 1, ((a, b), v, n * prob)

@@ -1,6 +1,7 @@
 """The host step of SP-STHOSVD (Alg. 6 steps 6-7: row selection and the interpolatory factor
-A = Q (P^T Q)^{-1}) through the C ABI, on CPU, for the three selections the library offers (strong
-RRQR, the one Alg. 6 uses; column-pivoted QR and DEIM, Sec. 5's alternatives): the library runs them
+A = Q (P^T Q)^{-1}) through the C ABI, on CPU, for the selections the library offers (strong RRQR,
+the one Alg. 6 uses; column-pivoted QR, DEIM, uniform and leverage-score sampling, Sec. 5's
+alternatives, the sampling ones with one Philox4x32-10 implementation on each side): the library runs them
 on the host, so they are compared with the oracle here on identical inputs.  The selection is index
 work and must equal the oracle's exactly; A follows from it and is checked against its definition.
 """
@@ -31,13 +32,18 @@ def _basis(I, ell, seed, row_scale=None):
     return np.linalg.qr(g)[0]
 
 
+SEED, STREAM = 0x1234ABCD5678, 3
+
+
 def _select(rh, Q, eta, method="srrqr"):
-    sel, A = rh.subset_select(torch.from_numpy(np.ascontiguousarray(Q)), method, eta)
+    sel, A = rh.subset_select(torch.from_numpy(np.ascontiguousarray(Q)), method, eta, seed=SEED, stream=STREAM)
     return sel.numpy().astype(np.int64), A.numpy().T
 
 
 ORACLE = {"srrqr": lambda Q, eta: otk.srrqr_select(Q, eta=eta), "cpqr": lambda Q, eta: otk.cpqr_select(Q),
-          "deim": lambda Q, eta: otk.deim_select(Q)}
+          "deim": lambda Q, eta: otk.deim_select(Q),
+          "uniform": lambda Q, eta: otk.sample_select(Q, False, SEED, STREAM),
+          "leverage": lambda Q, eta: otk.sample_select(Q, True, SEED, STREAM)}
 
 
 def _check_valid(Q, sel, A, eta):
@@ -54,7 +60,8 @@ def _check_valid(Q, sel, A, eta):
 
 @pytest.mark.parametrize("I,ell,seed", [(50, 5, 1), (200, 20, 2), (64, 63, 3), (300, 40, 4), (1000, 64, 5),
                                         (9, 1, 6)])
-@pytest.mark.parametrize("method,eta", [("srrqr", 2.0), ("srrqr", 1.0), ("cpqr", None), ("deim", None)])
+@pytest.mark.parametrize("method,eta", [("srrqr", 2.0), ("srrqr", 1.0), ("cpqr", None), ("deim", None),
+                                        ("uniform", None), ("leverage", None)])
 def test_selection_equals_the_oracle(rh, I, ell, seed, method, eta):
     Q = _basis(I, ell, seed)
     sel, A = _select(rh, Q, 2.0 if eta is None else eta, method)
@@ -116,8 +123,22 @@ def test_failures_are_reported(rh):
     with pytest.raises(ValueError):
         rh.subset_select(torch.zeros((4, 2), dtype=torch.float32))
     with pytest.raises(ValueError):
-        rh.subset_select(torch.from_numpy(_basis(30, 4, 12)), "leverage")
+        rh.subset_select(torch.from_numpy(_basis(30, 4, 12)), "volume")
     from paper_1905_07311_gb300 import _lib
     import ctypes
     one = ctypes.c_void_p(1)
-    assert _lib.lib().rh_subset_select(30, 4, one, 3, 2.0, one, one) == 1       # unknown method
+    assert _lib.lib().rh_subset_select(30, 4, one, 5, 2.0, 0, 0, one, one) == 1       # unknown method
+
+
+@pytest.mark.parametrize("method", ["uniform", "leverage"])
+def test_sampling_depends_on_seed_and_stream(rh, method):
+    Q = _basis(200, 10, 13)
+    t = torch.from_numpy(Q)
+    a, _ = rh.subset_select(t, method, seed=1, stream=0)
+    b, _ = rh.subset_select(t, method, seed=1, stream=0)
+    c, _ = rh.subset_select(t, method, seed=2, stream=0)
+    d, _ = rh.subset_select(t, method, seed=1, stream=1)
+    assert torch.equal(a, b) and not torch.equal(a, c) and not torch.equal(a, d)
+    for s_, st in [(1, 0), (2, 0), (1, 1), (99, 7)]:
+        sel, _ = rh.subset_select(t, method, seed=s_, stream=st)
+        assert np.array_equal(sel.numpy(), otk.sample_select(Q, method == "leverage", s_, st))
