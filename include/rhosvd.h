@@ -160,6 +160,8 @@ rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0,
  *           NULL; for RH_F32_BF16X2 it is ||head + tail||^2 (FP32 sums over 32 values per thread
  *           and tile, FP64 above).
  *   mode    0-based mode n;  ell  number of columns, 1 <= ell <= RH_MAX_ELL.
+ *   On the tensor-core forms the first int32 of the workspace receives the wait status once the
+ *   stream has synchronised: 0, or the code of a bounded wait that gave up (Y is then invalid).
  *   Y       output, I_n x ell FP64, column-major (ld = I_n).
  *   norm2   optional (may be NULL): receives ||X||_F^2 (one FP64 value), accumulated
  *           in FP64 from the same pass over X.
@@ -229,7 +231,8 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
  * rh_mode_product_bf16 -- the first-mode product Y = X x_0 A^T on the tensor cores for a tensor in
  * a BF16 form (RH_BF16 / RH_BF16X2 / RH_F32_BF16X2): A is I_0 x k FP64 (1 <= k <= 64), split exactly into two BF16
  * pieces; Y is k x (N / I_0) FP32 (layout c + k p), all four piece products with FP32
- * accumulation.  Needs I_0 % 8 == 0.  Workspace: rh_mode_product_workspace_size.
+ * accumulation.  Needs I_0 % 8 == 0.  Workspace: rh_mode_product_workspace_size; its first int32
+ * receives the wait status as in rhosvd_sketch (0, or the code of a bounded wait that gave up).
  */
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k);
 rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
@@ -264,7 +267,10 @@ rh_status rh_left_svd(int32_t order, const int64_t* dims, int32_t dtype, const v
  *            1 = the QR of the sketch took the Householder branch; 2 = the truncation
  *            SVD went through the Gram matrix (FP32 data only, see below); 4 = the sketch and
  *            mode product of mode n ran on the tensor cores (BF16 forms); 8 = the truncation
- *            SVD went through the double-float Gram matrix.
+ *            SVD went through the double-float Gram matrix; 16 = a tensor-core kernel of mode n
+ *            gave up a bounded wait (a TMA or MMA completion that never arrived): the outputs
+ *            of that mode and of every later step are invalid.  The call stays asynchronous;
+ *            read info after the stream has synchronised.
  *   Size rule: ell_n <= min(I_n, prod of the other current sizes), else RH_EINVAL (or
  *   clamped, opts->clamp).  Steps per mode n (in order rho):
  *     sketch Y = G_(n) Omega_n; Q = orth(Y); B = Q^T G_(n) (mode-n product);

@@ -306,11 +306,19 @@ Bufs carve(Arena& ar, const Plan& pl) {
   return b;
 }
 
-__global__ void info_or_kernel(int32_t* info, int32_t bits) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *info |= bits;
+// info |= bits, plus 16 when a tensor-core kernel recorded a bounded wait that gave up (*err != 0);
+// the wait flag is cleared so that the next mode reports its own.
+__global__ void info_or_kernel(int32_t* info, int32_t bits, int32_t* err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (err != nullptr && *err != 0) {
+      bits |= 16;
+      *err = 0;
+    }
+    if (bits) *info |= bits;
+  }
 }
-rh_status set_info_bits(int32_t* info, int32_t bits, cudaStream_t st) {
-  info_or_kernel<<<1, 32, 0, st>>>(info, bits);
+rh_status set_info_bits(int32_t* info, int32_t bits, cudaStream_t st, int32_t* err = nullptr) {
+  info_or_kernel<<<1, 32, 0, st>>>(info, bits, err);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -402,7 +410,6 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       else
         s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
       if (s != RH_OK) return s;
-      if (info && (s = set_info_bits(info + sp.mode, 4, st)) != RH_OK) return s;
     } else {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
@@ -464,6 +471,11 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         cur_buf = wb;
       }
     }
+    // info bit 4: this mode's sketch and mode product ran on the tensor cores; bit 16: a tensor-core
+    // kernel of this mode gave up a bounded wait (the mode's outputs are invalid)
+    if (info && (tc || (o.truncate && sp.cp && sp.cp_tc && !last)) &&
+        (s = set_info_bits(info + sp.mode, tc ? 4 : 0, st, b.err)) != RH_OK)
+      return s;
   }
   if (norms) {
     record_step(nsteps);
@@ -551,8 +563,8 @@ static bool is_bf16_form(int32_t dtype) { return bf16_form(dtype); }
 static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell) {
   const ModeView v = mode_view(order, dims, 0);
   Arena ar(nullptr);
+  ar.take<int32_t>(4);   // wait status, first (documented)
   ar.take<float>((size_t)sketch_tc_ctas(v) * ell * v.I);
-  ar.take<int32_t>(4);
   ar.take<double>((size_t)sketch_tc_ctas(v));
   return ar.used;
 }
@@ -608,8 +620,8 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     }
     Arena ar(workspace);
     const int S = sketch_tc_ctas(v);
+    int32_t* err = ar.take<int32_t>(4);   // wait status: the first int32 of the workspace
     float* part = ar.take<float>((size_t)S * ell * v.I);
-    int32_t* err = ar.take<int32_t>(4);
     double* norm_part = ar.take<double>((size_t)S);
     cudaStream_t st = (cudaStream_t)stream;
     RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
@@ -664,8 +676,8 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k) {
   if (!bf16_form(dtype) || order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode != 0) return 0;
   Arena ar(nullptr);
+  ar.take<int32_t>(4);   // wait status, first (documented)
   ar.take<uint16_t>((size_t)128 * dims[0]);
-  ar.take<int32_t>(4);
   (void)k;
   return ar.used;
 }
@@ -724,8 +736,8 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
     return RH_ENOMEM;
   }
   Arena ar(workspace);
+  int32_t* err = ar.take<int32_t>(4);   // wait status: the first int32 of the workspace
   uint16_t* qa = ar.take<uint16_t>((size_t)128 * dims[0]);
-  int32_t* err = ar.take<int32_t>(4);
   cudaStream_t st = (cudaStream_t)stream;
   RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
   if (dtype == RH_F32_BF16X2) return launch_ttm_tc_f32(v, k, static_cast<const float*>(X), A, qa, Y, err, st);

@@ -136,6 +136,7 @@ def test_rsthosvd_bf16x2_matches_oracle(rh, shape, ranks, p, rho):
     torch.cuda.synchronize()
     info = T.info.cpu().numpy().tolist()
     assert info[0] & 4, info          # the first mode always runs on the tensor cores
+    assert not any(x & 16 for x in info), info   # no tensor-core wait gave up
     if shape == (256, 128, 96):
         assert info[1] & 4, info      # mode 2 follows with a unit-stride core (I_2 = 128)
     bits = Xb.cpu().numpy().view(np.uint16)
@@ -235,6 +236,7 @@ def test_rsthosvd_f32_split_first_mode_on_cuda_cores(rh, shape, ranks, p, rho, t
     torch.cuda.synchronize()
     info = T.info.cpu().numpy().tolist()
     assert [m for m in range(d) if info[m] & 4] == tc_modes, info
+    assert not any(x & 16 for x in info), info   # no tensor-core wait gave up
     Xe = X.astype(np.float64)
     rnd = {m: "bf16" for m in tc_modes}
     out = otk.rsthosvd(Xe, list(ranks), p, 5, rho=rho, omega_round=rnd, record=True, clamp=True)
