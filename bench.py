@@ -820,6 +820,52 @@ def wl_sparse(torch, rh, L, args, device, peaks, src):
             "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
 
 
+def wl_peaks(torch, rh, L, args, device, peaks, src):
+    """Rates the rooflines of the non-BF16 paths need, measured on this device: dense matmul in FP64,
+    TF32 and FP32 (torch.matmul, 8192^3 for TF32 / FP32, 4096^3 for FP64: 2 n^3 flops, best of the
+    timed steps) and the Omega generator (rh_omega: Philox4x32-10 + Box-Muller normals per second,
+    2^24 rows x 64 columns per launch; the 4 GB it writes take ~0.6 ms of its time at HBM speed)."""
+    out = {}
+    steps = max(3, args.steps)
+
+    def best_ms(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        stream = torch.cuda.current_stream(device)
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    clocks = Clocks(device.index or 0)
+    clocks.start()
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, n, tf32 in (("fp64", torch.float64, 4096, False), ("tf32", torch.float32, 8192, True),
+                              ("fp32", torch.float32, 8192, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device=device)
+        b = torch.randn(n, n, dtype=dt, device=device)
+        ms = best_ms(lambda: torch.matmul(a, b), steps)
+        out[f"{name}_matmul_tflops"] = round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 2)
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    nrows, ell = 1 << 24, 64
+    om = torch.empty((ell, nrows), dtype=torch.float32, device=device)
+    st = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    ms = best_ms(lambda: rh._lib.check(L.rh_omega(0, 0, 0, 0, nrows, ell, ctypes.c_void_p(om.data_ptr()), st)), steps)
+    out["omega_normals_per_s"] = round(nrows * ell / (ms * 1e-3), -6)
+    out["omega_ms"] = round(ms, 4)
+    out["clocks"] = clocks.stop()
+    out["how"] = wl_peaks.__doc__.split("\n\n")[0].replace("\n", " ")
+    return out
+
+
 def run_workload(args):
     import torch
 
@@ -833,7 +879,8 @@ def run_workload(args):
 
     L = _lib.lib()
     peaks, src = measured_peaks()
-    fn = {"hilbert200": wl_hilbert200, "lowp192": wl_lowp192, "batched": wl_batched, "sparse": wl_sparse}[args.workload]
+    fn = {"hilbert200": wl_hilbert200, "lowp192": wl_lowp192, "batched": wl_batched, "sparse": wl_sparse,
+          "peaks": wl_peaks}[args.workload]
     line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
     line.update(fn(torch, rh, L, args, device, peaks, src))
     print(json.dumps(line))
@@ -856,7 +903,7 @@ def main():
     ap.add_argument("--dims", type=int, nargs=3, default=None,
                     help="smaller cube for profiling captures (default 1024 1024 1024)")
     ap.add_argument("--workload", default="dense1024",
-                    choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse"],
+                    choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse", "peaks"],
                     help="dense1024: the benchmark line (default); the others measure the further configurations "
                          "and print one JSON line each")
     ap.add_argument("--batch-orders", default="3,4",

@@ -114,10 +114,14 @@ typedef struct rh_options {
   int32_t svd_route;             /* SVD of B for FP32 data: 0 = automatic (FP32 Gram, double-    */
                                  /* float Gram, tall-skinny QR, see rsthosvd); 1 = always the    */
                                  /* tall-skinny Householder QR of B^T (FP64 data always use it)  */
+  int32_t power_iters;           /* q >= 0 steps of randomized subspace iteration in each range  */
+                                 /* finder (Sec. 5 "Variants", used in Sec. 6): after Q = orth(Y)*/
+                                 /* each step sets W = orth(G_(n)^T Q), Y = G_(n) W, Q = orth(Y) */
+                                 /* (0 = Alg. 1 as printed; at most 8)                           */
 } rh_options;
 
 /* Fill ``opts`` with defaults: seed 0, tensor_id 0, p 5, rho decreasing, clamp 0, truncate 1,
- * svd_route 0. */
+ * svd_route 0, power_iters 0. */
 void rh_options_default(rh_options* opts);
 
 /* Version string and the message of the last failure on this thread ("" after success). */
@@ -126,6 +130,19 @@ const char* rh_last_error(void);
 
 /* Number of CUDA kernels this library has launched in this process (all threads). */
 uint64_t rh_kernel_launches(void);
+
+/*
+ * rh_test_wait_probe -- test support for the bounded waits of the tensor-core kernels (the paper
+ * has no counterpart).  After rh_test_wait_probe(k) with k >= 0, the tensor-core launches of the
+ * process are counted from 0 and launch number k runs as a probe: right after initialising its
+ * mbarriers, before it allocates tensor memory or issues any copy or MMA, each CTA waits a short
+ * bounded time on a barrier that nothing arrives at, records wait code 64 in the call's wait
+ * status and returns without writing its outputs.  The call that made that launch then reports
+ * the give-up as it reports any other: info bit 16 for that mode (rsthosvd, rsthosvd_host), the
+ * first int32 of the workspace (rhosvd_sketch, rh_mode_product_bf16), RH_ETIMEOUT (adaptive_rank).
+ * k < 0 (the default) turns the probe off.  Process-wide; not for concurrent use with other work.
+ */
+void rh_test_wait_probe(int64_t launch);
 
 /*
  * Per-launch timing of the main kernels (measurement support, off by default).
@@ -179,15 +196,19 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
  * rhosvd_sketch_static -- rhosvd_sketch for callers that must not allocate device memory.
  *   The paper has no counterpart: this is a deployment variant of the sketch above, with the
  *   same arguments minus the workspace and the same output (up to the order of the FP32/FP64
- *   partial sums).  Its scratch lives in a 16 MiB static device array inside the library that
+ *   partial sums), for the plain forms only: dtype must be RH_F32 or RH_F64 (the BF16 and E4M3
+ *   forms that rhosvd_sketch also accepts return RH_EINVAL here).  Its scratch lives in a 16 MiB static device array inside the library that
  *   every GPU loading the library keeps until the process exits; the caller allocates only
  *   X, Y and norm2.  Intended for code that may not call cudaMalloc: plugins whose host
  *   framework owns all device memory, loops that cannot take cudaMalloc's implicit device
  *   synchronisation, processes whose device memory budget is fully reserved.
  *   Limit: I_mode * ell * (4 or 8 bytes) plus a few KB of partial norms must fit in 16 MiB,
  *   otherwise RH_EINVAL with a message (the number of split-K partials shrinks to fit).
- *   The first call on a device looks up the array's address (cudaGetSymbolAddress) and must
- *   precede any stream capture.  All calls share the array and leave their contents in it;
+ *   Every call outside stream capture looks up the array's address (cudaGetSymbolAddress), so
+ *   a device reset, which may move the array, is seen by the next call; a call on a capturing
+ *   stream reuses the address of the last uncaptured call on that device, so the first call on
+ *   a device must precede any stream capture (RH_EINVAL otherwise), and a graph captured before
+ *   a device reset holds the old address like any other captured pointer.  All calls share the array and leave their contents in it;
  *   every element a call reads is written by that call first, but calls that overlap on the
  *   GPU race.  No cudaMalloc, cudaFree or allocating library routine is called.
  */
@@ -506,6 +527,10 @@ rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t meth
  *   X_host       host tensor (pinned memory gives asynchronous copies), column-major.
  *   factors_host host array of ``order`` host pointers, I_n x k_n FP64 each.
  *   core_host    host buffer, k_1 x ... x k_d FP64;  norms_host optional, 2 FP64.
+ *   info_host    optional host array of ``order`` int32 receiving the per-mode flags of rsthosvd
+ *                (``info``), copied back with the results; bit 16 marks a mode whose tensor-core
+ *                kernel gave up a bounded wait, so that mode's outputs and every later step's
+ *                are invalid.  Read it after the stream has synchronised.
  *   workspace    DEVICE buffer of rsthosvd_host_workspace_size bytes; it holds the device
  *                copy of X, the device outputs and the rsthosvd workspace.
  */
@@ -513,8 +538,8 @@ size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t 
                                     const rh_options* opts);
 rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const void* X_host,
                         const int32_t* ranks, const rh_options* opts, double* const* factors_host,
-                        double* core_host, double* norms_host, void* workspace, size_t workspace_bytes,
-                        void* stream);
+                        double* core_host, double* norms_host, int32_t* info_host, void* workspace,
+                        size_t workspace_bytes, void* stream);
 
 #ifdef __cplusplus
 }

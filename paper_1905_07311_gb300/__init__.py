@@ -668,6 +668,7 @@ class RsthosvdHostCall:
             ncore *= k
         self.core = torch.empty(ncore, dtype=torch.float64).pin_memory()
         self.norms = torch.empty(2, dtype=torch.float64).pin_memory()
+        self.info = torch.zeros(d, dtype=torch.int32).pin_memory()
         self.fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in self.factors])
         n = 1
         for v in self.dims:
@@ -676,12 +677,12 @@ class RsthosvdHostCall:
             self.h2d_bytes = fp8_layout(self.dims)["bytes"]
         else:
             self.h2d_bytes = n * {RH_F64: 8, _lib.RH_BF16: 2}.get(self.dt, 4)
-        self.d2h_bytes = 8 * (sum(self.dims[k] * ko[k] for k in range(d)) + ncore + 2)
+        self.d2h_bytes = 8 * (sum(self.dims[k] * ko[k] for k in range(d)) + ncore + 2) + 4 * d
         self.device = torch.device(device)
 
     def run(self, X_host):
         if X_host.is_cuda:
             raise ValueError("X_host must be a host tensor")
         check(lib().rsthosvd_host(len(self.dims), self.da, self.dt, _ptr(X_host), self.ra, ctypes.byref(self.opts),
-                                  self.fptrs, _ptr(self.core), _ptr(self.norms), _ptr(self.ws), self.ws_bytes,
-                                  _stream(self.device)))
+                                  self.fptrs, _ptr(self.core), _ptr(self.norms), _ptr(self.info), _ptr(self.ws),
+                                  self.ws_bytes, _stream(self.device)))

@@ -21,7 +21,7 @@ STATUS = {0: "RH_OK", 1: "RH_EINVAL", 2: "RH_ENOMEM", 3: "RH_ECUDA", 4: "RH_ENUM
 class RhOptions(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("tensor_id", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("rho", ctypes.c_int32 * RH_MAX_ORDER), ("clamp", ctypes.c_int32), ("truncate", ctypes.c_int32),
-                ("svd_route", ctypes.c_int32)]
+                ("svd_route", ctypes.c_int32), ("power_iters", ctypes.c_int32)]
 
 
 class RhError(RuntimeError):
@@ -83,7 +83,8 @@ SIGNATURES = {
     "rsthosvd_batched_plan_destroy": (None, [_P]),
     "rh_subset_select": (_I32, [_I64, _I32, _P, _I32, ctypes.c_double, _U64, ctypes.c_uint32, _P, _P]),
     "rsthosvd_host_workspace_size": (_SZ, [_I32, _P, _I32, _P, ctypes.POINTER(RhOptions)]),
-    "rsthosvd_host": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _SZ, _P]),
+    "rsthosvd_host": (_I32, [_I32, _P, _I32, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
+    "rh_test_wait_probe": (None, [_I64]),
 }
 
 
@@ -117,7 +118,7 @@ def i32_array(vals):
     return (ctypes.c_int32 * len(vals))(*[int(v) for v in vals])
 
 
-def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True, svd_route=0):
+def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True, svd_route=0, power_iters=0):
     o = RhOptions()
     lib().rh_options_default(ctypes.byref(o))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
@@ -129,4 +130,5 @@ def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True,
     o.clamp = int(bool(clamp))
     o.truncate = int(bool(truncate))
     o.svd_route = int(svd_route)
+    o.power_iters = int(power_iters)
     return o

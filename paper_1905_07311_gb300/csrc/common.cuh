@@ -63,6 +63,10 @@ struct Arena {
   }
 };
 
+// Wait-timeout probe (profile.cu): 1 for the tensor-core launch that rh_test_wait_probe armed,
+// else 0; every tensor-core launch calls it once.
+int tc_probe_next();
+
 // Per-launch timing (profile.cu): a scope records an event before and after the kernels
 // it encloses when profiling is on.  kind: 0 sketch, 1 mode product, 2 QR of the sketch,
 // 3 truncation SVD; tag: the step of the algorithm (0 = first processed mode).

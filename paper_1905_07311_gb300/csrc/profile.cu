@@ -1,6 +1,7 @@
 // Optional per-launch timing of the library's main kernels with CUDA events recorded on
 // the launching stream (rh_profile_enable / rh_profile_collect in the C ABI).  Off by
 // default; when on, each timed launch is bracketed by two events from a pool.
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -51,9 +52,27 @@ ProfileScope::~ProfileScope() {
   if (idx_ < (int)g_recs.size()) cudaEventRecord(g_recs[idx_].b, st_);
 }
 
+// Wait-timeout probe: the tensor-core launches of this process are numbered from the last
+// rh_test_wait_probe call on; the one whose number equals the armed index gets probe = 1.
+namespace {
+std::atomic<int64_t> g_probe_at{-1};
+std::atomic<int64_t> g_tc_count{0};
+}  // namespace
+
+int tc_probe_next() {
+  const int64_t at = g_probe_at.load();
+  const int64_t k = g_tc_count.fetch_add(1);
+  return (at >= 0 && k == at) ? 1 : 0;
+}
+
 }  // namespace rh
 
 extern "C" {
+
+void rh_test_wait_probe(int64_t launch) {
+  rh::g_tc_count.store(0);
+  rh::g_probe_at.store(launch);
+}
 
 void rh_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(rh::g_mu);

@@ -909,13 +909,14 @@ size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t 
   }
   ar.take<double>((size_t)ncore);
   ar.take<double>(2);
+  ar.take<int32_t>((size_t)order);
   carve(ar, pl);
   return ar.used;
 }
 
 rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const void* X_host, const int32_t* ranks,
                         const rh_options* opts, double* const* factors_host, double* core_host, double* norms_host,
-                        void* workspace, size_t workspace_bytes, void* stream) {
+                        int32_t* info_host, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   const rh_options o = opts_or_default(opts);
   Plan pl;
@@ -943,14 +944,17 @@ rh_status rsthosvd_host(int32_t order, const int64_t* dims, int32_t dtype, const
   }
   double* cored = ar.take<double>((size_t)ncore);
   double* normsd = ar.take<double>(2);
+  int32_t* infod = ar.take<int32_t>((size_t)order);
   const Bufs b = carve(ar, pl);
   cudaStream_t st = (cudaStream_t)stream;
   RH_CUDA_TRY(cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, st));
+  if ((s = emit_memset(SITE_ENTRY, 0, infod, sizeof(int32_t) * order, st)) != RH_OK) return s;
   if (pl.dtype == RH_F64)
-    s = run_rsthosvd<double>(pl, Xd, o, fd.data(), cored, normsd, nullptr, b, st);
+    s = run_rsthosvd<double>(pl, Xd, o, fd.data(), cored, normsd, infod, b, st);
   else
-    s = run_rsthosvd<float>(pl, Xd, o, fd.data(), cored, normsd, nullptr, b, st);
+    s = run_rsthosvd<float>(pl, Xd, o, fd.data(), cored, normsd, infod, b, st);
   if (s != RH_OK) return s;
+  if (info_host) RH_CUDA_TRY(cudaMemcpyAsync(info_host, infod, sizeof(int32_t) * order, cudaMemcpyDeviceToHost, st));
   for (int k = 0; k < order; ++k)
     RH_CUDA_TRY(cudaMemcpyAsync(factors_host[k], fd[k], sizeof(double) * dims[k] * kout[k], cudaMemcpyDeviceToHost, st));
   RH_CUDA_TRY(cudaMemcpyAsync(core_host, cored, sizeof(double) * ncore, cudaMemcpyDeviceToHost, st));

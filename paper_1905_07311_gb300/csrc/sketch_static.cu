@@ -14,9 +14,11 @@
 //   * the scratch array is kStaticScratchBytes = 16 MiB; the split count is reduced to fit,
 //     and a request whose single-split scratch (I_mode * ell * sizeof(element) plus the
 //     partial norms) still exceeds it is rejected with RH_EINVAL and a message;
-//   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current) and caches it; make that first call
-//     before any stream capture;
+//   * every call made outside stream capture looks up the array's device address with
+//     cudaGetSymbolAddress (with the device current), so a device reset, which reloads the
+//     module and may move the array, is picked up by the next call; a call made while its
+//     stream is capturing uses the address of the last uncaptured call on that device, so the
+//     first call on a device must come before any stream capture;
 //   * every call on a device shares the one array and leaves the last call's contents in
 //     it; each call overwrites every scratch element it reads, so nothing needs clearing,
 //     but calls that overlap on the GPU (different streams, no ordering) race on the array.
@@ -37,19 +39,26 @@ static __device__ __align__(256) unsigned char g_sketch_scratch[kStaticScratchBy
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_sketch_scratch on the current device (looked up once per device).
-rh_status scratch_address(void** out) {
+// Device address of g_sketch_scratch on the current device: looked up on every call outside
+// stream capture (the module, and with it the array, is reloaded after a device reset); inside a
+// capture the address of the last uncaptured call on this device is used.
+rh_status scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
   RH_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("rhosvd_sketch_static: device ordinal beyond the supported 64 devices");
     return RH_EUNSUPPORTED;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RH_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (g_scratch_addr[dev] == nullptr) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     RH_CUDA_TRY(cudaGetSymbolAddress(&p, g_sketch_scratch));
     g_scratch_addr[dev] = p;
+  } else if (g_scratch_addr[dev] == nullptr) {
+    set_error("rhosvd_sketch_static: the first call on a device must come before any stream capture");
+    return RH_EINVAL;
   }
   *out = g_scratch_addr[dev];
   return RH_OK;
@@ -102,13 +111,13 @@ extern "C" rh_status rhosvd_sketch_static(int32_t order, const int64_t* dims, in
   SketchPlan pl;
   rh_status s = plan_static(mode_view(order, dims, mode), ell, esz, pl);
   if (s != RH_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
   void* base = nullptr;
-  if ((s = scratch_address(&base)) != RH_OK) return s;
+  if ((s = scratch_address(st, &base)) != RH_OK) return s;
   char* b = static_cast<char*>(base);
   void* part = b;
   double* part_norm = reinterpret_cast<double*>(b + align256(pl.part_elems() * esz));
   const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)mode;
-  cudaStream_t st = (cudaStream_t)stream;
   if (dtype == RH_F64) {
     if ((s = launch_sketch<double>(pl, static_cast<const double*>(X), seed, sid, static_cast<double*>(part), part_norm,
                                    st)) != RH_OK)

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, int npieces,
                      int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
                      uint32_t sid, float* __restrict__ part, double* __restrict__ norm_part,
-                     int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld) {
+                     int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld, int probe) {
   using Cfg = SketchCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -112,6 +112,10 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     }
     tc::mbar_init(&S.done, 1);
     tc::fence_mbar_init();
+  }
+  if (probe) {   // wait-timeout probe: nothing allocated or issued yet
+    if (threadIdx.x == 0) tc::mbar_wait(&S.done, 0, err, tc::kProbeCode, tc::kProbeSpin);
+    return;
   }
   if (warp == 1) {
     tc::tmem_alloc(&S.tmem_slot, tmem_cols);
@@ -471,7 +475,7 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m1, np, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      nullptr, err, nullptr, 0);
+      nullptr, err, nullptr, 0, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -494,7 +498,7 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, nullptr, 0);
+      norm_part, err, nullptr, 0, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -519,7 +523,7 @@ rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, con
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 1, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, scales, ld);
+      norm_part, err, scales, ld, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

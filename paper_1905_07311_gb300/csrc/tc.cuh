@@ -41,12 +41,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase with the given parity; returns false (and sets *err) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int32_t code) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int32_t code,
+                                          uint32_t limit = kSpinLimit) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   if (err) atomicExch(err, code);
   return false;
 }
+
+// Wait-timeout probe (test support).  A launch that the host marks as probed has thread 0 wait,
+// with a short limit, on an mbarrier that nothing arrives at, right after the barriers are
+// initialised -- before any TMEM allocation, TMA copy or MMA -- so the wait gives up with
+// nothing in flight, records kProbeCode in *err and the whole CTA returns.  This exercises the
+// reporting path of a bounded wait that gave up (info bit 16, the wait status words) without
+// stalling a pipeline.
+constexpr int32_t kProbeCode = 64;
+constexpr uint32_t kProbeSpin = 1u << 12;
 
 // ---- proxies -------------------------------------------------------------------------
 // Generic-proxy writes to shared memory that the async proxy (TMA, tensor cores) will read.

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
                   float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld,
-                  CoreOut co) {
+                  CoreOut co, int probe) {
   using Cfg = TtmCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -108,6 +108,10 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
       tc::mbar_init(&S.tempty[b], 128);
     }
     tc::fence_mbar_init();
+  }
+  if (probe) {   // wait-timeout probe: nothing allocated or issued yet
+    if (threadIdx.x == 0) tc::mbar_wait(&S.tfull[0], 0, err, tc::kProbeCode, tc::kProbeSpin);
+    return;
   }
   if (warp == 1) {
     tc::tmem_alloc(&S.tmem_slot, tmem_cols);
@@ -344,7 +348,7 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{});
+                                                                         nullptr, 0, CoreOut{}, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -369,7 +373,7 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{});
+                                                                         nullptr, 0, CoreOut{}, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -399,7 +403,7 @@ rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, Cor
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err, nullptr,
-                                                                         0, co);
+                                                                         0, co, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -425,7 +429,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 1, v.I, v.M(), ell, B, err,
-                                                                         scales, ld, CoreOut{});
+                                                                         scales, ld, CoreOut{}, tc_probe_next());
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

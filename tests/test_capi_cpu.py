@@ -281,9 +281,9 @@ def test_every_entry_point_validates_before_the_device(L):
     assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, ks, o, ptr3, None, one, None, one, 1, None) == 2
     # host-buffer R-STHOSVD and R-HOSVD (Alg. 3, Alg. 2)
     bad = _lib.i32_array([26, 4, 4])       # r_0 + p = 31 > I_0 = 30
-    assert L.rsthosvd_host(3, d3, 1, one, bad, o, ptr3, one, None, one, big, None) == 1
-    assert L.rsthosvd_host(3, d3, 1, None, ks, o, ptr3, one, None, one, big, None) == 1
-    assert L.rsthosvd_host(3, d3, 1, one, ks, o, ptr3, one, None, one, 1, None) == 2
+    assert L.rsthosvd_host(3, d3, 1, one, bad, o, ptr3, one, None, None, one, big, None) == 1
+    assert L.rsthosvd_host(3, d3, 1, None, ks, o, ptr3, one, None, None, one, big, None) == 1
+    assert L.rsthosvd_host(3, d3, 1, one, ks, o, ptr3, one, None, None, one, 1, None) == 2
     assert L.rsthosvd_host_workspace_size(3, d3, 1, ks, o) > L.rsthosvd_workspace_size(3, d3, 1, ks, o)
     assert L.rhosvd(3, d3, 1, one, bad, o, ptr3, one, None, None, one, big, None) == 1
     assert L.rhosvd(3, d3, 1, one, ks, o, ptr3, one, None, None, one, 1, None) == 2

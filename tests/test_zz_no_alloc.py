@@ -70,8 +70,10 @@ def test_static_sketch_rejects_sizes_beyond_the_array(rh):
     from paper_1905_07311_gb300 import _lib
 
     dims = [40000, 3]                 # 40000 * 64 * 8 bytes > 16 MiB even with one split
-    X = torch.zeros(1, dtype=torch.float64, device="cuda")
-    Y = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # full-size buffers: a regression of the size check gives a wrong return code, not an
+    # out-of-bounds access
+    X = torch.zeros(40000 * 3, dtype=torch.float64, device="cuda")
+    Y = torch.zeros(64 * 40000, dtype=torch.float64, device="cuda")
     code = _lib.lib().rhosvd_sketch_static(2, _lib.i64_array(dims), _lib.RH_F64, ctypes.c_void_p(X.data_ptr()), 0,
                                            64, 0, 0, ctypes.c_void_p(Y.data_ptr()), None, None)
     assert code == 1
