@@ -264,7 +264,7 @@ class RsthosvdCall:
     ALG = "rsthosvd"
 
     def __init__(self, dims, dtype, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True,
-                 device="cuda", svd_route=0):
+                 device="cuda", svd_route=0, power_iters=0):
         torch = _torch()
         self.dims = [int(x) for x in dims]
         d = len(self.dims)
@@ -275,7 +275,7 @@ class RsthosvdCall:
             self.dt = RH_F64 if dtype == torch.float64 else RH_F32
             self.factor = 1
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, truncate=truncate,
-                                 svd_route=svd_route)
+                                 svd_route=svd_route, power_iters=power_iters)
         self.da = i64_array(self.dims)
         self.ra = i32_array(ranks)
         self._fn = getattr(lib(), self.ALG)
@@ -337,10 +337,11 @@ class RhosvdCall(RsthosvdCall):
     ALG = "rhosvd"
 
 
-def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, svd_route=0):
-    """R-HOSVD (Alg. 2) of the flat column-major tensor X with sizes ``dims``."""
+def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, svd_route=0, power_iters=0):
+    """R-HOSVD (Alg. 2) of the flat column-major tensor X with sizes ``dims``; ``power_iters`` steps of
+    randomized subspace iteration in every range finder (rh_options.power_iters)."""
     call = RhosvdCall(dims, X.dtype, ranks, p=p, seed=seed, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
-                      device=X.device, svd_route=svd_route)
+                      device=X.device, svd_route=svd_route, power_iters=power_iters)
     return call.run(X)
 
 
@@ -497,15 +498,16 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, c
 
 
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None,
-             svd_route=0):
+             svd_route=0, power_iters=0):
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 
     ``form="bf16x2"`` (X from split_bf16x2), ``form="bf16"`` (X holding BF16 bit patterns),
     ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly) or ``form="fp8_e4m3"`` (X a uint8
     buffer in the layout of fp8_layout) selects the tensor-core forms for the first mode.
-    ``svd_route=1`` keeps the SVD of B on the tall-skinny QR (see rh_options.svd_route)."""
+    ``svd_route=1`` keeps the SVD of B on the tall-skinny QR (see rh_options.svd_route).
+    ``power_iters`` adds that many randomized subspace-iteration steps to every range finder."""
     call = RsthosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, rho=rho, tensor_id=tensor_id, clamp=clamp,
-                        truncate=truncate, device=X.device, svd_route=svd_route)
+                        truncate=truncate, device=X.device, svd_route=svd_route, power_iters=power_iters)
     return call.run(X)
 
 
@@ -516,7 +518,7 @@ class RsthosvdBatchedCall:
     returns one Tucker per tensor (views of buffers allocated once here)."""
 
     def __init__(self, dims_list, ranks_list, dtype, p=5, seed=0, tensor_id=0, clamp=False, truncate=True,
-                 streams=0, device="cuda", svd_route=0):
+                 streams=0, device="cuda", svd_route=0, power_iters=0):
         torch = _torch()
         if len(dims_list) != len(ranks_list) or not dims_list:
             raise ValueError("dims_list and ranks_list must be non-empty and of equal length")
@@ -529,7 +531,7 @@ class RsthosvdBatchedCall:
         else:
             self.dt = RH_F64 if dtype == torch.float64 else RH_F32
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
-                                 svd_route=svd_route)
+                                 svd_route=svd_route, power_iters=power_iters)
         self.orders = i32_array([len(d) for d in self.dims_list])
         self.da = i64_array([x for d in self.dims_list for x in d])
         self.ra = i32_array([int(r) for rk in ranks_list for r in rk])
@@ -624,13 +626,13 @@ class BatchedPlan:
 
 
 def rsthosvd_batched(Xs, dims_list, ranks_list, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, form=None,
-                     streams=0, svd_route=0):
+                     streams=0, svd_route=0, power_iters=0):
     """R-STHOSVD (Alg. 3) of every tensor in ``Xs`` (flat column-major, sizes ``dims_list[i]``) in
     one batched call; returns a list of Tucker results.  ``streams=0`` runs FP32 / FP64 truncated
     requests on the grouped engine (one launch per stage for the whole batch)."""
     call = RsthosvdBatchedCall(dims_list, ranks_list, form or Xs[0].dtype, p=p, seed=seed, tensor_id=tensor_id,
                                clamp=clamp, truncate=truncate, streams=streams, device=Xs[0].device,
-                               svd_route=svd_route)
+                               svd_route=svd_route, power_iters=power_iters)
     return call.run(Xs)
 
 

@@ -412,6 +412,7 @@ size_t adaptive_rank_workspace_size(int32_t order, const int64_t* dims, int32_t 
   rh_options o;
   rh_options_default(&o);
   if (opts) o = *opts;
+  if (o.power_iters != 0) return 0;
   bool tc = false, as_f32 = false;
   if (lowp_plan(order, dims, dtype, variant, max_ranks, o, &tc, &as_f32) != RH_OK) return 0;
   if (as_f32) dtype = RH_F32;
@@ -443,6 +444,10 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
   rh_options o;
   rh_options_default(&o);
   if (opts) o = *opts;
+  if (o.power_iters != 0) {
+    set_error("unsupported: the adaptive range finder runs without subspace iteration (power_iters must be 0)");
+    return RH_EUNSUPPORTED;
+  }
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
   RH_CHECK_ARG(o.svd_route == 0 || o.svd_route == 1, "svd_route must be 0 or 1");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");

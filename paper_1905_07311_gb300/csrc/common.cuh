@@ -70,7 +70,7 @@ int tc_probe_next();
 // Per-launch timing (profile.cu): a scope records an event before and after the kernels
 // it encloses when profiling is on.  kind: 0 sketch, 1 mode product, 2 QR of the sketch,
 // 3 truncation SVD; tag: the step of the algorithm (0 = first processed mode).
-enum { PROF_SKETCH = 0, PROF_TTM = 1, PROF_ORTH = 2, PROF_TRUNC = 3, PROF_TTM_CORE = 4, PROF_JACOBI = 5 };
+enum { PROF_SKETCH = 0, PROF_TTM = 1, PROF_ORTH = 2, PROF_TRUNC = 3, PROF_TTM_CORE = 4, PROF_JACOBI = 5, PROF_POWER = 6 };
 class ProfileScope {
  public:
   ProfileScope(int kind, int tag, cudaStream_t st);
@@ -269,6 +269,18 @@ KernelRef* kref() {
 // problems with the same key and kernel become one grouped launch (grouped.cu).
 enum LaunchSite : int {
   SITE_ENTRY = 0,
+  // a subspace-iteration step (its own step key, before the QR sites it reuses)
+  SITE_POWER_CAST = 1,
+  SITE_POWER_TTM,
+  SITE_POWER_ZERO,
+  SITE_POWER_TSQR,          // sub = level of the reduction tree
+  SITE_POWER_TRSM,
+  SITE_POWER_GRAM,          // + 1: its reduce
+  SITE_POWER_GRAM_REDUCE,
+  SITE_POWER_CHOL,
+  SITE_POWER_TRSM2,
+  SITE_POWER_SKETCH = 12,
+  SITE_POWER_SKETCH_REDUCE,
   SITE_SKETCH = 10,
   SITE_SKETCH_REDUCE,
   SITE_ORTH_ZERO = 20,
@@ -318,5 +330,8 @@ rh_status emit(int site, int sub, dim3 grid, size_t smem, cudaStream_t st, const
 rh_status emit_memset(int site, int sub, void* p, size_t bytes, cudaStream_t st);
 bool recording();
 void record_step(int step);
+// Step keys of a recorded program: mode step j of the algorithm starts key kStepStride j, its
+// subspace-iteration steps take the keys that follow (at most kStepStride - 1 of them).
+constexpr int kStepStride = 32;
 
 }  // namespace rh

@@ -48,8 +48,10 @@ __global__ void __launch_bounds__(256) table_copy_kernel(const TableChunk c, uin
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = c.w[i];
 }
 
+// The default dynamic shared-memory limit of a kernel is 48 KB minus its static shared memory, so
+// any dynamic size is opted in explicitly (once per kernel and size).
 rh_status opt_in_smem(const void* fn, size_t smem, std::atomic<size_t>* done) {
-  if (smem <= 48 * 1024 || smem <= done->load(std::memory_order_acquire)) return RH_OK;
+  if (smem == 0 || smem <= done->load(std::memory_order_acquire)) return RH_OK;
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (smem > done->load(std::memory_order_relaxed)) {
     RH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -22,7 +22,15 @@ rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_
                         cudaStream_t st);
 template <typename T>
 rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y,
-                               double* norm2, cudaStream_t st);
+                               double* norm2, cudaStream_t st, int site = SITE_SKETCH_REDUCE);
+// Y = G_(n) W with a dense M x ell operand W stored like a mode product's output, (L, ell, R):
+// element (p, c) at (p % L) + L (c + ell (p / L)) -- the sketch of a subspace-iteration step.
+// split (FP32): every element of G enters as the sum of its exact BF16 head and tail.  Partial
+// sketches in part (pl.part_elems()), summed by launch_sketch_reduce (no norm).
+SketchPlan plan_sketch_dense(const ModeView& v, int ell);
+template <typename T>
+rh_status launch_sketch_dense(const SketchPlan& pl, const T* G, const T* W, bool split, T* part, cudaStream_t st,
+                              int site);
 
 // ---- tensor-core sketch over BF16 pieces (sketch_tc.cu) --------------------------------
 bool sketch_tc_supported(const ModeView& v, int ell);
@@ -137,7 +145,15 @@ template <typename T>
 rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, const double* Ub, double* A, T* Uc,
                                  cudaStream_t st);
 template <typename T>
-rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st);
+rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st, int site = SITE_CAST_Q);
+
+// Basis of a subspace-iteration step: B (the (L, ell, R) view of tr, entries T) is replaced by W, an
+// orthonormal basis of range(B^T) stored in the same layout (tall-skinny Householder R, W = B^T R^{-1},
+// one CholeskyQR pass).  ws holds power_workspace_elems(tr) elements of T.
+template <typename T>
+size_t power_workspace_elems(const TruncPlan& tr);
+template <typename T>
+rh_status launch_power_basis(const TruncPlan& tr, T* B, T* ws, cudaStream_t st);
 rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st);
 
 }  // namespace rh

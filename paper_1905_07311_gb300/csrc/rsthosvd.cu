@@ -65,6 +65,7 @@ struct Step {
   int ell;      // sketch width r + p (possibly clamped)
   int ko;       // output width of the mode: r (truncate) or ell
   SketchPlan sk;
+  SketchPlan skd;       // sketch against a dense operand (subspace-iteration steps)
   TruncPlan tr;
   bool tc = false;      // sketch and mode product on the tensor cores (FP32 core split on the fly)
   bool cp = false;      // truncated core by the core product (B has the new mode fastest) in the order cout
@@ -81,7 +82,28 @@ struct Plan {
   int32_t in_form = -1;   // a bf16_form input (first mode on the tensor cores when possible), else -1
   size_t tc_part = 0, qa_elems = 0;
   std::vector<int64_t> dims0;   // the input sizes
+  int power = 0;                // subspace-iteration steps per range finder
 };
+
+// Subspace iteration (opts.power_iters): the dense-operand sketch plan of every step and the
+// workspace of its basis step.
+rh_status plan_power(const rh_options& o, Plan& pl) {
+  RH_CHECK_ARG(o.power_iters >= 0 && o.power_iters <= 8, "power_iters must be in [0, 8]");
+  pl.power = o.power_iters;
+  if (!pl.power) return RH_OK;
+  if (pl.in_form >= 0 && pl.in_form != RH_F32_BF16X2) {
+    set_error("unsupported: subspace iteration needs FP64, FP32 or RH_F32_BF16X2 input (its sketch reads G_(n) "
+              "on the CUDA cores)");
+    return RH_EUNSUPPORTED;
+  }
+  for (Step& st : pl.steps) {
+    st.skd = plan_sketch_dense(st.v, st.ell);
+    pl.max_part = std::max(pl.max_part, st.skd.part_elems());
+    pl.max_trunc = std::max(pl.max_trunc, pl.dtype == RH_F64 ? power_workspace_elems<double>(st.tr)
+                                                               : power_workspace_elems<float>(st.tr));
+  }
+  return RH_OK;
+}
 
 rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks, const rh_options& o,
                     Plan& pl) {
@@ -209,7 +231,7 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
       pl.qa_elems = std::max(pl.qa_elems, (size_t)128 * sp.v.I);
     }
   }
-  return RH_OK;
+  return plan_power(o, pl);
 }
 
 // Alg. 2: every mode is sketched on the input tensor itself (no current core).
@@ -260,7 +282,7 @@ rh_status make_plan_hosvd(int32_t order, const int64_t* dims, int32_t dtype, con
   size_t fe = 0;
   pl.max_tensor = std::max(pl.max_tensor, core_chain_elems(order, dims, ks.data(), &fe));
   pl.fac_elems = fe;
-  return RH_OK;
+  return plan_power(o, pl);
 }
 
 struct Bufs {
@@ -323,6 +345,42 @@ rh_status set_info_bits(int32_t* info, int32_t bits, cudaStream_t st, int32_t* e
   return RH_OK;
 }
 
+// Randomized subspace iteration (Sec. 5 "Variants"; used with one step in Sec. 6): q steps of
+// W = orth(G_(n)^T Q), Y = G_(n) W, Q = orth(Y) after the first QR of the range finder.  B = Q^T G_(n)
+// is the mode product (on the tensor cores when the mode's sketch runs there, with Q split into
+// BF16 pieces as for the mode product of Alg. 1 step 3), W replaces B in B's buffer
+// (launch_power_basis), Y = G_(n) W is a sketch against the dense W (on a tensor-core mode every
+// element of G enters as its BF16 head + tail, the value the tensor-core kernels read), then the
+// QR of Alg. 1 step 2.  Step keys j kStepStride + 1 + it keep a recorded program's keys increasing.
+template <typename T>
+rh_status run_power(const Plan& pl, const Step& sp, int j, const T* cur, const float* tc_src, bool tc, const Bufs& b,
+                    T* Bw, int32_t* info, cudaStream_t st) {
+  rh_status s;
+  for (int it = 0; it < pl.power; ++it) {
+    record_step(kStepStride * j + 1 + it);
+    ProfileScope ps(PROF_POWER, j, st);
+    if (tc) {
+      if ((s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(Bw), b.err, st)) != RH_OK)
+        return s;
+    } else {
+      if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st, SITE_POWER_CAST)) != RH_OK) return s;
+      if ((s = launch_ttm<T, T>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, Bw, st, SITE_POWER_TTM)) != RH_OK)
+        return s;
+    }
+    if ((s = launch_power_basis<T>(sp.tr, Bw, static_cast<T*>(b.trunc), st)) != RH_OK) return s;
+    const T* G = tc ? reinterpret_cast<const T*>(tc_src) : cur;
+    if ((s = launch_sketch_dense<T>(sp.skd, G, Bw, tc, static_cast<T*>(b.part), st, SITE_POWER_SKETCH)) != RH_OK)
+      return s;
+    if ((s = launch_sketch_reduce<T>(sp.skd, static_cast<const T*>(b.part), nullptr, b.Y, nullptr, st,
+                                     SITE_POWER_SKETCH_REDUCE)) != RH_OK)
+      return s;
+    if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st,
+                                   sizeof(T) == 4)) != RH_OK)
+      return s;
+  }
+  return RH_OK;
+}
+
 template <typename T>
 rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, double* const* factors, double* core,
                        double* norms, int32_t* info, const Bufs& b, cudaStream_t st) {
@@ -341,7 +399,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
   const uint16_t* piece1 = (pl.in_form == RH_BF16X2) ? piece0 + pl.steps[0].v.I * pl.steps[0].v.M() : nullptr;
   if (tc0) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
   for (int j = 0; j < nsteps; ++j) {
-    record_step(j);
+    record_step(kStepStride * j);
     const Step& sp = pl.steps[j];
     const bool last = (j == nsteps - 1);
     const bool tc = tc0 && sp.tc;
@@ -392,10 +450,11 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
           RH_OK)
         return s;
     }
-    if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
-    // Alg. 1 step 3: B = Q^T G_(n)   (the mode-n product G x_n Q^T)
     const int wb = (cur_buf == 0) ? 1 : 0;
     T* B = static_cast<T*>(b.W[wb]);
+    if (pl.power && (s = run_power<T>(pl, sp, j, cur, tc_src, tc, b, B, info, st)) != RH_OK) return s;
+    if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
+    // Alg. 1 step 3: B = Q^T G_(n)   (the mode-n product G x_n Q^T)
     const bool direct_core = last && !o.truncate;
     if (tc) {
       ProfileScope ps(PROF_TTM, j, st);
@@ -478,7 +537,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       return s;
   }
   if (norms) {
-    record_step(nsteps);
+    record_step(kStepStride * nsteps);
     int64_t ncore = 1;
     // final core sizes
     std::vector<int64_t> dims_out(pl.d, 0);
@@ -512,12 +571,13 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
           RH_OK)
         return s;
     }
+    T* B = static_cast<T*>(b.W[0]);
+    if (pl.power && (s = run_power<T>(pl, sp, (int)j, X, nullptr, false, b, B, info, st)) != RH_OK) return s;
     if (!o.truncate) {
       RH_CUDA_TRY(cudaMemcpyAsync(factors[sp.mode], b.Q, sizeof(double) * sp.v.I * sp.ell, cudaMemcpyDeviceToDevice, st));
       continue;
     }
     if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
-    T* B = static_cast<T*>(b.W[0]);
     {
       ProfileScope ps(PROF_TTM, (int)j, st);
       if ((s = launch_ttm<T, T>(sp.v, X, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) return s;

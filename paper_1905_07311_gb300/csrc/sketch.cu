@@ -12,9 +12,12 @@
 // element of G is read exactly once over the whole grid, so the same pass also
 // accumulates ||G||_F^2.  Partial sketches land in a workspace and are summed in FP64
 // in a fixed order (deterministic).
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "philox.cuh"
+#include "tc.cuh"
 
 namespace rh {
 
@@ -46,6 +49,14 @@ __device__ __forceinline__ int swz(int k, int col) {
   return col ^ ((k & 7) * Vec<T>::n);
 }
 
+// head + tail of the exact two-piece BF16 split of an FP32 value (ties to even), as the tensor-core
+// kernels form it: h = bf16(x), t = bf16(x - h), value h + t (exact in FP32)
+__device__ __forceinline__ float split_value(float x) {
+  const float h = tc::bf16_to_f(tc::bf16_rne(x));
+  return h + tc::bf16_to_f(tc::bf16_rne(x - h));
+}
+__device__ __forceinline__ double split_value(double x) { return x; }
+
 template <typename T>
 struct SketchArgs {
   const T* G;
@@ -54,18 +65,28 @@ struct SketchArgs {
   int64_t chunk;
   uint32_t k0, k1, sid;
   T* part;
-  double* part_norm;
+  double* part_norm;   // may be NULL
+  const T* W;          // dense operand (OPD != 0), laid out like the mode product's output (L, ell, R)
 };
 
-template <typename T, int ELLP, bool KCONTIG>
+// Operand of the sketch: kOpOmega, the Gaussian stream generated on the fly (Alg. 1 step 1);
+// kOpDense, a dense M x ell matrix W read from memory (the G_(n) W product of a subspace-iteration
+// step), element (p, c) at (p % L) + L (c + ell (p / L)); kOpDenseSplit, the same with every
+// element x of G replaced by the sum of its BF16 head and tail (the value the tensor-core kernels
+// read for an FP32 input), FP32 only.
+enum { kOpOmega = 0, kOpDense = 1, kOpDenseSplit = 2 };
+
+template <typename T, int ELLP, bool KCONTIG, int OPD = kOpOmega>
 struct SketchOp {
   using Args = SketchArgs<T>;
   static constexpr int kThreads = kNT, kMinBlocks = 2;
+  // the dense operand tile lives in dynamic shared memory (kKP x ELLP elements of T)
+  static constexpr size_t kDynSmem = OPD == kOpOmega ? 0 : sizeof(T) * kKP * ELLP;
   __device__ static void body(const Grid g, const Args& args);
 };
 
-template <typename T, int ELLP, bool KCONTIG>
-__device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, const Args& args) {
+template <typename T, int ELLP, bool KCONTIG, int OPD>
+__device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG, OPD>::body(const Grid g, const Args& args) {
   const T* __restrict__ G = args.G;
   const int64_t L = args.L, I = args.I, R = args.R;
   const int ell = args.ell;
@@ -78,12 +99,18 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, c
   constexpr int TM = kTI / IG;      // rows per thread
   constexpr int VN = Vec<T>::n;
   using V = typename Vec<T>::type;
+  using OT = std::conditional_t<OPD == kOpOmega, float, T>;   // element type of the operand tile
   static_assert(TM % VN == 0, "row group must be a whole number of vectors");
+  static_assert(OPD != kOpDenseSplit || sizeof(T) == 4, "the split form reads FP32 data");
 
   __shared__ __align__(16) T Xs[kKP][kTI];
-  __shared__ __align__(16) float Os[kKP][ELLP];
+  __shared__ __align__(16) float Os_gen[OPD == kOpOmega ? kKP : 1][OPD == kOpOmega ? ELLP : 4];
+  extern __shared__ __align__(16) unsigned char sketch_dense_raw[];
+  OT(*Os)[ELLP] = OPD == kOpOmega ? reinterpret_cast<OT(*)[ELLP]>(&Os_gen[0][0])
+                                  : reinterpret_cast<OT(*)[ELLP]>(sketch_dense_raw);
   __shared__ int64_t base_s[kKP];
   __shared__ double red[kNT / 32];
+  const T* __restrict__ W = args.W;
 
   const int tid = threadIdx.x;
   const int tc = tid % CG;
@@ -111,13 +138,23 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, c
       }
       __syncthreads();
     }
-    // -- Omega tile
-    for (int t = tid; t < kKP * CG; t += kNT) {
-      const int kp = t / CG, q = t % CG;
-      const int64_t p = p0 + kp;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p < pe) v = rng::omega4(k0, k1, sid, p, (uint32_t)q);
-      *reinterpret_cast<float4*>(&Os[kp][4 * q]) = v;
+    // -- operand tile: Omega generated, or rows p0 .. p0 + 31 of the dense W
+    if constexpr (OPD == kOpOmega) {
+      for (int t = tid; t < kKP * CG; t += kNT) {
+        const int kp = t / CG, q = t % CG;
+        const int64_t p = p0 + kp;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < pe) v = rng::omega4(k0, k1, sid, p, (uint32_t)q);
+        *reinterpret_cast<float4*>(&Os[kp][4 * q]) = v;
+      }
+    } else {
+      for (int t = tid; t < kKP * ELLP; t += kNT) {
+        const int kp = t / ELLP, c = t % ELLP;
+        const int64_t p = p0 + kp;
+        T v = T(0);
+        if (p < pe && c < ell) v = __ldg(W + (KCONTIG ? (int64_t)ell * p : (p % L) + L * (int64_t)ell * (p / L)) + L * c);
+        Os[kp][c] = v;
+      }
     }
     // -- G tile, Xs[kp][ii] = G(i0 + ii, p0 + kp)
     T ss = T(0);
@@ -130,6 +167,7 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, c
         const int64_t p = p0 + kp, i = i0 + ii;
         T x = T(0);
         if (p < pe && i < I) x = __ldg(G + I * p + i);
+        if constexpr (OPD == kOpDenseSplit) x = split_value(x);
         ss += x * x;
         Xs[kp][swz<T>(kp, ii)] = x;
       }
@@ -143,6 +181,7 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, c
         const int64_t i = i0 + ii;
         T x = T(0);
         if (b >= 0 && i < I) x = __ldg(G + b + L * i);
+        if constexpr (OPD == kOpDenseSplit) x = split_value(x);
         ss += x * x;
         Xs[kp][swz<T>(kp, ii)] = x;
       }
@@ -162,8 +201,14 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, c
           xv[a] = v.x; xv[a + 1] = v.y;
         }
       }
-      const float4 o = *reinterpret_cast<const float4*>(&Os[kp][4 * tc]);
-      const T ov[4] = {T(o.x), T(o.y), T(o.z), T(o.w)};
+      T ov[4];
+      if constexpr (OPD == kOpOmega) {
+        const float4 o = *reinterpret_cast<const float4*>(&Os[kp][4 * tc]);
+        ov[0] = T(o.x); ov[1] = T(o.y); ov[2] = T(o.z); ov[3] = T(o.w);
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ov[b] = Os[kp][4 * tc + b];
+      }
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -196,7 +241,7 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG>::body(const Grid g, c
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
   if ((tid & 31) == 0) red[tid >> 5] = nrm;
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && part_norm != nullptr) {
     double s = 0.0;
     for (int k = 0; k < kNT / 32; ++k) s += red[k];
     part_norm[(int64_t)g.by * g.gx + g.bx] = s;
@@ -541,7 +586,7 @@ rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_
   }
   const dim3 grid(pl.gx, pl.S);
   const bool kc = (pl.v.L == 1);
-  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm};
+  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm, nullptr};
   if (pl.ellp == 32)
     return kc ? emit<SketchOp<T, 32, true>>(SITE_SKETCH, 0, grid, 0, st, a)
               : emit<SketchOp<T, 32, false>>(SITE_SKETCH, 0, grid, 0, st, a);
@@ -549,15 +594,54 @@ rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_
             : emit<SketchOp<T, 64, false>>(SITE_SKETCH, 0, grid, 0, st, a);
 }
 
+SketchPlan plan_sketch_dense(const ModeView& v, int ell) {
+  SketchPlan pl;
+  pl.v = v;
+  pl.ell = ell;
+  pl.ellp = ell_pad_of(ell);
+  pl.gx = (int)ceil_div(v.I, kTI);
+  const int64_t ksteps = ceil_div(v.M(), kKP);
+  const int64_t target = 4LL * num_sms();
+  const int64_t S = std::max<int64_t>(1, std::min<int64_t>(ceil_div(target, pl.gx), ksteps));
+  pl.chunk = ceil_div(ceil_div(v.M(), S), kKP) * kKP;
+  pl.S = (int)ceil_div(v.M(), pl.chunk);
+  return pl;
+}
+
+template <typename T, int ELLP, int OPD>
+static rh_status emit_sketch_dense(const SketchPlan& pl, const SketchArgs<T>& a, cudaStream_t st, int site) {
+  const dim3 grid(pl.gx, pl.S);
+  using OpC = SketchOp<T, ELLP, true, OPD>;
+  using OpS = SketchOp<T, ELLP, false, OPD>;
+  return pl.v.L == 1 ? emit<OpC>(site, 0, grid, OpC::kDynSmem, st, a) : emit<OpS>(site, 0, grid, OpS::kDynSmem, st, a);
+}
+
+template <typename T>
+rh_status launch_sketch_dense(const SketchPlan& pl, const T* G, const T* W, bool split, T* part, cudaStream_t st,
+                              int site) {
+  if (pl.ti != 0) {
+    set_error("dense sketch: needs the plan of plan_sketch_dense");
+    return RH_EUNSUPPORTED;
+  }
+  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, 0u, 0u, 0u, part, nullptr, W};
+  if constexpr (sizeof(T) == 4) {
+    if (split)
+      return pl.ellp == 32 ? emit_sketch_dense<T, 32, kOpDenseSplit>(pl, a, st, site)
+                           : emit_sketch_dense<T, 64, kOpDenseSplit>(pl, a, st, site);
+  }
+  return pl.ellp == 32 ? emit_sketch_dense<T, 32, kOpDense>(pl, a, st, site)
+                       : emit_sketch_dense<T, 64, kOpDense>(pl, a, st, site);
+}
+
 template <typename T>
 rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y, double* norm2,
-                               cudaStream_t st) {
+                               cudaStream_t st, int site) {
   if (pl.ell > 65535) {
     set_error("sketch reduce: too many columns");
     return RH_EUNSUPPORTED;
   }
   const dim3 grid((unsigned)ceil_div(pl.v.I, 32), (unsigned)pl.ell);
-  return emit<SketchReduceOp<T>>(SITE_SKETCH_REDUCE, 0, grid, 0, st,
+  return emit<SketchReduceOp<T>>(site, 0, grid, 0, st,
                                  SketchReduceArgs<T>{part, pl.S, pl.v.I, pl.ell, Y, part_norm, (int)pl.norm_elems(), norm2});
 }
 
@@ -566,8 +650,12 @@ template rh_status launch_sketch<float>(const SketchPlan&, const float*, uint64_
 template rh_status launch_sketch<double>(const SketchPlan&, const double*, uint64_t, uint32_t, double*, double*,
                                          cudaStream_t);
 template rh_status launch_sketch_reduce<float>(const SketchPlan&, const float*, const double*, double*, double*,
-                                               cudaStream_t);
+                                               cudaStream_t, int);
 template rh_status launch_sketch_reduce<double>(const SketchPlan&, const double*, const double*, double*, double*,
-                                                cudaStream_t);
+                                                cudaStream_t, int);
+template rh_status launch_sketch_dense<float>(const SketchPlan&, const float*, const float*, bool, float*, cudaStream_t,
+                                              int);
+template rh_status launch_sketch_dense<double>(const SketchPlan&, const double*, const double*, bool, double*,
+                                               cudaStream_t, int);
 
 }  // namespace rh

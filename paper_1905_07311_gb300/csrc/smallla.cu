@@ -1987,6 +1987,135 @@ __device__ __forceinline__ void CastGatedOp<T>::body(const Grid g, const Args& a
 }  // namespace
 
 // ---------------------------------------------------------------------------------
+// Orthonormal basis W of range(B^T) for a subspace-iteration step (Sec. 5, "Variants")
+// ---------------------------------------------------------------------------------
+// W = B^T R^{-1} in place, row by row (forward substitution w R = b), for B^T stored in the
+// (L, n, R) view of a mode product's output: row p, column c at (p % L) + L (c + n (p / L)).  R is
+// upper triangular (n x n, column-major, element type TR).  A diagonal entry with
+// |R_cc| <= tiny max_k |R_kk| (a numerically dependent column of B^T) gets the reciprocal 0, so
+// column c of W is zero instead of overflowing.  Runs when flag is NULL or *flag == 0.  One warp
+// per row, lane l holding entries l and l + 32.
+template <typename T, typename TR>
+struct TrsmViewOp {
+  struct Args {
+    T* B;
+    int64_t L;
+    int64_t R;
+    int n;
+    const TR* Rm;
+    const int32_t* flag;
+    double tiny;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& args);
+};
+template <typename T, typename TR>
+__device__ __forceinline__ void TrsmViewOp<T, TR>::body(const Grid g, const Args& args) {
+  T* __restrict__ B = args.B;
+  const int64_t L = args.L, M = args.L * args.R;
+  const int n = args.n;
+  if (args.flag != nullptr && *args.flag != 0) return;
+  __shared__ T Rs[RH_MAX_ELL * (RH_MAX_ELL | 1)];
+  __shared__ T rd[RH_MAX_ELL];
+  __shared__ double dmax_s;
+  const int ld = n | 1;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Rs[(e % n) + ld * (e / n)] = (T)args.Rm[e];
+  if (threadIdx.x < 32) {
+    double m = 0.0;
+    for (int k = threadIdx.x; k < n; k += 32) m = fmax(m, fabs((double)args.Rm[k + n * k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) dmax_s = m;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double d = (double)args.Rm[k + n * k];
+    rd[k] = (fabs(d) > args.tiny * dmax_s && isfinite(d)) ? (T)(1.0 / d) : T(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)g.gx * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)g.bx * (blockDim.x >> 5) + (threadIdx.x >> 5); row < M; row += warps) {
+    T* b = B + (L == 1 ? (int64_t)n * row : (row % L) + L * (int64_t)n * (row / L));
+    T y0 = lane < n ? b[L * lane] : T(0);
+    T y1 = lane + 32 < n ? b[L * (lane + 32)] : T(0);
+    for (int c = 0; c < n; ++c) {
+      const T xc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31) * rd[c];
+      if (lane == (c & 31)) {
+        if (c < 32) y0 = xc; else y1 = xc;
+      }
+      if (lane > c && lane < n) y0 -= xc * Rs[c + ld * lane];
+      if (lane + 32 > c && lane + 32 < n) y1 -= xc * Rs[c + ld * (lane + 32)];
+    }
+    if (lane < n) b[L * lane] = y0;
+    if (lane + 32 < n) b[L * (lane + 32)] = y1;
+  }
+}
+
+// Gram matrix of B^T (FP64 data, (L, n, R) view): per-CTA partials part[cta][j + n k] =
+// sum over the CTA's rows p of B^T(p, j) B^T(p, k) for j <= k (summed by GramBReduceOp).  Tiles of
+// 32 rows in shared memory; thread t owns the upper-triangle entries t, t + 256, ...  Runs when
+// flag is NULL or *flag == 0.
+struct GramViewF64Op {
+  struct Args {
+    const double* B;
+    int64_t L;
+    int64_t R;
+    int n;
+    double* part;
+    const int32_t* flag;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static constexpr int kPer = (RH_MAX_ELL * (RH_MAX_ELL + 1) / 2 + kThreads - 1) / kThreads;
+  __device__ static void body(const Grid g, const Args& args);
+};
+__device__ __forceinline__ void GramViewF64Op::body(const Grid g, const Args& args) {
+  const double* __restrict__ B = args.B;
+  const int64_t L = args.L, M = args.L * args.R;
+  const int n = args.n;
+  if (args.flag != nullptr && *args.flag != 0) return;
+  __shared__ double As[32][RH_MAX_ELL + 1];
+  const int npairs = n * (n + 1) / 2;
+  int ja[kPer], ka[kPer];
+  double acc[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    int e = threadIdx.x + kThreads * q, j = 0;
+    while (e >= n - j && j < n) {   // row-by-row walk of the upper triangle
+      e -= n - j;
+      ++j;
+    }
+    ja[q] = j;
+    ka[q] = j + e;
+    acc[q] = 0.0;
+  }
+  const int64_t ntiles = (M + 31) / 32;
+  for (int64_t t = g.bx; t < ntiles; t += g.gx) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * n; e += blockDim.x) {
+      const int r = e / n, c = e % n;
+      const int64_t p = t * 32 + r;
+      double v = 0.0;
+      if (p < M) v = B[(L == 1 ? (int64_t)n * p : (p % L) + L * (int64_t)n * (p / L)) + L * c];
+      As[r][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      if (threadIdx.x + kThreads * q < npairs) {
+        double a = acc[q];
+        for (int r = 0; r < 32; ++r) a = fma(As[r][ja[q]], As[r][ka[q]], a);
+        acc[q] = a;
+      }
+    }
+  }
+  double* o = args.part + (int64_t)g.bx * n * n;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q)
+    if (threadIdx.x + kThreads * q < npairs) o[ja[q] + n * ka[q]] = acc[q];
+}
+
+// ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
 static int gram_rows(int64_t m) {
@@ -2251,6 +2380,70 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
   return RH_OK;
 }
 
+// ---- basis of a subspace-iteration step ----------------------------------------------------
+template <typename T>
+size_t power_workspace_elems(const TruncPlan& pl0) {
+  TruncPlan pl = pl0;
+  trunc_dims<T>(pl);
+  const int64_t nn = (int64_t)pl.ell * pl.ell;
+  const size_t tsqr = (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+  const size_t dbl = (size_t)gram_ctas() * nn + 3 * nn + pl.ell + 16;   // partials, C, R, rdiag, flag
+  return ((tsqr + 63) & ~size_t(63)) + (dbl * sizeof(double) + sizeof(T) - 1) / sizeof(T) + 64;
+}
+
+// W = orth(B^T) in place (Sec. 5, randomized subspace iteration: the basis of range(G_(n)^T Q)),
+// for B in the (L, n, R) view: R_1 from the tall-skinny Householder QR of B^T (backward stable
+// whatever the conditioning), W_1 = B^T R_1^{-1}, then one CholeskyQR pass on W_1 (Gram matrix
+// with FP64 sums, FP64 Cholesky, W = W_1 R_2^{-1}), skipped when that Cholesky breaks down (W_1
+// numerically rank deficient; its zero columns stay zero).
+template <typename T>
+rh_status launch_power_basis(const TruncPlan& pl0, T* B, T* ws, cudaStream_t st) {
+  TruncPlan pl = pl0;
+  trunc_dims<T>(pl);
+  const int n = pl.ell;
+  const int64_t nn = (int64_t)n * n;
+  T* buf0 = ws;
+  T* buf1 = ws + pl.nblk0 * nn;
+  const size_t tsqr = (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+  double* part = reinterpret_cast<double*>(ws + ((tsqr + 63) & ~size_t(63)));
+  double* C = part + (size_t)gram_ctas() * nn;
+  double* R2 = C + nn;
+  double* rdiag = R2 + nn;
+  int32_t* flag = reinterpret_cast<int32_t*>(rdiag + n + 8);
+  rh_status s = emit_memset(SITE_POWER_ZERO, 0, flag, sizeof(int32_t), st);
+  if (s != RH_OK) return s;
+  T* Rt = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    float* fin = nullptr;
+    s = launch_tsqr_rows(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, reinterpret_cast<float*>(buf0),
+                         reinterpret_cast<float*>(buf1), nullptr, &fin, st, SITE_POWER_TSQR);
+    Rt = reinterpret_cast<T*>(fin);
+  } else {
+    s = launch_tsqr_tree<T>(pl, B, buf0, buf1, nullptr, &Rt, st, SITE_POWER_TSQR);
+  }
+  if (s != RH_OK) return s;
+  const double tiny = (sizeof(T) == 4 ? 64.0 * 5.9604645e-8 : 64.0 * 1.1102230246251565e-16);
+  const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(pl.v.L * pl.v.R, 8), 8 * num_sms()));
+  using TrsmW1 = TrsmViewOp<T, T>;
+  using TrsmW2 = TrsmViewOp<T, double>;
+  RH_EMIT(TrsmW1, SITE_POWER_TRSM, 0, tblocks, 0, B, pl.v.L, pl.v.R, n, Rt, nullptr, tiny);
+  // second pass: Gram matrix of W_1 (FP64 sums), Cholesky, W = W_1 R_2^{-1}
+  if constexpr (sizeof(T) == 4) {
+    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, C, nullptr, st, false,
+                             SITE_POWER_GRAM)) != RH_OK)
+      return s;
+  } else {
+    const int64_t ntiles = ceil_div(pl.v.L * pl.v.R, 32);
+    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(gram_ctas(), ntiles));
+    RH_EMIT(GramViewF64Op, SITE_POWER_GRAM, 0, ctas, 0, reinterpret_cast<const double*>(B), pl.v.L, pl.v.R, n, part,
+            nullptr);
+    RH_EMIT(GramBReduceOp, SITE_POWER_GRAM + 1, 0, (int)ceil_div(nn, 32), 0, part, ctas, n, C, nullptr);
+  }
+  RH_EMIT(CholOp<ArithF64>, SITE_POWER_CHOL, 0, 1, chol_smem(n, sizeof(double)), C, n, R2, rdiag, flag, 0.0);
+  RH_EMIT(TrsmW2, SITE_POWER_TRSM2, 0, tblocks, 0, B, pl.v.L, pl.v.R, n, R2, flag, tiny);
+  return RH_OK;
+}
+
 // ---- staged truncation (adaptive variants) ----------------------------------------------
 template <typename T>
 rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram, double* part, double* W, T** R,
@@ -2318,9 +2511,9 @@ rh_status launch_factor_and_cast(int64_t I, int ell, int r, const double* Q, con
 }
 
 template <typename T>
-rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st) {
+rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st, int site) {
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * num_sms());
-  RH_EMIT(CastOp<T>, SITE_CAST_Q, 0, std::max(blocks, 1), 0, src, dst, n);
+  RH_EMIT(CastOp<T>, site, 0, std::max(blocks, 1), 0, src, dst, n);
   return RH_OK;
 }
 
@@ -2347,7 +2540,11 @@ template rh_status launch_factor_and_cast<float>(int64_t, int, int, const double
                                                  cudaStream_t);
 template rh_status launch_factor_and_cast<double>(int64_t, int, int, const double*, const double*, double*, double*,
                                                   cudaStream_t);
-template rh_status launch_cast<float>(const double*, float*, int64_t, cudaStream_t);
-template rh_status launch_cast<double>(const double*, double*, int64_t, cudaStream_t);
+template rh_status launch_cast<float>(const double*, float*, int64_t, cudaStream_t, int);
+template rh_status launch_cast<double>(const double*, double*, int64_t, cudaStream_t, int);
+template size_t power_workspace_elems<float>(const TruncPlan&);
+template size_t power_workspace_elems<double>(const TruncPlan&);
+template rh_status launch_power_basis<float>(const TruncPlan&, float*, float*, cudaStream_t);
+template rh_status launch_power_basis<double>(const TruncPlan&, double*, double*, cudaStream_t);
 
 }  // namespace rh

@@ -589,6 +589,7 @@ rh_status sp_plan(int32_t order, const int64_t* dims, int64_t nnz, const int32_t
   RH_CHECK_ARG(nnz >= 1 && nnz < (int64_t(1) << 31), "nnz must be in [1, 2^31)");
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  RH_CHECK_ARG(o.power_iters == 0, "the sparse range finder runs without subspace iteration (power_iters must be 0)");
   for (int k = 0; k < order; ++k) {
     RH_CHECK_ARG(dims[k] >= 1 && dims[k] < (int64_t(1) << 31), "every dimension must be in [1, 2^31)");
     RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");

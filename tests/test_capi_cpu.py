@@ -213,6 +213,25 @@ def test_svd_route_option(L):
     assert code == 1 and "svd_route" in msg
 
 
+def test_power_iters_option(L):
+    """rh_options.power_iters (subspace iteration): 0 by default, 0..8 accepted and growing the
+    workspace (dense-operand sketch partials, basis of range(B^T)); the adaptive range finder
+    runs without it."""
+    from paper_1905_07311_gb300 import _lib
+
+    assert _lib.make_options().power_iters == 0
+    base = _ws(L, [30, 20, 10], [4, 4, 4], p=5)
+    assert _ws(L, [30, 20, 10], [4, 4, 4], p=5, power_iters=2) >= base > 0
+    code, msg = _call_invalid(L, [30, 20, 10], [4, 4, 4], p=5, power_iters=9)
+    assert code == 1 and "power_iters" in msg
+    code, msg = _call_invalid(L, [30, 20, 10], [4, 4, 4], p=5, power_iters=-1)
+    assert code == 1
+    d3 = _lib.i64_array([30, 20, 10])
+    mr = _lib.i32_array([4, 4, 4])
+    o = ctypes.byref(_lib.make_options(p=5, power_iters=1))
+    assert L.adaptive_rank_workspace_size(3, d3, _lib.RH_F32, 1, mr, o) == 0
+
+
 def _err(L):
     return L.rh_last_error().decode()
 
