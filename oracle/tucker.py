@@ -435,8 +435,27 @@ def srrqr_select(Q, eta=2.0, max_swaps=100000):
     return np.array(sorted(sel), dtype=np.int64)
 
 
-def sp_sthosvd(X, ranks, p, seed, rho=None, tensor_id=0, eta=2.0, record=False):
-    """Alg. 6 (SP-STHOSVD) on a dense tensor.
+SELECT_METHODS = ("srrqr", "cpqr", "deim", "uniform", "leverage")
+
+
+def select_rows(Q, method="srrqr", eta=2.0, seed=0, stream=0):
+    """The row selection of Alg. 6 step 6 by one of the methods of Sec. 5 (strong RRQR, the
+    default; column-pivoted QR, DEIM, uniform or leverage-score sampling).  The sampling methods
+    draw with (seed, stream); the library passes stream = (tensor_id << 4) | mode."""
+    if method == "srrqr":
+        return srrqr_select(Q, eta)
+    if method == "cpqr":
+        return cpqr_select(Q)
+    if method == "deim":
+        return deim_select(Q)
+    if method in ("uniform", "leverage"):
+        return sample_select(Q, method == "leverage", seed, stream)
+    raise ValueError(method)
+
+
+def sp_sthosvd(X, ranks, p, seed, rho=None, tensor_id=0, eta=2.0, record=False, method="srrqr", omega_round=None):
+    """Alg. 6 (SP-STHOSVD) on a dense tensor (``method``: the row selection of step 6, see
+    ``select_rows``; ``omega_round='bf16'``: Omega rounded to BF16).
 
     G = X; for j in rho: Y = G_(j) Omega_j; Y = Q R; P_j by strong RRQR on Q^T;
     A_j = Q (P_j^T Q)^{-1}; G_(j) <- P_j^T G_(j).  The core holds entries of X.
@@ -453,10 +472,10 @@ def sp_sthosvd(X, ranks, p, seed, rho=None, tensor_id=0, eta=2.0, record=False):
         I = G.shape[n]
         M = G.size // I
         ell = _ell(ranks[n], p, I, M, clamp=False, strict=True)
-        Om = omega_matrix(seed, tensor_id, n, M, ell)                     # step 3
+        Om = omega_matrix(seed, tensor_id, n, M, ell, omega_round)        # step 3
         Y = unfold(G, n) @ Om                                             # step 4
         Q, _ = np.linalg.qr(Y)                                            # step 5
-        P = srrqr_select(Q, eta)                                          # step 6
+        P = select_rows(Q, method, eta, seed, (int(tensor_id) << 4) | n)  # step 6
         A[n] = Q @ np.linalg.inv(Q[P, :])                                 # step 7
         sel[n] = P
         G = np.take(G, P, axis=n)                                         # step 8
@@ -467,7 +486,7 @@ def sp_sthosvd(X, ranks, p, seed, rho=None, tensor_id=0, eta=2.0, record=False):
     return out
 
 
-def sp_hosvd(X, ranks, p, seed, tensor_id=0, eta=2.0):
+def sp_hosvd(X, ranks, p, seed, tensor_id=0, eta=2.0, method="srrqr", omega_round=None):
     """SP-HOSVD (Sec. 5, first remark after Alg. 6): the modes of Alg. 6 handled independently.
 
     For every mode j of the input: Y = X_(j) Omega_j; Y = QR; P_j by strong RRQR on Q^T;
@@ -483,10 +502,10 @@ def sp_hosvd(X, ranks, p, seed, tensor_id=0, eta=2.0):
         I = X.shape[n]
         M = X.size // I
         ell = _ell(ranks[n], p, I, M, clamp=False, strict=True)
-        Om = omega_matrix(seed, tensor_id, n, M, ell)
+        Om = omega_matrix(seed, tensor_id, n, M, ell, omega_round)
         Y = unfold(X, n) @ Om
         Q, _ = np.linalg.qr(Y)
-        P = srrqr_select(Q, eta)
+        P = select_rows(Q, method, eta, seed, (int(tensor_id) << 4) | n)
         A[n] = Q @ np.linalg.inv(Q[P, :])
         sel[n] = P
     G = X[np.ix_(*sel)]
@@ -517,23 +536,32 @@ def _kolda_rows(idx, dims, n):
     return row
 
 
-def coo_sketch(idx, vals, dims, n, ell, seed, tensor_id=0):
-    """Y = G_(n) Omega_n from COO entries without densifying (Alg. 6, step 4)."""
+def coo_sketch(idx, vals, dims, n, ell, seed, tensor_id=0, omega_round=None):
+    """Y = G_(n) Omega_n from COO entries without densifying (Alg. 6, step 4).
+    ``omega_round='bf16'``: every normal rounded to BF16 first (the BF16-Omega form)."""
     rows = _kolda_rows(idx, dims, n)
     urows, inv = np.unique(rows, return_inverse=True)
-    om = rng.omega(seed, tensor_id, n, urows, ell).astype(np.float64)
+    om = rng.omega(seed, tensor_id, n, urows, ell)
+    if omega_round == "bf16":
+        om = rng.round_bf16(om)
+    elif omega_round is not None:
+        raise ValueError(omega_round)
+    om = om.astype(np.float64)
     Y = np.zeros((int(dims[n]), ell))
     np.add.at(Y, idx[:, n].astype(np.int64), vals.astype(np.float64)[:, None] * om[inv])
     return Y
 
 
-def sp_sthosvd_coo(idx, vals, dims, ranks, p, seed, rho=None, tensor_id=0, eta=2.0):
+def sp_sthosvd_coo(idx, vals, dims, ranks, p, seed, rho=None, tensor_id=0, eta=2.0, method="srrqr",
+                   omega_round=None):
     """Alg. 6 on a COO tensor (0-based coordinates ``idx`` of shape nnz x d).
 
     Same steps as ``sp_sthosvd``; G_(j) <- P_j^T G_(j) keeps the nonzeros whose
     mode-j coordinate is selected and renumbers that coordinate to its position in
     the (sorted) selection.  The final core is the dense ell_1 x ... x ell_d array
-    of the surviving entries.
+    of the surviving entries.  ``method`` picks the row selection of step 6 (``select_rows``,
+    stream (tensor_id << 4) | mode for the sampling methods); ``omega_round='bf16'`` the
+    BF16-Omega sketch.
     """
     idx = np.asarray(idx, dtype=np.int64).copy()
     vals = np.asarray(vals, dtype=np.float64).copy()
@@ -546,9 +574,9 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p, seed, rho=None, tensor_id=0, eta=2
         I = dims[n]
         M = int(np.prod(dims)) // I
         ell = _ell(ranks[n], p, I, M, clamp=False, strict=True)
-        Y = coo_sketch(idx, vals, dims, n, ell, seed, tensor_id)
+        Y = coo_sketch(idx, vals, dims, n, ell, seed, tensor_id, omega_round)
         Q, _ = np.linalg.qr(Y)
-        P = srrqr_select(Q, eta)
+        P = select_rows(Q, method, eta, seed, (int(tensor_id) << 4) | n)
         A[n] = Q @ np.linalg.inv(Q[P, :])
         sel[n] = P
         pos = np.full(I, -1, dtype=np.int64)
@@ -564,10 +592,11 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p, seed, rho=None, tensor_id=0, eta=2
     return {"core": core, "factors": A, "selected": sel, "rho": rho}
 
 
-def sp_hosvd_coo(idx, vals, dims, ranks, p, seed, tensor_id=0, eta=2.0):
+def sp_hosvd_coo(idx, vals, dims, ranks, p, seed, tensor_id=0, eta=2.0, method="srrqr", omega_round=None):
     """SP-HOSVD (Sec. 5 remark 1) of a COO tensor: every mode's sketch from the input's nonzeros
     (``coo_sketch``), thin QR, strong-RRQR selection and A_j = Q (P_j^T Q)^{-1}; the core keeps the
-    nonzeros whose every coordinate is selected, renumbered to positions in the sorted selections."""
+    nonzeros whose every coordinate is selected, renumbered to positions in the sorted selections.
+    ``method`` and ``omega_round`` as in ``sp_sthosvd_coo``."""
     idx = np.asarray(idx, dtype=np.int64)
     vals = np.asarray(vals, dtype=np.float64)
     dims = [int(x) for x in dims]
@@ -579,9 +608,9 @@ def sp_hosvd_coo(idx, vals, dims, ranks, p, seed, tensor_id=0, eta=2.0):
     new = idx.copy()
     for n in range(d):
         ell = _ell(ranks[n], p, dims[n], N // dims[n], clamp=False, strict=True)
-        Y = coo_sketch(idx, vals, dims, n, ell, seed, tensor_id)
+        Y = coo_sketch(idx, vals, dims, n, ell, seed, tensor_id, omega_round)
         Q, _ = np.linalg.qr(Y)
-        P = srrqr_select(Q, eta)
+        P = select_rows(Q, method, eta, seed, (int(tensor_id) << 4) | n)
         A[n] = Q @ np.linalg.inv(Q[P, :])
         sel[n] = P
         pos = np.full(dims[n], -1, dtype=np.int64)

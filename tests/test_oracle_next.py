@@ -16,7 +16,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import tucker
+from oracle import rng, tucker
 from oracle.rng import omega
 from oracle.tensor import frob, multi_ttm, rel_error, unfold
 from workloads import lowrank_plus_noise_np
@@ -258,6 +258,49 @@ def test_sp_hosvd_coo_equals_dense():
         assert np.array_equal(oc["selected"][n], out["selected"][n])
         assert np.allclose(oc["factors"][n], out["factors"][n], atol=1e-10)
     assert np.array_equal(oc["core"], out["core"])
+
+
+@pytest.mark.parametrize("method", ["srrqr", "cpqr", "deim", "uniform", "leverage"])
+@pytest.mark.parametrize("omega_round", [None, "bf16"])
+def test_sp_coo_forms_equal_dense_for_every_selection(method, omega_round):
+    """Alg. 6 and SP-HOSVD from the nonzeros (unique Kolda rows, scatter-add) equal the dense forms
+    (the unfolding times the full Omega matrix) for every selection of Sec. 5 and for Omega rounded to
+    BF16 (the BF16-Omega form of the sparse sketch): two independent computations of each sketch."""
+    X = _sparse_tensor(4)
+    idx = np.argwhere(X != 0)
+    vals = X[X != 0]
+    kw = dict(method=method, omega_round=omega_round)
+    for dense, coo in ((tucker.sp_sthosvd(X, [3, 3, 3], 3, seed=2, tensor_id=1, **kw),
+                        tucker.sp_sthosvd_coo(idx, vals, X.shape, [3, 3, 3], 3, seed=2, tensor_id=1, **kw)),
+                       (tucker.sp_hosvd(X, [3, 3, 3], 3, seed=2, tensor_id=1, **kw),
+                        tucker.sp_hosvd_coo(idx, vals, X.shape, [3, 3, 3], 3, seed=2, tensor_id=1, **kw))):
+        for n in range(3):
+            assert np.array_equal(coo["selected"][n], dense["selected"][n])
+            assert np.allclose(coo["factors"][n], dense["factors"][n], atol=1e-10)
+            A = coo["factors"][n]
+            assert np.array_equal(A[coo["selected"][n]], np.eye(A.shape[1])) or \
+                np.allclose(A[coo["selected"][n]], np.eye(A.shape[1]), atol=1e-12)
+        assert np.array_equal(coo["core"], dense["core"])
+
+
+def test_bf16_omega_sketch_is_the_rounded_stream():
+    """The BF16-Omega COO sketch is X_(n) times Omega with every normal rounded to BF16 (ties to
+    even): against the FP32 stream it moves by at most 2^-9 |X_(n)| |Omega|, and the rounded values
+    are BF16 numbers (low 16 bits zero)."""
+    from oracle.tensor import unfold
+
+    X = _sparse_tensor(5)
+    idx = np.argwhere(X != 0)
+    vals = X[X != 0]
+    for n in range(3):
+        Yb = tucker.coo_sketch(idx, vals, X.shape, n, 6, 3, 0, omega_round="bf16")
+        Yf = tucker.coo_sketch(idx, vals, X.shape, n, 6, 3, 0)
+        M = X.size // X.shape[n]
+        om = rng.omega(3, 0, n, np.arange(M), 6)
+        omb = rng.round_bf16(om)
+        assert np.all((omb.view(np.uint32) & 0xFFFF) == 0)
+        assert np.allclose(Yb, unfold(X, n) @ omb.astype(np.float64), rtol=0, atol=1e-12)
+        assert np.all(np.abs(Yb - Yf) <= 2.0 ** -9 * (np.abs(unfold(X, n)) @ np.abs(om.astype(np.float64))) + 1e-15)
 
 
 def test_uniform_sampling_draws_every_subset_equally():
