@@ -118,10 +118,18 @@ typedef struct rh_options {
                                  /* finder (Sec. 5 "Variants", used in Sec. 6): after Q = orth(Y)*/
                                  /* each step sets W = orth(G_(n)^T Q), Y = G_(n) W, Q = orth(Y) */
                                  /* (0 = Alg. 1 as printed; at most 8)                           */
+  int32_t select;                /* row selection of the structure-preserving variants (Alg. 6   */
+                                 /* step 6; Sec. 5): RH_SELECT_SRRQR (eta = 2, default), _CPQR,  */
+                                 /* _DEIM, _UNIFORM, _LEVERAGE (see rh_subset_select); sampling  */
+                                 /* draws with seed and stream (tensor_id << 4) | mode          */
+  int32_t omega_prec;            /* Omega of the sparse sketches: RH_F32 (FP32 normals, default; */
+                                 /* RH_F64 means the same) or RH_BF16 (each normal rounded to     */
+                                 /* BF16, ties to even: the BF16-Omega form).  Dense paths ignore*/
+                                 /* it (their Omega precision follows the input form)            */
 } rh_options;
 
 /* Fill ``opts`` with defaults: seed 0, tensor_id 0, p 5, rho decreasing, clamp 0, truncate 1,
- * svd_route 0, power_iters 0. */
+ * svd_route 0, power_iters 0, select RH_SELECT_SRRQR, omega_prec RH_F32. */
 void rh_options_default(rh_options* opts);
 
 /* Version string and the message of the last failure on this thread ("" after success). */
@@ -395,6 +403,21 @@ rh_status core_ttm(int32_t order, const int64_t* dims, int32_t dtype, const void
                    const int32_t* ks, double* G, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * rh_orthonormalize_tucker -- the orthonormalising post-processing of Sec. 5 for the interpolatory
+ * (non-orthonormal) factors of Alg. 6 and SP-HOSVD: for each mode n, the thin QR A_n = Q_n R_n
+ * (Alg. 1 step 2's QR: CholeskyQR2 with the Householder fallback, each column's largest-magnitude
+ * entry positive) and the aggregation G <- G x_n R_n.  G x_1 A_1 ... x_d A_d is unchanged (up to
+ * rounding) and every factor becomes orthonormal, so ||G||_F = ||G x_1 A_1 ... x_d A_d||_F.
+ *   dims, ks   A_n is I_n x k_n (1 <= k_n <= min(I_n, 64)); the core is k_1 x ... x k_d.
+ *   factors    host array of device pointers to the FP64 column-major A_n: overwritten by Q_n.
+ *   core       device FP64 column-major core: overwritten by the new core.
+ *   Asynchronous; workspace: rh_orthonormalize_tucker_workspace_size.
+ */
+size_t rh_orthonormalize_tucker_workspace_size(int32_t order, const int64_t* dims, const int32_t* ks);
+rh_status rh_orthonormalize_tucker(int32_t order, const int64_t* dims, const int32_t* ks, double* const* factors,
+                                   double* core, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * rh_tucker_residual -- direct error of a Tucker approximation (validation of Thm. lem:st_mode_err
  * and of the bounds of Sec. 3.2 without the cancellation of ||X||^2 - ||G||^2).
  *   out[0] = ||X - G x_1 A_1 ... x_d A_d||_F^2,  out[1] = ||X||_F^2  (device, FP64).
@@ -446,10 +469,16 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
  * column index of the entry in the mode-``mode`` unfolding (the Omega stream of rhosvd_sketch).
  *   idx   host array of ``order`` DEVICE pointers to int32 arrays of nnz 0-based indices
  *         (deduplicated; duplicates are summed).  vals: device FP32 array of nnz values.
+ *   omega_prec  RH_F32 (RH_F64: the same FP32 normals) or RH_BF16: every normal rounded to BF16
+ *         (ties to even) before the products (the BF16-Omega form); FP32 products and sums either way.
  *   Y     device, I_mode x ell FP64, column-major.
  *   The entries are stably sorted by their mode index and each row's sum is formed in a fixed
  *   order (FP32 sums over at most 512 entries, FP64 above): the result is deterministic.  The call
  *   synchronises ``stream`` once (the work split is built on the host from the row counts).
+ *   Omega rows are shared between the entries with the same other-mode coordinates: when the
+ *   unfolding has fewer than 2^31 columns each distinct row is generated once into a table in the
+ *   workspace (up to nnz rows of ell rounded up to 4 entries, 4 bytes each) and read from there;
+ *   the normals, and so the sums, are the same as generating them per entry.
  *   Needs nnz < 2^31 and every I_n < 2^31; ell <= 64.  Workspace: rhosvd_sketch_coo_workspace_size.
  *   Indices of mode ``mode`` outside [0, I_mode) are counted on the device and the call returns
  *   RH_EINVAL after its synchronisation (Y undefined); they are never used as addresses.  Indices of
@@ -457,14 +486,15 @@ rh_status adaptive_rank(int32_t order, const int64_t* dims, int32_t dtype, const
  */
 size_t rhosvd_sketch_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, int32_t mode, int32_t ell);
 rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
-                            const float* vals, int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id, double* Y,
-                            void* workspace, size_t workspace_bytes, void* stream);
+                            const float* vals, int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id,
+                            int32_t omega_prec, double* Y, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * sp_sthosvd_coo -- structure-preserving STHOSVD of a COO tensor (Alg. 6).  Per mode n in the order
- * rho: Y = G_(n) Omega_n from the nonzeros; Y = QR; P_n = ell_n rows of Q chosen by strong RRQR
- * with eta = 2 (column-pivoted QR of Q^T, then swaps while some |A_ij| > 2 on an unselected row,
- * largest first, lowest (i, j) on ties); A_n = Q (P_n^T Q)^{-1}; G_(n) <- P_n^T G_(n), i.e. the
+ * rho: Y = G_(n) Omega_n from the nonzeros (opts->omega_prec: FP32 or BF16 Omega); Y = QR; P_n = ell_n
+ * rows of Q chosen by opts->select: by default strong RRQR with eta = 2 (column-pivoted QR of Q^T,
+ * then swaps while some |A_ij| > 2 on an unselected row, largest first, lowest (i, j) on ties), or
+ * another selection of Sec. 5 (rh_subset_select); A_n = Q (P_n^T Q)^{-1}; G_(n) <- P_n^T G_(n), i.e. the
  * nonzeros whose mode-n index is selected, renumbered to their position in the sorted selection.
  * The core is the dense ell_1 x ... x ell_d array of the surviving entries (entries of X).
  *   ell_n = ranks[n] + opts->p must be < min(I_n, prod of the other current sizes) (Alg. 6's strict
@@ -486,6 +516,22 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
                          const float* vals, const int32_t* ranks, const rh_options* opts, double* const* factors,
                          int32_t* const* selected, double* core, double* norms, void* workspace,
                          size_t workspace_bytes, void* stream);
+
+/*
+ * sp_hosvd_coo -- structure-preserving HOSVD of a COO tensor (Sec. 5, the first remark after Alg. 6:
+ * the modes of Alg. 6 handled independently).  For every mode n of the INPUT: Y = X_(n) Omega_n from
+ * the nonzeros (Omega_n the stream of R-HOSVD's mode n; opts->omega_prec), Y = QR, P_n by
+ * opts->select, A_n = Q (P_n^T Q)^{-1}; the core is X at the selected coordinates, X(P_1, ..., P_d):
+ * the nonzeros whose every index is selected, each index renumbered to its position in the sorted
+ * selection, scattered into the dense ell_1 x ... x ell_d array.  Arguments, outputs and errors as
+ * sp_sthosvd_coo, with Alg. 6's strict size rule ell_n < min(I_n, prod of the other INPUT sizes) and
+ * the modes taken in increasing order (opts->rho is ignored).  Synchronous (host selection per mode).
+ */
+size_t sp_hosvd_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks,
+                                   const rh_options* opts);
+rh_status sp_hosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx, const float* vals,
+                       const int32_t* ranks, const rh_options* opts, double* const* factors, int32_t* const* selected,
+                       double* core, double* norms, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * rh_subset_select -- the row selection and interpolatory factor of Alg. 6 steps 6-7 on one basis:

@@ -226,6 +226,23 @@ def core_ttm(X, dims, factors):
     return G, ks
 
 
+def orthonormalize_tucker(factors, core, dims):
+    """The orthonormalising post-processing of Sec. 5 in place: factors (list of (k_n, I_n) FP64 CUDA
+    tensors holding column-major I_n x k_n matrices) become Q_n of A_n = Q_n R_n and the flat FP64 core
+    G x_1 R_1 ... x_d R_d (k_1 x ... x k_d)."""
+    torch = _torch()
+    d = len(dims)
+    ks = [int(f.shape[0]) for f in factors]
+    da, ka = i64_array(dims), i32_array(ks)
+    ws_bytes = lib().rh_orthonormalize_tucker_workspace_size(d, da, ka)
+    if ws_bytes == 0:
+        raise ValueError("invalid Tucker sizes (need 1 <= k_n <= min(I_n, 64))")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=core.device)
+    check(lib().rh_orthonormalize_tucker(d, da, ka, _fptrs(factors), _ptr(core), _ptr(ws), ws_bytes,
+                                         _stream(core.device)))
+    return factors, core
+
+
 def tucker_residual(X, dims, factors, core):
     """Device tensor [||X - X_hat||^2, ||X||^2] for a Tucker tensor (FP64 core and factors)."""
     torch = _check_input(X, dims)
@@ -406,9 +423,10 @@ def _coo_args(idx, vals):
     return cols, (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols]), vals.contiguous()
 
 
-def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0):
+def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0, omega="f32"):
     """Y = X_(mode) Omega_mode of the COO tensor (``idx``: list of d int32 CUDA index tensors, ``vals``
-    FP32); returns the (ell, I_mode) FP64 tensor holding the column-major I_mode x ell Y."""
+    FP32); returns the (ell, I_mode) FP64 tensor holding the column-major I_mode x ell Y.
+    ``omega="bf16"``: Omega rounded to BF16 (the BF16-Omega form)."""
     torch = _torch()
     cols, iptr, vals = _coo_args(idx, vals)
     d = len(dims)
@@ -420,7 +438,8 @@ def rhosvd_sketch_coo(idx, vals, dims, mode, ell, seed=0, tensor_id=0):
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=vals.device)
     Y = torch.empty((int(ell), int(dims[mode])), dtype=torch.float64, device=vals.device)
     check(lib().rhosvd_sketch_coo(d, da, nnz, iptr, _ptr(vals), int(mode), int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                  int(tensor_id), _ptr(Y), _ptr(ws), ws_bytes, _stream(vals.device)))
+                                  int(tensor_id), {"f32": RH_F32, "bf16": _lib.RH_BF16}[omega], _ptr(Y), _ptr(ws),
+                                  ws_bytes, _stream(vals.device)))
     return Y
 
 
@@ -451,22 +470,30 @@ class SpTucker(Tucker):
     """SP-STHOSVD result: factors (ell_n, I_n), selected row indices per mode, dense core."""
 
 
-def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False):
-    """Alg. 6 (SP-STHOSVD) of a COO tensor; returns an SpTucker with ``selected``."""
+def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, select="srrqr",
+                   omega="f32", variant="sthosvd"):
+    """Alg. 6 (SP-STHOSVD) of a COO tensor, or SP-HOSVD (``variant="hosvd"``: every mode on the input,
+    Sec. 5); returns an SpTucker with ``selected``.  ``select``: the row selection (see subset_select);
+    ``omega="bf16"``: the BF16-Omega sketch."""
     torch = _torch()
     cols, iptr, vals = _coo_args(idx, vals)
     d = len(dims)
     dims = [int(v) for v in dims]
     da, ra = i64_array(dims), i32_array(ranks)
     nnz = int(vals.numel())
-    opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp)
-    ws_bytes = lib().sp_sthosvd_coo_workspace_size(d, da, nnz, ra, ctypes.byref(opts))
+    opts = make_options(seed=seed, p=p, tensor_id=tensor_id, rho=rho, clamp=clamp, select=select, omega_prec=omega)
+    fn = {"sthosvd": "sp_sthosvd_coo", "hosvd": "sp_hosvd_coo"}[variant]
+    ws_bytes = getattr(lib(), fn + "_workspace_size")(d, da, nnz, ra, ctypes.byref(opts))
     if ws_bytes == 0:
-        check(lib().sp_sthosvd_coo(d, da, nnz, iptr, _ptr(vals), ra, ctypes.byref(opts), None, None, None, None, None,
-                                   0, None))
-        raise ValueError("invalid SP-STHOSVD request")
+        check(getattr(lib(), fn)(d, da, nnz, iptr, _ptr(vals), ra, ctypes.byref(opts), None, None, None, None, None,
+                                 0, None))
+        raise ValueError("invalid structure-preserving request")
     # ell_n as the library computes it (same order and size rule)
-    order = list(rho) if rho is not None else sorted(range(d), key=lambda n: (-dims[n], n))
+    independent = variant == "hosvd"
+    if independent:
+        order = list(range(d))
+    else:
+        order = list(rho) if rho is not None else sorted(range(d), key=lambda n: (-dims[n], n))
     cur = list(dims)
     ells = [0] * d
     for n in order:
@@ -479,7 +506,8 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, c
         if ell >= lim:
             ell = lim - 1
         ells[n] = ell
-        cur[n] = ell
+        if not independent:
+            cur[n] = ell
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=vals.device)
     factors = [torch.empty((ells[n], dims[n]), dtype=torch.float64, device=vals.device) for n in range(d)]
     selected = [torch.empty(ells[n], dtype=torch.int32, device=vals.device) for n in range(d)]
@@ -490,11 +518,17 @@ def sp_sthosvd_coo(idx, vals, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, c
     norms = torch.empty(2, dtype=torch.float64, device=vals.device)
     fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in factors])
     sptrs = (ctypes.c_void_p * d)(*[s_.data_ptr() for s_ in selected])
-    check(lib().sp_sthosvd_coo(d, da, nnz, iptr, _ptr(vals), ra, ctypes.byref(opts), fptrs, sptrs, _ptr(core),
-                               _ptr(norms), _ptr(ws), ws_bytes, _stream(vals.device)))
+    check(getattr(lib(), fn)(d, da, nnz, iptr, _ptr(vals), ra, ctypes.byref(opts), fptrs, sptrs, _ptr(core),
+                             _ptr(norms), _ptr(ws), ws_bytes, _stream(vals.device)))
     T = SpTucker(factors, core, ells, norms, torch.zeros(d, dtype=torch.int32, device=vals.device))
     T.selected = selected
     return T
+
+
+def sp_hosvd_coo(idx, vals, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, select="srrqr", omega="f32"):
+    """SP-HOSVD (Sec. 5: Alg. 6 with every mode taken on the input) of a COO tensor."""
+    return sp_sthosvd_coo(idx, vals, dims, ranks, p=p, seed=seed, tensor_id=tensor_id, clamp=clamp, select=select,
+                          omega=omega, variant="hosvd")
 
 
 def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, truncate=True, form=None,

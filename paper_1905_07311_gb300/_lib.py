@@ -21,7 +21,8 @@ STATUS = {0: "RH_OK", 1: "RH_EINVAL", 2: "RH_ENOMEM", 3: "RH_ECUDA", 4: "RH_ENUM
 class RhOptions(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("tensor_id", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("rho", ctypes.c_int32 * RH_MAX_ORDER), ("clamp", ctypes.c_int32), ("truncate", ctypes.c_int32),
-                ("svd_route", ctypes.c_int32), ("power_iters", ctypes.c_int32)]
+                ("svd_route", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("select", ctypes.c_int32),
+                ("omega_prec", ctypes.c_int32)]
 
 
 class RhError(RuntimeError):
@@ -67,9 +68,13 @@ SIGNATURES = {
     "adaptive_rank": (_I32, [_I32, _P, _I32, _P, ctypes.c_double, _I32, _I32, _P, ctypes.POINTER(RhOptions), _P, _P,
                              _P, _P, _P, _SZ, _P]),
     "rhosvd_sketch_coo_workspace_size": (_SZ, [_I32, _P, _I64, _I32, _I32]),
-    "rhosvd_sketch_coo": (_I32, [_I32, _P, _I64, _P, _P, _I32, _I32, ctypes.c_uint64, _I32, _P, _P, _SZ, _P]),
+    "rhosvd_sketch_coo": (_I32, [_I32, _P, _I64, _P, _P, _I32, _I32, ctypes.c_uint64, _I32, _I32, _P, _P, _SZ, _P]),
+    "sp_hosvd_coo_workspace_size": (_SZ, [_I32, _P, _I64, _P, ctypes.POINTER(RhOptions)]),
+    "sp_hosvd_coo": (_I32, [_I32, _P, _I64, _P, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
     "sp_sthosvd_coo_workspace_size": (_SZ, [_I32, _P, _I64, _P, ctypes.POINTER(RhOptions)]),
     "sp_sthosvd_coo": (_I32, [_I32, _P, _I64, _P, _P, _P, ctypes.POINTER(RhOptions), _P, _P, _P, _P, _P, _SZ, _P]),
+    "rh_orthonormalize_tucker_workspace_size": (_SZ, [_I32, _P, _P]),
+    "rh_orthonormalize_tucker": (_I32, [_I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "rh_tucker_residual_workspace_size": (_SZ, [_I32, _P, _I32, _P]),
     "rh_tucker_residual": (_I32, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "rh_fp8_layout": (_I32, [_I32, _P, _P, _P, _P, _P]),
@@ -118,7 +123,11 @@ def i32_array(vals):
     return (ctypes.c_int32 * len(vals))(*[int(v) for v in vals])
 
 
-def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True, svd_route=0, power_iters=0):
+SELECT = {"srrqr": 0, "cpqr": 1, "deim": 2, "uniform": 3, "leverage": 4}
+
+
+def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True, svd_route=0, power_iters=0,
+                 select="srrqr", omega_prec="f32"):
     o = RhOptions()
     lib().rh_options_default(ctypes.byref(o))
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
@@ -131,4 +140,6 @@ def make_options(seed=0, p=5, tensor_id=0, rho=None, clamp=False, truncate=True,
     o.truncate = int(bool(truncate))
     o.svd_route = int(svd_route)
     o.power_iters = int(power_iters)
+    o.select = SELECT[select] if isinstance(select, str) else int(select)
+    o.omega_prec = {"f32": RH_F32, "bf16": RH_BF16}[omega_prec] if isinstance(omega_prec, str) else int(omega_prec)
     return o

@@ -58,6 +58,8 @@ void rh_options_default(rh_options* o) {
   o->truncate = 1;
   o->svd_route = 0;
   o->power_iters = 0;
+  o->select = RH_SELECT_SRRQR;
+  o->omega_prec = RH_F32;
 }
 
 rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0, int64_t nrows, int32_t ell,

@@ -12,9 +12,15 @@
 //
 // The sketch is deterministic: the nonzeros are stably sorted by i_n (CUB radix sort), each row's
 // run is cut into work items of at most kItem nonzeros, a warp turns an item into a partial row
-// (FP32 sums of products; ceil(ell / 4) lanes per nonzero, lane q generating Omega columns
-// 4q..4q+3 with the library's Philox / Box-Muller, 32 / ceil(ell / 4) nonzeros per pass, the
-// groups combined in a fixed order), and the partials of a row are added in FP64 in item order.  The item list is built on the host from the row counts, and the selection
+// (FP32 sums of products; ceil(ell / 4) lanes per nonzero, lane q handling Omega columns
+// 4q..4q+3, 32 / ceil(ell / 4) nonzeros per pass, the groups combined in a fixed order), and the
+// partials of a row are added in FP64 in item order.
+// Omega rows are shared: a row p of Omega_n (a Kolda column of the unfolding) is needed by every
+// nonzero with the same other-mode coordinates, and a count tensor repeats them often (a Zipf
+// tensor needs 0.17 to 0.27 distinct rows per nonzero).  When the unfolding has fewer than 2^31
+// columns the nonzeros are also sorted by p, each distinct row is generated once into a table
+// (FP32, or BF16 in the BF16-Omega form) and the work items read it from there; otherwise every
+// nonzero generates its row.  Both give the same normals, so the same sums.  The item list is built on the host from the row counts, and the selection
 // (strong RRQR: column-pivoted QR of Q^T, then swaps while some |A_ij| > eta, the largest entry first,
 // lowest (i, j) on ties) runs on the host in FP64, so the call synchronises its stream per mode.
 #include <cub/cub.cuh>
@@ -28,6 +34,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "philox.cuh"
+#include "tc.cuh"
 
 namespace rh {
 namespace {
@@ -53,11 +60,87 @@ struct SpIdx {
   int64_t stride[RH_MAX_ORDER];   // Kolda stride of each mode in the mode-n unfolding (0 for n)
 };
 
+// Kolda column index p of every nonzero in the mode-n unfolding (stride 0 for mode n), < 2^31
+__global__ void kolda_key_kernel(SpIdx ix, int d, int64_t n, int32_t* __restrict__ key) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = 0;
+    for (int k = 0; k < d; ++k) p += (int64_t)ix.idx[k][e] * ix.stride[k];
+    key[e] = (int32_t)p;
+  }
+}
+
+// head[k] = 1 where the sorted key changes (a new distinct Omega row)
+__global__ void run_heads_kernel(const int32_t* __restrict__ ks, int64_t n, int32_t* __restrict__ head) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    head[k] = (k == 0 || ks[k] != ks[k - 1]) ? 1 : 0;
+}
+
+// u1 = inclusive sum of the heads: nonzero es[k] uses distinct row u1[k] - 1, whose Omega row is
+// pd[u] = ks[k]
+__global__ void distinct_rows_kernel(const int32_t* __restrict__ ks, const int32_t* __restrict__ es,
+                                     const int32_t* __restrict__ head, const int32_t* __restrict__ u1, int64_t n,
+                                     int32_t* __restrict__ uid, int32_t* __restrict__ pd) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = u1[k] - 1;
+    uid[es[k]] = u;
+    if (head[k]) pd[u] = ks[k];
+  }
+}
+
+// Table of the distinct Omega rows: row u (of *count) holds Omega_n(pd[u], 0 .. 4 nq - 1) at
+// tab[u ldo ...], FP32 or rounded to BF16 (ties to even).
+template <bool BF16>
+__global__ void omega_table_kernel(const int32_t* __restrict__ pd, const int32_t* __restrict__ count, int nq, int ldo,
+                                   uint32_t k0, uint32_t k1, uint32_t sid, void* __restrict__ tab) {
+  const int64_t total = (int64_t)(*count) * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = t / nq;
+    const int q = (int)(t - u * nq);
+    const float4 w = rng::omega4(k0, k1, sid, pd[u], (uint32_t)q);
+    if constexpr (BF16) {
+      const uint32_t a = (uint32_t)tc::bf16_rne(w.x) | ((uint32_t)tc::bf16_rne(w.y) << 16);
+      const uint32_t b = (uint32_t)tc::bf16_rne(w.z) | ((uint32_t)tc::bf16_rne(w.w) << 16);
+      reinterpret_cast<uint2*>(tab)[(u * ldo + 4 * q) / 4] = make_uint2(a, b);
+    } else {
+      reinterpret_cast<float4*>(tab)[(u * ldo + 4 * q) / 4] = w;
+    }
+  }
+}
+
+// Source of the Omega columns 4q..4q+3 of a nonzero: generated (SRC 0), generated and rounded to
+// BF16 (1), or read from the table of distinct rows, FP32 (2) or BF16 (3).
+template <int SRC>
+__device__ __forceinline__ float4 omega_quad(const SpIdx& ix, int d, int e, int q, uint32_t k0, uint32_t k1,
+                                             uint32_t sid, const int32_t* __restrict__ uid, const void* __restrict__ tab,
+                                             int ldo) {
+  if constexpr (SRC <= 1) {
+    int64_t p = 0;
+    for (int k = 0; k < d; ++k) p += (int64_t)ix.idx[k][e] * ix.stride[k];
+    float4 w = rng::omega4(k0, k1, sid, p, (uint32_t)q);
+    if constexpr (SRC == 1) {
+      w.x = tc::bf16_to_f(tc::bf16_rne(w.x));
+      w.y = tc::bf16_to_f(tc::bf16_rne(w.y));
+      w.z = tc::bf16_to_f(tc::bf16_rne(w.z));
+      w.w = tc::bf16_to_f(tc::bf16_rne(w.w));
+    }
+    return w;
+  } else if constexpr (SRC == 2) {
+    return __ldg(reinterpret_cast<const float4*>(tab) + ((int64_t)uid[e] * ldo + 4 * q) / 4);
+  } else {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(tab) + ((int64_t)uid[e] * ldo + 4 * q) / 4);
+    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u), __uint_as_float(r.y << 16),
+                       __uint_as_float(r.y & 0xFFFF0000u));
+  }
+}
+
 // Warp per work item (row, [begin, end) of the sorted nonzeros): partial row of Y in FP64.
+template <int SRC>
 __global__ void __launch_bounds__(256) sp_sketch_items_kernel(SpIdx ix, int d, const float* __restrict__ vals,
                                                               const int32_t* __restrict__ perm,
                                                               const int3* __restrict__ items, int nitems, int ell,
                                                               uint32_t k0, uint32_t k1, uint32_t sid,
+                                                              const int32_t* __restrict__ uid,
+                                                              const void* __restrict__ tab, int ldo,
                                                               double* __restrict__ part) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -74,10 +157,8 @@ __global__ void __launch_bounds__(256) sp_sketch_items_kernel(SpIdx ix, int d, c
     if (active) {
       for (int j = item.y + g; j < item.z; j += npass) {
         const int e = perm[j];
-        int64_t p = 0;
-        for (int k = 0; k < d; ++k) p += (int64_t)ix.idx[k][e] * ix.stride[k];
         const float v = vals[e];
-        const float4 w = rng::omega4(k0, k1, sid, p, (uint32_t)q);
+        const float4 w = omega_quad<SRC>(ix, d, e, q, k0, k1, sid, uid, tab, ldo);
         acc[0] = fmaf(v, w.x, acc[0]);
         acc[1] = fmaf(v, w.y, acc[1]);
         acc[2] = fmaf(v, w.z, acc[2]);
@@ -130,6 +211,31 @@ __global__ void compact_kernel(SpIdx in, int d, int n, const float* __restrict__
       const int32_t v = in.idx[k][e];
       const_cast<int32_t*>(out.idx[k])[t] = (k == n) ? pos[v] : v;
     }
+    out_vals[t] = vals[e];
+  }
+}
+
+struct PosTabs {
+  const int32_t* pos[RH_MAX_ORDER];   // position of each index in its mode's sorted selection, or -1
+};
+
+// SP-HOSVD: keep the nonzeros whose every index is selected
+__global__ void keep_all_kernel(SpIdx in, int d, int64_t n, PosTabs pt, int32_t* __restrict__ flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int keep = 1;
+    for (int k = 0; k < d; ++k) keep &= pt.pos[k][in.idx[k][e]] >= 0 ? 1 : 0;
+    flag[e] = keep;
+  }
+}
+
+// stable compaction of the kept nonzeros with every index renumbered through its mode's table
+__global__ void compact_all_kernel(SpIdx in, int d, const float* __restrict__ vals, int64_t nnz,
+                                   const int32_t* __restrict__ flag, const int32_t* __restrict__ dest, PosTabs pt,
+                                   SpIdx out, float* __restrict__ out_vals) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[e]) continue;
+    const int64_t t = dest[e];
+    for (int k = 0; k < d; ++k) const_cast<int32_t*>(out.idx[k])[t] = pt.pos[k][in.idx[k][e]];
     out_vals[t] = vals[e];
   }
 }
@@ -468,6 +574,8 @@ rh_status subset_select_host(const std::vector<double>& Q, int64_t I, int ell, i
 
 struct SpBufs {
   int32_t *keys_in, *keys_out, *perm_in, *perm_out, *cnt, *flag, *dest, *pos, *row_items;
+  int32_t *uid, *pd;   // distinct Omega row of each nonzero, Kolda index of each distinct row
+  void* omtab;         // table of the distinct Omega rows (nnz rows of ldo entries at most)
   int3* items;
   double *part, *Y, *Q, *orth, *norm_part;
   int32_t* idx[2][RH_MAX_ORDER];
@@ -475,22 +583,30 @@ struct SpBufs {
   void* cub_tmp;
   size_t cub_bytes;
   int32_t* info;
+  int32_t* pos_all;   // SP-HOSVD position tables, mode after mode
 };
 
 struct SpSizes {
   int64_t nnz, I_max, items_max;
   int ell_max;
   size_t orth, cub_bytes;
+  int64_t pos_elems = 0;   // SP-HOSVD: one position table per mode (sum of I_n)
+  int om_esize = 4;        // bytes per entry of the Omega table (4 FP32, 2 BF16)
 };
 
 size_t cub_bytes_for(int64_t nnz) {
-  size_t a = 0, b = 0;
+  size_t a = 0, b = 0, c = 0;
   cub::DeviceRadixSort::SortPairs(nullptr, a, (const int32_t*)nullptr, (int32_t*)nullptr, (const int32_t*)nullptr,
                                   (int32_t*)nullptr, (int)std::max<int64_t>(nnz, 1), 0, 31, (cudaStream_t)0);
   cub::DeviceScan::ExclusiveSum(nullptr, b, (const int32_t*)nullptr, (int32_t*)nullptr,
                                 (int)std::max<int64_t>(nnz, 1), (cudaStream_t)0);
-  return std::max(a, b);
+  cub::DeviceScan::InclusiveSum(nullptr, c, (const int32_t*)nullptr, (int32_t*)nullptr,
+                                (int)std::max<int64_t>(nnz, 1), (cudaStream_t)0);
+  return std::max(a, std::max(b, c));
 }
+
+// entries per row of the Omega table: ell rounded up to a whole number of quads
+int omega_ldo(int ell) { return 4 * ((ell + 3) / 4); }
 
 SpBufs carve_sp(Arena& ar, int d, const SpSizes& z) {
   SpBufs b;
@@ -504,6 +620,9 @@ SpBufs carve_sp(Arena& ar, int d, const SpSizes& z) {
   b.cnt = ar.take<int32_t>((size_t)z.I_max + 1);
   b.pos = ar.take<int32_t>((size_t)z.I_max + 1);
   b.row_items = ar.take<int32_t>((size_t)z.I_max + 1);
+  b.uid = ar.take<int32_t>(n);
+  b.pd = ar.take<int32_t>(n);
+  b.omtab = ar.take<char>(n * (size_t)omega_ldo(z.ell_max) * (size_t)z.om_esize);
   b.items = ar.take<int3>((size_t)z.items_max);
   b.part = ar.take<double>((size_t)z.items_max * z.ell_max);
   b.Y = ar.take<double>((size_t)z.I_max * z.ell_max);
@@ -517,6 +636,7 @@ SpBufs carve_sp(Arena& ar, int d, const SpSizes& z) {
   b.cub_bytes = z.cub_bytes;
   b.cub_tmp = ar.take<char>(z.cub_bytes);
   b.info = ar.take<int32_t>(4);
+  b.pos_all = z.pos_elems ? ar.take<int32_t>((size_t)z.pos_elems) : nullptr;
   return b;
 }
 
@@ -528,16 +648,42 @@ int bits_for(int64_t v) {
 
 // Y = G_(n) Omega_n (I x ell, FP64, column-major) from the COO nonzeros (Alg. 6 step 4): stable sort
 // by i_n, work items of at most kItem nonzeros per row, warp partials, FP64 sums in item order.
-rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int ell, int64_t cnnz, const int32_t* key,
-                         const float* vals, uint64_t seed, int32_t tensor_id, int64_t items_max, const SpBufs& b,
-                         double* Y, cudaStream_t st) {
+rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int64_t M, int ell, int64_t cnnz,
+                         const int32_t* key, const float* vals, uint64_t seed, int32_t tensor_id, bool om_bf16,
+                         int64_t items_max, const SpBufs& b, double* Y, cudaStream_t st) {
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
-  // (a) stable sort of the nonzeros by i_n; row counts (an empty tensor has no items: Y = 0)
+  const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)n;
+  const int ldo = omega_ldo(ell), nq = ldo / 4;
+  const bool table = cnnz > 0 && M < (int64_t(1) << 31);
   size_t tb = b.cub_bytes;
-  RH_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * (I + 1), st));
   if (cnnz > 0) {
     iota_kernel<<<grid_for(cnnz), 256, 0, st>>>(b.perm_in, cnnz);
     RH_LAUNCH_CHECK();
+  }
+  if (table) {
+    // (0) the distinct Omega rows: sort the nonzeros' Kolda indices, number the distinct ones, and
+    // generate each row once into the table
+    kolda_key_kernel<<<grid_for(cnnz), 256, 0, st>>>(ix, order, cnnz, b.keys_in);
+    RH_LAUNCH_CHECK();
+    RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, b.keys_in, b.keys_out, b.perm_in, b.perm_out,
+                                                (int)cnnz, 0, bits_for(M), st));
+    run_heads_kernel<<<grid_for(cnnz), 256, 0, st>>>(b.keys_out, cnnz, b.flag);
+    RH_LAUNCH_CHECK();
+    tb = b.cub_bytes;
+    RH_CUDA_TRY(cub::DeviceScan::InclusiveSum(b.cub_tmp, tb, b.flag, b.dest, (int)cnnz, st));
+    distinct_rows_kernel<<<grid_for(cnnz), 256, 0, st>>>(b.keys_out, b.perm_out, b.flag, b.dest, cnnz, b.uid, b.pd);
+    RH_LAUNCH_CHECK();
+    const int tgrid = grid_for(cnnz * (int64_t)nq);
+    if (om_bf16)
+      omega_table_kernel<true><<<tgrid, 256, 0, st>>>(b.pd, b.dest + cnnz - 1, nq, ldo, k0, k1, sid, b.omtab);
+    else
+      omega_table_kernel<false><<<tgrid, 256, 0, st>>>(b.pd, b.dest + cnnz - 1, nq, ldo, k0, k1, sid, b.omtab);
+    RH_LAUNCH_CHECK();
+  }
+  // (a) stable sort of the nonzeros by i_n; row counts (an empty tensor has no items: Y = 0)
+  tb = b.cub_bytes;
+  RH_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * (I + 1), st));
+  if (cnnz > 0) {
     RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, key, b.keys_out, b.perm_in, b.perm_out,
                                                 (int)cnnz, 0, bits_for(I), st));
     count_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, I, b.cnt);
@@ -570,11 +716,22 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int ell, 
     RH_CUDA_TRY(cudaMemcpyAsync(b.items, items.data(), sizeof(int3) * items.size(), cudaMemcpyHostToDevice, st));
   RH_CUDA_TRY(cudaMemcpyAsync(b.row_items, row_items.data(), sizeof(int32_t) * (I + 1), cudaMemcpyHostToDevice, st));
   // (c) sketch Y = G_(n) Omega_n (step 4)
-  const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)n;
   if (!items.empty()) {
     const int nwarps = (int)std::min<int64_t>((int64_t)items.size(), 64LL * num_sms());
-    sp_sketch_items_kernel<<<(int)ceil_div(nwarps, 8), 256, 0, st>>>(ix, order, vals, b.perm_out, b.items,
-                                                                       (int)items.size(), ell, k0, k1, sid, b.part);
+    const dim3 grid((unsigned)ceil_div(nwarps, 8));
+    const int nit = (int)items.size();
+    if (table && om_bf16)
+      sp_sketch_items_kernel<3><<<grid, 256, 0, st>>>(ix, order, vals, b.perm_out, b.items, nit, ell, k0, k1, sid,
+                                                        b.uid, b.omtab, ldo, b.part);
+    else if (table)
+      sp_sketch_items_kernel<2><<<grid, 256, 0, st>>>(ix, order, vals, b.perm_out, b.items, nit, ell, k0, k1, sid,
+                                                        b.uid, b.omtab, ldo, b.part);
+    else if (om_bf16)
+      sp_sketch_items_kernel<1><<<grid, 256, 0, st>>>(ix, order, vals, b.perm_out, b.items, nit, ell, k0, k1, sid,
+                                                        nullptr, nullptr, ldo, b.part);
+    else
+      sp_sketch_items_kernel<0><<<grid, 256, 0, st>>>(ix, order, vals, b.perm_out, b.items, nit, ell, k0, k1, sid,
+                                                        nullptr, nullptr, ldo, b.part);
     RH_LAUNCH_CHECK();
   }
   sp_sketch_reduce_kernel<<<grid_for(I * ell), 256, 0, st>>>(b.part, b.row_items, I, ell, Y);
@@ -582,20 +739,28 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int ell, 
   return RH_OK;
 }
 
+// independent: SP-HOSVD (every mode on the input sizes, modes in increasing order, one position
+// table per mode); otherwise Alg. 6 (the size rule on the current core, order rho).
 rh_status sp_plan(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks, const rh_options& o,
-                  std::vector<int>& rho, std::vector<int>& ells, SpSizes& z) {
+                  std::vector<int>& rho, std::vector<int>& ells, SpSizes& z, bool independent = false) {
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
   RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
   RH_CHECK_ARG(nnz >= 1 && nnz < (int64_t(1) << 31), "nnz must be in [1, 2^31)");
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
   RH_CHECK_ARG(o.power_iters == 0, "the sparse range finder runs without subspace iteration (power_iters must be 0)");
+  RH_CHECK_ARG(o.select >= RH_SELECT_SRRQR && o.select <= RH_SELECT_LEVERAGE,
+               "select must be one of RH_SELECT_SRRQR, _CPQR, _DEIM, _UNIFORM, _LEVERAGE");
+  RH_CHECK_ARG(o.omega_prec == RH_F64 || o.omega_prec == RH_F32 || o.omega_prec == RH_BF16,
+               "omega_prec must be RH_F32 (or RH_F64: the same FP32 normals) or RH_BF16");
   for (int k = 0; k < order; ++k) {
     RH_CHECK_ARG(dims[k] >= 1 && dims[k] < (int64_t(1) << 31), "every dimension must be in [1, 2^31)");
     RH_CHECK_ARG(ranks[k] >= 1, "every rank must be >= 1");
   }
   rho.resize(order);
-  if (o.rho[0] < 0) {
+  if (independent) {
+    std::iota(rho.begin(), rho.end(), 0);
+  } else if (o.rho[0] < 0) {
     std::iota(rho.begin(), rho.end(), 0);
     std::stable_sort(rho.begin(), rho.end(), [&](int a, int c) { return dims[a] > dims[c]; });
   } else {
@@ -639,10 +804,37 @@ rh_status sp_plan(int32_t order, const int64_t* dims, int64_t nnz, const int32_t
     z.I_max = std::max(z.I_max, cur[n]);
     z.ell_max = std::max(z.ell_max, (int)ell);
     z.orth = std::max(z.orth, orth_workspace_elems(cur[n], (int)ell));
-    cur[n] = ell;
+    if (independent)
+      z.pos_elems += cur[n];
+    else
+      cur[n] = ell;
   }
   z.items_max = nnz / kItem + z.I_max + 1;
   z.cub_bytes = cub_bytes_for(nnz);
+  z.om_esize = o.omega_prec == RH_BF16 ? 2 : 4;
+  return RH_OK;
+}
+
+// Alg. 6 steps 5-7 for one mode: Y = QR (device), the row selection P (host, FP64, method of
+// Sec. 5; sampling with stream (tensor_id << 4) | n), A_n = Q (P^T Q)^{-1} into factors_n, P into
+// selected_n (optional); sel receives P (sorted).
+rh_status sp_select_mode(int64_t I, int ell, int n, const rh_options& o, const SpBufs& b, double* factor_n,
+                         int32_t* selected_n, std::vector<int>& sel, cudaStream_t st) {
+  rh_status s;
+  RH_CUDA_TRY(cudaMemsetAsync(b.info, 0, sizeof(int32_t), st));
+  if ((s = launch_orthonormalize(I, ell, b.Y, b.Q, b.info, b.orth, st, false)) != RH_OK) return s;
+  std::vector<double> Qh((size_t)I * ell);
+  RH_CUDA_TRY(cudaMemcpyAsync(Qh.data(), b.Q, sizeof(double) * I * ell, cudaMemcpyDeviceToHost, st));
+  RH_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<double> A;
+  if ((s = subset_select_host(Qh, I, ell, o.select, 2.0, sel, A, o.seed, ((uint32_t)o.tensor_id << 4) | (uint32_t)n)) !=
+      RH_OK)
+    return s;
+  std::sort(sel.begin(), sel.end());
+  RH_CUDA_TRY(cudaMemcpyAsync(factor_n, A.data(), sizeof(double) * I * ell, cudaMemcpyHostToDevice, st));
+  if (selected_n) RH_CUDA_TRY(cudaMemcpyAsync(selected_n, sel.data(), sizeof(int32_t) * ell, cudaMemcpyHostToDevice, st));
+  // the host vectors are read by the copies above: wait for them before they go out of scope
+  RH_CUDA_TRY(cudaStreamSynchronize(st));
   return RH_OK;
 }
 
@@ -726,22 +918,14 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
       ix.idx[k] = nullptr;
       ix.stride[k] = 0;
     }
-    if ((s = sp_sketch_mode(ix, order, n, I, ell, cnnz, b.idx[set][n], b.vals[set], o.seed, o.tensor_id, z.items_max,
-                            b, b.Y, st)) != RH_OK)
+    if ((s = sp_sketch_mode(ix, order, n, I, stride, ell, cnnz, b.idx[set][n], b.vals[set], o.seed, o.tensor_id,
+                            o.omega_prec == RH_BF16, z.items_max, b, b.Y, st)) != RH_OK)
       return s;
-    // (d) thin QR (step 5)
-    RH_CUDA_TRY(cudaMemsetAsync(b.info, 0, sizeof(int32_t), st));
-    if ((s = launch_orthonormalize(I, ell, b.Y, b.Q, b.info, b.orth, st, false)) != RH_OK) return s;
-    // (e) strong RRQR selection and A_n = Q (P^T Q)^{-1} on the host (steps 6-7)
-    std::vector<double> Qh((size_t)I * ell);
-    RH_CUDA_TRY(cudaMemcpyAsync(Qh.data(), b.Q, sizeof(double) * I * ell, cudaMemcpyDeviceToHost, st));
-    RH_CUDA_TRY(cudaStreamSynchronize(st));
+    // (d)-(e) thin QR (step 5), the row selection (step 6, strong RRQR by default) and
+    // A_n = Q (P^T Q)^{-1} (step 7)
     std::vector<int> sel;
-    std::vector<double> A;
-    if ((s = subset_select_host(Qh, I, ell, RH_SELECT_SRRQR, 2.0, sel, A)) != RH_OK) return s;
-    RH_CUDA_TRY(cudaMemcpyAsync(factors[n], A.data(), sizeof(double) * I * ell, cudaMemcpyHostToDevice, st));
-    if (selected && selected[n])
-      RH_CUDA_TRY(cudaMemcpyAsync(selected[n], sel.data(), sizeof(int32_t) * ell, cudaMemcpyHostToDevice, st));
+    if ((s = sp_select_mode(I, ell, n, o, b, factors[n], selected ? selected[n] : nullptr, sel, st)) != RH_OK)
+      return s;
     // (f) G_(n) <- P^T G_(n): keep the selected slices, renumber mode n (step 8)
     std::vector<int32_t> pos(I, -1);
     for (int a = 0; a < ell; ++a) pos[sel[a]] = a;
@@ -790,6 +974,119 @@ rh_status sp_sthosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const 
   return RH_OK;
 }
 
+size_t sp_hosvd_coo_workspace_size(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* ranks,
+                                   const rh_options* opts) {
+  rh_options o;
+  rh_options_default(&o);
+  if (opts) o = *opts;
+  std::vector<int> rho, ells;
+  SpSizes z;
+  if (sp_plan(order, dims, nnz, ranks, o, rho, ells, z, true) != RH_OK) return 0;
+  Arena ar(nullptr);
+  carve_sp(ar, order, z);
+  return ar.used;
+}
+
+rh_status sp_hosvd_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx, const float* vals,
+                       const int32_t* ranks, const rh_options* opts, double* const* factors, int32_t* const* selected,
+                       double* core, double* norms, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  rh_options o;
+  rh_options_default(&o);
+  if (opts) o = *opts;
+  std::vector<int> rho, ells;
+  SpSizes z;
+  rh_status s = sp_plan(order, dims, nnz, ranks, o, rho, ells, z, true);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(idx != nullptr && vals != nullptr && factors != nullptr && core != nullptr,
+               "idx, vals, factors and core must be non-NULL");
+  for (int k = 0; k < order; ++k)
+    RH_CHECK_ARG(idx[k] != nullptr && factors[k] != nullptr, "every idx[n] and factors[n] must be non-NULL");
+  Arena meas(nullptr);
+  carve_sp(meas, order, z);
+  if (workspace == nullptr || workspace_bytes < meas.used) {
+    set_error("workspace too small: need " + std::to_string(meas.used) + " bytes");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  SpBufs b = carve_sp(ar, order, z);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (norms) {
+    const int nb = (int)std::min<int64_t>(ceil_div(nnz, 256), 1024);
+    sumsq_f32_kernel<<<nb, 256, 0, st>>>(vals, nnz, b.norm_part);
+    RH_LAUNCH_CHECK();
+    sum_parts_kernel<<<1, 32, 0, st>>>(b.norm_part, nb, norms);
+    RH_LAUNCH_CHECK();
+  }
+  // every mode of the input on its own (Sec. 5, SP-HOSVD): sketch, QR, selection, A_n
+  SpIdx in;
+  PosTabs pt;
+  int64_t pos_off = 0;
+  for (int k = 0; k < RH_MAX_ORDER; ++k) {
+    in.idx[k] = k < order ? idx[k] : nullptr;
+    in.stride[k] = 0;
+    pt.pos[k] = nullptr;
+  }
+  for (int n = 0; n < order; ++n) {
+    const int ell = ells[n];
+    const int64_t I = dims[n];
+    SpIdx ix = in;
+    int64_t stride = 1;
+    for (int k = 0; k < order; ++k) {
+      ix.stride[k] = 0;
+      if (k != n) {
+        ix.stride[k] = stride;
+        stride *= dims[k];
+      }
+    }
+    if ((s = sp_sketch_mode(ix, order, n, I, stride, ell, nnz, idx[n], vals, o.seed, o.tensor_id,
+                            o.omega_prec == RH_BF16, z.items_max, b, b.Y, st)) != RH_OK)
+      return s;
+    std::vector<int> sel;
+    if ((s = sp_select_mode(I, ell, n, o, b, factors[n], selected ? selected[n] : nullptr, sel, st)) != RH_OK)
+      return s;
+    std::vector<int32_t> pos(I, -1);
+    for (int a = 0; a < ell; ++a) pos[sel[a]] = a;
+    int32_t* pn = b.pos_all + pos_off;
+    RH_CUDA_TRY(cudaMemcpyAsync(pn, pos.data(), sizeof(int32_t) * I, cudaMemcpyHostToDevice, st));
+    RH_CUDA_TRY(cudaStreamSynchronize(st));   // pos is read by the copy
+    pt.pos[n] = pn;
+    pos_off += I;
+  }
+  // the core: the nonzeros whose every index is selected, renumbered (X at the selected coordinates)
+  keep_all_kernel<<<grid_for(nnz), 256, 0, st>>>(in, order, nnz, pt, b.flag);
+  RH_LAUNCH_CHECK();
+  size_t tb = b.cub_bytes;
+  RH_CUDA_TRY(cub::DeviceScan::ExclusiveSum(b.cub_tmp, tb, b.flag, b.dest, (int)nnz, st));
+  int32_t last_dest = 0, last_flag = 0;
+  RH_CUDA_TRY(cudaMemcpyAsync(&last_dest, b.dest + nnz - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  RH_CUDA_TRY(cudaMemcpyAsync(&last_flag, b.flag + nnz - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SpIdx out;
+  for (int k = 0; k < RH_MAX_ORDER; ++k) {
+    out.idx[k] = k < order ? b.idx[0][k] : nullptr;
+    out.stride[k] = 0;
+  }
+  compact_all_kernel<<<grid_for(nnz), 256, 0, st>>>(in, order, vals, nnz, b.flag, b.dest, pt, out, b.vals[0]);
+  RH_LAUNCH_CHECK();
+  RH_CUDA_TRY(cudaStreamSynchronize(st));
+  const int64_t kept = (int64_t)last_dest + last_flag;
+  int64_t ncore = 1;
+  SpIdx cx;
+  for (int k = 0; k < RH_MAX_ORDER; ++k) {
+    cx.idx[k] = k < order ? b.idx[0][k] : nullptr;
+    cx.stride[k] = k < order ? ncore : 0;
+    if (k < order) ncore *= ells[k];
+  }
+  RH_CUDA_TRY(cudaMemsetAsync(core, 0, sizeof(double) * ncore, st));
+  if (kept > 0) {
+    scatter_core_kernel<<<grid_for(kept), 256, 0, st>>>(cx, order, b.vals[0], kept, core);
+    RH_LAUNCH_CHECK();
+  }
+  if (norms && (s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
+  RH_CUDA_TRY(cudaStreamSynchronize(st));
+  return RH_OK;
+}
+
 rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t method, double eta, uint64_t seed,
                            uint32_t stream, int32_t* selected, double* A) {
   clear_error();
@@ -828,12 +1125,14 @@ size_t rhosvd_sketch_coo_workspace_size(int32_t order, const int64_t* dims, int6
 }
 
 rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, const int32_t* const* idx,
-                            const float* vals, int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id, double* Y,
-                            void* workspace, size_t workspace_bytes, void* stream) {
+                            const float* vals, int32_t mode, int32_t ell, uint64_t seed, int32_t tensor_id,
+                            int32_t omega_prec, double* Y, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
   const size_t need = rhosvd_sketch_coo_workspace_size(order, dims, nnz, mode, ell);
   RH_CHECK_ARG(need > 0, "bad order, dims, nnz, mode or ell");
   RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
+  RH_CHECK_ARG(omega_prec == RH_F64 || omega_prec == RH_F32 || omega_prec == RH_BF16,
+               "omega_prec must be RH_F32 (or RH_F64: the same FP32 normals) or RH_BF16");
   RH_CHECK_ARG(idx != nullptr && Y != nullptr && (nnz == 0 || vals != nullptr), "idx, vals and Y must be non-NULL");
   for (int k = 0; k < order; ++k) RH_CHECK_ARG(nnz == 0 || idx[k] != nullptr, "every idx[n] must be non-NULL");
   if (workspace == nullptr || workspace_bytes < need) {
@@ -859,8 +1158,8 @@ rh_status rhosvd_sketch_coo(int32_t order, const int64_t* dims, int64_t nnz, con
       stride *= dims[k];
     }
   }
-  return sp_sketch_mode(ix, order, mode, dims[mode], ell, nnz, nnz ? idx[mode] : nullptr, vals, seed, tensor_id,
-                        z.items_max, b, Y, (cudaStream_t)stream);
+  return sp_sketch_mode(ix, order, mode, dims[mode], stride, ell, nnz, nnz ? idx[mode] : nullptr, vals, seed, tensor_id,
+                        omega_prec == RH_BF16, z.items_max, b, Y, (cudaStream_t)stream);
 }
 
 }  // extern "C"

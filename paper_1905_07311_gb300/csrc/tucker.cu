@@ -240,6 +240,80 @@ size_t rh_tucker_residual_workspace_size(int32_t order, const int64_t* dims, int
   return ar.used;
 }
 
+// ---- orthonormalising post-processing (Sec. 5) ---------------------------------------------
+static rh_status ortho_tucker_check(int32_t order, const int64_t* dims, const int32_t* ks) {
+  RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr && ks != nullptr, "bad order, dims or ks");
+  for (int n = 0; n < order; ++n) {
+    RH_CHECK_ARG(dims[n] >= 1, "every dimension must be >= 1");
+    RH_CHECK_ARG(ks[n] >= 1 && ks[n] <= dims[n] && ks[n] <= RH_MAX_ELL, "need 1 <= k_n <= min(I_n, 64)");
+  }
+  return RH_OK;
+}
+
+size_t rh_orthonormalize_tucker_workspace_size(int32_t order, const int64_t* dims, const int32_t* ks) {
+  if (ortho_tucker_check(order, dims, ks) != RH_OK) return 0;
+  size_t orth = 1, q = 1, ncore = 1;
+  for (int n = 0; n < order; ++n) {
+    orth = std::max(orth, orth_workspace_elems(dims[n], ks[n]));
+    q = std::max(q, (size_t)dims[n] * ks[n]);
+    ncore *= (size_t)ks[n];
+  }
+  Arena ar(nullptr);
+  ar.take<double>(orth);
+  ar.take<double>(q);
+  ar.take<double>((size_t)RH_MAX_ELL * RH_MAX_ELL);
+  ar.take<double>(ncore);
+  ar.take<double>(ncore);
+  return ar.used;
+}
+
+rh_status rh_orthonormalize_tucker(int32_t order, const int64_t* dims, const int32_t* ks, double* const* factors,
+                                   double* core, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  rh_status s = ortho_tucker_check(order, dims, ks);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(factors != nullptr && core != nullptr, "factors and core must be non-NULL");
+  for (int n = 0; n < order; ++n) RH_CHECK_ARG(factors[n] != nullptr, "every factors[n] must be non-NULL");
+  const size_t need = rh_orthonormalize_tucker_workspace_size(order, dims, ks);
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    return RH_ENOMEM;
+  }
+  size_t orth = 1, q = 1;
+  int64_t ncore = 1;
+  for (int n = 0; n < order; ++n) {
+    orth = std::max(orth, orth_workspace_elems(dims[n], ks[n]));
+    q = std::max(q, (size_t)dims[n] * ks[n]);
+    ncore *= ks[n];
+  }
+  Arena ar(workspace);
+  double* ows = ar.take<double>(orth);
+  double* Q = ar.take<double>(q);
+  double* R = ar.take<double>((size_t)RH_MAX_ELL * RH_MAX_ELL);
+  double* bufs[2] = {ar.take<double>((size_t)ncore), ar.take<double>((size_t)ncore)};
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> kd(ks, ks + order);
+  const double* in = core;
+  int nb = 0;
+  for (int n = 0; n < order; ++n) {
+    const int64_t I = dims[n];
+    const int k = ks[n];
+    // A_n = Q_n R_n: Q_n by the thin QR of Alg. 1 step 2 (column signs: largest entry positive),
+    // R_n = Q_n^T A_n (k x k, the mode-0 product of the I x k matrix A_n)
+    if ((s = launch_orthonormalize(I, k, factors[n], Q, nullptr, ows, st, false)) != RH_OK) return s;
+    if ((s = launch_ttm<double, double>(ModeView{1, I, (int64_t)k}, factors[n], Q, k, R, st)) != RH_OK) return s;
+    // G <- G x_n R_n (G_(n) <- R_n G_(n)); R_n(c, i) = R[c + k i]
+    if ((s = launch_ttm_strided<double, double>(mode_view(order, kd.data(), n), in, R, k, 1, k, bufs[nb], st)) !=
+        RH_OK)
+      return s;
+    in = bufs[nb];
+    nb ^= 1;
+    RH_CUDA_TRY(cudaMemcpyAsync(factors[n], Q, sizeof(double) * I * k, cudaMemcpyDeviceToDevice, st));
+  }
+  RH_CUDA_TRY(cudaMemcpyAsync(core, in, sizeof(double) * ncore, cudaMemcpyDeviceToDevice, st));
+  return RH_OK;
+}
+
 rh_status rh_tucker_residual(int32_t order, const int64_t* dims, int32_t dtype, const void* X,
                              const double* const* factors, const int32_t* ks, const double* core, double* out,
                              void* workspace, size_t workspace_bytes, void* stream) {

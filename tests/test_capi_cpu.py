@@ -287,10 +287,11 @@ def test_every_entry_point_validates_before_the_device(L):
                            ptr3, one, r3, None, one, big, None) == 6
     assert L.adaptive_rank(3, d3, 1, one, 0.1, 0, 4, ks, o, ptr3, one, r3, None, one, 1, None) == 2
     # sparse sketch and SP-STHOSVD (Alg. 6)
-    assert L.rhosvd_sketch_coo(3, d3, -1, ptr3, one, 0, 4, 0, 0, one, one, big, None) == 1
-    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 3, 4, 0, 0, one, one, big, None) == 1
-    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 65, 0, 0, one, one, big, None) == 1
-    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 4, 0, 0, one, one, 1, None) == 2
+    assert L.rhosvd_sketch_coo(3, d3, -1, ptr3, one, 0, 4, 0, 0, 1, one, one, big, None) == 1
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 3, 4, 0, 0, 1, one, one, big, None) == 1
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 65, 0, 0, 1, one, one, big, None) == 1
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 4, 0, 0, 7, one, one, big, None) == 1   # omega_prec
+    assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 0, 4, 0, 0, 1, one, one, 1, None) == 2
     strict = _lib.i32_array([4, 4, 5])     # mode 2 (processed last): ell = 10 is not < I_2 = 10
     assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, strict, o, ptr3, None, one, None, one, big, None) == 1
     assert "must be < min" in _err(L)
@@ -298,6 +299,15 @@ def test_every_entry_point_validates_before_the_device(L):
     assert L.sp_sthosvd_coo_workspace_size(3, d3, 10, strict, ctypes.byref(_lib.make_options(p=5, clamp=True))) > 0
     assert L.sp_sthosvd_coo(3, d3, 10, ptr3, None, ks, o, ptr3, None, one, None, one, big, None) == 1
     assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, ks, o, ptr3, None, one, None, one, 1, None) == 2
+    bad_sel = ctypes.byref(_lib.make_options(p=5, select=9))
+    assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, ks, bad_sel, ptr3, None, one, None, one, big, None) == 1
+    bad_om = ctypes.byref(_lib.make_options(p=5, omega_prec=4))
+    assert L.sp_sthosvd_coo(3, d3, 10, ptr3, one, ks, bad_om, ptr3, None, one, None, one, big, None) == 1
+    # SP-HOSVD: the strict size rule on the input sizes, every mode
+    assert L.sp_hosvd_coo(3, d3, 10, ptr3, one, strict, o, ptr3, None, one, None, one, big, None) == 1
+    assert L.sp_hosvd_coo_workspace_size(3, d3, 10, ks, o) > 0
+    assert L.sp_hosvd_coo(3, d3, 10, ptr3, None, ks, o, ptr3, None, one, None, one, big, None) == 1
+    assert L.sp_hosvd_coo(3, d3, 10, ptr3, one, ks, o, ptr3, None, one, None, one, 1, None) == 2
     # host-buffer R-STHOSVD and R-HOSVD (Alg. 3, Alg. 2)
     bad = _lib.i32_array([26, 4, 4])       # r_0 + p = 31 > I_0 = 30
     assert L.rsthosvd_host(3, d3, 1, one, bad, o, ptr3, one, None, None, one, big, None) == 1
