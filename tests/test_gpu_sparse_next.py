@@ -117,7 +117,8 @@ def _check_sp(T, out, idx, vals, dims, hosvd=False):
         for n in range(d):
             assert np.abs(A[n] - out["factors"][n]).max() <= 1e-5 * max(1.0, np.abs(out["factors"][n]).max())
         assert np.array_equal(G, out["core"])
-        assert abs(e_g - e_o) <= 1e-6
+        # relative to the error: a poorly conditioned P^T Q (uniform sampling) amplifies both
+        assert abs(e_g - e_o) <= 1e-5 * max(1.0, e_o)
         return True
     assert e_g <= 1.5 * e_o + 1e-12
     return False
