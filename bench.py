@@ -482,7 +482,7 @@ def run_reference(args):
 # Further workloads (--workload): the configurations the tests check for parity, measured with the
 # same rules (inputs resident, CUDA events on the launching stream, clocks sampled, warm-up).
 # ---------------------------------------------------------------------------------
-NAMES = {0: "sketch", 1: "mode_product", 2: "qr", 3: "trunc_svd", 4: "core_product", 5: "jacobi"}
+NAMES = {0: "sketch", 1: "mode_product", 2: "qr", 3: "trunc_svd", 4: "core_product", 5: "jacobi", 6: "power_step"}
 
 
 def _timed(torch, L, fn, steps, warmup, device, profile=True):
@@ -775,16 +775,25 @@ def wl_batched_waves(torch, rh, L, args, device, peaks, src, orders):
 
 def wl_sparse(torch, rh, L, args, device, peaks, src):
     """COO 20000 x 20000 x 5000 with 5e7 nonzeros (Zipf 1.1, log-count values), SP-STHOSVD rank 30,
-    p = 10.  The sketch is not HBM- or tensor-bound: its roof is max(COO bytes / HBM, Omega
+    p = 10, with FP32 Omega and with Omega rounded to BF16 (the two forms of the sparse sketch), and
+    SP-HOSVD.  The sketch is not HBM- or tensor-bound: each distinct Omega row (a distinct pair of
+    other-mode coordinates) is generated once, so its roof is max(COO bytes / HBM, distinct rows x ell
     normals / the measured rate of the library's Omega generator)."""
     from workloads import zipf_coo_torch
 
     dims, nnz = [20000, 20000, 5000], 50_000_000
     idx, vals = zipf_coo_torch(dims, nnz, 1.1, 3.0, 5, device)
     torch.cuda.synchronize()
-    ms, br, launches, clk = _timed(torch, L, lambda: rh.sp_sthosvd_coo(idx, vals, dims, [30] * 3, p=10, seed=0),
-                                   args.steps, args.warmup, device, profile=False)
-    ms_sk, _, _, _ = _timed(torch, L, lambda: rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0),
+    forms = {}
+    for om in ("f32", "bf16"):
+        ms, _, launches, clk = _timed(torch, L, lambda: rh.sp_sthosvd_coo(idx, vals, dims, [30] * 3, p=10, seed=0,
+                                                                           omega=om),
+                                      args.steps, args.warmup, device, profile=False)
+        ms_sk, _, _, _ = _timed(torch, L, lambda: rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0, omega=om),
+                                args.steps, args.warmup, device, profile=False)
+        forms[om] = {"sp_sthosvd_ms": round(ms, 3), "sketch_mode1_ms": round(ms_sk, 4), "launches": launches,
+                     "clocks": clk}
+    ms_ho, _, _, _ = _timed(torch, L, lambda: rh.sp_hosvd_coo(idx, vals, dims, [30] * 3, p=10, seed=0),
                             args.steps, args.warmup, device, profile=False)
     # Omega generator rate (normals per second) on a long stream
     rows = 1 << 24
@@ -792,15 +801,20 @@ def wl_sparse(torch, rh, L, args, device, peaks, src):
     o_ms, _, _, _ = _timed(torch, L, lambda: L.rh_omega(0, 0, 0, 0, rows, 40, ctypes.c_void_p(out.data_ptr()),
                                                         ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)),
                            args.steps, args.warmup, device, profile=False)
+    del out
     rate = 40.0 * rows / (o_ms * 1e-3)
+    # distinct Omega rows of mode 1: distinct (i_2, i_3) pairs
+    distinct = int(torch.unique(idx[1].long() + dims[1] * idx[2].long()).numel())
     sk_bytes = nnz * 16.0
-    t_roof = max(sk_bytes / (peaks["hbm_gbs"] * 1e9), nnz * 40.0 / rate) * 1e3
-    roof = {"kernel": "rhosvd_sketch_coo (mode 1, ell 40)", "bound": "alu", "achieved": round(t_roof / ms_sk, 4),
-            "peak": 1.0, "unit": "fraction of max(COO bytes / HBM, normals / Omega rate)",
+    t_roof = max(sk_bytes / (peaks["hbm_gbs"] * 1e9), distinct * 40.0 / rate) * 1e3
+    ms_sk = forms["f32"]["sketch_mode1_ms"]
+    roof = {"kernel": "rhosvd_sketch_coo (mode 1, ell 40, FP32 Omega)", "bound": "alu",
+            "achieved": round(t_roof / ms_sk, 4), "peak": 1.0,
+            "unit": "fraction of max(COO bytes / HBM, distinct Omega rows x ell / Omega rate)",
             "frac": round(t_roof / ms_sk, 4), "traffic": None,
             "peak_source": f"Omega generator measured at {rate / 1e9:.1f} G normals/s (rh_omega, 2^24 x 40), "
                            f"HBM {peaks['hbm_gbs']} GB/s ({src})",
-            "roof_ms": round(t_roof, 4), "avg_launch_ms": round(ms_sk, 4)}
+            "distinct_rows_mode1": distinct, "roof_ms": round(t_roof, 4), "avg_launch_ms": ms_sk}
     cpu = None
     if not args.no_cpu:
         from oracle import tucker
@@ -813,11 +827,63 @@ def wl_sparse(torch, rh, L, args, device, peaks, src):
         dt = time.perf_counter() - t
         cpu = {"value": round(m / dt / 1e6, 3), "unit": "M nonzeros/s (sketch, ell 40)", "cores": _cores(),
                "kind": "oracle", "sample": "oracle COO sketch of the first 1e6 nonzeros, mode 1, ell 40"}
-    return {"metric": "SP-STHOSVD time-to-Tucker, COO 20000x20000x5000, 5e7 nonzeros", "value": round(ms, 3),
-            "unit": "ms", "higher_is_better": False, "dtype": "f32", "sketch_mode1_ms": round(ms_sk, 4),
+    return {"metric": "SP-STHOSVD time-to-Tucker, COO 20000x20000x5000, 5e7 nonzeros",
+            "value": forms["f32"]["sp_sthosvd_ms"], "unit": "ms", "higher_is_better": False, "dtype": "f32",
+            "sketch_mode1_ms": ms_sk, "forms": forms, "sp_hosvd_ms": round(ms_ho, 3),
             "config": {"workload": "COO 20000x20000x5000, 5e7 distinct Zipf(1.1) coordinates, values "
                                    "log(1+Poisson(3)+1), seed 5; rank (30,30,30), p=10", "l2": "800 MB of COO; no flush"},
-            "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+            "roofline": roof, "gpu_launches": forms["f32"]["launches"], "clocks": forms["f32"]["clocks"],
+            "cpu_baseline": cpu}
+
+
+def _dense1024_error(torch, rh, X, T):
+    """Relative Tucker error by direct residual (FP64 reconstruction on the device)."""
+    A = [f.T.contiguous() for f in T.factors]
+    core = T.core.reshape(list(reversed(T.core_dims)))
+    X64 = X.double()
+    e = float(torch.linalg.vector_norm(X64 - _reconstruct(torch, core, A)) / torch.linalg.vector_norm(X64))
+    del X64
+    return e
+
+
+def wl_power1024(torch, rh, L, args, device, peaks, src):
+    """The benchmark tensor (1024^3 FP32, rank 50, p = 10, form f32_bf16x2) with q = 0, 1, 2 steps of
+    randomized subspace iteration in every range finder (Sec. 5 "Variants", Sec. 6): time-to-Tucker,
+    relative error, and the cost of a step.  A step is a mode product (tensor cores), the basis of
+    range(B^T) (tall-skinny QR + CholeskyQR), a sketch against that dense basis (CUDA cores, the
+    same head + tail split of X) and a QR."""
+    X = make_input(torch, device)
+    out = {}
+    for q in (0, 1, 2):
+        call = rh.RsthosvdCall(DIMS, "f32_bf16x2", RANKS, p=P, seed=SEED, rho=RHO, device=device, power_iters=q)
+        ms, br, launches, clk = _timed(torch, L, lambda: call.run(X), args.steps, args.warmup, device)
+        T = call.run(X)
+        torch.cuda.synchronize()
+        out[f"q{q}"] = {"ms": round(ms, 3), "rel_error": _dense1024_error(torch, rh, X, T),
+                        "launches": launches, "clocks": clk, "breakdown_ms": br}
+        del call
+    return {"metric": "R-STHOSVD time-to-Tucker with subspace iteration, 1024^3 FP32 rank 50 p 10",
+            "value": out["q1"]["ms"], "unit": "ms", "higher_is_better": False, "dtype": "bf16x2",
+            "power_iters": out, "config": {"workload": WORKLOAD, "form": "f32_bf16x2"}}
+
+
+def wl_rhosvd1024(torch, rh, L, args, device, peaks, src):
+    """R-HOSVD (Alg. 2) of the benchmark tensor (1024^3 FP32, rank 50, p = 10): every mode sketched
+    on the input, then the core chain.  Algorithmic bytes: X read once per mode's sketch and mode
+    product and once more for the core chain's first product."""
+    X = make_input(torch, device)
+    call = rh.RhosvdCall(DIMS, torch.float32, RANKS, p=P, seed=SEED, device=device)
+    ms, br, launches, clk = _timed(torch, L, lambda: call.run(X), args.steps, args.warmup, device)
+    T = call.run(X)
+    torch.cuda.synchronize()
+    e = _dense1024_error(torch, rh, X, T)
+    N = float(np.prod(DIMS))
+    nbytes = N * 4 * 4            # three sketches + the core chain's first mode product
+    return {"metric": "R-HOSVD time-to-Tucker, 1024^3 FP32 rank 50 p 10", "value": round(ms, 3), "unit": "ms",
+            "higher_is_better": False, "dtype": "f32", "rel_error": e, "breakdown_ms": br,
+            "gpu_launches": launches, "clocks": clk,
+            "roofline": _hbm_roof("R-HOSVD (whole call)", nbytes, ms, peaks, src),
+            "config": {"workload": WORKLOAD.replace("R-STHOSVD", "R-HOSVD")}}
 
 
 def wl_peaks(torch, rh, L, args, device, peaks, src):
@@ -880,7 +946,7 @@ def run_workload(args):
     L = _lib.lib()
     peaks, src = measured_peaks()
     fn = {"hilbert200": wl_hilbert200, "lowp192": wl_lowp192, "batched": wl_batched, "sparse": wl_sparse,
-          "peaks": wl_peaks}[args.workload]
+          "peaks": wl_peaks, "power1024": wl_power1024, "rhosvd1024": wl_rhosvd1024}[args.workload]
     line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
     line.update(fn(torch, rh, L, args, device, peaks, src))
     print(json.dumps(line))
@@ -903,7 +969,8 @@ def main():
     ap.add_argument("--dims", type=int, nargs=3, default=None,
                     help="smaller cube for profiling captures (default 1024 1024 1024)")
     ap.add_argument("--workload", default="dense1024",
-                    choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse", "peaks"],
+                    choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse", "peaks", "power1024",
+                             "rhosvd1024"],
                     help="dense1024: the benchmark line (default); the others measure the further configurations "
                          "and print one JSON line each")
     ap.add_argument("--batch-orders", default="3,4",

@@ -275,6 +275,18 @@ def test_sparse_full_size(rh):
         bound = (512 + 8) * 2.0 ** -24 * (np.abs(v) @ np.abs(om))
         got = Y[i, [0, 1, 38, 39]]
         assert np.all(np.abs(got - ref) <= bound + 1e-300), (i, got, ref)
+    # the BF16-Omega form: the same rows against the rounded stream
+    Yb = rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0, tensor_id=0, omega="bf16").cpu().numpy().T
+    for i in (0, 7, 19999):
+        sel = (idx[0] == i).nonzero().flatten()
+        sub = np.stack([t[sel].long().cpu().numpy() for t in idx], axis=1)
+        v = vals[sel].double().cpu().numpy()
+        p = otk._kolda_rows(sub, dims, 0)
+        om = orng.round_bf16(orng.omega_columns(0, 0, 0, p, [0, 1, 38, 39])).astype(np.float64)
+        ref = v @ om
+        bound = (512 + 8) * 2.0 ** -24 * (np.abs(v) @ np.abs(om))
+        got = Yb[i, [0, 1, 38, 39]]
+        assert np.all(np.abs(got - ref) <= bound + 1e-300), (i, got, ref)
     T = rh.sp_sthosvd_coo(idx, vals, dims, [30, 30, 30], p=10, seed=0)
     torch.cuda.synchronize()
     keys = (idx[0].long() * dims[1] + idx[1].long()) * dims[2] + idx[2].long()
