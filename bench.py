@@ -482,7 +482,8 @@ def run_reference(args):
 # Further workloads (--workload): the configurations the tests check for parity, measured with the
 # same rules (inputs resident, CUDA events on the launching stream, clocks sampled, warm-up).
 # ---------------------------------------------------------------------------------
-NAMES = {0: "sketch", 1: "mode_product", 2: "qr", 3: "trunc_svd", 4: "core_product", 5: "jacobi", 6: "power_step"}
+NAMES = {0: "sketch", 1: "mode_product", 2: "qr", 3: "trunc_svd", 4: "core_product", 5: "jacobi", 6: "power_step",
+         7: "sp_omega_table", 8: "sp_sort", 9: "sp_items", 10: "sp_row_reduce"}
 
 
 def _timed(torch, L, fn, steps, warmup, device, profile=True):
@@ -789,10 +790,10 @@ def wl_sparse(torch, rh, L, args, device, peaks, src):
         ms, _, launches, clk = _timed(torch, L, lambda: rh.sp_sthosvd_coo(idx, vals, dims, [30] * 3, p=10, seed=0,
                                                                            omega=om),
                                       args.steps, args.warmup, device, profile=False)
-        ms_sk, _, _, _ = _timed(torch, L, lambda: rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0, omega=om),
-                                args.steps, args.warmup, device, profile=False)
+        ms_sk, br_sk, _, _ = _timed(torch, L, lambda: rh.rhosvd_sketch_coo(idx, vals, dims, 0, 40, seed=0, omega=om),
+                                    args.steps, args.warmup, device, profile=True)
         forms[om] = {"sp_sthosvd_ms": round(ms, 3), "sketch_mode1_ms": round(ms_sk, 4), "launches": launches,
-                     "clocks": clk}
+                     "clocks": clk, "sketch_breakdown_ms": br_sk}
     ms_ho, _, _, _ = _timed(torch, L, lambda: rh.sp_hosvd_coo(idx, vals, dims, [30] * 3, p=10, seed=0),
                             args.steps, args.warmup, device, profile=False)
     # Omega generator rate (normals per second) on a long stream

@@ -70,7 +70,8 @@ int tc_probe_next();
 // Per-launch timing (profile.cu): a scope records an event before and after the kernels
 // it encloses when profiling is on.  kind: 0 sketch, 1 mode product, 2 QR of the sketch,
 // 3 truncation SVD; tag: the step of the algorithm (0 = first processed mode).
-enum { PROF_SKETCH = 0, PROF_TTM = 1, PROF_ORTH = 2, PROF_TRUNC = 3, PROF_TTM_CORE = 4, PROF_JACOBI = 5, PROF_POWER = 6 };
+enum { PROF_SKETCH = 0, PROF_TTM = 1, PROF_ORTH = 2, PROF_TRUNC = 3, PROF_TTM_CORE = 4, PROF_JACOBI = 5, PROF_POWER = 6,
+       PROF_SP_TABLE = 7, PROF_SP_SORT = 8, PROF_SP_ITEMS = 9, PROF_SP_REDUCE = 10 };
 class ProfileScope {
  public:
   ProfileScope(int kind, int tag, cudaStream_t st);

@@ -12,6 +12,7 @@ struct SketchPlan {
   int gx, S;
   int64_t chunk;
   int ti = 0;         // small-row kernel (I <= 128, ell <= 32): rows per CTA; 0 = the general kernel
+  int64_t row0 = 0;   // Omega row of Kolda column 0 (a slab of a larger tensor: its global offset)
   size_t part_elems() const { return (size_t)S * ell * v.I; }
   size_t norm_elems() const { return (size_t)S * gx; }
 };
@@ -36,16 +37,16 @@ rh_status launch_sketch_dense(const SketchPlan& pl, const T* G, const T* W, bool
 bool sketch_tc_supported(const ModeView& v, int ell);
 int sketch_tc_ctas(const ModeView& v);
 rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
-                           uint32_t sid, float* part, int32_t* err, cudaStream_t st);
+                           uint32_t sid, float* part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
 // FP32 input split on the fly into the same two pieces; norm_part (sketch_tc_ctas doubles, may
 // be NULL) receives per-CTA sums of squares of the split values
 rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
-                               double* norm_part, int32_t* err, cudaStream_t st);
+                               double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
 // E4M3 input (leading dimension ld, one FP32 scale per 128 bytes of storage), dequantized and
 // split on the fly into the same two pieces as FP32 input
 rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                                uint64_t seed, uint32_t sid, float* part, double* norm_part, int32_t* err,
-                               cudaStream_t st);
+                               cudaStream_t st, int64_t row0 = 0);
 rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st);
 rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 // ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles

@@ -67,6 +67,7 @@ struct SketchArgs {
   T* part;
   double* part_norm;   // may be NULL
   const T* W;          // dense operand (OPD != 0), laid out like the mode product's output (L, ell, R)
+  int64_t row0;        // Omega row of Kolda column 0 (a slab of a larger tensor: its global offset)
 };
 
 // Operand of the sketch: kOpOmega, the Gaussian stream generated on the fly (Alg. 1 step 1);
@@ -144,7 +145,7 @@ __device__ __forceinline__ void SketchOp<T, ELLP, KCONTIG, OPD>::body(const Grid
         const int kp = t / CG, q = t % CG;
         const int64_t p = p0 + kp;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p < pe) v = rng::omega4(k0, k1, sid, p, (uint32_t)q);
+        if (p < pe) v = rng::omega4(k0, k1, sid, p + args.row0, (uint32_t)q);
         *reinterpret_cast<float4*>(&Os[kp][4 * q]) = v;
       }
     } else {
@@ -265,6 +266,7 @@ struct SketchSmallArgs {
   T* part;
   double* part_norm;
   FastDiv fI, fL;   // division by I (unit-stride view) and by L (strided view)
+  int64_t row0;     // Omega row of Kolda column 0
 };
 
 template <typename T>
@@ -391,7 +393,7 @@ __device__ __forceinline__ void SketchSmallOp<T, TI, E, KC>::body(const Grid g, 
       const int kp = t / CG, q = t % CG;
       const int64_t p = p0 + kp;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p < pe && q < nq) v = rng::omega4(args.k0, args.k1, args.sid, p, (uint32_t)q);
+      if (p < pe && q < nq) v = rng::omega4(args.k0, args.k1, args.sid, p + args.row0, (uint32_t)q);
       *reinterpret_cast<float4*>(&sm.t.Os[kp][4 * q]) = v;
     }
     __syncthreads();
@@ -579,14 +581,14 @@ rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
   if (pl.ti > 0) {
     const SketchSmallArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm,
-                               FastDiv((uint32_t)pl.v.I), FastDiv((uint32_t)pl.v.L)};
+                               FastDiv((uint32_t)pl.v.I), FastDiv((uint32_t)pl.v.L), pl.row0};
     if (pl.ti == 32) return emit_sketch_small_e<T, 32>(pl, a, st);
     if (pl.ti == 64) return emit_sketch_small_e<T, 64>(pl, a, st);
     return emit_sketch_small_e<T, 128>(pl, a, st);
   }
   const dim3 grid(pl.gx, pl.S);
   const bool kc = (pl.v.L == 1);
-  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm, nullptr};
+  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, k0, k1, sid, part, part_norm, nullptr, pl.row0};
   if (pl.ellp == 32)
     return kc ? emit<SketchOp<T, 32, true>>(SITE_SKETCH, 0, grid, 0, st, a)
               : emit<SketchOp<T, 32, false>>(SITE_SKETCH, 0, grid, 0, st, a);
@@ -623,7 +625,7 @@ rh_status launch_sketch_dense(const SketchPlan& pl, const T* G, const T* W, bool
     set_error("dense sketch: needs the plan of plan_sketch_dense");
     return RH_EUNSUPPORTED;
   }
-  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, 0u, 0u, 0u, part, nullptr, W};
+  const SketchArgs<T> a{G, pl.v.L, pl.v.I, pl.v.R, pl.ell, pl.chunk, 0u, 0u, 0u, part, nullptr, W, 0};
   if constexpr (sizeof(T) == 4) {
     if (split)
       return pl.ellp == 32 ? emit_sketch_dense<T, 32, kOpDenseSplit>(pl, a, st, site)

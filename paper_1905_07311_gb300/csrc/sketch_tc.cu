@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, int npieces,
                      int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
                      uint32_t sid, float* __restrict__ part, double* __restrict__ norm_part,
-                     int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld, int probe) {
+                     int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld, int probe,
+                     int64_t row0) {
   using Cfg = SketchCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
       const uint32_t b = oc & 1;
       if (oc >= 2 && !tc::mbar_wait(&S.om_empty[b], ((oc >> 1) - 1) & 1, err, 4)) break;
       uint8_t* om = &S.om[b][0];
-      const int64_t row = c * kPChunk + p;
+      const int64_t row = row0 + c * kPChunk + p;
       for (int q = t >> 6; q < nq; q += 2) {
         float4 v = rng::omega4(k0, k1, sid, row, (uint32_t)q);
         const float vv[4] = {v.x, v.y, v.z, v.w};
@@ -452,7 +453,7 @@ int sketch_tc_ctas(const ModeView& v) {
 }
 
 rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
-                           uint32_t sid, float* part, int32_t* err, cudaStream_t st) {
+                           uint32_t sid, float* part, int32_t* err, cudaStream_t st, int64_t row0) {
   if (!sketch_tc_supported(v, ell)) {
     set_error("tensor-core sketch: unsupported shape (needs the first mode, I % 8 == 0, I <= 1024, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -475,13 +476,13 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m1, np, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      nullptr, err, nullptr, 0, tc_probe_next());
+      nullptr, err, nullptr, 0, tc_probe_next(), row0);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
 
 rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
-                               double* norm_part, int32_t* err, cudaStream_t st) {
+                               double* norm_part, int32_t* err, cudaStream_t st, int64_t row0) {
   if (!sketch_tc_supported(v, ell)) {
     set_error("tensor-core sketch: unsupported shape (needs the first mode, I % 8 == 0, I <= 1024, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -498,14 +499,14 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, nullptr, 0, tc_probe_next());
+      norm_part, err, nullptr, 0, tc_probe_next(), row0);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
 
 rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                                uint64_t seed, uint32_t sid, float* part, double* norm_part, int32_t* err,
-                               cudaStream_t st) {
+                               cudaStream_t st, int64_t row0) {
   if (!sketch_tc_supported(v, ell) || ld < v.I || ld % 16 != 0) {
     set_error("tensor-core sketch: unsupported E4M3 shape (needs the first mode, I % 8 == 0, I <= 1024, "
               "ell <= 64, a leading dimension that is a multiple of 16)");
@@ -523,7 +524,7 @@ rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, con
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 1, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, scales, ld, tc_probe_next());
+      norm_part, err, scales, ld, tc_probe_next(), row0);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

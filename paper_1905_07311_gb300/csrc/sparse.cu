@@ -182,15 +182,44 @@ __global__ void __launch_bounds__(256) sp_sketch_items_kernel(SpIdx ix, int d, c
   }
 }
 
-// Y[r, c] = sum of the partials of row r's items, in item order (rows without items: 0)
-__global__ void sp_sketch_reduce_kernel(const double* __restrict__ part, const int32_t* __restrict__ row_items,
-                                        int64_t I, int ell, double* __restrict__ Y) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < I * ell; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e % I;
-    const int c = (int)(e / I);
-    double s = 0.0;
-    for (int it = row_items[r]; it < row_items[r + 1]; ++it) s += part[(int64_t)it * ell + c];
-    Y[r + I * c] = s;
+// Y[r, c] = sum of the partials of row r's items (rows without items: 0).  CTA per row: lane l of
+// warp w owns columns l and l + 32 and sums the items w, w + 8, w + 16, ... of the row in four
+// interleaved chains (independent loads in flight), then warp 0 adds the eight warp sums in order:
+// a fixed summation order, so the result is deterministic, and a heavy row (a Zipf index can hold
+// thousands of items) is spread over 256 threads instead of one serial chain per column.
+constexpr int kRedRowWarps = 8;
+__global__ void __launch_bounds__(32 * kRedRowWarps) sp_sketch_reduce_kernel(const double* __restrict__ part,
+                                                                             const int32_t* __restrict__ row_items,
+                                                                             int64_t I, int ell,
+                                                                             double* __restrict__ Y) {
+  __shared__ double red[kRedRowWarps][2][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t r = blockIdx.x; r < I; r += gridDim.x) {
+    const int b = row_items[r], e = row_items[r + 1];
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      double ch[4] = {0.0, 0.0, 0.0, 0.0};
+      if (c < ell) {
+        int it = b + w;
+        for (; it + 3 * kRedRowWarps < e; it += 4 * kRedRowWarps) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ch[j] += part[(int64_t)(it + j * kRedRowWarps) * ell + c];
+        }
+        for (; it < e; it += kRedRowWarps) ch[0] += part[(int64_t)it * ell + c];
+      }
+      red[w][h][lane] = (ch[0] + ch[1]) + (ch[2] + ch[3]);
+    }
+    __syncthreads();
+    if (w == 0) {
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        double t = red[0][h][lane];
+#pragma unroll
+        for (int k = 1; k < kRedRowWarps; ++k) t += red[k][h][lane];
+        if (c < ell) Y[r + I * c] = t;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -663,6 +692,7 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int64_t M
   if (table) {
     // (0) the distinct Omega rows: sort the nonzeros' Kolda indices, number the distinct ones, and
     // generate each row once into the table
+    ProfileScope ps(PROF_SP_TABLE, n, st);
     kolda_key_kernel<<<grid_for(cnnz), 256, 0, st>>>(ix, order, cnnz, b.keys_in);
     RH_LAUNCH_CHECK();
     RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, b.keys_in, b.keys_out, b.perm_in, b.perm_out,
@@ -684,6 +714,7 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int64_t M
   tb = b.cub_bytes;
   RH_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * (I + 1), st));
   if (cnnz > 0) {
+    ProfileScope ps(PROF_SP_SORT, n, st);
     RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, key, b.keys_out, b.perm_in, b.perm_out,
                                                 (int)cnnz, 0, bits_for(I), st));
     count_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, I, b.cnt);
@@ -717,6 +748,7 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int64_t M
   RH_CUDA_TRY(cudaMemcpyAsync(b.row_items, row_items.data(), sizeof(int32_t) * (I + 1), cudaMemcpyHostToDevice, st));
   // (c) sketch Y = G_(n) Omega_n (step 4)
   if (!items.empty()) {
+    ProfileScope ps(PROF_SP_ITEMS, n, st);
     const int nwarps = (int)std::min<int64_t>((int64_t)items.size(), 64LL * num_sms());
     const dim3 grid((unsigned)ceil_div(nwarps, 8));
     const int nit = (int)items.size();
@@ -734,7 +766,9 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int64_t M
                                                         nullptr, nullptr, ldo, b.part);
     RH_LAUNCH_CHECK();
   }
-  sp_sketch_reduce_kernel<<<grid_for(I * ell), 256, 0, st>>>(b.part, b.row_items, I, ell, Y);
+  ProfileScope psr(PROF_SP_REDUCE, n, st);
+  sp_sketch_reduce_kernel<<<(unsigned)std::min<int64_t>(I, 64LL * num_sms()), 32 * kRedRowWarps, 0, st>>>(
+      b.part, b.row_items, I, ell, Y);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
