@@ -201,6 +201,49 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * rhosvd_sketch_offset -- rhosvd_sketch of a block of consecutive Kolda columns of a larger tensor's
+ * unfolding: the rows of Omega_mode used are row0, row0 + 1, ... instead of 0, 1, ...  For a slab
+ * X[..., k0:k1] of a tensor cut along its last mode, the slab's mode-n unfolding (n before the last
+ * mode) holds the global columns p + L R' k0 (L, R' the products of the sizes before and between),
+ * so the slabs' sketches with row0 = L R' k0 add up to the whole tensor's sketch (the partition of
+ * Alg. 3 over slabs).  accumulate = 1 adds the slab's sketch (and ||slab||^2) to Y (and *norm2)
+ * instead of overwriting them, so slabs streamed one after another sum on the device.  row0 >= 0;
+ * the rest as rhosvd_sketch (which is row0 = 0, accumulate = 0).
+ */
+rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
+                               int32_t ell, uint64_t seed, int32_t tensor_id, int64_t row0, int32_t accumulate,
+                               double* Y, double* norm2, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rh_tall_skinny_r -- the triangle R of the tall-skinny Householder QR B_(mode)^T = Q_B R (the
+ * factor the truncation of Alg. 1 step 4 starts from), for a tensor whose mode ``mode`` is short
+ * (I_mode <= 64): a tree of per-block Householder QRs in B's precision, never the Gram matrix.
+ *   R   device, I_mode x I_mode FP64 column-major, upper triangular (zeros below the diagonal); a
+ *       block of fewer columns than I_mode gives a trapezoid padded with zero rows.
+ *   Triangles of column blocks of one matrix combine by stacking and re-triangularising: the SVD of
+ *   B = [B_1 ... B_S] has the left singular vectors of [R_1^T ... R_S^T] (rh_left_svd of that
+ *   I_mode x S I_mode matrix), which is how the slab-sharded decomposition truncates.
+ */
+size_t rh_tall_skinny_r_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode);
+rh_status rh_tall_skinny_r(int32_t order, const int64_t* dims, int32_t dtype, const void* B, int32_t mode, double* R,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rh_cast_f64 -- dst[i] = src[i] converted to RH_F32 (round to nearest even) or copied (RH_F64), for
+ * i < n: the FP64 factors in the precision of an FP32 tensor's mode products.  Device pointers.
+ */
+rh_status rh_cast_f64(const double* src, int64_t n, int32_t dtype, void* dst, void* stream);
+
+/*
+ * rh_tucker_factor -- Alg. 1 step 5 with the library's column-sign convention: A = Q Ub(:, 1:r)
+ * (I x r FP64), then each column of A flipped so that its largest-magnitude entry (first on ties) is
+ * positive, and Ur = Ub(:, 1:r) (ell x r FP64) with the same flips, so that G <- Ur^T B keeps
+ * A Ur^T B = Q Ub(:, 1:r) Ub(:, 1:r)^T B.  Q: I x ell, Ub: ell x ell, column-major device FP64.
+ */
+rh_status rh_tucker_factor(int64_t I, int32_t ell, int32_t r, const double* Q, const double* Ub, double* A, double* Ur,
+                           void* stream);
+
+/*
  * rhosvd_sketch_static -- rhosvd_sketch for callers that must not allocate device memory.
  *   The paper has no counterpart: this is a deployment variant of the sketch above, with the
  *   same arguments minus the workspace and the same output (up to the order of the FP32/FP64

@@ -106,6 +106,68 @@ def rhosvd_sketch(X, dims, mode, ell, seed=0, tensor_id=0, with_norm=False):
     return (Y, nrm) if with_norm else Y
 
 
+def rhosvd_sketch_offset(X, dims, mode, ell, row0, seed=0, tensor_id=0, with_norm=False, form=None, Y=None,
+                         norm=None):
+    """rhosvd_sketch with Omega rows row0, row0 + 1, ... (a slab of a larger tensor; see the C ABI).
+    ``form="f32_bf16x2"`` runs a first-mode sketch of an FP32 tensor on the tensor cores.  Given
+    ``Y`` (and ``norm``), the sketch (and ||X||^2) is added to them on the device."""
+    torch = _torch()
+    d = len(dims)
+    dt = _FORMS[form] if form is not None else _dtype_code(X)
+    da = i64_array(dims)
+    ws_bytes = lib().rhosvd_sketch_workspace_size(d, da, dt, int(mode), int(ell))
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=X.device)
+    acc = Y is not None
+    if Y is None:
+        Y = torch.empty((ell, int(dims[mode])), dtype=torch.float64, device=X.device)
+    if with_norm and norm is None:
+        norm = torch.zeros(1, dtype=torch.float64, device=X.device)
+    check(lib().rhosvd_sketch_offset(d, da, dt, _ptr(X), int(mode), int(ell), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                     int(tensor_id), int(row0), int(acc), _ptr(Y), _ptr(norm if with_norm else None),
+                                     _ptr(ws), ws_bytes, _stream(X.device)))
+    return (Y, norm) if with_norm else Y
+
+
+def tall_skinny_r(B, dims, mode):
+    """R (I_mode x I_mode FP64, upper) of the tall-skinny QR of B_(mode)^T, as an (n, n) tensor holding
+    the column-major matrix (row c of the tensor = column c of R)."""
+    torch = _check_input(B, dims)
+    d = len(dims)
+    dt = _dtype_code(B)
+    da = i64_array(dims)
+    n = int(dims[mode])
+    ws_bytes = lib().rh_tall_skinny_r_workspace_size(d, da, dt, int(mode))
+    if ws_bytes == 0:
+        raise ValueError("invalid tall-skinny QR request (I_mode must be <= 64)")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=B.device)
+    R = torch.empty((n, n), dtype=torch.float64, device=B.device)
+    check(lib().rh_tall_skinny_r(d, da, dt, _ptr(B), int(mode), _ptr(R), _ptr(ws), ws_bytes, _stream(B.device)))
+    return R
+
+
+def tucker_factor(Q, Ub, r):
+    """A = Q Ub(:, 1:r) with the column-sign convention and Ur = Ub(:, 1:r) flipped alike; Q is the
+    (ell, I) tensor of the I x ell matrix, Ub the (ell, ell) tensor of the ell x ell matrix.  Returns
+    (A as (r, I), Ur as (r, ell))."""
+    torch = _torch()
+    ell, I = (int(v) for v in Q.shape)
+    A = torch.empty((r, I), dtype=torch.float64, device=Q.device)
+    Ur = torch.empty((r, ell), dtype=torch.float64, device=Q.device)
+    check(lib().rh_tucker_factor(I, ell, int(r), _ptr(Q), _ptr(Ub.contiguous()), _ptr(A), _ptr(Ur),
+                                 _stream(Q.device)))
+    return A, Ur
+
+
+def cast_f64(A, dtype):
+    """An FP64 CUDA tensor converted by the library to ``dtype`` (torch.float32 or torch.float64)."""
+    torch = _torch()
+    out = torch.empty(A.shape, dtype=dtype, device=A.device)
+    src = A.contiguous()
+    check(lib().rh_cast_f64(_ptr(src), src.numel(), RH_F64 if dtype == torch.float64 else RH_F32, _ptr(out),
+                            _stream(A.device)))
+    return out
+
+
 def split_bf16x2(X):
     """RH_BF16X2 representation of a flat FP32 CUDA tensor: an int16 tensor of 2 N BF16 bit patterns."""
     torch = _torch()

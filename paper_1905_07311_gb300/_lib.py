@@ -50,6 +50,11 @@ SIGNATURES = {
     "rhosvd_sketch_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _I32]),
     "rhosvd_sketch": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P, _SZ, _P]),
     "rhosvd_sketch_static": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _P, _P, _P]),
+    "rhosvd_sketch_offset": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _U64, _I32, _I64, _I32, _P, _P, _P, _SZ, _P]),
+    "rh_tall_skinny_r_workspace_size": (_SZ, [_I32, _P, _I32, _I32]),
+    "rh_tall_skinny_r": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _SZ, _P]),
+    "rh_tucker_factor": (_I32, [_I64, _I32, _I32, _P, _P, _P, _P, _P]),
+    "rh_cast_f64": (_I32, [_P, _I64, _I32, _P, _P]),
     "rh_mode_product": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P]),
     "rh_mode_product_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _I32]),
     "rh_mode_product_bf16": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),

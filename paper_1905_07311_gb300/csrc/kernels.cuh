@@ -23,7 +23,7 @@ rh_status launch_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_
                         cudaStream_t st);
 template <typename T>
 rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y,
-                               double* norm2, cudaStream_t st, int site = SITE_SKETCH_REDUCE);
+                               double* norm2, cudaStream_t st, int site = SITE_SKETCH_REDUCE, int accumulate = 0);
 // Y = G_(n) W with a dense M x ell operand W stored like a mode product's output, (L, ell, R):
 // element (p, c) at (p % L) + L (c + ell (p / L)) -- the sketch of a subspace-iteration step.
 // split (FP32): every element of G enters as the sum of its exact BF16 head and tail.  Partial
@@ -47,7 +47,7 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
 rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                                uint64_t seed, uint32_t sid, float* part, double* norm_part, int32_t* err,
                                cudaStream_t st, int64_t row0 = 0);
-rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st);
+rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st, int accumulate = 0);
 rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 // ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles
 rh_status launch_pieces_sumsq(const uint16_t* piece0, const uint16_t* piece1, int64_t n, double* part, double* out,
@@ -151,6 +151,9 @@ rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st, int
 // Basis of a subspace-iteration step: B (the (L, ell, R) view of tr, entries T) is replaced by W, an
 // orthonormal basis of range(B^T) stored in the same layout (tall-skinny Householder R, W = B^T R^{-1},
 // one CholeskyQR pass).  ws holds power_workspace_elems(tr) elements of T.
+// R (n x n FP64, upper) of the tall-skinny Householder QR of B^T; ws: trunc_workspace_elems(tr) of T
+template <typename T>
+rh_status launch_tall_skinny_r(const TruncPlan& tr, const T* B, T* ws, double* R, cudaStream_t st);
 template <typename T>
 size_t power_workspace_elems(const TruncPlan& tr);
 template <typename T>

@@ -52,10 +52,11 @@ SketchBufs carve_sketch(Arena& ar, const SketchPlan& pl, int32_t dtype) {
 
 template <typename T>
 rh_status run_sketch(const SketchPlan& pl, const T* G, uint64_t seed, uint32_t sid, const SketchBufs& b, double* Y,
-                     double* norm2, cudaStream_t st) {
+                     double* norm2, cudaStream_t st, int accumulate = 0) {
   rh_status s = launch_sketch<T>(pl, G, seed, sid, static_cast<T*>(b.part), b.part_norm, st);
   if (s != RH_OK) return s;
-  return launch_sketch_reduce<T>(pl, static_cast<const T*>(b.part), b.part_norm, Y, norm2, st);
+  return launch_sketch_reduce<T>(pl, static_cast<const T*>(b.part), b.part_norm, Y, norm2, st, SITE_SKETCH_REDUCE,
+                                 accumulate);
 }
 
 // ---- R-STHOSVD plan ------------------------------------------------------------------
@@ -659,7 +660,16 @@ size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t 
 rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode, int32_t ell,
                         uint64_t seed, int32_t tensor_id, double* Y, double* norm2, void* workspace,
                         size_t workspace_bytes, void* stream) {
+  return rhosvd_sketch_offset(order, dims, dtype, X, mode, ell, seed, tensor_id, 0, 0, Y, norm2, workspace,
+                              workspace_bytes, stream);
+}
+
+rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t mode,
+                               int32_t ell, uint64_t seed, int32_t tensor_id, int64_t row0, int32_t accumulate,
+                               double* Y, double* norm2, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
+  RH_CHECK_ARG(row0 >= 0, "row0 must be >= 0");
+  RH_CHECK_ARG(accumulate == 0 || accumulate == 1, "accumulate must be 0 or 1");
   if (is_bf16_form(dtype)) {
     RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
     for (int k = 0; k < order; ++k) RH_CHECK_ARG(dims[k] >= 1, "every dimension must be >= 1");
@@ -689,18 +699,18 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     rh_status s;
     if (dtype == RH_F32_BF16X2) {
       s = launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part, norm2 ? norm_part : nullptr, err,
-                               st);
-      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st);
+                               st, row0);
+      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st, accumulate);
     } else if (dtype == RH_FP8_E4M3) {
       const Fp8Layout f8 = fp8_layout(order, dims);
       const uint8_t* x8 = static_cast<const uint8_t*>(X);
       s = launch_sketch_tc_fp8(v, ell, x8, reinterpret_cast<const float*>(x8 + f8.scale_off), f8.ld, seed, sid, part,
-                               norm2 ? norm_part : nullptr, err, st);
-      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st);
+                               norm2 ? norm_part : nullptr, err, st, row0);
+      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st, accumulate);
     } else {
       const uint16_t* p0 = static_cast<const uint16_t*>(X);
       const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
-      s = launch_sketch_tc(v, ell, p0, p1, seed, sid, part, err, st);
+      s = launch_sketch_tc(v, ell, p0, p1, seed, sid, part, err, st, row0);
     }
     if (s != RH_OK) return s;
     SketchPlan rp;
@@ -710,7 +720,7 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
     rp.gx = 0;
     rp.S = S;
     rp.chunk = 0;
-    return launch_sketch_reduce<float>(rp, part, nullptr, Y, nullptr, st);
+    return launch_sketch_reduce<float>(rp, part, nullptr, Y, nullptr, st, SITE_SKETCH_REDUCE, accumulate);
   }
   rh_status s = check_tensor(order, dims, dtype);
   if (s != RH_OK) return s;
@@ -718,7 +728,8 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
   RH_CHECK_ARG(ell >= 1 && ell <= RH_MAX_ELL, "ell must be in [1, 64]");
   RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
   RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
-  const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
+  SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
+  pl.row0 = row0;
   Arena ar(workspace);
   Arena meas(nullptr);
   carve_sketch(meas, pl, dtype);
@@ -729,8 +740,9 @@ rh_status rhosvd_sketch(int32_t order, const int64_t* dims, int32_t dtype, const
   const SketchBufs b = carve_sketch(ar, pl, dtype);
   const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)mode;
   cudaStream_t st = (cudaStream_t)stream;
-  if (dtype == RH_F64) return run_sketch<double>(pl, static_cast<const double*>(X), seed, sid, b, Y, norm2, st);
-  return run_sketch<float>(pl, static_cast<const float*>(X), seed, sid, b, Y, norm2, st);
+  if (dtype == RH_F64)
+    return run_sketch<double>(pl, static_cast<const double*>(X), seed, sid, b, Y, norm2, st, accumulate);
+  return run_sketch<float>(pl, static_cast<const float*>(X), seed, sid, b, Y, norm2, st, accumulate);
 }
 
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k) {
@@ -847,6 +859,50 @@ rh_status rh_split_bf16x2(const float* X, int64_t n, uint16_t* out, void* stream
   RH_CHECK_ARG((X != nullptr && out != nullptr) || n == 0, "X and out must be non-NULL");
   if (n == 0) return RH_OK;
   return launch_split_bf16x2(X, n, out, out + n, (cudaStream_t)stream);
+}
+
+size_t rh_tall_skinny_r_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode) {
+  if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || dims[mode] > RH_MAX_ELL) return 0;
+  const TruncPlan tp = plan_trunc(mode_view(order, dims, mode), (int)dims[mode]);
+  return (dtype == RH_F64 ? trunc_workspace_elems<double>(tp) * sizeof(double)
+                          : trunc_workspace_elems<float>(tp) * sizeof(float)) + 256;
+}
+
+rh_status rh_tall_skinny_r(int32_t order, const int64_t* dims, int32_t dtype, const void* B, int32_t mode, double* R,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  rh_status s = check_tensor(order, dims, dtype);
+  if (s != RH_OK) return s;
+  RH_CHECK_ARG(mode >= 0 && mode < order, "mode out of range");
+  RH_CHECK_ARG(dims[mode] <= RH_MAX_ELL, "I_mode must be <= 64");
+  RH_CHECK_ARG(B != nullptr && R != nullptr, "B and R must be non-NULL");
+  const size_t need = rh_tall_skinny_r_workspace_size(order, dims, dtype, mode);
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    return RH_ENOMEM;
+  }
+  const TruncPlan tp = plan_trunc(mode_view(order, dims, mode), (int)dims[mode]);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == RH_F64)
+    return launch_tall_skinny_r<double>(tp, static_cast<const double*>(B), static_cast<double*>(workspace), R, st);
+  return launch_tall_skinny_r<float>(tp, static_cast<const float*>(B), static_cast<float*>(workspace), R, st);
+}
+
+rh_status rh_cast_f64(const double* src, int64_t n, int32_t dtype, void* dst, void* stream) {
+  clear_error();
+  RH_CHECK_ARG(n >= 0 && (n == 0 || (src != nullptr && dst != nullptr)), "src and dst must be non-NULL");
+  RH_CHECK_ARG(dtype == RH_F32 || dtype == RH_F64, "dtype must be RH_F32 or RH_F64");
+  if (n == 0) return RH_OK;
+  if (dtype == RH_F32) return launch_cast<float>(src, static_cast<float*>(dst), n, (cudaStream_t)stream, SITE_OTHER);
+  return launch_cast<double>(src, static_cast<double*>(dst), n, (cudaStream_t)stream, SITE_OTHER);
+}
+
+rh_status rh_tucker_factor(int64_t I, int32_t ell, int32_t r, const double* Q, const double* Ub, double* A, double* Ur,
+                           void* stream) {
+  clear_error();
+  RH_CHECK_ARG(I >= 1 && ell >= 1 && ell <= RH_MAX_ELL && r >= 1 && r <= ell, "need I >= 1, 1 <= r <= ell <= 64");
+  RH_CHECK_ARG(Q != nullptr && Ub != nullptr && A != nullptr && Ur != nullptr, "Q, Ub, A and Ur must be non-NULL");
+  return launch_factor_and_cast<double>(I, ell, r, Q, Ub, A, Ur, (cudaStream_t)stream);
 }
 
 size_t rh_orthonormalize_workspace_size(int64_t m, int32_t n) {

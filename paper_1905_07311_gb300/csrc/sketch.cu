@@ -470,6 +470,7 @@ struct SketchReduceArgs {
   const double* part_norm;
   int nnorm;
   double* norm2;
+  int accumulate;   // 1: add to Y (and *norm2) instead of overwriting them
 };
 
 template <typename T>
@@ -513,7 +514,7 @@ __device__ __forceinline__ void SketchReduceOp<T>::body(const Grid g, const Args
     double t = red[0][lane];
 #pragma unroll
     for (int j = 1; j < kRedWarps; ++j) t += red[j][lane];
-    Y[i + I * c] = t;
+    Y[i + I * c] = args.accumulate ? Y[i + I * c] + t : t;
   }
   if (norm2 != nullptr && g.bx == 0 && g.by == 0) {
     __syncthreads();
@@ -526,7 +527,7 @@ __device__ __forceinline__ void SketchReduceOp<T>::body(const Grid g, const Args
       if (threadIdx.x < h) flat[threadIdx.x] += flat[threadIdx.x + h];
       __syncthreads();
     }
-    if (threadIdx.x == 0) *norm2 = flat[0];
+    if (threadIdx.x == 0) *norm2 = args.accumulate ? *norm2 + flat[0] : flat[0];
   }
 }
 
@@ -637,14 +638,15 @@ rh_status launch_sketch_dense(const SketchPlan& pl, const T* G, const T* W, bool
 
 template <typename T>
 rh_status launch_sketch_reduce(const SketchPlan& pl, const T* part, const double* part_norm, double* Y, double* norm2,
-                               cudaStream_t st, int site) {
+                               cudaStream_t st, int site, int accumulate) {
   if (pl.ell > 65535) {
     set_error("sketch reduce: too many columns");
     return RH_EUNSUPPORTED;
   }
   const dim3 grid((unsigned)ceil_div(pl.v.I, 32), (unsigned)pl.ell);
   return emit<SketchReduceOp<T>>(site, 0, grid, 0, st,
-                                 SketchReduceArgs<T>{part, pl.S, pl.v.I, pl.ell, Y, part_norm, (int)pl.norm_elems(), norm2});
+                                 SketchReduceArgs<T>{part, pl.S, pl.v.I, pl.ell, Y, part_norm, (int)pl.norm_elems(), norm2,
+                                                     accumulate});
 }
 
 template rh_status launch_sketch<float>(const SketchPlan&, const float*, uint64_t, uint32_t, float*, double*,
@@ -652,9 +654,9 @@ template rh_status launch_sketch<float>(const SketchPlan&, const float*, uint64_
 template rh_status launch_sketch<double>(const SketchPlan&, const double*, uint64_t, uint32_t, double*, double*,
                                          cudaStream_t);
 template rh_status launch_sketch_reduce<float>(const SketchPlan&, const float*, const double*, double*, double*,
-                                               cudaStream_t, int);
+                                               cudaStream_t, int, int);
 template rh_status launch_sketch_reduce<double>(const SketchPlan&, const double*, const double*, double*, double*,
-                                                cudaStream_t, int);
+                                                cudaStream_t, int, int);
 template rh_status launch_sketch_dense<float>(const SketchPlan&, const float*, const float*, bool, float*, cudaStream_t,
                                               int);
 template rh_status launch_sketch_dense<double>(const SketchPlan&, const double*, const double*, bool, double*,

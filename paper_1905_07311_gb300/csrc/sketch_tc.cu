@@ -341,11 +341,11 @@ __global__ void pieces_sumsq_kernel(const uint16_t* __restrict__ a, const uint16
   }
 }
 
-__global__ void sum_n_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+__global__ void sum_n_kernel(const double* __restrict__ part, int n, double* __restrict__ out, int accumulate) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double t = 0.0;
     for (int k = 0; k < n; ++k) t += part[k];
-    *out = t;
+    *out = accumulate ? *out + t : t;
   }
 }
 
@@ -533,13 +533,13 @@ rh_status launch_pieces_sumsq(const uint16_t* piece0, const uint16_t* piece1, in
                               cudaStream_t st) {
   pieces_sumsq_kernel<<<1024, 256, 0, st>>>(piece0, piece1, n, part);
   RH_LAUNCH_CHECK();
-  sum_n_kernel<<<1, 32, 0, st>>>(part, 1024, out);
+  sum_n_kernel<<<1, 32, 0, st>>>(part, 1024, out, 0);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
 
-rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st) {
-  sum_n_kernel<<<1, 32, 0, st>>>(part, n, out);
+rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st, int accumulate) {
+  sum_n_kernel<<<1, 32, 0, st>>>(part, n, out, accumulate);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

@@ -2444,6 +2444,44 @@ rh_status launch_power_basis(const TruncPlan& pl0, T* B, T* ws, cudaStream_t st)
   return RH_OK;
 }
 
+// R of the tall-skinny Householder QR of B^T (B: the (L, n, R) view of tr), as an n x n FP64 upper
+// triangle (zeros below the diagonal); ws holds trunc_workspace_elems(tr) elements of T.
+__global__ void triangle_to_f64_kernel(const float* __restrict__ Rf, const double* __restrict__ Rd, int n,
+                                       double* __restrict__ R) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int j = e % n, k = e / n;
+    R[e] = j <= k ? (Rf ? (double)Rf[e] : Rd[e]) : 0.0;
+  }
+}
+
+template <typename T>
+rh_status launch_tall_skinny_r(const TruncPlan& pl0, const T* B, T* ws, double* R, cudaStream_t st) {
+  TruncPlan pl = pl0;
+  trunc_dims<T>(pl);
+  const int n = pl.ell;
+  const int64_t nn = (int64_t)n * n;
+  T* buf0 = ws;
+  T* buf1 = ws + pl.nblk0 * nn;
+  T* fin = nullptr;
+  rh_status s;
+  if constexpr (sizeof(T) == 4) {
+    float* f = nullptr;
+    s = launch_tsqr_rows(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, reinterpret_cast<float*>(buf0),
+                         reinterpret_cast<float*>(buf1), nullptr, &f, st, SITE_OTHER);
+    fin = reinterpret_cast<T*>(f);
+  } else {
+    s = launch_tsqr_tree<T>(pl, B, buf0, buf1, nullptr, &fin, st, SITE_OTHER);
+  }
+  if (s != RH_OK) return s;
+  triangle_to_f64_kernel<<<(unsigned)std::max<int64_t>(1, ceil_div(nn, 256)), 256, 0, st>>>(
+      sizeof(T) == 4 ? reinterpret_cast<const float*>(fin) : nullptr,
+      sizeof(T) == 8 ? reinterpret_cast<const double*>(fin) : nullptr, n, R);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+template rh_status launch_tall_skinny_r<float>(const TruncPlan&, const float*, float*, double*, cudaStream_t);
+template rh_status launch_tall_skinny_r<double>(const TruncPlan&, const double*, double*, double*, cudaStream_t);
+
 // ---- staged truncation (adaptive variants) ----------------------------------------------
 template <typename T>
 rh_status launch_trunc_factor(const TruncPlan& pl0, const T* B, T* ws, bool gram, double* part, double* W, T** R,

@@ -46,13 +46,42 @@ __global__ void iota_kernel(int32_t* __restrict__ a, int64_t n) {
     a[e] = (int32_t)e;
 }
 
-// Row counts of the keys; a key outside [0, I) is counted in cnt[I] (the host turns that into
-// RH_EINVAL before any kernel uses the key as an address).
-__global__ void count_kernel(const int32_t* __restrict__ key, int64_t n, int64_t I, int32_t* __restrict__ cnt) {
+// Keys outside [0, I) are counted in *bad (one atomic per block; the host turns a nonzero count
+// into RH_EINVAL before any kernel uses a key as an address).
+__global__ void __launch_bounds__(256) bad_keys_kernel(const int32_t* __restrict__ key, int64_t n, int64_t I,
+                                                       int32_t* __restrict__ bad) {
+  __shared__ int32_t cnt_s;
+  if (threadIdx.x == 0) cnt_s = 0;
+  __syncthreads();
+  int32_t c = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = key[e];
-    atomicAdd(&cnt[(k >= 0 && k < I) ? (int64_t)k : I], 1);
+    c += (k < 0 || k >= I) ? 1 : 0;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt_s, c);
+  __syncthreads();
+  if (threadIdx.x == 0 && cnt_s) atomicAdd(bad, cnt_s);
+}
+
+// Row runs of the sorted keys: begin[r] and end[r] of row r's run; rows without entries keep their
+// zero fill.  No atomics, so a heavy row (a Zipf index) costs nothing extra.  Keys outside [0, I)
+// are skipped (never used as addresses; bad_keys_kernel reports them).
+__global__ void run_bounds_kernel(const int32_t* __restrict__ ks, int64_t n, int64_t I, int32_t* __restrict__ begin,
+                                  int32_t* __restrict__ end) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = ks[k];
+    if (r < 0 || r >= I) continue;
+    if (k == 0 || ks[k - 1] != r) begin[r] = (int32_t)k;
+    if (k == n - 1 || ks[k + 1] != r) end[r] = (int32_t)(k + 1);
+  }
+}
+
+// cnt[r] = end[r] - begin[r] for r < I (cnt holds the ends on entry)
+__global__ void run_counts_kernel(const int32_t* __restrict__ begin, int64_t I, int32_t* __restrict__ cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x)
+    cnt[r] -= begin[r];
 }
 
 struct SpIdx {
@@ -717,7 +746,13 @@ rh_status sp_sketch_mode(const SpIdx& ix, int order, int n, int64_t I, int64_t M
     ProfileScope ps(PROF_SP_SORT, n, st);
     RH_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.cub_tmp, tb, key, b.keys_out, b.perm_in, b.perm_out,
                                                 (int)cnnz, 0, bits_for(I), st));
-    count_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, I, b.cnt);
+    // row counts from the runs of the sorted keys; keys outside [0, I) counted in cnt[I]
+    bad_keys_kernel<<<grid_for(cnnz), 256, 0, st>>>(key, cnnz, I, b.cnt + I);
+    RH_LAUNCH_CHECK();
+    RH_CUDA_TRY(cudaMemsetAsync(b.pos, 0, sizeof(int32_t) * I, st));
+    run_bounds_kernel<<<grid_for(cnnz), 256, 0, st>>>(b.keys_out, cnnz, I, b.pos, b.cnt);
+    RH_LAUNCH_CHECK();
+    run_counts_kernel<<<grid_for(I), 256, 0, st>>>(b.pos, I, b.cnt);
     RH_LAUNCH_CHECK();
   }
   std::vector<int32_t> cnt(I + 1);
