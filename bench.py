@@ -228,6 +228,8 @@ def run_ours(args):
     from paper_1905_07311_gb300 import _lib
 
     L = _lib.lib()
+    if world > 1:
+        return run_sharded(args, torch, dist, world, rank, local, device, rh, L)
     X = make_input(torch, device, seed_offset=rank)
     tc = args.form == "f32_bf16x2"
     form = "f32_bf16x2" if tc else torch.float32
@@ -387,6 +389,61 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_sharded(args, torch, dist, world, rank, local, device, rh, L):
+    """N > 1: one R-STHOSVD of the global tensor 1024 x 1024 x (1024 N), cut along its last mode into
+    one 1024^3 slab per GPU (this rank's slab is the benchmark construction with seed 2 + rank): the
+    slab partition of Alg. 3 with NCCL all-reduces of the sketches and the last mode's partial
+    products and all-gathers of the tall-skinny triangles and the last mode's row blocks.  Weak
+    scaling: the work per GPU is one 1024^3 slab; value = the global algorithmic flops / the slowest
+    rank's time."""
+    from paper_1905_07311_gb300 import slab
+
+    X = make_input(torch, device, seed_offset=rank)
+    gdims = DIMS[:-1] + [DIMS[-1] * world]
+    k0 = DIMS[-1] * rank
+    slabs = [slab.Slab(k0, k0 + DIMS[-1], X)]
+    comm = slab.TorchComm()
+    be = slab.LibraryBackend(args.form)
+    run = lambda: slab.rsthosvd_slabs(slabs, gdims, RANKS, p=P, seed=SEED, comm=comm, backend=be)   # noqa: E731
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(device)
+    n0 = L.rh_kernel_launches()
+    clocks = Clocks(local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    launches = (L.rh_kernel_launches() - n0) / args.steps
+    flops = algorithmic_flops(gdims, RANKS, P, list(range(len(gdims))))
+    ms_step, value = job_time_and_value(torch, dist, e0.elapsed_time(e1) / args.steps, flops / world, world, device)
+    nx = float(res.norm_x2.item())
+    ng = float((res.core.double() ** 2).sum().item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x2" if args.form == "f32_bf16x2" else "f32",
+                "data": "synthetic (seeded generator, inputs resident in HBM before timing)",
+                "config": {"workload": f"dense 3-way FP32 {gdims[0]}x{gdims[1]}x{gdims[2]} cut into {world} slabs of "
+                                       "1024^3 along the last mode; R-STHOSVD rank (50,50,50), p=10",
+                           "dims": gdims, "ranks": RANKS, "p": P, "seed": SEED,
+                           "parallelism": f"slab partition along the last mode x{world} (NCCL all-reduce / all-gather)",
+                           "l2": "input larger than L2; no flush"},
+                "rel_error_from_norms": max(nx - ng, 0.0) ** 0.5 / nx ** 0.5,
+                "gpu_launches": int(round(launches * args.steps)), "clocks": clk, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line))
+    dist.barrier()
+    dist.destroy_process_group()
 
 
 def traffic_for(kind, tc=False):
@@ -887,6 +944,76 @@ def wl_rhosvd1024(torch, rh, L, args, device, peaks, src):
             "config": {"workload": WORKLOAD.replace("R-STHOSVD", "R-HOSVD")}}
 
 
+def wl_outofcore(torch, rh, L, args, device, peaks, src):
+    """Out-of-core R-STHOSVD: a 1024 x 1024 x 2048 FP32 tensor (8.6 GB, the benchmark's construction)
+    held in pinned host memory and streamed to the device in slabs of 128 last-mode planes (512 MB)
+    -- twice, for the first mode's sketch and its mode product; after the first mode the truncated
+    core (50 x 1024 x 2048) stays on the device.  The first mode runs on the tensor cores (BF16 head +
+    tail split on the fly).  Its roof is the host link: 2 x 8.6 GB / the measured host-to-device copy
+    bandwidth.  The relative error comes from ||X||^2 - ||G||^2 (orthonormal factors, Alg. 3)."""
+    from paper_1905_07311_gb300 import slab
+
+    dims = [1024, 1024, 2048]
+    Xr = lowrank_plus_noise_torch_host(torch, dims, device)      # axes reversed: Xr[i_3, i_2, i_1]
+    bounds = slab.even_slabs(dims[-1], dims[-1] // 128)
+    # a slab X[:, :, k0:k1] is the contiguous block Xr[k0:k1], column-major in (i_1, i_2, i_3 - k0)
+    slabs = [slab.Slab(k0, k1, Xr[k0:k1].reshape(-1).pin_memory(), device=device) for k0, k1 in bounds]
+    del Xr
+    be = slab.LibraryBackend("f32_bf16x2")
+    run = lambda: slab.rsthosvd_slabs(slabs, dims, RANKS, p=P, seed=SEED, backend=be)   # noqa: E731
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(device.index or 0)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    nx = float(res.norm_x2.item())
+    ng = float((res.core.double() ** 2).sum().item())
+    err = max(nx - ng, 0.0) ** 0.5 / nx ** 0.5
+    # host link: one slab's pinned copy, timed alone
+    buf = torch.empty(slabs[0].data.numel(), dtype=torch.float32, device=device)
+    h2d = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        buf.copy_(slabs[0].data, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        h2d.append(slabs[0].data.numel() * 4 / (a.elapsed_time(b) * 1e-3) / 1e9)
+    gbs = max(h2d)
+    nbytes = float(np.prod(dims)) * 4
+    roof_ms = 2 * nbytes / (gbs * 1e9) * 1e3
+    return {"metric": "out-of-core R-STHOSVD time-to-Tucker, 1024x1024x2048 FP32 streamed from host memory",
+            "value": round(ms, 3), "unit": "ms", "higher_is_better": False, "dtype": "bf16x2",
+            "rel_error_from_norms": err, "clocks": clk,
+            "roofline": {"kernel": "whole call (host link)", "bound": "host link", "achieved": round(2 * nbytes / (ms * 1e-3) / 1e9, 1),
+                         "peak": round(gbs, 1), "unit": "GB/s", "frac": round(roof_ms / ms, 4), "traffic": None,
+                         "peak_source": "measured pinned host-to-device copy of one 512 MB slab (best of 5)",
+                         "roof_ms": round(roof_ms, 3)},
+            "config": {"workload": "dense 3-way FP32 1024x1024x2048 (low rank 50^3, decay 0.9, 1e-3 noise) in pinned "
+                                   "host memory, 16 slabs of 1024x1024x128; R-STHOSVD rank (50,50,50), p=10",
+                       "device_resident_x": False}}
+
+
+def lowrank_plus_noise_torch_host(torch, dims, device):
+    """The benchmark construction at ``dims`` (generated on the device), in host memory as the tensor
+    with reversed axes whose C-order buffer is the column-major flat tensor."""
+    from workloads import lowrank_plus_noise_torch
+
+    X = lowrank_plus_noise_torch(dims, [50] * len(dims), 0.9, 1e-3, 2, torch.float32, device)
+    out = X.reshape(list(reversed(dims))).cpu()
+    del X
+    return out
+
+
 def wl_peaks(torch, rh, L, args, device, peaks, src):
     """Rates the rooflines of the non-BF16 paths need, measured on this device: dense matmul in FP64,
     TF32 and FP32 (torch.matmul, 8192^3 for TF32 / FP32, 4096^3 for FP64: 2 n^3 flops, best of the
@@ -947,7 +1074,8 @@ def run_workload(args):
     L = _lib.lib()
     peaks, src = measured_peaks()
     fn = {"hilbert200": wl_hilbert200, "lowp192": wl_lowp192, "batched": wl_batched, "sparse": wl_sparse,
-          "peaks": wl_peaks, "power1024": wl_power1024, "rhosvd1024": wl_rhosvd1024}[args.workload]
+          "peaks": wl_peaks, "power1024": wl_power1024, "rhosvd1024": wl_rhosvd1024,
+          "outofcore": wl_outofcore}[args.workload]
     line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
     line.update(fn(torch, rh, L, args, device, peaks, src))
     print(json.dumps(line))
@@ -971,7 +1099,7 @@ def main():
                     help="smaller cube for profiling captures (default 1024 1024 1024)")
     ap.add_argument("--workload", default="dense1024",
                     choices=["dense1024", "hilbert200", "lowp192", "batched", "sparse", "peaks", "power1024",
-                             "rhosvd1024"],
+                             "rhosvd1024", "outofcore"],
                     help="dense1024: the benchmark line (default); the others measure the further configurations "
                          "and print one JSON line each")
     ap.add_argument("--batch-orders", default="3,4",
