@@ -132,10 +132,45 @@ class Slab:
     def __init__(self, k0, k1, data, device=None):
         self.k0, self.k1, self.data, self.device = int(k0), int(k1), data, device
 
+    def resident(self):
+        return self.device is None or self.data.device == self.device
+
     def get(self):
-        if self.device is None or self.data.device == self.device:
+        if self.resident():
             return self.data
         return self.data.to(self.device, non_blocking=True)
+
+
+def _streamed(slabs, torch):
+    """The slabs' device tensors in order.  Host-resident slabs are copied on a side stream one slab
+    ahead of their use (two slabs in flight at most), so the host-to-device copy of slab s + 1
+    overlaps the kernels of slab s; each copy is ordered before its use by an event."""
+    if all(s.resident() for s in slabs):
+        for s in slabs:
+            yield s.data
+        return
+    cur = torch.cuda.current_stream()
+    side = torch.cuda.Stream(device=cur.device)
+
+    def issue(s):
+        if s.resident():
+            return s.data, None
+        side.wait_stream(cur)          # the slot the copy lands in is free once earlier work is done
+        with torch.cuda.stream(side):
+            t = s.data.to(s.device, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(side)
+        return t, ev
+
+    nxt = issue(slabs[0])
+    for i in range(len(slabs)):
+        t, ev = nxt
+        if i + 1 < len(slabs):
+            nxt = issue(slabs[i + 1])
+        if ev is not None:
+            cur.wait_event(ev)
+            t.record_stream(cur)
+        yield t
 
 
 def _prod(v):
@@ -192,9 +227,9 @@ def rsthosvd_slabs(slabs, dims, ranks, p=5, seed=0, tensor_id=0, comm=None, back
         # Y_n: the slabs' sketches with their global Omega rows, summed on the device, then across ranks
         Y = nrm = None
         if first:
-            for s in slabs:
+            for s, Xs in zip(slabs, _streamed(slabs, torch)):
                 sd = cur[:-1] + [s.k1 - s.k0]
-                Y, nrm = be.sketch(s.get(), sd, 0, ell, L * Rm * s.k0, seed, tensor_id, Y=Y, norm=nrm, first=True)
+                Y, nrm = be.sketch(Xs, sd, 0, ell, L * Rm * s.k0, seed, tensor_id, Y=Y, norm=nrm, first=True)
         else:
             Y, _ = be.sketch(local, ldims, n, ell, L * Rm * k_lo, seed, tensor_id)
         Y = comm.allreduce_sum(Y)
@@ -204,9 +239,9 @@ def rsthosvd_slabs(slabs, dims, ranks, p=5, seed=0, tensor_id=0, comm=None, back
         # B_s = Q^T X_(n),s (local), stacked along the last mode
         if first:
             parts = []
-            for s in slabs:
+            for s, Xs in zip(slabs, _streamed(slabs, torch)):
                 sd = cur[:-1] + [s.k1 - s.k0]
-                Bs, bd = be.mode_product(s.get(), sd, 0, Q, first=True)
+                Bs, bd = be.mode_product(Xs, sd, 0, Q, first=True)
                 parts.append(Bs)
             B = parts[0] if len(parts) == 1 else torch.cat(parts)
             bdims = [ell] + cur[1:-1] + [K]
