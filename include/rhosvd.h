@@ -180,8 +180,10 @@ rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0,
  * rhosvd_sketch -- range-finder sketch Y = X_(mode) Omega_mode (Alg. 1 step 1 applied to an
  * unfolding, as in Alg. 2 step 3 and Alg. 3 step 4).
  *   X       order-``order`` tensor with sizes dims[0..order-1], column-major, dtype RH_F64/RH_F32, or
- *           RH_BF16/RH_BF16X2/RH_F32_BF16X2 for mode 0 (tensor cores; needs I_0 % 8 == 0,
- *           I_0 <= 1024; Omega in BF16).  norm2 is not computed for RH_BF16/RH_BF16X2 and must be
+ *           RH_BF16/RH_BF16X2/RH_F32_BF16X2/RH_FP8_E4M3 for mode 0 (tensor cores; needs I_0 % 8 == 0,
+ *           I_0 <= 1024; Omega in BF16), or RH_F32_BF16X2 for a later mode whose earlier sizes
+ *           multiply to a multiple of 64, I_mode <= 1024 (tensor cores, the FP32 values read through
+ *           the 3-D view (l, i, r) of the mode and split on the fly).  norm2 is not computed for RH_BF16/RH_BF16X2 and must be
  *           NULL; for RH_F32_BF16X2 it is ||head + tail||^2 (FP32 sums over 32 values per thread
  *           and tile, FP64 above).
  *   mode    0-based mode n;  ell  number of columns, 1 <= ell <= RH_MAX_ELL.
@@ -309,6 +311,20 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k);
 rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
                                const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * rh_mode_product_split -- Y = X x_mode A^T on the tensor cores for an FP32 tensor read as
+ * RH_F32_BF16X2 (each value split on the fly into BF16 head and tail, A (I_mode x k FP64, k <= 64)
+ * into two pieces, all four piece products with FP32 accumulation): the mode product of Alg. 1
+ * step 3 for mode 0 (I_0 % 8 == 0) or for a later mode whose earlier sizes multiply to a multiple of
+ * 128 (its unfolding read through the 3-D view (l, i, r)).  Y (FP32) is in the layout of
+ * rh_mode_product: dims with dims[mode] replaced by k, column-major.  Workspace:
+ * rh_mode_product_split_workspace_size; its first int32 receives the wait status as in
+ * rhosvd_sketch.  RH_EUNSUPPORTED for other shapes.
+ */
+size_t rh_mode_product_split_workspace_size(int32_t order, const int64_t* dims, int32_t mode, int32_t k);
+rh_status rh_mode_product_split(int32_t order, const int64_t* dims, const float* X, int32_t mode, int32_t k,
+                                const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * rh_left_svd -- left singular vectors and singular values of the mode-n unfolding B_(n) of a tensor

@@ -249,6 +249,28 @@ def mode_product_bf16(Xb, dims, A, pieces=2):
     return Y
 
 
+def mode_product_split(X, dims, mode, A):
+    """Y = X x_mode A^T on the tensor cores for a flat FP32 tensor X read as RH_F32_BF16X2; A the
+    (k, I_mode) FP64 tensor of the I_mode x k matrix.  Returns (Y flat FP32, out dims)."""
+    torch = _torch()
+    d = len(dims)
+    da = i64_array(dims)
+    k = int(A.shape[0])
+    ws_bytes = lib().rh_mode_product_split_workspace_size(d, da, int(mode), k)
+    if ws_bytes == 0:
+        raise ValueError("invalid split mode product request")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=X.device)
+    out = [int(v) for v in dims]
+    out[mode] = k
+    n = 1
+    for v in out:
+        n *= v
+    Y = torch.empty(n, dtype=torch.float32, device=X.device)
+    check(lib().rh_mode_product_split(d, da, _ptr(X), int(mode), k, _ptr(A.contiguous()), _ptr(Y), _ptr(ws), ws_bytes,
+                                      _stream(X.device)))
+    return Y, out
+
+
 def left_svd(B, dims, mode):
     """(U, sv) of the mode-``mode`` unfolding of B (I_mode <= 64); U as (I, I) holding column-major U."""
     torch = _check_input(B, dims)
@@ -416,11 +438,13 @@ class RhosvdCall(RsthosvdCall):
     ALG = "rhosvd"
 
 
-def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, svd_route=0, power_iters=0):
+def rhosvd(X, dims, ranks, p=5, seed=0, tensor_id=0, clamp=False, truncate=True, svd_route=0, power_iters=0,
+           form=None):
     """R-HOSVD (Alg. 2) of the flat column-major tensor X with sizes ``dims``; ``power_iters`` steps of
-    randomized subspace iteration in every range finder (rh_options.power_iters)."""
-    call = RhosvdCall(dims, X.dtype, ranks, p=p, seed=seed, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
-                      device=X.device, svd_route=svd_route, power_iters=power_iters)
+    randomized subspace iteration in every range finder (rh_options.power_iters); ``form="f32_bf16x2"``
+    runs every mode the tensor-core kernels cover there (FP32 X split on the fly)."""
+    call = RhosvdCall(dims, form or X.dtype, ranks, p=p, seed=seed, tensor_id=tensor_id, clamp=clamp,
+                      truncate=truncate, device=X.device, svd_route=svd_route, power_iters=power_iters)
     return call.run(X)
 
 

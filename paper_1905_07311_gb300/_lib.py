@@ -58,6 +58,8 @@ SIGNATURES = {
     "rh_mode_product": (_I32, [_I32, _P, _I32, _P, _I32, _I32, _P, _I32, _I32, _P, _P]),
     "rh_mode_product_workspace_size": (_SZ, [_I32, _P, _I32, _I32, _I32]),
     "rh_mode_product_bf16": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
+    "rh_mode_product_split_workspace_size": (_SZ, [_I32, _P, _I32, _I32]),
+    "rh_mode_product_split": (_I32, [_I32, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "rh_left_svd_workspace_size": (_SZ, [_I32, _P, _I32, _I32]),
     "rh_left_svd": (_I32, [_I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
     "rh_split_bf16x2": (_I32, [_P, _I64, _P, _P]),

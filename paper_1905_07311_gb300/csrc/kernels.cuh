@@ -47,6 +47,11 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
 rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                                uint64_t seed, uint32_t sid, float* part, double* norm_part, int32_t* err,
                                cudaStream_t st, int64_t row0 = 0);
+// A mode with L > 1 (L % 64 == 0) on the tensor cores: the FP32 tensor read through its 3-D view
+// (l, i, r), split on the fly, K-major pieces (rows i, K = l); same partial sketches as launch_sketch_tc_f32
+bool sketch_tc_strided_supported(const ModeView& v, int ell);
+rh_status launch_sketch_tc_f32s(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
+                                double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
 rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st, int accumulate = 0);
 rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 // ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles
@@ -61,6 +66,10 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
                         uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
                             int32_t* err, cudaStream_t st);
+// a mode with L > 1 (L % 128 == 0): B in the (L, ell, R) layout, qa 128 x ceil8(I) BF16
+bool ttm_tc_strided_supported(const ModeView& v, int ell);
+rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
+                             int32_t* err, cudaStream_t st);
 // G <- U^T B on the tensor cores for a truncated core (Alg. 1 step 6): B ell x M FP32 (layout
 // c + ell p, split on the fly), U ell x ko FP32 (split into two BF16 pieces in qa, 128 x ceil8(ell)),
 // out[co.base(p) + c co.cstride()] FP32 (see CoreOut).  Needs ell % 4 == 0, ell, ko <= 64.
@@ -95,9 +104,12 @@ rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, CoreOu
 // ---- core G = X x_1 A_1^T ... x_d A_d^T (tucker.cu) ----------------------------------------
 // returns the elements of each of the two ping-pong buffers; *fac_elems = sum I_n k_n
 size_t core_chain_elems(int d, const int64_t* dims, const int32_t* ks, size_t* fac_elems);
+// split_tc: FP32 data in the RH_F32_BF16X2 form, the products the tensor-core mode product covers run
+// there (qa: 128 x ceil8(max I_n) BF16 scratch, err: wait status)
 template <typename T>
 rh_status launch_core_ttm(int d, const int64_t* dims, const T* X, const double* const* factors, const int32_t* ks,
-                          double* G, T* fac, T* W0, T* W1, cudaStream_t st);
+                          double* G, T* fac, T* W0, T* W1, cudaStream_t st, bool split_tc = false,
+                          uint16_t* qa = nullptr, int32_t* err = nullptr);
 
 // ---- small dense linear algebra (smallla.cu) --------------------------------------------
 size_t orth_workspace_elems(int64_t m, int n);   // doubles

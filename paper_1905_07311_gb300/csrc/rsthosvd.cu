@@ -235,11 +235,20 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
   return plan_power(o, pl);
 }
 
-// Alg. 2: every mode is sketched on the input tensor itself (no current core).
+// Alg. 2: every mode is sketched on the input tensor itself (no current core).  RH_F32_BF16X2: every
+// mode whose shape the tensor-core kernels cover (mode 0 with I_0 % 8 == 0, I_0 <= 1024; a mode with
+// L % 128 == 0 and I_n <= 1024) runs its sketch and mode product there, the FP32 input split on the
+// fly; the others, and the core chain's products that the tensor-core mode product does not cover,
+// in FP32 on the CUDA cores.
 rh_status make_plan_hosvd(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
                           const rh_options& o, Plan& pl) {
-  rh_status s = check_tensor(order, dims, dtype);
+  const bool split = dtype == RH_F32_BF16X2;
+  rh_status s = check_tensor(order, dims, split ? RH_F32 : dtype);
   if (s != RH_OK) return s;
+  if (split) {
+    dtype = RH_F32;
+    pl.in_form = RH_F32_BF16X2;
+  }
   RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
   RH_CHECK_ARG(o.p >= 0, "oversampling p must be >= 0");
   RH_CHECK_ARG(o.tensor_id >= 0 && o.tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
@@ -283,6 +292,19 @@ rh_status make_plan_hosvd(int32_t order, const int64_t* dims, int32_t dtype, con
   size_t fe = 0;
   pl.max_tensor = std::max(pl.max_tensor, core_chain_elems(order, dims, ks.data(), &fe));
   pl.fac_elems = fe;
+  if (split) {
+    pl.max_pnorm = std::max<size_t>(pl.max_pnorm, 1024);
+    for (Step& st : pl.steps) {
+      const bool k0 = st.v.L == 1 && sketch_tc_supported(st.v, st.ell) && ttm_tc_supported(st.v, st.ell);
+      const bool ks_ = st.v.L > 1 && sketch_tc_strided_supported(st.v, st.ell) &&
+                       ttm_tc_strided_supported(st.v, st.ell);
+      st.tc = k0 || ks_;
+      if (st.tc) pl.tc_part = std::max(pl.tc_part, (size_t)sketch_tc_ctas(st.v) * st.ell * st.v.I);
+    }
+    int64_t imax = 1;
+    for (int n = 0; n < order; ++n) imax = std::max<int64_t>(imax, dims[n]);
+    pl.qa_elems = (size_t)128 * ((imax + 7) / 8 * 8);   // the split Q of any mode or factor of the core chain
+  }
   return plan_power(o, pl);
 }
 
@@ -361,8 +383,9 @@ rh_status run_power(const Plan& pl, const Step& sp, int j, const T* cur, const f
     record_step(kStepStride * j + 1 + it);
     ProfileScope ps(PROF_POWER, j, st);
     if (tc) {
-      if ((s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(Bw), b.err, st)) != RH_OK)
-        return s;
+      s = sp.v.L == 1 ? launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(Bw), b.err, st)
+                      : launch_ttm_tc_f32s(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(Bw), b.err, st);
+      if (s != RH_OK) return s;
     } else {
       if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st, SITE_POWER_CAST)) != RH_OK) return s;
       if ((s = launch_ttm<T, T>(sp.v, cur, static_cast<const T*>(b.Qc), sp.ell, Bw, st, SITE_POWER_TTM)) != RH_OK)
@@ -554,17 +577,37 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
                      double* core, double* norms, int32_t* info, const Bufs& b, cudaStream_t st) {
   rh_status s;
   std::vector<int32_t> ks(pl.d);
+  const bool split = pl.in_form == RH_F32_BF16X2;
+  const float* Xf = reinterpret_cast<const float*>(X);
+  if (split) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
   for (size_t j = 0; j < pl.steps.size(); ++j) {
     const Step& sp = pl.steps[j];
     ks[sp.mode] = sp.ko;
     const uint32_t sid = ((uint32_t)o.tensor_id << 4) | (uint32_t)sp.mode;
     double* n2 = (j == 0) ? (norms ? norms : b.normx) : nullptr;
-    {
-      ProfileScope ps(PROF_SKETCH, (int)j, st);
-      if ((s = launch_sketch<T>(sp.sk, X, o.seed, sid, static_cast<T*>(b.part), b.part_norm, st)) != RH_OK) return s;
+    const bool tc = split && sp.tc;
+    if (tc) {
+      // the sketch of Alg. 2 step 3 on the tensor cores (mode 0 MN-major, other modes K-major pieces)
+      {
+        ProfileScope ps(PROF_SKETCH, (int)j, st);
+        double* np = n2 ? b.part_norm : nullptr;
+        s = sp.v.L == 1 ? launch_sketch_tc_f32(sp.v, sp.ell, Xf, o.seed, sid, b.tc_part, np, b.err, st)
+                        : launch_sketch_tc_f32s(sp.v, sp.ell, Xf, o.seed, sid, b.tc_part, np, b.err, st);
+        if (s != RH_OK) return s;
+      }
+      SketchPlan rp = sp.sk;
+      rp.S = sketch_tc_ctas(sp.v);
+      if ((s = launch_sketch_reduce<float>(rp, b.tc_part, nullptr, b.Y, nullptr, st)) != RH_OK) return s;
+      if (n2 && (s = launch_sum_n(b.part_norm, rp.S, n2, st)) != RH_OK) return s;
+    } else {
+      {
+        ProfileScope ps(PROF_SKETCH, (int)j, st);
+        if ((s = launch_sketch<T>(sp.sk, X, o.seed, sid, static_cast<T*>(b.part), b.part_norm, st)) != RH_OK)
+          return s;
+      }
+      if ((s = launch_sketch_reduce<T>(sp.sk, static_cast<const T*>(b.part), b.part_norm, b.Y, n2, st)) != RH_OK)
+        return s;
     }
-    if ((s = launch_sketch_reduce<T>(sp.sk, static_cast<const T*>(b.part), b.part_norm, b.Y, n2, st)) != RH_OK)
-      return s;
     {
       ProfileScope ps(PROF_ORTH, (int)j, st);
       if ((s = launch_orthonormalize(sp.v.I, sp.ell, b.Y, b.Q, info ? info + sp.mode : nullptr, b.orth, st,
@@ -573,15 +616,23 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
         return s;
     }
     T* B = static_cast<T*>(b.W[0]);
-    if (pl.power && (s = run_power<T>(pl, sp, (int)j, X, nullptr, false, b, B, info, st)) != RH_OK) return s;
+    if (pl.power && (s = run_power<T>(pl, sp, (int)j, X, Xf, tc, b, B, info, st)) != RH_OK) return s;
     if (!o.truncate) {
       RH_CUDA_TRY(cudaMemcpyAsync(factors[sp.mode], b.Q, sizeof(double) * sp.v.I * sp.ell, cudaMemcpyDeviceToDevice, st));
+      if (info && tc && (s = set_info_bits(info + sp.mode, 4, st, b.err)) != RH_OK) return s;
       continue;
     }
     if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
     {
       ProfileScope ps(PROF_TTM, (int)j, st);
-      if ((s = launch_ttm<T, T>(sp.v, X, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) return s;
+      if (tc) {
+        float* Bf = reinterpret_cast<float*>(B);
+        s = sp.v.L == 1 ? launch_ttm_tc_f32(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st)
+                        : launch_ttm_tc_f32s(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st);
+        if (s != RH_OK) return s;
+      } else if ((s = launch_ttm<T, T>(sp.v, X, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) {
+        return s;
+      }
     }
     {
       ProfileScope ps(PROF_TRUNC, (int)j, st);
@@ -591,13 +642,16 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
     if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
                                        st)) != RH_OK)
       return s;
+    // info bit 4: this mode's sketch and mode product ran on the tensor cores; 16: a wait gave up
+    if (info && tc && (s = set_info_bits(info + sp.mode, 4, st, b.err)) != RH_OK) return s;
   }
   {
     ProfileScope ps(PROF_TTM_CORE, 0, st);
     if ((s = launch_core_ttm<T>(pl.d, dims, X, factors, ks.data(), core, static_cast<T*>(b.fac),
-                                static_cast<T*>(b.W[0]), static_cast<T*>(b.W[1]), st)) != RH_OK)
+                                static_cast<T*>(b.W[0]), static_cast<T*>(b.W[1]), st, split, b.qa, b.err)) != RH_OK)
       return s;
   }
+  if (split && info && (s = set_info_bits(info + pl.steps.back().mode, 0, st, b.err)) != RH_OK) return s;
   if (norms) {
     int64_t ncore = 1;
     for (int k = 0; k < pl.d; ++k) ncore *= ks[k];
@@ -621,8 +675,8 @@ extern "C" {
 
 static bool is_bf16_form(int32_t dtype) { return bf16_form(dtype); }
 
-static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell) {
-  const ModeView v = mode_view(order, dims, 0);
+static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell, int32_t mode = 0) {
+  const ModeView v = mode_view(order, dims, mode);
   Arena ar(nullptr);
   ar.take<int32_t>(4);   // wait status, first (documented)
   ar.take<float>((size_t)sketch_tc_ctas(v) * ell * v.I);
@@ -645,10 +699,13 @@ rh_status rh_fp8_layout(int32_t order, const int64_t* dims, int64_t* ld, size_t*
 
 size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t ell) {
   if (is_bf16_form(dtype)) {
-    if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode != 0 || ell < 1 || ell > RH_MAX_ELL) return 0;
+    if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode < 0 || mode >= order || ell < 1 ||
+        ell > RH_MAX_ELL)
+      return 0;
+    if (mode != 0 && dtype != RH_F32_BF16X2) return 0;
     for (int k = 0; k < order; ++k)
       if (dims[k] < 1) return 0;
-    return sketch_tc_ws(order, dims, ell);
+    return sketch_tc_ws(order, dims, ell, mode);
   }
   if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || ell < 1 || ell > RH_MAX_ELL) return 0;
   const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
@@ -673,17 +730,20 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
   if (is_bf16_form(dtype)) {
     RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
     for (int k = 0; k < order; ++k) RH_CHECK_ARG(dims[k] >= 1, "every dimension must be >= 1");
-    RH_CHECK_ARG(mode == 0, "the BF16 forms sketch mode 0 only");
+    RH_CHECK_ARG(mode >= 0 && mode < order, "mode out of range");
+    RH_CHECK_ARG(mode == 0 || dtype == RH_F32_BF16X2, "the BF16 and E4M3 forms sketch mode 0 only");
     RH_CHECK_ARG(ell >= 1 && ell <= RH_MAX_ELL, "ell must be in [1, 64]");
     RH_CHECK_ARG(tensor_id >= 0 && tensor_id < (1 << 28), "tensor_id must be in [0, 2^28)");
     RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
     RH_CHECK_ARG(norm2 == nullptr || converted_form(dtype), "norm2 is not available for RH_BF16 / RH_BF16X2");
-    const ModeView v = mode_view(order, dims, 0);
-    if (!sketch_tc_supported(v, ell)) {
-      set_error("unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024");
+    const ModeView v = mode_view(order, dims, mode);
+    if (mode == 0 ? !sketch_tc_supported(v, ell) : !sketch_tc_strided_supported(v, ell)) {
+      set_error(mode == 0 ? "unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024"
+                          : "unsupported: a split sketch of a later mode needs the product of the earlier sizes to "
+                            "be a multiple of 64 and I_n <= 1024");
       return RH_EUNSUPPORTED;
     }
-    const size_t need = sketch_tc_ws(order, dims, ell);
+    const size_t need = sketch_tc_ws(order, dims, ell, mode);
     if (workspace == nullptr || workspace_bytes < need) {
       set_error("workspace too small: need " + std::to_string(need) + " bytes");
       return RH_ENOMEM;
@@ -695,11 +755,13 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
     double* norm_part = ar.take<double>((size_t)S);
     cudaStream_t st = (cudaStream_t)stream;
     RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
-    const uint32_t sid = ((uint32_t)tensor_id << 4);
+    const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)mode;
     rh_status s;
     if (dtype == RH_F32_BF16X2) {
-      s = launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part, norm2 ? norm_part : nullptr, err,
-                               st, row0);
+      s = mode == 0 ? launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part,
+                                           norm2 ? norm_part : nullptr, err, st, row0)
+                    : launch_sketch_tc_f32s(v, ell, static_cast<const float*>(X), seed, sid, part,
+                                            norm2 ? norm_part : nullptr, err, st, row0);
       if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st, accumulate);
     } else if (dtype == RH_FP8_E4M3) {
       const Fp8Layout f8 = fp8_layout(order, dims);
@@ -821,6 +883,44 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
   const uint16_t* p0 = static_cast<const uint16_t*>(X);
   const uint16_t* p1 = dtype == RH_BF16X2 ? p0 + v.I * v.M() : nullptr;
   return launch_ttm_tc(v, k, p0, p1, A, qa, Y, err, st);
+}
+
+size_t rh_mode_product_split_workspace_size(int32_t order, const int64_t* dims, int32_t mode, int32_t k) {
+  if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode < 0 || mode >= order || k < 1 || k > 64) return 0;
+  for (int q = 0; q < order; ++q)
+    if (dims[q] < 1) return 0;
+  Arena ar(nullptr);
+  ar.take<int32_t>(4);   // wait status, first (documented)
+  ar.take<uint16_t>((size_t)128 * ((dims[mode] + 7) / 8 * 8));
+  return ar.used;
+}
+
+rh_status rh_mode_product_split(int32_t order, const int64_t* dims, const float* X, int32_t mode, int32_t k,
+                                const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
+  for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
+  RH_CHECK_ARG(mode >= 0 && mode < order, "mode out of range");
+  RH_CHECK_ARG(k >= 1 && k <= 64, "k must be in [1, 64]");
+  RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
+  const ModeView v = mode_view(order, dims, mode);
+  const bool ok = mode == 0 ? ttm_tc_supported(v, k) : ttm_tc_strided_supported(v, k);
+  if (!ok) {
+    set_error("unsupported: the split mode product needs I_0 % 8 == 0 (mode 0) or the product of the earlier "
+              "sizes to be a multiple of 128 (later modes)");
+    return RH_EUNSUPPORTED;
+  }
+  const size_t need = rh_mode_product_split_workspace_size(order, dims, mode, k);
+  if (workspace == nullptr || workspace_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes");
+    return RH_ENOMEM;
+  }
+  Arena ar(workspace);
+  int32_t* err = ar.take<int32_t>(4);
+  uint16_t* qa = ar.take<uint16_t>((size_t)128 * ((dims[mode] + 7) / 8 * 8));
+  cudaStream_t st = (cudaStream_t)stream;
+  RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  return mode == 0 ? launch_ttm_tc_f32(v, k, X, A, qa, Y, err, st) : launch_ttm_tc_f32s(v, k, X, A, qa, Y, err, st);
 }
 
 size_t rh_left_svd_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode) {
@@ -1003,7 +1103,7 @@ rh_status rhosvd(int32_t order, const int64_t* dims, int32_t dtype, const void* 
   const Bufs b = carve(ar, pl);
   cudaStream_t st = (cudaStream_t)stream;
   if (info) RH_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * order, st));
-  if (dtype == RH_F64)
+  if (pl.dtype == RH_F64)
     return run_rhosvd<double>(pl, dims, static_cast<const double*>(X), o, factors, core, norms, info, b, st);
   return run_rhosvd<float>(pl, dims, static_cast<const float*>(X), o, factors, core, norms, info, b, st);
 }

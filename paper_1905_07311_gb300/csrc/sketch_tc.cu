@@ -47,8 +47,9 @@ template <int IN>
 struct SketchCfg {
   static constexpr bool kConvIn = IN != tc::kInPieces;
   static constexpr int kPStages = kConvIn ? 2 : 4;
-  static constexpr int kF32Stages = IN == tc::kInF32 ? 3 : (IN == tc::kInFp8 ? 12 : 1);
-  static constexpr uint32_t kStageBytes = IN == tc::kInF32 ? kF32Tile : (IN == tc::kInFp8 ? kFp8Tile : 1024);
+  static constexpr bool kF32Like = IN == tc::kInF32 || IN == tc::kInF32S;
+  static constexpr int kF32Stages = kF32Like ? 3 : (IN == tc::kInFp8 ? 12 : 1);
+  static constexpr uint32_t kStageBytes = kF32Like ? kF32Tile : (IN == tc::kInFp8 ? kFp8Tile : 1024);
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
   static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
 };
@@ -71,7 +72,10 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int col) {
 }
 
 // IN = kInPieces: map0 / map1 are the BF16 pieces (box 64 x 64).  IN = kInF32: map0 is the FP32
-// tensor (one unswizzled 128 x 64 box), split on the fly.  IN = kInFp8: map0 is the E4M3 tensor
+// tensor (one unswizzled 128 x 64 box), split on the fly.  IN = kInF32S: a mode with L > 1 (L a
+// multiple of 64): map0 is the 3-D view (l, i, r) of the FP32 tensor, each chunk one box of 64 l x
+// 128 i at one r (chunk c covers Kolda columns 64 c .. 64 c + 63, all inside one r block), split on
+// the fly into K-major pieces (rows i, K = l).  IN = kInFp8: map0 is the E4M3 tensor
 // (box 128 x 64 bytes, leading dimension ld), dequantized with ``scales`` and rounded to one BF16
 // piece on the fly (npieces = 1).  With converted
 // input, norm_part[blockIdx.x] receives this CTA's sum of squares of the split values (head + tail).
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
                      int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
                      uint32_t sid, float* __restrict__ part, double* __restrict__ norm_part,
                      int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld, int probe,
-                     int64_t row0) {
+                     int64_t row0, int64_t L) {
   using Cfg = SketchCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -142,6 +146,10 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
             if constexpr (IN == tc::kInFp8) {
               tc::mbar_arrive_expect_tx(&S.f32full[s], kFp8Tile);
               tc::tma_load_2d(&S.xf[s][0], &map0, m * kRowsTile, p0, &S.f32full[s]);
+            } else if constexpr (IN == tc::kInF32S) {
+              tc::mbar_arrive_expect_tx(&S.f32full[s], kF32Tile);
+              tc::tma_load_3d(&S.xf[s][0], &map0, (int32_t)(((int64_t)p0) % L), m * kRowsTile,
+                              (int32_t)(((int64_t)p0) / L), &S.f32full[s]);   // 64 l x 128 i at one r
             } else {
               tc::mbar_arrive_expect_tx(&S.f32full[s], kF32Tile);
               tc::tma_load_2d(&S.xf[s][0], &map0, m * kRowsTile, p0, &S.f32full[s]);   // 128 x 64, unswizzled
@@ -162,7 +170,8 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0 && c_begin < c_end) {
-      constexpr uint32_t idesc = tc::idesc_bf16(128, 64, /*A MN-major*/ 1, /*B K-major*/ 0);
+      // A (the X pieces) MN-major, or K-major for a strided mode; B (Omega) K-major
+      constexpr uint32_t idesc = tc::idesc_bf16(128, 64, IN == tc::kInF32S ? 0 : 1, 0);
       uint32_t it = 0, oc = 0;
       bool first = true;
       for (int64_t c = c_begin; c < c_end; c += c_step, ++oc) {
@@ -178,7 +187,9 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
           for (int kk = 0; kk < kPChunk / 16; ++kk) {
             const uint64_t bdesc = tc::sdesc_sw128(om_addr + kk * 32, 16, 1024);
             for (int pc = 0; pc < npieces; ++pc) {
-              const uint64_t adesc = tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 2048, 8192, 1024);
+              const uint64_t adesc = IN == tc::kInF32S
+                                         ? tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 32, 16, 1024)
+                                         : tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 2048, 8192, 1024);
               tc::mma_bf16(d, adesc, bdesc, idesc, (first && kk == 0 && pc == 0) ? 0u : 1u);
             }
           }
@@ -255,6 +266,8 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
         if constexpr (IN == tc::kInFp8)
           acc += (double)tc::convert_fp8_tile<128, 64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], nullptr, t, scales,
                                                                    ld, (int64_t)m * kRowsTile, c * kPChunk, I, M);
+        else if constexpr (IN == tc::kInF32S)
+          acc += (double)tc::convert_tile_kmajor<Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         else
           acc += (double)tc::convert_tile_plain<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         tc::fence_proxy_async_smem();
@@ -442,6 +455,56 @@ rh_status make_u8_map_2d(CUtensorMap* map, const void* base, int64_t rows, int64
   return RH_OK;
 }
 
+// 3-D tensor map over an FP32 tensor viewed as (L, I, R) (l fastest), box 64 l x 128 i x 1 r, no
+// swizzle, zero fill outside; needs L % 4 == 0 (16-byte strides).
+rh_status make_map_3d_f32(CUtensorMap* map, const void* base, int64_t L, int64_t I, int64_t R, int box0, int box1) {
+  EncodeTiledFn enc;
+  rh_status s = get_encoder(&enc);
+  if (s != RH_OK) return s;
+  const cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)I, (cuuint64_t)R};
+  const cuuint64_t strides[2] = {(cuuint64_t)L * 4, (cuuint64_t)L * (cuuint64_t)I * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (3-D) failed with code " + std::to_string((int)r));
+    return RH_ECUDA;
+  }
+  return RH_OK;
+}
+
+// A mode with L > 1 on the tensor cores: L a multiple of 64 (every 64-column chunk inside one r
+// block; 16-byte strides), at most 1024 rows, ell <= 64.
+bool sketch_tc_strided_supported(const ModeView& v, int ell) {
+  return v.L > 1 && v.L % 64 == 0 && v.I >= 1 && v.I <= (int64_t)kRowsTile * kMaxTiles && ell >= 1 && ell <= 64 &&
+         v.M() < (int64_t(1) << 31) && v.R < (int64_t(1) << 31);
+}
+
+rh_status launch_sketch_tc_f32s(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
+                                double* norm_part, int32_t* err, cudaStream_t st, int64_t row0) {
+  if (!sketch_tc_strided_supported(v, ell)) {
+    set_error("tensor-core sketch: unsupported strided shape (needs L % 64 == 0, I <= 1024, ell <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  CUtensorMap m0;
+  rh_status s = make_map_3d_f32(&m0, X, v.L, v.I, v.R, 64, kRowsTile);
+  if (s != RH_OK) return s;
+  const int ctas = sketch_tc_ctas(v);
+  const int64_t nchunks = ceil_div(v.M(), kPChunk);
+  const int64_t cpc = ceil_div(nchunks, ctas);
+  const int mtiles = (int)ceil_div(v.I, kRowsTile);
+  constexpr int IN = tc::kInF32S;
+  const size_t smem = sizeof(SketchSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
+      m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
+      norm_part, err, nullptr, 0, tc_probe_next(), row0, v.L);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
 bool sketch_tc_supported(const ModeView& v, int ell) {
   return v.L == 1 && v.I % 8 == 0 && v.I <= (int64_t)kRowsTile * kMaxTiles && ell >= 1 && ell <= 64 &&
          v.M() < (int64_t(1) << 31);
@@ -476,7 +539,7 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m1, np, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      nullptr, err, nullptr, 0, tc_probe_next(), row0);
+      nullptr, err, nullptr, 0, tc_probe_next(), row0, 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -499,7 +562,7 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, nullptr, 0, tc_probe_next(), row0);
+      norm_part, err, nullptr, 0, tc_probe_next(), row0, 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -524,7 +587,7 @@ rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, con
   RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
       m0, m0, 1, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, scales, ld, tc_probe_next(), row0);
+      norm_part, err, scales, ld, tc_probe_next(), row0, 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }

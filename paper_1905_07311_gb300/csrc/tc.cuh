@@ -71,6 +71,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1, int32_t c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -236,8 +243,47 @@ __device__ __forceinline__ float convert_tile_plain(const uint8_t* __restrict__ 
 }
 
 // Input kinds of the tensor-core sketch and mode product: BF16 pieces loaded by TMA as they are,
-// FP32 values or E4M3 bytes (with per-128-element scales) converted in shared memory.
-constexpr int kInPieces = 0, kInF32 = 1, kInFp8 = 2;
+// FP32 values or E4M3 bytes (with per-128-element scales) converted in shared memory; kInF32S, FP32
+// values of a mode with L > 1 (its unfolding's rows strided by L, the L-index contiguous), read by
+// 3-D boxes over (l, i, r) and converted like kInF32.
+constexpr int kInPieces = 0, kInF32 = 1, kInFp8 = 2, kInF32S = 3;
+
+// As convert_tile, for a 128-row x 64-value FP32 tile staged unswizzled with the 64 values of a row
+// consecutive (value (row, k) at byte 256 row + 4 k: a 3-D box of 64 l x 128 i): head and tail as
+// 128 rows of 64 values in the K-major 128-byte-swizzled layout (value (row, k) at
+// (row / 8) 1024 + (row % 8) 128 + ((k / 8) ^ (row % 8)) 16 + 2 (k % 8)).  A warp reads two 256-byte
+// rows and writes two 128-byte output rows.
+template <int kThreadsConv>
+__device__ __forceinline__ float convert_tile_kmajor(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
+                                                     uint8_t* __restrict__ lo, int t) {
+  constexpr int kUnits = 2048 / kThreadsConv;
+  float4 v[kUnits];
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {
+    const int u = j * kThreadsConv + t;
+    v[j] = *reinterpret_cast<const float4*>(f32 + (u >> 4) * 256 + (u & 15) * 16);
+  }
+  float ss = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kUnits; ++j) {
+    const int u = j * kThreadsConv + t;
+    const int row = u >> 4, q = u & 15;
+    const uint32_t h01 = pack_bf16x2(v[j].x, v[j].y), h23 = pack_bf16x2(v[j].z, v[j].w);
+    const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
+    const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
+    const uint32_t t01 = pack_bf16x2(v[j].x - f0, v[j].y - f1), t23 = pack_bf16x2(v[j].z - f2, v[j].w - f3);
+    const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
+    const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
+    ss = fmaf(g0, g0, ss);
+    ss = fmaf(g1, g1, ss);
+    ss = fmaf(g2, g2, ss);
+    ss = fmaf(g3, g3, ss);
+    const int off = (row >> 3) * 1024 + (row & 7) * 128 + (((q >> 1) ^ (row & 7)) << 4) + (q & 1) * 8;
+    *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
+    *reinterpret_cast<uint2*>(lo + off) = make_uint2(t01, t23);
+  }
+  return ss;
+}
 
 // Value of an E4M3 byte (OCP FP8: 1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no
 // infinities, S.1111.111 = NaN) as an FP32 number, exactly: a normal code has value

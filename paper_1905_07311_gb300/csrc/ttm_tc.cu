@@ -48,8 +48,9 @@ template <int IN>
 struct TtmCfg {
   static constexpr bool kConvIn = IN != tc::kInPieces;
   static constexpr int kPStages = kConvIn ? 2 : 3;
-  static constexpr int kF32Stages = IN == tc::kInF32 ? 3 : (IN == tc::kInFp8 ? 8 : 1);
-  static constexpr uint32_t kStageBytes = IN == tc::kInF32 ? 2 * kF32Box : (IN == tc::kInFp8 ? kFp8Box : 1024);
+  static constexpr bool kF32Like = IN == tc::kInF32 || IN == tc::kInF32S;
+  static constexpr int kF32Stages = kF32Like ? 3 : (IN == tc::kInFp8 ? 8 : 1);
+  static constexpr uint32_t kStageBytes = kF32Like ? 2 * kF32Box : (IN == tc::kInFp8 ? kFp8Box : 1024);
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
   static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
 };
@@ -71,14 +72,17 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 }
 
 // IN = kInPieces: mapX0 / mapX1 are the BF16 pieces (box 64 x 128).  IN = kInF32: mapX0 is the
-// FP32 tensor (box 32 x 128), split on the fly into the same two pieces.  IN = kInFp8: mapX0 is
+// FP32 tensor (box 32 x 128), split on the fly into the same two pieces.  IN = kInF32S: a mode with
+// L > 1 (L a multiple of 128): mapX0 is the 3-D view (l, i, r), each stage one box of 128 l x 64 i at
+// one r, split into MN-major pieces (K = i, N = l), B written through ``co`` in the (L, ell, R)
+// layout of the mode product.  IN = kInFp8: mapX0 is
 // the E4M3 tensor (box 64 x 128 bytes, leading dimension ld), dequantized with ``scales`` and split.
 template <int IN>
 __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
                   float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld,
-                  CoreOut co, int probe) {
+                  CoreOut co, int probe, int64_t L) {
   using Cfg = TtmCfg<IN>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -143,6 +147,10 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
             if constexpr (IN == tc::kInFp8) {
               tc::mbar_arrive_expect_tx(&S.f32full[s], kFp8Box);
               tc::tma_load_2d(&S.xf[s][0], &mapX0, ks * kKStage, p0, &S.f32full[s]);
+            } else if constexpr (IN == tc::kInF32S) {
+              tc::mbar_arrive_expect_tx(&S.f32full[s], 2 * kF32Box);
+              tc::tma_load_3d(&S.xf[s][0], &mapX0, (int32_t)((int64_t)p0 % L), ks * kKStage,
+                              (int32_t)((int64_t)p0 / L), &S.f32full[s]);   // 128 l x 64 i at one r
             } else {
               tc::mbar_arrive_expect_tx(&S.f32full[s], 2 * kF32Box);
               tc::tma_load_2d(&S.xf[s][0], &mapX0, ks * kKStage, p0, &S.f32full[s]);
@@ -164,7 +172,8 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16(128, kNTile, 0, 0);
+      // A = [Q_h^T; Q_t^T] K-major; B (the X pieces) K-major, or MN-major for a strided mode
+      constexpr uint32_t idesc = tc::idesc_bf16(128, kNTile, 0, IN == tc::kInF32S ? 1 : 0);
       uint32_t it = 0, tl = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
@@ -184,7 +193,9 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
           for (int kk = 0; kk < kKStage / 16; ++kk) {
             const uint64_t adesc = tc::sdesc_sw128(a_addr + kk * 32, 16, 1024);
             for (int pc = 0; pc < npieces; ++pc) {
-              const uint64_t bdesc = tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 32, 16, 1024);
+              const uint64_t bdesc = IN == tc::kInF32S
+                                         ? tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 2048, 8192, 1024)
+                                         : tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 32, 16, 1024);
               tc::mma_bf16(d, adesc, bdesc, idesc, (ks == 0 && kk == 0 && pc == 0) ? 0u : 1u);
             }
           }
@@ -280,6 +291,8 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
         if constexpr (IN == tc::kInFp8)
           (void)tc::convert_fp8_tile<64, 128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], nullptr, t, scales, ld,
                                                           (int64_t)ks * kKStage, tt * kNTile, I, M);
+        else if constexpr (IN == tc::kInF32S)
+          (void)tc::convert_tile_plain<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         else
           (void)tc::convert_tile<128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
         tc::fence_proxy_async_smem();
@@ -348,7 +361,7 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{}, tc_probe_next());
+                                                                         nullptr, 0, CoreOut{}, tc_probe_next(), 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -373,7 +386,42 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{}, tc_probe_next());
+                                                                         nullptr, 0, CoreOut{}, tc_probe_next(), 1);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
+rh_status make_map_3d_f32(CUtensorMap* map, const void* base, int64_t L, int64_t I, int64_t R, int box0, int box1);
+
+// A mode with L > 1 on the tensor cores: L a multiple of 128 (every 128-column tile inside one r
+// block), ell <= 64, B in the (L, ell, R) layout of the mode product.
+bool ttm_tc_strided_supported(const ModeView& v, int ell) {
+  return v.L > 1 && v.L % 128 == 0 && v.I >= 1 && ell >= 1 && ell <= 64 && v.M() < (int64_t(1) << 31) &&
+         v.R < (int64_t(1) << 31);
+}
+
+rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
+                             int32_t* err, cudaStream_t st) {
+  if (!ttm_tc_strided_supported(v, ell)) {
+    set_error("tensor-core mode product: unsupported strided shape (needs L % 128 == 0, ell <= 64)");
+    return RH_EUNSUPPORTED;
+  }
+  const int64_t ldA = (v.I + 7) / 8 * 8;
+  {
+    const int64_t total = 128 * ldA;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 2 * num_sms()));
+    q_pieces_kernel<double><<<blocks, 256, 0, st>>>(Q, v.I, ell, ldA, qa);
+    RH_LAUNCH_CHECK();
+  }
+  CUtensorMap mA, m0;
+  rh_status s = make_bf16_map_2d(&mA, qa, ldA, 128, 128);
+  if (s != RH_OK) return s;
+  if ((s = make_map_3d_f32(&m0, X, v.L, v.I, v.R, kNTile, kKStage)) != RH_OK) return s;
+  constexpr int IN = tc::kInF32S;
+  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(
+      mA, m0, m0, 2, v.I, v.M(), ell, B, err, nullptr, 0, CoreOut::make(1, v.L, 1, v.M()), tc_probe_next(), v.L);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -403,7 +451,7 @@ rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, Cor
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err, nullptr,
-                                                                         0, co, tc_probe_next());
+                                                                         0, co, tc_probe_next(), 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
@@ -429,7 +477,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 1, v.I, v.M(), ell, B, err,
-                                                                         scales, ld, CoreOut{}, tc_probe_next());
+                                                                         scales, ld, CoreOut{}, tc_probe_next(), 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
