@@ -186,7 +186,7 @@ def _fold_rev(torch, Mt, perm, shape_rev):
     return tmp.permute(inv).contiguous()
 
 
-def fp64_gpu_rsthosvd(torch, rh, X64, dims, ranks, p, seed, rho):
+def fp64_gpu_rsthosvd(torch, rh, X64, dims, ranks, p, seed, rho, tensor_id=0, clamp=False):
     """Alg. 3 in plain PyTorch FP64 on the device (matmul, linalg.qr, linalg.svd);
     Omega columns from the library's stream, so both runs use the same test matrices."""
     d = len(dims)
@@ -196,11 +196,13 @@ def fp64_gpu_rsthosvd(torch, rh, X64, dims, ranks, p, seed, rho):
         Gm, perm = _unfold_rev(torch, G, n)
         I, M = Gm.shape
         ell = ranks[n] + p
-        Om = rh.omega(seed, 0, n, 0, M, ell).double().T      # M x ell
+        if clamp:
+            ell = min(ell, I, M)
+        Om = rh.omega(seed, tensor_id, n, 0, M, ell).double().T      # M x ell
         Q, _ = torch.linalg.qr(Gm @ Om)
         B = Q.T @ Gm
         Ub, s, Vt = torch.linalg.svd(B, full_matrices=False)
-        r = ranks[n]
+        r = min(ranks[n], ell)
         factors[n] = Q @ Ub[:, :r]
         shape_rev = list(G.shape)
         shape_rev[d - 1 - n] = r
@@ -690,25 +692,19 @@ def wl_lowp192(torch, rh, L, args, device, peaks, src):
             "forms": forms, "adaptive_bf16": adapt, "roofline": roof, "cpu_baseline": cpu}
 
 
-def wl_batched(torch, rh, L, args, device, peaks, src):
-    """The batched workload's order-3 and order-4 tensors (339 of 512, 8.0 GB FP32).  Grouped engine
-    (--streams 0): a batched plan (each tensor's launches recorded once, one grouped launch per stage)
-    whose run is captured in a CUDA graph and replayed; stream engine (--streams N): one
-    rsthosvd_batched call captured and replayed."""
-    from workloads import batch_recipe, lowrank_plus_noise_torch
+def _batch_errors(torch, Ts, X64s):
+    """Relative Tucker error ||X - G x_1 A_1 ... x_d A_d|| / ||X|| of every tensor (FP64 on the device)."""
+    out = []
+    for T, X in zip(Ts, X64s):
+        A = [f.T.contiguous() for f in T.factors]
+        core = T.core.reshape(list(reversed(T.core_dims)))
+        nx = torch.linalg.vector_norm(X)
+        out.append(float(torch.linalg.vector_norm(X - _reconstruct(torch, core, A).reshape(-1)) / nx))
+    return out
 
-    orders = tuple(int(v) for v in args.batch_orders.split(","))
-    rec = [b for b in batch_recipe() if len(b[0]) in orders]
-    if args.batch_count > 0:
-        rec = rec[:args.batch_count]
-    if 5 in orders:
-        return wl_batched_waves(torch, rh, L, args, device, peaks, src, orders)
-    Xs = [lowrank_plus_noise_torch(d, r, 0.9, 1e-3, sd, torch.float32, device) for d, r, sd in rec]
-    nbytes = sum(4 * x.numel() for x in Xs)
-    call = rh.RsthosvdBatchedCall([b[0] for b in rec], [b[1] for b in rec], torch.float32, p=5, seed=4, clamp=True,
-                                  streams=args.streams, device=device)
-    plan = call.plan(Xs) if args.streams == 0 else None
-    step = plan.run if plan is not None else (lambda: call.run(Xs))
+
+def _graph_timed(torch, L, step, args, device):
+    """CUDA-graph capture of ``step`` on a side stream, replayed ``steps`` times after ``warmup``."""
     step()
     torch.cuda.synchronize()
     s = torch.cuda.Stream(device=device)
@@ -723,9 +719,120 @@ def wl_batched(torch, rh, L, args, device, peaks, src):
     n0 = L.rh_kernel_launches()
     step()
     torch.cuda.synchronize()
-    launches = L.rh_kernel_launches() - n0
+    return ms, clk, L.rh_kernel_launches() - n0, g
+
+
+def wl_batched(torch, rh, L, args, device, peaks, src):
+    """The batched workload's order-3 and order-4 tensors (339 of 512, 8.0 GB FP32).  Grouped engine
+    (--streams 0): a batched plan (each tensor's launches recorded once, one grouped launch per stage)
+    whose run is captured in a CUDA graph and replayed; stream engine (--streams N): one
+    rsthosvd_batched call captured and replayed.  --batch-form: f32 (FP32 on the CUDA cores),
+    f32_bf16x2 (FP32 split into BF16 head + tail on the fly) or bf16 (BF16 storage); the BF16 forms
+    process mode 0 first, on the small-row tensor-core kernels.  Unless --no-fp64: the same batch as
+    FP64 data on the library's FP64 path (grouped, graph-replayed) and as a plain PyTorch FP64 loop
+    (matmul, linalg.qr, linalg.svd per tensor, same Omega), the relative errors of all three against
+    the FP32 tensors, and for the bf16 form the smallest oversampling p (from 5 up) whose errors are
+    all within 1.02 x the FP64 ones."""
+    from workloads import batch_recipe, lowrank_plus_noise_torch
+
+    orders = tuple(int(v) for v in args.batch_orders.split(","))
+    rec = [b for b in batch_recipe() if len(b[0]) in orders]
+    if args.batch_count > 0:
+        rec = rec[:args.batch_count]
+    if 5 in orders:
+        return wl_batched_waves(torch, rh, L, args, device, peaks, src, orders)
+    form = args.batch_form
+    rho = "natural" if form != "f32" else None
+    Xs = [lowrank_plus_noise_torch(d, r, 0.9, 1e-3, sd, torch.float32, device) for d, r, sd in rec]
+    nel = sum(x.numel() for x in Xs)
+    if form == "bf16":
+        Xin = [x.to(torch.bfloat16).view(torch.int16) for x in Xs]   # ties to even
+        esize, dt = 2, "bf16"
+    else:
+        Xin = Xs
+        esize, dt = 4, ("f32_bf16x2" if form == "f32_bf16x2" else torch.float32)
+    dims_list = [b[0] for b in rec]
+    ranks_list = [b[1] for b in rec]
+    nbytes = esize * nel
+
+    def run_form(p):
+        call = rh.RsthosvdBatchedCall(dims_list, ranks_list, dt, p=p, seed=4, clamp=True, streams=args.streams,
+                                      device=device, rho=rho)
+        plan = call.plan(Xin) if args.streams == 0 else None
+        step = plan.run if plan is not None else (lambda: call.run(Xin))
+        return call, plan, step
+
+    fp64 = None
+    e64 = None
+    if not args.no_fp64:
+        X64s = [x.double() for x in Xs]
+        c64 = rh.RsthosvdBatchedCall(dims_list, ranks_list, torch.float64, p=5, seed=4, clamp=True, streams=0,
+                                     device=device, rho=rho)
+        pl64 = c64.plan(X64s)
+        ms64, clk64, _, g64 = _graph_timed(torch, L, pl64.run, args, device)
+        e64 = _batch_errors(torch, pl64.run(), X64s)
+        torch.cuda.synchronize()
+        del g64
+        pl64.close()
+        # plain PyTorch FP64, one tensor after another (same Omega stream and tensor ids)
+        rr = list(range(max(orders)))
+        for i in range(min(3, len(rec))):
+            fp64_gpu_rsthosvd(torch, rh, X64s[i], dims_list[i], ranks_list[i], 5, 4,
+                              rr[:len(dims_list[i])] if rho else _default_rho(dims_list[i]), tensor_id=i, clamp=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        tout = []
+        for i in range(len(rec)):
+            tout.append(fp64_gpu_rsthosvd(torch, rh, X64s[i], dims_list[i], ranks_list[i], 5, 4,
+                                          rr[:len(dims_list[i])] if rho else _default_rho(dims_list[i]),
+                                          tensor_id=i, clamp=True))
+        b.record()
+        torch.cuda.synchronize()
+        ms_t = a.elapsed_time(b)
+        et = []
+        for (fac, G), X in zip(tout, X64s):
+            nx = torch.linalg.vector_norm(X)
+            et.append(float(torch.linalg.vector_norm(X - _reconstruct(torch, G, fac).reshape(-1)) / nx))
+        del tout
+        fp64 = {"library_fp64_grouped": {"ms_per_step": round(ms64, 3), "mean_rel_error": float(np.mean(e64)),
+                                         "max_rel_error": float(np.max(e64))},
+                "torch_fp64_loop": {"ms_per_step": round(ms_t, 3), "mean_rel_error": float(np.mean(et)),
+                                    "max_rel_error": float(np.max(et)),
+                                    "what": "plain PyTorch FP64 (matmul, linalg.qr, linalg.svd) Alg. 3 per tensor on "
+                                            "the same device, Omega stream and processing order"}}
+    p_used, search = 5, []
+    if form == "bf16" and e64 is not None and not args.no_psearch:
+        for pp in (5, 6, 7, 8, 10, 12, 16):
+            call, plan, step = run_form(pp)
+            Ts = step()
+            torch.cuda.synchronize()
+            eb = _batch_errors(torch, Ts, X64s)
+            worst = max(x / y for x, y in zip(eb, e64))
+            search.append({"p": pp, "max_error_ratio_vs_fp64": round(worst, 5)})
+            if plan is not None:
+                plan.close()
+            del call, plan, step
+            if worst <= 1.02:
+                p_used = pp
+                break
+    call, plan, step = run_form(p_used)
+    ms, clk, launches, g = _graph_timed(torch, L, step, args, device)
+    Ts = step()
+    torch.cuda.synchronize()
     tps = len(Xs) / (ms * 1e-3)
-    # roofline of the whole call: each tensor is read twice (sketch and mode product of mode 1)
+    res_err = None
+    if e64 is not None:
+        eo = _batch_errors(torch, Ts, X64s)
+        ratios = [x / y for x, y in zip(eo, e64)]
+        res_err = {"mean_rel_error": float(np.mean(eo)), "max_rel_error": float(np.max(eo)),
+                   "max_error_ratio_vs_fp64": round(max(ratios), 5), "mean_error_ratio_vs_fp64": round(
+                       float(np.mean(ratios)), 5)}
+        fp64["speedup_vs_library_fp64"] = round(fp64["library_fp64_grouped"]["ms_per_step"] / ms, 2)
+        fp64["speedup_vs_torch_fp64"] = round(fp64["torch_fp64_loop"]["ms_per_step"] / ms, 2)
+        fp64["equal_error"] = max(ratios) <= 1.02
+        del X64s
+    # roofline of the whole call: each tensor is read twice (sketch and mode product of its first mode)
     roof = _hbm_roof("rsthosvd_batched (whole call)", 2 * nbytes, ms, peaks, src)
     cpu = None
     if not args.no_cpu:
@@ -735,18 +842,37 @@ def wl_batched(torch, rh, L, args, device, peaks, src):
         for (d, r, _), X in list(zip(rec, Xs))[:6]:
             Xn = np.reshape(X.double().cpu().numpy(), d, order="F")
             tucker.rsthosvd(Xn, r, 5, 4, clamp=True)
-        dt = time.perf_counter() - t
-        cpu = {"value": round(6 / dt, 3), "unit": "tensors/s", "cores": _cores(), "kind": "oracle",
+        dt_ = time.perf_counter() - t
+        cpu = {"value": round(6 / dt_, 3), "unit": "tensors/s", "cores": _cores(), "kind": "oracle",
                "sample": "oracle R-STHOSVD (numpy FP64) of the first 6 tensors of the same set"}
-    return {"metric": "batched R-STHOSVD throughput (order-3 and order-4 tensors of the batch)",
-            "value": round(tps, 1), "unit": "tensors/s", "higher_is_better": True, "dtype": "f32",
-            "ms_per_step": round(ms, 3),
-            "config": {"workload": f"{len(Xs)} tensors, order {args.batch_orders}, sizes U[16,96], ranks U[4,16] capped, "
-                                   "low rank + "
-                                   f"1e-3 noise, seed 4, p=5 clamped; {nbytes / 1e9:.2f} GB FP32",
-                       "engine": "grouped (batched plan)" if args.streams == 0 else f"{args.streams} streams",
-                       "graph": True, "l2": "inputs 8 GB (larger than L2); no flush"},
-            "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+    names = {"f32": "FP32 on the CUDA cores", "f32_bf16x2": "FP32 split into BF16 head + tail on the fly, first mode "
+             "on the small-row tensor-core kernels", "bf16": "BF16 storage, first mode on the small-row tensor-core "
+             "kernels"}
+    out = {"metric": "batched R-STHOSVD throughput (order-3 and order-4 tensors of the batch)",
+           "value": round(tps, 1), "unit": "tensors/s", "higher_is_better": True,
+           "dtype": {"f32": "f32", "f32_bf16x2": "bf16x2", "bf16": "bf16"}[form], "form": names[form],
+           "ms_per_step": round(ms, 3),
+           "config": {"workload": f"{len(Xs)} tensors, order {args.batch_orders}, sizes U[16,96], ranks U[4,16] capped, "
+                                  "low rank + "
+                                  f"1e-3 noise, seed 4, p={p_used} clamped; {nbytes / 1e9:.2f} GB "
+                                  f"{'BF16' if form == 'bf16' else 'FP32'}",
+                      "processing_order": "mode 0 first (natural)" if rho else "decreasing sizes",
+                      "engine": "grouped (batched plan)" if args.streams == 0 else f"{args.streams} streams",
+                      "graph": True, "l2": f"inputs {nbytes / 1e9:.1f} GB (larger than L2); no flush"},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+    if res_err is not None:
+        out["errors"] = res_err
+        out["fp64_gpu"] = fp64
+    if search:
+        out["p_search"] = search
+    if plan is not None:
+        plan.close()
+    return out
+
+
+def _default_rho(dims):
+    """The library's default processing order: decreasing sizes, ties to the lower mode."""
+    return sorted(range(len(dims)), key=lambda k: (-dims[k], k))
 
 
 def wl_batched_waves(torch, rh, L, args, device, peaks, src, orders):
@@ -1113,6 +1239,10 @@ def main():
                     help="batched workload: tensor orders taken from the 512-tensor recipe (comma list)")
     ap.add_argument("--wave-gb", type=float, default=120.0,
                     help="batched workload with order-5 tensors: data + workspace per wave (GB)")
+    ap.add_argument("--batch-form", default="f32", choices=["f32", "f32_bf16x2", "bf16"],
+                    help="batched workload: input form (f32 on the CUDA cores; the BF16 forms take mode 0 first)")
+    ap.add_argument("--no-psearch", action="store_true",
+                    help="batched bf16 form: keep p = 5 (no search for the p that reaches the FP64 error)")
     ap.add_argument("--batch-count", type=int, default=0,
                     help="batched workload: first N tensors of those orders (0 = all)")
     ap.add_argument("--streams", type=int, default=0,

@@ -90,7 +90,12 @@ enum {
  * R-STHOSVD (truncating) the core after a mode is written with the next mode fastest when that
  * mode is the smallest other one, and that mode then runs on the tensor cores too (its FP32 core
  * split on the fly, Omega in BF16) if I_n % 8 == 0, I_n <= 1024 and r + p <= 64; the other modes
- * run in FP32 on the CUDA cores.  info bit 4 marks the modes that ran on the tensor cores. */
+ * run in FP32 on the CUDA cores.  A first mode with few rows (mode 0 processed first, I_0 <= 128,
+ * r + p <= 32, any I_0; every BF16 form, without subspace iteration) runs on the small-row
+ * tensor-core kernels instead (plain loads converted in shared memory into the same pieces, Omega in
+ * BF16, FP32 sums in tensor memory over a CTA's columns and FP64 across CTAs), and every later mode
+ * in FP32 on the CUDA cores; such requests can run on the grouped engine of rsthosvd_batched.
+ * info bit 4 marks the modes that ran on the tensor cores. */
 enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4, RH_FP8_E4M3 = 5 };
 
 /* rh_fp8_layout -- storage of an RH_FP8_E4M3 tensor with sizes dims (see above): *ld = the stride
@@ -181,7 +186,8 @@ rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0,
  * unfolding, as in Alg. 2 step 3 and Alg. 3 step 4).
  *   X       order-``order`` tensor with sizes dims[0..order-1], column-major, dtype RH_F64/RH_F32, or
  *           RH_BF16/RH_BF16X2/RH_F32_BF16X2/RH_FP8_E4M3 for mode 0 (tensor cores; needs I_0 % 8 == 0,
- *           I_0 <= 1024; Omega in BF16), or RH_F32_BF16X2 for a later mode whose earlier sizes
+ *           I_0 <= 1024, or I_0 <= 128 and ell <= 32 on the small-row kernel;
+ *           Omega in BF16), or RH_F32_BF16X2 for a later mode whose earlier sizes
  *           multiply to a multiple of 64, I_mode <= 1024 (tensor cores, the FP32 values read through
  *           the 3-D view (l, i, r) of the mode and split on the fly).  norm2 is not computed for RH_BF16/RH_BF16X2 and must be
  *           NULL; for RH_F32_BF16X2 it is ||head + tail||^2 (FP32 sums over 32 values per thread
@@ -305,7 +311,8 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
  * rh_mode_product_bf16 -- the first-mode product Y = X x_0 A^T on the tensor cores for a tensor in
  * a BF16 form (RH_BF16 / RH_BF16X2 / RH_F32_BF16X2): A is I_0 x k FP64 (1 <= k <= 64), split exactly into two BF16
  * pieces; Y is k x (N / I_0) FP32 (layout c + k p), all four piece products with FP32
- * accumulation.  Needs I_0 % 8 == 0.  Workspace: rh_mode_product_workspace_size; its first int32
+ * accumulation.  Needs I_0 % 8 == 0, or I_0 <= 128 and k <= 32 (the small-row kernel).
+ * Workspace: rh_mode_product_workspace_size; its first int32
  * receives the wait status as in rhosvd_sketch (0, or the code of a bounded wait that gave up).
  */
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k);
@@ -389,9 +396,12 @@ rh_status rsthosvd(int32_t order, const int64_t* dims, int32_t dtype, const void
  *   norms    optional device buffer of 2 * count FP64 values (tensor i at 2 i); info optional
  *            device int32 array laid out like dims.
  *   opts     shared by every tensor; tensor i draws Omega with tensor_id = opts->tensor_id + i.
- *            The processing order must be the default (opts->rho[0] < 0).
+ *            opts->rho is the default order (rho[0] < 0) or one whose first order_i entries are a
+ *            permutation of 0 .. order_i - 1 for every tensor i (tensor i takes those entries).
  *   streams  0 = the grouped engine when every request is FP32 or FP64 data with truncation
- *            (opts->truncate): each tensor's launch sequence is recorded on the host and the same
+ *            (opts->truncate), or a BF16 form whose first mode
+ *            runs on the small-row tensor-core kernels (see the element types above): each
+ *            tensor's launch sequence is recorded on the host and the same
  *            stage of all tensors runs as one launch (about 30 launches per mode for the whole
  *            batch; the per-tensor argument tables are copied into the workspace by stream-ordered
  *            kernels that carry them in their parameters).  Otherwise, and for streams >= 1, that

@@ -638,7 +638,7 @@ class RsthosvdBatchedCall:
     returns one Tucker per tensor (views of buffers allocated once here)."""
 
     def __init__(self, dims_list, ranks_list, dtype, p=5, seed=0, tensor_id=0, clamp=False, truncate=True,
-                 streams=0, device="cuda", svd_route=0, power_iters=0):
+                 streams=0, device="cuda", svd_route=0, power_iters=0, rho=None):
         torch = _torch()
         if len(dims_list) != len(ranks_list) or not dims_list:
             raise ValueError("dims_list and ranks_list must be non-empty and of equal length")
@@ -650,8 +650,10 @@ class RsthosvdBatchedCall:
                 raise ValueError("batched calls take float32/float64 or the f32_bf16x2 and bf16 forms")
         else:
             self.dt = RH_F64 if dtype == torch.float64 else RH_F32
+        if rho == "natural":
+            rho = list(range(max(len(d) for d in self.dims_list)))
         self.opts = make_options(seed=seed, p=p, tensor_id=tensor_id, clamp=clamp, truncate=truncate,
-                                 svd_route=svd_route, power_iters=power_iters)
+                                 svd_route=svd_route, power_iters=power_iters, rho=rho)
         self.orders = i32_array([len(d) for d in self.dims_list])
         self.da = i64_array([x for d in self.dims_list for x in d])
         self.ra = i32_array([int(r) for rk in ranks_list for r in rk])

@@ -66,7 +66,8 @@ rh_status batch_layout(int32_t count, const int32_t* orders, const int64_t* dims
   rh_options o;
   rh_options_default(&o);
   if (opts) o = *opts;
-  RH_CHECK_ARG(o.rho[0] < 0, "batched calls use the default processing order (opts->rho[0] < 0)");
+  // opts->rho: the default order, or an order whose first order_i entries every tensor i takes
+  // (make_plan checks that they are a permutation of 0 .. order_i - 1)
   RH_CHECK_ARG(o.tensor_id >= 0 && (int64_t)o.tensor_id + count <= (int64_t(1) << 28),
                "tensor_id + count must stay below 2^28");
   bl.dim_off.assign(count + 1, 0);

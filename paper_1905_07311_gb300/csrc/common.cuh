@@ -315,6 +315,7 @@ enum LaunchSite : int {
   SITE_FACTOR = 70,
   SITE_FACTOR_SIGN,
   SITE_CORE = 80,
+  SITE_INFO = 85,           // info bits of the mode (and the wait status of its tensor-core kernels)
   SITE_FINAL = 90,
   SITE_OTHER = 1000         // launches of entry points that never run grouped
 };

@@ -52,6 +52,24 @@ rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, con
 bool sketch_tc_strided_supported(const ModeView& v, int ell);
 rh_status launch_sketch_tc_f32s(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
                                 double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
+// A first mode with few rows (L = 1, I <= 128, ell <= 32) on the tensor cores as grouped operations
+// (small_tc.cu).  The input in one of the BF16 forms: RH_F32_BF16X2 (FP32, split on the fly into
+// head + tail), RH_BF16, RH_BF16X2 (the two pieces) or RH_FP8_E4M3 (bytes at stride ld, scales).
+// The sketch writes the partial sketches of plan_sketch_small_tc (part [S][ell][I], FP32; part_norm
+// [S] or NULL), summed by launch_sketch_reduce<float>; the mode product writes B[c + ell p] (FP32)
+// from the FP64 Q (I x ell) split into two BF16 pieces.
+struct SmallInput {
+  const void* X;
+  int32_t form;
+  int64_t ld = 0;                 // RH_FP8_E4M3
+  const float* scales = nullptr;  // RH_FP8_E4M3
+};
+bool small_tc_supported(const ModeView& v, int ell);
+SketchPlan plan_sketch_small_tc(const ModeView& v, int ell);
+rh_status launch_sketch_small_tc(const SketchPlan& pl, const SmallInput& in, uint64_t seed, uint32_t sid, float* part,
+                                 double* part_norm, int32_t* err, cudaStream_t st, int site = SITE_SKETCH);
+rh_status launch_ttm_small_tc(const ModeView& v, const SmallInput& in, const double* Q, int ell, float* B, int32_t* err,
+                              cudaStream_t st, int site = SITE_MODE_PRODUCT);
 rh_status launch_sum_n(const double* part, int n, double* out, cudaStream_t st, int accumulate = 0);
 rh_status launch_split_bf16x2(const float* x, int64_t n, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 // ||X_1 + X_2||^2 of BF16 pieces (piece1 may be NULL); part holds 1024 doubles

@@ -72,6 +72,8 @@ struct Step {
   bool cp = false;      // truncated core by the core product (B has the new mode fastest) in the order cout
   CoreOut cout;
   bool cp_tc = false;   // that core product on the tensor cores (B and U_r split into BF16 pieces)
+  bool stc = false;     // first mode with few rows: sketch and mode product on the small-row
+                        // tensor-core kernels (grouped operations), later modes FP32 on the CUDA cores
 };
 
 struct Plan {
@@ -170,6 +172,19 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
     // on the fly can also take the FP32 CUDA-core path for a first mode the tensor-core kernels
     // do not cover (later modes still go to the tensor cores where their shape allows).
     const Step& s0 = pl.steps[0];
+    if (o.power_iters == 0 && small_tc_supported(s0.v, s0.ell)) {
+      // A first mode with few rows (mode 0, I_0 <= 128, ell <= 32): the small-row tensor-core
+      // sketch and mode product, written as grouped operations; the later modes run in FP32 on
+      // the CUDA cores on the FP32 core the first mode leaves.
+      Step& f = pl.steps[0];
+      f.stc = true;
+      f.sk = plan_sketch_small_tc(f.v, f.ell);
+      pl.max_part = std::max(pl.max_part, f.sk.part_elems());
+      pl.max_pnorm = std::max(pl.max_pnorm, f.sk.norm_elems());
+      pl.dtype = RH_F32;
+      pl.in_form = dtype;
+      return plan_power(o, pl);
+    }
     const bool s0_tc = s0.mode == 0 && sketch_tc_supported(s0.v, s0.ell) && ttm_tc_supported(s0.v, s0.ell);
     if (!s0_tc && dtype != RH_F32_BF16X2) {
       set_error("unsupported: the BF16 and E4M3 forms need mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024, "
@@ -353,19 +368,26 @@ Bufs carve(Arena& ar, const Plan& pl) {
 
 // info |= bits, plus 16 when a tensor-core kernel recorded a bounded wait that gave up (*err != 0);
 // the wait flag is cleared so that the next mode reports its own.
-__global__ void info_or_kernel(int32_t* info, int32_t bits, int32_t* err) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    if (err != nullptr && *err != 0) {
-      bits |= 16;
-      *err = 0;
+struct InfoOrOp {
+  struct Args {
+    int32_t* info;
+    int32_t bits;
+    int32_t* err;
+  };
+  static constexpr int kThreads = 32, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& a) {
+    if (threadIdx.x == 0 && g.bx == 0 && g.by == 0) {
+      int32_t bits = a.bits;
+      if (a.err != nullptr && *a.err != 0) {
+        bits |= 16;
+        *a.err = 0;
+      }
+      if (bits) *a.info |= bits;
     }
-    if (bits) *info |= bits;
   }
-}
+};
 rh_status set_info_bits(int32_t* info, int32_t bits, cudaStream_t st, int32_t* err = nullptr) {
-  info_or_kernel<<<1, 32, 0, st>>>(info, bits, err);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return emit<InfoOrOp>(SITE_INFO, 0, dim3(1), 0, st, InfoOrOp::Args{info, bits, err});
 }
 
 // Randomized subspace iteration (Sec. 5 "Variants"; used with one step in Sec. 6): q steps of
@@ -421,7 +443,13 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
   const float* scales8 = fp8in ? reinterpret_cast<const float*>(x8 + f8.scale_off) : nullptr;
   const uint16_t* piece0 = (f32in || fp8in) ? nullptr : static_cast<const uint16_t*>(Xraw);
   const uint16_t* piece1 = (pl.in_form == RH_BF16X2) ? piece0 + pl.steps[0].v.I * pl.steps[0].v.M() : nullptr;
-  if (tc0) RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
+  const bool stc0 = pl.steps[0].stc;
+  const SmallInput small_in{Xraw, pl.in_form, fp8in ? f8.ld : 0, scales8};
+  if (stc0) {
+    if ((s = emit_memset(SITE_ENTRY, 1, b.err, sizeof(int32_t), st)) != RH_OK) return s;
+  } else if (tc0) {
+    RH_CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(int32_t), st));
+  }
   for (int j = 0; j < nsteps; ++j) {
     record_step(kStepStride * j);
     const Step& sp = pl.steps[j];
@@ -436,7 +464,17 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     const bool in_pieces = tc && first && !f32in && !fp8in;
     const bool in_fp8 = tc && first && fp8in;
     const float* tc_src = first ? static_cast<const float*>(Xraw) : reinterpret_cast<const float*>(cur);
-    if (tc) {
+    if (sp.stc) {
+      {
+        ProfileScope ps(PROF_SKETCH, j, st);
+        if ((s = launch_sketch_small_tc(sp.sk, small_in, o.seed, sid, static_cast<float*>(sb.part), sb.part_norm, b.err,
+                                        st)) != RH_OK)
+          return s;
+      }
+      if ((s = launch_sketch_reduce<float>(sp.sk, static_cast<const float*>(sb.part), sb.part_norm, b.Y, n2, st)) !=
+          RH_OK)
+        return s;
+    } else if (tc) {
       {
         ProfileScope ps(PROF_SKETCH, j, st);
         if (in_pieces)
@@ -480,7 +518,15 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
     // Alg. 1 step 3: B = Q^T G_(n)   (the mode-n product G x_n Q^T)
     const bool direct_core = last && !o.truncate;
-    if (tc) {
+    if (sp.stc) {
+      ProfileScope ps(PROF_TTM, j, st);
+      if (direct_core) {
+        set_error("unsupported: single-mode untruncated BF16 request");
+        return RH_EUNSUPPORTED;
+      }
+      if ((s = launch_ttm_small_tc(sp.v, small_in, b.Q, sp.ell, reinterpret_cast<float*>(B), b.err, st)) != RH_OK)
+        return s;
+    } else if (tc) {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
         set_error("unsupported: single-mode untruncated BF16 request");
@@ -556,8 +602,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     }
     // info bit 4: this mode's sketch and mode product ran on the tensor cores; bit 16: a tensor-core
     // kernel of this mode gave up a bounded wait (the mode's outputs are invalid)
-    if (info && (tc || (o.truncate && sp.cp && sp.cp_tc && !last)) &&
-        (s = set_info_bits(info + sp.mode, tc ? 4 : 0, st, b.err)) != RH_OK)
+    if (info && (tc || sp.stc || (o.truncate && sp.cp && sp.cp_tc && !last)) &&
+        (s = set_info_bits(info + sp.mode, (tc || sp.stc) ? 4 : 0, st, b.err)) != RH_OK)
       return s;
   }
   if (norms) {
@@ -675,12 +721,20 @@ extern "C" {
 
 static bool is_bf16_form(int32_t dtype) { return bf16_form(dtype); }
 
-static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell, int32_t mode = 0) {
+// The sketch of mode 0 in a BF16 form whose I_0 the persistent tensor-core kernel does not take
+// (I_0 % 8 != 0) runs on the small-row kernel when I_0 <= 128 and ell <= 32.
+static bool sketch_small_route(int32_t dtype, const ModeView& v, int32_t ell, int32_t mode) {
+  (void)dtype;
+  return mode == 0 && !sketch_tc_supported(v, ell) && small_tc_supported(v, ell);
+}
+
+static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell, int32_t mode = 0, int32_t dtype = RH_BF16) {
   const ModeView v = mode_view(order, dims, mode);
+  const int64_t S = sketch_small_route(dtype, v, ell, mode) ? plan_sketch_small_tc(v, ell).S : sketch_tc_ctas(v);
   Arena ar(nullptr);
   ar.take<int32_t>(4);   // wait status, first (documented)
-  ar.take<float>((size_t)sketch_tc_ctas(v) * ell * v.I);
-  ar.take<double>((size_t)sketch_tc_ctas(v));
+  ar.take<float>((size_t)S * ell * v.I);
+  ar.take<double>((size_t)S);
   return ar.used;
 }
 
@@ -705,7 +759,7 @@ size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t 
     if (mode != 0 && dtype != RH_F32_BF16X2) return 0;
     for (int k = 0; k < order; ++k)
       if (dims[k] < 1) return 0;
-    return sketch_tc_ws(order, dims, ell, mode);
+    return sketch_tc_ws(order, dims, ell, mode, dtype);
   }
   if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || ell < 1 || ell > RH_MAX_ELL) return 0;
   const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
@@ -737,19 +791,26 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
     RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
     RH_CHECK_ARG(norm2 == nullptr || converted_form(dtype), "norm2 is not available for RH_BF16 / RH_BF16X2");
     const ModeView v = mode_view(order, dims, mode);
-    if (mode == 0 ? !sketch_tc_supported(v, ell) : !sketch_tc_strided_supported(v, ell)) {
-      set_error(mode == 0 ? "unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024"
+    const bool small = sketch_small_route(dtype, v, ell, mode);
+    if (!small && (mode == 0 ? !sketch_tc_supported(v, ell) : !sketch_tc_strided_supported(v, ell))) {
+      set_error(mode == 0 ? "unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024, or I_0 <= 128 and "
+                            "ell <= 32"
                           : "unsupported: a split sketch of a later mode needs the product of the earlier sizes to "
                             "be a multiple of 64 and I_n <= 1024");
       return RH_EUNSUPPORTED;
     }
-    const size_t need = sketch_tc_ws(order, dims, ell, mode);
+    const size_t need = sketch_tc_ws(order, dims, ell, mode, dtype);
     if (workspace == nullptr || workspace_bytes < need) {
       set_error("workspace too small: need " + std::to_string(need) + " bytes");
       return RH_ENOMEM;
     }
     Arena ar(workspace);
-    const int S = sketch_tc_ctas(v);
+    SketchPlan sp_small;
+    if (small) {
+      sp_small = plan_sketch_small_tc(v, ell);
+      sp_small.row0 = row0;
+    }
+    const int S = small ? sp_small.S : sketch_tc_ctas(v);
     int32_t* err = ar.take<int32_t>(4);   // wait status: the first int32 of the workspace
     float* part = ar.take<float>((size_t)S * ell * v.I);
     double* norm_part = ar.take<double>((size_t)S);
@@ -757,7 +818,16 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
     RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
     const uint32_t sid = ((uint32_t)tensor_id << 4) | (uint32_t)mode;
     rh_status s;
-    if (dtype == RH_F32_BF16X2) {
+    if (small) {
+      SmallInput in{X, dtype};
+      if (dtype == RH_FP8_E4M3) {
+        const Fp8Layout f8 = fp8_layout(order, dims);
+        in.ld = f8.ld;
+        in.scales = reinterpret_cast<const float*>(static_cast<const uint8_t*>(X) + f8.scale_off);
+      }
+      s = launch_sketch_small_tc(sp_small, in, seed, sid, part, norm2 ? norm_part : nullptr, err, st, SITE_OTHER);
+      if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st, accumulate);
+    } else if (dtype == RH_F32_BF16X2) {
       s = mode == 0 ? launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part,
                                            norm2 ? norm_part : nullptr, err, st, row0)
                     : launch_sketch_tc_f32s(v, ell, static_cast<const float*>(X), seed, sid, part,
@@ -860,8 +930,10 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
   for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
   RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
   const ModeView v = mode_view(order, dims, 0);
-  if (!ttm_tc_supported(v, k)) {
-    set_error("unsupported: the BF16 mode product needs I_0 % 8 == 0 and 1 <= k <= 64");
+  // I_0 % 8 != 0: the small-row kernel (I_0 <= 128, k <= 32)
+  const bool small = !ttm_tc_supported(v, k) && small_tc_supported(v, k);
+  if (!ttm_tc_supported(v, k) && !small) {
+    set_error("unsupported: the BF16 mode product needs I_0 % 8 == 0 and 1 <= k <= 64, or I_0 <= 128 and k <= 32");
     return RH_EUNSUPPORTED;
   }
   const size_t need = rh_mode_product_workspace_size(order, dims, dtype, 0, k);
@@ -874,6 +946,15 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
   uint16_t* qa = ar.take<uint16_t>((size_t)128 * dims[0]);
   cudaStream_t st = (cudaStream_t)stream;
   RH_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  if (small) {
+    SmallInput in{X, dtype};
+    if (dtype == RH_FP8_E4M3) {
+      const Fp8Layout f8 = fp8_layout(order, dims);
+      in.ld = f8.ld;
+      in.scales = reinterpret_cast<const float*>(static_cast<const uint8_t*>(X) + f8.scale_off);
+    }
+    return launch_ttm_small_tc(v, in, A, k, Y, err, st, SITE_OTHER);
+  }
   if (dtype == RH_F32_BF16X2) return launch_ttm_tc_f32(v, k, static_cast<const float*>(X), A, qa, Y, err, st);
   if (dtype == RH_FP8_E4M3) {
     const Fp8Layout f8 = fp8_layout(order, dims);
@@ -1042,7 +1123,7 @@ bool rsthosvd_groupable(int32_t order, const int64_t* dims, int32_t dtype, const
   const rh_options o = opts_or_default(opts);
   Plan pl;
   if (make_plan(order, dims, dtype, ranks, o, pl) != RH_OK) return false;
-  return (dtype == RH_F32 || dtype == RH_F64) && pl.in_form < 0 && o.truncate;
+  return (((dtype == RH_F32 || dtype == RH_F64) && pl.in_form < 0) || pl.steps[0].stc) && o.truncate;
 }
 }  // namespace rh
 

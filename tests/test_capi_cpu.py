@@ -148,10 +148,16 @@ def test_batched_workspace_is_one_slice_per_stream(L):
     slices32 = sum((_ws(L, d, r, dtype=1, p=5) + 255) // 256 * 256 for d, r in zip(dims_list, ranks_list))
     g32 = _batched_ws(L, dims_list, ranks_list, streams=0, dtype=1, p=5)
     assert slices32 < g32 < slices32 + (1 << 20)
-    # requests outside the grouped engine (a converted input form, or no truncation) keep the
-    # stream engine at streams = 0: min(8, count) slices
-    one4 = max(_ws(L, d, r, dtype=4, p=5) for d, r in zip(dims_list, ranks_list))
-    assert _batched_ws(L, dims_list, ranks_list, streams=0, dtype=4, p=5) == 3 * ((one4 + 255) // 256 * 256)
+    # the split form whose first mode (mode 0, I_0 <= 128, r + p <= 32) runs on the small-row
+    # tensor-core kernels is recorded for the grouped engine too
+    slices4 = sum((_ws(L, d, r, dtype=4, p=5) + 255) // 256 * 256 for d, r in zip(dims_list, ranks_list))
+    g4 = _batched_ws(L, dims_list, ranks_list, streams=0, dtype=4, p=5)
+    assert slices4 < g4 < slices4 + (1 << 20)
+    # requests outside the grouped engine (a converted input form whose first mode runs elsewhere,
+    # or no truncation) keep the stream engine at streams = 0: min(8, count) slices
+    big = [[130, 20, 10], [40, 12, 11, 9], [16, 16, 16]]
+    one4 = max(_ws(L, d, r, dtype=4, p=5) for d, r in zip(big, ranks_list))
+    assert _batched_ws(L, big, ranks_list, streams=0, dtype=4, p=5) == 3 * ((one4 + 255) // 256 * 256)
     one_nt = max(_ws(L, d, r, p=5, truncate=False) for d, r in zip(dims_list, ranks_list))
     assert _batched_ws(L, dims_list, ranks_list, streams=0, p=5, truncate=False) == 3 * ((one_nt + 255) // 256 * 256)
 
@@ -170,8 +176,10 @@ def test_batched_plan_argument_checks(L):
     # no plan pointer
     assert L.rsthosvd_batched_plan_create(2, orders, dims, 1, xs, ranks, ctypes.byref(o), fs, cs, None, None,
                                           None, 0, None) == 1
-    # a converted input form is not on the grouped engine
-    assert L.rsthosvd_batched_plan_create(2, orders, dims, 4, xs, ranks, ctypes.byref(o), fs, cs, None, None,
+    # a converted input form whose first mode is outside the small-row tensor-core kernels
+    # (I_0 = 130 > 128) is not on the grouped engine
+    big = _lib.i64_array([130, 20, 10, 16, 16, 16])
+    assert L.rsthosvd_batched_plan_create(2, orders, big, 4, xs, ranks, ctypes.byref(o), fs, cs, None, None,
                                           None, 0, ctypes.byref(h)) == 6
     assert "grouped engine" in L.rh_last_error().decode() and not h.value
     # workspace too small (checked before anything touches the device)
@@ -200,8 +208,11 @@ def test_batched_argument_checks(L):
     assert _batched_ws(L, [[4] * 9], [[1] * 9], p=1) == 0
     assert L.rsthosvd_batched_workspace_size(0, None, None, 0, None, None, 0) == 0
     assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], streams=64, p=5) > 0    # capped at count = 1
-    # a custom processing order is not accepted for a batch
-    assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], p=5, rho=[2, 1, 0]) == 0
+    # a processing order applies to every tensor of a batch: its first order_i entries must be a
+    # permutation of 0 .. order_i - 1 for each tensor
+    assert _batched_ws(L, [[30, 20, 10]], [[4, 4, 4]], p=5, rho=[2, 1, 0]) > 0
+    assert _batched_ws(L, [[30, 20, 10], [9, 8, 7, 6]], [[4, 4, 4], [3, 3, 3, 3]], p=1, rho=[0, 1, 2, 3]) > 0
+    assert _batched_ws(L, [[30, 20, 10], [9, 8, 7, 6]], [[4, 4, 4], [3, 3, 3, 3]], p=1, rho=[3, 0, 1, 2]) == 0
 
 
 def test_svd_route_option(L):
@@ -262,7 +273,9 @@ def test_every_entry_point_validates_before_the_device(L):
     assert L.rh_mode_product(3, d3, 0, one, 0, 4, one, 1, 1, one, None) == 1      # FP64 in, FP32 out
     assert L.rh_mode_product_bf16(3, d3, 1, one, 4, one, one, one, big, None) == 1
     assert L.rh_mode_product_bf16(3, _lib.i64_array([32, 20, 10]), 2, one, 65, one, one, one, big, None) == 6
-    assert L.rh_mode_product_bf16(3, d3, 2, one, 4, one, one, one, big, None) == 6   # I_0 % 8 != 0
+    # I_0 % 8 != 0 with I_0 > 128 (neither the persistent nor the small-row kernel), or k > 32 there
+    assert L.rh_mode_product_bf16(3, _lib.i64_array([130, 20, 10]), 2, one, 4, one, one, one, big, None) == 6
+    assert L.rh_mode_product_bf16(3, d3, 2, one, 33, one, one, one, big, None) == 6
     # left SVD of a short mode (Alg. 1 step 4)
     assert L.rh_left_svd(3, _lib.i64_array([65, 20, 10]), 1, one, 0, one, one, one, big, None) == 1
     assert L.rh_left_svd(3, d3, 1, None, 2, one, one, one, big, None) == 1
