@@ -188,6 +188,8 @@ template <typename T>
 size_t power_workspace_elems(const TruncPlan& tr);
 template <typename T>
 rh_status launch_power_basis(const TruncPlan& tr, T* B, T* ws, cudaStream_t st);
-rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st);
+// ||x||^2 (FP64); with a scratch part of part_elems >= 2 doubles a large x is summed over many CTAs
+rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st, double* part = nullptr,
+                       size_t part_elems = 0);
 
 }  // namespace rh

@@ -347,7 +347,7 @@ Bufs carve(Arena& ar, const Plan& pl) {
   const bool f64 = pl.dtype == RH_F64;
   auto takeT = [&](size_t n) -> void* { return f64 ? (void*)ar.take<double>(n) : (void*)ar.take<float>(n); };
   b.part = takeT(pl.max_part);
-  b.part_norm = ar.take<double>(pl.max_pnorm);
+  b.part_norm = ar.take<double>(std::max<size_t>(pl.max_pnorm, 256));   // also the final norm's partials
   b.normx = ar.take<double>(1);
   b.Y = ar.take<double>(pl.max_I_ell);
   b.orth = ar.take<double>(pl.max_orth);
@@ -613,7 +613,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     std::vector<int64_t> dims_out(pl.d, 0);
     for (const Step& sp : pl.steps) dims_out[sp.mode] = sp.ko;
     for (int k = 0; k < pl.d; ++k) ncore *= dims_out[k];
-    if ((s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
+    if ((s = launch_sumsq(core, ncore, norms + 1, st, b.part_norm, std::max<size_t>(pl.max_pnorm, 256))) != RH_OK) return s;
   }
   return RH_OK;
 }
@@ -701,7 +701,7 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
   if (norms) {
     int64_t ncore = 1;
     for (int k = 0; k < pl.d; ++k) ncore *= ks[k];
-    if ((s = launch_sumsq(core, ncore, norms + 1, st)) != RH_OK) return s;
+    if ((s = launch_sumsq(core, ncore, norms + 1, st, b.part_norm, std::max<size_t>(pl.max_pnorm, 256))) != RH_OK) return s;
   }
   return RH_OK;
 }

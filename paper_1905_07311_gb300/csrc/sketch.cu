@@ -500,13 +500,37 @@ __device__ __forceinline__ void SketchReduceOp<T>::body(const Grid g, const Args
     const int64_t step = (int64_t)ell * I;
     int k = w;
     // eight independent chains per lane (loads in flight together), combined in a fixed order
-    double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (; k + 7 * kRedWarps < S; k += 8 * kRedWarps) {
+    if constexpr (sizeof(T) == 4) {
+      // FP32 partials: each chain is an FP32 sum that keeps its rounding errors (Knuth's TwoSum,
+      // every error exact), so the chain's value hi + lo carries ~2^-44 relative error at FP32
+      // arithmetic rate (FP64 runs at a small fraction of it on this part)
+      float hi[8], lo[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) c[j] += (double)src[(int64_t)(k + j * kRedWarps) * step];
+      for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0.0f;
+      auto acc = [](float& h, float& l, float v) {
+        const float t = __fadd_rn(h, v);
+        const float bp = __fsub_rn(t, h);
+        l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+        h = t;
+      };
+      for (; k + 7 * kRedWarps < S; k += 8 * kRedWarps) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc(hi[j], lo[j], (float)src[(int64_t)(k + j * kRedWarps) * step]);
+      }
+      for (; k < S; k += kRedWarps) acc(hi[0], lo[0], (float)src[(int64_t)k * step]);
+      double c[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) c[j] = (double)hi[j] + (double)lo[j];
+      s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+    } else {
+      double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (; k + 7 * kRedWarps < S; k += 8 * kRedWarps) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c[j] += (double)src[(int64_t)(k + j * kRedWarps) * step];
+      }
+      for (; k < S; k += kRedWarps) c[0] += (double)src[(int64_t)k * step];
+      s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
     }
-    for (; k < S; k += kRedWarps) c[0] += (double)src[(int64_t)k * step];
-    s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
   }
   red[w][lane] = s;
   __syncthreads();

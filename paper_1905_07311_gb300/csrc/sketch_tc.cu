@@ -354,12 +354,16 @@ __global__ void pieces_sumsq_kernel(const uint16_t* __restrict__ a, const uint16
   }
 }
 
+// *out (+)= sum of part[0 .. n): one warp, lane l sums part[l], part[l + 32], ..., then a fixed
+// butterfly over the lanes (deterministic)
 __global__ void sum_n_kernel(const double* __restrict__ part, int n, double* __restrict__ out, int accumulate) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < n; ++k) t += part[k];
-    *out = accumulate ? *out + t : t;
-  }
+  if (blockIdx.x != 0) return;
+  const int l = threadIdx.x;
+  double t = 0.0;
+  for (int k = l; k < n; k += 32) t += part[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (l == 0) *out = accumulate ? *out + t : t;
 }
 
 // ---- tensor maps (driver entry point, no link-time dependency on libcuda) ----------------

@@ -1349,6 +1349,52 @@ __device__ __forceinline__ void SumsqOp::body(const Grid g, const Args& args) {
   if (threadIdx.x == 0) *out = s;
 }
 
+// ||x||^2 over many CTAs (FP64 arithmetic runs at a small fraction of the FP32 rate on this part, so
+// one CTA is bound by its SM's FP64 pipe): CTA b sums the contiguous range [b chunk, (b + 1) chunk)
+// into part[b] (eight chains per thread, fixed-order combine), SumPartsOp adds the partials in a
+// fixed order.
+struct SumsqPartOp {
+  struct Args {
+    const double* x;
+    int64_t n, chunk;
+    double* part;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& a) {
+    __shared__ double scratch[33];
+    const int64_t b0 = (int64_t)g.bx * a.chunk, b1 = min(a.n, b0 + a.chunk);
+    double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int64_t e = b0 + threadIdx.x;
+    for (; e + 7 * 256 < b1; e += 8 * 256) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const double v = a.x[e + j * 256];
+        c[j] = fma(v, v, c[j]);
+      }
+    }
+    for (; e < b1; e += 256) c[0] = fma(a.x[e], a.x[e], c[0]);
+    double s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+    s = block_sum(s, scratch);
+    if (threadIdx.x == 0) a.part[g.bx] = s;
+  }
+};
+struct SumPartsOp {
+  struct Args {
+    const double* part;
+    int n;
+    double* out;
+  };
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  __device__ static void body(const Grid g, const Args& a) {
+    __shared__ double scratch[33];
+    (void)g;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < a.n; k += 256) s += a.part[k];
+    s = block_sum(s, scratch);
+    if (threadIdx.x == 0) *a.out = s;
+  }
+};
+
 // Gram matrix W = B_(n) B_(n)^T (ell x ell) of a (L, ell, R) tensor, streamed once: CTAs walk
 // tiles of 128 unfolding columns staged in shared memory (row pp = column p of B_(n), 16-byte
 // aligned rows).  W is split into 4 x 4 blocks and thread t < NB (NB + 1) / 2 owns the t-th
@@ -1715,6 +1761,9 @@ __device__ __forceinline__ void PivotedCholeskyOp::body(const Grid g, const Args
 // at convergence X = U S, so U is read off by normalising the columns.  Same circle schedule and
 // rotation rule as jacobi_svd_kernel, but a warp rotates four pairs at once (eight lanes per pair,
 // each lane holding entries 4l..4l+3 and 32+4l..32+4l+3 of both columns as two 16-byte vectors).
+// Sweeps end when one rotates nothing, or when the largest coupling it rotated was at most
+// sqrt(tol / n) (the quadratic convergence of the cyclic Jacobi method then leaves every coupling
+// of the next sweep below tol, so that sweep is not run).
 // Afterwards the columns are normalised, sorted by decreasing norm and made orthonormal to FP32
 // rounding by one polar correction U <- U (3 I - U^T U) / 2 (the Jacobi tolerance leaves
 // |u_i^T u_j| <= tol).  Writes Ub (n x n, FP64) and sv = the column norms (FP64), sorted.
@@ -1754,13 +1803,18 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
   __shared__ float nrm2[2][RH_MAX_ELL];
   __shared__ float sig[RH_MAX_ELL];
   __shared__ int rankof[RH_MAX_ELL];
+  __shared__ int cmax[2];   // per sweep (two slots): largest |g| / sqrt(al be) rotated, as FP32 bits
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int e = t; e < 64 * 64; e += blockDim.x) {
     const int i = e & 63, q = e >> 6;
     buf0[e] = (q < n && i < n) ? Xin[i + n * q] : 0.0f;
   }
+  if (t < 2) cmax[t] = 0;
   __syncthreads();
   const float tol = (float)(8 * (n > 8 ? n : 8)) * 5.9604645e-8f;
+  // Quadratic convergence: a sweep whose largest rotated coupling is c leaves couplings of order
+  // c^2, so once c <= sqrt(tol / n) the next sweep would rotate nothing and is skipped.
+  const float cstop = sqrtf(tol / (float)(n > 1 ? n : 1));
   const int grp = lane >> 3, l = lane & 7;
   const int pr = 4 * w + grp;           // pair index of this lane group
   const bool active = pr < half;
@@ -1779,6 +1833,7 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
         if (lane == 0) nrm2[cur][q] = v;
       }
       __syncthreads();
+      if (t == 0) cmax[(sweep + 1) & 1] = 0;   // every thread has read the previous sweep's slot
     }
     int rotated = 0;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
@@ -1796,7 +1851,9 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
         g += __shfl_xor_sync(0xffffffffu, g, 1);
         g += __shfl_xor_sync(0xffffffffu, g, 2);
         g += __shfl_xor_sync(0xffffffffu, g, 4);
-        if (active && g != 0.0f && fabsf(g) * rsqrtf(al) * rsqrtf(be) > tol) {
+        const float cpl = fabsf(g) * rsqrtf(al) * rsqrtf(be);
+        if (active && g != 0.0f && cpl > tol) {
+          if (l == 0) atomicMax(&cmax[sweep & 1], __float_as_int(cpl));
           // the angle needs no correctly rounded division or square root: the rotation is applied
           // with c = rsqrt(1 + t^2), s = c t whatever t is, and the polar step at the end restores
           // orthonormality; the hardware reciprocal and rsqrt keep the critical path short
@@ -1835,6 +1892,7 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
       __syncthreads();
     }
     if (!__syncthreads_or(rotated)) break;
+    if (__int_as_float(cmax[sweep & 1]) <= cstop) break;
   }
   // every sweep ends with player q at position q: columns are X's columns, rotated
   const float* fin = cur ? buf1 : buf0;
@@ -2555,7 +2613,15 @@ rh_status launch_cast(const double* src, T* dst, int64_t n, cudaStream_t st, int
   return RH_OK;
 }
 
-rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st) {
+rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st, double* part, size_t part_elems) {
+  if (part != nullptr && part_elems >= 2 && n > 16384) {
+    const int64_t G = std::min<int64_t>(std::min<int64_t>((int64_t)part_elems, 256), ceil_div(n, 4096));
+    const int64_t chunk = ceil_div(n, G);
+    const int64_t gg = ceil_div(n, chunk);
+    RH_EMIT(SumsqPartOp, SITE_FINAL, 0, (int)gg, 0, x, n, chunk, part);
+    RH_EMIT(SumPartsOp, SITE_FINAL, 1, 1, 0, part, (int)gg, out);
+    return RH_OK;
+  }
   RH_EMIT(SumsqOp, SITE_FINAL, 0, 1, 0, x, n, out);
   return RH_OK;
 }
