@@ -494,51 +494,75 @@ __device__ __forceinline__ void SketchReduceOp<T>::body(const Grid g, const Args
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t c = g.by;
   const int64_t i = (int64_t)g.bx * 32 + lane;
-  double s = 0.0;
-  if (i < I) {
-    const T* src = part + c * I + i;
-    const int64_t step = (int64_t)ell * I;
-    int k = w;
-    // eight independent chains per lane (loads in flight together), combined in a fixed order
-    if constexpr (sizeof(T) == 4) {
-      // FP32 partials: each chain is an FP32 sum that keeps its rounding errors (Knuth's TwoSum,
-      // every error exact), so the chain's value hi + lo carries ~2^-44 relative error at FP32
-      // arithmetic rate (FP64 runs at a small fraction of it on this part)
+  if constexpr (sizeof(T) == 4) {
+    // FP32 partials, summed in FP32 pairs (hi, lo) that keep every rounding error (Knuth's TwoSum):
+    // ~2^-44 relative error at FP32 arithmetic rate, converted to FP64 once per output (FP64 runs
+    // at a small fraction of the FP32 rate on this part).  Eight chains per lane (loads in flight
+    // together) and the eight warps are combined in a fixed order, so the result is deterministic.
+    __shared__ float redh[kRedWarps][33], redl[kRedWarps][33];
+    auto acc = [](float& h, float& l, float v) {
+      const float t = __fadd_rn(h, v);
+      const float bp = __fsub_rn(t, h);
+      l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+      h = t;
+    };
+    float H = 0.0f, L = 0.0f;
+    if (i < I) {
+      const T* src = part + c * I + i;
+      const int64_t step = (int64_t)ell * I;
+      int k = w;
       float hi[8], lo[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0.0f;
-      auto acc = [](float& h, float& l, float v) {
-        const float t = __fadd_rn(h, v);
-        const float bp = __fsub_rn(t, h);
-        l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
-        h = t;
-      };
       for (; k + 7 * kRedWarps < S; k += 8 * kRedWarps) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc(hi[j], lo[j], (float)src[(int64_t)(k + j * kRedWarps) * step]);
       }
       for (; k < S; k += kRedWarps) acc(hi[0], lo[0], (float)src[(int64_t)k * step]);
-      double c[8];
+      H = hi[0];
+      L = lo[0];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) c[j] = (double)hi[j] + (double)lo[j];
-      s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
-    } else {
-      double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int j = 1; j < 8; ++j) {
+        acc(H, L, hi[j]);
+        L = __fadd_rn(L, lo[j]);
+      }
+    }
+    redh[w][lane] = H;
+    redl[w][lane] = L;
+    __syncthreads();
+    if (w == 0 && i < I) {
+      float h = redh[0][lane], l = redl[0][lane];
+#pragma unroll
+      for (int j = 1; j < kRedWarps; ++j) {
+        acc(h, l, redh[j][lane]);
+        l = __fadd_rn(l, redl[j][lane]);
+      }
+      const double t = (double)h + (double)l;
+      Y[i + I * c] = args.accumulate ? Y[i + I * c] + t : t;
+    }
+  } else {
+    double s = 0.0;
+    if (i < I) {
+      const T* src = part + c * I + i;
+      const int64_t step = (int64_t)ell * I;
+      int k = w;
+      // eight independent chains per lane (loads in flight together), combined in a fixed order
+      double cc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       for (; k + 7 * kRedWarps < S; k += 8 * kRedWarps) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) c[j] += (double)src[(int64_t)(k + j * kRedWarps) * step];
+        for (int j = 0; j < 8; ++j) cc[j] += (double)src[(int64_t)(k + j * kRedWarps) * step];
       }
-      for (; k < S; k += kRedWarps) c[0] += (double)src[(int64_t)k * step];
-      s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+      for (; k < S; k += kRedWarps) cc[0] += (double)src[(int64_t)k * step];
+      s = ((cc[0] + cc[1]) + (cc[2] + cc[3])) + ((cc[4] + cc[5]) + (cc[6] + cc[7]));
     }
-  }
-  red[w][lane] = s;
-  __syncthreads();
-  if (w == 0 && i < I) {
-    double t = red[0][lane];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < I) {
+      double t = red[0][lane];
 #pragma unroll
-    for (int j = 1; j < kRedWarps; ++j) t += red[j][lane];
-    Y[i + I * c] = args.accumulate ? Y[i + I * c] + t : t;
+      for (int j = 1; j < kRedWarps; ++j) t += red[j][lane];
+      Y[i + I * c] = args.accumulate ? Y[i + I * c] + t : t;
+    }
   }
   if (norm2 != nullptr && g.bx == 0 && g.by == 0) {
     __syncthreads();

@@ -1499,11 +1499,13 @@ __device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args
     }
     cp_async_commit();
   };
-  double accd[4][4];
+  // tile sums accumulate in FP32 pairs (hi, lo) that keep every rounding error (TwoSum): FP64
+  // arithmetic runs at a small fraction of the FP32 rate on this part
+  float acch[4][4], accl[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acch[a][b] = accl[a][b] = 0.0f;
   float* bufs[2] = {gram_sm, gram_sm + 128 * C::LDS};
   int cur = 0;
   __syncthreads();   // padding written before any tile lands next to it
@@ -1553,7 +1555,14 @@ __device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) accd[a][b] += DF ? (double)acc[a][b] + (double)err[a][b] : (double)acc[a][b];
+        for (int b = 0; b < 4; ++b) {
+          const float v = acc[a][b];
+          const float t = __fadd_rn(acch[a][b], v);
+          const float bp = __fsub_rn(t, acch[a][b]);
+          accl[a][b] = __fadd_rn(accl[a][b], __fadd_rn(__fsub_rn(acch[a][b], __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+          acch[a][b] = t;
+          if constexpr (DF) accl[a][b] = __fadd_rn(accl[a][b], err[a][b]);
+        }
     }
     __syncthreads();   // this tile's buffer is refilled two tiles later
     cur ^= 1;
@@ -1565,7 +1574,7 @@ __device__ __forceinline__ void GramBOp<ELLP, DF>::body(const Grid g, const Args
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int r = 4 * bi + a, c = 4 * bj + b;
-      if (r <= c && c < ell) o[r + ell * c] = accd[a][b];
+      if (r <= c && c < ell) o[r + ell * c] = (double)acch[a][b] + (double)accl[a][b];
     }
 }
 
@@ -1759,8 +1768,10 @@ __device__ __forceinline__ void PivotedCholeskyOp::body(const Grid g, const Args
 
 // One-sided Jacobi on the columns of X (n x n, FP32, n <= 64) without accumulating the rotations:
 // at convergence X = U S, so U is read off by normalising the columns.  Same circle schedule and
-// rotation rule as jacobi_svd_kernel, but a warp rotates four pairs at once (eight lanes per pair,
-// each lane holding entries 4l..4l+3 and 32+4l..32+4l+3 of both columns as two 16-byte vectors).
+// rotation rule as jacobi_svd_kernel; the sweeps run in four warps, a group of four lanes per pair
+// (a two-step shuffle reduction of each product, a 128-thread barrier per round).  Eight lanes per
+// pair over eight warps with a block barrier per round took 193 us for n = 60, one lane per pair
+// in one warp (no reduction, issue-bound on one scheduler) 257 us.
 // Sweeps end when one rotates nothing, or when the largest coupling it rotated was at most
 // sqrt(tol / n) (the quadratic convergence of the cyclic Jacobi method then leaves every coupling
 // of the next sweep below tol, so that sweep is not run).
@@ -1768,6 +1779,10 @@ __device__ __forceinline__ void PivotedCholeskyOp::body(const Grid g, const Args
 // rounding by one polar correction U <- U (3 I - U^T U) / 2 (the Jacobi tolerance leaves
 // |u_i^T u_j| <= tol).  Writes Ub (n x n, FP64) and sv = the column norms (FP64), sorted.
 constexpr int kRowJacThreads = 256;
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 struct JacobiRowsOp {
   struct Args {
@@ -1796,64 +1811,76 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
   extern __shared__ __align__(16) float jsm[];
   const int np = (n + 1) & ~1;
   const int half = np / 2;
-  float* buf0 = jsm;                    // [position][64]
-  float* buf1 = buf0 + 64 * 64;
-  float* U = buf1 + 64 * 64;            // [64][65]: U(i, c) at i + 65 c
+  // columns by position, rows padded to kLdb floats (320 bytes): the two pair groups of a 16-byte
+  // access phase read two neighbouring columns at one offset and land on disjoint banks
+  constexpr int kLdb = 80;
+  float* buf0 = jsm;                    // [position][kLdb]
+  float* buf1 = buf0 + 64 * kLdb;
+  float* U = buf1 + 64 * kLdb;          // [64][65]: U(i, c) at i + 65 c
   float* E = U + 64 * 65;               // [64][65]
   __shared__ float nrm2[2][RH_MAX_ELL];
   __shared__ float sig[RH_MAX_ELL];
   __shared__ int rankof[RH_MAX_ELL];
-  __shared__ int cmax[2];   // per sweep (two slots): largest |g| / sqrt(al be) rotated, as FP32 bits
+  __shared__ int s_cur;
+  __shared__ unsigned s_red[2][4];      // per sweep-warp: any rotation, largest rotated coupling
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int e = t; e < 64 * 64; e += blockDim.x) {
     const int i = e & 63, q = e >> 6;
-    buf0[e] = (q < n && i < n) ? Xin[i + n * q] : 0.0f;
+    buf0[kLdb * q + i] = (q < n && i < n) ? Xin[i + n * q] : 0.0f;
   }
-  if (t < 2) cmax[t] = 0;
   __syncthreads();
   const float tol = (float)(8 * (n > 8 ? n : 8)) * 5.9604645e-8f;
   // Quadratic convergence: a sweep whose largest rotated coupling is c leaves couplings of order
   // c^2, so once c <= sqrt(tol / n) the next sweep would rotate nothing and is skipped.
   const float cstop = sqrtf(tol / (float)(n > 1 ? n : 1));
-  const int grp = lane >> 3, l = lane & 7;
-  const int pr = 4 * w + grp;           // pair index of this lane group
-  const bool active = pr < half;
-  const int qa = pr, qb = np - 1 - pr;
-  const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
-  const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
-  int cur = 0;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    {
-      const float* src = cur ? buf1 : buf0;
-      for (int q = w; q < np; q += blockDim.x >> 5) {
-        const float a = src[64 * q + lane], b = src[64 * q + 32 + lane];
-        float v = a * a + b * b;
+  // The sweeps run in warps 0..3 (one per scheduler) with a 128-thread barrier between rounds; a
+  // group of four lanes rotates one pair, lane l holding entries 4l..4l+3 + 16m (m < 4) of both
+  // columns.  The other warps wait for the epilogue.
+  if (w < 4) {
+    const int grp = lane >> 2, l = lane & 3;
+    const int pr = 8 * w + grp;
+    const bool active = pr < half;
+    const int qa = active ? pr : 0, qb = active ? np - 1 - pr : 0;
+    const int na = (qa == 0) ? 0 : (qa == np - 1 ? 1 : qa + 1);
+    const int nb = (qb == 0) ? 0 : (qb == np - 1 ? 1 : qb + 1);
+    int cur = 0;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      {
+        const float* src = cur ? buf1 : buf0;
+        for (int q = w; q < np; q += 4) {
+          const float x0 = src[kLdb * q + lane], x1 = src[kLdb * q + 32 + lane];
+          float v = x0 * x0 + x1 * x1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) nrm2[cur][q] = v;
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) nrm2[cur][q] = v;
+        }
+        named_bar_sync(1, 128);
       }
-      __syncthreads();
-      if (t == 0) cmax[(sweep + 1) & 1] = 0;   // every thread has read the previous sweep's slot
-    }
-    int rotated = 0;
-    for (int rnd = 0; rnd < np - 1; ++rnd) {
-      const float* src = cur ? buf1 : buf0;
-      float* dst = cur ? buf0 : buf1;
-      if (w * 4 < half) {
-        const int qa_ = active ? qa : 0, qb_ = active ? qb : 0;
-        float4 a0 = *reinterpret_cast<const float4*>(src + 64 * qa_ + 4 * l);
-        float4 a1 = *reinterpret_cast<const float4*>(src + 64 * qa_ + 32 + 4 * l);
-        float4 b0 = *reinterpret_cast<const float4*>(src + 64 * qb_ + 4 * l);
-        float4 b1 = *reinterpret_cast<const float4*>(src + 64 * qb_ + 32 + 4 * l);
-        float al = nrm2[cur][qa_], be = nrm2[cur][qb_];
-        float g = a0.x * b0.x + a0.y * b0.y + a0.z * b0.z + a0.w * b0.w + a1.x * b1.x + a1.y * b1.y + a1.z * b1.z +
-                  a1.w * b1.w;
+      int rotated = 0;
+      float cmx = 0.0f;
+      for (int rnd = 0; rnd < np - 1; ++rnd) {
+        const float* src = cur ? buf1 : buf0;
+        float* dst = cur ? buf0 : buf1;
+        float4 a[4], b[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          a[m] = *reinterpret_cast<const float4*>(src + kLdb * qa + 4 * l + 16 * m);
+          b[m] = *reinterpret_cast<const float4*>(src + kLdb * qb + 4 * l + 16 * m);
+        }
+        float al = nrm2[cur][qa], be = nrm2[cur][qb];
+        float g0 = 0.0f, g1 = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          g0 = fmaf(a[m].x, b[m].x, g0);
+          g1 = fmaf(a[m].y, b[m].y, g1);
+          g0 = fmaf(a[m].z, b[m].z, g0);
+          g1 = fmaf(a[m].w, b[m].w, g1);
+        }
+        float g = g0 + g1;
         g += __shfl_xor_sync(0xffffffffu, g, 1);
         g += __shfl_xor_sync(0xffffffffu, g, 2);
-        g += __shfl_xor_sync(0xffffffffu, g, 4);
         const float cpl = fabsf(g) * rsqrtf(al) * rsqrtf(be);
         if (active && g != 0.0f && cpl > tol) {
-          if (l == 0) atomicMax(&cmax[sweep & 1], __float_as_int(cpl));
           // the angle needs no correctly rounded division or square root: the rotation is applied
           // with c = rsqrt(1 + t^2), s = c t whatever t is, and the polar step at the end restores
           // orthonormality; the hardware reciprocal and rsqrt keep the critical path short
@@ -1864,40 +1891,53 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
           const float tt = zeta < 0.0f ? -tm : tm;
           const float c = rsqrtf(fmaf(tt, tt, 1.0f));
           const float sn = c * tt;
-          float u;
-          u = a0.x; a0.x = c * u - sn * b0.x; b0.x = sn * u + c * b0.x;
-          u = a0.y; a0.y = c * u - sn * b0.y; b0.y = sn * u + c * b0.y;
-          u = a0.z; a0.z = c * u - sn * b0.z; b0.z = sn * u + c * b0.z;
-          u = a0.w; a0.w = c * u - sn * b0.w; b0.w = sn * u + c * b0.w;
-          u = a1.x; a1.x = c * u - sn * b1.x; b1.x = sn * u + c * b1.x;
-          u = a1.y; a1.y = c * u - sn * b1.y; b1.y = sn * u + c * b1.y;
-          u = a1.z; a1.z = c * u - sn * b1.z; b1.z = sn * u + c * b1.z;
-          u = a1.w; a1.w = c * u - sn * b1.w; b1.w = sn * u + c * b1.w;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            float u;
+            u = a[m].x; a[m].x = c * u - sn * b[m].x; b[m].x = sn * u + c * b[m].x;
+            u = a[m].y; a[m].y = c * u - sn * b[m].y; b[m].y = sn * u + c * b[m].y;
+            u = a[m].z; a[m].z = c * u - sn * b[m].z; b[m].z = sn * u + c * b[m].z;
+            u = a[m].w; a[m].w = c * u - sn * b[m].w; b[m].w = sn * u + c * b[m].w;
+          }
           al = al - tt * g;
           be = be + tt * g;
           rotated = 1;
+          cmx = fmaxf(cmx, cpl);
         }
         if (active) {
-          *reinterpret_cast<float4*>(dst + 64 * na + 4 * l) = a0;
-          *reinterpret_cast<float4*>(dst + 64 * na + 32 + 4 * l) = a1;
-          *reinterpret_cast<float4*>(dst + 64 * nb + 4 * l) = b0;
-          *reinterpret_cast<float4*>(dst + 64 * nb + 32 + 4 * l) = b1;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            *reinterpret_cast<float4*>(dst + kLdb * na + 4 * l + 16 * m) = a[m];
+            *reinterpret_cast<float4*>(dst + kLdb * nb + 4 * l + 16 * m) = b[m];
+          }
           if (l == 0) {
             nrm2[cur ^ 1][na] = al;
             nrm2[cur ^ 1][nb] = be;
           }
         }
+        cur ^= 1;
+        named_bar_sync(1, 128);
       }
-      cur ^= 1;
-      __syncthreads();
+      // couplings are >= 0: their FP32 bit patterns order like the values
+      const unsigned anyw = __any_sync(0xffffffffu, rotated);
+      const unsigned mxw = __reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(cmx));
+      if (lane == 0) {
+        s_red[0][w] = anyw;
+        s_red[1][w] = mxw;
+      }
+      named_bar_sync(1, 128);
+      const unsigned any4 = s_red[0][0] | s_red[0][1] | s_red[0][2] | s_red[0][3];
+      const unsigned mx4 = max(max(s_red[1][0], s_red[1][1]), max(s_red[1][2], s_red[1][3]));
+      if (!any4 || __int_as_float((int)mx4) <= cstop) break;
     }
-    if (!__syncthreads_or(rotated)) break;
-    if (__int_as_float(cmax[sweep & 1]) <= cstop) break;
+    if (t == 0) s_cur = cur;
   }
+  __syncthreads();
+  const int cur = s_cur;
   // every sweep ends with player q at position q: columns are X's columns, rotated
   const float* fin = cur ? buf1 : buf0;
   for (int q = w; q < n; q += blockDim.x >> 5) {
-    const float a = fin[64 * q + lane], b = fin[64 * q + 32 + lane];
+    const float a = fin[kLdb * q + lane], b = fin[kLdb * q + 32 + lane];
     float v = a * a + b * b;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1914,7 +1954,7 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
   for (int e = t; e < n * n; e += blockDim.x) {
     const int i = e % n, q = e / n;
     const float s = sig[q];
-    U[i + 65 * rankof[q]] = s > 0.0f ? fin[64 * q + i] / s : (i == q ? 1.0f : 0.0f);
+    U[i + 65 * rankof[q]] = s > 0.0f ? fin[kLdb * q + i] / s : (i == q ? 1.0f : 0.0f);
   }
   __syncthreads();
   // polar correction: E = U^T U, U <- 1.5 U - 0.5 U E
@@ -2394,7 +2434,7 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
                              SITE_TRUNC_GRAM)) != RH_OK)
       return s;
     RH_EMIT(PivotedCholeskyOp, SITE_TRUNC_PCHOL, 0, 1, chol_smem(n, sizeof(dfl::F2)), W, n, Rf, flags, nullptr);
-    const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
+    const size_t smr = sizeof(float) * (2 * 64 * 80 + 2 * 64 * 65);
     {
       ProfileScope ps(PROF_JACOBI, 0, st);
       RH_EMIT(JacobiRowsOp, SITE_TRUNC_JACOBI, 0, 1, smr, Rf, n, Ub, sv, flags, nullptr, 0);
@@ -2584,7 +2624,7 @@ rh_status launch_trunc_leading_svd(int n, int k, bool gram, const double* W, con
     copy_leading_kernel<double, double><<<blocks, 256, 0, st>>>(W, n, k, Wk);
     RH_LAUNCH_CHECK();
     RH_EMIT(PivotedCholeskyOp, SITE_OTHER, 0, 1, chol_smem(k, sizeof(dfl::F2)), Wk, k, Xf, flag, nullptr);
-    const size_t smr = sizeof(float) * (2 * 64 * 64 + 2 * 64 * 65);
+    const size_t smr = sizeof(float) * (2 * 64 * 80 + 2 * 64 * 65);
     RH_EMIT(JacobiRowsOp, SITE_OTHER, 0, 1, smr, Xf, k, Ub, sv, flag, nullptr, 0);
     return RH_OK;
   }
