@@ -7,8 +7,9 @@
 // Both are grouped operations (a body over block coordinates), so a batch of small tensors runs
 // each stage as one launch.  A TMA tile of X_(1) would need its rows (I values) to be a multiple of
 // 16 bytes; here every thread reads consecutive elements of the contiguous column run of its tile
-// with plain coalesced loads instead (any I), converts them into the BF16 operand layout in shared
-// memory, and one thread issues the MMAs.  The next tile's loads are in registers while the current
+// with plain loads instead (any I), eight consecutive rows of one column at a time, converts them
+// into the BF16 operand layout in shared memory (one 16-byte unit per piece), and one thread issues
+// the MMAs.  The next tile's loads are in registers while the current
 // tile is multiplied.
 //
 //   sketch   part[by](i, c) = sum over the CTA's columns p of X(i, p) Omega(p, c):
@@ -43,78 +44,87 @@ struct SmallSrc {
   const float* scales;    // E4M3: the block scales
 };
 
-// Raw bits of the tile's elements as 32-bit registers: the FP32 bits, the BF16 bits, head | tail << 16,
-// or the FP32 bits of the dequantized E4M3 value.  Element e = tid + NT j of a tile of columns
-// p0 .. p0 + nv - 1 (nv valid) is (k, i) = (e / I, e % I); zero outside the tensor.
-template <int IN, int PER, int NT>
-__device__ __forceinline__ void small_load(uint32_t (&xr)[PER], const SmallSrc& src, int64_t I, int64_t p0, int64_t nv,
-                                           int k, int i, int dk, int di) {
+// Eight consecutive rows i0 .. i0 + 7 of column p of X_(1) as raw 32-bit registers: the FP32 bits,
+// the BF16 bits, head | tail << 16 (two pieces), or the FP32 bits of the dequantized E4M3 value;
+// rows >= I and a column outside the tensor (valid = false) read as zero.
+template <int IN>
+__device__ __forceinline__ void chunk_load(uint32_t (&r)[8], const SmallSrc& src, int64_t I, int64_t p, int i0,
+                                           bool valid) {
+  const int lim = valid ? (int)min((int64_t)8, I - i0) : 0;
   if constexpr (IN == kSmFp8) {
     const uint8_t* x8 = static_cast<const uint8_t*>(src.X);
-    const int Ii = (int)I;
+    const int64_t b0 = src.ld * p + i0;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      uint32_t r = 0u;
-      if (k < nv) {
-        const int64_t b = src.ld * (p0 + k) + i;
-        r = __float_as_uint(__fmul_rn(tc::e4m3_to_f32(__ldg(x8 + b)), __ldg(src.scales + (b >> 7))));
-      }
-      xr[j] = r;
-      i += di;
-      k += dk;
-      if (i >= Ii) {
-        i -= Ii;
-        ++k;
-      }
-    }
+    for (int j = 0; j < 8; ++j)
+      r[j] = j < lim ? __float_as_uint(__fmul_rn(tc::e4m3_to_f32(__ldg(x8 + b0 + j)), __ldg(src.scales + ((b0 + j) >> 7))))
+                     : 0u;
   } else {
-    const int64_t lim = nv * I, o = I * p0;
+    const int64_t e0 = I * p + i0;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int e = (int)threadIdx.x + NT * j;
-      uint32_t r = 0u;
-      if (e < lim) {
+    for (int j = 0; j < 8; ++j) {
+      uint32_t v = 0u;
+      if (j < lim) {
         if constexpr (IN == kSmF32) {
-          r = __float_as_uint(__ldg(static_cast<const float*>(src.X) + o + e));
+          v = __float_as_uint(__ldg(static_cast<const float*>(src.X) + e0 + j));
         } else if constexpr (IN == kSmBf16) {
-          r = (uint32_t)__ldg(static_cast<const unsigned short*>(src.X) + o + e);
+          v = (uint32_t)__ldg(static_cast<const unsigned short*>(src.X) + e0 + j);
         } else {
           const unsigned short* q = static_cast<const unsigned short*>(src.X);
-          r = (uint32_t)__ldg(q + o + e) | ((uint32_t)__ldg(q + src.n + o + e) << 16);
+          v = (uint32_t)__ldg(q + e0 + j) | ((uint32_t)__ldg(q + src.n + e0 + j) << 16);
         }
       }
-      xr[j] = r;
+      r[j] = v;
     }
   }
 }
 
-// Write the element with raw bits r into the piece(s) at byte offset off (the tail piece of the FP32
-// split is bf16(x - head), so head + tail holds the 16 leading significant bits of x); returns the
-// value represented.
+// A chunk's eight values written as one 16-byte unit per piece at byte offset off: FP32 split into
+// head bf16(x) and tail bf16(x - head) (ties to even, packed conversions; head + tail holds the 16
+// leading significant bits of x), E4M3 values rounded to one piece, BF16 values and given pieces as
+// they are.  Returns the sum of the squares of the values represented.
 template <int IN>
-__device__ __forceinline__ float small_put(uint8_t* p0, uint8_t* p1, uint32_t off, uint32_t r) {
-  if constexpr (IN == kSmF32) {
-    const float x = __uint_as_float(r);
-    const uint16_t h = tc::bf16_rne(x);
-    const float hf = tc::bf16_to_f(h);
-    const uint16_t t = tc::bf16_rne(x - hf);
-    *reinterpret_cast<uint16_t*>(p0 + off) = h;
-    *reinterpret_cast<uint16_t*>(p1 + off) = t;
-    return hf + tc::bf16_to_f(t);
+__device__ __forceinline__ float chunk_put(uint8_t* p0, uint8_t* p1, uint32_t off, const uint32_t (&r)[8]) {
+  uint32_t h[4], t[4];
+  float ss = 0.0f;
+  if constexpr (IN == kSmF32 || IN == kSmFp8) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x0 = __uint_as_float(r[2 * q]), x1 = __uint_as_float(r[2 * q + 1]);
+      h[q] = tc::pack_bf16x2(x0, x1);
+      const float h0 = __uint_as_float(h[q] << 16), h1 = __uint_as_float(h[q] & 0xFFFF0000u);
+      if constexpr (IN == kSmF32) {
+        t[q] = tc::pack_bf16x2(x0 - h0, x1 - h1);
+        const float g0 = h0 + __uint_as_float(t[q] << 16), g1 = h1 + __uint_as_float(t[q] & 0xFFFF0000u);
+        ss = fmaf(g0, g0, ss);
+        ss = fmaf(g1, g1, ss);
+      } else {
+        ss = fmaf(h0, h0, ss);
+        ss = fmaf(h1, h1, ss);
+      }
+    }
   } else if constexpr (IN == kSmBf16) {
-    (void)p1;
-    *reinterpret_cast<uint16_t*>(p0 + off) = (uint16_t)r;
-    return tc::bf16_to_f((uint16_t)r);
-  } else if constexpr (IN == kSmPieces) {
-    *reinterpret_cast<uint16_t*>(p0 + off) = (uint16_t)(r & 0xFFFFu);
-    *reinterpret_cast<uint16_t*>(p1 + off) = (uint16_t)(r >> 16);
-    return tc::bf16_to_f((uint16_t)(r & 0xFFFFu)) + tc::bf16_to_f((uint16_t)(r >> 16));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      h[q] = r[2 * q] | (r[2 * q + 1] << 16);
+      const float h0 = __uint_as_float(h[q] << 16), h1 = __uint_as_float(h[q] & 0xFFFF0000u);
+      ss = fmaf(h0, h0, ss);
+      ss = fmaf(h1, h1, ss);
+    }
   } else {
-    (void)p1;
-    const uint16_t h = tc::bf16_rne(__uint_as_float(r));
-    *reinterpret_cast<uint16_t*>(p0 + off) = h;
-    return tc::bf16_to_f(h);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      h[q] = (r[2 * q] & 0xFFFFu) | (r[2 * q + 1] << 16);
+      t[q] = (r[2 * q] >> 16) | (r[2 * q + 1] & 0xFFFF0000u);
+      const float g0 = __uint_as_float(h[q] << 16) + __uint_as_float(t[q] << 16);
+      const float g1 = __uint_as_float(h[q] & 0xFFFF0000u) + __uint_as_float(t[q] & 0xFFFF0000u);
+      ss = fmaf(g0, g0, ss);
+      ss = fmaf(g1, g1, ss);
+    }
   }
+  *reinterpret_cast<uint4*>(p0 + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  if constexpr (IN == kSmF32 || IN == kSmPieces) *reinterpret_cast<uint4*>(p1 + off) = make_uint4(t[0], t[1], t[2], t[3]);
+  else (void)p1;
+  return ss;
 }
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
@@ -132,8 +142,8 @@ struct SmallTcSketchArgs {
   float* part;            // [S][ell][I]
   double* part_norm;      // [S] (NULL: no norm)
   int32_t* err;
-  int32_t d256, r256;     // 256 = d256 I + r256
-  FastDiv fI;
+  int32_t nch, dnc, rnc;  // chunks of eight rows per column; 256 = dnc nch + rnc
+  FastDiv fN;
   int32_t probe;          // wait-timeout probe (test support): wait on a barrier nothing arrives at
 };
 
@@ -143,7 +153,7 @@ struct SmallTcSketchOp {
   static constexpr int kThreads = 256, kMinBlocks = TI == 128 ? 2 : 3;
   static constexpr int NP = (IN == kSmBf16 || IN == kSmFp8) ? 1 : 2;
   static constexpr int KT = 64;                         // columns per tile
-  static constexpr int PER = KT * TI / 256;             // elements per thread per tile (bound)
+  static constexpr int ITEMS = KT * (TI / 8) / 256;     // eight-row chunks per thread per tile (bound)
   static constexpr uint32_t kPiece = 128 * KT * 2;      // 128 rows x 64 columns BF16
   static constexpr uint32_t kOm = 32 * KT * 2;          // up to 32 Omega columns x 64 rows BF16
   static constexpr size_t kDynSmem = 1024 + NP * kPiece + 2 * kOm + 64;
@@ -153,7 +163,7 @@ struct SmallTcSketchOp {
 template <int IN, int TI>
 __device__ __forceinline__ void SmallTcSketchOp<IN, TI>::body(const Grid g, const Args& a) {
   using Op = SmallTcSketchOp<IN, TI>;
-  constexpr int KT = Op::KT, PER = Op::PER, NP = Op::NP;
+  constexpr int KT = Op::KT, ITEMS = Op::ITEMS, NP = Op::NP;
   constexpr uint32_t kPiece = Op::kPiece, kOm = Op::kOm;
   extern __shared__ uint8_t dsm_raw[];
   uint8_t* base = align1024(dsm_raw);
@@ -194,30 +204,41 @@ __device__ __forceinline__ void SmallTcSketchOp<IN, TI>::body(const Grid g, cons
   tc::tc_fence_after();
   const uint32_t tmem = *slot;
 
-  // this thread's first element of a tile: e = tid -> (k, i); later ones step by 256 = d256 I + r256
-  const int k_first = (int)a.fI.div((uint32_t)tid);
-  const int i_first = tid - k_first * Ii;
-  uint32_t xr[PER];
+  // items of a tile: chunks of eight rows (ch) of one column (k); item u = tid + 256 j is
+  // (k, ch) = (u / nch, u % nch), later ones step by 256 = dnc nch + rnc
+  const int nch = a.nch;
+  const int k_first = (int)a.fN.div((uint32_t)tid);
+  const int c_first = tid - k_first * nch;
+  uint32_t xr[ITEMS][8];
   auto load = [&](int64_t p0) {
-    small_load<IN, PER, 256>(xr, a.src, I, p0, min(pe, p0 + KT) - p0, k_first, i_first, a.d256, a.r256);
+    const int64_t nv = min(pe, p0 + KT) - p0;
+    int k = k_first, ch = c_first;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      if (k < KT) chunk_load<IN>(xr[j], a.src, I, p0 + k, 8 * ch, k < nv);
+      ch += a.rnc;
+      k += a.dnc;
+      if (ch >= nch) {
+        ch -= nch;
+        ++k;
+      }
+    }
   };
-  // element (i, k) of the MN-major 128-byte-swizzled pieces: two 64-row halves of 64 x 128 B
+  // chunk (ch, k) of the MN-major 128-byte-swizzled pieces (two 64-row halves of 64 x 128 B) is the
+  // 16-byte unit at (ch / 8) 8192 + 128 k + ((ch % 8) ^ (k % 8)) 16
   auto store = [&]() {
     float ss = 0.f;
-    int k = k_first, i = i_first;
+    int k = k_first, ch = c_first;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
       if (k < KT) {
-        const int il = i & 63;
-        const uint32_t off =
-            (uint32_t)((i >> 6) * 8192 + k * 128 + ((((il >> 3) ^ (k & 7))) << 4) + ((il & 7) << 1));
-        const float r = small_put<IN>(xs0, xs1, off, xr[j]);
-        ss = fmaf(r, r, ss);
+        const uint32_t off = (uint32_t)((ch >> 3) * 8192 + k * 128 + (((ch & 7) ^ (k & 7)) << 4));
+        ss += chunk_put<IN>(xs0, xs1, off, xr[j]);
       }
-      i += a.r256;
-      k += a.d256;
-      if (i >= Ii) {
-        i -= Ii;
+      ch += a.rnc;
+      k += a.dnc;
+      if (ch >= nch) {
+        ch -= nch;
         ++k;
       }
     }
@@ -318,8 +339,8 @@ struct SmallTcTtmArgs {
   float* B;               // B[c + ell p]
   int64_t tiles_per_cta;  // 128-column tiles
   int32_t* err;
-  int32_t dnt, rnt;       // the block size = dnt I + rnt
-  FastDiv fI;
+  int32_t nch, dnc, rnc;  // chunks of eight rows per column; the block size = dnc nch + rnc
+  FastDiv fN;
   int32_t probe;
 };
 
@@ -331,7 +352,7 @@ struct SmallTcTtmOp {
   static constexpr int NP = (IN == kSmBf16 || IN == kSmFp8) ? 1 : 2;
   static constexpr int KB = TI > 64 ? 2 : 1;            // 64-wide blocks of K = i
   static constexpr int PT = 128;                        // columns p per tile (the MMA's M)
-  static constexpr int PER = PT * TI / kThreads;
+  static constexpr int ITEMS = PT * (TI / 8) / kThreads;   // eight-row chunks per thread per tile (bound)
   static constexpr uint32_t kPiece = KB * 128 * 128;    // KB blocks of 128 rows x 128 B
   static constexpr uint32_t kQ = KB * 64 * 128;         // [Q_h | Q_t]: up to 64 rows x KB blocks
   static constexpr uint32_t kStage = PT * 32 * 4;       // the tile's output, FP32
@@ -342,7 +363,7 @@ struct SmallTcTtmOp {
 template <int IN, int TI>
 __device__ __forceinline__ void SmallTcTtmOp<IN, TI>::body(const Grid g, const Args& a) {
   using Op = SmallTcTtmOp<IN, TI>;
-  constexpr int PT = Op::PT, PER = Op::PER, NP = Op::NP, KB = Op::KB, NT = Op::kThreads;
+  constexpr int PT = Op::PT, ITEMS = Op::ITEMS, NP = Op::NP, KB = Op::KB, NT = Op::kThreads;
   constexpr uint32_t kPiece = Op::kPiece, kQ = Op::kQ;
   extern __shared__ uint8_t dsm_raw[];
   uint8_t* base = align1024(dsm_raw);
@@ -399,29 +420,42 @@ __device__ __forceinline__ void SmallTcTtmOp<IN, TI>::body(const Grid g, const A
   tc::tc_fence_after();
   const uint32_t tmem = *slot;
 
-  const int k_first = (int)a.fI.div((uint32_t)tid);   // e = tid -> (p = k_first, i = i_first); steps of NT
-  const int i_first = tid - k_first * Ii;
-  uint32_t xr[PER];
+  // items of a tile: chunks of eight rows (ch) of one column (p); item u = tid + NT j is
+  // (p, ch) = (u / nch, u % nch), later ones step by NT = dnc nch + rnc
+  const int nch = a.nch;
+  const int k_first = (int)a.fN.div((uint32_t)tid);
+  const int c_first = tid - k_first * nch;
+  uint32_t xr[ITEMS][8];
   auto load = [&](int64_t tile) {
     const int64_t p0 = tile * PT;
-    small_load<IN, PER, NT>(xr, a.src, I, p0, min(M, p0 + PT) - p0, k_first, i_first, a.dnt, a.rnt);
-  };
-  // element (p, i) of the K-major pieces: (i / 64) 16384 + (p / 8) 1024 + (p % 8) 128 +
-  // ((i % 64 / 8) ^ (p % 8)) 16 + 2 (i % 8)
-  auto store = [&]() {
-    int p = k_first, i = i_first;
+    const int64_t nv = min(M, p0 + PT) - p0;
+    int p = k_first, ch = c_first;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      if (p < PT) {
-        const int il = i & 63;
-        const uint32_t off = (uint32_t)((i >> 6) * 16384 + (p >> 3) * 1024 + (p & 7) * 128 +
-                                        ((((il >> 3) ^ (p & 7))) << 4) + ((il & 7) << 1));
-        (void)small_put<IN>(xs0, xs1, off, xr[j]);
+    for (int j = 0; j < ITEMS; ++j) {
+      if (p < PT) chunk_load<IN>(xr[j], a.src, I, p0 + p, 8 * ch, p < nv);
+      ch += a.rnc;
+      p += a.dnc;
+      if (ch >= nch) {
+        ch -= nch;
+        ++p;
       }
-      i += a.rnt;
-      p += a.dnt;
-      if (i >= Ii) {
-        i -= Ii;
+    }
+  };
+  // chunk (p, ch) of the K-major pieces is the 16-byte unit at (ch / 8) 16384 + (p / 8) 1024 +
+  // (p % 8) 128 + ((ch % 8) ^ (p % 8)) 16
+  auto store = [&]() {
+    int p = k_first, ch = c_first;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      if (p < PT) {
+        const uint32_t off =
+            (uint32_t)((ch >> 3) * 16384 + (p >> 3) * 1024 + (p & 7) * 128 + (((ch & 7) ^ (p & 7)) << 4));
+        (void)chunk_put<IN>(xs0, xs1, off, xr[j]);
+      }
+      ch += a.rnc;
+      p += a.dnc;
+      if (ch >= nch) {
+        ch -= nch;
         ++p;
       }
     }
@@ -538,11 +572,11 @@ rh_status launch_sketch_small_tc(const SketchPlan& pl, const SmallInput& in, uin
     set_error("internal: small-row tensor-core sketch outside its shapes");
     return RH_EUNSUPPORTED;
   }
-  const int Ii = (int)pl.v.I;
+  const int nch = (int)((pl.v.I + 7) / 8);
   const int32_t form = in.form;
   SmallTcSketchArgs a{SmallSrc{in.X, pl.v.I * pl.v.M(), in.ld, in.scales}, pl.v.I, pl.v.M(), pl.ell, pl.ellp, pl.chunk, (uint32_t)(seed & 0xFFFFFFFFu),
-                      (uint32_t)(seed >> 32), sid, pl.row0, part, part_norm, err, 256 / Ii, 256 % Ii,
-                      FastDiv((uint32_t)Ii), tc_probe_next()};
+                      (uint32_t)(seed >> 32), sid, pl.row0, part, part_norm, err, nch, 256 / nch, 256 % nch,
+                      FastDiv((uint32_t)nch), tc_probe_next()};
   if (form == RH_BF16) {
     if (pl.ti == 32) return emit_small_tc_sketch<kSmBf16, 32>(pl, a, st, site);
     if (pl.ti == 64) return emit_small_tc_sketch<kSmBf16, 64>(pl, a, st, site);
@@ -569,7 +603,7 @@ rh_status launch_ttm_small_tc(const ModeView& v, const SmallInput& in, const dou
     set_error("internal: small-row tensor-core mode product outside its shapes");
     return RH_EUNSUPPORTED;
   }
-  const int Ii = (int)v.I;
+  const int nch = (int)((v.I + 7) / 8);
   const int ti = v.I <= 32 ? 32 : (v.I <= 64 ? 64 : 128);
   const int64_t ntiles = ceil_div(v.M(), 128);
   // at least 2 tiles per CTA (the pipeline), at most 2 CTAs per SM
@@ -577,8 +611,8 @@ rh_status launch_ttm_small_tc(const ModeView& v, const SmallInput& in, const dou
   const int64_t tpc = ceil_div(ntiles, ctas);
   const int nt = ti == 128 ? 512 : 256;
   const int32_t form = in.form;
-  const SmallTcTtmArgs a{SmallSrc{in.X, v.I * v.M(), in.ld, in.scales}, v.I, v.M(), Q, ell, ell <= 8 ? 8 : (ell <= 16 ? 16 : 32), B, tpc, err, nt / Ii, nt % Ii,
-                         FastDiv((uint32_t)Ii), tc_probe_next()};
+  const SmallTcTtmArgs a{SmallSrc{in.X, v.I * v.M(), in.ld, in.scales}, v.I, v.M(), Q, ell, ell <= 8 ? 8 : (ell <= 16 ? 16 : 32), B, tpc, err, nch, nt / nch, nt % nch,
+                         FastDiv((uint32_t)nch), tc_probe_next()};
   const int64_t g = ceil_div(ntiles, tpc);
   if (form == RH_BF16) {
     if (ti == 32) return emit_small_tc_ttm<kSmBf16, 32>(g, a, st, site);
