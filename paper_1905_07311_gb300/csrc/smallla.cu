@@ -107,8 +107,9 @@ __device__ __forceinline__ void GramPartialOp::body(const Grid g, const Args& ar
   __syncthreads();
   const int npair = n * (n + 1) / 2;
   for (int e = threadIdx.x; e < npair; e += blockDim.x) {
-    // e -> (j, k), j <= k, column-major upper triangle
-    int k = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    // e -> (j, k), j <= k, column-major upper triangle (an FP32 estimate of k, corrected exactly;
+    // an FP64 square root per entry would cost more than the entry's products on this part)
+    int k = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
     while ((k + 1) * (k + 2) / 2 <= e) ++k;
     while (k * (k + 1) / 2 > e) --k;
     const int j = e - k * (k + 1) / 2;
@@ -118,7 +119,9 @@ __device__ __forceinline__ void GramPartialOp::body(const Grid g, const Args& ar
   }
 }
 
-// C = sum_b Gpart[b] (fixed order), upper triangle; one thread per entry.
+// C = sum_b Gpart[b], upper triangle.  A block of 256 threads owns 32 consecutive entries: warp w
+// sums the partials w, w + 8, ... (eight chains, loads in flight together) and warp 0 adds the eight
+// warp sums in a fixed order, so the result does not depend on timing.
 struct GramReduceOp {
   struct Args {
     const double* Gpart;
@@ -138,13 +141,30 @@ __device__ __forceinline__ void GramReduceOp::body(const Grid g, const Args& arg
   const int32_t* __restrict__ flag = args.flag;
 
   if (flag != nullptr && *flag) return;
-  const int e = g.bx * blockDim.x + threadIdx.x;
-  if (e >= n * n) return;
-  const int j = e % n, k = e / n;
-  if (j > k) return;
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nn = n * n;
+  const int e = g.bx * 32 + lane;
+  const bool upper = e < nn && (e % n) <= (e / n);
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += Gpart[(int64_t)b * n * n + e];
-  C[e] = s;
+  if (upper) {
+    double ch[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int b = w;
+    for (; b + 56 < nb; b += 64) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ch[q] += Gpart[(int64_t)(b + 8 * q) * nn + e];
+    }
+    for (; b < nb; b += 8) ch[0] += Gpart[(int64_t)b * nn + e];
+    s = ((ch[0] + ch[1]) + (ch[2] + ch[3])) + ((ch[4] + ch[5]) + (ch[6] + ch[7]));
+  }
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && upper) {
+    double t = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += red[q][lane];
+    C[e] = t;
+  }
 }
 
 // Arithmetic of the small Cholesky factorizations: FP64, or double-float (about 48 bits on the FP32
@@ -2247,7 +2267,7 @@ rh_status launch_orthonormalize(int64_t m, int n, const double* Y, double* Q, in
   if (s != RH_OK) return s;
   if ((s = emit_memset(SITE_ORTH_ZERO, 1, C, sizeof(double) * n * n, st)) != RH_OK) return s;
   const size_t gsm = sizeof(double) * rb * n;
-  const int rblocks = (int)ceil_div((int64_t)n * n, 256);
+  const int rblocks = (int)ceil_div((int64_t)n * n, 32);
   const int tblocks = (int)std::min<int64_t>(ceil_div(m, 8), 4 * num_sms());
   if (f32) {
     // FP32 data: CholeskyQR2 whose first pass keeps what its stability needs -- the Gram matrix in
