@@ -158,6 +158,23 @@ uint64_t rh_kernel_launches(void);
 void rh_test_wait_probe(int64_t launch);
 
 /*
+ * Launch-shape knobs of the small-tensor kernels (the paper has no counterpart): how many CTAs the
+ * small-row sketches and mode products, and the Gram matrix of B in the truncation, spread one
+ * tensor's work over (a minimum of work per CTA and a maximum of CTAs per SM).  Their defaults are a
+ * table written by the project's tuner (`python -m paper_1905_07311_gb300.tune`) from measurements
+ * of the batched workload.  The setting changes how sums are split over CTAs, so results can differ
+ * in the last bits between settings; calls with the same settings give the same results.
+ *   rh_tuning_count / rh_tuning_name  the knobs (index 0 .. count - 1; NULL out of range).
+ *   rh_tuning_get(name)  the current value, -1 for an unknown name.
+ *   rh_tuning_set(name, value)  value in [1, 4096], or 0 for the table's value; RH_EINVAL otherwise.
+ *   Process-wide; set them between calls, not while a call of another thread plans its launches.
+ */
+int32_t rh_tuning_count(void);
+const char* rh_tuning_name(int32_t index);
+int32_t rh_tuning_get(const char* name);
+rh_status rh_tuning_set(const char* name, int32_t value);
+
+/*
  * Per-launch timing of the main kernels (measurement support, off by default).
  *   rh_profile_enable(1) makes later calls bracket these launches with CUDA events on the
  *   caller's stream: kind 0 the sketch kernel, 1 the mode product B = Q^T G_(n),

@@ -43,6 +43,10 @@ SIGNATURES = {
     "rh_version": (ctypes.c_char_p, []),
     "rh_last_error": (ctypes.c_char_p, []),
     "rh_kernel_launches": (ctypes.c_uint64, []),
+    "rh_tuning_count": (_I32, []),
+    "rh_tuning_name": (ctypes.c_char_p, [_I32]),
+    "rh_tuning_get": (_I32, [ctypes.c_char_p]),
+    "rh_tuning_set": (_I32, [ctypes.c_char_p, _I32]),
     "rh_profile_enable": (None, [_I32]),
     "rh_profile_collect": (_I32, [_P, _P, _P, _I32]),
     "rh_options_default": (None, [ctypes.POINTER(RhOptions)]),

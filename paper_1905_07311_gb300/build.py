@@ -37,7 +37,8 @@ def _sources():
 
 
 def _deps():
-    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "rhosvd.h")]
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(CSRC, "*.inc")))
+            + [os.path.join(ROOT, "include", "rhosvd.h")]
             + [os.path.abspath(__file__)])   # the flags live here
 
 

@@ -88,6 +88,15 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // SM count of the device current at the first call (initialised once, thread-safe); 152 (GB300)
 // when no device answers, as in workspace queries on a machine without a GPU.
+// Launch-shape knobs of the small-tensor kernels (tuning.cu; defaults in tuning_table.inc).
+enum TuneKey : int {
+#define RH_TUNE(key, name, value) key,
+#include "tuning_table.inc"
+#undef RH_TUNE
+  TUNE_COUNT
+};
+int32_t tune(TuneKey k);
+
 inline int num_sms() {
   static const int n = [] {
     int dev = 0, v = 0;

@@ -587,13 +587,15 @@ SketchPlan plan_sketch(const ModeView& v, int ell) {
   pl.ell = ell;
   const int64_t M = v.M();
   if (v.I <= 128 && ell <= 32 && M < (int64_t(1) << 31)) {
-    // small-row kernel: one row tile; at least 8 k-steps per CTA, about 6 CTAs per SM at most
+    // small-row kernel: one row tile; at least tune(min_steps) k-steps per CTA, tune(ctas_per_sm)
+    // CTAs per SM at most (tuning_table.inc)
     pl.ti = v.I <= 32 ? 32 : (v.I <= 64 ? 64 : 128);
     pl.ellp = ell <= 8 ? 8 : (ell <= 16 ? 16 : 32);
     pl.gx = 1;
     const int64_t kp = 4096 / pl.ti;   // FP32 tile columns (a multiple of the FP64 ones)
     const int64_t ksteps = ceil_div(M, kp);
-    const int64_t S = std::max<int64_t>(1, std::min<int64_t>(6LL * num_sms(), ceil_div(ksteps, 8)));
+    const int64_t S = std::max<int64_t>(1, std::min<int64_t>((int64_t)tune(TUNE_SKETCH_SMALL_CTAS_PER_SM) * num_sms(),
+                                                             ceil_div(ksteps, tune(TUNE_SKETCH_SMALL_MIN_STEPS))));
     pl.chunk = ceil_div(ksteps, S) * kp;
     pl.S = (int)ceil_div(M, pl.chunk);
     return pl;

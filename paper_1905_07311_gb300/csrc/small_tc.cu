@@ -559,8 +559,9 @@ SketchPlan plan_sketch_small_tc(const ModeView& v, int ell) {
   pl.gx = 1;
   pl.ti = v.I <= 32 ? 32 : (v.I <= 64 ? 64 : 128);
   const int64_t tiles = ceil_div(v.M(), 64);
-  // at least 4 tiles per CTA, about 4 CTAs per SM at most
-  const int64_t S = std::max<int64_t>(1, std::min<int64_t>(4LL * num_sms(), ceil_div(tiles, 4)));
+  // at least tune(min_tiles) tiles per CTA, tune(ctas_per_sm) CTAs per SM at most (tuning_table.inc)
+  const int64_t S = std::max<int64_t>(1, std::min<int64_t>((int64_t)tune(TUNE_SMALL_TC_SKETCH_CTAS_PER_SM) * num_sms(),
+                                                           ceil_div(tiles, tune(TUNE_SMALL_TC_SKETCH_MIN_TILES))));
   pl.chunk = ceil_div(tiles, S) * 64;
   pl.S = (int)ceil_div(v.M(), pl.chunk);
   return pl;
@@ -606,8 +607,9 @@ rh_status launch_ttm_small_tc(const ModeView& v, const SmallInput& in, const dou
   const int nch = (int)((v.I + 7) / 8);
   const int ti = v.I <= 32 ? 32 : (v.I <= 64 ? 64 : 128);
   const int64_t ntiles = ceil_div(v.M(), 128);
-  // at least 2 tiles per CTA (the pipeline), at most 2 CTAs per SM
-  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((ti == 128 ? 1LL : 2LL) * num_sms(), ceil_div(ntiles, 2)));
+  // at least tune(min_tiles) tiles per CTA (two keep the pipeline busy), at most the resident CTAs
+  const int64_t ctas = std::max<int64_t>(
+      1, std::min<int64_t>((ti == 128 ? 1LL : 2LL) * num_sms(), ceil_div(ntiles, tune(TUNE_SMALL_TC_TTM_MIN_TILES))));
   const int64_t tpc = ceil_div(ntiles, ctas);
   const int nt = ti == 128 ? 512 : 256;
   const int32_t form = in.form;

@@ -2351,11 +2351,12 @@ int gram_ctas() { return 3 * num_sms(); }
 rh_status launch_gram_f32(const float* B, int64_t L, int64_t R, int ell, double* part, double* W,
                           const int32_t* gate, cudaStream_t st, bool df, int site) {
   const int64_t ntiles = ceil_div(L * R, 128);
-  // one CTA per SM at least (a single matrix fills the GPU), beyond that at least eight tiles per
+  // one CTA per SM at least (a single matrix fills the GPU), beyond that at least tune(min_tiles) per
   // CTA: a CTA's set-up and its ell^2 FP64 partial (written here, read by the reduce) would
   // otherwise outweigh its work on the many small matrices of a batch
   const int ctas = (int)std::max<int64_t>(
-      1, std::min<int64_t>(std::min<int64_t>(gram_ctas(), ntiles), std::max<int64_t>(num_sms(), ceil_div(ntiles, 8))));
+      1, std::min<int64_t>(std::min<int64_t>(gram_ctas(), ntiles),
+                           std::max<int64_t>(num_sms(), ceil_div(ntiles, tune(TUNE_GRAM_MIN_TILES)))));
   if (!df) {
     using G32 = GramBOp<32, false>;
     using G64 = GramBOp<64, false>;

@@ -431,10 +431,11 @@ static rh_status launch_ttm_impl(const ModeView& v, const T* G, const T* Q, int6
   }
   if constexpr (!RESID && sizeof(T) == 4) {
     if (v.I <= 128 && ko <= 32 && M < (int64_t(1) << 31) && (int64_t)ko * M < (int64_t(1) << 31)) {
-      // small path: at least 4 tiles per CTA, at most 8 CTAs per SM
+      // small path: at least tune(min_tiles) tiles per CTA, tune(ctas_per_sm) CTAs per SM at most
       const int E = ko <= 16 ? 16 : 32;
       const int64_t ntiles = ceil_div(M, 4096 / E);
-      const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(8LL * num_sms(), ceil_div(ntiles, 4)));
+      const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((int64_t)tune(TUNE_TTM_SMALL_CTAS_PER_SM) * num_sms(),
+                                                                  ceil_div(ntiles, tune(TUNE_TTM_SMALL_MIN_TILES))));
       const int64_t tpc = ceil_div(ntiles, ctas);
       const dim3 g1((unsigned)ceil_div(ntiles, tpc));
       const TtmSmallArgs<TO> a{G, v.L, v.I, v.R, Q, qsi, qsc, ko, B, tpc, FastDiv((uint32_t)v.L),

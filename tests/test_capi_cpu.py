@@ -26,7 +26,7 @@ def L():
 def _declared():
     text = open(os.path.join(ROOT, "include", "rhosvd.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:rh_status|size_t|const char\*|void|uint64_t)\s+(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:rh_status|size_t|const char\*|void|uint64_t|int32_t)\s+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
@@ -52,6 +52,35 @@ def test_version_and_defaults(L):
     assert b"sm_103a" in L.rh_version()
     o = _lib.make_options()
     assert o.p == 5 and o.rho[0] == -1 and o.truncate == 1 and o.clamp == 0
+
+
+def _tuning_table():
+    text = open(os.path.join(ROOT, "paper_1905_07311_gb300", "csrc", "tuning_table.inc")).read()
+    return {n: int(v) for n, v in re.findall(r'RH_TUNE\(\w+,\s*"([\w.]+)",\s*(\d+)\)', text)}
+
+
+def test_tuning_knobs_round_trip(L):
+    table = _tuning_table()
+    n = L.rh_tuning_count()
+    assert n == len(table) and n > 0
+    names = [L.rh_tuning_name(i).decode() for i in range(n)]
+    assert sorted(names) == sorted(table)
+    assert L.rh_tuning_name(-1) is None and L.rh_tuning_name(n) is None
+    for name in names:
+        assert L.rh_tuning_get(name.encode()) == table[name]
+    k = names[0].encode()
+    try:
+        assert L.rh_tuning_set(k, 3) == 0 and L.rh_tuning_get(k) == 3
+        for bad in (-1, 4097):
+            assert L.rh_tuning_set(k, bad) != 0
+            assert "tuning value" in L.rh_last_error().decode()
+            assert L.rh_tuning_get(k) == 3
+    finally:
+        assert L.rh_tuning_set(k, 0) == 0
+    assert L.rh_tuning_get(k) == table[names[0]]
+    assert L.rh_tuning_get(b"no.such.knob") == -1
+    assert L.rh_tuning_set(b"no.such.knob", 2) != 0
+    assert "unknown tuning key" in L.rh_last_error().decode()
 
 
 def _ws(L, dims, ranks, dtype=0, **kw):

@@ -4,7 +4,8 @@ oracle and the definitions (needs a GB300).
 Every product on the tensor cores is exact (BF16 pieces times BF16 pieces), so only the sums round:
   sketch        |Y - X_rep Omega_bf16| <= (K + 8) 2^-24 (|X_rep| |Omega_bf16|), K the columns one CTA
                 accumulates in FP32 (the chunk of the kernel's plan: ceil(ceil(M / 64) / S) 64 with
-                S = max(1, min(4 SMs, ceil(ceil(M / 64) / 4)))), FP64 across CTAs;
+                S = max(1, min(c SMs, ceil(ceil(M / 64) / t))), c and t the launch-shape knobs), FP64
+                across CTAs;
   mode product  |B - A_rep^T X_rep| <= (I + 8) 2^-24 (|A_rep|^T |X_rep|), A split into two pieces;
   R-STHOSVD     the oracle on the values the tensor cores read (head + tail of FP32, the BF16 values,
                 the pieces, or bf16 of the dequantized E4M3 values) with Omega of the first mode
@@ -12,8 +13,11 @@ Every product on the tensor cores is exact (BF16 pieces times BF16 pieces), so o
                 and within 2 % of the oracle's error on the tensor the storage stands for (the FP32
                 tensor; for E4M3 the values its bytes and scales denote).
 The batched grouped engine runs BF16-form batches of uneven shapes whose results equal single calls
-bit for bit.
+bit for bit, and so do batches planned under non-default launch-shape knobs, which keep the oracle's
+error.
 """
+
+import contextlib
 
 import numpy as np
 import pytest
@@ -85,9 +89,15 @@ FORMS = {"f32": "f32_bf16x2", "pieces": "bf16x2", "bf16": "bf16", "fp8": "fp8_e4
 
 
 def _chunk(M):
+    """Columns per CTA of the small-row tensor-core sketch under the current launch-shape knobs."""
+    from paper_1905_07311_gb300 import _lib
+
+    L = _lib.lib()
+    per_sm = L.rh_tuning_get(b"small_tc_sketch.ctas_per_sm")
+    min_tiles = L.rh_tuning_get(b"small_tc_sketch.min_tiles")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     tiles = -(-M // 64)
-    S = max(1, min(4 * sms, -(-tiles // 4)))
+    S = max(1, min(per_sm * sms, -(-tiles // min_tiles)))
     return -(-tiles // S) * 64
 
 
@@ -230,3 +240,79 @@ def test_batched_small_form_grouped_equals_single_calls(rh, form):
     A = [f.cpu().numpy().T for f in got[0][0]]
     G = np.reshape(got[0][1].cpu().numpy(), call.core_dims[0], order="F")
     assert abs(rel_error(reps[0], G, A) - rel_error(reps[0], out["core"], out["factors"])) <= 1e-5
+
+
+@contextlib.contextmanager
+def _knobs(per_sm, min_work):
+    """Every launch-shape knob set: CTAs per SM to ``per_sm``, minimum work per CTA to ``min_work``;
+    the table's values come back on exit."""
+    from paper_1905_07311_gb300 import _lib
+
+    L = _lib.lib()
+    names = [L.rh_tuning_name(i) for i in range(L.rh_tuning_count())]
+    try:
+        for n in names:
+            _lib.check(L.rh_tuning_set(n, per_sm if n.endswith(b"ctas_per_sm") else min_work))
+        yield
+    finally:
+        for n in names:
+            _lib.check(L.rh_tuning_set(n, 0))
+
+
+# spread: one tile (or k step) per CTA, up to 16 CTAs per SM; packed: one CTA per SM, 64 tiles each
+@pytest.mark.parametrize("setting", [(16, 1), (1, 64)], ids=["spread", "packed"])
+@pytest.mark.parametrize("form", ["f32", "cuda_cores"])
+def test_launch_shape_knobs_keep_parity(rh, setting, form):
+    batch = _uneven_batch(8, 11)
+    Xs, reps = [], []
+    for t, (dims, ranks) in enumerate(batch):
+        X = lowrank_plus_noise_np(dims, [min(max(ranks) + 1, n) for n in dims], 0.9, 1e-3, seed=300 + t)
+        if form == "cuda_cores":
+            Xs.append(_flat32(X))
+            reps.append(np.asarray(X, dtype=np.float32).astype(np.float64))
+        else:
+            Xin, Xrep = _input(rh, X, form)
+            Xs.append(Xin)
+            reps.append(Xrep)
+    dims_list = [b[0] for b in batch]
+    ranks_list = [b[1] for b in batch]
+    dt = torch.float32 if form == "cuda_cores" else FORMS[form]
+    rho = None if form == "cuda_cores" else "natural"
+    with _knobs(*setting):
+        if form == "f32":
+            # the sketch bound with the chunk these knobs give
+            X = np.random.default_rng(8).standard_normal((97, 50, 41)).astype(np.float32)
+            Xin, Xrep = _input(rh, X, form)
+            Y = rh.rhosvd_sketch_bf16(Xin, [97, 50, 41], 13, seed=9, tensor_id=4, pieces="f32")
+            Y = (Y[0] if isinstance(Y, tuple) else Y).cpu().numpy().T
+            Xm = unfold(Xrep, 0)
+            Om = orng.round_bf16(orng.omega(9, 4, 0, np.arange(Xm.shape[1]), 13)).astype(np.float64)
+            bound = (_chunk(Xm.shape[1]) + 8) * 2.0 ** -24 * (np.abs(Xm) @ np.abs(Om)) + 1e-300
+            assert np.all(np.abs(Y - Xm @ Om) <= bound)
+        call = rh.RsthosvdBatchedCall(dims_list, ranks_list, dt, p=5, seed=2, tensor_id=3, clamp=True, streams=0,
+                                      rho=rho)
+        plan = call.plan(Xs)
+        Ts = plan.run()
+        torch.cuda.synchronize()
+        got = [([f.clone() for f in T.factors], T.core.clone(), T.norms.clone()) for T in Ts]
+        plan.close()
+        for i, X in enumerate(Xs):
+            kw = {} if rho is None else {"rho": list(range(len(dims_list[i]))), "form": FORMS[form]}
+            T1 = rh.rsthosvd(X, dims_list[i], ranks_list[i], p=5, seed=2, tensor_id=3 + i, clamp=True, **kw)
+            torch.cuda.synchronize()
+            for a, b in zip(got[i][0], T1.factors):
+                assert torch.equal(a, b)
+            assert torch.equal(got[i][1], T1.core)
+            assert torch.equal(got[i][2], T1.norms)
+    for i, ((dims, ranks), Xr) in enumerate(zip(batch, reps)):
+        if rho is None:
+            out = otk.rsthosvd(Xr, ranks, 5, 2, tensor_id=3 + i, clamp=True)
+        else:
+            out = otk.rsthosvd(Xr, ranks, 5, 2, rho=list(range(len(dims))), tensor_id=3 + i,
+                               omega_round={0: "bf16"}, clamp=True)
+        A = [f.cpu().numpy().T for f in got[i][0]]
+        G = np.reshape(got[i][1].cpu().numpy(), [a.shape[1] for a in A], order="F")
+        assert abs(rel_error(Xr, G, A) - rel_error(Xr, out["core"], out["factors"])) <= 1e-5, (i, dims)
+        if rho is None:
+            n2 = float(np.sum(Xr ** 2))
+            assert abs(got[i][2][0].item() - n2) <= 40 * 2.0 ** -24 * n2
