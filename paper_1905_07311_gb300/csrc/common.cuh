@@ -240,8 +240,20 @@ __device__ __forceinline__ int group_find(const int32_t* __restrict__ start, int
   return lo;
 }
 
+// Programmatic dependent launch.  Op kernels are launched with programmatic stream serialization,
+// so a grid may start while the grid before it in the stream is still running; the first thing
+// every Op kernel does is wait for that grid to complete and its memory to be visible
+// (griddepcontrol.wait, a no-op when nothing is pending), and only then does it let the next grid
+// launch.  The next grid's blocks thus get resident (and past their launch latency) while this one
+// runs, and no Op touches memory before its predecessor has finished.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <class Op>
 __global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks) single_kernel(const typename Op::Args a) {
+  pdl_enter();
   Op::body(hw_grid(), a);
 }
 
@@ -249,6 +261,7 @@ template <class Op>
 __global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks)
     group_kernel(const typename Op::Args* __restrict__ args, const int32_t* __restrict__ start,
                  const uint2* __restrict__ gdim, int n) {
+  pdl_enter();
   const int t = group_find(start, n);
   const uint2 d = gdim[t];
   const uint32_t lb = blockIdx.x - (uint32_t)start[t];
@@ -328,6 +341,10 @@ enum LaunchSite : int {
   SITE_FINAL = 90,
   SITE_OTHER = 1000         // launches of entry points that never run grouped
 };
+
+// Launch of an Op kernel (single_kernel or group_kernel) with programmatic stream serialization
+// (pdl_enter); RHOSVD_PDL=0 in the environment launches them in plain stream order instead.
+rh_status launch_op_kernel(const void* fn, dim3 grid, int threads, size_t smem, cudaStream_t st, void** params);
 
 // Direct launch (the caller's stream), or, while this thread records a tape, an entry of it.
 rh_status emit_raw(KernelRef* k, int site, int sub, dim3 grid, size_t smem, cudaStream_t st, const void* args);

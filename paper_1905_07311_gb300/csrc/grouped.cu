@@ -11,6 +11,7 @@
 // stream-ordered copy kernels whose payload travels in their parameters, which CUDA graph capture
 // records by value, so a captured call needs no host memory to stay alive.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -75,6 +76,29 @@ void note_direct_launch() {
 TapeScope::TapeScope(Tape* t) : prev_(g_tape) { g_tape = t; }
 TapeScope::~TapeScope() { g_tape = prev_; }
 
+rh_status launch_op_kernel(const void* fn, dim3 grid, int threads, size_t smem, cudaStream_t st, void** params) {
+  static const bool pdl = [] {
+    const char* v = std::getenv("RHOSVD_PDL");
+    return !(v != nullptr && v[0] == '0');
+  }();
+  if (!pdl) {
+    RH_CUDA_TRY(cudaLaunchKernel(fn, grid, dim3(threads), params, smem, st));
+    return RH_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RH_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, params));
+  return RH_OK;
+}
+
 rh_status emit_raw(KernelRef* k, int site, int sub, dim3 grid, size_t smem, cudaStream_t st, const void* args) {
   if (g_tape) {
     TapeEntry e{k, g_tape->step, site, sub, grid, smem, g_tape->bytes.size()};
@@ -87,8 +111,7 @@ rh_status emit_raw(KernelRef* k, int site, int sub, dim3 grid, size_t smem, cuda
   if (s != RH_OK) return s;
   void* params[1] = {const_cast<void*>(args)};
   count_launch();
-  RH_CUDA_TRY(cudaLaunchKernel(k->single, grid, dim3(k->threads), params, smem, st));
-  return RH_OK;
+  return launch_op_kernel(k->single, grid, k->threads, smem, st, params);
 }
 
 rh_status emit_memset(int site, int sub, void* p, size_t bytes, cudaStream_t st) {
@@ -198,7 +221,8 @@ rh_status run_grouped(const GroupedProgram& gp, const void* dev, cudaStream_t st
     int n = L.n;
     void* params[4] = {&args, &start, &gdim, &n};
     count_launch();
-    RH_CUDA_TRY(cudaLaunchKernel(L.k->group, dim3((unsigned)L.blocks), dim3(L.k->threads), params, L.smem, st));
+    if ((s = launch_op_kernel(L.k->group, dim3((unsigned)L.blocks), L.k->threads, L.smem, st, params)) != RH_OK)
+      return s;
   }
   return RH_OK;
 }
