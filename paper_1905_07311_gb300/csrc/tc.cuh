@@ -162,6 +162,51 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return d;
 }
 
+// Packed FP32 pairs: one instruction for two lanes, each rounded to nearest even exactly as the
+// scalar instruction would round it.
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nsub.rn.f32x2 rd, ra, rb;\n"
+      "mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nadd.rn.f32x2 rd, ra, rb;\n"
+      "mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
+      "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 bf16x2_unpack(uint32_t h) {
+  return make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xFFFF0000u));
+}
+
+// The exact head / tail split of four FP32 values: h = bf16(v), t = bf16(v - h), packed two per
+// word (h01 = values 0, 1); s01 / s23 accumulate (h + t)^2 lane-wise.  The subtractions and sums
+// run on packed pairs.
+__device__ __forceinline__ void split4_bf16x2(const float4 v, uint2& h, uint2& t, float2& s01, float2& s23) {
+  h.x = pack_bf16x2(v.x, v.y);
+  h.y = pack_bf16x2(v.z, v.w);
+  const float2 f01 = bf16x2_unpack(h.x), f23 = bf16x2_unpack(h.y);
+  const float2 d01 = f2_sub(make_float2(v.x, v.y), f01), d23 = f2_sub(make_float2(v.z, v.w), f23);
+  t.x = pack_bf16x2(d01.x, d01.y);
+  t.y = pack_bf16x2(d23.x, d23.y);
+  const float2 g01 = f2_add(f01, bf16x2_unpack(t.x)), g23 = f2_add(f23, bf16x2_unpack(t.y));
+  s01 = f2_fma(g01, g01, s01);
+  s23 = f2_fma(g23, g23, s23);
+}
+
 // Split a 32 KB tile of FP32 values staged by TMA (boxes of 32 values x kRowsPerBox rows, 128-byte
 // rows, 128-byte swizzle) into its BF16 head and tail, written as 128 rows of 64 values (128-byte
 // rows, 128-byte swizzle): box b, row r holds the values 32 (b & 1) .. 32 (b & 1) + 31 of output
@@ -213,33 +258,26 @@ __device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, u
 template <int kPRows, int kThreadsConv>
 __device__ __forceinline__ float convert_tile_plain(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
                                                     uint8_t* __restrict__ lo, int t) {
+  static_assert(kThreadsConv % 256 == 0, "unit j of a thread is column 8 j + (t / 32) of its first one");
   constexpr int kUnits = kPRows * 32 / kThreadsConv;
+  constexpr int kColStep = kThreadsConv / 32;   // columns between a thread's consecutive units
+  // unit j of thread t: column p = kColStep j + t / 32, rows i = 4 (t % 32) .. + 3; p % 8 does not
+  // depend on j, so the swizzled output offset is off0 + 128 kColStep j
+  const int p0 = t >> 5, i = (t & 31) * 4;
+  const uint8_t* src = f32 + p0 * 512 + (t & 31) * 16;
+  const int off0 = (i >> 6) * (kPRows * 128) + p0 * 128 + ((((i & 63) >> 3) ^ (p0 & 7)) << 4) + ((i >> 2) & 1) * 8;
   float4 v[kUnits];
 #pragma unroll
-  for (int j = 0; j < kUnits; ++j) {
-    const int u = j * kThreadsConv + t;
-    v[j] = *reinterpret_cast<const float4*>(f32 + (u >> 5) * 512 + (u & 31) * 16);
-  }
-  float ss = 0.0f;
+  for (int j = 0; j < kUnits; ++j) v[j] = *reinterpret_cast<const float4*>(src + j * kColStep * 512);
+  float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int j = 0; j < kUnits; ++j) {
-    const int u = j * kThreadsConv + t;
-    const int p = u >> 5, i = (u & 31) * 4;
-    const uint32_t h01 = pack_bf16x2(v[j].x, v[j].y), h23 = pack_bf16x2(v[j].z, v[j].w);
-    const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
-    const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
-    const uint32_t t01 = pack_bf16x2(v[j].x - f0, v[j].y - f1), t23 = pack_bf16x2(v[j].z - f2, v[j].w - f3);
-    const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
-    const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
-    ss = fmaf(g0, g0, ss);
-    ss = fmaf(g1, g1, ss);
-    ss = fmaf(g2, g2, ss);
-    ss = fmaf(g3, g3, ss);
-    const int off = (i >> 6) * (kPRows * 128) + p * 128 + ((((i & 63) >> 3) ^ (p & 7)) << 4) + ((i >> 2) & 1) * 8;
-    *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
-    *reinterpret_cast<uint2*>(lo + off) = make_uint2(t01, t23);
+    uint2 h, tl;
+    split4_bf16x2(v[j], h, tl, s01, s23);
+    *reinterpret_cast<uint2*>(hi + off0 + j * kColStep * 128) = h;
+    *reinterpret_cast<uint2*>(lo + off0 + j * kColStep * 128) = tl;
   }
-  return ss;
+  return (s01.x + s01.y) + (s23.x + s23.y);
 }
 
 // Input kinds of the tensor-core sketch and mode product: BF16 pieces loaded by TMA as they are,
@@ -256,33 +294,26 @@ constexpr int kInPieces = 0, kInF32 = 1, kInFp8 = 2, kInF32S = 3;
 template <int kThreadsConv>
 __device__ __forceinline__ float convert_tile_kmajor(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
                                                      uint8_t* __restrict__ lo, int t) {
+  static_assert(kThreadsConv % 128 == 0, "unit j of a thread is row 16 j + (t / 16) of its first one");
   constexpr int kUnits = 2048 / kThreadsConv;
+  constexpr int kRowStep = kThreadsConv / 16;   // rows between a thread's consecutive units
+  // unit j of thread t: row 16 j' + t / 16 (kRowStep = 16 j'), values 4 (t % 16) .. + 3; row % 8
+  // does not depend on j, so the swizzled output offset is off0 + 128 kRowStep j
+  const int r0 = t >> 4, q = t & 15;
+  const uint8_t* src = f32 + r0 * 256 + q * 16;
+  const int off0 = (r0 >> 3) * 1024 + (r0 & 7) * 128 + (((q >> 1) ^ (r0 & 7)) << 4) + (q & 1) * 8;
   float4 v[kUnits];
 #pragma unroll
-  for (int j = 0; j < kUnits; ++j) {
-    const int u = j * kThreadsConv + t;
-    v[j] = *reinterpret_cast<const float4*>(f32 + (u >> 4) * 256 + (u & 15) * 16);
-  }
-  float ss = 0.0f;
+  for (int j = 0; j < kUnits; ++j) v[j] = *reinterpret_cast<const float4*>(src + j * kRowStep * 256);
+  float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int j = 0; j < kUnits; ++j) {
-    const int u = j * kThreadsConv + t;
-    const int row = u >> 4, q = u & 15;
-    const uint32_t h01 = pack_bf16x2(v[j].x, v[j].y), h23 = pack_bf16x2(v[j].z, v[j].w);
-    const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
-    const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
-    const uint32_t t01 = pack_bf16x2(v[j].x - f0, v[j].y - f1), t23 = pack_bf16x2(v[j].z - f2, v[j].w - f3);
-    const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
-    const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
-    ss = fmaf(g0, g0, ss);
-    ss = fmaf(g1, g1, ss);
-    ss = fmaf(g2, g2, ss);
-    ss = fmaf(g3, g3, ss);
-    const int off = (row >> 3) * 1024 + (row & 7) * 128 + (((q >> 1) ^ (row & 7)) << 4) + (q & 1) * 8;
-    *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
-    *reinterpret_cast<uint2*>(lo + off) = make_uint2(t01, t23);
+    uint2 h, tl;
+    split4_bf16x2(v[j], h, tl, s01, s23);
+    *reinterpret_cast<uint2*>(hi + off0 + j * kRowStep * 128) = h;
+    *reinterpret_cast<uint2*>(lo + off0 + j * kRowStep * 128) = tl;
   }
-  return ss;
+  return (s01.x + s01.y) + (s23.x + s23.y);
 }
 
 // Value of an E4M3 byte (OCP FP8: 1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no
