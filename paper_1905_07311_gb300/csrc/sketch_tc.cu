@@ -39,6 +39,7 @@ constexpr uint32_t kF32Box = 32 * 64 * 4;           // FP32 TMA box: 32 rows x 6
 constexpr uint32_t kF32Tile = 4 * kF32Box;          // 128 x 64 FP32
 
 constexpr uint32_t kFp8Tile = 128 * 64;           // E4M3 TMA box: 128 rows (bytes) x 64 columns
+constexpr int kOmBufs = 2;                        // Omega tiles in flight (generated ahead of the MMAs)
 
 // BF16 pieces in: 4 stages filled by TMA.  FP32 in: 3 stages of FP32 tiles filled by TMA, split by
 // eight converter warps into 2 stages of BF16 pieces (a fourth stage measured no faster).  E4M3
@@ -58,9 +59,9 @@ template <int IN>
 struct alignas(1024) SketchSmem {
   uint8_t xf[SketchCfg<IN>::kF32Stages][SketchCfg<IN>::kStageBytes];
   uint8_t x[SketchCfg<IN>::kPStages][2][kPieceTile];   // [stage][piece][128 x 64]
-  uint8_t om[2][kOmegaTile];
+  uint8_t om[kOmBufs][kOmegaTile];
   uint64_t f32full[SketchCfg<IN>::kF32Stages], f32empty[SketchCfg<IN>::kF32Stages];
-  uint64_t full[SketchCfg<IN>::kPStages], empty[SketchCfg<IN>::kPStages], om_full[2], om_empty[2], done;
+  uint64_t full[SketchCfg<IN>::kPStages], empty[SketchCfg<IN>::kPStages], om_full[kOmBufs], om_empty[kOmBufs], done;
   uint32_t tmem_slot;
   double nrm[16];
 };
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
         tc::mbar_init(&S.f32empty[s], Cfg::kConv);
       }
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kOmBufs; ++b) {
       tc::mbar_init(&S.om_full[b], 128);
       tc::mbar_init(&S.om_empty[b], 1);
     }
@@ -175,8 +176,8 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
       uint32_t it = 0, oc = 0;
       bool first = true;
       for (int64_t c = c_begin; c < c_end; c += c_step, ++oc) {
-        const uint32_t b = oc & 1;
-        if (!tc::mbar_wait(&S.om_full[b], (oc >> 1) & 1, err, 2)) break;
+        const uint32_t b = oc % kOmBufs;
+        if (!tc::mbar_wait(&S.om_full[b], (oc / kOmBufs) & 1, err, 2)) break;
         tc::tc_fence_after();
         const uint32_t om_addr = tc::smem_u32(&S.om[b][0]);
         for (int m = 0; m < mtiles; ++m, ++it) {
@@ -207,12 +208,12 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     // only the ceil(ell / 4) quads of Omega that reach the output are generated; the N columns
     // past them are zeroed once in both buffers (their accumulator columns are never read)
     const int nq = (ell + 3) / 4;
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kOmBufs; ++b)
       for (int n = 4 * nq + (t >> 6); n < 64; n += 2) *reinterpret_cast<uint16_t*>(&S.om[b][0] + sw128_off(n, p)) = 0;
     uint32_t oc = 0;
     for (int64_t c = c_begin; c < c_end; c += c_step, ++oc) {
-      const uint32_t b = oc & 1;
-      if (oc >= 2 && !tc::mbar_wait(&S.om_empty[b], ((oc >> 1) - 1) & 1, err, 4)) break;
+      const uint32_t b = oc % kOmBufs;
+      if (oc >= kOmBufs && !tc::mbar_wait(&S.om_empty[b], ((oc / kOmBufs) - 1) & 1, err, 4)) break;
       uint8_t* om = &S.om[b][0];
       const int64_t row = row0 + c * kPChunk + p;
       for (int q = t >> 6; q < nq; q += 2) {

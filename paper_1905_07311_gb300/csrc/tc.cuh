@@ -5,6 +5,7 @@
 // *err and gives up, so a kernel can always finish (the caller reads the flag).
 #pragma once
 
+#include "f32x2.cuh"
 #include <cuda.h>
 #include <stdint.h>
 
@@ -162,32 +163,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return d;
 }
 
-// Packed FP32 pairs: one instruction for two lanes, each rounded to nearest even exactly as the
-// scalar instruction would round it.
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
-  float2 d;
-  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nsub.rn.f32x2 rd, ra, rb;\n"
-      "mov.b64 {%0, %1}, rd;\n}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
-  float2 d;
-  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nadd.rn.f32x2 rd, ra, rb;\n"
-      "mov.b64 {%0, %1}, rd;\n}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
-      "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
 __device__ __forceinline__ float2 bf16x2_unpack(uint32_t h) {
   return make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xFFFF0000u));
 }
@@ -217,38 +192,26 @@ __device__ __forceinline__ void split4_bf16x2(const float4 v, uint2& h, uint2& t
 template <int kRowsPerBox, int kThreadsConv>
 __device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
                                               uint8_t* __restrict__ lo, int t) {
+  static_assert(kThreadsConv == 256 && kRowsPerBox >= 128, "unit j of a thread is row 16 j + (t / 16) of box (t / 8) % 2");
   constexpr int kUnits = 2048 / kThreadsConv;
+  // unit j of thread t: 16-byte piece k = t % 8 of row r = 16 j + t / 16 of box b = (t / 8) % 2;
+  // r % 8 does not depend on j, so both offsets advance by 16 rows (2048 bytes) per unit
+  const int k = t & 7, b = (t >> 3) & 1, r0 = t >> 4;
+  const uint8_t* src = f32 + b * (kRowsPerBox * 128) + r0 * 128 + ((k ^ (r0 & 7)) << 4);
+  const int ci = 4 * b + (k >> 1);
+  const int off0 = r0 * 128 + ((ci ^ (r0 & 7)) << 4) + (k & 1) * 8;
   float4 v[kUnits];
 #pragma unroll
-  for (int j = 0; j < kUnits; ++j) {   // all loads first: kUnits independent 16-byte reads in flight
-    const int u = j * kThreadsConv + t;
-    const int k = u & 7, g = u >> 3, rest = g >> 1;
-    const int b = 2 * (rest / kRowsPerBox) + (g & 1), r = rest % kRowsPerBox;
-    v[j] = *reinterpret_cast<const float4*>(f32 + b * (kRowsPerBox * 128) + r * 128 + ((k ^ (r & 7)) << 4));
-  }
-  float ss = 0.0f;
+  for (int j = 0; j < kUnits; ++j) v[j] = *reinterpret_cast<const float4*>(src + j * 2048);   // all loads first
+  float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int j = 0; j < kUnits; ++j) {
-    const int u = j * kThreadsConv + t;
-    const int k = u & 7, g = u >> 3, rest = g >> 1;
-    const int b = 2 * (rest / kRowsPerBox) + (g & 1), r = rest % kRowsPerBox;
-    const uint32_t h01 = pack_bf16x2(v[j].x, v[j].y), h23 = pack_bf16x2(v[j].z, v[j].w);
-    const float f0 = __uint_as_float(h01 << 16), f1 = __uint_as_float(h01 & 0xFFFF0000u);
-    const float f2 = __uint_as_float(h23 << 16), f3 = __uint_as_float(h23 & 0xFFFF0000u);
-    const uint32_t t01 = pack_bf16x2(v[j].x - f0, v[j].y - f1), t23 = pack_bf16x2(v[j].z - f2, v[j].w - f3);
-    const float g0 = f0 + __uint_as_float(t01 << 16), g1 = f1 + __uint_as_float(t01 & 0xFFFF0000u);
-    const float g2 = f2 + __uint_as_float(t23 << 16), g3 = f3 + __uint_as_float(t23 & 0xFFFF0000u);
-    ss = fmaf(g0, g0, ss);
-    ss = fmaf(g1, g1, ss);
-    ss = fmaf(g2, g2, ss);
-    ss = fmaf(g3, g3, ss);
-    const int rho = (b >> 1) * kRowsPerBox + r;
-    const int ci = 4 * (b & 1) + (k >> 1);
-    const int off = rho * 128 + ((ci ^ (rho & 7)) << 4) + (k & 1) * 8;
-    *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
-    *reinterpret_cast<uint2*>(lo + off) = make_uint2(t01, t23);
+    uint2 h, tl;
+    split4_bf16x2(v[j], h, tl, s01, s23);
+    *reinterpret_cast<uint2*>(hi + off0 + j * 2048) = h;
+    *reinterpret_cast<uint2*>(lo + off0 + j * 2048) = tl;
   }
-  return ss;
+  return (s01.x + s01.y) + (s23.x + s23.y);
 }
 
 // As convert_tile, for a tile staged unswizzled: kPRows columns of 128 consecutive FP32 rows each
