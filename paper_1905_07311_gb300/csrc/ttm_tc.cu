@@ -77,7 +77,12 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // one r, split into MN-major pieces (K = i, N = l), B written through ``co`` in the (L, ell, R)
 // layout of the mode product.  IN = kInFp8: mapX0 is
 // the E4M3 tensor (box 64 x 128 bytes, leading dimension ld), dequantized with ``scales`` and split.
-template <int IN>
+// kT (FP32 input only; the truncated-core product): the accumulator is transposed, D(p, n) =
+// X_k(p, :) A(n, :)^T with the X pieces as operand A (rows p) and [Q_h^T; Q_t^T] as operand B, so
+// TMEM lane p holds column p's head sums in columns c and its tail sums in columns 64 + c.  Each
+// epilogue warp then finishes its own 32 columns p (no exchange between warps) and writes
+// B[co.base(p) + c co.cstride()] with the lanes along p.
+template <int IN, bool kT = false>
 __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
@@ -196,7 +201,10 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
               const uint64_t bdesc = IN == tc::kInF32S
                                          ? tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 2048, 8192, 1024)
                                          : tc::sdesc_sw128(tc::smem_u32(&S.x[s][pc][0]) + kk * 32, 16, 1024);
-              tc::mma_bf16(d, adesc, bdesc, idesc, (ks == 0 && kk == 0 && pc == 0) ? 0u : 1u);
+              if constexpr (kT)
+                tc::mma_bf16(d, bdesc, adesc, idesc, (ks == 0 && kk == 0 && pc == 0) ? 0u : 1u);
+              else
+                tc::mma_bf16(d, adesc, bdesc, idesc, (ks == 0 && kk == 0 && pc == 0) ? 0u : 1u);
             }
           }
           tc::mma_commit(&S.empty[s]);
@@ -215,6 +223,26 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
       if (!tc::mbar_wait(&S.tfull[b], (tl >> 1) & 1, err, 14)) break;
       tc::tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + b * kNTile;
+      if constexpr (kT) {
+        const int64_t p = t * kNTile + quad * 32 + lane;
+        const int64_t ob = p < M ? co.base(p, ell) : 0;
+        const int64_t cs = co.cstride();
+        for (int cc = 0; cc < (ell + 15) / 16; ++cc) {
+          float h[16], tv[16];
+          tc::tmem_ld16(base + (uint32_t)(cc * 16), h);
+          tc::tmem_ld16(base + (uint32_t)(64 + cc * 16), tv);
+          if (p < M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int c = cc * 16 + j;
+              if (c < ell) B[ob + cs * c] = h[j] + tv[j];
+            }
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&S.tempty[b]);
+        continue;
+      }
       if (tail) {
         for (int cc = 0; cc < kNTile / 16; ++cc) {
           float v[16];
@@ -449,9 +477,10 @@ rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, Cor
   const ModeView v{1, (int64_t)ell, M};
   constexpr int IN = tc::kInF32;
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err, nullptr,
-                                                                         0, co, tc_probe_next(), 1);
+  RH_CUDA_TRY(
+      cudaFuncSetAttribute(ttm_tc_kernel<IN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN, true><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err,
+                                                                               nullptr, 0, co, tc_probe_next(), 1);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
