@@ -1,7 +1,7 @@
-// Packed FP32 pair arithmetic (sm_100 and later): add / sub / fma on two lanes in one instruction.
-// The head / tail split uses them where the result is exact (x - bf16(x), head + tail) or where a
-// fused multiply-add is meant (sums of squares), so no result depends on how the compiler pairs a
-// packed product with a packed sum.
+// Packed FP32 pair arithmetic (sm_100 and later): add / sub / mul / fma on two lanes in one
+// instruction.  The head / tail split uses them where the result is exact (x - bf16(x), head +
+// tail) or where a fused multiply-add is meant (sums of squares); the Jacobi rotations use them
+// where no other computation has to reproduce the bits.
 #pragma once
 
 namespace rh {
@@ -28,6 +28,14 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
       "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
       : "=f"(d.x), "=f"(d.y)
       : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmul.rn.f32x2 rd, ra, rb;\n"
+      "mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
   return d;
 }
 

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "f32x2.cuh"
 #include "kernels.cuh"
 
 namespace rh {
@@ -1792,6 +1793,16 @@ __device__ __forceinline__ void PivotedCholeskyOp::body(const Grid g, const Args
 // (a two-step shuffle reduction of each product, a 128-thread barrier per round).  Eight lanes per
 // pair over eight warps with a block barrier per round took 193 us for n = 60, one lane per pair
 // in one warp (no reduction, issue-bound on one scheduler) 257 us.
+// A round is a chain of dependent steps, so its length is what counts: multi-function-unit
+// operations (reciprocal, square root) take ~40 cycles each against ~5 for an FMA on this part.
+// The rotation of a pair with squared norms al, be and product g therefore needs two of them:
+// with d = be - al, r = sqrt(d^2 + 4 g^2) and u = |d| + r, the angle of the classical rule
+// (t = sign(d) 2 g / u, c = 1 / sqrt(1 + t^2), s = c t) has 1 + t^2 = 2 r / u, so
+// c = u w, s = sign(d) 2 g w with w = 1 / sqrt(2 r u), and t g = sign(d) 4 g^2 r w^2 updates the
+// squared norms (al - t g, be + t g) without a division.  The pair is rotated when
+// g^2 > tol^2 al be (no square root on the way).  X is first scaled by a power of two so that
+// its largest squared column norm lies in [1, 4) (d^2 + 4 g^2 cannot overflow); the singular
+// values are scaled back at the end.  Products and rotations run on packed FP32 pairs.
 // Sweeps end when one rotates nothing, or when the largest coupling it rotated was at most
 // sqrt(tol / n) (the quadratic convergence of the cyclic Jacobi method then leaves every coupling
 // of the next sweep below tol, so that sweep is not run).
@@ -1841,18 +1852,42 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
   __shared__ float nrm2[2][RH_MAX_ELL];
   __shared__ float sig[RH_MAX_ELL];
   __shared__ int rankof[RH_MAX_ELL];
-  __shared__ int s_cur;
-  __shared__ unsigned s_red[2][4];      // per sweep-warp: any rotation, largest rotated coupling
+  __shared__ int s_cur, s_exp;
+  __shared__ unsigned s_red[2][4];      // per sweep-warp: any rotation, largest rotated coupling^2
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int e = t; e < 64 * 64; e += blockDim.x) {
     const int i = e & 63, q = e >> 6;
     buf0[kLdb * q + i] = (q < n && i < n) ? Xin[i + n * q] : 0.0f;
   }
   __syncthreads();
+  // largest squared column norm -> the power-of-two scale 2^-s_exp applied to every entry
+  {
+    float mx = 0.0f;
+    for (int q = w; q < np; q += blockDim.x >> 5) {
+      const float x0 = buf0[kLdb * q + lane], x1 = buf0[kLdb * q + 32 + lane];
+      float v = x0 * x0 + x1 * x1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      mx = fmaxf(mx, v);
+    }
+    if (lane == 0) sig[w] = mx;
+    __syncthreads();
+    if (t == 0) {
+      float m = 0.0f;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, sig[k]);
+      // 2^(2 e) <= m < 2^(2 e + 2); the entries are divided by 2^e
+      s_exp = (m > 0.0f && isfinite(m)) ? (ilogbf(m) >> 1) : 0;
+    }
+    __syncthreads();
+    const float sc = ldexpf(1.0f, -s_exp);
+    for (int e = t; e < 64 * kLdb; e += blockDim.x) buf0[e] *= sc;
+    __syncthreads();
+  }
   const float tol = (float)(8 * (n > 8 ? n : 8)) * 5.9604645e-8f;
+  const float tol2 = tol * tol;
   // Quadratic convergence: a sweep whose largest rotated coupling is c leaves couplings of order
   // c^2, so once c <= sqrt(tol / n) the next sweep would rotate nothing and is skipped.
-  const float cstop = sqrtf(tol / (float)(n > 1 ? n : 1));
+  const float cstop2 = tol / (float)(n > 1 ? n : 1);
   // The sweeps run in warps 0..3 (one per scheduler) with a 128-thread barrier between rounds; a
   // group of four lanes rotates one pair, lane l holding entries 4l..4l+3 + 16m (m < 4) of both
   // columns.  The other warps wait for the epilogue.
@@ -1877,58 +1912,60 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
         named_bar_sync(1, 128);
       }
       int rotated = 0;
-      float cmx = 0.0f;
+      float cmx2 = 0.0f;
       for (int rnd = 0; rnd < np - 1; ++rnd) {
         const float* src = cur ? buf1 : buf0;
         float* dst = cur ? buf0 : buf1;
-        float4 a[4], b[4];
+        float2 a[8], b[8];   // a[2 m], a[2 m + 1]: entries 4 l + 16 m + {0, 1} and + {2, 3}
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          a[m] = *reinterpret_cast<const float4*>(src + kLdb * qa + 4 * l + 16 * m);
-          b[m] = *reinterpret_cast<const float4*>(src + kLdb * qb + 4 * l + 16 * m);
+          const float4 va = *reinterpret_cast<const float4*>(src + kLdb * qa + 4 * l + 16 * m);
+          const float4 vb = *reinterpret_cast<const float4*>(src + kLdb * qb + 4 * l + 16 * m);
+          a[2 * m] = make_float2(va.x, va.y);
+          a[2 * m + 1] = make_float2(va.z, va.w);
+          b[2 * m] = make_float2(vb.x, vb.y);
+          b[2 * m + 1] = make_float2(vb.z, vb.w);
         }
         float al = nrm2[cur][qa], be = nrm2[cur][qb];
-        float g0 = 0.0f, g1 = 0.0f;
+        float2 g0 = make_float2(0.0f, 0.0f), g1 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          g0 = fmaf(a[m].x, b[m].x, g0);
-          g1 = fmaf(a[m].y, b[m].y, g1);
-          g0 = fmaf(a[m].z, b[m].z, g0);
-          g1 = fmaf(a[m].w, b[m].w, g1);
+          g0 = f2_fma(a[2 * m], b[2 * m], g0);
+          g1 = f2_fma(a[2 * m + 1], b[2 * m + 1], g1);
         }
-        float g = g0 + g1;
-        g += __shfl_xor_sync(0xffffffffu, g, 1);
-        g += __shfl_xor_sync(0xffffffffu, g, 2);
-        const float cpl = fabsf(g) * rsqrtf(al) * rsqrtf(be);
-        if (active && g != 0.0f && cpl > tol) {
-          // the angle needs no correctly rounded division or square root: the rotation is applied
-          // with c = rsqrt(1 + t^2), s = c t whatever t is, and the polar step at the end restores
-          // orthonormality; the hardware reciprocal and rsqrt keep the critical path short
-          const float zeta = __fdividef(be - al, 2.0f * g);
-          const float az = fabsf(zeta);
-          const float az2 = fmaf(az, az, 1.0f);
-          const float tm = az < 1e18f ? __frcp_rn(az + az2 * rsqrtf(az2)) : __fdividef(0.5f, az);
-          const float tt = zeta < 0.0f ? -tm : tm;
-          const float c = rsqrtf(fmaf(tt, tt, 1.0f));
-          const float sn = c * tt;
+        float gg = (g0.x + g0.y) + (g1.x + g1.y);
+        gg += __shfl_xor_sync(0xffffffffu, gg, 1);
+        gg += __shfl_xor_sync(0xffffffffu, gg, 2);
+        const float g2 = gg * gg;
+        const float albe = al * be;
+        const float d = be - al;
+        const float q = fmaf(d, d, 4.0f * g2);
+        if (active && g2 > tol2 * albe && albe > 0.0f && q > 0.0f) {
+          const float r = q * rsqrtf(q);
+          const float u = fabsf(d) + r;
+          const float wv = rsqrtf(2.0f * r * u);
+          const float c = u * wv;
+          const float sn = copysignf(2.0f, d) * gg * wv;   // sign(d) 2 g w, sign(0) = +
+          const float tg = copysignf(4.0f, d) * g2 * r * wv * wv;
+          const float2 c2 = make_float2(c, c), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            float u;
-            u = a[m].x; a[m].x = c * u - sn * b[m].x; b[m].x = sn * u + c * b[m].x;
-            u = a[m].y; a[m].y = c * u - sn * b[m].y; b[m].y = sn * u + c * b[m].y;
-            u = a[m].z; a[m].z = c * u - sn * b[m].z; b[m].z = sn * u + c * b[m].z;
-            u = a[m].w; a[m].w = c * u - sn * b[m].w; b[m].w = sn * u + c * b[m].w;
+          for (int m = 0; m < 8; ++m) {
+            const float2 x = a[m], y = b[m];
+            a[m] = f2_fma(c2, x, f2_mul(ns2, y));
+            b[m] = f2_fma(c2, y, f2_mul(s2, x));
           }
-          al = al - tt * g;
-          be = be + tt * g;
+          al = al - tg;
+          be = be + tg;
           rotated = 1;
-          cmx = fmaxf(cmx, cpl);
+          cmx2 = fmaxf(cmx2, __fdividef(g2, albe));
         }
         if (active) {
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
-            *reinterpret_cast<float4*>(dst + kLdb * na + 4 * l + 16 * m) = a[m];
-            *reinterpret_cast<float4*>(dst + kLdb * nb + 4 * l + 16 * m) = b[m];
+            *reinterpret_cast<float4*>(dst + kLdb * na + 4 * l + 16 * m) =
+                make_float4(a[2 * m].x, a[2 * m].y, a[2 * m + 1].x, a[2 * m + 1].y);
+            *reinterpret_cast<float4*>(dst + kLdb * nb + 4 * l + 16 * m) =
+                make_float4(b[2 * m].x, b[2 * m].y, b[2 * m + 1].x, b[2 * m + 1].y);
           }
           if (l == 0) {
             nrm2[cur ^ 1][na] = al;
@@ -1938,9 +1975,10 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
         cur ^= 1;
         named_bar_sync(1, 128);
       }
-      // couplings are >= 0: their FP32 bit patterns order like the values
+      // squared couplings are >= 0 (or +inf when a norm underflowed): their FP32 bit patterns
+      // order like the values
       const unsigned anyw = __any_sync(0xffffffffu, rotated);
-      const unsigned mxw = __reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(cmx));
+      const unsigned mxw = __reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(cmx2));
       if (lane == 0) {
         s_red[0][w] = anyw;
         s_red[1][w] = mxw;
@@ -1948,7 +1986,7 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
       named_bar_sync(1, 128);
       const unsigned any4 = s_red[0][0] | s_red[0][1] | s_red[0][2] | s_red[0][3];
       const unsigned mx4 = max(max(s_red[1][0], s_red[1][1]), max(s_red[1][2], s_red[1][3]));
-      if (!any4 || __int_as_float((int)mx4) <= cstop) break;
+      if (!any4 || __int_as_float((int)mx4) <= cstop2) break;
     }
     if (t == 0) s_cur = cur;
   }
@@ -1964,11 +2002,12 @@ __device__ __forceinline__ void JacobiRowsOp::body(const Grid g, const Args& arg
     if (lane == 0) sig[q] = sqrtf(v);
   }
   __syncthreads();
+  const float unsc = ldexpf(1.0f, s_exp);   // exact
   for (int q = t; q < n; q += blockDim.x) {
     int rank = 0;
     for (int k = 0; k < n; ++k) rank += (sig[k] > sig[q]) || (sig[k] == sig[q] && k < q);
     rankof[q] = rank;
-    sv[rank] = (double)sig[q];
+    sv[rank] = (double)sig[q] * (double)unsc;
   }
   __syncthreads();
   for (int e = t; e < n * n; e += blockDim.x) {
