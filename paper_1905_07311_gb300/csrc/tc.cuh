@@ -283,6 +283,17 @@ __device__ __forceinline__ float convert_tile_kmajor(const uint8_t* __restrict__
 // infinities, S.1111.111 = NaN) as an FP32 number, exactly: a normal code has value
 // 2^(e - 7) (1 + m / 8), i.e. FP32 exponent field e + 120 and the 3 mantissa bits on top of the
 // FP32 mantissa; a subnormal code (e = 0) has value m 2^-9.
+// The E4M3 values in bits 0-7 (e0) and 8-15 (e1) of w, by the hardware conversion to a pair of
+// FP16 values (every E4M3 value, subnormals included, is an FP16 value) and then to FP32: exact,
+// and equal to e4m3_to_f32 of each byte for every finite value.
+__device__ __forceinline__ void e4m3x2_to_f32(uint32_t w, float& e0, float& e1) {
+  const uint16_t b = (uint16_t)(w & 0xFFFFu);
+  asm("{\n.reg .b32 h2;\n.reg .b16 lo, hi;\ncvt.rn.f16x2.e4m3x2 h2, %2;\nmov.b32 {lo, hi}, h2;\n"
+      "cvt.f32.f16 %0, lo;\ncvt.f32.f16 %1, hi;\n}"
+      : "=f"(e0), "=f"(e1)
+      : "h"(b));
+}
+
 __device__ __forceinline__ float e4m3_to_f32(uint32_t b) {
   const uint32_t e = (b >> 3) & 15u, m = b & 7u;
   float v = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : __fmul_rn((float)m, 0x1p-9f);
@@ -327,8 +338,10 @@ __device__ __forceinline__ float convert_fp8_tile(const uint8_t* __restrict__ sr
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const uint32_t word = w[q >> 1] >> (16 * (q & 1));
-      const float x0 = __fmul_rn(e4m3_to_f32(word & 0xFFu), sc[j]);
-      const float x1 = __fmul_rn(e4m3_to_f32((word >> 8) & 0xFFu), sc[j]);
+      float e0, e1;   // the two E4M3 values of the low 16 bits, decoded exactly
+      e4m3x2_to_f32(word, e0, e1);
+      const float x0 = __fmul_rn(e0, sc[j]);
+      const float x1 = __fmul_rn(e1, sc[j]);
       h[q] = pack_bf16x2(x0, x1);
       const float f0 = __uint_as_float(h[q] << 16), f1 = __uint_as_float(h[q] & 0xFFFF0000u);
       if constexpr (kTwoPieces) {
