@@ -253,7 +253,7 @@ size_t chol_smem(int n, size_t velem) {
 // pivot <= kPivot C_kk (1e-14 in FP64 / double-float, 1e-5 in FP32) or not finite: CholeskyQR2 is then not accurate enough and the Householder
 // branch takes over.  Right-looking on the unscaled Schur complement S (S_kj = R_kk R_kj after step
 // k - 1): S_ij -= S_ki S_kj / S_kk for k < i <= j, one barrier per step.  Thread 0 updates the next
-// pivot S_{k+1,k+1} first and prepares its 1 / sqrt; the other threads share the remaining
+// pivot S_{k+1,k+1} first and prepares its 1 / sqrt; warps 1.. share the remaining
 // entries of the trailing triangle through the table (no idle predicated work).
 template <class Ar>
 struct CholOp {
@@ -343,11 +343,13 @@ __device__ __forceinline__ void CholOp<Ar>::body(const Grid g, const Args& args)
         bad = 1;
       else
         rinv[k + 1] = Ar::rsq(v);
-    } else {
-      // two table entries per pass, operands read before either result is written
+    } else if (t >= 32) {
+      // warps 1.. share the trailing triangle, two table entries per pass, operands read before
+      // either result is written; warp 0 is left to thread 0's pivot chain (lanes of one warp that
+      // took both paths would run them one after the other)
       const int T = (n - k - 1) * (n - k) / 2;
-      const int stride = blockDim.x - 1;
-      for (int e = t - 1; e < T; e += 2 * stride) {
+      const int stride = blockDim.x - 32;
+      for (int e = t - 32; e < T; e += 2 * stride) {
         const int e2 = e + stride;
         const int ij = tab[e];
         const int ij2 = e2 < T ? tab[e2] : ij;
