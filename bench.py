@@ -233,8 +233,8 @@ def run_ours(args):
     if world > 1:
         return run_sharded(args, torch, dist, world, rank, local, device, rh, L)
     X = make_input(torch, device, seed_offset=rank)
-    tc = args.form == "f32_bf16x2"
-    form = "f32_bf16x2" if tc else torch.float32
+    tc = args.form in ("f32_bf16x2", "f32_bf16x3")
+    form = args.form if tc else torch.float32
     call = rh.RsthosvdCall(DIMS, form, RANKS, p=P, seed=SEED, rho=RHO, device=device)
     for _ in range(args.warmup):
         call.run(X)
@@ -372,10 +372,13 @@ def run_ours(args):
         line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "time_to_tucker_ms": round(ms_step, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x2" if tc else "f32",
-                "form": ("FP32 X split on the fly into exact BF16 head + tail (16 significant bits) for the "
-                         "first mode's tensor-core sketch and mode product, Omega in BF16, FP32 accumulation; "
-                         "later modes FP32 on the CUDA cores") if tc else "FP32 on the CUDA cores",
+                "dtype": {"f32_bf16x2": "bf16x2", "f32_bf16x3": "bf16x3"}.get(args.form, "f32"),
+                "form": {"f32_bf16x2": "FP32 X split on the fly into BF16 head + tail (16 significant bits) in every "
+                                       "tensor-core sketch, mode product and core product, Omega in BF16, FP32 "
+                                       "accumulation",
+                         "f32_bf16x3": "FP32 X split on the fly exactly into three BF16 pieces (24 significant "
+                                       "bits) in every tensor-core sketch, mode product and core product, Omega in "
+                                       "BF16, FP32 accumulation"}.get(args.form, "FP32 on the CUDA cores"),
                 "data": "synthetic (seeded generator, inputs resident in HBM before timing)",
                 "config": {"workload": WORKLOAD, "dims": DIMS, "ranks": RANKS, "p": P, "seed": SEED,
                            "order": [n + 1 for n in RHO], "parallelism": f"independent tensor per GPU x{world}",
@@ -1222,9 +1225,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-slab", type=int, default=None,
                     help="mode-3 extent of the CPU sample (default 384 for the baseline, 128 per reference step)")
-    ap.add_argument("--form", default="f32_bf16x2", choices=["f32_bf16x2", "f32"],
-                    help="f32_bf16x2: first mode on the tensor cores over the on-the-fly BF16 split of X "
-                         "(default); f32: CUDA-core FP32 throughout")
+    ap.add_argument("--form", default="f32_bf16x2", choices=["f32_bf16x2", "f32_bf16x3", "f32"],
+                    help="f32_bf16x2: tensor cores over the on-the-fly BF16 head + tail split of X (default); "
+                         "f32_bf16x3: the exact three-piece split; f32: CUDA-core FP32 throughout")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -75,6 +75,16 @@ enum {
  *                   or I_0 % 8 != 0, I_0 > 1024) runs in FP32 on the CUDA cores instead of being
  *                   rejected, so the form accepts any FP32 tensor (info bit 4 shows which modes
  *                   ran on the tensor cores).
+ *   RH_F32_BF16X3   a plain FP32 array read exactly: every tensor-core kernel of rsthosvd and
+ *                   rhosvd (sketches, mode products, core products) splits each FP32 tile into
+ *                   three BF16 pieces h = bf16(x), m = bf16(x - h), t = bf16(x - h - m) with
+ *                   h + m + t = x (24 significant bits), so every product with a BF16 operand is
+ *                   the exact product with x; the factor Q of a mode product and U of a core
+ *                   product keep two pieces (16 significant bits).  ||X||^2 is that of the FP32
+ *                   values.  Shapes the tensor-core kernels do not cover (and first modes with few
+ *                   rows) run in FP32 on the CUDA cores.  Not with subspace iteration
+ *                   (power_iters > 0), and not on the grouped engine of rsthosvd_batched (its
+ *                   stream engine runs it).
  *   RH_FP8_E4M3     a tensor stored in FP8 E4M3 (OCP FP8: bias 7, max 448, no infinities) with one
  *                   FP32 scale per 128 bytes of storage.  Buffer layout (see rh_fp8_layout): the
  *                   E4M3 bytes column-major with the mode-1 fibres at a stride of ld = I_1 rounded up
@@ -96,7 +106,7 @@ enum {
  * BF16, FP32 sums in tensor memory over a CTA's columns and FP64 across CTAs), and every later mode
  * in FP32 on the CUDA cores; such requests can run on the grouped engine of rsthosvd_batched.
  * info bit 4 marks the modes that ran on the tensor cores. */
-enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4, RH_FP8_E4M3 = 5 };
+enum { RH_F64 = 0, RH_F32 = 1, RH_BF16 = 2, RH_BF16X2 = 3, RH_F32_BF16X2 = 4, RH_FP8_E4M3 = 5, RH_F32_BF16X3 = 6 };
 
 /* rh_fp8_layout -- storage of an RH_FP8_E4M3 tensor with sizes dims (see above): *ld = the stride
  * of the mode-1 fibres in bytes, *scale_offset = the byte offset of the scales, *nscales = their

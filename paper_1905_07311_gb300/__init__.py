@@ -55,14 +55,17 @@ def _check_input(X, dims, factor=1):
     return torch
 
 
-_FORMS = {"bf16": 2, "bf16x2": 3, "f32_bf16x2": 4, "fp8_e4m3": 5}
+_FORMS = {"bf16": 2, "bf16x2": 3, "f32_bf16x2": 4, "fp8_e4m3": 5, "f32_bf16x3": 6}
 
 
 def _piece_form(pieces):
     """dtype code of a tensor-core input: pieces=2 (split_bf16x2 output), 1 (BF16 bits), "f32"
-    (a plain FP32 tensor split on the fly, RH_F32_BF16X2) or "fp8" (an RH_FP8_E4M3 buffer)."""
+    (a plain FP32 tensor split on the fly, RH_F32_BF16X2), "f32x3" (split exactly into three pieces,
+    RH_F32_BF16X3) or "fp8" (an RH_FP8_E4M3 buffer)."""
     if pieces == "f32":
         return _lib.RH_F32_BF16X2
+    if pieces == "f32x3":
+        return _lib.RH_F32_BF16X3
     if pieces == "fp8":
         return _lib.RH_FP8_E4M3
     return _lib.RH_BF16X2 if pieces == 2 else _lib.RH_BF16
@@ -622,7 +625,8 @@ def rsthosvd(X, dims, ranks, p=5, seed=0, rho=None, tensor_id=0, clamp=False, tr
     """R-STHOSVD (Alg. 3) of the flat column-major tensor X with sizes ``dims``.
 
     ``form="bf16x2"`` (X from split_bf16x2), ``form="bf16"`` (X holding BF16 bit patterns),
-    ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly) or ``form="fp8_e4m3"`` (X a uint8
+    ``form="f32_bf16x2"`` (a plain FP32 X, split on the fly), ``form="f32_bf16x3"`` (a plain FP32 X
+    split exactly into three pieces in every tensor-core kernel) or ``form="fp8_e4m3"`` (X a uint8
     buffer in the layout of fp8_layout) selects the tensor-core forms for the first mode.
     ``svd_route=1`` keeps the SVD of B on the tall-skinny QR (see rh_options.svd_route).
     ``power_iters`` adds that many randomized subspace-iteration steps to every range finder."""

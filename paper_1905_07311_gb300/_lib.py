@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "librhosvd.so")
 
 RH_MAX_ORDER = 8
 RH_MAX_ELL = 64
-RH_F64, RH_F32, RH_BF16, RH_BF16X2, RH_F32_BF16X2, RH_FP8_E4M3 = 0, 1, 2, 3, 4, 5
+RH_F64, RH_F32, RH_BF16, RH_BF16X2, RH_F32_BF16X2, RH_FP8_E4M3, RH_F32_BF16X3 = 0, 1, 2, 3, 4, 5, 6
 STATUS = {0: "RH_OK", 1: "RH_EINVAL", 2: "RH_ENOMEM", 3: "RH_ECUDA", 4: "RH_ENUMERIC", 5: "RH_ETIMEOUT",
           6: "RH_EUNSUPPORTED"}
 

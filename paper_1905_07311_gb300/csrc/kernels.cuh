@@ -38,10 +38,11 @@ bool sketch_tc_supported(const ModeView& v, int ell);
 int sketch_tc_ctas(const ModeView& v);
 rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, uint64_t seed,
                            uint32_t sid, float* part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
-// FP32 input split on the fly into the same two pieces; norm_part (sketch_tc_ctas doubles, may
-// be NULL) receives per-CTA sums of squares of the split values
+// FP32 input split on the fly into the same two pieces (pieces = 3: an exact three-piece split);
+// norm_part (sketch_tc_ctas doubles, may be NULL) receives per-CTA sums of squares of the split
+// values
 rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
-                               double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
+                               double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0, int pieces = 2);
 // E4M3 input (leading dimension ld, one FP32 scale per 128 bytes of storage), dequantized and
 // split on the fly into the same two pieces as FP32 input
 rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
@@ -51,7 +52,7 @@ rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, con
 // (l, i, r), split on the fly, K-major pieces (rows i, K = l); same partial sketches as launch_sketch_tc_f32
 bool sketch_tc_strided_supported(const ModeView& v, int ell);
 rh_status launch_sketch_tc_f32s(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
-                                double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0);
+                                double* norm_part, int32_t* err, cudaStream_t st, int64_t row0 = 0, int pieces = 2);
 // A first mode with few rows (L = 1, I <= 128, ell <= 32) on the tensor cores as grouped operations
 // (small_tc.cu).  The input in one of the BF16 forms: RH_F32_BF16X2 (FP32, split on the fly into
 // head + tail), RH_BF16, RH_BF16X2 (the two pieces) or RH_FP8_E4M3 (bytes at stride ld, scales).
@@ -82,18 +83,19 @@ int ttm_tc_ctas(const ModeView& v);
 // qa: 128 x I BF16 scratch for the split Q; B: ell x M FP32 (layout c + ell p)
 rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
                         uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
+// FP32 X split on the fly into two BF16 pieces (pieces = 3: exactly, into three)
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                            int32_t* err, cudaStream_t st);
+                            int32_t* err, cudaStream_t st, int pieces = 2);
 // a mode with L > 1 (L % 128 == 0): B in the (L, ell, R) layout, qa 128 x ceil8(I) BF16
 bool ttm_tc_strided_supported(const ModeView& v, int ell);
 rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                             int32_t* err, cudaStream_t st);
+                             int32_t* err, cudaStream_t st, int pieces = 2);
 // G <- U^T B on the tensor cores for a truncated core (Alg. 1 step 6): B ell x M FP32 (layout
 // c + ell p, split on the fly), U ell x ko FP32 (split into two BF16 pieces in qa, 128 x ceil8(ell)),
 // out[co.base(p) + c co.cstride()] FP32 (see CoreOut).  Needs ell % 4 == 0, ell, ko <= 64.
 bool core_product_tc_supported(int ell, int ko, int64_t M);
 rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, uint16_t* qa,
-                                 float* out, int32_t* err, cudaStream_t st);
+                                 float* out, int32_t* err, cudaStream_t st, int pieces = 2);
 rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
                             const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
 
@@ -123,11 +125,11 @@ rh_status launch_core_product(const float* B, int ell, int ko, int64_t M, CoreOu
 // returns the elements of each of the two ping-pong buffers; *fac_elems = sum I_n k_n
 size_t core_chain_elems(int d, const int64_t* dims, const int32_t* ks, size_t* fac_elems);
 // split_tc: FP32 data in the RH_F32_BF16X2 form, the products the tensor-core mode product covers run
-// there (qa: 128 x ceil8(max I_n) BF16 scratch, err: wait status)
+// there (qa: 128 x ceil8(max I_n) BF16 scratch, err: wait status; pieces = 3: the exact split)
 template <typename T>
 rh_status launch_core_ttm(int d, const int64_t* dims, const T* X, const double* const* factors, const int32_t* ks,
                           double* G, T* fac, T* W0, T* W1, cudaStream_t st, bool split_tc = false,
-                          uint16_t* qa = nullptr, int32_t* err = nullptr);
+                          uint16_t* qa = nullptr, int32_t* err = nullptr, int pieces = 2);
 
 // ---- small dense linear algebra (smallla.cu) --------------------------------------------
 size_t orth_workspace_elems(int64_t m, int n);   // doubles

@@ -86,6 +86,7 @@ struct Plan {
   size_t tc_part = 0, qa_elems = 0;
   std::vector<int64_t> dims0;   // the input sizes
   int power = 0;                // subspace-iteration steps per range finder
+  int pieces = 2;               // BF16 pieces of the on-the-fly split (3: RH_F32_BF16X3, exact)
 };
 
 // Subspace iteration (opts.power_iters): the dense-operand sketch plan of every step and the
@@ -94,7 +95,7 @@ rh_status plan_power(const rh_options& o, Plan& pl) {
   RH_CHECK_ARG(o.power_iters >= 0 && o.power_iters <= 8, "power_iters must be in [0, 8]");
   pl.power = o.power_iters;
   if (!pl.power) return RH_OK;
-  if (pl.in_form >= 0 && pl.in_form != RH_F32_BF16X2) {
+  if ((pl.in_form >= 0 && pl.in_form != RH_F32_BF16X2) || pl.pieces != 2) {
     set_error("unsupported: subspace iteration needs FP64, FP32 or RH_F32_BF16X2 input (its sketch reads G_(n) "
               "on the CUDA cores)");
     return RH_EUNSUPPORTED;
@@ -110,6 +111,9 @@ rh_status plan_power(const rh_options& o, Plan& pl) {
 
 rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks, const rh_options& o,
                     Plan& pl) {
+  // RH_F32_BF16X3 is the split form with three exact pieces in every tensor-core kernel
+  pl.pieces = dtype == RH_F32_BF16X3 ? 3 : 2;
+  if (dtype == RH_F32_BF16X3) dtype = RH_F32_BF16X2;
   rh_status s = check_tensor(order, dims, bf16_form(dtype) ? RH_F32 : dtype);
   if (s != RH_OK) return s;
   RH_CHECK_ARG(ranks != nullptr, "ranks is NULL");
@@ -172,7 +176,7 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
     // on the fly can also take the FP32 CUDA-core path for a first mode the tensor-core kernels
     // do not cover (later modes still go to the tensor cores where their shape allows).
     const Step& s0 = pl.steps[0];
-    if (o.power_iters == 0 && small_tc_supported(s0.v, s0.ell)) {
+    if (o.power_iters == 0 && pl.pieces == 2 && small_tc_supported(s0.v, s0.ell)) {
       // A first mode with few rows (mode 0, I_0 <= 128, ell <= 32): the small-row tensor-core
       // sketch and mode product, written as grouped operations; the later modes run in FP32 on
       // the CUDA cores on the FP32 core the first mode leaves.
@@ -257,6 +261,8 @@ rh_status make_plan(int32_t order, const int64_t* dims, int32_t dtype, const int
 // in FP32 on the CUDA cores.
 rh_status make_plan_hosvd(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
                           const rh_options& o, Plan& pl) {
+  pl.pieces = dtype == RH_F32_BF16X3 ? 3 : 2;
+  if (dtype == RH_F32_BF16X3) dtype = RH_F32_BF16X2;
   const bool split = dtype == RH_F32_BF16X2;
   rh_status s = check_tensor(order, dims, split ? RH_F32 : dtype);
   if (s != RH_OK) return s;
@@ -484,7 +490,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
                                    norms ? b.part_norm : nullptr, b.err, st);
         else
           s = launch_sketch_tc_f32(sp.v, sp.ell, tc_src, o.seed, sid, b.tc_part,
-                                   (first && norms) ? b.part_norm : nullptr, b.err, st);
+                                   (first && norms) ? b.part_norm : nullptr, b.err, st, 0, pl.pieces);
         if (s != RH_OK) return s;
       }
       SketchPlan rp = sp.sk;
@@ -537,7 +543,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       else if (in_fp8)
         s = launch_ttm_tc_fp8(sp.v, sp.ell, x8, scales8, f8.ld, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
       else
-        s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
+        s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st, pl.pieces);
       if (s != RH_OK) return s;
     } else {
       ProfileScope ps(PROF_TTM, j, st);
@@ -574,7 +580,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
           const int wg = 1 - wb;
           if (sp.cp_tc)
             s = launch_core_product_tc(Bf, sp.ell, sp.ko, sp.v.M(), sp.cout, Uf, b.qa, static_cast<float*>(b.W[wg]),
-                                       b.err, st);
+                                       b.err, st, pl.pieces);
           else
             s = launch_core_product<float>(Bf, sp.ell, sp.ko, sp.v.M(), sp.cout, Uf, static_cast<float*>(b.W[wg]),
                                            st);
@@ -637,8 +643,8 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
       {
         ProfileScope ps(PROF_SKETCH, (int)j, st);
         double* np = n2 ? b.part_norm : nullptr;
-        s = sp.v.L == 1 ? launch_sketch_tc_f32(sp.v, sp.ell, Xf, o.seed, sid, b.tc_part, np, b.err, st)
-                        : launch_sketch_tc_f32s(sp.v, sp.ell, Xf, o.seed, sid, b.tc_part, np, b.err, st);
+        s = sp.v.L == 1 ? launch_sketch_tc_f32(sp.v, sp.ell, Xf, o.seed, sid, b.tc_part, np, b.err, st, 0, pl.pieces)
+                        : launch_sketch_tc_f32s(sp.v, sp.ell, Xf, o.seed, sid, b.tc_part, np, b.err, st, 0, pl.pieces);
         if (s != RH_OK) return s;
       }
       SketchPlan rp = sp.sk;
@@ -673,8 +679,8 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
       ProfileScope ps(PROF_TTM, (int)j, st);
       if (tc) {
         float* Bf = reinterpret_cast<float*>(B);
-        s = sp.v.L == 1 ? launch_ttm_tc_f32(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st)
-                        : launch_ttm_tc_f32s(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st);
+        s = sp.v.L == 1 ? launch_ttm_tc_f32(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st, pl.pieces)
+                        : launch_ttm_tc_f32s(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st, pl.pieces);
         if (s != RH_OK) return s;
       } else if ((s = launch_ttm<T, T>(sp.v, X, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) {
         return s;
@@ -694,7 +700,8 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
   {
     ProfileScope ps(PROF_TTM_CORE, 0, st);
     if ((s = launch_core_ttm<T>(pl.d, dims, X, factors, ks.data(), core, static_cast<T*>(b.fac),
-                                static_cast<T*>(b.W[0]), static_cast<T*>(b.W[1]), st, split, b.qa, b.err)) != RH_OK)
+                                static_cast<T*>(b.W[0]), static_cast<T*>(b.W[1]), st, split, b.qa, b.err,
+                                pl.pieces)) != RH_OK)
       return s;
   }
   if (split && info && (s = set_info_bits(info + pl.steps.back().mode, 0, st, b.err)) != RH_OK) return s;
@@ -728,9 +735,11 @@ static bool sketch_small_route(int32_t dtype, const ModeView& v, int32_t ell, in
   return mode == 0 && !sketch_tc_supported(v, ell) && small_tc_supported(v, ell);
 }
 
-static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell, int32_t mode = 0, int32_t dtype = RH_BF16) {
+static size_t sketch_tc_ws(int32_t order, const int64_t* dims, int32_t ell, int32_t mode = 0, int32_t dtype = RH_BF16,
+                           bool allow_small = true) {
   const ModeView v = mode_view(order, dims, mode);
-  const int64_t S = sketch_small_route(dtype, v, ell, mode) ? plan_sketch_small_tc(v, ell).S : sketch_tc_ctas(v);
+  const int64_t S =
+      allow_small && sketch_small_route(dtype, v, ell, mode) ? plan_sketch_small_tc(v, ell).S : sketch_tc_ctas(v);
   Arena ar(nullptr);
   ar.take<int32_t>(4);   // wait status, first (documented)
   ar.take<float>((size_t)S * ell * v.I);
@@ -752,6 +761,9 @@ rh_status rh_fp8_layout(int32_t order, const int64_t* dims, int64_t* ld, size_t*
 }
 
 size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t ell) {
+  // RH_F32_BF16X3: the split form's tensor-core kernels with three exact pieces (no small-row route)
+  const bool x3 = dtype == RH_F32_BF16X3;
+  if (x3) dtype = RH_F32_BF16X2;
   if (is_bf16_form(dtype)) {
     if (order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode < 0 || mode >= order || ell < 1 ||
         ell > RH_MAX_ELL)
@@ -759,7 +771,7 @@ size_t rhosvd_sketch_workspace_size(int32_t order, const int64_t* dims, int32_t 
     if (mode != 0 && dtype != RH_F32_BF16X2) return 0;
     for (int k = 0; k < order; ++k)
       if (dims[k] < 1) return 0;
-    return sketch_tc_ws(order, dims, ell, mode, dtype);
+    return sketch_tc_ws(order, dims, ell, mode, dtype, !x3);
   }
   if (check_tensor(order, dims, dtype) != RH_OK || mode < 0 || mode >= order || ell < 1 || ell > RH_MAX_ELL) return 0;
   const SketchPlan pl = plan_sketch(mode_view(order, dims, mode), ell);
@@ -781,6 +793,8 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
   clear_error();
   RH_CHECK_ARG(row0 >= 0, "row0 must be >= 0");
   RH_CHECK_ARG(accumulate == 0 || accumulate == 1, "accumulate must be 0 or 1");
+  const bool x3 = dtype == RH_F32_BF16X3;
+  if (x3) dtype = RH_F32_BF16X2;
   if (is_bf16_form(dtype)) {
     RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
     for (int k = 0; k < order; ++k) RH_CHECK_ARG(dims[k] >= 1, "every dimension must be >= 1");
@@ -791,7 +805,7 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
     RH_CHECK_ARG(X != nullptr && Y != nullptr, "X and Y must be non-NULL");
     RH_CHECK_ARG(norm2 == nullptr || converted_form(dtype), "norm2 is not available for RH_BF16 / RH_BF16X2");
     const ModeView v = mode_view(order, dims, mode);
-    const bool small = sketch_small_route(dtype, v, ell, mode);
+    const bool small = !x3 && sketch_small_route(dtype, v, ell, mode);
     if (!small && (mode == 0 ? !sketch_tc_supported(v, ell) : !sketch_tc_strided_supported(v, ell))) {
       set_error(mode == 0 ? "unsupported: the BF16 sketch needs I_0 % 8 == 0 and I_0 <= 1024, or I_0 <= 128 and "
                             "ell <= 32"
@@ -799,7 +813,7 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
                             "be a multiple of 64 and I_n <= 1024");
       return RH_EUNSUPPORTED;
     }
-    const size_t need = sketch_tc_ws(order, dims, ell, mode, dtype);
+    const size_t need = sketch_tc_ws(order, dims, ell, mode, dtype, !x3);
     if (workspace == nullptr || workspace_bytes < need) {
       set_error("workspace too small: need " + std::to_string(need) + " bytes");
       return RH_ENOMEM;
@@ -829,9 +843,9 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
       if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st, accumulate);
     } else if (dtype == RH_F32_BF16X2) {
       s = mode == 0 ? launch_sketch_tc_f32(v, ell, static_cast<const float*>(X), seed, sid, part,
-                                           norm2 ? norm_part : nullptr, err, st, row0)
+                                           norm2 ? norm_part : nullptr, err, st, row0, x3 ? 3 : 2)
                     : launch_sketch_tc_f32s(v, ell, static_cast<const float*>(X), seed, sid, part,
-                                            norm2 ? norm_part : nullptr, err, st, row0);
+                                            norm2 ? norm_part : nullptr, err, st, row0, x3 ? 3 : 2);
       if (s == RH_OK && norm2) s = launch_sum_n(norm_part, S, norm2, st, accumulate);
     } else if (dtype == RH_FP8_E4M3) {
       const Fp8Layout f8 = fp8_layout(order, dims);
@@ -878,7 +892,9 @@ rh_status rhosvd_sketch_offset(int32_t order, const int64_t* dims, int32_t dtype
 }
 
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k) {
-  if (!bf16_form(dtype) || order < 1 || order > RH_MAX_ORDER || dims == nullptr || mode != 0) return 0;
+  if (!(bf16_form(dtype) || dtype == RH_F32_BF16X3) || order < 1 || order > RH_MAX_ORDER || dims == nullptr ||
+      mode != 0)
+    return 0;
   Arena ar(nullptr);
   ar.take<int32_t>(4);   // wait status, first (documented)
   ar.take<uint16_t>((size_t)128 * dims[0]);
@@ -925,13 +941,15 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
 rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
                                const double* A, float* Y, void* workspace, size_t workspace_bytes, void* stream) {
   clear_error();
-  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16, RH_BF16X2, RH_F32_BF16X2 or RH_FP8_E4M3");
+  const bool x3 = dtype == RH_F32_BF16X3;   // the split form with three exact pieces
+  if (x3) dtype = RH_F32_BF16X2;
+  RH_CHECK_ARG(bf16_form(dtype), "dtype must be RH_BF16, RH_BF16X2, RH_F32_BF16X2, RH_F32_BF16X3 or RH_FP8_E4M3");
   RH_CHECK_ARG(order >= 1 && order <= RH_MAX_ORDER && dims != nullptr, "bad order or dims");
   for (int q = 0; q < order; ++q) RH_CHECK_ARG(dims[q] >= 1, "every dimension must be >= 1");
   RH_CHECK_ARG(X != nullptr && A != nullptr && Y != nullptr, "X, A and Y must be non-NULL");
   const ModeView v = mode_view(order, dims, 0);
-  // I_0 % 8 != 0: the small-row kernel (I_0 <= 128, k <= 32)
-  const bool small = !ttm_tc_supported(v, k) && small_tc_supported(v, k);
+  // I_0 % 8 != 0: the small-row kernel (I_0 <= 128, k <= 32); not for the three-piece form
+  const bool small = !x3 && !ttm_tc_supported(v, k) && small_tc_supported(v, k);
   if (!ttm_tc_supported(v, k) && !small) {
     set_error("unsupported: the BF16 mode product needs I_0 % 8 == 0 and 1 <= k <= 64, or I_0 <= 128 and k <= 32");
     return RH_EUNSUPPORTED;
@@ -955,7 +973,8 @@ rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype
     }
     return launch_ttm_small_tc(v, in, A, k, Y, err, st, SITE_OTHER);
   }
-  if (dtype == RH_F32_BF16X2) return launch_ttm_tc_f32(v, k, static_cast<const float*>(X), A, qa, Y, err, st);
+  if (dtype == RH_F32_BF16X2)
+    return launch_ttm_tc_f32(v, k, static_cast<const float*>(X), A, qa, Y, err, st, x3 ? 3 : 2);
   if (dtype == RH_FP8_E4M3) {
     const Fp8Layout f8 = fp8_layout(order, dims);
     const uint8_t* x8 = static_cast<const uint8_t*>(X);

@@ -55,10 +55,10 @@ struct SketchCfg {
   static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
 };
 
-template <int IN>
+template <int IN, int NP = 2>
 struct alignas(1024) SketchSmem {
   uint8_t xf[SketchCfg<IN>::kF32Stages][SketchCfg<IN>::kStageBytes];
-  uint8_t x[SketchCfg<IN>::kPStages][2][kPieceTile];   // [stage][piece][128 x 64]
+  uint8_t x[SketchCfg<IN>::kPStages][NP][kPieceTile];   // [stage][piece][128 x 64]
   uint8_t om[kOmBufs][kOmegaTile];
   uint64_t f32full[SketchCfg<IN>::kF32Stages], f32empty[SketchCfg<IN>::kF32Stages];
   uint64_t full[SketchCfg<IN>::kPStages], empty[SketchCfg<IN>::kPStages], om_full[kOmBufs], om_empty[kOmBufs], done;
@@ -80,7 +80,9 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int col) {
 // (box 128 x 64 bytes, leading dimension ld), dequantized with ``scales`` and rounded to one BF16
 // piece on the fly (npieces = 1).  With converted
 // input, norm_part[blockIdx.x] receives this CTA's sum of squares of the split values (head + tail).
-template <int IN>
+// NP = 3 (FP32 input): the values are split exactly into three BF16 pieces (npieces = 3), three
+// MMAs per K step, and the norm is that of the FP32 values themselves.
+template <int IN, int NP = 2>
 __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, int npieces,
                      int64_t I, int64_t M, int ell, int mtiles, int64_t chunks_per_cta, uint32_t k0, uint32_t k1,
@@ -92,8 +94,8 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
   constexpr int NS = Cfg::kPStages;
   constexpr int NF = Cfg::kF32Stages;
   extern __shared__ uint8_t smem_raw[];
-  SketchSmem<IN>& S =
-      *reinterpret_cast<SketchSmem<IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  SketchSmem<IN, NP>& S =
+      *reinterpret_cast<SketchSmem<IN, NP>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (M + kPChunk - 1) / kPChunk;
   // chunks are dealt round-robin (c = blockIdx.x, blockIdx.x + gridDim.x, ...)
@@ -268,9 +270,11 @@ __global__ void __launch_bounds__(SketchCfg<IN>::kThreads, 1)
           acc += (double)tc::convert_fp8_tile<128, 64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], nullptr, t, scales,
                                                                    ld, (int64_t)m * kRowsTile, c * kPChunk, I, M);
         else if constexpr (IN == tc::kInF32S)
-          acc += (double)tc::convert_tile_kmajor<Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+          acc += (double)tc::convert_tile_kmajor<Cfg::kConv, NP>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t,
+                                                                 NP == 3 ? &S.x[ps][NP - 1][0] : nullptr);
         else
-          acc += (double)tc::convert_tile_plain<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+          acc += (double)tc::convert_tile_plain<64, Cfg::kConv, NP>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t,
+                                                                    NP == 3 ? &S.x[ps][NP - 1][0] : nullptr);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&S.f32empty[s]);
         tc::mbar_arrive(&S.full[ps]);
@@ -487,8 +491,25 @@ bool sketch_tc_strided_supported(const ModeView& v, int ell) {
          v.M() < (int64_t(1) << 31) && v.R < (int64_t(1) << 31);
 }
 
+template <int IN, int NP>
+static rh_status launch_sketch_tc_conv(const CUtensorMap& m0, const ModeView& v, int ell, uint64_t seed, uint32_t sid,
+                                       float* part, double* norm_part, int32_t* err, cudaStream_t st, int64_t row0,
+                                       int64_t L) {
+  const int ctas = sketch_tc_ctas(v);
+  const int64_t nchunks = ceil_div(v.M(), kPChunk);
+  const int64_t cpc = ceil_div(nchunks, ctas);
+  const int mtiles = (int)ceil_div(v.I, kRowsTile);
+  const size_t smem = sizeof(SketchSmem<IN, NP>) + 1024;
+  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<IN, NP><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
+      m0, m0, NP, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
+      norm_part, err, nullptr, 0, tc_probe_next(), row0, L);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
 rh_status launch_sketch_tc_f32s(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
-                                double* norm_part, int32_t* err, cudaStream_t st, int64_t row0) {
+                                double* norm_part, int32_t* err, cudaStream_t st, int64_t row0, int pieces) {
   if (!sketch_tc_strided_supported(v, ell)) {
     set_error("tensor-core sketch: unsupported strided shape (needs L % 64 == 0, I <= 1024, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -496,18 +517,8 @@ rh_status launch_sketch_tc_f32s(const ModeView& v, int ell, const float* X, uint
   CUtensorMap m0;
   rh_status s = make_map_3d_f32(&m0, X, v.L, v.I, v.R, 64, kRowsTile);
   if (s != RH_OK) return s;
-  const int ctas = sketch_tc_ctas(v);
-  const int64_t nchunks = ceil_div(v.M(), kPChunk);
-  const int64_t cpc = ceil_div(nchunks, ctas);
-  const int mtiles = (int)ceil_div(v.I, kRowsTile);
-  constexpr int IN = tc::kInF32S;
-  const size_t smem = sizeof(SketchSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
-      m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, nullptr, 0, tc_probe_next(), row0, v.L);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return pieces == 3 ? launch_sketch_tc_conv<tc::kInF32S, 3>(m0, v, ell, seed, sid, part, norm_part, err, st, row0, v.L)
+                     : launch_sketch_tc_conv<tc::kInF32S, 2>(m0, v, ell, seed, sid, part, norm_part, err, st, row0, v.L);
 }
 
 bool sketch_tc_supported(const ModeView& v, int ell) {
@@ -550,7 +561,7 @@ rh_status launch_sketch_tc(const ModeView& v, int ell, const uint16_t* piece0, c
 }
 
 rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint64_t seed, uint32_t sid, float* part,
-                               double* norm_part, int32_t* err, cudaStream_t st, int64_t row0) {
+                               double* norm_part, int32_t* err, cudaStream_t st, int64_t row0, int pieces) {
   if (!sketch_tc_supported(v, ell)) {
     set_error("tensor-core sketch: unsupported shape (needs the first mode, I % 8 == 0, I <= 1024, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -558,18 +569,8 @@ rh_status launch_sketch_tc_f32(const ModeView& v, int ell, const float* X, uint6
   CUtensorMap m0;
   rh_status s = make_map_2d_plain(&m0, X, 4, v.I, v.M(), kRowsTile, 64);
   if (s != RH_OK) return s;
-  const int ctas = sketch_tc_ctas(v);
-  const int64_t nchunks = ceil_div(v.M(), kPChunk);
-  const int64_t cpc = ceil_div(nchunks, ctas);
-  const int mtiles = (int)ceil_div(v.I, kRowsTile);
-  constexpr int IN = tc::kInF32;
-  const size_t smem = sizeof(SketchSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sketch_tc_kernel<IN><<<ctas, SketchCfg<IN>::kThreads, smem, st>>>(
-      m0, m0, 2, v.I, v.M(), ell, mtiles, cpc, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), sid, part,
-      norm_part, err, nullptr, 0, tc_probe_next(), row0, 1);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return pieces == 3 ? launch_sketch_tc_conv<tc::kInF32, 3>(m0, v, ell, seed, sid, part, norm_part, err, st, row0, 1)
+                     : launch_sketch_tc_conv<tc::kInF32, 2>(m0, v, ell, seed, sid, part, norm_part, err, st, row0, 1);
 }
 
 rh_status launch_sketch_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,

@@ -182,16 +182,56 @@ __device__ __forceinline__ void split4_bf16x2(const float4 v, uint2& h, uint2& t
   s23 = f2_fma(g23, g23, s23);
 }
 
+// The exact three-piece split of four FP32 values: h = bf16(v), m = bf16(v - h), t = bf16(v - h - m)
+// with both differences exact (each operand lies within a factor of two of the other) and t exact
+// in BF16 (v has 24 significant bits, h and m take the leading 8 each), so v = h + m + t.  s01 /
+// s23 accumulate v^2 lane-wise (the pieces add up to v exactly).
+__device__ __forceinline__ void split4_bf16x3(const float4 v, uint2& h, uint2& m, uint2& t, float2& s01,
+                                              float2& s23) {
+  const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
+  h.x = pack_bf16x2(v.x, v.y);
+  h.y = pack_bf16x2(v.z, v.w);
+  const float2 r01 = f2_sub(v01, bf16x2_unpack(h.x)), r23 = f2_sub(v23, bf16x2_unpack(h.y));
+  m.x = pack_bf16x2(r01.x, r01.y);
+  m.y = pack_bf16x2(r23.x, r23.y);
+  const float2 q01 = f2_sub(r01, bf16x2_unpack(m.x)), q23 = f2_sub(r23, bf16x2_unpack(m.y));
+  t.x = pack_bf16x2(q01.x, q01.y);
+  t.y = pack_bf16x2(q23.x, q23.y);
+  s01 = f2_fma(v01, v01, s01);
+  s23 = f2_fma(v23, v23, s23);
+}
+
+// Split of one float4 into NP = 2 pieces (head, tail: 16 significant bits; s accumulates
+// (head + tail)^2) or NP = 3 (exact; s accumulates v^2), stored at byte offset off of each piece.
+template <int NP>
+__device__ __forceinline__ void split_store(const float4 v, uint8_t* __restrict__ p0, uint8_t* __restrict__ p1,
+                                            uint8_t* __restrict__ p2, int off, float2& s01, float2& s23) {
+  static_assert(NP == 2 || NP == 3, "two or three pieces");
+  if constexpr (NP == 2) {
+    uint2 h, tl;
+    split4_bf16x2(v, h, tl, s01, s23);
+    *reinterpret_cast<uint2*>(p0 + off) = h;
+    *reinterpret_cast<uint2*>(p1 + off) = tl;
+  } else {
+    uint2 h, md, tl;
+    split4_bf16x3(v, h, md, tl, s01, s23);
+    *reinterpret_cast<uint2*>(p0 + off) = h;
+    *reinterpret_cast<uint2*>(p1 + off) = md;
+    *reinterpret_cast<uint2*>(p2 + off) = tl;
+  }
+}
+
 // Split a 32 KB tile of FP32 values staged by TMA (boxes of 32 values x kRowsPerBox rows, 128-byte
 // rows, 128-byte swizzle) into its BF16 head and tail, written as 128 rows of 64 values (128-byte
 // rows, 128-byte swizzle): box b, row r holds the values 32 (b & 1) .. 32 (b & 1) + 31 of output
 // row (b >> 1) kRowsPerBox + r.  Eight consecutive threads read one 128-byte FP32 row (4 values
 // each); the four rows of a warp are boxes b, b ^ 1 of two consecutive rows, so its 8-byte stores
 // fill whole 128-byte output rows (no bank conflicts).  Returns the FP32 sum of (head + tail)^2
-// over the values this thread handled.
-template <int kRowsPerBox, int kThreadsConv>
+// over the values this thread handled.  NP = 3: three pieces (hi, lo, lo2: exact, split_store) and
+// the sum of the values' squares.
+template <int kRowsPerBox, int kThreadsConv, int NP = 2>
 __device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
-                                              uint8_t* __restrict__ lo, int t) {
+                                              uint8_t* __restrict__ lo, int t, uint8_t* __restrict__ lo2 = nullptr) {
   static_assert(kThreadsConv == 256 && kRowsPerBox >= 128, "unit j of a thread is row 16 j + (t / 16) of box (t / 8) % 2");
   constexpr int kUnits = 2048 / kThreadsConv;
   // unit j of thread t: 16-byte piece k = t % 8 of row r = 16 j + t / 16 of box b = (t / 8) % 2;
@@ -205,12 +245,7 @@ __device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, u
   for (int j = 0; j < kUnits; ++j) v[j] = *reinterpret_cast<const float4*>(src + j * 2048);   // all loads first
   float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int j = 0; j < kUnits; ++j) {
-    uint2 h, tl;
-    split4_bf16x2(v[j], h, tl, s01, s23);
-    *reinterpret_cast<uint2*>(hi + off0 + j * 2048) = h;
-    *reinterpret_cast<uint2*>(lo + off0 + j * 2048) = tl;
-  }
+  for (int j = 0; j < kUnits; ++j) split_store<NP>(v[j], hi, lo, lo2, off0 + j * 2048, s01, s23);
   return (s01.x + s01.y) + (s23.x + s23.y);
 }
 
@@ -218,9 +253,9 @@ __device__ __forceinline__ float convert_tile(const uint8_t* __restrict__ f32, u
 // (value (i, p) at byte 512 p + 4 i, one TMA box of 512-byte rows); the output pieces are the same
 // (value (p, i) at (i / 64) kPRows 128 + 128 p + ((i % 64 / 8) ^ (p % 8)) 16 + 2 (i % 8)).  A warp
 // reads one 512-byte column (conflict-free) and writes two 128-byte output rows.
-template <int kPRows, int kThreadsConv>
+template <int kPRows, int kThreadsConv, int NP = 2>
 __device__ __forceinline__ float convert_tile_plain(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
-                                                    uint8_t* __restrict__ lo, int t) {
+                                                    uint8_t* __restrict__ lo, int t, uint8_t* __restrict__ lo2 = nullptr) {
   static_assert(kThreadsConv % 256 == 0, "unit j of a thread is column 8 j + (t / 32) of its first one");
   constexpr int kUnits = kPRows * 32 / kThreadsConv;
   constexpr int kColStep = kThreadsConv / 32;   // columns between a thread's consecutive units
@@ -234,12 +269,7 @@ __device__ __forceinline__ float convert_tile_plain(const uint8_t* __restrict__ 
   for (int j = 0; j < kUnits; ++j) v[j] = *reinterpret_cast<const float4*>(src + j * kColStep * 512);
   float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int j = 0; j < kUnits; ++j) {
-    uint2 h, tl;
-    split4_bf16x2(v[j], h, tl, s01, s23);
-    *reinterpret_cast<uint2*>(hi + off0 + j * kColStep * 128) = h;
-    *reinterpret_cast<uint2*>(lo + off0 + j * kColStep * 128) = tl;
-  }
+  for (int j = 0; j < kUnits; ++j) split_store<NP>(v[j], hi, lo, lo2, off0 + j * kColStep * 128, s01, s23);
   return (s01.x + s01.y) + (s23.x + s23.y);
 }
 
@@ -254,9 +284,9 @@ constexpr int kInPieces = 0, kInF32 = 1, kInFp8 = 2, kInF32S = 3;
 // 128 rows of 64 values in the K-major 128-byte-swizzled layout (value (row, k) at
 // (row / 8) 1024 + (row % 8) 128 + ((k / 8) ^ (row % 8)) 16 + 2 (k % 8)).  A warp reads two 256-byte
 // rows and writes two 128-byte output rows.
-template <int kThreadsConv>
+template <int kThreadsConv, int NP = 2>
 __device__ __forceinline__ float convert_tile_kmajor(const uint8_t* __restrict__ f32, uint8_t* __restrict__ hi,
-                                                     uint8_t* __restrict__ lo, int t) {
+                                                     uint8_t* __restrict__ lo, int t, uint8_t* __restrict__ lo2 = nullptr) {
   static_assert(kThreadsConv % 128 == 0, "unit j of a thread is row 16 j + (t / 16) of its first one");
   constexpr int kUnits = 2048 / kThreadsConv;
   constexpr int kRowStep = kThreadsConv / 16;   // rows between a thread's consecutive units
@@ -270,12 +300,7 @@ __device__ __forceinline__ float convert_tile_kmajor(const uint8_t* __restrict__
   for (int j = 0; j < kUnits; ++j) v[j] = *reinterpret_cast<const float4*>(src + j * kRowStep * 256);
   float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int j = 0; j < kUnits; ++j) {
-    uint2 h, tl;
-    split4_bf16x2(v[j], h, tl, s01, s23);
-    *reinterpret_cast<uint2*>(hi + off0 + j * kRowStep * 128) = h;
-    *reinterpret_cast<uint2*>(lo + off0 + j * kRowStep * 128) = tl;
-  }
+  for (int j = 0; j < kUnits; ++j) split_store<NP>(v[j], hi, lo, lo2, off0 + j * kRowStep * 128, s01, s23);
   return (s01.x + s01.y) + (s23.x + s23.y);
 }
 

@@ -44,25 +44,26 @@ constexpr uint32_t kFp8Box = kNTile * 64;      // E4M3 TMA box: 64 rows (bytes) 
 // filled by TMA, split by eight converter warps into 2 stages of pieces; the converters also
 // request the A slice of their stage.  E4M3 in: 8 stages of byte slices, dequantized and split
 // the same way.
-template <int IN>
+// NP = 3 (FP32 input split exactly into three pieces): one FP32 stage fewer, for the third piece.
+template <int IN, int NP = 2>
 struct TtmCfg {
   static constexpr bool kConvIn = IN != tc::kInPieces;
   static constexpr int kPStages = kConvIn ? 2 : 3;
   static constexpr bool kF32Like = IN == tc::kInF32 || IN == tc::kInF32S;
-  static constexpr int kF32Stages = kF32Like ? 3 : (IN == tc::kInFp8 ? 8 : 1);
+  static constexpr int kF32Stages = kF32Like ? (NP == 3 ? 2 : 3) : (IN == tc::kInFp8 ? 8 : 1);
   static constexpr uint32_t kStageBytes = kF32Like ? 2 * kF32Box : (IN == tc::kInFp8 ? kFp8Box : 1024);
   static constexpr int kConv = 256;   // converter threads (warps 6..13)
   static constexpr int kThreads = kConvIn ? 192 + kConv : 192;
 };
 
-template <int IN>
+template <int IN, int NP = 2>
 struct alignas(1024) TtmSmem {
-  uint8_t xf[TtmCfg<IN>::kF32Stages][TtmCfg<IN>::kStageBytes];
-  uint8_t a[TtmCfg<IN>::kPStages][kATile];
-  uint8_t x[TtmCfg<IN>::kPStages][2][kXTile];
+  uint8_t xf[TtmCfg<IN, NP>::kF32Stages][TtmCfg<IN, NP>::kStageBytes];
+  uint8_t a[TtmCfg<IN, NP>::kPStages][kATile];
+  uint8_t x[TtmCfg<IN, NP>::kPStages][NP][kXTile];
   float xchg[64][kNTile + 1];
-  uint64_t f32full[TtmCfg<IN>::kF32Stages], f32empty[TtmCfg<IN>::kF32Stages];
-  uint64_t full[TtmCfg<IN>::kPStages], empty[TtmCfg<IN>::kPStages], afull[TtmCfg<IN>::kPStages];
+  uint64_t f32full[TtmCfg<IN, NP>::kF32Stages], f32empty[TtmCfg<IN, NP>::kF32Stages];
+  uint64_t full[TtmCfg<IN, NP>::kPStages], empty[TtmCfg<IN, NP>::kPStages], afull[TtmCfg<IN, NP>::kPStages];
   uint64_t tfull[2], tempty[2];
   uint32_t tmem_slot;
 };
@@ -82,19 +83,19 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // TMEM lane p holds column p's head sums in columns c and its tail sums in columns 64 + c.  Each
 // epilogue warp then finishes its own 32 columns p (no exchange between warps) and writes
 // B[co.base(p) + c co.cstride()] with the lanes along p.
-template <int IN, bool kT = false>
-__global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
+template <int IN, bool kT = false, int NP = 2>
+__global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
                   float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld,
                   CoreOut co, int probe, int64_t L) {
-  using Cfg = TtmCfg<IN>;
+  using Cfg = TtmCfg<IN, NP>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
   constexpr int NF = Cfg::kF32Stages;
   extern __shared__ uint8_t smem_raw[];
-  TtmSmem<IN>& S =
-      *reinterpret_cast<TtmSmem<IN>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TtmSmem<IN, NP>& S =
+      *reinterpret_cast<TtmSmem<IN, NP>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (M + kNTile - 1) / kNTile;
   const int kstages = (int)((I + kKStage - 1) / kKStage);
@@ -320,9 +321,11 @@ __global__ void __launch_bounds__(TtmCfg<IN>::kThreads, 1)
           (void)tc::convert_fp8_tile<64, 128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], nullptr, t, scales, ld,
                                                           (int64_t)ks * kKStage, tt * kNTile, I, M);
         else if constexpr (IN == tc::kInF32S)
-          (void)tc::convert_tile_plain<64, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+          (void)tc::convert_tile_plain<64, Cfg::kConv, NP>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t,
+                                                           NP == 3 ? &S.x[ps][NP - 1][0] : nullptr);
         else
-          (void)tc::convert_tile<128, Cfg::kConv>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t);
+          (void)tc::convert_tile<128, Cfg::kConv, NP>(&S.xf[s][0], &S.x[ps][0][0], &S.x[ps][1][0], t,
+                                                      NP == 3 ? &S.x[ps][NP - 1][0] : nullptr);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&S.f32empty[s]);
         tc::mbar_arrive(&S.full[ps]);
@@ -394,8 +397,21 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   return RH_OK;
 }
 
+// A converted-input launch (FP32 split on the fly into NP pieces).
+template <int IN, bool kT, int NP>
+static rh_status launch_ttm_conv(const CUtensorMap& mA, const CUtensorMap& m0, const ModeView& v, int64_t I, int64_t M,
+                                 int ell, float* B, int32_t* err, CoreOut co, int64_t L, cudaStream_t st) {
+  const size_t smem = sizeof(TtmSmem<IN, NP>) + 1024;
+  RH_CUDA_TRY(
+      cudaFuncSetAttribute(ttm_tc_kernel<IN, kT, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN, kT, NP><<<ttm_tc_ctas(v), TtmCfg<IN, NP>::kThreads, smem, st>>>(
+      mA, m0, m0, NP, I, M, ell, B, err, nullptr, 0, co, tc_probe_next(), L);
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                            int32_t* err, cudaStream_t st) {
+                            int32_t* err, cudaStream_t st, int pieces) {
   if (!ttm_tc_supported(v, ell)) {
     set_error("tensor-core mode product: unsupported shape (needs the first mode, I % 8 == 0, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -410,13 +426,8 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
   if (s != RH_OK) return s;
   if ((s = make_map_2d(&m0, X, 4, v.I, v.M(), kNTile)) != RH_OK) return s;
-  constexpr int IN = tc::kInF32;
-  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{}, tc_probe_next(), 1);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return pieces == 3 ? launch_ttm_conv<tc::kInF32, false, 3>(mA, m0, v, v.I, v.M(), ell, B, err, CoreOut{}, 1, st)
+                     : launch_ttm_conv<tc::kInF32, false, 2>(mA, m0, v, v.I, v.M(), ell, B, err, CoreOut{}, 1, st);
 }
 
 rh_status make_map_3d_f32(CUtensorMap* map, const void* base, int64_t L, int64_t I, int64_t R, int box0, int box1);
@@ -429,7 +440,7 @@ bool ttm_tc_strided_supported(const ModeView& v, int ell) {
 }
 
 rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                             int32_t* err, cudaStream_t st) {
+                             int32_t* err, cudaStream_t st, int pieces) {
   if (!ttm_tc_strided_supported(v, ell)) {
     set_error("tensor-core mode product: unsupported strided shape (needs L % 128 == 0, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -445,13 +456,9 @@ rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const d
   rh_status s = make_bf16_map_2d(&mA, qa, ldA, 128, 128);
   if (s != RH_OK) return s;
   if ((s = make_map_3d_f32(&m0, X, v.L, v.I, v.R, kNTile, kKStage)) != RH_OK) return s;
-  constexpr int IN = tc::kInF32S;
-  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(
-      mA, m0, m0, 2, v.I, v.M(), ell, B, err, nullptr, 0, CoreOut::make(1, v.L, 1, v.M()), tc_probe_next(), v.L);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  const CoreOut co = CoreOut::make(1, v.L, 1, v.M());
+  return pieces == 3 ? launch_ttm_conv<tc::kInF32S, false, 3>(mA, m0, v, v.I, v.M(), ell, B, err, co, v.L, st)
+                     : launch_ttm_conv<tc::kInF32S, false, 2>(mA, m0, v, v.I, v.M(), ell, B, err, co, v.L, st);
 }
 
 bool core_product_tc_supported(int ell, int ko, int64_t M) {
@@ -459,7 +466,7 @@ bool core_product_tc_supported(int ell, int ko, int64_t M) {
 }
 
 rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, uint16_t* qa,
-                                 float* out, int32_t* err, cudaStream_t st) {
+                                 float* out, int32_t* err, cudaStream_t st, int pieces) {
   if (!core_product_tc_supported(ell, ko, M) || co.S < 1 || co.I < 1 || co.Ln < 1 || M % (co.S * co.I) != 0) {
     set_error("tensor-core core product: unsupported shape (needs ell % 4 == 0, ell, r <= 64)");
     return RH_EUNSUPPORTED;
@@ -475,14 +482,8 @@ rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, Cor
   if (s != RH_OK) return s;
   if ((s = make_map_2d(&m0, B, 4, ell, M, kNTile)) != RH_OK) return s;
   const ModeView v{1, (int64_t)ell, M};
-  constexpr int IN = tc::kInF32;
-  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
-  RH_CUDA_TRY(
-      cudaFuncSetAttribute(ttm_tc_kernel<IN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN, true><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 2, ell, M, ko, out, err,
-                                                                               nullptr, 0, co, tc_probe_next(), 1);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return pieces == 3 ? launch_ttm_conv<tc::kInF32, true, 3>(mA, m0, v, ell, M, ko, out, err, co, 1, st)
+                     : launch_ttm_conv<tc::kInF32, true, 2>(mA, m0, v, ell, M, ko, out, err, co, 1, st);
 }
 
 rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,

@@ -95,11 +95,12 @@ CorePlan plan_core(int d, const int64_t* dims, const int32_t* ks) {
 
 // split_tc (FP32 data, the RH_F32_BF16X2 form): every product but the last whose shape the
 // tensor-core mode product covers runs there (the FP32 input split into BF16 head and tail on the
-// fly, the factor into two pieces in qa); the others, and the last (FP64 output), on the CUDA cores.
+// fly -- pieces = 3: exactly, into three -- the factor into two pieces in qa); the others, and the
+// last (FP64 output), on the CUDA cores.
 template <typename T>
 rh_status run_core(int d, const int64_t* dims, const T* X, const double* const* factors, const int32_t* ks,
                    double* G, const CorePlan& pl, T* fac, T* W0, T* W1, cudaStream_t st, bool split_tc = false,
-                   uint16_t* qa = nullptr, int32_t* err = nullptr) {
+                   uint16_t* qa = nullptr, int32_t* err = nullptr, int pieces = 2) {
   std::vector<const T*> fc(d);
   size_t off = 0;
   rh_status s;
@@ -125,10 +126,10 @@ rh_status run_core(int d, const int64_t* dims, const T* X, const double* const* 
           const float* xin = reinterpret_cast<const float*>(in);
           float* out = reinterpret_cast<float*>(bufs[nb]);
           if (v.L == 1 && ttm_tc_supported(v, ks[n])) {
-            if ((s = launch_ttm_tc_f32(v, ks[n], xin, factors[n], qa, out, err, st)) != RH_OK) return s;
+            if ((s = launch_ttm_tc_f32(v, ks[n], xin, factors[n], qa, out, err, st, pieces)) != RH_OK) return s;
             done = true;
           } else if (ttm_tc_strided_supported(v, ks[n])) {
-            if ((s = launch_ttm_tc_f32s(v, ks[n], xin, factors[n], qa, out, err, st)) != RH_OK) return s;
+            if ((s = launch_ttm_tc_f32s(v, ks[n], xin, factors[n], qa, out, err, st, pieces)) != RH_OK) return s;
             done = true;
           }
         }
@@ -155,13 +156,13 @@ size_t core_chain_elems(int d, const int64_t* dims, const int32_t* ks, size_t* f
 template <typename T>
 rh_status launch_core_ttm(int d, const int64_t* dims, const T* X, const double* const* factors, const int32_t* ks,
                           double* G, T* fac, T* W0, T* W1, cudaStream_t st, bool split_tc, uint16_t* qa,
-                          int32_t* err) {
-  return run_core<T>(d, dims, X, factors, ks, G, plan_core(d, dims, ks), fac, W0, W1, st, split_tc, qa, err);
+                          int32_t* err, int pieces) {
+  return run_core<T>(d, dims, X, factors, ks, G, plan_core(d, dims, ks), fac, W0, W1, st, split_tc, qa, err, pieces);
 }
 template rh_status launch_core_ttm<float>(int, const int64_t*, const float*, const double* const*, const int32_t*,
-                                          double*, float*, float*, float*, cudaStream_t, bool, uint16_t*, int32_t*);
+                                          double*, float*, float*, float*, cudaStream_t, bool, uint16_t*, int32_t*, int);
 template rh_status launch_core_ttm<double>(int, const int64_t*, const double*, const double* const*, const int32_t*,
-                                           double*, double*, double*, double*, cudaStream_t, bool, uint16_t*, int32_t*);
+                                           double*, double*, double*, double*, cudaStream_t, bool, uint16_t*, int32_t*, int);
 
 }  // namespace rh
 
