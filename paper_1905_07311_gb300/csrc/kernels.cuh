@@ -83,13 +83,16 @@ int ttm_tc_ctas(const ModeView& v);
 // qa: 128 x I BF16 scratch for the split Q; B: ell x M FP32 (layout c + ell p)
 rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
                         uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
-// FP32 X split on the fly into two BF16 pieces (pieces = 3: exactly, into three)
+// FP32 X split on the fly into two BF16 pieces (pieces = 3: exactly, into three).  gram_part
+// (ell <= 60, ttm_tc_gram_supported): also the FP32 Gram route's per-CTA partials of W = B B^T
+// (ttm_tc_ctas(v) upper triangles of ell^2 doubles), see launch_trunc_svd.
+bool ttm_tc_gram_supported(int ell);
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                            int32_t* err, cudaStream_t st, int pieces = 2);
+                            int32_t* err, cudaStream_t st, int pieces = 2, double* gram_part = nullptr);
 // a mode with L > 1 (L % 128 == 0): B in the (L, ell, R) layout, qa 128 x ceil8(I) BF16
 bool ttm_tc_strided_supported(const ModeView& v, int ell);
 rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                             int32_t* err, cudaStream_t st, int pieces = 2);
+                             int32_t* err, cudaStream_t st, int pieces = 2, double* gram_part = nullptr);
 // G <- U^T B on the tensor cores for a truncated core (Alg. 1 step 6): B ell x M FP32 (layout
 // c + ell p, split on the fly), U ell x ko FP32 (split into two BF16 pieces in qa, 128 x ceil8(ell)),
 // out[co.base(p) + c co.cstride()] FP32 (see CoreOut).  Needs ell % 4 == 0, ell, ko <= 64.
@@ -155,9 +158,16 @@ size_t trunc_workspace_elems(const TruncPlan& pl);   // elements of T
 // FP32 tile sums), Cholesky W = R^T R, Jacobi on R.  It is kept when the Cholesky succeeds and
 // sigma_r^2 - sigma_{r+1}^2 >= 1e-5 sigma_1^2 (then *info |= 2, if info is given); otherwise
 // device-side flags run the tall-skinny QR route.  r = 0 (and FP64) take the QR route only.
+// gram_nparts > 0: the FP32 Gram route's per-CTA partials of W = B B^T were already written (by the
+// tensor-core mode product that produced B) into trunc_gram_part(pl, ws), gram_nparts of them, so
+// only their reduction runs here.
 template <typename T>
 rh_status launch_trunc_svd(const TruncPlan& pl, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st, int r,
-                           int32_t* info);
+                           int32_t* info, int gram_nparts = 0);
+// Where launch_trunc_svd<float> keeps the per-CTA partials of its Gram route (gram_ctas() ell^2
+// doubles) inside its workspace ws.
+double* trunc_gram_part(const TruncPlan& pl, float* ws);
+int gram_ctas();
 
 // Staged truncation (adaptive variants).  Stage 1, the factor of the whole ell x M matrix B:
 // gram (FP32 data) -> W = B B^T in W (part: gram partials, see launch_gram_f32); otherwise the

@@ -524,6 +524,11 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
     // Alg. 1 step 3: B = Q^T G_(n)   (the mode-n product G x_n Q^T)
     const bool direct_core = last && !o.truncate;
+    // the FP32 Gram route of the truncation gets W's partials from the tensor-core mode product
+    const bool gram_fused = tc && !in_pieces && !in_fp8 && !sp.stc && o.truncate && !o.svd_route && sp.ko >= 1 &&
+                            sizeof(T) == 4 && ttm_tc_gram_supported(sp.ell);
+    double* gram_part = gram_fused ? trunc_gram_part(sp.tr, reinterpret_cast<float*>(b.trunc)) : nullptr;
+    const int gram_nparts = gram_fused ? ttm_tc_ctas(sp.v) : 0;
     if (sp.stc) {
       ProfileScope ps(PROF_TTM, j, st);
       if (direct_core) {
@@ -543,7 +548,8 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
       else if (in_fp8)
         s = launch_ttm_tc_fp8(sp.v, sp.ell, x8, scales8, f8.ld, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
       else
-        s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st, pl.pieces);
+        s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st, pl.pieces,
+                              gram_part);
       if (s != RH_OK) return s;
     } else {
       ProfileScope ps(PROF_TTM, j, st);
@@ -562,7 +568,7 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         ProfileScope ps(PROF_TRUNC, j, st);
         // r = 0 keeps the truncation SVD on the tall-skinny QR (svd_route 1)
         if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, o.svd_route ? 0 : sp.ko,
-                                      info ? info + sp.mode : nullptr)) != RH_OK) return s;
+                                      info ? info + sp.mode : nullptr, gram_nparts)) != RH_OK) return s;
       }
       if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
                                          st)) != RH_OK)
@@ -675,12 +681,15 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
       continue;
     }
     if ((s = launch_cast<T>(b.Q, static_cast<T*>(b.Qc), sp.v.I * sp.ell, st)) != RH_OK) return s;
+    const bool gram_fused = tc && !o.svd_route && sp.ko >= 1 && sizeof(T) == 4 && ttm_tc_gram_supported(sp.ell);
+    double* gram_part = gram_fused ? trunc_gram_part(sp.tr, reinterpret_cast<float*>(b.trunc)) : nullptr;
+    const int gram_nparts = gram_fused ? ttm_tc_ctas(sp.v) : 0;
     {
       ProfileScope ps(PROF_TTM, (int)j, st);
       if (tc) {
         float* Bf = reinterpret_cast<float*>(B);
-        s = sp.v.L == 1 ? launch_ttm_tc_f32(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st, pl.pieces)
-                        : launch_ttm_tc_f32s(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st, pl.pieces);
+        s = sp.v.L == 1 ? launch_ttm_tc_f32(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st, pl.pieces, gram_part)
+                        : launch_ttm_tc_f32s(sp.v, sp.ell, Xf, b.Q, b.qa, Bf, b.err, st, pl.pieces, gram_part);
         if (s != RH_OK) return s;
       } else if ((s = launch_ttm<T, T>(sp.v, X, static_cast<const T*>(b.Qc), sp.ell, B, st)) != RH_OK) {
         return s;
@@ -689,7 +698,7 @@ rh_status run_rhosvd(const Plan& pl, const int64_t* dims, const T* X, const rh_o
     {
       ProfileScope ps(PROF_TRUNC, (int)j, st);
       if ((s = launch_trunc_svd<T>(sp.tr, B, static_cast<T*>(b.trunc), b.Ub, b.sv, st, o.svd_route ? 0 : sp.ko,
-                                      info ? info + sp.mode : nullptr)) != RH_OK) return s;
+                                      info ? info + sp.mode : nullptr, gram_nparts)) != RH_OK) return s;
     }
     if ((s = launch_factor_and_cast<T>(sp.v.I, sp.ell, sp.ko, b.Q, b.Ub, factors[sp.mode], static_cast<T*>(b.Uc),
                                        st)) != RH_OK)

@@ -2468,9 +2468,17 @@ static rh_status launch_tsqr_tree(const TruncPlan& pl, const T* B, T* buf0, T* b
   return RH_OK;
 }
 
+double* trunc_gram_part(const TruncPlan& pl0, float* ws) {
+  TruncPlan pl = pl0;
+  trunc_dims<float>(pl);
+  const int64_t nn = (int64_t)pl.ell * pl.ell;
+  const size_t tsqr_elems = (size_t)(pl.nblk0 * nn + ceil_div(pl.nblk0, pl.fan) * nn + 2 * nn) + 64;
+  return reinterpret_cast<double*>(ws + ((tsqr_elems + 63) & ~size_t(63)));
+}
+
 template <typename T>
 rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, double* sv, cudaStream_t st, int r,
-                           int32_t* info) {
+                           int32_t* info, int gram_nparts) {
   TruncPlan pl = pl0;
   trunc_dims<T>(pl);
   const int n = pl.ell;
@@ -2496,9 +2504,14 @@ rh_status launch_trunc_svd(const TruncPlan& pl0, const T* B, T* ws, double* Ub, 
     (void)ctas;
     rh_status s = emit_memset(SITE_TRUNC_ZERO, 0, flags, 8 * sizeof(int32_t), st);
     if (s != RH_OK) return s;
-    if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st, false,
-                             SITE_TRUNC_GRAM)) != RH_OK)
+    if (gram_nparts > 0) {
+      // the partials came with B (tensor-core mode product): their fixed-order reduction only
+      RH_EMIT(GramBReduceOp, SITE_TRUNC_GRAM_REDUCE, 0, (int)ceil_div((int64_t)n * n, 32), 0, part, gram_nparts, n,
+              W, nullptr);
+    } else if ((s = launch_gram_f32(reinterpret_cast<const float*>(B), pl.v.L, pl.v.R, n, part, W, nullptr, st, false,
+                                    SITE_TRUNC_GRAM)) != RH_OK) {
       return s;
+    }
     RH_EMIT(PivotedCholeskyOp, SITE_TRUNC_PCHOL, 0, 1, chol_smem(n, sizeof(dfl::F2)), W, n, Rf, flags, nullptr);
     const size_t smr = sizeof(float) * (2 * 64 * 80 + 2 * 64 * 65);
     {
@@ -2735,9 +2748,9 @@ rh_status launch_sumsq(const double* x, int64_t n, double* out, cudaStream_t st,
 template size_t trunc_workspace_elems<float>(const TruncPlan&);
 template size_t trunc_workspace_elems<double>(const TruncPlan&);
 template rh_status launch_trunc_svd<float>(const TruncPlan&, const float*, float*, double*, double*, cudaStream_t, int,
-                                           int32_t*);
+                                           int32_t*, int);
 template rh_status launch_trunc_svd<double>(const TruncPlan&, const double*, double*, double*, double*, cudaStream_t,
-                                            int, int32_t*);
+                                            int, int32_t*, int);
 template rh_status launch_trunc_factor<float>(const TruncPlan&, const float*, float*, bool, double*, double*, float**,
                                              double*, cudaStream_t, bool);
 template rh_status launch_trunc_factor<double>(const TruncPlan&, const double*, double*, bool, double*, double*,

@@ -78,17 +78,56 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // one r, split into MN-major pieces (K = i, N = l), B written through ``co`` in the (L, ell, R)
 // layout of the mode product.  IN = kInFp8: mapX0 is
 // the E4M3 tensor (box 64 x 128 bytes, leading dimension ld), dequantized with ``scales`` and split.
+// One 128-column tile's contribution to the 4 x 4 block (bi, bj) of W = B B^T, B's tile held as
+// xc[c][p]: the 128 products of each entry summed in FP32 in column order, the sum added to the
+// FP32 pair (gh, gl) that keeps every rounding error (TwoSum).
+__device__ __forceinline__ void gram_tile(const float (*xc)[kNTile + 1], int bi, int bj, float (&gh)[4][4],
+                                          float (&gl)[4][4]) {
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+#pragma unroll 4
+  for (int pp = 0; pp < kNTile; ++pp) {
+    float xa[4], yb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xa[a] = xc[4 * bi + a][pp];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) yb[b] = xc[4 * bj + b][pp];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float v = acc[a][b];
+      const float t = __fadd_rn(gh[a][b], v);
+      const float bp = __fsub_rn(t, gh[a][b]);
+      gl[a][b] = __fadd_rn(gl[a][b], __fadd_rn(__fsub_rn(gh[a][b], __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+      gh[a][b] = t;
+    }
+}
+
 // kT (FP32 input only; the truncated-core product): the accumulator is transposed, D(p, n) =
 // X_k(p, :) A(n, :)^T with the X pieces as operand A (rows p) and [Q_h^T; Q_t^T] as operand B, so
 // TMEM lane p holds column p's head sums in columns c and its tail sums in columns 64 + c.  Each
 // epilogue warp then finishes its own 32 columns p (no exchange between warps) and writes
 // B[co.base(p) + c co.cstride()] with the lanes along p.
-template <int IN, bool kT = false, int NP = 2>
+// kG (ell <= 60): the epilogue warps also form W = B B^T of the B they write, as the FP32 Gram
+// route of the truncation does (each 128-column tile's products summed in FP32 in column order, the
+// tile sums accumulated in FP32 pairs), thread t of the four warps owning the t-th 4 x 4 block of
+// the upper triangle; gram_part[blockIdx.x] receives the CTA's partial (upper triangle, FP64), so
+// the truncation only reduces the partials instead of reading B again.
+template <int IN, bool kT = false, int NP = 2, bool kG = false>
 __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
     ttm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX0,
                   const __grid_constant__ CUtensorMap mapX1, int npieces, int64_t I, int64_t M, int ell,
                   float* __restrict__ B, int32_t* __restrict__ err, const float* __restrict__ scales, int64_t ld,
-                  CoreOut co, int probe, int64_t L) {
+                  CoreOut co, int probe, int64_t L, double* __restrict__ gram_part) {
   using Cfg = TtmCfg<IN, NP>;
   constexpr bool F32IN = Cfg::kConvIn;   // any converted input (FP32 or E4M3)
   constexpr int NS = Cfg::kPStages;
@@ -218,6 +257,21 @@ __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
     const int quad = warp & 3;
     const bool tail = quad >= 2;        // rows 64..127: Q_t^T X
     const int crow = (quad & 1) * 32 + lane;   // output row c (0..63)
+    // kG: this thread's 4 x 4 block (gbi, gbj) of the upper triangle of W
+    const int et = threadIdx.x - 64;   // 0..127
+    int gbi = 0, gbj = et;
+    const int gnb = (ell + 3) / 4;
+    while (gbi < gnb && gbj >= gnb - gbi) {
+      gbj -= gnb - gbi;
+      ++gbi;
+    }
+    gbj += gbi;
+    const bool gact = kG && et < gnb * (gnb + 1) / 2;
+    float gh[4][4], gl[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) gh[a][b2] = gl[a][b2] = 0.0f;
     uint32_t tl = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const uint32_t b = tl & 1;
@@ -264,13 +318,19 @@ __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
                 const int64_t p = p0 + cc * 16 + j;
-                if (p < M) B[crow + (int64_t)ell * p] = v[j] + S.xchg[crow][cc * 16 + j];
+                const float f = v[j] + S.xchg[crow][cc * 16 + j];
+                if constexpr (kG) S.xchg[crow][cc * 16 + j] = f;   // this lane's own row
+                if (p < M) B[crow + (int64_t)ell * p] = f;
               }
             }
           }
         }
         tc::tc_fence_before();
         tc::mbar_arrive(&S.tempty[b]);
+        if constexpr (kG) {
+          named_sync(1, 128);   // the tile's final values are in xchg
+          if (gact) gram_tile(S.xchg, gbi, gbj, gh, gl);
+        }
       } else {
         // B[co.base(p) + c co.cstride()] (CoreOut): sum the halves in shared memory, then each
         // warp writes whole rows c with its lanes along p
@@ -294,8 +354,23 @@ __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
             for (int c = wq; c < ell; c += 4) B[base + cs * c] = S.xchg[c][jj];
           }
         }
+        if constexpr (kG) {
+          if (gact) gram_tile(S.xchg, gbi, gbj, gh, gl);
+        }
       }
       named_sync(1, 128);   // xchg is free again
+    }
+    if constexpr (kG) {
+      if (gact) {
+        double* o = gram_part + (int64_t)blockIdx.x * ell * ell;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) {
+            const int r = 4 * gbi + a, c = 4 * gbj + b2;
+            if (r <= c && c < ell) o[r + (int64_t)ell * c] = (double)gh[a][b2] + (double)gl[a][b2];
+          }
+      }
     }
   } else if constexpr (F32IN) {
     // converters (warps 6..13): FP32 / E4M3 slice -> BF16 head + tail; thread 0 also requests the A slice
@@ -392,26 +467,31 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{}, tc_probe_next(), 1);
+                                                                         nullptr, 0, CoreOut{}, tc_probe_next(), 1,
+                                                                         nullptr);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
 
-// A converted-input launch (FP32 split on the fly into NP pieces).
-template <int IN, bool kT, int NP>
+// A converted-input launch (FP32 split on the fly into NP pieces); kG: with the Gram partials of B.
+template <int IN, bool kT, int NP, bool kG = false>
 static rh_status launch_ttm_conv(const CUtensorMap& mA, const CUtensorMap& m0, const ModeView& v, int64_t I, int64_t M,
-                                 int ell, float* B, int32_t* err, CoreOut co, int64_t L, cudaStream_t st) {
+                                 int ell, float* B, int32_t* err, CoreOut co, int64_t L, cudaStream_t st,
+                                 double* gram_part = nullptr) {
   const size_t smem = sizeof(TtmSmem<IN, NP>) + 1024;
   RH_CUDA_TRY(
-      cudaFuncSetAttribute(ttm_tc_kernel<IN, kT, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN, kT, NP><<<ttm_tc_ctas(v), TtmCfg<IN, NP>::kThreads, smem, st>>>(
-      mA, m0, m0, NP, I, M, ell, B, err, nullptr, 0, co, tc_probe_next(), L);
+      cudaFuncSetAttribute(ttm_tc_kernel<IN, kT, NP, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ttm_tc_kernel<IN, kT, NP, kG><<<ttm_tc_ctas(v), TtmCfg<IN, NP>::kThreads, smem, st>>>(
+      mA, m0, m0, NP, I, M, ell, B, err, nullptr, 0, co, tc_probe_next(), L, gram_part);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
 
+// The Gram partials of B ride along with the mode product when its rows fit the epilogue's blocks.
+bool ttm_tc_gram_supported(int ell) { return ell >= 1 && ell <= 60; }
+
 rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                            int32_t* err, cudaStream_t st, int pieces) {
+                            int32_t* err, cudaStream_t st, int pieces, double* gram_part) {
   if (!ttm_tc_supported(v, ell)) {
     set_error("tensor-core mode product: unsupported shape (needs the first mode, I % 8 == 0, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -426,6 +506,16 @@ rh_status launch_ttm_tc_f32(const ModeView& v, int ell, const float* X, const do
   rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
   if (s != RH_OK) return s;
   if ((s = make_map_2d(&m0, X, 4, v.I, v.M(), kNTile)) != RH_OK) return s;
+  if (gram_part != nullptr && !ttm_tc_gram_supported(ell)) {
+    set_error("internal: Gram partials with the mode product need ell <= 60");
+    return RH_EUNSUPPORTED;
+  }
+  if (gram_part != nullptr)
+    return pieces == 3
+               ? launch_ttm_conv<tc::kInF32, false, 3, true>(mA, m0, v, v.I, v.M(), ell, B, err, CoreOut{}, 1, st,
+                                                             gram_part)
+               : launch_ttm_conv<tc::kInF32, false, 2, true>(mA, m0, v, v.I, v.M(), ell, B, err, CoreOut{}, 1, st,
+                                                             gram_part);
   return pieces == 3 ? launch_ttm_conv<tc::kInF32, false, 3>(mA, m0, v, v.I, v.M(), ell, B, err, CoreOut{}, 1, st)
                      : launch_ttm_conv<tc::kInF32, false, 2>(mA, m0, v, v.I, v.M(), ell, B, err, CoreOut{}, 1, st);
 }
@@ -440,7 +530,7 @@ bool ttm_tc_strided_supported(const ModeView& v, int ell) {
 }
 
 rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const double* Q, uint16_t* qa, float* B,
-                             int32_t* err, cudaStream_t st, int pieces) {
+                             int32_t* err, cudaStream_t st, int pieces, double* gram_part) {
   if (!ttm_tc_strided_supported(v, ell)) {
     set_error("tensor-core mode product: unsupported strided shape (needs L % 128 == 0, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -457,6 +547,14 @@ rh_status launch_ttm_tc_f32s(const ModeView& v, int ell, const float* X, const d
   if (s != RH_OK) return s;
   if ((s = make_map_3d_f32(&m0, X, v.L, v.I, v.R, kNTile, kKStage)) != RH_OK) return s;
   const CoreOut co = CoreOut::make(1, v.L, 1, v.M());
+  if (gram_part != nullptr && !ttm_tc_gram_supported(ell)) {
+    set_error("internal: Gram partials with the mode product need ell <= 60");
+    return RH_EUNSUPPORTED;
+  }
+  if (gram_part != nullptr)
+    return pieces == 3
+               ? launch_ttm_conv<tc::kInF32S, false, 3, true>(mA, m0, v, v.I, v.M(), ell, B, err, co, v.L, st, gram_part)
+               : launch_ttm_conv<tc::kInF32S, false, 2, true>(mA, m0, v, v.I, v.M(), ell, B, err, co, v.L, st, gram_part);
   return pieces == 3 ? launch_ttm_conv<tc::kInF32S, false, 3>(mA, m0, v, v.I, v.M(), ell, B, err, co, v.L, st)
                      : launch_ttm_conv<tc::kInF32S, false, 2>(mA, m0, v, v.I, v.M(), ell, B, err, co, v.L, st);
 }
@@ -507,7 +605,8 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   const size_t smem = sizeof(TtmSmem<IN>) + 1024;
   RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 1, v.I, v.M(), ell, B, err,
-                                                                         scales, ld, CoreOut{}, tc_probe_next(), 1);
+                                                                         scales, ld, CoreOut{}, tc_probe_next(), 1,
+                                                                         nullptr);
   RH_LAUNCH_CHECK();
   return RH_OK;
 }
