@@ -82,7 +82,7 @@ bool ttm_tc_supported(const ModeView& v, int ell);
 int ttm_tc_ctas(const ModeView& v);
 // qa: 128 x I BF16 scratch for the split Q; B: ell x M FP32 (layout c + ell p)
 rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
-                        uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
+                        uint16_t* qa, float* B, int32_t* err, cudaStream_t st, double* gram_part = nullptr);
 // FP32 X split on the fly into two BF16 pieces (pieces = 3: exactly, into three).  gram_part
 // (ell <= 60, ttm_tc_gram_supported): also the FP32 Gram route's per-CTA partials of W = B B^T
 // (ttm_tc_ctas(v) upper triangles of ell^2 doubles), see launch_trunc_svd.
@@ -100,7 +100,8 @@ bool core_product_tc_supported(int ell, int ko, int64_t M);
 rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, CoreOut co, const float* U, uint16_t* qa,
                                  float* out, int32_t* err, cudaStream_t st, int pieces = 2);
 rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
-                            const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st);
+                            const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st,
+                            double* gram_part = nullptr);
 
 // ---- mode-n product B = G x_n Q^T  (ttm.cu) ------------------------------------------
 // B[(p%L) + L*ko*(p/L) + L*c] = sum_i Q[i + I*c] G[(p%L) + L*I*(p/L) + L*i],  c < ko.

@@ -525,8 +525,9 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
     // Alg. 1 step 3: B = Q^T G_(n)   (the mode-n product G x_n Q^T)
     const bool direct_core = last && !o.truncate;
     // the FP32 Gram route of the truncation gets W's partials from the tensor-core mode product
-    const bool gram_fused = tc && !in_pieces && !in_fp8 && !sp.stc && o.truncate && !o.svd_route && sp.ko >= 1 &&
-                            sizeof(T) == 4 && ttm_tc_gram_supported(sp.ell);
+    // (every tensor-core form, so that the forms stay bit-identical to one another)
+    const bool gram_fused = tc && !sp.stc && o.truncate && !o.svd_route && sp.ko >= 1 && sizeof(T) == 4 &&
+                            ttm_tc_gram_supported(sp.ell);
     double* gram_part = gram_fused ? trunc_gram_part(sp.tr, reinterpret_cast<float*>(b.trunc)) : nullptr;
     const int gram_nparts = gram_fused ? ttm_tc_ctas(sp.v) : 0;
     if (sp.stc) {
@@ -544,9 +545,10 @@ rh_status run_rsthosvd(const Plan& pl, const void* Xraw, const rh_options& o, do
         return RH_EUNSUPPORTED;
       }
       if (in_pieces)
-        s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
+        s = launch_ttm_tc(sp.v, sp.ell, piece0, piece1, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st, gram_part);
       else if (in_fp8)
-        s = launch_ttm_tc_fp8(sp.v, sp.ell, x8, scales8, f8.ld, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st);
+        s = launch_ttm_tc_fp8(sp.v, sp.ell, x8, scales8, f8.ld, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st,
+                              gram_part);
       else
         s = launch_ttm_tc_f32(sp.v, sp.ell, tc_src, b.Q, b.qa, reinterpret_cast<float*>(B), b.err, st, pl.pieces,
                               gram_part);

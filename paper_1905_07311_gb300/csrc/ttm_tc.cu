@@ -61,7 +61,7 @@ struct alignas(1024) TtmSmem {
   uint8_t xf[TtmCfg<IN, NP>::kF32Stages][TtmCfg<IN, NP>::kStageBytes];
   uint8_t a[TtmCfg<IN, NP>::kPStages][kATile];
   uint8_t x[TtmCfg<IN, NP>::kPStages][NP][kXTile];
-  float xchg[64][kNTile + 1];
+  float xchg[64][kNTile + 2];   // rows of 130 floats: pairs of columns 8-byte aligned, lanes c on distinct banks
   uint64_t f32full[TtmCfg<IN, NP>::kF32Stages], f32empty[TtmCfg<IN, NP>::kF32Stages];
   uint64_t full[TtmCfg<IN, NP>::kPStages], empty[TtmCfg<IN, NP>::kPStages], afull[TtmCfg<IN, NP>::kPStages];
   uint64_t tfull[2], tempty[2];
@@ -79,32 +79,34 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // layout of the mode product.  IN = kInFp8: mapX0 is
 // the E4M3 tensor (box 64 x 128 bytes, leading dimension ld), dequantized with ``scales`` and split.
 // One 128-column tile's contribution to the 4 x 4 block (bi, bj) of W = B B^T, B's tile held as
-// xc[c][p]: the 128 products of each entry summed in FP32 in column order, the sum added to the
-// FP32 pair (gh, gl) that keeps every rounding error (TwoSum).
-__device__ __forceinline__ void gram_tile(const float (*xc)[kNTile + 1], int bi, int bj, float (&gh)[4][4],
+// xc[c][p]: the products of the even and of the odd columns each summed in FP32 in column order
+// (the two lanes of packed pairs), their sum added to the FP32 pair (gh, gl) that keeps every
+// rounding error (TwoSum).
+__device__ __forceinline__ void gram_tile(const float (*xc)[kNTile + 2], int bi, int bj, float (&gh)[4][4],
                                           float (&gl)[4][4]) {
-  float acc[4][4];
+  // even and odd columns in the two lanes of packed FP32 pairs, added at the end of the tile
+  float2 acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-#pragma unroll 4
-  for (int pp = 0; pp < kNTile; ++pp) {
-    float xa[4], yb[4];
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+  for (int pp = 0; pp < kNTile; pp += 2) {
+    float2 xa[4], yb[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) xa[a] = xc[4 * bi + a][pp];
+    for (int a = 0; a < 4; ++a) xa[a] = *reinterpret_cast<const float2*>(&xc[4 * bi + a][pp]);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) yb[b] = xc[4 * bj + b][pp];
+    for (int b = 0; b < 4; ++b) yb[b] = *reinterpret_cast<const float2*>(&xc[4 * bj + b][pp]);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+      for (int b = 0; b < 4; ++b) acc[a][b] = f2_fma(xa[a], yb[b], acc[a][b]);
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const float v = acc[a][b];
+      const float v = acc[a][b].x + acc[a][b].y;
       const float t = __fadd_rn(gh[a][b], v);
       const float bp = __fsub_rn(t, gh[a][b]);
       gl[a][b] = __fadd_rn(gl[a][b], __fadd_rn(__fsub_rn(gh[a][b], __fsub_rn(t, bp)), __fsub_rn(v, bp)));
@@ -303,7 +305,8 @@ __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
           float v[16];
           tc::tmem_ld16(base + cc * 16, v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) S.xchg[crow][cc * 16 + j] = v[j];
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float2*>(&S.xchg[crow][cc * 16 + 2 * j]) = make_float2(v[2 * j], v[2 * j + 1]);
         }
       }
       named_sync(1, 128);
@@ -316,11 +319,14 @@ __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
             tc::tmem_ld16(base + cc * 16, v);
             if (crow < ell) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int64_t p = p0 + cc * 16 + j;
-                const float f = v[j] + S.xchg[crow][cc * 16 + j];
-                if constexpr (kG) S.xchg[crow][cc * 16 + j] = f;   // this lane's own row
-                if (p < M) B[crow + (int64_t)ell * p] = f;
+              for (int j = 0; j < 8; ++j) {
+                float2* xp = reinterpret_cast<float2*>(&S.xchg[crow][cc * 16 + 2 * j]);
+                const float2 tv = *xp;
+                const float f0 = v[2 * j] + tv.x, f1 = v[2 * j + 1] + tv.y;
+                if constexpr (kG) *xp = make_float2(f0, f1);   // this lane's own row
+                const int64_t p = p0 + cc * 16 + 2 * j;
+                if (p < M) B[crow + (int64_t)ell * p] = f0;
+                if (p + 1 < M) B[crow + (int64_t)ell * (p + 1)] = f1;
               }
             }
           }
@@ -339,7 +345,11 @@ __global__ void __launch_bounds__(TtmCfg<IN, NP>::kThreads, 1)
             float v[16];
             tc::tmem_ld16(base + cc * 16, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) S.xchg[crow][cc * 16 + j] += v[j];
+            for (int j = 0; j < 8; ++j) {
+              float2* xp = reinterpret_cast<float2*>(&S.xchg[crow][cc * 16 + 2 * j]);
+              const float2 tv = *xp;
+              *xp = make_float2(tv.x + v[2 * j], tv.y + v[2 * j + 1]);
+            }
           }
         }
         tc::tc_fence_before();
@@ -441,8 +451,33 @@ int ttm_tc_ctas(const ModeView& v) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(v.M(), kNTile)));
 }
 
+// The launch of a form whose input the producer warp loads as it is (BF16 pieces) or converts
+// in one piece (E4M3), with or without the Gram partials of B.
+template <int IN>
+static rh_status launch_ttm_plain(const CUtensorMap& mA, const CUtensorMap& m0, const CUtensorMap& m1, int np,
+                                  const ModeView& v, int ell, float* B, int32_t* err, const float* scales, int64_t ld,
+                                  cudaStream_t st, double* gram_part) {
+  if (gram_part != nullptr && !ttm_tc_gram_supported(ell)) {
+    set_error("internal: Gram partials with the mode product need ell <= 60");
+    return RH_EUNSUPPORTED;
+  }
+  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
+  if (gram_part != nullptr) {
+    RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN, false, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    ttm_tc_kernel<IN, false, 2, true><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(
+        mA, m0, m1, np, v.I, v.M(), ell, B, err, scales, ld, CoreOut{}, tc_probe_next(), 1, gram_part);
+  } else {
+    RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(
+        mA, m0, m1, np, v.I, v.M(), ell, B, err, scales, ld, CoreOut{}, tc_probe_next(), 1, nullptr);
+  }
+  RH_LAUNCH_CHECK();
+  return RH_OK;
+}
+
 rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, const uint16_t* piece1, const double* Q,
-                        uint16_t* qa, float* B, int32_t* err, cudaStream_t st) {
+                        uint16_t* qa, float* B, int32_t* err, cudaStream_t st, double* gram_part) {
   if (!ttm_tc_supported(v, ell)) {
     set_error("tensor-core mode product: unsupported shape (needs the first mode, I % 8 == 0, ell <= 64)");
     return RH_EUNSUPPORTED;
@@ -463,14 +498,7 @@ rh_status launch_ttm_tc(const ModeView& v, int ell, const uint16_t* piece0, cons
   } else {
     m1 = m0;
   }
-  constexpr int IN = tc::kInPieces;
-  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m1, np, v.I, v.M(), ell, B, err,
-                                                                         nullptr, 0, CoreOut{}, tc_probe_next(), 1,
-                                                                         nullptr);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return launch_ttm_plain<tc::kInPieces>(mA, m0, m1, np, v, ell, B, err, nullptr, 0, st, gram_part);
 }
 
 // A converted-input launch (FP32 split on the fly into NP pieces); kG: with the Gram partials of B.
@@ -585,7 +613,7 @@ rh_status launch_core_product_tc(const float* B, int ell, int ko, int64_t M, Cor
 }
 
 rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const float* scales, int64_t ld,
-                            const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st) {
+                            const double* Q, uint16_t* qa, float* B, int32_t* err, cudaStream_t st, double* gram_part) {
   if (!ttm_tc_supported(v, ell) || ld < v.I || ld % 16 != 0) {
     set_error("tensor-core mode product: unsupported E4M3 shape (needs the first mode, I % 8 == 0, ell <= 64, "
               "a leading dimension that is a multiple of 16)");
@@ -601,14 +629,7 @@ rh_status launch_ttm_tc_fp8(const ModeView& v, int ell, const uint8_t* X, const 
   rh_status s = make_bf16_map_2d(&mA, qa, v.I, 128, 128);
   if (s != RH_OK) return s;
   if ((s = make_u8_map_2d(&m0, X, v.I, ld, v.M(), 64, kNTile)) != RH_OK) return s;
-  constexpr int IN = tc::kInFp8;
-  const size_t smem = sizeof(TtmSmem<IN>) + 1024;
-  RH_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ttm_tc_kernel<IN><<<ttm_tc_ctas(v), TtmCfg<IN>::kThreads, smem, st>>>(mA, m0, m0, 1, v.I, v.M(), ell, B, err,
-                                                                         scales, ld, CoreOut{}, tc_probe_next(), 1,
-                                                                         nullptr);
-  RH_LAUNCH_CHECK();
-  return RH_OK;
+  return launch_ttm_plain<tc::kInFp8>(mA, m0, m0, 1, v, ell, B, err, scales, ld, st, gram_part);
 }
 
 }  // namespace rh
