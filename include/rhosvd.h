@@ -218,7 +218,8 @@ rh_status rh_omega(uint64_t seed, int32_t tensor_id, int32_t mode, int64_t row0,
  *           multiply to a multiple of 64, I_mode <= 1024 (tensor cores, the FP32 values read through
  *           the 3-D view (l, i, r) of the mode and split on the fly).  norm2 is not computed for RH_BF16/RH_BF16X2 and must be
  *           NULL; for RH_F32_BF16X2 it is ||head + tail||^2 (FP32 sums over 32 values per thread
- *           and tile, FP64 above).
+ *           and tile, FP64 above).  RH_F32_BF16X3: as RH_F32_BF16X2 with the exact three-piece split
+ *           (no small-row route: I_0 % 8 == 0 for mode 0), norm2 = ||X||^2 of the FP32 values.
  *   mode    0-based mode n;  ell  number of columns, 1 <= ell <= RH_MAX_ELL.
  *   On the tensor-core forms the first int32 of the workspace receives the wait status once the
  *   stream has synchronised: 0, or the code of a bounded wait that gave up (Y is then invalid).
@@ -339,6 +340,7 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
  * a BF16 form (RH_BF16 / RH_BF16X2 / RH_F32_BF16X2): A is I_0 x k FP64 (1 <= k <= 64), split exactly into two BF16
  * pieces; Y is k x (N / I_0) FP32 (layout c + k p), all four piece products with FP32
  * accumulation.  Needs I_0 % 8 == 0, or I_0 <= 128 and k <= 32 (the small-row kernel).
+ * RH_F32_BF16X3: the FP32 X split exactly into three pieces (I_0 % 8 == 0 only).
  * Workspace: rh_mode_product_workspace_size; its first int32
  * receives the wait status as in rhosvd_sketch (0, or the code of a bounded wait that gave up).
  */
