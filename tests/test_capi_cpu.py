@@ -414,3 +414,19 @@ def test_header_is_plain_c_and_links(L):
     res = subprocess.run([exe], capture_output=True, text=True, check=True)
     ws, deim = res.stdout.split()
     assert int(ws) == _ws(L, [30, 20, 10], [4, 4, 4], dtype=1) and int(deim) == 2
+
+
+def test_three_piece_form_plans(L):
+    """RH_F32_BF16X3 is planned like the two-piece split form (a first mode outside the tensor-core
+    kernels on the CUDA cores), and refused with subspace iteration, whose sketch reads head + tail."""
+    from paper_1905_07311_gb300 import _lib
+
+    x3, x2 = _lib.RH_F32_BF16X3, _lib.RH_F32_BF16X2
+    assert _ws(L, [256, 128, 96], [20, 20, 20], dtype=x3, p=10) > 0
+    assert _ws(L, [90, 64, 40], [6, 5, 4], dtype=x3, p=5) > 0
+    assert _ws(L, [256, 128, 96], [20, 20, 20], dtype=x3, p=10, power_iters=1) == 0
+    assert "subspace iteration" in L.rh_last_error().decode()
+    assert _ws(L, [256, 128, 96], [20, 20, 20], dtype=x2, p=10, power_iters=1) > 0
+    dims = _lib.i64_array([256, 40, 30])
+    assert L.rhosvd_sketch_workspace_size(3, dims, x3, 0, 25) > 0
+    assert L.rh_mode_product_workspace_size(3, dims, x3, 0, 25) > 0
