@@ -49,7 +49,8 @@ def read_table(path=TABLE):
     """[(key, name, value)] in the file's order."""
     import re
 
-    text = open(path).read()
+    with open(path) as f:
+        text = f.read()
     return [(k, n, int(v)) for k, n, v in re.findall(r'RH_TUNE\((\w+),\s*"([\w.]+)",\s*(\d+)\)', text)]
 
 
@@ -156,6 +157,42 @@ def _affects(name, objs):
     return [o for o in objs if name.startswith("gram") or o.startswith("batched")]
 
 
+def coordinate_descent(rows, values, objectives, measure, apply, passes, min_gain, log=lambda rec: None):
+    """Tune the knobs of ``rows`` one after another, in the table's order; return the chosen values.
+
+    ``measure(names)`` returns {objective: ms} under the knobs as currently applied, and
+    ``apply(name, value)`` sets one knob.  A candidate scores sum over the objectives the knob
+    affects of ms / ms at the knob's current value, so the current value scores len(affected).  The
+    knob moves to the best-scoring candidate only if that score is below len(affected) - min_gain,
+    and it is applied again either way.  Passes repeat until one moves no knob, at most ``passes``.
+    """
+    values = dict(values)
+    for it in range(passes):
+        moved = False
+        for _, name, _ in rows:
+            on = _affects(name, objectives)
+            ref = measure(on)
+            best_v, best_s = values[name], float(len(on))
+            for v in _candidates(name):
+                if v == values[name]:
+                    continue
+                apply(name, v)
+                ms = measure(on)
+                score = sum(ms[o] / ref[o] for o in on)
+                log({"pass": it, "knob": name, "value": v, "score": round(score / len(on), 4),
+                     "ms": {k: round(x, 4) for k, x in ms.items()}})
+                if score < best_s:
+                    best_v, best_s = v, score
+            if best_v != values[name] and best_s < len(on) - min_gain:
+                values[name] = best_v
+                moved = True
+            apply(name, values[name])
+            log({"pass": it, "knob": name, "chosen": values[name]})
+        if not moved:
+            break
+    return values
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--passes", type=int, default=2)
@@ -191,29 +228,14 @@ def main(argv=None):
     base.update({k: o.time() for k, o in report.items()})
     print(json.dumps({"table": values, "ms": {k: round(v, 4) for k, v in base.items()}, "tensors": ntens}),
           flush=True)
-    for it in range(args.passes):
-        moved = False
-        for _, name, _ in rows:
-            on = _affects(name, objs)
-            ref = measure(on)
-            best_v, best_s = values[name], float(len(on))
-            for v in _candidates(name):
-                if v == values[name]:
-                    continue
-                _lib.check(L.rh_tuning_set(name.encode(), v))
-                ms = measure(on)
-                score = sum(ms[o] / ref[o] for o in on)
-                print(json.dumps({"pass": it, "knob": name, "value": v, "score": round(score / len(on), 4),
-                                  "ms": {k: round(x, 4) for k, x in ms.items()}}), flush=True)
-                if score < best_s:
-                    best_v, best_s = v, score
-            if best_v != values[name] and best_s < len(on) - args.min_gain:
-                values[name] = best_v
-                moved = True
-            _lib.check(L.rh_tuning_set(name.encode(), values[name]))
-            print(json.dumps({"pass": it, "knob": name, "chosen": values[name]}), flush=True)
-        if not moved:
-            break
+
+    def apply(name, v):
+        _lib.check(L.rh_tuning_set(name.encode(), v))
+
+    def log(rec):
+        print(json.dumps(rec), flush=True)
+
+    values = coordinate_descent(rows, values, list(objs), measure, apply, args.passes, args.min_gain, log)
     final = measure(list(objs))
     final.update({k: o.time() for k, o in report.items()})
     print(json.dumps({"table": values, "ms": {k: round(v, 4) for k, v in final.items()},
