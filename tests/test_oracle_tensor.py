@@ -4,14 +4,15 @@
   written as explicit index loops on tiny tensors;
 * the Kronecker form of a multi-mode product (Eq. kron), which fixes the column
   order of the unfolding;
-* Lemma lem:proj (error decomposition for orthogonal projectors).
+* Lemma lem:proj (error decomposition for orthogonal projectors);
+* the relative error of the zero approximation (1) and its invariance under scaling.
 """
 
 import itertools
 
 import numpy as np
 
-from oracle.tensor import fold, frob, multi_ttm, ttm, unfold
+from oracle.tensor import fold, frob, multi_ttm, rel_error, ttm, unfold
 
 
 def _tiny(shape, seed=0):
@@ -78,3 +79,18 @@ def test_projector_lemma():
     rhs = sum(frob(X - ttm(X, P[j], j)) ** 2 for j in range(3))
     assert abs(lhs - sum(terms)) < 1e-10 * lhs
     assert lhs <= rhs + 1e-12
+
+
+def test_rel_error_of_the_zero_and_of_a_scaled_approximation():
+    # ||X - 0|| / ||X|| = 1 for any X, and the relative error does not change when X and the
+    # approximation are scaled together (||X|| = 2.5 here, so a norm of the wrong power shows)
+    rs = np.random.default_rng(9)
+    X = rs.standard_normal((4, 3, 5))
+    X *= 2.5 / frob(X)
+    A = [np.linalg.qr(rs.standard_normal((n, 2)))[0] for n in X.shape]
+    assert abs(rel_error(X, np.zeros((2, 2, 2)), A) - 1.0) < 1e-15
+    G = multi_ttm(X, A, transpose=True)
+    e = rel_error(X, G, A)
+    assert 0.0 < e < 1.0
+    assert abs(rel_error(3.0 * X, 3.0 * G, A) - e) < 1e-14
+    assert abs(e - frob(X - multi_ttm(G, A)) / 2.5) < 1e-14

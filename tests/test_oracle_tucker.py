@@ -244,3 +244,56 @@ def test_srrqr_condition_and_determinant_growth():
             S = P.copy()
             S[j] = i
             assert abs(np.linalg.det(Q[S])) <= 2.0 * d0 * (1 + 1e-9)
+
+
+def test_adapt_range_finder_meets_its_tolerance_without_oversampling():
+    # Sec. 4's guarantee for the trimmed basis: ||G - A A^T G||_F <= tol.  With p = 0 the range
+    # finder stops with ||G - Q B||_F just below tol, so the trimming has to count that residual
+    # next to the discarded singular values of B
+    rs = np.random.default_rng(31)
+    for trial in range(12):
+        m, n = 40, 60
+        U = np.linalg.qr(rs.standard_normal((m, m)))[0]
+        V = np.linalg.qr(rs.standard_normal((n, m)))[0]
+        s = 0.7 ** np.arange(m) * (1.0 + 0.1 * rs.random(m))
+        G = (U * s) @ V.T
+        tol = float(rs.uniform(0.02, 0.3)) * np.linalg.norm(G)
+        omega = rs.standard_normal((n, m))
+        A, info = tucker.adapt_range_finder(G, tol, 1 + trial % 4, 0, lambda c0, c1: omega[:, c0:c1])
+        assert np.abs(A.T @ A - np.eye(A.shape[1])).max() < 1e-12
+        assert np.linalg.norm(G - A @ (A.T @ G)) <= tol * (1 + 1e-12), trial
+        # and no smaller rank would do: dropping A's last column breaks the tolerance
+        if A.shape[1] > 1:
+            A1 = A[:, :-1]
+            assert np.linalg.norm(G - A1 @ (A1.T @ G)) > tol, trial
+
+
+def test_adaptive_rhosvd_ranks_of_a_superdiagonal_tensor():
+    # X(k, k, k) = 2^-k, k = 0..7: every unfolding has the singular values 2^-k, ||X||^2 =
+    # (1 - 4^-8) / (3/4).  With eps = 0.08, Alg. 4's per-mode tolerance eps ||X|| / sqrt(3) has
+    # tol^2 = 0.0028444; the discarded energy sum_{k > r} 4^-k is 0.0051880 for r = 4 and 0.0012817
+    # for r = 5, so every mode keeps rank 5 (p = 8 makes Q span the whole range, B's singular values
+    # are the 2^-k).  The approximation keeps the entries k < 5, so the error is
+    # sqrt(0.0012817) / ||X|| = 0.0310 <= eps.
+    X = np.zeros((8, 8, 8))
+    for k in range(8):
+        X[k, k, k] = 2.0 ** -k
+    for b in (1, 2, 3):
+        out = tucker.adaptive_rhosvd(X, 0.08, b, 8, seed=3)
+        assert [A.shape[1] for A in out["factors"]] == [5, 5, 5], b
+        e = rel_error(X, out["core"], out["factors"])
+        assert abs(e - math.sqrt((4.0 ** -5 + 4.0 ** -6 + 4.0 ** -7) / ((1 - 4.0 ** -8) / 0.75))) < 1e-12
+
+
+def test_randomized_bound_is_at_least_the_best_tucker_error():
+    # Thm. rhosvd_err / rst_err bound the expected error, and no rank-(r_1, ..., r_d) Tucker
+    # approximation has an error below max_j Delta_j (its mode-j unfolding has rank <= r_j), so the
+    # bound can never be smaller -- also for a large oversampling p, where r / (p - 1) is small
+    X = lowrank_plus_noise_np([20, 18, 16], [6, 6, 6], 0.8, 1e-2, seed=8)
+    ranks = [4, 4, 4]
+    lower = max(np.linalg.norm(np.linalg.svd(unfold(X, n), compute_uv=False)[4:]) for n in range(3))
+    for p in (2, 5, 41, 401):
+        assert tucker.randomized_bound(X, ranks, p) >= lower
+    # and at p -> infinity the bound tends to the deterministic HOSVD bound sqrt(sum_j Delta_j^2)
+    hosvd_bound = math.sqrt(sum(np.sum(np.linalg.svd(unfold(X, n), compute_uv=False)[4:] ** 2) for n in range(3)))
+    assert abs(tucker.randomized_bound(X, ranks, 4001) / hosvd_bound - 1.0) < 2e-3
