@@ -108,6 +108,39 @@ MUTANTS = [
      "idx[:, n] = pos[idx[:, n]][::-1]", SELECT),
     ("orthonormalize_transposed_triangle", "oracle.tucker", "orthonormalize_tucker", "G = ttm(G, R, n)",
      "G = ttm(G, R.T, n)", SELECT),
+    # helpers shared by the algorithms
+    ("default_order_increasing", "oracle.tucker", "default_order", "(-int(dims[n]), n)", "(int(dims[n]), n)",
+     TUCKER),
+    ("clamp_ignores_other_modes", "oracle.tucker", "_ell", "min(ell, int(I), int(M))", "min(ell, int(I))", TUCKER),
+    ("strict_size_rule_lax", "oracle.tucker", "_check_ell", "ell < min(I, M) if strict", "ell <= min(I, M) if strict",
+     TUCKER),
+    ("canon_signs_flipped", "oracle.tucker", "canon_signs", "np.where(v < 0, -1.0, 1.0)", "np.where(v > 0, -1.0, 1.0)",
+     TUCKER),
+    ("omega_matrix_not_rounded", "oracle.tucker", "omega_matrix", 'if omega_round == "bf16":',
+     'if omega_round == "never":', TUCKER),
+    ("omega_matrix_wrong_mode", "oracle.tucker", "omega_matrix", "rng.omega(seed, tensor_id, mode,",
+     "rng.omega(seed, tensor_id, 0,", TUCKER),
+    ("coo_sketch_not_rounded", "oracle.tucker", "coo_sketch", 'if omega_round == "bf16":', 'if omega_round == "never":',
+     SELECT),
+    ("hosvd_rank_off_by_one", "oracle.tucker", "hosvd", "unfold(X, n), ranks[n])", "unfold(X, n), ranks[n] + 1)",
+     TUCKER),
+    ("uniform_sampling_stream_ignored", "oracle.tucker", "sample_select", "np.uint32(stream), np.uint32(0)",
+     "np.uint32(0), np.uint32(0)", SELECT),
+    ("sampling_keeps_taken_rows", "oracle.tucker", "sample_select", "taken[pick] = True", "taken[pick] = False",
+     SELECT),
+    ("sp_hosvd_selection_stream", "oracle.tucker", "sp_hosvd", "(int(tensor_id) << 4) | n)", "int(tensor_id) << 4)",
+     SELECT),
+    ("sp_coo_keeps_unselected", "oracle.tucker", "sp_sthosvd_coo", "keep = pos[idx[:, n]] >= 0",
+     "keep = pos[idx[:, n]] >= -1", SELECT),
+    ("fp8_rows_wrong_stride", "oracle.storage", "fp8_dequantize_rows", "e = int(i) + ld * p", "e = int(i) + dims[0] * p",
+     STORAGE),
+    ("omega_columns_wrong_lane", "oracle.rng", "omega_columns", "out[:, j] = groups[q][c % 4]",
+     "out[:, j] = groups[q][(c + 1) % 4]", RNG),
+    ("stream_id_shift", "oracle.rng", "stream_id", "(int(tensor_id) << 4) | int(mode)", "(int(tensor_id) << 3) | int(mode)",
+     RNG),
+    ("sp_bound_drops_growth", "oracle.tucker", "sp_bound", "gprod *= math.sqrt(1.0 + 4.0 * ell * (I - ell))",
+     "gprod *= 1.0", TUCKER),
+    ("sp_bound_growth_not_cumulative", "oracle.tucker", "sp_bound", "gprod *= math.sqrt(", "gprod = math.sqrt(", TUCKER),
     # the error bounds of Sec. 3.2 / 5.2 (a bound that is too small fails the seed-averaged checks)
     ("bound_drops_one", "oracle.tucker", "randomized_bound", "(1.0 + ranks[n] / (p - 1.0))",
      "(ranks[n] / (p - 1.0))", TUCKER),

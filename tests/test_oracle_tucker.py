@@ -297,3 +297,42 @@ def test_randomized_bound_is_at_least_the_best_tucker_error():
     # and at p -> infinity the bound tends to the deterministic HOSVD bound sqrt(sum_j Delta_j^2)
     hosvd_bound = math.sqrt(sum(np.sum(np.linalg.svd(unfold(X, n), compute_uv=False)[4:] ** 2) for n in range(3)))
     assert abs(tucker.randomized_bound(X, ranks, 4001) / hosvd_bound - 1.0) < 2e-3
+
+
+def test_clamped_sketch_width_obeys_the_size_requirement():
+    # Alg. 1-3 need r + p <= min(I_n, product of the other current sizes); clamping takes the widest
+    # sketch the requirement allows.  30 x 3 x 2, ranks (5, 2, 2), p = 10, modes in order 0, 1, 2:
+    # R-STHOSVD: mode 0 has 6 other entries (ell 6, rank 5), mode 1 I = 3 (ell 3, rank 2), mode 2
+    # I = 2 (ell 2); R-HOSVD: 6, 3 and 2 as well (I_1 = 3, I_2 = 2 bind there)
+    X = lowrank_plus_noise_np([30, 3, 2], [3, 2, 2], 0.8, 1e-3, seed=6)
+    for alg in ("rsthosvd", "rhosvd"):
+        out = getattr(tucker, alg)(X, [5, 2, 2], 10, seed=1, clamp=True, record=True)
+        assert [rec["ell"] for rec in out["records"]] == [6, 3, 2], alg
+        assert [rec["Y"].shape[1] for rec in out["records"]] == [6, 3, 2], alg
+        assert [A.shape[1] for A in out["factors"]] == [5, 2, 2], alg
+    with pytest.raises(ValueError):
+        tucker.rsthosvd(X, [5, 2, 2], 10, seed=1)
+
+
+def test_factor_columns_follow_the_sign_convention():
+    # the QR and the SVD of Alg. 1 fix each column only up to sign; the convention used on both
+    # sides of the parity tests: a column's entry of largest magnitude is positive
+    X = lowrank_plus_noise_np([12, 10, 9], [4, 4, 4], 0.8, 1e-2, seed=13)
+    outs = [tucker.rsthosvd(X, [3, 3, 3], 2, seed=5), tucker.rhosvd(X, [3, 3, 3], 2, seed=5),
+            tucker.rsthosvd(X, [3, 3, 3], 2, seed=5, truncate=False)]
+    for out in outs:
+        for A in out["factors"]:
+            j = np.argmax(np.abs(A), axis=0)
+            assert np.all(A[j, np.arange(A.shape[1])] > 0)
+
+
+def test_sp_bound_of_a_superdiagonal_tensor():
+    # Thm. pass_error's right side evaluated by hand on X(k, k, k) = 2^-k (8 x 8 x 8), ranks 2,
+    # p = 2: ell = 4, the growth factor g(8, 4) = sqrt(1 + 4 * 4 * (8 - 4)) = sqrt(65) multiplies
+    # up over the processed modes, Delta_j^2 = sum_{k >= 2} 4^-k = 0.08331298828125 on every mode and
+    # sqrt(1 + r / (p - 1)) = sqrt(3): bound = sqrt(3) Delta (g + g^2 + g^3) = 298.5180588273678
+    X = np.zeros((8, 8, 8))
+    for k in range(8):
+        X[k, k, k] = 2.0 ** -k
+    assert abs(tucker.sp_bound(X, [2, 2, 2], 2) - 298.5180588273678) < 1e-9
+    assert abs(tucker.randomized_bound(X, [2, 2, 2], 2) - math.sqrt(3 * 3 * 0.08331298828125)) < 1e-12
