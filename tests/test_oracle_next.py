@@ -333,3 +333,26 @@ def test_leverage_sampling_follows_its_law():
         prob = w[a] / T * w[b] / (T - w[a]) + w[b] / T * w[a] / (T - w[b])
         sd = math.sqrt(n * prob * (1 - prob))
         assert abs(v - n * prob) <= 5 * sd + 1, ((a, b), v, n * prob)
+
+
+def test_adaptive_bf16_omega_is_the_rounded_stream():
+    """Alg. 5 with the BF16-rounded Omega on a mode (the BF16 storage forms): that mode's range
+    finder sees the FP32 normals rounded to BF16 (ties to even), so its first block's sketch is
+    X_(n) times the rounded columns, and the factor differs from the FP32 stream's by the rounding
+    only (the rounded stream is not the FP32 one)."""
+    from oracle.tensor import unfold
+    from workloads import lowrank_plus_noise_np
+
+    X = lowrank_plus_noise_np([24, 20, 18], [5, 5, 5], 0.7, 1e-3, seed=21)
+    cols = tucker._omega_cols_fn(7, 0, 0, 20 * 18, "bf16")
+    om = rng.omega(7, 0, 0, np.arange(20 * 18), 4)
+    omb = rng.round_bf16(om).astype(np.float64)
+    assert np.array_equal(cols(0, 4), omb)
+    assert not np.array_equal(omb, om.astype(np.float64))
+    tol = 0.05 * np.linalg.norm(X) / np.sqrt(3)
+    Ab, ib = tucker.adapt_range_finder(unfold(X, 0), tol, 4, 2, cols)
+    out = tucker.adaptive_rsthosvd(X, 0.05, 4, 2, 7, rho=[0, 1, 2], omega_round={0: "bf16"})
+    assert np.allclose(out["factors"][0], Ab, atol=1e-13)
+    out32 = tucker.adaptive_rsthosvd(X, 0.05, 4, 2, 7, rho=[0, 1, 2])
+    assert out32["factors"][0].shape == Ab.shape
+    assert not np.allclose(out32["factors"][0], Ab, atol=1e-13)
