@@ -1,4 +1,4 @@
-"""The slab partition of R-STHOSVD (``paper_1905_07311_gb300.slab``) on CPU ranks (gloo, world size 2).
+"""The slab partition of R-STHOSVD (``paper_1905_07311_gb300.slab``) on CPU ranks (gloo, world sizes 2 and 3).
 
 The partition and exchange logic -- global Omega rows per slab, the all-reduce of the sketches, the
 all-gather of the tall-skinny triangles and of the last mode's row blocks, the all-reduce of the
@@ -7,7 +7,7 @@ backend written with numpy for these host tensors (the library itself needs a GP
   * the slabs' sketches with their global Omega rows add up to the whole tensor's sketch;
   * the left singular vectors of the stacked triangles [R_1^T R_2^T] are those of B itself;
   * the whole decomposition equals the oracle's R-STHOSVD (Alg. 3, modes in order) to 1e-12,
-    with even and uneven slabs and with two slabs on one rank.
+    with even and uneven slabs, with two slabs on one rank, and on three ranks for a 4-way tensor.
 """
 
 import os
@@ -135,19 +135,25 @@ def _rank_main(rank, world, port, dims, ranks, p, seed, bounds_per_rank, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("bounds", [[[(0, 8)], [(8, 16)]],
-                                    [[(0, 5)], [(5, 16)]],
-                                    [[(0, 3), (3, 9)], [(9, 16)]]])
-def test_slab_partition_on_two_gloo_ranks_equals_one_tensor(bounds):
+@pytest.mark.parametrize("dims,ranks,bounds", [
+    ([20, 18, 16], [4, 5, 3], [[(0, 8)], [(8, 16)]]),
+    ([20, 18, 16], [4, 5, 3], [[(0, 5)], [(5, 16)]]),
+    ([20, 18, 16], [4, 5, 3], [[(0, 3), (3, 9)], [(9, 16)]]),
+    # three ranks on a 4-way tensor, uneven slabs, one rank with two slabs
+    ([10, 9, 8, 12], [4, 3, 4, 3], [[(0, 2)], [(2, 5), (5, 9)], [(9, 12)]]),
+])
+def test_slab_partition_on_gloo_ranks_equals_one_tensor(dims, ranks, bounds):
     from oracle import rng, tucker
     from oracle.tensor import rel_error, unfold
 
-    dims, ranks, p, seed = [20, 18, 16], [4, 5, 3], 3, 11
+    p, seed = 3, 11
+    world = len(bounds)
     mp = torch.multiprocessing.get_context("spawn")
     with mp.Manager() as m:
         out = m.dict()
         port = _free_port()
-        procs = [mp.Process(target=_rank_main, args=(r, 2, port, dims, ranks, p, seed, bounds, out)) for r in range(2)]
+        procs = [mp.Process(target=_rank_main, args=(r, world, port, dims, ranks, p, seed, bounds, out))
+                 for r in range(world)]
         for pr in procs:
             pr.start()
         for pr in procs:
@@ -158,14 +164,14 @@ def test_slab_partition_on_two_gloo_ranks_equals_one_tensor(bounds):
     # the slab sketches with global Omega rows sum to the whole tensor's sketch
     Xm = unfold(X, 0)
     Yfull = Xm @ rng.omega(seed, 0, 0, np.arange(Xm.shape[1]), ranks[0] + p).astype(np.float64)
-    for r in range(2):
+    for r in range(world):
         assert np.allclose(res[r]["Y"].T, Yfull, rtol=0, atol=1e-12 * np.abs(Yfull).max())
     # every rank holds the same decomposition, equal to the oracle's
-    ref = tucker.rsthosvd(X, ranks, p, seed, rho=[0, 1, 2])
-    for r in range(2):
+    ref = tucker.rsthosvd(X, ranks, p, seed, rho=list(range(len(dims))))
+    for r in range(world):
         A = [f.T for f in res[r]["factors"]]
         G = np.reshape(res[r]["core"], res[r]["core_dims"], order="F")
-        for n in range(3):
+        for n in range(len(dims)):
             assert np.allclose(A[n], ref["factors"][n], rtol=0, atol=1e-10)
         assert np.allclose(G, ref["core"], rtol=0, atol=1e-10 * np.abs(ref["core"]).max())
         assert abs(rel_error(X, G, A) - rel_error(X, ref["core"], ref["factors"])) <= 1e-12
