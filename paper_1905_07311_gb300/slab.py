@@ -36,16 +36,32 @@ class SelfComm:
     def allgather(self, t):
         return [t]
 
+    def allgather_ints(self, values):
+        return [[int(v) for v in values]]
+
 
 class TorchComm:
     """torch.distributed (NCCL for CUDA tensors, gloo for host tensors) on the default group."""
 
     def __init__(self):
+        import torch
         import torch.distributed as dist
 
         self.dist = dist
         self.rank = dist.get_rank()
         self.world = dist.get_world_size()
+        # where the small host-side exchanges live: NCCL moves device tensors only
+        nccl = dist.get_backend() == "nccl"
+        self.device = torch.device("cuda", torch.cuda.current_device()) if nccl else torch.device("cpu")
+
+    def allgather_ints(self, values):
+        """Every rank's list of integers (the lists have the same length on every rank)."""
+        import torch
+
+        t = torch.tensor([int(v) for v in values], dtype=torch.int64, device=self.device)
+        out = [torch.empty_like(t) for _ in range(self.world)]
+        self.dist.all_gather(out, t)
+        return [[int(v) for v in o.tolist()] for o in out]
 
     def allreduce_sum(self, t):
         self.dist.all_reduce(t)
@@ -191,23 +207,57 @@ def _ell(r, p, I, M, clamp):
     return ell
 
 
+def _validate(slabs, dims, ranks, p, seed, tensor_id, clamp, comm):
+    """Checks that every rank takes in the same order and answers the same way, before any collective
+    of the decomposition, so that a misconfigured rank makes every rank raise the same error instead
+    of leaving the others in a collective of another size: the same sizes, ranks and options on every
+    rank; each rank's slabs consecutive, non-empty and of sizes dims[:-1] + [k1 - k0]; the ranks'
+    ranges tiling 0 .. dims[-1] in rank order."""
+    import hashlib
+
+    per = _prod(dims[:-1])
+    ok = 1 if slabs and len(ranks) == len(dims) else 0
+    for a, b in zip(slabs, slabs[1:]):
+        ok &= 1 if a.k1 == b.k0 else 0
+    for sl in slabs:
+        ok &= 1 if sl.k1 > sl.k0 and sl.data.numel() == per * (sl.k1 - sl.k0) else 0
+    k_lo, k_hi = (slabs[0].k0, slabs[-1].k1) if slabs else (-1, -1)
+    conf = repr(([int(v) for v in dims], [int(v) for v in ranks], int(p), int(seed), int(tensor_id), bool(clamp)))
+    digest = int.from_bytes(hashlib.sha256(conf.encode()).digest()[:7], "little")
+    rows = comm.allgather_ints([k_lo, k_hi, ok, digest])
+    if any(r[3] != rows[0][3] for r in rows):
+        raise ValueError("the ranks disagree on the sizes, ranks or options of the decomposition")
+    bad = [i for i, r in enumerate(rows) if not r[2]]
+    if bad:
+        raise ValueError(f"rank(s) {bad}: slabs empty, not consecutive, or not of sizes dims[:-1] + [k1 - k0]")
+    edges = [0] + [r[1] for r in rows]
+    if any(r[0] != e for r, e in zip(rows, edges)) or edges[-1] != int(dims[-1]):
+        raise ValueError("the ranks' slabs do not tile 0 .. dims[-1] in rank order: "
+                         + ", ".join(f"[{r[0]}, {r[1]})" for r in rows))
+
+
 class SlabResult:
     def __init__(self, factors, core, core_dims, norm_x2):
         self.factors, self.core, self.core_dims, self.norm_x2 = factors, core, core_dims, norm_x2
 
 
-def rsthosvd_slabs(slabs, dims, ranks, p=5, seed=0, tensor_id=0, comm=None, backend=None, clamp=False):
+def rsthosvd_slabs(slabs, dims, ranks, p=5, seed=0, tensor_id=0, comm=None, backend=None, clamp=False,
+                   validate=True):
     """R-STHOSVD of the global tensor of sizes ``dims`` whose slabs along the last mode are given by
     ``slabs`` (this rank's, consecutive, in increasing k0; together the ranks' slabs cover
     0 .. dims[-1] in rank order).  Modes 0 .. d-2 in increasing order, then the last mode.  Returns the
     factors (list of (r_n, I_n) FP64 tensors: column-major I_n x r_n), the FP64 core (flat,
-    r_0 x ... x r_{d-1}) on every rank and ||X||^2."""
+    r_0 x ... x r_{d-1}) on every rank and ||X||^2.  ``validate`` first checks across the ranks that
+    they agree on the problem and that their slabs tile the last mode (one small all-gather; every
+    rank raises the same ValueError otherwise); a caller repeating the same call may skip it."""
     comm = comm or SelfComm()
     be = backend or LibraryBackend()
     torch = be.torch
     d = len(dims)
     if d < 2:
         raise ValueError("a slab partition needs at least two modes")
+    if validate:
+        _validate(slabs, dims, ranks, p, seed, tensor_id, clamp, comm)
     cur = [int(v) for v in dims]
     k_lo, k_hi = slabs[0].k0, slabs[-1].k1
     for a, b in zip(slabs, slabs[1:]):

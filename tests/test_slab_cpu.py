@@ -190,3 +190,61 @@ def test_stacked_triangles_give_the_left_singular_vectors_of_b():
     Uc, sc, _ = np.linalg.svd(C, full_matrices=False)
     assert np.allclose(s, sc, rtol=1e-12)
     assert np.allclose(np.abs(U.T @ Uc), np.eye(9), atol=1e-10)
+
+
+def _bad_rank_main(rank, world, port, case, out):
+    import datetime
+
+    sys.path.insert(0, ROOT)
+    from paper_1905_07311_gb300 import slab
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        dims, ranks, p = [12, 10, 8], [3, 3, 3], 2
+        X = _tensor(dims, 4)
+        bounds = {"good": [[(0, 4)], [(4, 8)]], "options": [[(0, 4)], [(4, 8)]], "gap": [[(0, 3)], [(4, 8)]],
+                  "order": [[(4, 8)], [(0, 4)]], "short": [[(0, 4)], [(4, 7)]], "size": [[(0, 4)], [(4, 8)]],
+                  "empty": [[(0, 8)], []]}[case][rank]
+        slabs = _slabs_of(X, bounds)
+        if case == "options" and rank == 1:
+            p = 3
+        if case == "size" and rank == 1:
+            slabs[0] = slab.Slab(4, 8, slabs[0].data[:-1])
+        try:
+            slab.rsthosvd_slabs(slabs, dims, ranks, p=p, seed=1, comm=slab.TorchComm(), backend=NumpyBackend())
+            out[rank] = "ok"
+        except ValueError as e:
+            out[rank] = "ValueError: " + str(e)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("case,words", [("good", None), ("options", "disagree"), ("gap", "tile"),
+                                        ("order", "tile"), ("short", "tile"), ("size", "rank(s) [1]"),
+                                        ("empty", "rank(s) [1]")])
+def test_misconfigured_ranks_all_raise_the_same_error(case, words):
+    """A rank with other options, slabs that leave a gap, come out of rank order or stop short of the
+    last mode, a slab of the wrong size, or no slab at all: every rank raises the same ValueError
+    before the decomposition's first collective, so none is left waiting in it."""
+    mp = torch.multiprocessing.get_context("spawn")
+    with mp.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [mp.Process(target=_bad_rank_main, args=(r, 2, port, case, out)) for r in range(2)]
+        for pr in procs:
+            pr.start()
+        try:
+            for pr in procs:
+                pr.join(timeout=120)
+                assert pr.exitcode == 0
+        finally:
+            for pr in procs:
+                if pr.is_alive():
+                    pr.kill()
+        res = dict(out)
+    if words is None:
+        assert res == {0: "ok", 1: "ok"}
+    else:
+        assert res[0] == res[1] and res[0].startswith("ValueError") and words in res[0], res
