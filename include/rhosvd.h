@@ -267,6 +267,8 @@ rh_status rh_tall_skinny_r(int32_t order, const int64_t* dims, int32_t dtype, co
 /*
  * rh_cast_f64 -- dst[i] = src[i] converted to RH_F32 (round to nearest even) or copied (RH_F64), for
  * i < n: the FP64 factors in the precision of an FP32 tensor's mode products.  Device pointers.
+ *   The paper has no counterpart (a storage-precision helper of the slab partition).  n = 0 does
+ *   nothing.  RH_EINVAL: n < 0, a NULL pointer with n > 0, dtype other than RH_F32 / RH_F64.
  */
 rh_status rh_cast_f64(const double* src, int64_t n, int32_t dtype, void* dst, void* stream);
 
@@ -306,6 +308,10 @@ rh_status rhosvd_sketch_static(int32_t order, const int64_t* dims, int32_t dtype
 /*
  * rh_split_bf16x2 -- write the RH_BF16X2 representation of an FP32 array: out[0..n) = bf16(x),
  * out[n..2n) = bf16(x - bf16(x)) (ties to even).  n % 8 == 0 keeps the tail 16-byte aligned.
+ *   The paper has no counterpart (the storage form that the tensor-core kernels read; the FP32
+ *   split form computes the same pieces inside the kernels).  X: n FP32 values, out: 2 n BF16
+ *   values, device pointers owned by the caller.  n = 0 does nothing.  RH_EINVAL: n < 0, a NULL
+ *   pointer with n > 0.
  */
 rh_status rh_split_bf16x2(const float* X, int64_t n, uint16_t* out, void* stream);
 
@@ -343,6 +349,11 @@ rh_status rh_mode_product(int32_t order, const int64_t* dims, int32_t dtype, con
  * RH_F32_BF16X3: the FP32 X split exactly into three pieces (I_0 % 8 == 0 only).
  * Workspace: rh_mode_product_workspace_size; its first int32
  * receives the wait status as in rhosvd_sketch (0, or the code of a bounded wait that gave up).
+ * RH_FP8_E4M3 (the block-scaled layout of rh_fp8_layout) is read the same way, dequantized and
+ * rounded to one BF16 piece.  This is Alg. 1 step 3 (B = Q^T X_(1)) with Q = A, for the input forms
+ * whose first mode runs on the tensor cores.  RH_EINVAL: another dtype, bad order or dims, NULL
+ * pointers; RH_EUNSUPPORTED: k or a shape that neither kernel takes; RH_ENOMEM: workspace_bytes
+ * below the query.
  */
 size_t rh_mode_product_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, int32_t mode, int32_t k);
 rh_status rh_mode_product_bf16(int32_t order, const int64_t* dims, int32_t dtype, const void* X, int32_t k,
@@ -677,6 +688,9 @@ rh_status rh_subset_select(int64_t I, int32_t ell, const double* Q, int32_t meth
  *                are invalid.  Read it after the stream has synchronised.
  *   workspace    DEVICE buffer of rsthosvd_host_workspace_size bytes; it holds the device
  *                copy of X, the device outputs and the rsthosvd workspace.
+ *   The decomposition is Alg. 3 exactly as rsthosvd computes it (bit-identical results); the
+ *   host copies are the end-to-end leg of the measurement, not part of the paper's method.
+ *   Errors as rsthosvd (RH_EINVAL before anything is enqueued, RH_ENOMEM for a short workspace).
  */
 size_t rsthosvd_host_workspace_size(int32_t order, const int64_t* dims, int32_t dtype, const int32_t* ranks,
                                     const rh_options* opts);
