@@ -475,7 +475,9 @@ rh_status rsthosvd_batched(int32_t count, const int32_t* orders, const int64_t* 
  * (no host synchronisation; capturable); every run recomputes all outputs from the current
  * contents of X.  The buffers named at create must stay valid while the plan is used.  destroy
  * frees the tables (it synchronises the device through cudaFree).  RH_EUNSUPPORTED when a request
- * is not FP32 / FP64 with truncation.
+ * cannot run on the grouped engine.  The engine takes truncated requests (truncate = 1) of FP32 or
+ * FP64 data, and of the BF16 forms whose first mode is processed first and takes the small-row
+ * tensor-core kernels (I_0 <= 128, ell <= 32).
  */
 typedef struct rh_batched_plan_s* rh_batched_plan;
 rh_status rsthosvd_batched_plan_create(int32_t count, const int32_t* orders, const int64_t* dims, int32_t dtype,

@@ -262,7 +262,8 @@ rh_status rsthosvd_batched_plan_create(int32_t count, const int32_t* orders, con
   rh_status s = batch_layout(count, orders, dims, dtype, ranks, opts, 1, bl);
   if (s != RH_OK) return s;
   if (!bl.groupable) {
-    set_error("unsupported: a batched plan needs FP32 or FP64 truncated requests (every tensor on the grouped engine)");
+    set_error("unsupported: a batched plan needs every request on the grouped engine (truncated, FP32 or FP64 "
+              "data, or a BF16 form whose first mode takes the small-row tensor-core kernels)");
     return RH_EUNSUPPORTED;
   }
   RH_CHECK_ARG(X != nullptr && factors != nullptr && cores != nullptr, "X, factors and cores must be non-NULL");
