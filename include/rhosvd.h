@@ -550,7 +550,12 @@ rh_status rh_tucker_residual(int32_t order, const int64_t* dims, int32_t dtype, 
  * opts->p more columns of the same stream; the SVD of B = Q^T G_(n) is trimmed to the smallest r
  * with sum_{i>r} sigma_i^2 + ||G_(n) - Q B||^2 <= tau^2.  One sketch of width max_ranks[n] + p
  * serves every block size (the leading columns of its thin QR span the leading blocks).
- *   X          tensor (order, dims, RH_F64 or RH_F32), column-major, device.
+ *   X          tensor (order, dims, dtype), column-major, device.  RH_F64 and RH_F32 with either
+ *              variant; the BF16 and E4M3 forms (RH_BF16, RH_BF16X2, RH_F32_BF16X2, RH_FP8_E4M3)
+ *              with variant 1 only (RH_EUNSUPPORTED otherwise).  Their first mode runs on the tensor
+ *              cores, which needs mode 0 processed first, I_0 % 8 == 0, I_0 <= 1024 and
+ *              max_ranks[0] + p <= 64; otherwise RH_F32_BF16X2 runs as RH_F32 and the other forms
+ *              return RH_EUNSUPPORTED.  RH_F32_BF16X3 is not taken (RH_EINVAL).
  *   max_ranks  host array: cap on the range-finder size per mode (max_ranks[n] + p <= 64 after
  *              clamping to min(I_n, prod of the other sizes)).
  *   opts       p (trim oversampling), seed, tensor_id, rho (variant 1; rho[0] < 0: decreasing
