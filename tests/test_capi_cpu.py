@@ -328,6 +328,10 @@ def test_every_entry_point_validates_before_the_device(L):
     assert L.adaptive_rank(3, _lib.i64_array([100, 100, 100]), 1, one, 0.1, 0, 4, _lib.i32_array([60, 4, 4]), o,
                            ptr3, one, r3, None, one, big, None) == 6
     assert L.adaptive_rank(3, d3, 1, one, 0.1, 0, 4, ks, o, ptr3, one, r3, None, one, 1, None) == 2
+    # the three-piece split form is not an adaptive input form
+    assert L.adaptive_rank(3, d3, _lib.RH_F32_BF16X3, one, 0.1, 1, 4, ks, o, ptr3, one, r3, None, one, big,
+                           None) == 1
+    assert "dense input form" in _err(L)
     # sparse sketch and SP-STHOSVD (Alg. 6)
     assert L.rhosvd_sketch_coo(3, d3, -1, ptr3, one, 0, 4, 0, 0, 1, one, one, big, None) == 1
     assert L.rhosvd_sketch_coo(3, d3, 10, ptr3, one, 3, 4, 0, 0, 1, one, one, big, None) == 1
