@@ -26,7 +26,8 @@ def L():
 def _declared():
     text = open(os.path.join(ROOT, "include", "rhosvd.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:rh_status|size_t|const char\*|void|uint64_t|int32_t)\s+(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:rh_status|size_t|const char\s*\*|void|uint64_t|int64_t|int32_t|double)\s+\**\s*(\w+)\s*\(",
+                       text, flags=re.M)
     return sorted(set(names))
 
 
@@ -34,6 +35,16 @@ def test_header_declares_the_entry_points():
     names = _declared()
     for n in ["rh_omega", "rhosvd_sketch", "rh_orthonormalize", "rsthosvd", "rh_last_error", "rh_version"]:
         assert n in names
+
+
+def test_binding_signatures_match_the_header():
+    # every entry point has its argument and return types in the binding's table (a size_t or int64_t
+    # result read through ctypes' default int would be truncated), and the table names nothing else
+    from paper_1905_07311_gb300 import _lib
+
+    declared = set(_declared())
+    assert len(declared) > 50
+    assert set(_lib.SIGNATURES) == declared
 
 
 def test_every_declared_symbol_is_exported(L):
