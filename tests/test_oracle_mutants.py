@@ -34,6 +34,10 @@ MUTANTS = [
      "fold(A.T @ unfold(X, n), n, shape)", TENSOR),
     ("multi_ttm_ignores_transpose", "oracle.tensor", "multi_ttm", "M.T if transpose else M", "M", TENSOR),
     ("rel_error_squared_norm", "oracle.tensor", "rel_error", "/ frob(X)", "/ frob(X) ** 2", TENSOR),
+    ("frob_drops_square_root", "oracle.tensor", "frob", "float(np.sqrt(", "float((", TENSOR),
+    ("tucker_full_transposed_factors", "oracle.tensor", "tucker_full",
+     "[np.asarray(A, dtype=np.float64) for A in factors]",
+     "[np.asarray(A, dtype=np.float64)[::-1] for A in factors]", TENSOR),
     # Omega stream (Philox4x32-10, Box-Muller)
     ("philox_key_words_swapped", "oracle.rng", "philox4x32_10", "(hi1 ^ c1 ^ np.uint64(k0))",
      "(hi1 ^ c1 ^ np.uint64(k1))", RNG),
