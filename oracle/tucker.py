@@ -245,12 +245,21 @@ def adapt_range_finder(Gm, tol, b, p, omega_cols, cap=None):
     Q = np.zeros((m, 0))
     B = np.zeros((0, n))
     tol2 = float(tol) ** 2
+    gnorm = frob(Gm)
 
     def grow(Q, B, nb):
         k = Q.shape[1]
         Y = Gm @ omega_cols(k, k + nb)
         Y = Y - Q @ (Q.T @ Y)
-        Qi, _ = np.linalg.qr(Y)
+        Qi, Ri = np.linalg.qr(Y)
+        if np.abs(np.diag(Ri)).min() <= 1e-12 * gnorm:
+            # part of the block lies in span(Q) up to rounding: G is exactly rank deficient and Q
+            # already holds (part of) the block's range, so the QR of the rounding noise left by the
+            # projection would give directions that are not orthogonal to Q.  The block's columns
+            # are taken from a complete Householder QR of [Q, Y] instead (its columns k .. k + nb - 1
+            # are orthonormal to Q), which keeps the QB decomposition's Q orthonormal; B gains rows of
+            # (numerically) zero energy.
+            Qi = np.linalg.qr(np.hstack([Q, Y]), mode="complete")[0][:, k:k + nb]
         Qi = Qi - Q @ (Q.T @ Qi)
         Qi = canon_qr(Qi)
         Bi = Qi.T @ Gm

@@ -88,6 +88,8 @@ MUTANTS = [
      "np.sum(s[r:] ** 2)", TUCKER),
     ("adaptive_no_reorthogonalisation", "oracle.tucker", "adapt_range_finder", "Y = Y - Q @ (Q.T @ Y)", "Y = Y",
      TUCKER),
+    ("adaptive_no_basis_completion", "oracle.tucker", "adapt_range_finder",
+     "if np.abs(np.diag(Ri)).min() <= 1e-12 * gnorm:", "if False:", TUCKER),
     ("adaptive_tolerance_scaling", "oracle.tucker", "adaptive_rsthosvd", "/ math.sqrt(d)", "/ d", TUCKER),
     ("adaptive_rhosvd_tolerance_scaling", "oracle.tucker", "adaptive_rhosvd", "/ math.sqrt(d)", "/ d", TUCKER),
     # Sec. 5 (selections, SP-STHOSVD, SP-HOSVD, post-processing)

@@ -336,3 +336,31 @@ def test_sp_bound_of_a_superdiagonal_tensor():
         X[k, k, k] = 2.0 ** -k
     assert abs(tucker.sp_bound(X, [2, 2, 2], 2) - 298.5180588273678) < 1e-9
     assert abs(tucker.randomized_bound(X, [2, 2, 2], 2) - math.sqrt(3 * 3 * 0.08331298828125)) < 1e-12
+
+
+def test_adaptive_on_exactly_rank_deficient_unfoldings():
+    # X(k, k, k) = 2^-k, k = 0..7, in a 10 x 9 x 8 array: the unfoldings have rank 8 < I_1 = 10, and
+    # after the first truncation Alg. 5's next unfolding has rank 5 < I_2 = 9, so the oversampling
+    # columns fall inside the range already found.  The range finder's Q must stay orthonormal there:
+    # both algorithms keep the hand-computed rank 5 per mode (the superdiagonal case above), with
+    # orthonormal factors and the error sqrt(sum_{k >= 5} 4^-k) / ||X||
+    X = np.zeros((10, 9, 8))
+    for k in range(8):
+        X[k, k, k] = 2.0 ** -k
+    want = math.sqrt((4.0 ** -5 + 4.0 ** -6 + 4.0 ** -7) / ((1 - 4.0 ** -8) / 0.75))
+    for b in (1, 2, 3):
+        for out in (tucker.adaptive_rhosvd(X, 0.08, b, 8, seed=3), tucker.adaptive_rsthosvd(X, 0.08, b, 8, seed=3)):
+            assert [A.shape[1] for A in out["factors"]] == [5, 5, 5], b
+            for A in out["factors"]:
+                assert np.abs(A.T @ A - np.eye(A.shape[1])).max() < 1e-13
+            assert abs(rel_error(X, out["core"], out["factors"]) - want) < 1e-12
+    # the QB decomposition itself: an exactly rank-3 matrix with zero rows and oversampling past its
+    # rank; Q stays orthonormal and ||G - Q B|| vanishes
+    rs = np.random.default_rng(2)
+    G = np.zeros((12, 30))
+    G[:6] = rs.standard_normal((6, 3)) @ rs.standard_normal((3, 30))
+    omega = rs.standard_normal((30, 12))
+    A, info = tucker.adapt_range_finder(G, 1e-9 * np.linalg.norm(G), 2, 8, lambda c0, c1: omega[:, c0:c1])
+    assert info["ell"] > 3 and A.shape[1] == 3 and info["res2"] < 1e-24 * np.linalg.norm(G) ** 2
+    assert np.abs(A.T @ A - np.eye(3)).max() < 1e-13
+    assert np.linalg.norm(G - A @ (A.T @ G)) < 1e-12 * np.linalg.norm(G)
